@@ -1,0 +1,66 @@
+/*
+ * gsc_oracle.h -- declarations of the plain CPU oracle (test infrastructure only).
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may load
+ * this library. The product path (the CUDA library under the package) never does.
+ * This header is the oracle's own; it shares nothing with include/gsc.h.
+ */
+#ifndef GSC_ORACLE_H
+#define GSC_ORACLE_H
+#include <stdint.h>
+
+#define OR_SH 16
+#define OR_MODES 14
+
+typedef struct {
+  int32_t bands;       /* coefficients kept per Gaussian (1, 4, 9 or 16) */
+  int32_t bc7_blocks;  /* leading blocks coded BC7; the rest of the kept blocks are BC1 */
+  int64_t first_group; /* first group (in final order) of this stream */
+  int64_t n_groups;
+  int64_t byte_offset; /* offset of the stream in the block buffer */
+} or_stream;
+
+typedef struct {
+  int32_t n_streams;
+  int32_t format;      /* 1 BC1, 7 BC7, 0 rate-controlled */
+  int64_t n, n_groups, total_bytes;
+  uint64_t budget_bits, used_bits, lambda;
+  float scales[OR_SH];
+  uint32_t weights[OR_SH];
+  or_stream s[OR_MODES];
+} or_table;
+
+int or_scales(const float* sh, int64_t n, uint32_t permille, float* scales);
+uint8_t or_quant1(float x, float s);
+void or_quantise(const float* sh, int64_t n, const float* scales, uint8_t* q);
+uint32_t or_morton30(uint32_t x, uint32_t y, uint32_t z);
+uint32_t or_colour_key(uint32_t r, uint32_t g, uint32_t b);
+int or_plan(const float* pos, const uint8_t* q, int64_t n, int64_t group_size, int sort, int32_t* perm);
+void or_stage_group(const uint8_t* q, const int32_t* perm, int64_t g, uint8_t* tex /*[16 blocks][16 texels][3]*/);
+
+void or_bc1_palette(uint16_t c0, uint16_t c1, uint8_t* pal /*[4][4] RGBA*/);
+void or_bc1_decode(const uint8_t* blk, uint8_t* out /*[16][4]*/);
+uint64_t or_bc1_candidate_sse(const uint8_t* tex, uint16_t c0, uint16_t c1);
+uint64_t or_bc1_encode(const uint8_t* tex /*[16][3]*/, uint8_t* out /*[8]*/);
+
+int or_bc7_subset(int ns, int part, int t);
+int or_bc7_anchor(int ns, int part, int s);
+void or_bc7_decode(const uint8_t* blk, uint8_t* out /*[16][4]*/);
+int or_bc7_n_candidates(void);
+uint64_t or_bc7_candidate(const uint8_t* tex, int cand, uint8_t* out /*[16] or NULL*/);
+uint64_t or_bc7_encode(const uint8_t* tex /*[16][3]*/, uint8_t* out /*[16]*/);
+void or_encode_blocks(const uint8_t* tex, int64_t nblk, int format, uint8_t* out, uint64_t* sse);
+
+void or_mode_table(int32_t* bands, int32_t* bc7);
+void or_weights(const float* scales, uint32_t* w);
+int or_rate_choose(const uint64_t* D, int64_t ng, uint64_t lambda, uint8_t* mode);
+int or_rate_control(const uint64_t* D, int64_t ng, uint64_t budget, uint8_t* mode, uint64_t* lambda);
+int or_encode(const uint8_t* q, int64_t n, const int32_t* perm, const float* scales, int format,
+              uint32_t target_x4, uint8_t* blocks, int32_t* perm_out, or_table* t, uint64_t* dtab);
+int or_decode(const or_table* t, const uint8_t* blocks, const int32_t* perm, uint8_t* texels);
+
+void or_sh_basis(double x, double y, double z, double* Y /*[16]*/);
+void or_eval_sh(const uint8_t* texels, int64_t n, const float* scales, const float* pos,
+                const float* dirs, const float* cams, int V, double* out /*[V][n][3]*/,
+                double* abs_sum /*[V][n][3] or NULL*/);
+#endif

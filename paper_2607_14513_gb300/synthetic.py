@@ -1,0 +1,83 @@
+"""Seeded synthetic 3DGS scenes: the inputs both the CUDA path and the CPU oracle consume.
+
+This module only draws random numbers. It holds none of the codec's arithmetic
+(no scaling, quantisation, ordering, block coding or SH evaluation), so it can be
+shared by the tests, the benchmark and the oracle without coupling them.
+
+What is generated stands in for the trained scenes of the paper's experiments
+(Sec. V-A: bicycle, bonsai, garden), which are not available here:
+
+* positions ``p`` in [0, 1]^3, drawn from a mixture of ``clusters`` isotropic
+  Gaussians (centres uniform in [0.1, 0.9]^3, sigma 0.05, clipped to the cube);
+  each Gaussian's cluster is drawn independently, so storage order is not
+  spatially coherent;
+* premultiplied SH colour coefficients ``H~ = mu H`` (Sec. II, Eq. premult),
+  shape [N, 16, 3] float32, coefficient k = l*l + l + m:
+  DC (k = 0) ~ N(0, 0.8), band l >= 1 ~ N(0, 0.15 / (l + 1)) (standard deviations);
+  optionally a heavy-tailed fraction whose bands 2-3 are Laplace(0, 0.3);
+* view directions uniform on the unit sphere, and camera centres uniform on a
+  sphere of radius 2 around (0.5, 0.5, 0.5).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+SH_COEFFS = 16
+
+
+def band_of(k: int) -> int:
+    """SH band l of coefficient index k = l*l + l + m."""
+    l = 0
+    while (l + 1) * (l + 1) <= k:
+        l += 1
+    return l
+
+
+@dataclass
+class Scene:
+    pos: np.ndarray  # [N, 3] float32
+    sh: np.ndarray   # [N, 16, 3] float32, premultiplied by opacity
+
+
+def make_scene(n: int, seed: int, clusters: int = 8, heavy_frac: float = 0.0) -> Scene:
+    """Draw one synthetic scene of ``n`` Gaussians (see module docstring)."""
+    rng = np.random.default_rng(seed)
+    centres = rng.uniform(0.1, 0.9, size=(clusters, 3))
+    which = rng.integers(0, clusters, size=n)
+    pos = centres[which] + rng.normal(0.0, 0.05, size=(n, 3))
+    pos = np.clip(pos, 0.0, 1.0).astype(np.float32)
+    std = np.array([0.8] + [0.15 / (band_of(k) + 1) for k in range(1, SH_COEFFS)], dtype=np.float64)
+    sh = rng.standard_normal(size=(n, SH_COEFFS, 3)) * std[None, :, None]
+    if heavy_frac > 0.0:
+        heavy = rng.random(n) < heavy_frac
+        idx = np.nonzero(heavy)[0]
+        k_hi = np.arange(4, SH_COEFFS)  # bands 2 and 3
+        sh[np.ix_(idx, k_hi, np.arange(3))] = rng.laplace(0.0, 0.3, size=(idx.size, k_hi.size, 3))
+    return Scene(pos=pos, sh=sh.astype(np.float32))
+
+
+def make_dirs(v: int, seed: int) -> np.ndarray:
+    """``v`` unit view directions, uniform on the sphere, [V, 3] float32."""
+    rng = np.random.default_rng(seed)
+    d = rng.standard_normal(size=(v, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return d.astype(np.float32)
+
+
+def make_cams(v: int, seed: int, radius: float = 2.0) -> np.ndarray:
+    """``v`` camera centres uniform on a sphere of ``radius`` around the cube centre, [V, 3] float32."""
+    return (0.5 + radius * make_dirs(v, seed).astype(np.float64)).astype(np.float32)
+
+
+# The benchmark configurations, by what they are.
+TINY = dict(n=4096, seed=1001, clusters=8, heavy_frac=0.0)              # 4,096 Gaussians, BC1, 16 shared dirs
+MEDIUM = dict(n=262144, seed=1002, clusters=8, heavy_frac=0.0)          # 262,144 Gaussians, BC1/BC7/rate
+SCENE = dict(n=3000000, seed=1003, clusters=64, heavy_frac=0.10)        # 3M Gaussians, 64 clusters, 10% heavy tail
+
+
+def batch_sizes(n_scenes: int, seed: int, lo: int, hi: int) -> np.ndarray:
+    """Scene sizes log-uniform in [lo, hi] (batched and served workloads)."""
+    rng = np.random.default_rng(seed)
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_scenes)).astype(np.int64)

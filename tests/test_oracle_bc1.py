@@ -1,0 +1,182 @@
+"""Pins of the oracle's BC1 decoder and encoder (Sec. III-A with P = 16, Q = 2 on 4x4
+blocks; Sec. III-B, the D3D BC1 format).
+
+The format fixes: two RGB565 endpoints (little-endian), 2-bit indices with texel t at
+bits 2t, the four-colour mode when c0 > c1 as unsigned 16-bit values, otherwise three
+colours plus transparent black. It leaves the rounding of the interior entries to a
+tolerance; the reading is the GB300 texture unit's rule, pinned bit for bit against
+the texture unit in the GPU tests and bounded here.
+"""
+import numpy as np
+import pytest
+
+ex5 = lambda v: (v << 3) | (v >> 2)
+ex6 = lambda v: (v << 2) | (v >> 4)
+
+
+def _blk(c0, c1, idx):
+    return np.array([c0 & 255, c0 >> 8, c1 & 255, c1 >> 8, idx & 255, (idx >> 8) & 255, (idx >> 16) & 255, idx >> 24],
+                    np.uint8)
+
+
+def test_hand_built_four_colour_block(O):
+    # red (31,0,0) vs blue (0,0,31); texel t uses index t % 4 (0xE4 = 11 10 01 00)
+    out = O.bc1_decode(_blk(0xF800, 0x001F, 0xE4E4E4E4))
+    expect = {0: (255, 0, 0, 255), 1: (0, 0, 255, 255), 2: (170, 0, 85, 255), 3: (85, 0, 170, 255)}
+    for t in range(16):
+        assert tuple(out[t]) == expect[t % 4]
+    # index layout: only texel 9 uses index 1
+    out = O.bc1_decode(_blk(0xF800, 0x001F, 1 << 18))
+    assert tuple(out[9]) == (0, 0, 255, 255) and all(tuple(out[t]) == (255, 0, 0, 255) for t in range(16) if t != 9)
+
+
+def test_hand_built_three_colour_block(O):
+    out = O.bc1_decode(_blk(0x001F, 0xF800, 0xE4E4E4E4))       # c0 < c1: three colours + transparent black
+    expect = {0: (0, 0, 255, 255), 1: (255, 0, 0, 255), 2: (127, 0, 127, 255), 3: (0, 0, 0, 0)}
+    for t in range(16):
+        assert tuple(out[t]) == expect[t % 4]
+    out = O.bc1_decode(_blk(0x1234, 0x1234, 0xFFFFFFFF))       # c0 == c1 is the three-colour mode too
+    assert all(tuple(out[t]) == (0, 0, 0, 0) for t in range(16))
+
+
+def _third_table(O, ch):
+    """2/3 x + 1/3 y for every code pair of channel ch, read from four-colour palettes."""
+    bits = 6 if ch == 1 else 5
+    sh = {0: 11, 1: 5, 2: 0}[ch]
+    lim = 1 << bits
+    tab = np.zeros((lim, lim), np.int64)
+    for x in range(lim):
+        for y in range(lim):
+            if ch != 0:                       # R decides the mode: c0 > c1 always
+                tab[x, y] = O.bc1_palette((31 << 11) | (x << sh), y << sh)[2, ch]
+            elif x >= y:                      # G breaks the tie in favour of c0
+                tab[x, y] = O.bc1_palette((x << 11) | (63 << 5), y << 11)[2, 0]
+            else:                             # entry 3 is 2/3 c1 + 1/3 c0
+                tab[x, y] = O.bc1_palette((y << 11) | (63 << 5), x << 11)[3, 0]
+    return tab
+
+
+def test_interpolation_reading_properties(O):
+    # over every code pair: diagonal = expansion, monotone, within the measured distance
+    # of the exact thirds; R and B (both 5-bit) follow one rule
+    t_r, t_g, t_b = _third_table(O, 0), _third_table(O, 1), _third_table(O, 2)
+    assert np.array_equal(t_r, t_b)
+    for tab, ex, bound in [(t_b, ex5, 0.67), (t_g, ex6, 5.34)]:
+        n = tab.shape[0]
+        X = ex(np.arange(n))[:, None].astype(np.float64)
+        Y = ex(np.arange(n))[None, :].astype(np.float64)
+        assert np.all(np.abs(tab - (2 * X + Y) / 3.0) <= bound)
+        assert np.all(np.diff(tab, axis=0) >= 0) and np.all(np.diff(tab, axis=1) >= 0)
+        assert np.array_equal(np.diag(tab), ex(np.arange(n)))
+    # endpoints are the plain expansions; entry 3 mirrors entry 2 (G channel, four-colour mode)
+    for x in range(0, 64, 7):
+        for y in range(0, 64, 5):
+            pal = O.bc1_palette((31 << 11) | (x << 5), y << 5)
+            assert pal[0, 1] == ex6(x) and pal[1, 1] == ex6(y)
+            assert pal[3, 1] == t_g[y, x] and pal[3, 3] == 255
+
+
+def test_three_colour_midpoint_properties(O):
+    for ch, bits, ex in [(1, 6, ex6), (2, 5, ex5)]:
+        sh = {1: 5, 2: 0}[ch]
+        lim = 1 << bits
+        half = np.zeros((lim, lim), np.int64)
+        for x in range(lim):
+            for y in range(lim):
+                pal = O.bc1_palette(x << sh, (31 << 11) | (y << sh))     # c0 < c1
+                half[x, y] = pal[2, ch]
+                assert tuple(pal[3]) == (0, 0, 0, 0)
+        X = ex(np.arange(lim))[:, None].astype(np.float64)
+        Y = ex(np.arange(lim))[None, :].astype(np.float64)
+        assert np.all(np.abs(half - (X + Y) / 2.0) <= 0.5)
+        assert np.array_equal(np.diag(half), ex(np.arange(lim)))
+
+
+def _const_block(rgb):
+    return np.tile(np.array(rgb, np.uint8), (16, 1))
+
+
+def _best_const_sse(O, rgb):
+    """Brute force over every per-channel code pair of the four-colour two-thirds entry
+    (which also covers the endpoints, a == b)."""
+    tot = 0
+    for ch, bits in [(0, 5), (1, 6), (2, 5)]:
+        best = None
+        sh = {0: 11, 1: 5, 2: 0}[ch]
+        for a in range(1 << bits):
+            for b in range(1 << bits):
+                c0 = a << sh
+                c1 = b << sh
+                # force the four-colour mode with a top channel that does not affect this one
+                if ch != 0:
+                    c0 |= 31 << 11
+                else:
+                    c0 |= 63 << 5
+                v = int(O.bc1_palette(c0, c1)[2, ch])
+                e = (v - int(rgb[ch])) ** 2
+                best = e if best is None else min(best, e)
+        tot += best
+    return 16 * tot
+
+
+def test_constant_blocks_reach_brute_force(O):
+    rng = np.random.default_rng(5)
+    colours = [(0, 0, 0), (255, 255, 255), (128, 128, 128), (8, 4, 8), (255, 0, 0), (1, 2, 3), (254, 253, 252)]
+    colours += [tuple(c) for c in rng.integers(0, 256, size=(6, 3)).tolist()]
+    for rgb in colours:
+        blk = np.zeros(8, np.uint8)
+        out, sse = O.encode_blocks(_const_block(rgb)[None], 1, threads=1)
+        assert int(sse[0]) == _best_const_sse(O, rgb), rgb
+        dec = O.bc1_decode(out[0])
+        assert int(((dec[:, :3].astype(int) - np.array(rgb)) ** 2).sum()) == int(sse[0])
+
+
+def test_exact_565_colours_round_trip(O):
+    rng = np.random.default_rng(6)
+    for _ in range(40):
+        r, g, b = ex5(rng.integers(0, 32)), ex6(rng.integers(0, 64)), ex5(rng.integers(0, 32))
+        out, sse = O.encode_blocks(_const_block((r, g, b))[None], 1, threads=1)
+        assert sse[0] == 0
+    # two exact colours anywhere in the block: least squares lands on them exactly
+    for _ in range(40):
+        cols = [(ex5(rng.integers(0, 32)), ex6(rng.integers(0, 64)), ex5(rng.integers(0, 32))) for _ in range(2)]
+        if cols[0] == cols[1]:
+            continue
+        tex = np.array([cols[rng.integers(0, 2)] for _ in range(16)], np.uint8)
+        tex[0], tex[1] = cols[0], cols[1]
+        out, sse = O.encode_blocks(tex[None], 1, threads=1)
+        assert sse[0] == 0
+
+
+def test_encoder_output_is_canonical_and_consistent(O):
+    rng = np.random.default_rng(8)
+    tex = rng.integers(0, 256, size=(300, 16, 3)).astype(np.uint8)
+    tex[:100] = (tex[:100] // 32) * 32 + 5         # coarser content
+    blocks, sse = O.encode_blocks(tex, 1, threads=4)
+    for i in range(tex.shape[0]):
+        c0 = int(blocks[i, 0]) | (int(blocks[i, 1]) << 8)
+        c1 = int(blocks[i, 2]) | (int(blocks[i, 3]) << 8)
+        assert c0 > c1 or (c0 == c1 and not blocks[i, 4:].any())
+        dec = O.bc1_decode(blocks[i])
+        assert int(((dec[:, :3].astype(int) - tex[i].astype(int)) ** 2).sum()) == int(sse[i])
+        assert O.bc1_candidate_sse(tex[i], c0, c1) == sse[i]
+
+
+def test_encoder_against_local_brute_force(O):
+    # exhaustive search over all endpoint pairs in a +-1 code box around the encoder's result:
+    # the encoder's neighbourhood search must leave no single-channel step that improves
+    rng = np.random.default_rng(9)
+    base = rng.integers(40, 200, size=3)
+    tex = np.clip(base[None, :] + rng.integers(-12, 13, size=(16, 3)), 0, 255).astype(np.uint8)
+    blocks, sse = O.encode_blocks(tex[None], 1, threads=1)
+    c0 = int(blocks[0, 0]) | (int(blocks[0, 1]) << 8)
+    c1 = int(blocks[0, 2]) | (int(blocks[0, 3]) << 8)
+    best = int(sse[0])
+    for ep in range(2):
+        for sh, mask in [(11, 31), (5, 63), (0, 31)]:
+            for d in (-1, 1):
+                cc = [c0, c1]
+                v = ((cc[ep] >> sh) & mask) + d
+                if 0 <= v <= mask:
+                    cc[ep] = (cc[ep] & ~(mask << sh)) | (v << sh)
+                    assert O.bc1_candidate_sse(tex, cc[0], cc[1]) >= best

@@ -1,0 +1,119 @@
+"""Pins of the oracle's rate control (Sec. IV-B: several fixed-rate bitstreams give a
+variable number of bits per primitive while keeping random access; Figs. SetupC/SetupD:
+zero high-order coefficients are not stored; Table I rate arithmetic).
+
+The paper gives the mechanism but no allocation algorithm; the integer Lagrangian
+choice among 14 group modes is this codec's reading. The pins are the rate arithmetic
+the paper prints, an exhaustive knapsack on tiny instances, monotonicity and the budget.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from paper_2607_14513_gb300 import synthetic as S
+
+
+def test_mode_rates_match_table_one_arithmetic(O):
+    b, j = O.mode_table()
+    assert list(zip(b.tolist(), j.tolist())) == [(1, 0), (1, 1), (4, 0), (4, 1), (4, 4), (9, 0), (9, 1), (9, 4),
+                                                 (9, 9), (16, 0), (16, 1), (16, 4), (16, 9), (16, 16)]
+    bytes_per_gaussian = {(int(bb), int(jj)): (16 * jj + 8 * (bb - jj)) / 16 for bb, jj in zip(b, j)}
+    # Table I, Setup D rows: all BC1 -> 8 B, BC7 first + BC1 rest -> 8.5 B, all BC7 -> 16 B per primitive
+    # (8 B per BC1 block, 16 B per BC7 block; the table prints 8.5 / 9 / 17, a uniform 17/16 factor)
+    assert bytes_per_gaussian[(16, 0)] == 8.0
+    assert bytes_per_gaussian[(16, 1)] == 8.5
+    assert bytes_per_gaussian[(16, 16)] == 16.0
+    assert all(len({64 * (int(x) + int(y)) for x, y in zip(b, j)}) == 14 for _ in [0])   # rates are distinct
+
+
+def _rates(O):
+    b, j = O.mode_table()
+    return 64 * (b.astype(np.int64) + j.astype(np.int64))
+
+
+def _random_D(rng, ng):
+    # distortions that mostly fall with rate, with noise so the hull is non-trivial
+    R = np.array([1, 2, 4, 5, 8, 9, 10, 13, 18, 16, 17, 20, 25, 32], np.float64)
+    base = rng.uniform(1e3, 1e7, size=(ng, 1)) * np.exp(-R[None, :] * rng.uniform(0.05, 0.3, size=(ng, 1)))
+    return (base * rng.uniform(0.7, 1.3, size=(ng, 14))).astype(np.uint64)
+
+
+def test_lagrangian_choice_is_on_the_hull(O):
+    # exhaustive knapsack over 14^4 assignments: at lambda*, no assignment of no more total
+    # rate has lower total distortion
+    rng = np.random.default_rng(21)
+    R = _rates(O)
+    for trial in range(6):
+        ng = 4
+        D = _random_D(rng, ng)
+        budget = int(rng.integers(R.min() * ng, R.max() * ng))
+        rc, mode, lam = O.rate_control(D, budget)
+        assert rc == 0
+        base = O.rate_choose(D, lam)
+        r_star = int(R[base].sum())
+        d_star = int(D[np.arange(ng), base].sum())
+        combos = np.array(list(itertools.product(range(14), repeat=ng)))
+        rr = R[combos].sum(axis=1)
+        dd = D[np.arange(ng)[None, :], combos].astype(np.float64).sum(axis=1)
+        assert dd[rr <= r_star].min() >= d_star - 1e-6 * d_star
+        # lambda* is the smallest feasible multiplier
+        assert r_star <= budget
+        if lam > 0:
+            assert int(R[O.rate_choose(D, lam - 1)].sum()) > budget
+        # the fill step stays within the budget and only raises rates
+        used = int(R[mode].sum())
+        assert r_star <= used <= budget
+        assert np.all(R[mode] >= R[base])
+
+
+def test_rate_monotone_in_lambda(O):
+    rng = np.random.default_rng(22)
+    R = _rates(O)
+    D = _random_D(rng, 200)
+    lams = [0] + sorted(set(int(x) for x in np.exp(rng.uniform(0, 60, size=60))))
+    tot = [int(R[O.rate_choose(D, l)].sum()) for l in lams]
+    assert all(a >= b for a, b in zip(tot, tot[1:]))
+    assert int(R[O.rate_choose(D, 1 << 62)].sum()) == 64 * 200      # huge lambda: cheapest mode everywhere
+
+
+def test_budget_infeasible_and_exact(O):
+    rng = np.random.default_rng(23)
+    D = _random_D(rng, 10)
+    rc, _, _ = O.rate_control(D, 64 * 10 - 1)
+    assert rc != 0
+    rc, mode, _ = O.rate_control(D, 2048 * 10)
+    assert rc == 0 and np.all(mode == 13)               # everything affordable: the all-BC7 mode wins
+    # groups whose distortion does not depend on the mode take the cheapest mode
+    rc, mode, lam = O.rate_control(np.full((5, 14), 1000, np.uint64), 10_000)
+    assert rc == 0 and np.all(mode == 0)
+
+
+@pytest.mark.parametrize("fmt,bpt", [(1, 4), (7, 8)])
+def test_forced_formats_hit_their_rate(O, fmt, bpt):
+    sc = S.make_scene(512, 31)
+    r = O.full_encode(sc.pos, sc.sh, fmt)
+    t = r["table"]
+    assert t.used_bits == bpt * 16 * 512
+    assert t.total_bytes == (16 if fmt == 7 else 8) * 16 * 512 // 16
+
+
+@pytest.mark.parametrize("target_x4", [12, 16, 24, 32])
+def test_rate_targets_respect_budget(O, target_x4):
+    n = 480                                      # 30 groups, not a power of two
+    sc = S.make_scene(n, 32)
+    r = O.full_encode(sc.pos, sc.sh, 0, target_x4=target_x4)
+    t = r["table"]
+    budget = target_x4 * 4 * n
+    assert t.budget_bits == budget
+    assert t.used_bits <= budget
+    # within one group's largest upgrade of the budget
+    assert t.used_bits > budget - 64 * 32
+    # streams: consecutive, by mode id, offsets add up
+    off, g = 0, 0
+    for i in range(t.n_streams):
+        s = t.s[i]
+        assert s.first_group == g and s.byte_offset == off
+        g += s.n_groups
+        off += s.n_groups * (16 * s.bc7_blocks + 8 * (s.bands - s.bc7_blocks))
+    assert g == t.n_groups and off == t.total_bytes
