@@ -1,0 +1,170 @@
+/*
+ * gsc.h -- C ABI of the GB300 block-texture codec for 3DGS spherical-harmonic colour
+ * (Said & Rauwendaal, "Compression of 3D Gaussian Splatting Data Using GPU-friendly
+ * Graphics Texture Coding").
+ *
+ * Problem statement (Sec. II and Sec. V-A): a scene holds n Gaussians with centres
+ * p in R^3 and opacity-premultiplied SH colour coefficients H~ = mu H (Eq. premult),
+ * 16 RGB coefficients each (k = l*l + l + m, degree 3). The codec quantises H~ to
+ * 8-bit texels, reorders the Gaussians by colour inside spatial groups (Sec. III-C),
+ * packs coefficient k of 16 Gaussians into one 4x4 block (Sec. IV-B, Fig. SetupD),
+ * codes every block with BC1 (8 bytes) or BC7 (16 bytes) (Sec. III-B), optionally
+ * spreading groups over several fixed-rate streams (Sec. IV-B), and decodes the
+ * blocks back, evaluating the view-dependent colour c(f) = H w(f - p) (Sec. II).
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are device pointers on the context's device; h_* are host
+ *    pointers. The caller owns every buffer and the stream; the library owns only the
+ *    context. Scratch memory is passed in as d_ws / ws_bytes (size from
+ *    gsc_workspace_bytes); the library allocates no device memory on these paths,
+ *    except gsc_decode_tex, which builds CUDA arrays for texture objects.
+ *  - stream is a cudaStream_t (NULL = legacy default stream). Calls are asynchronous
+ *    on that stream unless stated otherwise.
+ *  - Argument errors are returned synchronously and nothing is launched. Errors the
+ *    device detects are recorded in the context and returned by gsc_ctx_sync.
+ *  - Arrays are C-contiguous: float positions [n][3]; float SH [n][16][3] with the
+ *    RGB triple innermost; texels uint8 [n][16][3]; perm int32 [n_groups * 16].
+ *  - There is no CPU fallback: without a usable GB300 every call returns
+ *    GSC_ERR_UNSUPPORTED.
+ */
+#ifndef GSC_H
+#define GSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GSC_OK = 0,
+  GSC_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or parameter */
+  GSC_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  GSC_ERR_OOM = 3,         /* workspace too small */
+  GSC_ERR_BUDGET = 4,      /* rate target below the cheapest coding of the scene */
+  GSC_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  GSC_ERR_UNSUPPORTED = 6, /* no usable sm_103 device, or a feature the device lacks */
+  GSC_ERR_DEVICE = 7       /* an index check inside a kernel failed (record in the context) */
+} gsc_status;
+
+typedef enum { GSC_FMT_RATE = 0, GSC_FMT_BC1 = 1, GSC_FMT_BC7 = 7 } gsc_format;
+
+typedef enum {
+  GSC_OUT_VIEW_MAJOR = 0,  /* rgb [V][n][3], original Gaussian order (through the inverse permutation) */
+  GSC_OUT_SLOT_ORDER = 1,  /* rgb [V][n_groups*16][3], slot order, padding slots written as 0 */
+  GSC_OUT_GAUSS_MAJOR = 2  /* rgb [n][V][3], original Gaussian order */
+} gsc_out_order;
+
+typedef struct gsc_ctx gsc_ctx;
+
+/* Reorder and scale parameters (Sec. III-C, Sec. V-A). */
+typedef struct {
+  int64_t n;                  /* number of Gaussians, 0 <= n < 2^31 - 16 */
+  int64_t group_size;         /* spatial chunk G for the colour sort; multiple of 16; 0 = whole scene */
+  int32_t sort;               /* 0: keep the original order; 1: colour sort inside spatial chunks */
+  uint32_t quantile_permille; /* coverage of [-0.5, 0.5] after scaling, 1..1000 (paper: 995) */
+} gsc_plan_params;
+
+/* Coding parameters (Sec. III-B, Sec. IV-B). */
+typedef struct {
+  int32_t format;         /* gsc_format: BC1 or BC7 in every block, or rate-controlled */
+  uint32_t target_bpt_x4; /* rate target in quarter bits per coefficient texel (e.g. 12, 16, 24, 32) */
+} gsc_encode_params;
+
+/* One fixed-rate stream: every group in it keeps `bands` coefficients, the first
+ * `bc7_blocks` coded BC7 (16 B) and the rest BC1 (8 B); coefficients not kept
+ * decode to zero (texel 128). Group bytes = 16 * bc7_blocks + 8 * (bands - bc7_blocks). */
+typedef struct {
+  int32_t bands, bc7_blocks;
+  int64_t first_group, n_groups, byte_offset;
+} gsc_stream;
+
+/* Everything a decoder needs besides the blocks and the permutation. */
+typedef struct {
+  int32_t n_streams, format;
+  int64_t n, n_groups, total_bytes;
+  uint64_t budget_bits, used_bits, lambda;
+  float scales[16];     /* s_k: x' = (q - 128) / 255 * s_k */
+  uint32_t weights[16]; /* w_k used by the rate control */
+  gsc_stream s[14];
+} gsc_stream_table;
+
+/* Context on one device (made current by every call). */
+gsc_status gsc_ctx_create(gsc_ctx** out, int device);
+gsc_status gsc_ctx_destroy(gsc_ctx* ctx);
+/* Waits for `stream` and returns the first error a kernel recorded since the last
+ * sync (then clears it). */
+gsc_status gsc_ctx_sync(gsc_ctx* ctx, void* stream);
+const char* gsc_status_string(gsc_status s);
+
+/* Bytes of scratch that gsc_plan_reorder and gsc_encode need for n Gaussians. */
+size_t gsc_workspace_bytes(int64_t n, const gsc_encode_params* ep);
+
+/* Sec. V-A and Sec. III-C. Computes the 16 scales s_k = 2 a_k, a_k the
+ * ceil(permille * 3n / 1000)-th smallest |H~[:, k, :]| (exact order statistic; 1 if
+ * zero), quantises the DC coefficient, and writes the slot order
+ * d_perm[s] = original index of slot s, s < n_groups * 16 (padding slots = -1).
+ * Slot order: sort = 1 ranks Gaussians by 30-bit Morton code of the bounding-box
+ * grid (10 bits per axis; original index breaks ties), cuts the ranks into chunks
+ * of group_size, and orders by (chunk, 24-bit RGB bit interleave of the DC texel,
+ * rank). d_pos [n][3] float, d_sh [n][16][3] float, d_scales [16] float. */
+gsc_status gsc_plan_reorder(gsc_ctx* ctx, const float* d_pos, const float* d_sh, const gsc_plan_params* pp,
+                            int32_t* d_perm, float* d_scales, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Sec. V-A: q = clamp(128 + rint(fl(fl(x / s_k) * 255)), 0, 255), round half to even.
+ * d_sh [n][16][3] float -> d_q [n][16][3] uint8. */
+gsc_status gsc_quantise(gsc_ctx* ctx, const float* d_sh, int64_t n, const float* d_scales, uint8_t* d_q, void* stream);
+
+/* Sec. IV-B (Fig. SetupD), Sec. III-B, Sec. IV-B rate control. Group g = slots
+ * 16g..16g+15; block k of group g holds coefficient k of those 16 Gaussians, texel t
+ * in raster order = slot 16g + t (a padding slot repeats the group's last valid
+ * slot). BC1 / BC7 formats code all 16 blocks of every group; GSC_FMT_RATE picks one
+ * of 14 stream modes per group under the budget floor(target_bpt_x4 * 4 * n) bits.
+ * d_blocks receives the streams back to back (capacity n_groups * 256 bytes),
+ * d_perm_out the final slot order, *h_table the stream table. Synchronises `stream`
+ * before returning in GSC_FMT_RATE (the table depends on device results); returns
+ * GSC_ERR_BUDGET if even the cheapest mode everywhere exceeds the budget. */
+gsc_status gsc_encode(gsc_ctx* ctx, const float* d_sh, int64_t n, const int32_t* d_perm, const float* d_scales,
+                      const gsc_encode_params* ep, uint8_t* d_blocks, int32_t* d_perm_out, gsc_stream_table* h_table,
+                      void* d_ws, size_t ws_bytes, void* stream);
+
+/* Sec. I and III-A (random access: block = stream offset + index x block size) and
+ * Sec. II. Decodes every stream to texels d_texels [n][16][3] uint8 in original order
+ * (through the inverse permutation); coefficients a stream does not keep are 128. */
+gsc_status gsc_decode(gsc_ctx* ctx, const gsc_stream_table* table, const uint8_t* d_blocks, const int32_t* d_perm,
+                      uint8_t* d_texels, void* stream);
+
+/* Sec. II, c(f) = H w(f - p): fused decode and SH evaluation in FP32.
+ * x'_{k} = (q - 128) / 255 * s_k; rgb = sum_k x'_k Y_k(d), with real SH to degree 3
+ * (k = l*l + l + m, Condon-Shortley phase), no offset and no clamp. Directions: either
+ * d_dirs [V][3] unit vectors shared by all Gaussians, or d_cams [V][3] camera centres
+ * with d = (cam - p) / |cam - p| from d_pos [n][3] ((0, 0, 1) if the camera sits on p).
+ * Exactly one of d_dirs, d_cams is non-NULL. 1 <= V <= 64. out_order: gsc_out_order. */
+gsc_status gsc_decode_eval_sh(gsc_ctx* ctx, const gsc_stream_table* table, const uint8_t* d_blocks,
+                              const int32_t* d_perm, const float* d_dirs, const float* d_pos, const float* d_cams,
+                              int32_t V, int32_t out_order, float* d_rgb, void* stream);
+
+/* Same output as gsc_decode, sampled through CUDA BC1/BC7 texture objects (the GPU's
+ * fixed-function block decoders, Sec. I): blocks are gathered into 2-D CUDA arrays
+ * and read with point sampling; texel = rint(255 * f). Allocates and frees CUDA
+ * arrays and staging buffers; synchronises `stream`. */
+gsc_status gsc_decode_tex(gsc_ctx* ctx, const gsc_stream_table* table, const uint8_t* d_blocks,
+                          const int32_t* d_perm, uint8_t* d_texels, void* stream);
+
+/* Block-level codecs (Sec. III-B): nblk independent 4x4 blocks.
+ * d_tex [nblk][16][3] uint8 -> d_out [nblk][8 or 16] bytes; d_sse [nblk] (optional)
+ * receives each block's squared error. format: GSC_FMT_BC1 or GSC_FMT_BC7. */
+gsc_status gsc_encode_blocks(gsc_ctx* ctx, const uint8_t* d_tex, int64_t nblk, int32_t format, uint8_t* d_out,
+                             uint64_t* d_sse, void* stream);
+/* d_blocks [nblk][8 or 16] -> d_rgba [nblk][16][4] uint8 (software decoder). */
+gsc_status gsc_decode_blocks(gsc_ctx* ctx, const uint8_t* d_blocks, int64_t nblk, int32_t format, uint8_t* d_rgba,
+                             void* stream);
+/* Same through a texture object; synchronises `stream`. */
+gsc_status gsc_decode_blocks_tex(gsc_ctx* ctx, const uint8_t* d_blocks, int64_t nblk, int32_t format,
+                                 uint8_t* d_rgba, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

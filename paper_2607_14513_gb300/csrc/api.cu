@@ -1,0 +1,281 @@
+// api.cu -- the C ABI declared in include/gsc.h: context, argument checks, orchestration.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "gsc_internal.cuh"
+
+#define PINNED_BYTES 65536
+
+static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+extern "C" const char* gsc_status_string(gsc_status s) {
+  switch (s) {
+    case GSC_OK: return "ok";
+    case GSC_ERR_INVALID_ARG: return "invalid argument";
+    case GSC_ERR_CUDA: return "CUDA runtime error";
+    case GSC_ERR_OOM: return "workspace too small";
+    case GSC_ERR_BUDGET: return "rate target below the cheapest coding of the scene";
+    case GSC_ERR_TIMEOUT: return "device-side wait timed out";
+    case GSC_ERR_UNSUPPORTED: return "no usable sm_103 device";
+    case GSC_ERR_DEVICE: return "device-side check failed";
+    default: return "unknown status";
+  }
+}
+
+extern "C" gsc_status gsc_ctx_create(gsc_ctx** out, int device) {
+  if (!out) return GSC_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return GSC_ERR_UNSUPPORTED;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return GSC_ERR_UNSUPPORTED;
+  if (!(prop.major == 10 && prop.minor == 3)) return GSC_ERR_UNSUPPORTED;  // kernels are built for sm_103a only
+  if (cudaSetDevice(device) != cudaSuccess) return GSC_ERR_CUDA;
+  gsc_ctx* c = (gsc_ctx*)calloc(1, sizeof(gsc_ctx));
+  if (!c) return GSC_ERR_OOM;
+  c->device = device;
+  c->sm_count = prop.multiProcessorCount;
+  cudaError_t e = cudaMalloc(&c->d_status, 2 * sizeof(int));
+  if (e == cudaSuccess) { c->d_diag = c->d_status + 1; e = cudaMemset(c->d_status, 0, 2 * sizeof(int)); }
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_pinned, PINNED_BYTES);
+  c->h_pinned_bytes = PINNED_BYTES;
+  if (e == cudaSuccess) e = bc1_init_tables();
+  if (e == cudaSuccess) e = bc7_init_tables();
+  if (e == cudaSuccess) e = decode_init_tables();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    if (c->d_status) cudaFree(c->d_status);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    free(c);
+    return GSC_ERR_CUDA;
+  }
+  *out = c;
+  return GSC_OK;
+}
+
+extern "C" gsc_status gsc_ctx_destroy(gsc_ctx* c) {
+  if (!c) return GSC_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  if (c->d_status) cudaFree(c->d_status);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  free(c);
+  return GSC_OK;
+}
+
+extern "C" gsc_status gsc_ctx_sync(gsc_ctx* c, void* stream) {
+  if (!c) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  GSC_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  int st[2] = {0, 0};
+  GSC_CUDA(cudaMemcpy(st, c->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st[0] != 0) {
+    GSC_CUDA(cudaMemset(c->d_status, 0, sizeof(st)));
+    return (gsc_status)st[0];
+  }
+  return GSC_OK;
+}
+
+extern "C" size_t gsc_workspace_bytes(int64_t n, const gsc_encode_params* ep) {
+  if (n < 0) return 0;
+  size_t b = plan_ws_bytes(n);
+  if (ep && ep->format == GSC_FMT_RATE) {
+    size_t r = rate_ws_bytes(ceil_div64(n, 16));
+    if (r > b) b = r;
+  }
+  return b;
+}
+
+static bool n_ok(int64_t n) { return n >= 0 && n < (int64_t)0x7FFFFFF0; }
+
+extern "C" gsc_status gsc_plan_reorder(gsc_ctx* c, const float* d_pos, const float* d_sh, const gsc_plan_params* pp,
+                                       int32_t* d_perm, float* d_scales, void* d_ws, size_t ws_bytes, void* stream) {
+  if (!c || !pp || !n_ok(pp->n)) return GSC_ERR_INVALID_ARG;
+  if (pp->group_size < 0 || pp->group_size % 16 != 0) return GSC_ERR_INVALID_ARG;
+  if (pp->quantile_permille == 0 || pp->quantile_permille > 1000) return GSC_ERR_INVALID_ARG;
+  if (pp->sort != 0 && pp->sort != 1) return GSC_ERR_INVALID_ARG;
+  if (!d_scales || (pp->n > 0 && (!d_sh || !d_perm || (pp->sort && !d_pos)))) return GSC_ERR_INVALID_ARG;
+  if (!aligned(d_sh, 16) || !aligned(d_ws, 256)) return GSC_ERR_INVALID_ARG;
+  if (pp->n > 0 && !d_ws) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  return plan_run(c, d_pos, d_sh, pp, d_perm, d_scales, d_ws, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" gsc_status gsc_quantise(gsc_ctx* c, const float* d_sh, int64_t n, const float* d_scales, uint8_t* d_q,
+                                   void* stream) {
+  if (!c || !n_ok(n) || !d_scales || (n > 0 && (!d_sh || !d_q))) return GSC_ERR_INVALID_ARG;
+  if (!aligned(d_sh, 16) || !aligned(d_q, 4)) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  GSC_CUDA(launch_quantise(d_sh, n, d_scales, d_q, (cudaStream_t)stream));
+  return GSC_OK;
+}
+
+static void host_weights(const float* scales, uint32_t* w) {
+  double mx = 0.0;
+  for (int k = 0; k < GSC_SH; k++) { double s = scales[k]; if (s * s > mx) mx = s * s; }
+  for (int k = 0; k < GSC_SH; k++) {
+    double s = scales[k];
+    double v = rint((s * s * 65536.0) / mx);
+    w[k] = v < 1.0 ? 1u : (uint32_t)v;
+  }
+}
+
+extern "C" gsc_status gsc_encode(gsc_ctx* c, const float* d_sh, int64_t n, const int32_t* d_perm,
+                                 const float* d_scales, const gsc_encode_params* ep, uint8_t* d_blocks,
+                                 int32_t* d_perm_out, gsc_stream_table* h_table, void* d_ws, size_t ws_bytes,
+                                 void* stream) {
+  if (!c || !ep || !h_table || !n_ok(n) || !d_scales) return GSC_ERR_INVALID_ARG;
+  if (ep->format != GSC_FMT_BC1 && ep->format != GSC_FMT_BC7 && ep->format != GSC_FMT_RATE) return GSC_ERR_INVALID_ARG;
+  if (ep->format == GSC_FMT_RATE && (ep->target_bpt_x4 == 0 || ep->target_bpt_x4 > 64)) return GSC_ERR_INVALID_ARG;
+  if (n > 0 && (!d_sh || !d_perm || !d_blocks || !d_perm_out)) return GSC_ERR_INVALID_ARG;
+  if (!aligned(d_sh, 16) || !aligned(d_blocks, 16) || !aligned(d_ws, 256)) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t ng = ceil_div64(n, 16);
+  memset(h_table, 0, sizeof(*h_table));
+  float* hs = reinterpret_cast<float*>(c->h_pinned);
+  GSC_CUDA(cudaMemcpyAsync(hs, d_scales, sizeof(float) * GSC_SH, cudaMemcpyDeviceToHost, st));
+  if (ep->format == GSC_FMT_RATE) {
+    if (n > 0 && !d_ws) return GSC_ERR_INVALID_ARG;
+    GSC_CUDA(cudaStreamSynchronize(st));
+    float scales[GSC_SH];
+    memcpy(scales, hs, sizeof(scales));
+    gsc_status s = GSC_OK;
+    if (n > 0) {
+      s = rate_run(c, d_sh, n, d_perm, d_scales, ep->target_bpt_x4, d_blocks, d_perm_out, h_table, d_ws, ws_bytes, st);
+    } else {
+      h_table->n_streams = GSC_MODES;
+      h_table->format = GSC_FMT_RATE;
+    }
+    memcpy(h_table->scales, scales, sizeof(scales));
+    return s;
+  }
+  if (ep->format == GSC_FMT_BC1) {
+    GSC_CUDA(launch_bc1_groups(d_sh, d_perm, d_scales, ng, d_blocks, nullptr, nullptr, st));
+  } else {
+    GSC_CUDA(launch_bc7_groups(d_sh, d_perm, d_scales, ng, d_blocks, nullptr, st));
+  }
+  if (ng > 0 && d_perm_out != d_perm)
+    GSC_CUDA(cudaMemcpyAsync(d_perm_out, d_perm, sizeof(int32_t) * ng * 16, cudaMemcpyDeviceToDevice, st));
+  GSC_CUDA(cudaStreamSynchronize(st));
+  const int bpb = ep->format == GSC_FMT_BC7 ? 16 : 8;
+  h_table->n_streams = 1;
+  h_table->format = ep->format;
+  h_table->n = n;
+  h_table->n_groups = ng;
+  h_table->total_bytes = ng * 16 * bpb;
+  h_table->used_bits = (uint64_t)h_table->total_bytes * 8;
+  memcpy(h_table->scales, hs, sizeof(float) * GSC_SH);
+  host_weights(h_table->scales, h_table->weights);
+  h_table->s[0].bands = 16;
+  h_table->s[0].bc7_blocks = ep->format == GSC_FMT_BC7 ? 16 : 0;
+  h_table->s[0].first_group = 0;
+  h_table->s[0].n_groups = ng;
+  h_table->s[0].byte_offset = 0;
+  return GSC_OK;
+}
+
+gsc_status make_dev_table(const gsc_stream_table* t, DevTable* d) {
+  if (!t || !d) return GSC_ERR_INVALID_ARG;
+  if (t->n_streams < 1 || t->n_streams > GSC_MODES || !n_ok(t->n)) return GSC_ERR_INVALID_ARG;
+  if (t->n_groups != ceil_div64(t->n, 16)) return GSC_ERR_INVALID_ARG;
+  memset(d, 0, sizeof(*d));
+  d->n_streams = t->n_streams;
+  d->n = (int32_t)t->n;
+  d->n_groups = (int32_t)t->n_groups;
+  int64_t g = 0, off = 0;
+  for (int i = 0; i < t->n_streams; i++) {
+    const gsc_stream& s = t->s[i];
+    if (s.bands < 0 || s.bands > 16 || s.bc7_blocks < 0 || s.bc7_blocks > s.bands) return GSC_ERR_INVALID_ARG;
+    if (s.first_group != g || s.n_groups < 0 || s.byte_offset != off) return GSC_ERR_INVALID_ARG;
+    d->bands[i] = s.bands;
+    d->bc7[i] = s.bc7_blocks;
+    d->first_group[i] = s.first_group;
+    d->stream_groups[i] = s.n_groups;
+    d->byte_offset[i] = s.byte_offset;
+    g += s.n_groups;
+    off += s.n_groups * (16 * s.bc7_blocks + 8 * (s.bands - s.bc7_blocks));
+  }
+  if (g != t->n_groups || off != t->total_bytes) return GSC_ERR_INVALID_ARG;
+  for (int k = 0; k < GSC_SH; k++) {
+    if (!(t->scales[k] > 0.0f) || isinf(t->scales[k])) return GSC_ERR_INVALID_ARG;
+    d->scales[k] = t->scales[k];
+  }
+  return GSC_OK;
+}
+
+extern "C" gsc_status gsc_decode(gsc_ctx* c, const gsc_stream_table* table, const uint8_t* d_blocks,
+                                 const int32_t* d_perm, uint8_t* d_texels, void* stream) {
+  if (!c) return GSC_ERR_INVALID_ARG;
+  DevTable T;
+  gsc_status s = make_dev_table(table, &T);
+  if (s != GSC_OK) return s;
+  if (T.n_groups > 0 && (!d_blocks || !d_perm || !d_texels)) return GSC_ERR_INVALID_ARG;
+  if (!aligned(d_blocks, 8) || !aligned(d_texels, 16)) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  GSC_CUDA(launch_decode(T, d_blocks, d_perm, d_texels, (cudaStream_t)stream));
+  return GSC_OK;
+}
+
+extern "C" gsc_status gsc_decode_eval_sh(gsc_ctx* c, const gsc_stream_table* table, const uint8_t* d_blocks,
+                                         const int32_t* d_perm, const float* d_dirs, const float* d_pos,
+                                         const float* d_cams, int32_t V, int32_t out_order, float* d_rgb,
+                                         void* stream) {
+  if (!c) return GSC_ERR_INVALID_ARG;
+  DevTable T;
+  gsc_status s = make_dev_table(table, &T);
+  if (s != GSC_OK) return s;
+  if (V < 1 || V > 64 || out_order < 0 || out_order > 2) return GSC_ERR_INVALID_ARG;
+  if ((d_dirs == nullptr) == (d_cams == nullptr)) return GSC_ERR_INVALID_ARG;
+  if (d_cams && !d_pos && T.n > 0) return GSC_ERR_INVALID_ARG;
+  if (T.n_groups > 0 && (!d_blocks || !d_perm || !d_rgb)) return GSC_ERR_INVALID_ARG;
+  if (!aligned(d_blocks, 8) || !aligned(d_rgb, 4)) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  GSC_CUDA(launch_decode_eval(T, d_blocks, d_perm, d_dirs, d_pos, d_cams, V, out_order, d_rgb, c->sm_count,
+                              (cudaStream_t)stream));
+  return GSC_OK;
+}
+
+extern "C" gsc_status gsc_decode_tex(gsc_ctx* c, const gsc_stream_table* table, const uint8_t* d_blocks,
+                                     const int32_t* d_perm, uint8_t* d_texels, void* stream) {
+  if (!c) return GSC_ERR_INVALID_ARG;
+  DevTable T;
+  gsc_status s = make_dev_table(table, &T);
+  if (s != GSC_OK) return s;
+  if (T.n_groups > 0 && (!d_blocks || !d_perm || !d_texels)) return GSC_ERR_INVALID_ARG;
+  if (!aligned(d_blocks, 8)) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  return decode_tex_run(c, T, d_blocks, d_perm, d_texels, (cudaStream_t)stream);
+}
+
+static bool fmt_ok(int f) { return f == GSC_FMT_BC1 || f == GSC_FMT_BC7; }
+
+extern "C" gsc_status gsc_encode_blocks(gsc_ctx* c, const uint8_t* d_tex, int64_t nblk, int32_t format,
+                                        uint8_t* d_out, uint64_t* d_sse, void* stream) {
+  if (!c || nblk < 0 || !fmt_ok(format) || (nblk > 0 && (!d_tex || !d_out))) return GSC_ERR_INVALID_ARG;
+  if (!aligned(d_out, format == GSC_FMT_BC7 ? 16 : 8) || !aligned(d_sse, 8)) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  if (format == GSC_FMT_BC1) GSC_CUDA(launch_bc1_blocks(d_tex, nblk, d_out, d_sse, (cudaStream_t)stream));
+  else GSC_CUDA(launch_bc7_blocks(d_tex, nblk, d_out, d_sse, (cudaStream_t)stream));
+  return GSC_OK;
+}
+
+extern "C" gsc_status gsc_decode_blocks(gsc_ctx* c, const uint8_t* d_blocks, int64_t nblk, int32_t format,
+                                        uint8_t* d_rgba, void* stream) {
+  if (!c || nblk < 0 || !fmt_ok(format) || (nblk > 0 && (!d_blocks || !d_rgba))) return GSC_ERR_INVALID_ARG;
+  if (!aligned(d_blocks, format == GSC_FMT_BC7 ? 16 : 8) || !aligned(d_rgba, 4)) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  GSC_CUDA(launch_decode_blocks(d_blocks, nblk, format, d_rgba, (cudaStream_t)stream));
+  return GSC_OK;
+}
+
+extern "C" gsc_status gsc_decode_blocks_tex(gsc_ctx* c, const uint8_t* d_blocks, int64_t nblk, int32_t format,
+                                            uint8_t* d_rgba, void* stream) {
+  if (!c || nblk < 0 || !fmt_ok(format) || (nblk > 0 && (!d_blocks || !d_rgba))) return GSC_ERR_INVALID_ARG;
+  if (!aligned(d_blocks, 8) || !aligned(d_rgba, 4)) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  return decode_blocks_tex_run(c, d_blocks, nblk, format, d_rgba, (cudaStream_t)stream);
+}

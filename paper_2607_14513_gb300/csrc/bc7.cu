@@ -1,0 +1,495 @@
+// bc7.cu -- BC7 encoder (Sec. III-B; D3D11 / Khronos BC7 format).
+//
+// One thread per block; the 32 lanes of a warp walk the same candidate enumeration
+// on 32 different blocks, so the partition of the current candidate is warp-uniform
+// (constant-cache broadcast) and so is almost every branch. Texels sit in registers.
+//
+// The search is the codec's own deterministic integer encoder. Candidates, in order:
+// mode 0 partitions 0..15; modes 1, 2, 3 partitions 0..63; mode 4 rotation 0..3 x
+// index selection 0..1; mode 5 rotation 0..3; mode 6; mode 7 partitions 0..63. For
+// each subset: bounding-box diagonal oriented by covariance signs, indices against the
+// unquantised palette, one least-squares refinement, then every p-bit combination
+// quantised to the nearest codes and re-indexed; the best combination (lowest squared
+// error, first on ties) scores the subset. The block takes the first candidate of
+// least total error; the winner is solved again, anchors are fixed losslessly by
+// swapping endpoints and inverting indices, and the fields are packed LSB first.
+#include "bc7_tables.h"
+#include "gsc_internal.cuh"
+#include "stage.cuh"
+
+__constant__ uint32_t c_part2[64];
+__constant__ uint32_t c_part3[64];
+__constant__ uint8_t c_anc2[64];
+__constant__ uint8_t c_anc3a[64];
+__constant__ uint8_t c_anc3b[64];
+// nearest endpoint code per 8-bit target: code | expanded value << 8, 12 configurations
+__device__ uint16_t g_qtab[12][256];
+
+static int h_expand(int v, int n) { return n >= 8 ? v : ((v << (8 - n)) | (v >> (2 * n - 8))); }
+
+cudaError_t bc7_init_tables() {
+  uint32_t p2[64], p3[64];
+  uint8_t a2[64], a3a[64], a3b[64];
+  for (int p = 0; p < 64; p++) {
+    p2[p] = bc7_pack_part2(p);
+    p3[p] = bc7_pack_part3(p);
+    a2[p] = kBC7Anchor2[p];
+    a3a[p] = kBC7Anchor3a[p];
+    a3b[p] = kBC7Anchor3b[p];
+  }
+  static const int cfg[12][3] = {{4, 1, 0}, {4, 1, 1}, {5, 0, 0}, {5, 1, 0}, {5, 1, 1}, {6, 0, 0},
+                                 {6, 1, 0}, {6, 1, 1}, {7, 0, 0}, {7, 1, 0}, {7, 1, 1}, {8, 0, 0}};
+  static uint16_t q[12][256];
+  for (int c = 0; c < 12; c++) {
+    int bits = cfg[c][0], hp = cfg[c][1], pb = cfg[c][2];
+    for (int e = 0; e < 256; e++) {
+      int best = 0, be = -1, bv = 0;
+      for (int code = 0; code < (1 << bits); code++) {
+        int v = h_expand(hp ? (code << 1) | pb : code, bits + hp);
+        int d = abs(v - e);
+        if (be < 0 || d < be) { be = d; best = code; bv = v; }
+      }
+      q[c][e] = (uint16_t)(best | (bv << 8));
+    }
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(c_part2, p2, sizeof(p2))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_part3, p3, sizeof(p3))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_anc2, a2, sizeof(a2))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_anc3a, a3a, sizeof(a3a))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_anc3b, a3b, sizeof(a3b))) != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(g_qtab, q, sizeof(q));
+}
+
+// table ids: (bits, p-bit present, p)
+__host__ __device__ constexpr int qid(int bits, int hp, int p) {
+  return bits == 4 ? p : bits == 5 ? (hp ? 3 + p : 2) : bits == 6 ? (hp ? 6 + p : 5) : bits == 7 ? (hp ? 9 + p : 8) : 11;
+}
+
+enum { PT_NONE = 0, PT_UNIQUE = 1, PT_SHARED = 2 };
+
+template <int IB> __device__ __forceinline__ int wgt(int j) {
+  if (IB == 2) return (0x402B1500u >> (8 * j)) & 255;              // 0, 21, 43, 64
+  if (IB == 3) return (int)((0x40372E251B120900ull >> (8 * j)) & 255);  // 0 9 18 27 37 46 55 64
+  // 0 4 9 13 17 21 26 30 34 38 43 47 51 55 60 64
+  return j < 8 ? (int)((0x1E1A15110D090400ull >> (8 * j)) & 255) : (int)((0x403C37332F2B2622ull >> (8 * (j - 8))) & 255);
+}
+__device__ __forceinline__ int interp64(int e0, int e1, int w) { return ((64 - w) * e0 + w * e1 + 32) >> 6; }
+__device__ __forceinline__ int chan(uint32_t v, int c) { return (v >> (8 * c)) & 255; }
+
+struct FitOut {
+  int code[2][3];  // per endpoint, per channel R, G, B (unused channels untouched)
+  int p[2];
+  uint32_t idx_lo, idx_hi;  // 4 bits per texel, texel t at bits 4t of the 64-bit pair
+};
+
+__device__ __forceinline__ void set_idx(FitOut* o, int t, int j) {
+  if (t < 8) o->idx_lo |= (uint32_t)j << (4 * t); else o->idx_hi |= (uint32_t)j << (4 * (t - 8));
+}
+
+// Fits subset s of partition `part` (2 bits per texel) over the channels in CHMASK.
+template <int IB, int CHMASK, int PT, int BITS, bool OUT>
+__device__ __forceinline__ uint32_t fit_subset(const uint32_t (&tx)[16], uint32_t part, int s, FitOut* out) {
+  constexpr int F = 1 << IB;
+  constexpr int NCH = ((CHMASK >> 0) & 1) + ((CHMASK >> 1) & 1) + ((CHMASK >> 2) & 1);
+  int ch[3];
+  {
+    int k = 0;
+#pragma unroll
+    for (int c = 0; c < 3; c++) if ((CHMASK >> c) & 1) ch[k++] = c;
+  }
+  int n = 0, lo[NCH], hi[NCH], s1[NCH], s2[NCH][NCH];
+#pragma unroll
+  for (int i = 0; i < NCH; i++) {
+    lo[i] = 255; hi[i] = 0; s1[i] = 0;
+#pragma unroll
+    for (int j = 0; j < NCH; j++) s2[i][j] = 0;
+  }
+#pragma unroll
+  for (int t = 0; t < 16; t++) {
+    if ((int)((part >> (2 * t)) & 3) != s) continue;
+    n++;
+    int v[NCH];
+#pragma unroll
+    for (int i = 0; i < NCH; i++) v[i] = chan(tx[t], ch[i]);
+#pragma unroll
+    for (int i = 0; i < NCH; i++) {
+      lo[i] = min(lo[i], v[i]); hi[i] = max(hi[i], v[i]); s1[i] += v[i];
+#pragma unroll
+      for (int j = i + 1; j < NCH; j++) s2[i][j] += v[i] * v[j];
+    }
+  }
+  if (OUT) { out->idx_lo = 0; out->idx_hi = 0; out->p[0] = out->p[1] = 0;
+#pragma unroll
+    for (int i = 0; i < 3; i++) out->code[0][i] = out->code[1][i] = 0; }
+  if (n == 0) return 0;
+  int ref = 0;
+#pragma unroll
+  for (int i = 1; i < NCH; i++) if (hi[i] - lo[i] > hi[ref] - lo[ref]) ref = i;
+  int e0[NCH], e1[NCH];
+#pragma unroll
+  for (int i = 0; i < NCH; i++) {
+    bool flip = false;
+    if (i != ref) {
+      int cross = 0;
+#pragma unroll
+      for (int a = 0; a < NCH; a++)
+#pragma unroll
+        for (int b = a + 1; b < NCH; b++)
+          if ((a == ref && b == i) || (a == i && b == ref)) cross = s2[a][b];
+      flip = (n * cross - s1[ref] * s1[i]) < 0;
+    }
+    e0[i] = flip ? lo[i] : hi[i];
+    e1[i] = flip ? hi[i] : lo[i];
+  }
+  // initial indices against the unquantised endpoints, accumulated straight into LS sums
+  int saa = 0, sbb = 0, sab = 0, sav[NCH], sbv[NCH];
+  {
+    int pal[F][NCH];
+#pragma unroll
+    for (int j = 0; j < F; j++)
+#pragma unroll
+      for (int i = 0; i < NCH; i++) pal[j][i] = interp64(e0[i], e1[i], wgt<IB>(j));
+#pragma unroll
+    for (int i = 0; i < NCH; i++) { sav[i] = 0; sbv[i] = 0; }
+#pragma unroll
+    for (int t = 0; t < 16; t++) {
+      if ((int)((part >> (2 * t)) & 3) != s) continue;
+      int v[NCH];
+#pragma unroll
+      for (int i = 0; i < NCH; i++) v[i] = chan(tx[t], ch[i]);
+      int best = 0x7FFFFFFF, bj = 0;
+#pragma unroll
+      for (int j = 0; j < F; j++) {
+        int e = 0;
+#pragma unroll
+        for (int i = 0; i < NCH; i++) { int d = v[i] - pal[j][i]; e += d * d; }
+        if (e < best) { best = e; bj = j; }
+      }
+      int w = wgt<IB>(bj), a = 64 - w;
+      saa += a * a; sbb += w * w; sab += a * w;
+#pragma unroll
+      for (int i = 0; i < NCH; i++) { sav[i] += a * v[i]; sbv[i] += w * v[i]; }
+    }
+  }
+  long long det = (long long)saa * sbb - (long long)sab * sab;
+  if (det != 0) {
+#pragma unroll
+    for (int i = 0; i < NCH; i++) {
+      e0[i] = round_div_clamp255(64LL * ((long long)sbb * sav[i] - (long long)sab * sbv[i]), det);
+      e1[i] = round_div_clamp255(64LL * ((long long)saa * sbv[i] - (long long)sab * sav[i]), det);
+    }
+  }
+  constexpr int NCOMBO = PT == PT_NONE ? 1 : (PT == PT_UNIQUE ? 4 : 2);
+  constexpr int HP = PT == PT_NONE ? 0 : 1;
+  uint32_t best_sse = 0xFFFFFFFFu;
+#pragma unroll
+  for (int cmb = 0; cmb < NCOMBO; cmb++) {
+    const int p0 = PT == PT_UNIQUE ? (cmb & 1) : (PT == PT_SHARED ? cmb : 0);
+    const int p1 = PT == PT_UNIQUE ? (cmb >> 1) : (PT == PT_SHARED ? cmb : 0);
+    const uint16_t* q0 = g_qtab[qid(BITS, HP, p0)];
+    const uint16_t* q1 = g_qtab[qid(BITS, HP, p1)];
+    int c0[NCH], c1[NCH], pal[F][NCH];
+#pragma unroll
+    for (int i = 0; i < NCH; i++) {
+      uint32_t a = __ldg(q0 + e0[i]), b = __ldg(q1 + e1[i]);
+      c0[i] = a & 255; c1[i] = b & 255;
+      int v0 = a >> 8, v1 = b >> 8;
+#pragma unroll
+      for (int j = 0; j < F; j++) pal[j][i] = interp64(v0, v1, wgt<IB>(j));
+    }
+    uint32_t sse = 0, il = 0, ih = 0;
+#pragma unroll
+    for (int t = 0; t < 16; t++) {
+      if ((int)((part >> (2 * t)) & 3) != s) continue;
+      int v[NCH];
+#pragma unroll
+      for (int i = 0; i < NCH; i++) v[i] = chan(tx[t], ch[i]);
+      int best = 0x7FFFFFFF, bj = 0;
+#pragma unroll
+      for (int j = 0; j < F; j++) {
+        int e = 0;
+#pragma unroll
+        for (int i = 0; i < NCH; i++) { int d = v[i] - pal[j][i]; e += d * d; }
+        if (e < best) { best = e; bj = j; }
+      }
+      sse += best;
+      if (OUT) { if (t < 8) il |= (uint32_t)bj << (4 * t); else ih |= (uint32_t)bj << (4 * (t - 8)); }
+    }
+    if (sse < best_sse) {
+      best_sse = sse;
+      if (OUT) {
+        out->idx_lo = il; out->idx_hi = ih; out->p[0] = p0; out->p[1] = p1;
+#pragma unroll
+        for (int i = 0; i < NCH; i++) { out->code[0][ch[i]] = c0[i]; out->code[1][ch[i]] = c1[i]; }
+      }
+    }
+  }
+  return best_sse;
+}
+
+// ---- candidate scoring (search phase) ----------------------------------------------
+template <int NS, int IB, int PT, int BITS>
+__device__ __forceinline__ uint32_t score_part(const uint32_t (&tx)[16], uint32_t part) {
+  uint32_t s = fit_subset<IB, 7, PT, BITS, false>(tx, part, 0, nullptr);
+  if (NS > 1) s += fit_subset<IB, 7, PT, BITS, false>(tx, part, 1, nullptr);
+  if (NS > 2) s += fit_subset<IB, 7, PT, BITS, false>(tx, part, 2, nullptr);
+  return s;
+}
+
+// modes 4 / 5: colour over the channels other than rot-1, scalar channel rot-1 in the alpha slot
+template <int MODE, int ROT, int ISB>
+__device__ __forceinline__ uint32_t score_rot(const uint32_t (&tx)[16], FitOut* oc, FitOut* oa) {
+  constexpr int CB = MODE == 4 ? 5 : 7, AB = MODE == 4 ? 6 : 8;
+  constexpr int CIB = MODE == 4 ? (ISB ? 3 : 2) : 2, AIB = MODE == 4 ? (ISB ? 2 : 3) : 2;
+  constexpr int CM = ROT == 0 ? 7 : (7 & ~(1 << (ROT - 1)));
+  const bool out = oc != nullptr;
+  uint32_t s;
+  if (out) s = fit_subset<CIB, CM, PT_NONE, CB, true>(tx, 0u, 0, oc);
+  else s = fit_subset<CIB, CM, PT_NONE, CB, false>(tx, 0u, 0, nullptr);
+  if constexpr (ROT != 0) {
+    constexpr int AM = 1 << (ROT > 0 ? ROT - 1 : 0);
+    if (out) s += fit_subset<AIB, AM, PT_NONE, AB, true>(tx, 0u, 0, oa);
+    else s += fit_subset<AIB, AM, PT_NONE, AB, false>(tx, 0u, 0, nullptr);
+  }
+  return s;
+}
+
+__device__ __noinline__ int search_best(const uint32_t (&tx)[16], uint32_t* best_sse) {
+  uint32_t best = 0xFFFFFFFFu;
+  int be = 0, e = 0;
+#define CAND(expr)                 \
+  do {                             \
+    uint32_t s_ = (expr);          \
+    if (s_ < best) { best = s_; be = e; } \
+    e++;                           \
+  } while (0)
+  for (int p = 0; p < 16; p++) CAND((score_part<3, 3, PT_UNIQUE, 4>(tx, c_part3[p])));
+  for (int p = 0; p < 64; p++) CAND((score_part<2, 3, PT_SHARED, 6>(tx, c_part2[p])));
+  for (int p = 0; p < 64; p++) CAND((score_part<3, 2, PT_NONE, 5>(tx, c_part3[p])));
+  for (int p = 0; p < 64; p++) CAND((score_part<2, 2, PT_UNIQUE, 7>(tx, c_part2[p])));
+  CAND((score_rot<4, 0, 0>(tx, nullptr, nullptr)));
+  CAND((score_rot<4, 0, 1>(tx, nullptr, nullptr)));
+  CAND((score_rot<4, 1, 0>(tx, nullptr, nullptr)));
+  CAND((score_rot<4, 1, 1>(tx, nullptr, nullptr)));
+  CAND((score_rot<4, 2, 0>(tx, nullptr, nullptr)));
+  CAND((score_rot<4, 2, 1>(tx, nullptr, nullptr)));
+  CAND((score_rot<4, 3, 0>(tx, nullptr, nullptr)));
+  CAND((score_rot<4, 3, 1>(tx, nullptr, nullptr)));
+  CAND((score_rot<5, 0, 0>(tx, nullptr, nullptr)));
+  CAND((score_rot<5, 1, 0>(tx, nullptr, nullptr)));
+  CAND((score_rot<5, 2, 0>(tx, nullptr, nullptr)));
+  CAND((score_rot<5, 3, 0>(tx, nullptr, nullptr)));
+  CAND((score_part<1, 4, PT_UNIQUE, 7>(tx, 0u)));
+  for (int p = 0; p < 64; p++) CAND((score_part<2, 2, PT_UNIQUE, 5>(tx, c_part2[p])));
+#undef CAND
+  *best_sse = best;
+  return be;
+}
+
+// ---- final solve and packing -----------------------------------------------------------
+struct BitW {
+  uint32_t w[4];
+  int pos;
+  __device__ void put(uint32_t v, int n) {
+    if (n == 0) return;
+    v &= (n >= 32) ? 0xFFFFFFFFu : ((1u << n) - 1u);
+    int word = pos >> 5, off = pos & 31;
+    w[word] |= v << off;
+    if (off + n > 32) w[word + 1] |= v >> (32 - off);
+    pos += n;
+  }
+};
+
+__device__ __forceinline__ int get_idx(const FitOut& f, int t) {
+  return t < 8 ? (f.idx_lo >> (4 * t)) & 15 : (f.idx_hi >> (4 * (t - 8))) & 15;
+}
+
+struct ModeInfo { int ns, pb, rb, isb, cb, ab, epb, spb, ib, ib2; };
+__device__ __forceinline__ ModeInfo mode_info(int m) {
+  switch (m) {
+    case 0: return {3, 4, 0, 0, 4, 0, 1, 0, 3, 0};
+    case 1: return {2, 6, 0, 0, 6, 0, 0, 1, 3, 0};
+    case 2: return {3, 6, 0, 0, 5, 0, 0, 0, 2, 0};
+    case 3: return {2, 6, 0, 0, 7, 0, 1, 0, 2, 0};
+    case 4: return {1, 0, 2, 1, 5, 6, 0, 0, 2, 3};
+    case 5: return {1, 0, 2, 0, 7, 8, 0, 0, 2, 2};
+    case 6: return {1, 0, 0, 0, 7, 7, 1, 0, 4, 0};
+    default: return {2, 6, 0, 0, 5, 5, 1, 0, 2, 0};
+  }
+}
+
+__device__ __forceinline__ uint32_t part_of(int ns, int p) { return ns == 1 ? 0u : (ns == 2 ? c_part2[p] : c_part3[p]); }
+__device__ __forceinline__ int anchor_of(int ns, int p, int s) {
+  return s == 0 ? 0 : (ns == 2 ? c_anc2[p] : (s == 1 ? c_anc3a[p] : c_anc3b[p]));
+}
+
+// Solves candidate e into per-subset fits, fixes anchors and packs the 128 bits.
+__device__ __noinline__ uint4 solve_pack(const uint32_t (&tx)[16], int e) {
+  int mode, part = 0, rot = 0, isb = 0;
+  if (e < 16) { mode = 0; part = e; }
+  else if (e < 208) { mode = 1 + (e - 16) / 64; part = (e - 16) % 64; }
+  else if (e < 216) { mode = 4; rot = (e - 208) / 2; isb = (e - 208) % 2; }
+  else if (e < 220) { mode = 5; rot = e - 216; }
+  else if (e < 221) { mode = 6; }
+  else { mode = 7; part = e - 221; }
+  const ModeInfo M = mode_info(mode);
+  FitOut f[3], fa;
+  const uint32_t pm = part_of(M.ns, part);
+  int acode[3][2];
+  for (int s = 0; s < 3; s++) acode[s][0] = acode[s][1] = (1 << M.ab) - 1;
+  switch (mode) {
+    case 0: for (int s = 0; s < 3; s++) fit_subset<3, 7, PT_UNIQUE, 4, true>(tx, pm, s, &f[s]); break;
+    case 1: for (int s = 0; s < 2; s++) fit_subset<3, 7, PT_SHARED, 6, true>(tx, pm, s, &f[s]); break;
+    case 2: for (int s = 0; s < 3; s++) fit_subset<2, 7, PT_NONE, 5, true>(tx, pm, s, &f[s]); break;
+    case 3: for (int s = 0; s < 2; s++) fit_subset<2, 7, PT_UNIQUE, 7, true>(tx, pm, s, &f[s]); break;
+    case 6: fit_subset<4, 7, PT_UNIQUE, 7, true>(tx, 0u, 0, &f[0]); break;
+    case 7: for (int s = 0; s < 2; s++) fit_subset<2, 7, PT_UNIQUE, 5, true>(tx, pm, s, &f[s]); break;
+    case 4:
+      switch (rot * 2 + isb) {
+        case 0: score_rot<4, 0, 0>(tx, &f[0], &fa); break;
+        case 1: score_rot<4, 0, 1>(tx, &f[0], &fa); break;
+        case 2: score_rot<4, 1, 0>(tx, &f[0], &fa); break;
+        case 3: score_rot<4, 1, 1>(tx, &f[0], &fa); break;
+        case 4: score_rot<4, 2, 0>(tx, &f[0], &fa); break;
+        case 5: score_rot<4, 2, 1>(tx, &f[0], &fa); break;
+        case 6: score_rot<4, 3, 0>(tx, &f[0], &fa); break;
+        default: score_rot<4, 3, 1>(tx, &f[0], &fa); break;
+      }
+      break;
+    default:
+      switch (rot) {
+        case 0: score_rot<5, 0, 0>(tx, &f[0], &fa); break;
+        case 1: score_rot<5, 1, 0>(tx, &f[0], &fa); break;
+        case 2: score_rot<5, 2, 0>(tx, &f[0], &fa); break;
+        default: score_rot<5, 3, 0>(tx, &f[0], &fa); break;
+      }
+      break;
+  }
+  // gather codes [subset][endpoint][R, G, B] and indices
+  int code[3][2][3], pb[3][2];
+  int cidx[16], aidx[16];
+  for (int t = 0; t < 16; t++) { cidx[t] = 0; aidx[t] = 0; }
+  for (int s = 0; s < M.ns; s++) {
+    for (int ep = 0; ep < 2; ep++) {
+      for (int c = 0; c < 3; c++) code[s][ep][c] = f[s].code[ep][c];
+      pb[s][ep] = f[s].p[ep];
+    }
+  }
+  for (int t = 0; t < 16; t++) {
+    int s = (pm >> (2 * t)) & 3;
+    cidx[t] = get_idx(f[s], t);
+  }
+  if (mode == 4 || mode == 5) {
+    if (rot != 0) {
+      acode[0][0] = fa.code[0][rot - 1];
+      acode[0][1] = fa.code[1][rot - 1];
+      for (int t = 0; t < 16; t++) aidx[t] = get_idx(fa, t);
+    }
+    const int cib = isb ? M.ib2 : M.ib, aib = isb ? M.ib : M.ib2;
+    if ((cidx[0] >> (cib - 1)) & 1) {
+      for (int c = 0; c < 3; c++) { int tmp = code[0][0][c]; code[0][0][c] = code[0][1][c]; code[0][1][c] = tmp; }
+      for (int t = 0; t < 16; t++) cidx[t] = (1 << cib) - 1 - cidx[t];
+    }
+    if ((aidx[0] >> (aib - 1)) & 1) {
+      int tmp = acode[0][0]; acode[0][0] = acode[0][1]; acode[0][1] = tmp;
+      for (int t = 0; t < 16; t++) aidx[t] = (1 << aib) - 1 - aidx[t];
+    }
+  } else {
+    for (int s = 0; s < M.ns; s++) {
+      int a = anchor_of(M.ns, part, s);
+      if (!((cidx[a] >> (M.ib - 1)) & 1)) continue;
+      for (int c = 0; c < 3; c++) { int tmp = code[s][0][c]; code[s][0][c] = code[s][1][c]; code[s][1][c] = tmp; }
+      { int tmp = acode[s][0]; acode[s][0] = acode[s][1]; acode[s][1] = tmp; }
+      if (M.epb) { int tmp = pb[s][0]; pb[s][0] = pb[s][1]; pb[s][1] = tmp; }
+      for (int t = 0; t < 16; t++)
+        if ((int)((pm >> (2 * t)) & 3) == s) cidx[t] = (1 << M.ib) - 1 - cidx[t];
+    }
+  }
+  BitW w;
+  w.w[0] = w.w[1] = w.w[2] = w.w[3] = 0;
+  w.pos = 0;
+  w.put(1u << mode, mode + 1);
+  w.put(part, M.pb);
+  w.put(rot, M.rb);
+  w.put(isb, M.isb);
+  for (int c = 0; c < 3; c++)
+    for (int s = 0; s < M.ns; s++)
+      for (int ep = 0; ep < 2; ep++) w.put(code[s][ep][c], M.cb);
+  if (M.ab)
+    for (int s = 0; s < M.ns; s++)
+      for (int ep = 0; ep < 2; ep++) w.put(acode[s][ep], M.ab);
+  if (M.epb)
+    for (int s = 0; s < M.ns; s++)
+      for (int ep = 0; ep < 2; ep++) w.put(pb[s][ep], 1);
+  if (M.spb)
+    for (int s = 0; s < M.ns; s++) w.put(pb[s][0], 1);
+  if (M.ib2) {
+    for (int t = 0; t < 16; t++) w.put(isb ? aidx[t] : cidx[t], M.ib - (t == 0));
+    for (int t = 0; t < 16; t++) w.put(isb ? cidx[t] : aidx[t], M.ib2 - (t == 0));
+  } else {
+    int a1 = M.ns >= 2 ? anchor_of(M.ns, part, 1) : -1, a2 = M.ns >= 3 ? anchor_of(M.ns, part, 2) : -1;
+    for (int t = 0; t < 16; t++) w.put(cidx[t], M.ib - ((t == 0) || t == a1 || t == a2));
+  }
+  return make_uint4(w.w[0], w.w[1], w.w[2], w.w[3]);
+}
+
+// One kernel for both sources: staged layout-D groups (sh / perm / scales) or raw
+// texels [nblk][16][3] (texin != nullptr), so the search is compiled once.
+__global__ void __launch_bounds__(STAGE_THREADS) k_bc7(const float* __restrict__ sh, const int32_t* __restrict__ perm,
+                                                       const float* __restrict__ scales, int64_t n_groups,
+                                                       const uint8_t* __restrict__ texin, int64_t nblk,
+                                                       uint4* __restrict__ blocks, uint32_t* __restrict__ sse7,
+                                                       uint64_t* __restrict__ sse64) {
+  __shared__ uint32_t tex[16][STAGE_STRIDE];
+  __shared__ float s_scale[16];
+  if (!texin) {
+    if (threadIdx.x < 16) s_scale[threadIdx.x] = scales[threadIdx.x];
+    __syncthreads();
+  }
+  const int64_t total = texin ? nblk : n_groups * 16;
+  for (int64_t b0 = (int64_t)blockIdx.x * STAGE_THREADS; b0 < total; b0 += (int64_t)gridDim.x * STAGE_THREADS) {
+    const int64_t blk = b0 + threadIdx.x;
+    uint32_t tx[16];
+    if (!texin) {
+      stage_groups(sh, perm, s_scale, b0 / 16, n_groups, tex);
+      __syncthreads();
+#pragma unroll
+      for (int t = 0; t < 16; t++) tx[t] = tex[t][threadIdx.x];
+      __syncthreads();
+    } else if (blk < total) {
+      const uint8_t* p = texin + blk * 48;
+#pragma unroll
+      for (int t = 0; t < 16; t++)
+        tx[t] = (uint32_t)p[3 * t] | ((uint32_t)p[3 * t + 1] << 8) | ((uint32_t)p[3 * t + 2] << 16);
+    }
+    if (blk < total) {
+      uint32_t best;
+      int e = search_best(tx, &best);
+      blocks[blk] = solve_pack(tx, e);
+      if (sse7) sse7[blk] = best;
+      if (sse64) sse64[blk] = best;
+    }
+  }
+}
+
+static int grid_for7(int64_t work, int per_cta) {
+  int64_t g = ceil_div64(work, per_cta);
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+
+cudaError_t launch_bc7_groups(const float* sh, const int32_t* perm, const float* scales, int64_t n_groups,
+                              uint8_t* blocks, uint32_t* sse7, cudaStream_t st) {
+  if (n_groups <= 0) return cudaSuccess;
+  k_bc7<<<grid_for7(n_groups, STAGE_GROUPS), STAGE_THREADS, 0, st>>>(
+      sh, perm, scales, n_groups, nullptr, 0, reinterpret_cast<uint4*>(blocks), sse7, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bc7_blocks(const uint8_t* tex, int64_t nblk, uint8_t* out, uint64_t* sse, cudaStream_t st) {
+  if (nblk <= 0) return cudaSuccess;
+  k_bc7<<<grid_for7(nblk, STAGE_THREADS), STAGE_THREADS, 0, st>>>(nullptr, nullptr, nullptr, 0, tex, nblk,
+                                                                reinterpret_cast<uint4*>(out), nullptr, sse);
+  return cudaGetLastError();
+}

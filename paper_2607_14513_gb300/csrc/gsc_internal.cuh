@@ -1,0 +1,111 @@
+// gsc_internal.cuh -- shared declarations of the CUDA library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gsc.h"
+
+#define GSC_SH 16
+#define GSC_MODES 14
+
+struct gsc_ctx {
+  int device;
+  int sm_count;
+  int* d_status;        // first device-side error code (0 = none)
+  int* d_diag;          // where it happened (kernel-defined)
+  void* h_pinned;       // small pinned host buffer for table read-back
+  size_t h_pinned_bytes;
+};
+
+#define GSC_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return GSC_ERR_CUDA;          \
+  } while (0)
+
+static inline int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Records the first device-detected error into the context status word.
+__device__ __forceinline__ void gsc_record(int* status, int* diag, int code, int where) {
+  if (atomicCAS(status, 0, code) == 0 && diag) *diag = where;
+}
+
+// 8-bit quantisation of Sec. V-A: q = clamp(128 + rint(fl(fl(x / s) * 255)), 0, 255).
+__device__ __forceinline__ uint32_t gsc_quant1(float x, float s) {
+  float t = __fmul_rn(__fdiv_rn(x, s), 255.0f);
+  t = fminf(fmaxf(t, -256.0f), 256.0f);  // NaN-free inputs assumed; clamping first keeps rint in range
+  int q = 128 + __float2int_rn(t);
+  return (uint32_t)min(max(q, 0), 255);
+}
+
+// Bump allocator over a caller-provided workspace (256-byte aligned pieces).
+struct Carve {
+  uint8_t* base;
+  size_t off, cap;
+  template <class T> T* take(int64_t count) {
+    off = align_up(off, 256);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += sizeof(T) * (size_t)(count > 0 ? count : 1);
+    return p;
+  }
+};
+
+// ---- launchers implemented by the translation units ------------------------------
+// plan.cu
+size_t plan_ws_bytes(int64_t n);
+gsc_status plan_run(gsc_ctx* ctx, const float* pos, const float* sh, const gsc_plan_params* pp, int32_t* perm,
+                    float* scales, void* ws, size_t ws_bytes, cudaStream_t st);
+cudaError_t launch_quantise(const float* sh, int64_t n, const float* scales, uint8_t* q, cudaStream_t st);
+size_t radix_ws_bytes(int64_t n);
+size_t scan_ws_bytes(int64_t n);
+// Exclusive scan of n values (uint32 or uint64); *total (device, optional) gets the sum.
+template <class T>
+cudaError_t scan_exclusive(const T* in, T* out, int64_t n, uint64_t* total, void* ws, cudaStream_t st);
+// Stable LSD radix sort of (64-bit key, 32-bit value) pairs on the low key_bits bits.
+// Result lands in keys/vals (the input arrays); ws holds the ping-pong buffers.
+cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int key_bits, void* ws, cudaStream_t st);
+
+// bc1.cu
+cudaError_t bc1_init_tables();
+// Group kernel: stage layout-D texels from sh/perm/scales and code all 16 blocks of
+// each group; blocks [g][k][8]; sse1 / sse0 [g][k] optional (BC1 error, error of 128).
+cudaError_t launch_bc1_groups(const float* sh, const int32_t* perm, const float* scales, int64_t n_groups,
+                              uint8_t* blocks, uint32_t* sse1, uint32_t* sse0, cudaStream_t st);
+cudaError_t launch_bc1_blocks(const uint8_t* tex, int64_t nblk, uint8_t* out, uint64_t* sse, cudaStream_t st);
+
+// bc7.cu
+cudaError_t bc7_init_tables();
+cudaError_t launch_bc7_groups(const float* sh, const int32_t* perm, const float* scales, int64_t n_groups,
+                              uint8_t* blocks, uint32_t* sse7, cudaStream_t st);
+cudaError_t launch_bc7_blocks(const uint8_t* tex, int64_t nblk, uint8_t* out, uint64_t* sse, cudaStream_t st);
+
+// rate.cu
+size_t rate_ws_bytes(int64_t n_groups);
+gsc_status rate_run(gsc_ctx* ctx, const float* sh, int64_t n, const int32_t* perm, const float* scales,
+                    uint32_t target_x4, uint8_t* blocks, int32_t* perm_out, gsc_stream_table* table, void* ws,
+                    size_t ws_bytes, cudaStream_t st);
+
+// decode.cu
+cudaError_t decode_init_tables();
+// Flattened stream table for kernels (passed by value).
+struct DevTable {
+  int32_t n_streams;
+  int32_t n;
+  int32_t n_groups;
+  int32_t bands[GSC_MODES], bc7[GSC_MODES];
+  int64_t first_group[GSC_MODES], stream_groups[GSC_MODES], byte_offset[GSC_MODES];
+  float scales[GSC_SH];
+};
+gsc_status make_dev_table(const gsc_stream_table* t, DevTable* d);
+cudaError_t launch_decode(const DevTable& t, const uint8_t* blocks, const int32_t* perm, uint8_t* texels,
+                          cudaStream_t st);
+cudaError_t launch_decode_eval(const DevTable& t, const uint8_t* blocks, const int32_t* perm, const float* dirs,
+                               const float* pos, const float* cams, int V, int out_order, float* rgb, int sm_count,
+                               cudaStream_t st);
+cudaError_t launch_decode_blocks(const uint8_t* blocks, int64_t nblk, int format, uint8_t* rgba, cudaStream_t st);
+gsc_status decode_tex_run(gsc_ctx* ctx, const DevTable& t, const uint8_t* blocks, const int32_t* perm,
+                          uint8_t* texels, cudaStream_t st);
+gsc_status decode_blocks_tex_run(gsc_ctx* ctx, const uint8_t* blocks, int64_t nblk, int format, uint8_t* rgba,
+                                 cudaStream_t st);

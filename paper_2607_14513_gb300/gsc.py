@@ -1,0 +1,246 @@
+"""Thin Python binding of libgsc.so (include/gsc.h): argument marshalling only.
+
+Every step of the codec runs in the CUDA library; PyTorch supplies device memory
+and streams. There is no CPU fallback: if the library cannot be loaded, or no
+sm_103 GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "lib", "libgsc.so")
+HEADER = os.path.join(PKG, "..", "include", "gsc.h")
+
+GSC_OK = 0
+STATUS = {0: "GSC_OK", 1: "GSC_ERR_INVALID_ARG", 2: "GSC_ERR_CUDA", 3: "GSC_ERR_OOM", 4: "GSC_ERR_BUDGET",
+          5: "GSC_ERR_TIMEOUT", 6: "GSC_ERR_UNSUPPORTED", 7: "GSC_ERR_DEVICE"}
+FMT_RATE, FMT_BC1, FMT_BC7 = 0, 1, 7
+OUT_VIEW_MAJOR, OUT_SLOT_ORDER, OUT_GAUSS_MAJOR = 0, 1, 2
+
+
+class GscError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (where, STATUS.get(code, "?"), code))
+
+
+class PlanParams(C.Structure):
+    _fields_ = [("n", C.c_int64), ("group_size", C.c_int64), ("sort", C.c_int32), ("quantile_permille", C.c_uint32)]
+
+
+class EncodeParams(C.Structure):
+    _fields_ = [("format", C.c_int32), ("target_bpt_x4", C.c_uint32)]
+
+
+class Stream(C.Structure):
+    _fields_ = [("bands", C.c_int32), ("bc7_blocks", C.c_int32), ("first_group", C.c_int64),
+                ("n_groups", C.c_int64), ("byte_offset", C.c_int64)]
+
+
+class StreamTable(C.Structure):
+    _fields_ = [("n_streams", C.c_int32), ("format", C.c_int32), ("n", C.c_int64), ("n_groups", C.c_int64),
+                ("total_bytes", C.c_int64), ("budget_bits", C.c_uint64), ("used_bits", C.c_uint64),
+                ("lambda_", C.c_uint64), ("scales", C.c_float * 16), ("weights", C.c_uint32 * 16),
+                ("s", Stream * 14)]
+
+    def streams(self):
+        return [dict(bands=self.s[i].bands, bc7_blocks=self.s[i].bc7_blocks, first_group=self.s[i].first_group,
+                     n_groups=self.s[i].n_groups, byte_offset=self.s[i].byte_offset) for i in range(self.n_streams)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_P = C.c_void_p
+_SIGS = {
+    "gsc_ctx_create": [C.POINTER(C.c_void_p), C.c_int],
+    "gsc_ctx_destroy": [_P],
+    "gsc_ctx_sync": [_P, _P],
+    "gsc_status_string": [C.c_int],
+    "gsc_workspace_bytes": [C.c_int64, C.POINTER(EncodeParams)],
+    "gsc_plan_reorder": [_P, _P, _P, C.POINTER(PlanParams), _P, _P, _P, C.c_size_t, _P],
+    "gsc_quantise": [_P, _P, C.c_int64, _P, _P, _P],
+    "gsc_encode": [_P, _P, C.c_int64, _P, _P, C.POINTER(EncodeParams), _P, _P, C.POINTER(StreamTable), _P,
+                   C.c_size_t, _P],
+    "gsc_decode": [_P, C.POINTER(StreamTable), _P, _P, _P, _P],
+    "gsc_decode_eval_sh": [_P, C.POINTER(StreamTable), _P, _P, _P, _P, _P, C.c_int32, C.c_int32, _P, _P],
+    "gsc_decode_tex": [_P, C.POINTER(StreamTable), _P, _P, _P, _P],
+    "gsc_encode_blocks": [_P, _P, C.c_int64, C.c_int32, _P, _P, _P],
+    "gsc_decode_blocks": [_P, _P, C.c_int64, C.c_int32, _P, _P],
+    "gsc_decode_blocks_tex": [_P, _P, C.c_int64, C.c_int32, _P, _P],
+}
+
+
+def header_symbols():
+    """Names of the functions include/gsc.h declares."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(gsc_[a-z0-9_]+)\s*\(", txt)))
+
+
+def load(path: str | None = None):
+    """Load libgsc.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError("libgsc.so not built (%s); run __graft_entry__.build()" % p)
+            lib = C.CDLL(p)
+            for name, args in _SIGS.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = C.c_int
+            lib.gsc_status_string.restype = C.c_char_p
+            lib.gsc_workspace_bytes.restype = C.c_size_t
+            _lib = lib
+    return _lib
+
+
+def _check(code, where):
+    if code != GSC_OK:
+        raise GscError(code, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """A gsc_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        self.device = device
+        h = C.c_void_p()
+        _check(self.lib.gsc_ctx_create(C.byref(h), device), "gsc_ctx_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.lib.gsc_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self, stream=None):
+        _check(self.lib.gsc_ctx_sync(self.h, _stream(stream)), "gsc_ctx_sync")
+
+    def workspace(self, n, fmt=FMT_BC1, target_x4=0):
+        import torch
+        ep = EncodeParams(fmt, target_x4)
+        nb = self.lib.gsc_workspace_bytes(n, C.byref(ep))
+        return torch.empty(max(int(nb), 256), dtype=torch.uint8, device="cuda:%d" % self.device)
+
+
+def gsc_plan_reorder(ctx, pos, sh, group_size=4096, sort=1, permille=995, ws=None, stream=None):
+    """-> (perm int32 [n_groups*16], scales float32 [16])."""
+    import torch
+    n = sh.shape[0]
+    dev = sh.device
+    ns = (n + 15) // 16 * 16
+    perm = torch.empty(max(ns, 1), dtype=torch.int32, device=dev)[:ns]
+    scales = torch.empty(16, dtype=torch.float32, device=dev)
+    ws = ws if ws is not None else ctx.workspace(n)
+    pp = PlanParams(n, group_size, sort, permille)
+    _check(ctx.lib.gsc_plan_reorder(ctx.h, _ptr(pos), _ptr(sh), C.byref(pp), _ptr(perm), _ptr(scales), _ptr(ws),
+                                    ws.numel(), _stream(stream)), "gsc_plan_reorder")
+    return perm, scales
+
+
+def gsc_quantise(ctx, sh, scales, stream=None):
+    import torch
+    q = torch.empty(sh.shape, dtype=torch.uint8, device=sh.device)
+    _check(ctx.lib.gsc_quantise(ctx.h, _ptr(sh), sh.shape[0], _ptr(scales), _ptr(q), _stream(stream)), "gsc_quantise")
+    return q
+
+
+def gsc_encode(ctx, sh, perm, scales, fmt, target_x4=0, ws=None, out=None, perm_out=None, stream=None):
+    """-> (blocks uint8 [total_bytes], perm_out int32, StreamTable)."""
+    import torch
+    n = sh.shape[0]
+    ng = (n + 15) // 16
+    dev = sh.device
+    blocks = out if out is not None else torch.empty(max(ng * 256, 16), dtype=torch.uint8, device=dev)
+    po = perm_out if perm_out is not None else torch.empty(max(ng * 16, 1), dtype=torch.int32, device=dev)
+    ws = ws if ws is not None else ctx.workspace(n, fmt, target_x4)
+    ep = EncodeParams(fmt, target_x4)
+    tab = StreamTable()
+    _check(ctx.lib.gsc_encode(ctx.h, _ptr(sh), n, _ptr(perm), _ptr(scales), C.byref(ep), _ptr(blocks), _ptr(po),
+                              C.byref(tab), _ptr(ws), ws.numel(), _stream(stream)), "gsc_encode")
+    return blocks[:tab.total_bytes], po[:ng * 16], tab
+
+
+def gsc_decode(ctx, table, blocks, perm, stream=None):
+    import torch
+    tex = torch.empty((max(table.n, 1), 16, 3), dtype=torch.uint8, device=blocks.device)[:table.n]
+    _check(ctx.lib.gsc_decode(ctx.h, C.byref(table), _ptr(blocks), _ptr(perm), _ptr(tex), _stream(stream)),
+           "gsc_decode")
+    return tex
+
+
+def gsc_decode_eval_sh(ctx, table, blocks, perm, dirs=None, pos=None, cams=None, out_order=OUT_VIEW_MAJOR,
+                       out=None, stream=None):
+    import torch
+    src = dirs if dirs is not None else cams
+    V = src.shape[0]
+    n, ns = table.n, table.n_groups * 16
+    shape = {OUT_VIEW_MAJOR: (V, n, 3), OUT_SLOT_ORDER: (V, ns, 3), OUT_GAUSS_MAJOR: (n, V, 3)}[out_order]
+    rgb = out if out is not None else torch.empty(shape, dtype=torch.float32, device=blocks.device)
+    _check(ctx.lib.gsc_decode_eval_sh(ctx.h, C.byref(table), _ptr(blocks), _ptr(perm), _ptr(dirs), _ptr(pos),
+                                      _ptr(cams), V, out_order, _ptr(rgb), _stream(stream)), "gsc_decode_eval_sh")
+    return rgb
+
+
+def gsc_decode_tex(ctx, table, blocks, perm, stream=None):
+    import torch
+    tex = torch.zeros((max(table.n, 1), 16, 3), dtype=torch.uint8, device=blocks.device)[:table.n]
+    _check(ctx.lib.gsc_decode_tex(ctx.h, C.byref(table), _ptr(blocks), _ptr(perm), _ptr(tex), _stream(stream)),
+           "gsc_decode_tex")
+    return tex
+
+
+def gsc_encode_blocks(ctx, tex, fmt, stream=None):
+    """tex uint8 [nblk, 16, 3] -> (blocks [nblk, 8|16], sse uint64 [nblk])."""
+    import torch
+    nb = tex.shape[0]
+    bpb = 16 if fmt == FMT_BC7 else 8
+    out = torch.empty((max(nb, 1), bpb), dtype=torch.uint8, device=tex.device)[:nb]
+    sse = torch.empty(max(nb, 1), dtype=torch.int64, device=tex.device)[:nb]
+    _check(ctx.lib.gsc_encode_blocks(ctx.h, _ptr(tex.contiguous()), nb, fmt, _ptr(out), _ptr(sse), _stream(stream)),
+           "gsc_encode_blocks")
+    return out, sse
+
+
+def gsc_decode_blocks(ctx, blocks, fmt, stream=None):
+    import torch
+    nb = blocks.shape[0]
+    rgba = torch.empty((max(nb, 1), 16, 4), dtype=torch.uint8, device=blocks.device)[:nb]
+    _check(ctx.lib.gsc_decode_blocks(ctx.h, _ptr(blocks.contiguous()), nb, fmt, _ptr(rgba), _stream(stream)),
+           "gsc_decode_blocks")
+    return rgba
+
+
+def gsc_decode_blocks_tex(ctx, blocks, fmt, stream=None):
+    import torch
+    nb = blocks.shape[0]
+    rgba = torch.empty((max(nb, 1), 16, 4), dtype=torch.uint8, device=blocks.device)[:nb]
+    _check(ctx.lib.gsc_decode_blocks_tex(ctx.h, _ptr(blocks.contiguous()), nb, fmt, _ptr(rgba), _stream(stream)),
+           "gsc_decode_blocks_tex")
+    return rgba
