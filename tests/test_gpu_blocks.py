@@ -60,7 +60,7 @@ def test_decode_arbitrary_blocks_bit_exact(ctx, O, fmt):
     if fmt == 7:
         blk[:8, 0] = 0                                     # reserved mode
         for m in range(8):                                 # every mode, many times
-            blk[8 + m::8, 0] = (blk[8 + m::8, 0] & ~((1 << (m + 1)) - 1)) | (1 << m)
+            blk[8 + m::8, 0] = (blk[8 + m::8, 0] & np.uint8(0xFF ^ ((1 << (m + 1)) - 1))) | np.uint8(1 << m)
     ref = O.decode_blocks(blk, fmt)
     got = gsc.gsc_decode_blocks(ctx, torch.from_numpy(blk).cuda(), fmt).cpu().numpy()
     assert np.array_equal(got, ref)
@@ -102,7 +102,7 @@ def test_texture_unit_bc7_every_candidate(ctx, O):
             blks.append(O.bc7_candidate(tex, e)[1])
     rnd = rng.integers(0, 256, size=(2048, 16)).astype(np.uint8)
     for m in range(8):
-        rnd[m::8, 0] = (rnd[m::8, 0] & ~((1 << (m + 1)) - 1)) | (1 << m)
+        rnd[m::8, 0] = (rnd[m::8, 0] & np.uint8(0xFF ^ ((1 << (m + 1)) - 1))) | np.uint8(1 << m)
     blks = np.concatenate([np.array(blks), rnd])
     hw = gsc.gsc_decode_blocks_tex(ctx, torch.from_numpy(blks).cuda(), 7).cpu().numpy()
     ref = O.decode_blocks(blks, 7)
