@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the SH block-texture codec on GB300 (one JSON line on rank 0).
+
+Workload (default): scene-scale plain method, 3,000,000 synthetic Gaussians (64 clusters,
+10% heavy-tailed bands 2-3), SH degree 3. One step runs every stage of the hot path once:
+scales + quantisation + reorder plan; rate-controlled encode at 6 bits per texel, which
+codes every block with both BC1 and BC7 (kept as the all-BC1 4 bpt and all-BC7 8 bpt
+codings) and selects the fixed-rate streams; fused decode + SH evaluation for 8 camera
+poses of each of the three codings; software decode and texture-unit decode of the BC1
+and BC7 codings, compared bit for bit on the device.
+
+`value` is whole-job throughput in millions of Gaussians per second through that step
+(inputs resident in HBM). Multi-GPU runs are weak scaling: every rank codes its own scene.
+`--impl reference` times the plain CPU oracle on this host's cores on a bounded sample of
+the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2607_14513_gb300 import synthetic as S  # noqa: E402
+
+METRIC = "BC1/BC7 encode Mblocks/s; decode+SH-eval MGauss/s & GB/s; served p50/p99 ms"
+UNIT = "MGauss/s"
+RATE_TARGET_X4 = 24          # 6 bits per coefficient texel
+N_CAMS = 8
+# BC7 search: palette-distance evaluations per block (the candidate enumeration of the
+# encoder: initial indices + every p-bit combination, per mode / partition / rotation /
+# index selection), and integer operations per evaluation (3 differences, 3 squares
+# accumulated, compare, select).
+BC7_EVALS_PER_BLOCK = (16 * (16 * 8 + 4 * 16 * 8) + 64 * (16 * 8 + 2 * 16 * 8) + 64 * (16 * 4 + 16 * 4)
+                       + 64 * (16 * 4 + 4 * 16 * 4) + (128 + 256 + 3 * 768) + (128 + 3 * 256)
+                       + (16 * 16 + 4 * 16 * 16) + 64 * (16 * 4 + 4 * 16 * 4))
+OPS_PER_EVAL = 8
+
+
+def workload_cfg(name):
+    return {"scene3m": S.SCENE, "medium262k": S.MEDIUM, "tiny4k": S.TINY}[name]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--id=" + self.uuid, "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [x for x in sm if mx and x > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------------
+def run_gsc(args, world, rank, local):
+    import torch
+    from paper_2607_14513_gb300 import gsc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = dict(workload_cfg(args.workload))
+    cfg["seed"] = cfg["seed"] + 1000 * rank
+    n = cfg["n"]
+    ng = (n + 15) // 16
+    ns = ng * 16
+    sc = S.make_scene(**cfg)
+    cams_np = S.make_cams(N_CAMS, 1100 + rank)
+    ctx = gsc.Context(local)
+    stream = torch.cuda.Stream(dev)
+    pos = torch.from_numpy(sc.pos).to(dev)
+    sh = torch.from_numpy(sc.sh).to(dev)
+    cams = torch.from_numpy(cams_np).to(dev)
+    ws = ctx.workspace(n, gsc.FMT_RATE, RATE_TARGET_X4)
+    bc1 = torch.empty(ng * 128, dtype=torch.uint8, device=dev)
+    bc7 = torch.empty(ng * 256, dtype=torch.uint8, device=dev)
+    rate_buf = torch.empty(ng * 256, dtype=torch.uint8, device=dev)
+    rate_perm = torch.empty(ns, dtype=torch.int32, device=dev)
+    rgb = torch.empty((3, n, N_CAMS, 3), dtype=torch.float32, device=dev)
+    ok = torch.ones((), dtype=torch.bool, device=dev)
+
+    def step(pos_d, sh_d):
+        perm, scales = gsc.gsc_plan_reorder(ctx, pos_d, sh_d, ws=ws, stream=stream)
+        rblk, rperm, rtab = gsc.gsc_encode(ctx, sh_d, perm, scales, gsc.FMT_RATE, RATE_TARGET_X4, ws=ws,
+                                           out=rate_buf, perm_out=rate_perm, stream=stream, bc1_all=bc1, bc7_all=bc7)
+        t1, t7 = gsc.forced_table(rtab, gsc.FMT_BC1), gsc.forced_table(rtab, gsc.FMT_BC7)
+        for i, (tab, blk, p) in enumerate([(t7, bc7, perm), (t1, bc1, perm), (rtab, rblk, rperm)]):
+            gsc.gsc_decode_eval_sh(ctx, tab, blk, p, pos=pos_d, cams=cams, out_order=gsc.OUT_GAUSS_MAJOR,
+                                   out=rgb[i], stream=stream)
+        with torch.cuda.stream(stream):
+            for tab, blk in [(t7, bc7), (t1, bc1)]:
+                sw = gsc.gsc_decode(ctx, tab, blk, perm, stream=stream)
+                hw = gsc.gsc_decode_tex(ctx, tab, blk, perm, stream=stream)
+                ok.logical_and_((sw == hw).all())
+        return rtab, rblk, rperm
+
+    # warm-up (also compiles nothing: the library is prebuilt)
+    for _ in range(args.warmup):
+        step(pos, sh)
+    stream.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    gsc.set_timing(ctx, True)
+    launches0 = gsc.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        rtab, rblk, rperm = step(pos, sh)
+    e1.record(stream)
+    stream.synchronize()
+    launches = gsc.launch_count() - launches0
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    kt = {k: gsc.kernel_time(ctx, k) for k in ["plan", "bc1_encode", "bc7_encode", "rate_select", "decode",
+                                               "decode_eval", "decode_tex"]}
+    gsc.set_timing(ctx, False)
+    ms_step = max_over_ranks(ms_total / args.steps, world, dev)
+    value = world * n / (ms_step * 1e-3) / 1e6
+    match = bool(ok.item())
+
+    # dominant kernel: the BC7 search (integer ALU bound)
+    bc7_ms = kt["bc7_encode"][0] / max(1, kt["bc7_encode"][1])
+    int_peak = gsc.int_peak(ctx, stream=stream)
+    bc7_ops = BC7_EVALS_PER_BLOCK * OPS_PER_EVAL * ns
+    bc7_achieved = bc7_ops / (bc7_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(bc7_achieved, 3), "peak": round(int_peak / 1e12, 3),
+                "unit": "Tops/s", "frac": round(bc7_achieved / (int_peak / 1e12), 4), "traffic": None,
+                "kernel": "k_bc7 (BC7 candidate search)",
+                "peak_source": "measured on this GPU by gsc_probe_int_peak (IADD3/LOP3/IMAD chains)",
+                "algorithmic": "%d palette evaluations x %d int ops per block, %d blocks" % (
+                    BC7_EVALS_PER_BLOCK, OPS_PER_EVAL, ns)}
+    # the fused decode + SH evaluation (HBM bound): algorithmic bytes per launch
+    hbm, hbm_src = peaks()
+    ev_ms = kt["decode_eval"][0] / max(1, kt["decode_eval"][1])
+    ev_bytes = np.mean([16 * ns, 8 * ns, rtab.total_bytes]) + 4 * ns + 12 * n + N_CAMS * 12 * n
+    ev_gbs = ev_bytes / (ev_ms * 1e-3) / 1e9
+    roofline_eval = {"bound": "hbm", "achieved": round(ev_gbs, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(ev_gbs / hbm, 4), "traffic": None, "peak_source": hbm_src,
+                     "kernel": "k_decode_eval (decode + SH eval, %d cameras, Gaussian-major output)" % N_CAMS,
+                     "algorithmic": "blocks + perm 4 B + position 12 B + %d x 12 B output per Gaussian" % N_CAMS}
+    stages = {}
+    for k, (ms, cnt) in kt.items():
+        stages[k + "_ms"] = round(ms / max(1, cnt), 4)
+    stages["bc1_encode_Mblocks_s"] = round(ns / (kt["bc1_encode"][0] / max(1, kt["bc1_encode"][1]) * 1e-3) / 1e6, 2)
+    stages["bc7_encode_Mblocks_s"] = round(ns / (bc7_ms * 1e-3) / 1e6, 3)
+    stages["decode_eval_MGauss_s"] = round(n / (ev_ms * 1e-3) / 1e6, 1)
+    stages["decode_eval_GB_s"] = round(ev_gbs, 1)
+    stages["rate_bits_per_texel"] = round(rtab.used_bits / (16.0 * n), 4)
+
+    # end to end through the public API with host buffers
+    e2e = run_e2e(args, ctx, gsc, stream, dev, sc, step, world)
+
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u8 texels / int32 search / f32 SH eval",
+           "data": "synthetic (seeded; stands in for the paper's trained scenes)",
+           "config": {"workload": "scene-scale plain method: %d Gaussians, SH degree 3, %d clusters, %d%% heavy "
+                                  "tail; rate 6 bpt + all-BC1 4 bpt + all-BC7 8 bpt; %d camera poses"
+                                  % (n, cfg["clusters"], int(cfg["heavy_frac"] * 100), N_CAMS),
+                      "n_gaussians": n, "parallelism": "weak, one scene per GPU" if world > 1 else "single GPU",
+                      "l2": "inputs larger than L2 (SH 192 B/Gaussian)", "texture_path_bit_exact": match},
+           "roofline": roofline, "roofline_decode_eval": roofline_eval, "stages": stages,
+           "clocks": clk, "e2e": e2e, "gpu_launches": int(launches)}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(args, ctx, gsc, stream, dev, sc, step, world):
+    import torch
+    pos_h = torch.from_numpy(sc.pos).pin_memory()
+    sh_h = torch.from_numpy(sc.sh).pin_memory()
+    pos_d = torch.empty_like(pos_h, device=dev)
+    sh_d = torch.empty_like(sh_h, device=dev)
+    n = sc.pos.shape[0]
+    ns = (n + 15) // 16 * 16
+    out_blocks = torch.empty(ns * 16, dtype=torch.uint8).pin_memory()
+    out_perm = torch.empty(ns, dtype=torch.int32).pin_memory()
+    bo = 0
+
+    def one():
+        nonlocal bo
+        with torch.cuda.stream(stream):
+            pos_d.copy_(pos_h, non_blocking=True)
+            sh_d.copy_(sh_h, non_blocking=True)
+        rtab, rblk, rperm = step(pos_d, sh_d)
+        with torch.cuda.stream(stream):
+            out_blocks[:rtab.total_bytes].copy_(rblk, non_blocking=True)
+            out_perm.copy_(rperm, non_blocking=True)
+        bo = rtab.total_bytes + 4 * ns
+        return rtab
+
+    for _ in range(max(1, args.warmup // 2)):
+        one()
+    stream.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    stream.synchronize()
+    t = (time.perf_counter() - t0) / args.steps
+    t = max_over_ranks(t, world, dev)
+    return {"value": round(world * n / t / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": int(n * (12 + 192)),
+            "d2h_bytes_per_step": int(bo), "ms_per_step": round(t * 1e3, 3),
+            "path": "pinned host pos+SH -> plan/encode/decode/eval/texture compare -> rate streams + perm to host"}
+
+
+# ------------------------------------------------------------------------------------------------
+def cpu_baseline(workload, budget_s=20.0):
+    """The oracle, as it stands, single-threaded on a bounded sample of the workload.
+
+    Per stage it codes a sample and charges the per-Gaussian time; the stages are the
+    step's: plan (scales, quantisation, reorder), BC1 and BC7 coding of every block plus
+    the rate control, decode + SH evaluation of 8 cameras for three codings, and the
+    software decode twice (the CPU has no texture unit: the second decode stands in)."""
+    from oracle import oracle as O
+    cfg = dict(workload_cfg(workload))
+    n_plan = min(cfg["n"], 200_000)
+    sc = S.make_scene(**dict(cfg, n=n_plan))
+    cams = S.make_cams(N_CAMS, 1100)
+    t0 = time.perf_counter()
+    scl = O.scales(sc.sh)
+    q = O.quantise(sc.sh, scl)
+    perm = O.plan(sc.pos, q, 4096, 1)
+    t_plan = (time.perf_counter() - t0) / n_plan
+    st = O.stage(q, perm[: (min(n_plan, 4096) // 16) * 16])
+    blocks = st.reshape(-1, 16, 3)
+    nb7 = 256 if budget_s < 10 else 1024
+    t0 = time.perf_counter()
+    O.encode_blocks(blocks[:nb7], 7, threads=1)
+    t_bc7 = (time.perf_counter() - t0) / nb7
+    nb1 = min(blocks.shape[0], 8192)
+    t0 = time.perf_counter()
+    O.encode_blocks(blocks[:nb1], 1, threads=1)
+    t_bc1 = (time.perf_counter() - t0) / nb1
+    n_ev = 4096
+    r = O.encode(q[:n_ev], np.arange(n_ev, dtype=np.int32), scl, 1)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        tex = O.decode(r["table"], r["blocks"], r["perm"])
+        O.eval_sh(tex, scl, pos=sc.pos[:n_ev], cams=cams)
+    t_eval = (time.perf_counter() - t0) / (3 * n_ev)
+    t0 = time.perf_counter()
+    for _ in range(4):
+        O.decode(r["table"], r["blocks"], r["perm"])
+    t_dec = (time.perf_counter() - t0) / n_ev
+    # one block per Gaussian per coding (16 blocks per 16-Gaussian group)
+    per_gauss = t_plan + t_bc7 + t_bc1 + t_eval + t_dec
+    return {"value": round(1.0 / per_gauss / 1e6, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "plan on %d Gaussians; BC7 on %d and BC1 on %d staged blocks; decode + SH eval (8 cams, x3) "
+                      "and 4 decodes on %d Gaussians; scaled per Gaussian" % (n_plan, nb7, nb1, n_ev),
+            "stage_us_per_gaussian": {"plan": round(t_plan * 1e6, 3), "bc7": round(t_bc7 * 1e6, 1),
+                                      "bc1": round(t_bc1 * 1e6, 2), "decode_eval": round(t_eval * 1e6, 2),
+                                      "decode": round(t_dec * 1e6, 2)}}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    times = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        base = cpu_baseline(args.workload, budget_s=5.0)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    v = base["value"]
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * statistics.median(times), 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u8 texels / int search / f64 SH eval", "impl": "reference",
+           "data": "synthetic (seeded)", "config": {"workload": args.workload},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                            "sample": base["sample"]},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gsc", choices=["gsc", "reference"])
+    ap.add_argument("--workload", default="scene3m", choices=["scene3m", "medium262k", "tiny4k"])
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_gsc(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

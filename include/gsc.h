@@ -70,6 +70,12 @@ typedef struct {
 typedef struct {
   int32_t format;         /* gsc_format: BC1 or BC7 in every block, or rate-controlled */
   uint32_t target_bpt_x4; /* rate target in quarter bits per coefficient texel (e.g. 12, 16, 24, 32) */
+  /* GSC_FMT_RATE only, optional (NULL = not wanted): the rate control codes every block
+   * both ways, and these receive the all-BC1 and all-BC7 layouts of the same planned order
+   * ([n_groups][16][8] and [n_groups][16][16] bytes, 16-byte aligned), i.e. exactly what
+   * GSC_FMT_BC1 and GSC_FMT_BC7 would write for d_perm. */
+  uint8_t* d_bc1_blocks;
+  uint8_t* d_bc7_blocks;
 } gsc_encode_params;
 
 /* One fixed-rate stream: every group in it keeps `bands` coefficients, the first
@@ -123,8 +129,8 @@ gsc_status gsc_quantise(gsc_ctx* ctx, const float* d_sh, int64_t n, const float*
  * of 14 stream modes per group under the budget floor(target_bpt_x4 * 4 * n) bits.
  * d_blocks receives the streams back to back (capacity n_groups * 256 bytes),
  * d_perm_out the final slot order, *h_table the stream table. Synchronises `stream`
- * before returning in GSC_FMT_RATE (the table depends on device results); returns
- * GSC_ERR_BUDGET if even the cheapest mode everywhere exceeds the budget. */
+ * before returning (the table carries the scales and, in GSC_FMT_RATE, device results);
+ * returns GSC_ERR_BUDGET if even the cheapest mode everywhere exceeds the budget. */
 gsc_status gsc_encode(gsc_ctx* ctx, const float* d_sh, int64_t n, const int32_t* d_perm, const float* d_scales,
                       const gsc_encode_params* ep, uint8_t* d_blocks, int32_t* d_perm_out, gsc_stream_table* h_table,
                       void* d_ws, size_t ws_bytes, void* stream);
@@ -163,6 +169,20 @@ gsc_status gsc_decode_blocks(gsc_ctx* ctx, const uint8_t* d_blocks, int64_t nblk
 /* Same through a texture object; synchronises `stream`. */
 gsc_status gsc_decode_blocks_tex(gsc_ctx* ctx, const uint8_t* d_blocks, int64_t nblk, int32_t format,
                                  uint8_t* d_rgba, void* stream);
+
+/* Measurement helpers (not part of the codec).
+ * gsc_launch_count: kernels this library has launched in this process so far.
+ * gsc_probe_int_peak: runs an integer microbenchmark (independent IADD3 / LOP3 / IMAD
+ * chains, 3 source-level operations per step, full occupancy) on the context's device
+ * and stores the achieved 32-bit integer operations per second; synchronises `stream`. */
+uint64_t gsc_launch_count(void);
+gsc_status gsc_probe_int_peak(gsc_ctx* ctx, double* ops_per_s, void* stream);
+/* Kernel timing: when enabled, each call records CUDA events on its own stream around its
+ * main kernels. gsc_kernel_time waits for the recorded events and returns the summed
+ * milliseconds and launch count of one kernel ("plan", "bc1_encode", "bc7_encode",
+ * "rate_select", "decode", "decode_eval", "decode_tex") since timing was last enabled. */
+gsc_status gsc_ctx_set_timing(gsc_ctx* ctx, int enable);
+gsc_status gsc_kernel_time(gsc_ctx* ctx, const char* name, double* ms, int64_t* launches);
 
 #ifdef __cplusplus
 }

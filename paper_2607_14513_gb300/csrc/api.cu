@@ -5,7 +5,120 @@
 
 #include "gsc_internal.cuh"
 
+#include <atomic>
+
 #define PINNED_BYTES 65536
+
+static std::atomic<unsigned long long> g_launches{0};
+void gsc_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+extern "C" uint64_t gsc_launch_count(void) { return g_launches.load(); }
+
+static const char* kTimerNames[T_COUNT] = {"plan", "bc1_encode", "bc7_encode", "rate_select", "decode",
+                                           "decode_eval", "decode_tex"};
+
+int gsc_timer_begin(gsc_ctx* c, int id, cudaStream_t st) {
+  if (!c || !c->timing) return -1;
+  if (c->n_recs == c->cap_recs) {
+    int cap = c->cap_recs ? 2 * c->cap_recs : 256;
+    gsc_timer_rec* r = (gsc_timer_rec*)realloc(c->recs, sizeof(gsc_timer_rec) * cap);
+    if (!r) return -1;
+    c->recs = r;
+    c->cap_recs = cap;
+  }
+  gsc_timer_rec& r = c->recs[c->n_recs];
+  if (cudaEventCreate(&r.a) != cudaSuccess) return -1;
+  if (cudaEventCreate(&r.b) != cudaSuccess) { cudaEventDestroy(r.a); return -1; }
+  r.id = id;
+  cudaEventRecord(r.a, st);
+  return c->n_recs++;
+}
+
+void gsc_timer_end(gsc_ctx* c, int rec, cudaStream_t st) {
+  if (!c || rec < 0) return;
+  cudaEventRecord(c->recs[rec].b, st);
+}
+
+static void timer_drain(gsc_ctx* c) {
+  for (int i = 0; i < c->n_recs; i++) {
+    gsc_timer_rec& r = c->recs[i];
+    cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      c->t_ms[r.id] += ms;
+      c->t_launches[r.id] += 1;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  c->n_recs = 0;
+}
+
+extern "C" gsc_status gsc_ctx_set_timing(gsc_ctx* c, int enable) {
+  if (!c) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  timer_drain(c);
+  for (int i = 0; i < T_COUNT; i++) { c->t_ms[i] = 0.0; c->t_launches[i] = 0; }
+  c->timing = enable ? 1 : 0;
+  return GSC_OK;
+}
+
+extern "C" gsc_status gsc_kernel_time(gsc_ctx* c, const char* name, double* ms, int64_t* launches) {
+  if (!c || !name || !ms || !launches) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  timer_drain(c);
+  for (int i = 0; i < T_COUNT; i++)
+    if (strcmp(name, kTimerNames[i]) == 0) { *ms = c->t_ms[i]; *launches = c->t_launches[i]; return GSC_OK; }
+  return GSC_ERR_INVALID_ARG;
+}
+
+// Integer throughput probe: 8 independent chains per thread, each step an add of three
+// values, a three-input logic op and a multiply-add.
+__global__ void k_int_peak(uint32_t* out, int iters, uint32_t seed) {
+  uint32_t a[8], b[8];
+#pragma unroll
+  for (int j = 0; j < 8; j++) { a[j] = seed * (threadIdx.x + 1) + j; b[j] = seed ^ (blockIdx.x * 77 + j); }
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      a[j] = a[j] + b[j] + 0x9E3779B9u;
+      b[j] = (b[j] ^ a[j]) | 0x5BD1E995u;
+      a[j] = a[j] * b[j] + 0x3C6EF372u;
+    }
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; j++) s ^= a[j] + b[j];
+  if (s == 0x12345678u) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+extern "C" gsc_status gsc_probe_int_peak(gsc_ctx* c, double* ops_per_s, void* stream) {
+  if (!c || !ops_per_s) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int threads = 256, blocks = c->sm_count * 8, iters = 4096;
+  uint32_t* d = nullptr;
+  GSC_CUDA(cudaMalloc(&d, sizeof(uint32_t) * threads * blocks));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; rep++) {
+    cudaEventRecord(e0, st);
+    gsc_count_launch(); k_int_peak<<<blocks, threads, 0, st>>>(d, iters, 0x1234567u + rep);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaError_t e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d);
+  if (e != cudaSuccess) return GSC_ERR_CUDA;
+  *ops_per_s = (double)threads * blocks * iters * 8.0 * 3.0 / (best * 1e-3);
+  return GSC_OK;
+}
 
 static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
@@ -60,6 +173,8 @@ extern "C" gsc_status gsc_ctx_create(gsc_ctx** out, int device) {
 extern "C" gsc_status gsc_ctx_destroy(gsc_ctx* c) {
   if (!c) return GSC_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
+  timer_drain(c);
+  free(c->recs);
   if (c->d_status) cudaFree(c->d_status);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   free(c);
@@ -101,6 +216,7 @@ extern "C" gsc_status gsc_plan_reorder(gsc_ctx* c, const float* d_pos, const flo
   if (!aligned(d_sh, 16) || !aligned(d_ws, 256)) return GSC_ERR_INVALID_ARG;
   if (pp->n > 0 && !d_ws) return GSC_ERR_INVALID_ARG;
   GSC_CUDA(cudaSetDevice(c->device));
+  GscTimed tm(c, T_PLAN, (cudaStream_t)stream);
   return plan_run(c, d_pos, d_sh, pp, d_perm, d_scales, d_ws, ws_bytes, (cudaStream_t)stream);
 }
 
@@ -145,7 +261,9 @@ extern "C" gsc_status gsc_encode(gsc_ctx* c, const float* d_sh, int64_t n, const
     memcpy(scales, hs, sizeof(scales));
     gsc_status s = GSC_OK;
     if (n > 0) {
-      s = rate_run(c, d_sh, n, d_perm, d_scales, ep->target_bpt_x4, d_blocks, d_perm_out, h_table, d_ws, ws_bytes, st);
+      if (!aligned(ep->d_bc1_blocks, 16) || !aligned(ep->d_bc7_blocks, 16)) return GSC_ERR_INVALID_ARG;
+      s = rate_run(c, d_sh, n, d_perm, d_scales, ep->target_bpt_x4, d_blocks, d_perm_out, h_table, d_ws, ws_bytes,
+                   ep->d_bc1_blocks, ep->d_bc7_blocks, st);
     } else {
       h_table->n_streams = GSC_MODES;
       h_table->format = GSC_FMT_RATE;
@@ -154,8 +272,10 @@ extern "C" gsc_status gsc_encode(gsc_ctx* c, const float* d_sh, int64_t n, const
     return s;
   }
   if (ep->format == GSC_FMT_BC1) {
+    GscTimed tm(c, T_BC1, st);
     GSC_CUDA(launch_bc1_groups(d_sh, d_perm, d_scales, ng, d_blocks, nullptr, nullptr, st));
   } else {
+    GscTimed tm(c, T_BC7, st);
     GSC_CUDA(launch_bc7_groups(d_sh, d_perm, d_scales, ng, d_blocks, nullptr, st));
   }
   if (ng > 0 && d_perm_out != d_perm)
@@ -216,6 +336,7 @@ extern "C" gsc_status gsc_decode(gsc_ctx* c, const gsc_stream_table* table, cons
   if (T.n_groups > 0 && (!d_blocks || !d_perm || !d_texels)) return GSC_ERR_INVALID_ARG;
   if (!aligned(d_blocks, 8) || !aligned(d_texels, 16)) return GSC_ERR_INVALID_ARG;
   GSC_CUDA(cudaSetDevice(c->device));
+  GscTimed tm(c, T_DECODE, (cudaStream_t)stream);
   GSC_CUDA(launch_decode(T, d_blocks, d_perm, d_texels, (cudaStream_t)stream));
   return GSC_OK;
 }
@@ -234,6 +355,7 @@ extern "C" gsc_status gsc_decode_eval_sh(gsc_ctx* c, const gsc_stream_table* tab
   if (T.n_groups > 0 && (!d_blocks || !d_perm || !d_rgb)) return GSC_ERR_INVALID_ARG;
   if (!aligned(d_blocks, 8) || !aligned(d_rgb, 4)) return GSC_ERR_INVALID_ARG;
   GSC_CUDA(cudaSetDevice(c->device));
+  GscTimed tm(c, T_EVAL, (cudaStream_t)stream);
   GSC_CUDA(launch_decode_eval(T, d_blocks, d_perm, d_dirs, d_pos, d_cams, V, out_order, d_rgb, c->sm_count,
                               (cudaStream_t)stream));
   return GSC_OK;
@@ -248,6 +370,7 @@ extern "C" gsc_status gsc_decode_tex(gsc_ctx* c, const gsc_stream_table* table, 
   if (T.n_groups > 0 && (!d_blocks || !d_perm || !d_texels)) return GSC_ERR_INVALID_ARG;
   if (!aligned(d_blocks, 8)) return GSC_ERR_INVALID_ARG;
   GSC_CUDA(cudaSetDevice(c->device));
+  GscTimed tm(c, T_TEX, (cudaStream_t)stream);
   return decode_tex_run(c, T, d_blocks, d_perm, d_texels, (cudaStream_t)stream);
 }
 

@@ -249,13 +249,13 @@ static int grid_for(int64_t work, int per_cta) {
 cudaError_t launch_bc1_groups(const float* sh, const int32_t* perm, const float* scales, int64_t n_groups,
                               uint8_t* blocks, uint32_t* sse1, uint32_t* sse0, cudaStream_t st) {
   if (n_groups <= 0) return cudaSuccess;
-  k_bc1_groups<<<grid_for(n_groups, STAGE_GROUPS), STAGE_THREADS, 0, st>>>(sh, perm, scales, n_groups,
+  gsc_count_launch(); k_bc1_groups<<<grid_for(n_groups, STAGE_GROUPS), STAGE_THREADS, 0, st>>>(sh, perm, scales, n_groups,
                                                                          reinterpret_cast<uint2*>(blocks), sse1, sse0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bc1_blocks(const uint8_t* tex, int64_t nblk, uint8_t* out, uint64_t* sse, cudaStream_t st) {
   if (nblk <= 0) return cudaSuccess;
-  k_bc1_blocks<<<grid_for(nblk, 128), 128, 0, st>>>(tex, nblk, reinterpret_cast<uint2*>(out), sse);
+  gsc_count_launch(); k_bc1_blocks<<<grid_for(nblk, 128), 128, 0, st>>>(tex, nblk, reinterpret_cast<uint2*>(out), sse);
   return cudaGetLastError();
 }

@@ -482,14 +482,14 @@ static int grid_for7(int64_t work, int per_cta) {
 cudaError_t launch_bc7_groups(const float* sh, const int32_t* perm, const float* scales, int64_t n_groups,
                               uint8_t* blocks, uint32_t* sse7, cudaStream_t st) {
   if (n_groups <= 0) return cudaSuccess;
-  k_bc7<<<grid_for7(n_groups, STAGE_GROUPS), STAGE_THREADS, 0, st>>>(
+  gsc_count_launch(); k_bc7<<<grid_for7(n_groups, STAGE_GROUPS), STAGE_THREADS, 0, st>>>(
       sh, perm, scales, n_groups, nullptr, 0, reinterpret_cast<uint4*>(blocks), sse7, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bc7_blocks(const uint8_t* tex, int64_t nblk, uint8_t* out, uint64_t* sse, cudaStream_t st) {
   if (nblk <= 0) return cudaSuccess;
-  k_bc7<<<grid_for7(nblk, STAGE_THREADS), STAGE_THREADS, 0, st>>>(nullptr, nullptr, nullptr, 0, tex, nblk,
+  gsc_count_launch(); k_bc7<<<grid_for7(nblk, STAGE_THREADS), STAGE_THREADS, 0, st>>>(nullptr, nullptr, nullptr, 0, tex, nblk,
                                                                 reinterpret_cast<uint4*>(out), nullptr, sse);
   return cudaGetLastError();
 }

@@ -201,7 +201,7 @@ cudaError_t launch_decode(const DevTable& T, const uint8_t* blocks, const int32_
   if (ns == 0) return cudaSuccess;
   int64_t grid = ceil_div64(ns, 256);
   if (grid > 152 * 16) grid = 152 * 16;
-  k_decode<<<(int)grid, 256, 0, st>>>(T, blocks, perm, texels);
+  gsc_count_launch(); k_decode<<<(int)grid, 256, 0, st>>>(T, blocks, perm, texels);
   return cudaGetLastError();
 }
 
@@ -300,7 +300,7 @@ cudaError_t launch_decode_eval(const DevTable& T, const uint8_t* blocks, const i
   int64_t grid = ceil_div64(ns, 256);
   int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * 8;
   if (grid > cap) grid = cap;
-  k_decode_eval<<<(int)grid, 256, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order, rgb);
+  gsc_count_launch(); k_decode_eval<<<(int)grid, 256, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order, rgb);
   return cudaGetLastError();
 }
 
@@ -326,7 +326,7 @@ cudaError_t launch_decode_blocks(const uint8_t* blocks, int64_t nblk, int format
   if (nblk <= 0) return cudaSuccess;
   int64_t grid = ceil_div64(nblk * 16, 256);
   if (grid > 152 * 16) grid = 152 * 16;
-  k_decode_blocks<<<(int)grid, 256, 0, st>>>(blocks, nblk, format, reinterpret_cast<uint32_t*>(rgba));
+  gsc_count_launch(); k_decode_blocks<<<(int)grid, 256, 0, st>>>(blocks, nblk, format, reinterpret_cast<uint32_t*>(rgba));
   return cudaGetLastError();
 }
 
@@ -408,7 +408,7 @@ gsc_status decode_blocks_tex_run(gsc_ctx* ctx, const uint8_t* blocks, int64_t nb
   if (e == cudaSuccess) {
     int64_t grid = ceil_div64(nblk * 16, 256);
     if (grid > 152 * 16) grid = 152 * 16;
-    k_tex_blocks<<<(int)grid, 256, 0, st>>>(img.tex, nblk, reinterpret_cast<uint32_t*>(rgba));
+    gsc_count_launch(); k_tex_blocks<<<(int)grid, 256, 0, st>>>(img.tex, nblk, reinterpret_cast<uint32_t*>(rgba));
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   }
@@ -485,7 +485,7 @@ gsc_status decode_tex_run(gsc_ctx* ctx, const DevTable& T, const uint8_t* blocks
   if (e == cudaSuccess) {
     int64_t grid = ceil_div64(T.n_groups * 16, 256);
     if (grid > 152 * 16) grid = 152 * 16;
-    k_gather_streams<<<(int)grid, 256, 0, st>>>(T, blocks, d_base, d_base + GSC_MODES, lin7, lin1);
+    gsc_count_launch(); k_gather_streams<<<(int)grid, 256, 0, st>>>(T, blocks, d_base, d_base + GSC_MODES, lin7, lin1);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -494,7 +494,7 @@ gsc_status decode_tex_run(gsc_ctx* ctx, const DevTable& T, const uint8_t* blocks
   if (e == cudaSuccess) {
     int64_t grid = ceil_div64(T.n_groups * 256, 256);
     if (grid > 152 * 16) grid = 152 * 16;
-    k_tex_streams<<<(int)grid, 256, 0, st>>>(T, i7.tex, i1.tex, d_base, d_base + GSC_MODES, perm, texels);
+    gsc_count_launch(); k_tex_streams<<<(int)grid, 256, 0, st>>>(T, i7.tex, i1.tex, d_base, d_base + GSC_MODES, perm, texels);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

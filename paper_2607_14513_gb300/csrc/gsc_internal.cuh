@@ -9,9 +9,18 @@
 #define GSC_SH 16
 #define GSC_MODES 14
 
+enum { T_PLAN = 0, T_BC1, T_BC7, T_RATE, T_DECODE, T_EVAL, T_TEX, T_COUNT };
+
+struct gsc_timer_rec { int id; cudaEvent_t a, b; };
+
 struct gsc_ctx {
   int device;
   int sm_count;
+  int timing;                 // record events around kernels
+  gsc_timer_rec* recs;        // pending records
+  int n_recs, cap_recs;
+  double t_ms[T_COUNT];
+  int64_t t_launches[T_COUNT];
   int* d_status;        // first device-side error code (0 = none)
   int* d_diag;          // where it happened (kernel-defined)
   void* h_pinned;       // small pinned host buffer for table read-back
@@ -26,6 +35,17 @@ struct gsc_ctx {
 
 static inline int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Host-side count of kernel launches (measurement only).
+void gsc_count_launch();
+// Event pair around a kernel when the context's timing is on (measurement only).
+int gsc_timer_begin(gsc_ctx* c, int id, cudaStream_t st);
+void gsc_timer_end(gsc_ctx* c, int rec, cudaStream_t st);
+struct GscTimed {
+  gsc_ctx* c; int rec; cudaStream_t st;
+  GscTimed(gsc_ctx* c_, int id, cudaStream_t st_) : c(c_), rec(gsc_timer_begin(c_, id, st_)), st(st_) {}
+  ~GscTimed() { gsc_timer_end(c, rec, st); }
+};
 
 // Records the first device-detected error into the context status word.
 __device__ __forceinline__ void gsc_record(int* status, int* diag, int code, int where) {
@@ -85,7 +105,7 @@ cudaError_t launch_bc7_blocks(const uint8_t* tex, int64_t nblk, uint8_t* out, ui
 size_t rate_ws_bytes(int64_t n_groups);
 gsc_status rate_run(gsc_ctx* ctx, const float* sh, int64_t n, const int32_t* perm, const float* scales,
                     uint32_t target_x4, uint8_t* blocks, int32_t* perm_out, gsc_stream_table* table, void* ws,
-                    size_t ws_bytes, cudaStream_t st);
+                    size_t ws_bytes, uint8_t* bc1_all, uint8_t* bc7_all, cudaStream_t st);
 
 // decode.cu
 cudaError_t decode_init_tables();

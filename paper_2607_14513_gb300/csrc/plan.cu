@@ -84,9 +84,9 @@ cudaError_t scan_exclusive(const T* in, T* out, int64_t n, uint64_t* total, void
   if (n <= 0) return cudaSuccess;
   int64_t nb = scan_blocks(n);
   uint64_t* sums = reinterpret_cast<uint64_t*>(ws);
-  k_scan_reduce<T><<<(int)nb, SCAN_BLOCK, 0, st>>>(in, n, sums);
-  k_scan_single<<<1, SCAN_BLOCK, 0, st>>>(sums, nb);
-  k_scan_apply<T><<<(int)nb, SCAN_BLOCK, 0, st>>>(in, n, sums, out, total);
+  gsc_count_launch(); k_scan_reduce<T><<<(int)nb, SCAN_BLOCK, 0, st>>>(in, n, sums);
+  gsc_count_launch(); k_scan_single<<<1, SCAN_BLOCK, 0, st>>>(sums, nb);
+  gsc_count_launch(); k_scan_apply<T><<<(int)nb, SCAN_BLOCK, 0, st>>>(in, n, sums, out, total);
   return cudaGetLastError();
 }
 template cudaError_t scan_exclusive<uint32_t>(const uint32_t*, uint32_t*, int64_t, uint64_t*, void*, cudaStream_t);
@@ -177,10 +177,10 @@ cudaError_t radix_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int key_
   uint32_t* vb = v2;
   int passes = (key_bits + 7) / 8;
   for (int p = 0; p < passes; p++) {
-    k_rs_hist<<<(int)nt, RS_THREADS, 0, st>>>(ka, n, 8 * p, hist, nt);
+    gsc_count_launch(); k_rs_hist<<<(int)nt, RS_THREADS, 0, st>>>(ka, n, 8 * p, hist, nt);
     cudaError_t e = scan_exclusive<uint32_t>(hist, hist, 256 * nt, nullptr, sws, st);
     if (e != cudaSuccess) return e;
-    k_rs_scatter<<<(int)nt, RS_THREADS, 0, st>>>(ka, va, n, 8 * p, hist, nt, kb, vb);
+    gsc_count_launch(); k_rs_scatter<<<(int)nt, RS_THREADS, 0, st>>>(ka, va, n, 8 * p, hist, nt, kb, vb);
     uint64_t* tk = ka; ka = kb; kb = tk;
     uint32_t* tv = va; va = vb; vb = tv;
   }
@@ -277,7 +277,7 @@ static int grid_stride(int64_t n, int threads, int cap = 152 * 8) {
 cudaError_t launch_quantise(const float* sh, int64_t n, const float* scales, uint8_t* q, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int64_t n4 = n * 12;
-  k_quantise<<<grid_stride(n4, 256), 256, 0, st>>>(reinterpret_cast<const float4*>(sh), n4, scales,
+  gsc_count_launch(); k_quantise<<<grid_stride(n4, 256), 256, 0, st>>>(reinterpret_cast<const float4*>(sh), n4, scales,
                                                     reinterpret_cast<uchar4*>(q));
   return cudaGetLastError();
 }
@@ -400,39 +400,39 @@ gsc_status plan_run(gsc_ctx* ctx, const float* pos, const float* sh, const gsc_p
   void* rws = c.take<uint8_t>((int64_t)radix_ws_bytes(n));
   // scales
   if (n == 0) {
-    k_fill_scales_one<<<1, 32, 0, st>>>(scales);
+    gsc_count_launch(); k_fill_scales_one<<<1, 32, 0, st>>>(scales);
   } else {
     const uint64_t m = 3ull * (uint64_t)n;
     const uint64_t r = ((uint64_t)pp->quantile_permille * m + 999) / 1000 - 1;
     GSC_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * GSC_SH * 256, st));
-    k_sel_init<<<1, 32, 0, st>>>(sel, r);
+    gsc_count_launch(); k_sel_init<<<1, 32, 0, st>>>(sel, r);
     const int64_t n4 = n * 12;
     const int g = grid_stride(n4, 256, ctx->sm_count * 4);
     for (int shift = 24; shift >= 0; shift -= 8) {
-      k_sel_hist<<<g, 256, 0, st>>>(reinterpret_cast<const float4*>(sh), n4, shift, sel, hist);
-      k_sel_pick<<<1, 32, 0, st>>>(sel, hist, shift);
+      gsc_count_launch(); k_sel_hist<<<g, 256, 0, st>>>(reinterpret_cast<const float4*>(sh), n4, shift, sel, hist);
+      gsc_count_launch(); k_sel_pick<<<1, 32, 0, st>>>(sel, hist, shift);
     }
-    k_sel_finish<<<1, 32, 0, st>>>(sel, scales);
+    gsc_count_launch(); k_sel_finish<<<1, 32, 0, st>>>(sel, scales);
   }
   GSC_CUDA(cudaGetLastError());
   if (ns == 0) return GSC_OK;
   if (!pp->sort || n == 0) {
-    k_finish_perm<<<grid_stride(ns, 256), 256, 0, st>>>(vals, n, ns, 1, perm);
+    gsc_count_launch(); k_finish_perm<<<grid_stride(ns, 256), 256, 0, st>>>(vals, n, ns, 1, perm);
     GSC_CUDA(cudaGetLastError());
     return GSC_OK;
   }
   // spatial rank: stable sort by 30-bit Morton code of the bounding-box grid
-  k_bbox_init<<<1, 32, 0, st>>>(bb);
-  k_bbox<<<grid_stride(n, 256, ctx->sm_count * 2), 256, 0, st>>>(pos, n, bb);
-  k_morton<<<grid_stride(n, 256), 256, 0, st>>>(pos, n, bb, keys, vals);
+  gsc_count_launch(); k_bbox_init<<<1, 32, 0, st>>>(bb);
+  gsc_count_launch(); k_bbox<<<grid_stride(n, 256, ctx->sm_count * 2), 256, 0, st>>>(pos, n, bb);
+  gsc_count_launch(); k_morton<<<grid_stride(n, 256), 256, 0, st>>>(pos, n, bb, keys, vals);
   GSC_CUDA(cudaGetLastError());
   GSC_CUDA(radix_sort_pairs(keys, vals, n, 30, rws, st));
   // slot order: stable sort by (chunk, colour key) of the rank-ordered Gaussians
-  k_colour_keys<<<grid_stride(n, 256), 256, 0, st>>>(sh, scales, n, pp->group_size, keys, vals);
+  gsc_count_launch(); k_colour_keys<<<grid_stride(n, 256), 256, 0, st>>>(sh, scales, n, pp->group_size, keys, vals);
   GSC_CUDA(cudaGetLastError());
   const uint64_t max_chunk = pp->group_size ? (uint64_t)((n - 1) / pp->group_size) : 0;
   GSC_CUDA(radix_sort_pairs(keys, vals, n, 24 + bits_for(max_chunk), rws, st));
-  k_finish_perm<<<grid_stride(ns, 256), 256, 0, st>>>(vals, n, ns, 0, perm);
+  gsc_count_launch(); k_finish_perm<<<grid_stride(ns, 256), 256, 0, st>>>(vals, n, ns, 0, perm);
   GSC_CUDA(cudaGetLastError());
   return GSC_OK;
 }

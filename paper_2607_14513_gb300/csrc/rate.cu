@@ -303,12 +303,14 @@ static int gsz(int64_t n, int threads, int cap) {
 
 gsc_status rate_run(gsc_ctx* ctx, const float* sh, int64_t n, const int32_t* perm, const float* scales,
                     uint32_t target_x4, uint8_t* blocks, int32_t* perm_out, gsc_stream_table* table, void* ws,
-                    size_t ws_bytes, cudaStream_t st) {
+                    size_t ws_bytes, uint8_t* bc1_all, uint8_t* bc7_all, cudaStream_t st) {
   const int64_t ng = ceil_div64(n, 16);
   if (ws_bytes < rate_ws_bytes(ng)) return GSC_ERR_OOM;
   Carve c{reinterpret_cast<uint8_t*>(ws), 0, ws_bytes};
   uint8_t* b1 = c.take<uint8_t>(8 * ng * 16);
   uint8_t* b7 = c.take<uint8_t>(16 * ng * 16);
+  if (bc1_all) b1 = bc1_all;   // the caller keeps the all-BC1 / all-BC7 codings
+  if (bc7_all) b7 = bc7_all;
   uint32_t* sse1 = c.take<uint32_t>(ng * 16);
   uint32_t* sse7 = c.take<uint32_t>(ng * 16);
   uint32_t* sse0 = c.take<uint32_t>(ng * 16);
@@ -331,25 +333,34 @@ gsc_status rate_run(gsc_ctx* ctx, const float* sh, int64_t n, const int32_t* per
   const int cap = ctx->sm_count * 8;
 
   GSC_CUDA(cudaMemsetAsync(S, 0, sizeof(RateState), st));
-  k_weights<<<1, 32, 0, st>>>(scales, w);
-  GSC_CUDA(launch_bc1_groups(sh, perm, scales, ng, b1, sse1, sse0, st));
-  GSC_CUDA(launch_bc7_groups(sh, perm, scales, ng, b7, sse7, st));
-  k_dtable<<<gsz(ng, 128, cap), 128, 0, st>>>(sse1, sse7, sse0, w, ng, dtab, step_l, step_m, n_steps, S);
-  k_search_init<<<1, 32, 0, st>>>(S, budget);
-  for (int p = 0; p < N_PASSES; p++) {
-    k_search_count<<<gsz(ng, 256, cap), 256, 0, st>>>(step_l, step_m, n_steps, ng, S, p);
-    k_search_narrow<<<1, 32, 0, st>>>(S, p);
+  gsc_count_launch(); k_weights<<<1, 32, 0, st>>>(scales, w);
+  {
+    GscTimed tm(ctx, T_BC1, st);
+    GSC_CUDA(launch_bc1_groups(sh, perm, scales, ng, b1, sse1, sse0, st));
   }
-  k_fill_prep<<<gsz(ng, 256, cap), 256, 0, st>>>(step_l, step_m, n_steps, ng, S, mode, alt, delta);
+  {
+    GscTimed tm(ctx, T_BC7, st);
+    GSC_CUDA(launch_bc7_groups(sh, perm, scales, ng, b7, sse7, st));
+  }
+  GscTimed tm_rate(ctx, T_RATE, st);
+  gsc_count_launch(); k_dtable<<<gsz(ng, 128, cap), 128, 0, st>>>(sse1, sse7, sse0, w, ng, dtab, step_l, step_m, n_steps, S);
+  gsc_count_launch(); k_search_init<<<1, 32, 0, st>>>(S, budget);
+  for (int p = 0; p < N_PASSES; p++) {
+    gsc_count_launch(); k_search_count<<<gsz(ng, 256, cap), 256, 0, st>>>(step_l, step_m, n_steps, ng, S, p);
+    gsc_count_launch(); k_search_narrow<<<1, 32, 0, st>>>(S, p);
+  }
+  gsc_count_launch(); k_fill_prep<<<gsz(ng, 256, cap), 256, 0, st>>>(step_l, step_m, n_steps, ng, S, mode, alt, delta);
   GSC_CUDA(cudaGetLastError());
   GSC_CUDA(scan_exclusive<uint64_t>(delta, prefix, ng, nullptr, sws, st));
-  k_fill_apply<<<gsz(ng, 256, cap), 256, 0, st>>>(ng, S, mode, alt, delta, prefix, keys, vals);
-  k_stream_info<<<1, 32, 0, st>>>(S, w, info);
+  gsc_count_launch(); k_fill_apply<<<gsz(ng, 256, cap), 256, 0, st>>>(ng, S, mode, alt, delta, prefix, keys, vals);
+  gsc_count_launch(); k_stream_info<<<1, 32, 0, st>>>(S, w, info);
   GSC_CUDA(cudaGetLastError());
   GSC_CUDA(radix_sort_pairs(keys, vals, ng, 4, rws, st));
-  k_assemble<<<gsz(ng, 128, cap), 128, 0, st>>>(keys, vals, ng, info, reinterpret_cast<const uint2*>(b1),
+  gsc_count_launch(); k_assemble<<<gsz(ng, 128, cap), 128, 0, st>>>(keys, vals, ng, info, reinterpret_cast<const uint2*>(b1),
                                                  reinterpret_cast<const uint2*>(b7), perm, blocks, perm_out);
   GSC_CUDA(cudaGetLastError());
+  gsc_timer_end(ctx, tm_rate.rec, st);
+  tm_rate.rec = -1;
   StreamInfo* h = reinterpret_cast<StreamInfo*>(ctx->h_pinned);
   GSC_CUDA(cudaMemcpyAsync(h, info, sizeof(StreamInfo), cudaMemcpyDeviceToHost, st));
   GSC_CUDA(cudaStreamSynchronize(st));

@@ -33,7 +33,8 @@ class PlanParams(C.Structure):
 
 
 class EncodeParams(C.Structure):
-    _fields_ = [("format", C.c_int32), ("target_bpt_x4", C.c_uint32)]
+    _fields_ = [("format", C.c_int32), ("target_bpt_x4", C.c_uint32), ("d_bc1_blocks", C.c_void_p),
+                ("d_bc7_blocks", C.c_void_p)]
 
 
 class Stream(C.Structure):
@@ -72,6 +73,10 @@ _SIGS = {
     "gsc_encode_blocks": [_P, _P, C.c_int64, C.c_int32, _P, _P, _P],
     "gsc_decode_blocks": [_P, _P, C.c_int64, C.c_int32, _P, _P],
     "gsc_decode_blocks_tex": [_P, _P, C.c_int64, C.c_int32, _P, _P],
+    "gsc_launch_count": [],
+    "gsc_probe_int_peak": [_P, C.POINTER(C.c_double), _P],
+    "gsc_ctx_set_timing": [_P, C.c_int],
+    "gsc_kernel_time": [_P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)],
 }
 
 
@@ -97,6 +102,7 @@ def load(path: str | None = None):
                 f.restype = C.c_int
             lib.gsc_status_string.restype = C.c_char_p
             lib.gsc_workspace_bytes.restype = C.c_size_t
+            lib.gsc_launch_count.restype = C.c_uint64
             _lib = lib
     return _lib
 
@@ -144,7 +150,7 @@ class Context:
 
     def workspace(self, n, fmt=FMT_BC1, target_x4=0):
         import torch
-        ep = EncodeParams(fmt, target_x4)
+        ep = EncodeParams(fmt, target_x4, None, None)
         nb = self.lib.gsc_workspace_bytes(n, C.byref(ep))
         return torch.empty(max(int(nb), 256), dtype=torch.uint8, device="cuda:%d" % self.device)
 
@@ -171,8 +177,12 @@ def gsc_quantise(ctx, sh, scales, stream=None):
     return q
 
 
-def gsc_encode(ctx, sh, perm, scales, fmt, target_x4=0, ws=None, out=None, perm_out=None, stream=None):
-    """-> (blocks uint8 [total_bytes], perm_out int32, StreamTable)."""
+def gsc_encode(ctx, sh, perm, scales, fmt, target_x4=0, ws=None, out=None, perm_out=None, stream=None,
+               bc1_all=None, bc7_all=None):
+    """-> (blocks uint8 [total_bytes], perm_out int32, StreamTable).
+
+    In rate mode, bc1_all / bc7_all (optional uint8 device tensors of n_groups*128 and
+    n_groups*256 bytes) receive the all-BC1 and all-BC7 codings of the planned order."""
     import torch
     n = sh.shape[0]
     ng = (n + 15) // 16
@@ -180,11 +190,46 @@ def gsc_encode(ctx, sh, perm, scales, fmt, target_x4=0, ws=None, out=None, perm_
     blocks = out if out is not None else torch.empty(max(ng * 256, 16), dtype=torch.uint8, device=dev)
     po = perm_out if perm_out is not None else torch.empty(max(ng * 16, 1), dtype=torch.int32, device=dev)
     ws = ws if ws is not None else ctx.workspace(n, fmt, target_x4)
-    ep = EncodeParams(fmt, target_x4)
+    ep = EncodeParams(fmt, target_x4, _ptr(bc1_all), _ptr(bc7_all))
     tab = StreamTable()
     _check(ctx.lib.gsc_encode(ctx.h, _ptr(sh), n, _ptr(perm), _ptr(scales), C.byref(ep), _ptr(blocks), _ptr(po),
                               C.byref(tab), _ptr(ws), ws.numel(), _stream(stream)), "gsc_encode")
     return blocks[:tab.total_bytes], po[:ng * 16], tab
+
+
+def forced_table(table, fmt):
+    """Stream table of the all-BC1 / all-BC7 layout that shares `table`'s scene and scales."""
+    t = StreamTable()
+    t.n_streams, t.format, t.n, t.n_groups = 1, fmt, table.n, table.n_groups
+    bpb = 16 if fmt == FMT_BC7 else 8
+    t.total_bytes = table.n_groups * 16 * bpb
+    t.used_bits = t.total_bytes * 8
+    t.scales[:] = table.scales[:]
+    t.weights[:] = table.weights[:]
+    t.s[0].bands, t.s[0].bc7_blocks = 16, (16 if fmt == FMT_BC7 else 0)
+    t.s[0].first_group, t.s[0].n_groups, t.s[0].byte_offset = 0, table.n_groups, 0
+    return t
+
+
+def int_peak(ctx, stream=None):
+    v = C.c_double(0.0)
+    _check(ctx.lib.gsc_probe_int_peak(ctx.h, C.byref(v), _stream(stream)), "gsc_probe_int_peak")
+    return v.value
+
+
+def set_timing(ctx, enable=True):
+    _check(ctx.lib.gsc_ctx_set_timing(ctx.h, 1 if enable else 0), "gsc_ctx_set_timing")
+
+
+def kernel_time(ctx, name):
+    """-> (total ms, launches) of one kernel since timing was enabled."""
+    ms, n = C.c_double(0.0), C.c_int64(0)
+    _check(ctx.lib.gsc_kernel_time(ctx.h, name.encode(), C.byref(ms), C.byref(n)), "gsc_kernel_time")
+    return ms.value, n.value
+
+
+def launch_count():
+    return int(load().gsc_launch_count())
 
 
 def gsc_decode(ctx, table, blocks, perm, stream=None):
