@@ -17,7 +17,8 @@
  *    pointers. The caller owns every buffer and the stream; the library owns only the
  *    context. Scratch memory is passed in as d_ws / ws_bytes (size from
  *    gsc_workspace_bytes); the library allocates no device memory on these paths,
- *    except gsc_decode_tex, which builds CUDA arrays for texture objects.
+ *    except the texture path (gsc_decode_tex, gsc_decode_blocks_tex), which builds CUDA
+ *    arrays for texture objects.
  *  - stream is a cudaStream_t (NULL = legacy default stream). Calls are asynchronous
  *    on that stream unless stated otherwise.
  *  - Argument errors are returned synchronously and nothing is launched. Errors the
@@ -153,8 +154,10 @@ gsc_status gsc_decode_eval_sh(gsc_ctx* ctx, const gsc_stream_table* table, const
 
 /* Same output as gsc_decode, sampled through CUDA BC1/BC7 texture objects (the GPU's
  * fixed-function block decoders, Sec. I): blocks are gathered into 2-D CUDA arrays
- * and read with point sampling; texel = rint(255 * f). Allocates and frees CUDA
- * arrays and staging buffers; synchronises `stream`. */
+ * (16384 blocks per row) and read with point sampling; texel = rint(255 * f). The
+ * arrays and staging buffers live in the context and are rebuilt (with a stream
+ * synchronisation) only when the block counts change; otherwise the call is
+ * asynchronous. Calls on one context must not overlap on different streams. */
 gsc_status gsc_decode_tex(gsc_ctx* ctx, const gsc_stream_table* table, const uint8_t* d_blocks,
                           const int32_t* d_perm, uint8_t* d_texels, void* stream);
 

@@ -152,6 +152,7 @@ extern "C" gsc_status gsc_ctx_create(gsc_ctx** out, int device) {
   if (!c) return GSC_ERR_OOM;
   c->device = device;
   c->sm_count = prop.multiProcessorCount;
+  c->tex[0].nblk = c->tex[1].nblk = -1;
   cudaError_t e = cudaMalloc(&c->d_status, 2 * sizeof(int));
   if (e == cudaSuccess) { c->d_diag = c->d_status + 1; e = cudaMemset(c->d_status, 0, 2 * sizeof(int)); }
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_pinned, PINNED_BYTES);
@@ -175,6 +176,8 @@ extern "C" gsc_status gsc_ctx_destroy(gsc_ctx* c) {
   cudaSetDevice(c->device);
   timer_drain(c);
   free(c->recs);
+  cudaDeviceSynchronize();
+  tex_cache_free(c);
   if (c->d_status) cudaFree(c->d_status);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   free(c);

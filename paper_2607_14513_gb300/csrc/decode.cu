@@ -164,50 +164,6 @@ __device__ __forceinline__ uint32_t decode_at(const uint8_t* __restrict__ blocks
   return bc7_texel(((uint64_t)w0.y << 32) | w0.x, ((uint64_t)w1.y << 32) | w1.x, t);
 }
 
-// ---- decode to texels ----------------------------------------------------------------------
-__global__ void k_decode(DevTable T, const uint8_t* __restrict__ blocks, const int32_t* __restrict__ perm,
-                         uint8_t* __restrict__ texels) {
-  const int64_t ns = (int64_t)T.n_groups * 16;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t o = __ldg(perm + s);
-    const int64_t g = s >> 4;
-    const int t = (int)(s & 15);
-    const int si = stream_of(T, g);
-    uint32_t w[12];
-#pragma unroll
-    for (int i = 0; i < 12; i++) w[i] = 0;
-#pragma unroll
-    for (int k = 0; k < 16; k++) {
-      uint32_t px = decode_at(blocks, locate(T, si, g, k), t) & 0xFFFFFFu;
-      // bytes 3k .. 3k+2 of the Gaussian's 48-byte row
-#pragma unroll
-      for (int c = 0; c < 3; c++) {
-        const int byte = 3 * k + c;
-        w[byte >> 2] |= ((px >> (8 * c)) & 255u) << (8 * (byte & 3));
-      }
-    }
-    if (o >= 0) {
-      uint4* dst = reinterpret_cast<uint4*>(texels + (int64_t)o * 48);
-      dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-      dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
-      dst[2] = make_uint4(w[8], w[9], w[10], w[11]);
-    }
-  }
-}
-
-cudaError_t launch_decode(const DevTable& T, const uint8_t* blocks, const int32_t* perm, uint8_t* texels,
-                          cudaStream_t st) {
-  const int64_t ns = (int64_t)T.n_groups * 16;
-  if (ns == 0) return cudaSuccess;
-  int64_t grid = ceil_div64(ns, 256);
-  if (grid > 152 * 16) grid = 152 * 16;
-  gsc_count_launch(); k_decode<<<(int)grid, 256, 0, st>>>(T, blocks, perm, texels);
-  return cudaGetLastError();
-}
-
-// ---- fused decode + SH evaluation ----------------------------------------------------------
-// Real SH to degree 3 (k = l*l + l + m, Condon-Shortley phase), constants from the closed
-// forms sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) with the sqrt(2) of m != 0 folded in.
 #define SH_C0 0.28209479177387814f   /* sqrt(1/(4 pi)) */
 #define SH_C1 0.4886025119029199f    /* sqrt(3/(4 pi)) */
 #define SH_C2A 1.0925484305920792f   /* sqrt(15/(4 pi)) */
@@ -219,88 +175,368 @@ cudaError_t launch_decode(const DevTable& T, const uint8_t* blocks, const int32_
 #define SH_C3D 0.3731763325901154f   /* sqrt(7/(16 pi)) */
 #define SH_C3E 1.445305721320277f    /* sqrt(105/(16 pi)) */
 
-__device__ __forceinline__ void sh_basis(float x, float y, float z, float (&Y)[16]) {
-  const float xx = x * x, yy = y * y, zz = z * z;
-  Y[0] = SH_C0;
-  Y[1] = -SH_C1 * y;
-  Y[2] = SH_C1 * z;
-  Y[3] = -SH_C1 * x;
-  Y[4] = SH_C2A * x * y;
-  Y[5] = -SH_C2A * y * z;
-  Y[6] = SH_C2B * (2.0f * zz - xx - yy);
-  Y[7] = -SH_C2A * x * z;
-  Y[8] = SH_C2C * (xx - yy);
-  Y[9] = -SH_C3A * y * (3.0f * xx - yy);
-  Y[10] = SH_C3B * x * y * z;
-  Y[11] = -SH_C3C * y * (4.0f * zz - xx - yy);
-  Y[12] = SH_C3D * z * (2.0f * zz - 3.0f * xx - 3.0f * yy);
-  Y[13] = -SH_C3C * x * (4.0f * zz - xx - yy);
-  Y[14] = SH_C3E * z * (xx - yy);
-  Y[15] = -SH_C3A * x * (xx - 3.0f * yy);
+// ---- warp-cooperative decode: one whole block per lane ----------------------------------
+// A warp owns two groups (32 slots, 32 blocks). Phase A: lane l decodes block k = l % 16 of
+// group l / 16 completely (the block is parsed once) into a shared tile; phase B: lane l
+// owns slot l % 16 of the same group and reads its 16 texels back. The tile index
+// gw * 272 + 17 k + t keeps both phases free of bank conflicts.
+#define WTILE 544
+
+struct DecTables {
+  uint32_t part2[64], part3[64];
+  uint8_t anc2[64], anc3a[64], anc3b[64];
+  uint32_t desc[8];
+  uint8_t wt[48];
+};
+
+__device__ __forceinline__ void load_tables(DecTables* s) {
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+    s->part2[i] = d_part2[i]; s->part3[i] = d_part3[i];
+    s->anc2[i] = d_anc2[i]; s->anc3a[i] = d_anc3a[i]; s->anc3b[i] = d_anc3b[i];
+  }
+  if (threadIdx.x < 8) {
+    const DModeInfo M = d_mode_info(threadIdx.x);
+    s->desc[threadIdx.x] = (uint32_t)M.ns | (M.pb << 2) | (M.rb << 5) | (M.isb << 7) | (M.cb << 8) | (M.ab << 11) |
+                           (M.epb << 15) | (M.spb << 16) | (M.ib << 17) | (M.ib2 << 20);
+  }
+  if (threadIdx.x < 48) s->wt[threadIdx.x] = (uint8_t)d_wgt(2 + threadIdx.x / 16, threadIdx.x % 16);
 }
 
-__global__ void k_decode_eval(DevTable T, const uint8_t* __restrict__ blocks, const int32_t* __restrict__ perm,
-                              const float* __restrict__ dirs, const float* __restrict__ pos,
-                              const float* __restrict__ cams, int V, int out_order, float* __restrict__ rgb) {
-  __shared__ float s_deq[16];
-  if (threadIdx.x < 16) s_deq[threadIdx.x] = __fdiv_rn(T.scales[threadIdx.x], 255.0f);
-  __syncthreads();
-  const int64_t ns = (int64_t)T.n_groups * 16;
-  const int64_t n = T.n;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t o = __ldg(perm + s);
-    const int64_t g = s >> 4;
-    const int t = (int)(s & 15);
-    if (o < 0) {
-      if (out_order == GSC_OUT_SLOT_ORDER)
-        for (int v = 0; v < V; v++) { float* d = rgb + ((int64_t)v * ns + s) * 3; d[0] = d[1] = d[2] = 0.0f; }
-      continue;
-    }
-    const int si = stream_of(T, g);
-    float x[16][3];
+// bits [off, off + 64) of the 128-bit block (off <= 127)
+__device__ __forceinline__ uint64_t shr128(uint64_t lo, uint64_t hi, int off) {
+  return off >= 64 ? (hi >> (off - 64)) : (off == 0 ? lo : ((lo >> off) | (hi << (64 - off))));
+}
+
+__device__ __forceinline__ void bc1_block(uint2 w, uint32_t (&tx)[16]) {
+  const uint32_t c0 = w.x & 0xFFFF, c1 = w.x >> 16;
+  const int r0 = c0 >> 11, g0 = (c0 >> 5) & 63, b0 = c0 & 31;
+  const int r1 = c1 >> 11, g1 = (c1 >> 5) & 63, b1 = c1 & 31;
+  const uint32_t p0 = dx5(r0) | (dx6(g0) << 8) | (dx5(b0) << 16) | 0xFF000000u;
+  const uint32_t p1 = dx5(r1) | (dx6(g1) << 8) | (dx5(b1) << 16) | 0xFF000000u;
+  uint32_t p2, p3;
+  if (c0 > c1) {
+    p2 = d_third5(r0, r1) | (d_third6(g0, g1) << 8) | (d_third5(b0, b1) << 16) | 0xFF000000u;
+    p3 = d_third5(r1, r0) | (d_third6(g1, g0) << 8) | (d_third5(b1, b0) << 16) | 0xFF000000u;
+  } else {
+    p2 = d_half5(r0, r1) | (d_half6(g0, g1) << 8) | (d_half5(b0, b1) << 16) | 0xFF000000u;
+    p3 = 0u;
+  }
 #pragma unroll
-    for (int k = 0; k < 16; k++) {
-      uint32_t px = decode_at(blocks, locate(T, si, g, k), t);
+  for (int t = 0; t < 16; t++) {
+    const uint32_t j = (w.y >> (2 * t)) & 3;
+    tx[t] = (j & 2) ? ((j & 1) ? p3 : p2) : ((j & 1) ? p1 : p0);
+  }
+}
+
+// Whole BC7 block, uniform control flow across modes (fields located from the mode descriptor).
+__device__ __forceinline__ void bc7_block(uint64_t lo, uint64_t hi, uint32_t (&tx)[16], const DecTables* S) {
+  const uint32_t b0 = (uint32_t)(lo & 0xFF);
+  const int mode = b0 ? __ffs(b0) - 1 : 0;
+  const uint32_t d = S->desc[mode];
+  const int ns = d & 3, pb = (d >> 2) & 7, rb = (d >> 5) & 3, isb = (d >> 7) & 1, cb = (d >> 8) & 7;
+  const int ab = (d >> 11) & 15, epb = (d >> 15) & 1, spb = (d >> 16) & 1, ib = (d >> 17) & 7, ib2 = (d >> 20) & 3;
+  int pos = mode + 1;
+  const uint64_t head = shr128(lo, hi, pos);
+  const int part = (int)(head & ((1u << pb) - 1u));
+  const int rot = (int)((head >> pb) & ((1u << rb) - 1u));
+  const int isbv = (int)((head >> (pb + rb)) & (uint64_t)isb);
+  pos += pb + rb + isb;
+  const uint32_t pm = ns == 2 ? S->part2[part] : (ns == 3 ? S->part3[part] : 0u);
+  const int a1 = ns == 2 ? S->anc2[part] : (ns == 3 ? S->anc3a[part] : 16);
+  const int a2 = ns == 3 ? S->anc3b[part] : 16;
+  const int cstart = pos, astart = cstart + 6 * ns * cb, pstart = astart + 2 * ns * ab;
+  const int istart = pstart + (epb ? 2 * ns : (spb ? ns : 0));
+  const int hp = epb | spb, nb = cb + hp, na = ab + epb;
+  const uint64_t pbits = shr128(lo, hi, pstart);
+  uint32_t E0rg[3], E0ba[3], E1rg[3], E1ba[3];
 #pragma unroll
-      for (int c = 0; c < 3; c++) x[k][c] = (float)((int)((px >> (8 * c)) & 255u) - 128) * s_deq[k];
-    }
-    float px0 = 0.f, py0 = 0.f, pz0 = 0.f;
-    if (cams) { px0 = __ldg(pos + 3 * o); py0 = __ldg(pos + 3 * o + 1); pz0 = __ldg(pos + 3 * o + 2); }
-    for (int v = 0; v < V; v++) {
-      float dx, dy, dz;
-      if (cams) {
-        dx = __ldg(cams + 3 * v) - px0; dy = __ldg(cams + 3 * v + 1) - py0; dz = __ldg(cams + 3 * v + 2) - pz0;
-      } else {
-        dx = __ldg(dirs + 3 * v); dy = __ldg(dirs + 3 * v + 1); dz = __ldg(dirs + 3 * v + 2);
+  for (int s = 0; s < 3; s++) {
+    E0rg[s] = E0ba[s] = E1rg[s] = E1ba[s] = 0;
+    if (s < ns) {
+      const int p0 = epb ? (int)((pbits >> (2 * s)) & 1) : (spb ? (int)((pbits >> s) & 1) : 0);
+      const int p1 = epb ? (int)((pbits >> (2 * s + 1)) & 1) : p0;
+      int v0[4], v1[4];
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const uint64_t f = shr128(lo, hi, cstart + (c * ns + s) * 2 * cb);
+        const int c0 = (int)(f & ((1u << cb) - 1u)), c1 = (int)((f >> cb) & ((1u << cb) - 1u));
+        v0[c] = d_expand(hp ? (c0 << 1) | p0 : c0, nb);
+        v1[c] = d_expand(hp ? (c1 << 1) | p1 : c1, nb);
       }
-      float n2 = dx * dx + dy * dy + dz * dz;
-      if (n2 > 0.0f) { float r = rsqrtf(n2); dx *= r; dy *= r; dz *= r; }
-      else { dx = 0.0f; dy = 0.0f; dz = 1.0f; }
-      float Y[16];
-      sh_basis(dx, dy, dz, Y);
-      float acc[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-      for (int k = 0; k < 16; k++)
-#pragma unroll
-        for (int c = 0; c < 3; c++) acc[c] = fmaf(x[k][c], Y[k], acc[c]);
-      float* d;
-      if (out_order == GSC_OUT_VIEW_MAJOR) d = rgb + ((int64_t)v * n + o) * 3;
-      else if (out_order == GSC_OUT_SLOT_ORDER) d = rgb + ((int64_t)v * ns + s) * 3;
-      else d = rgb + ((int64_t)o * V + v) * 3;
-      d[0] = acc[0]; d[1] = acc[1]; d[2] = acc[2];
+      if (ab) {
+        const uint64_t f = shr128(lo, hi, astart + 2 * s * ab);
+        const int c0 = (int)(f & ((1u << ab) - 1u)), c1 = (int)((f >> ab) & ((1u << ab) - 1u));
+        v0[3] = d_expand(epb ? (c0 << 1) | p0 : c0, na);
+        v1[3] = d_expand(epb ? (c1 << 1) | p1 : c1, na);
+      } else {
+        v0[3] = v1[3] = 255;
+      }
+      E0rg[s] = v0[0] | (v0[1] << 16); E0ba[s] = v0[2] | (v0[3] << 16);
+      E1rg[s] = v1[0] | (v1[1] << 16); E1ba[s] = v1[2] | (v1[3] << 16);
     }
   }
+  uint64_t prim = shr128(lo, hi, istart);
+  uint64_t sec = ib2 ? shr128(lo, hi, istart + 16 * ib - 1) : 0;
+  const int cib = (ib2 && isbv) ? ib2 : ib, aib = ib2 ? (isbv ? ib : ib2) : ib;
+  const uint32_t rsel = rot == 0 ? 0x3210u : (rot == 1 ? 0x0213u : (rot == 2 ? 0x1230u : 0x2310u));
+#pragma unroll
+  for (int t = 0; t < 16; t++) {
+    const int anc = (t == 0) | (t == a1) | (t == a2);
+    const int n1 = ib - anc;
+    const int pi = (int)(prim & ((1u << n1) - 1u));
+    prim >>= n1;
+    int si = pi;
+    if (ib2) {
+      const int n2 = ib2 - (t == 0);
+      si = (int)(sec & ((1u << n2) - 1u));
+      sec >>= n2;
+    }
+    const int ci = (ib2 && isbv) ? si : pi;
+    const int ai = ib2 ? (isbv ? pi : si) : pi;
+    const int cw = S->wt[(cib - 2) * 16 + ci], aw = S->wt[(aib - 2) * 16 + ai];
+    const int s = (pm >> (2 * t)) & 3;
+    const uint32_t e0rg = s == 0 ? E0rg[0] : (s == 1 ? E0rg[1] : E0rg[2]);
+    const uint32_t e1rg = s == 0 ? E1rg[0] : (s == 1 ? E1rg[1] : E1rg[2]);
+    const uint32_t e0ba = s == 0 ? E0ba[0] : (s == 1 ? E0ba[1] : E0ba[2]);
+    const uint32_t e1ba = s == 0 ? E1ba[0] : (s == 1 ? E1ba[1] : E1ba[2]);
+    const uint32_t rg = (((64 - cw) * e0rg + cw * e1rg + 0x00200020u) >> 6) & 0x00FF00FFu;
+    const uint32_t bb = (((64 - cw) * (e0ba & 0xFFFF) + cw * (e1ba & 0xFFFF) + 32) >> 6);
+    const uint32_t aa = (((64 - aw) * (e0ba >> 16) + aw * (e1ba >> 16) + 32) >> 6);
+    const uint32_t px = (rg & 0xFF) | ((rg >> 16) << 8) | (bb << 16) | (aa << 24);
+    tx[t] = b0 ? __byte_perm(px, 0, rsel) : 0u;
+  }
+}
+
+// Block k of group g of the stream table into 16 packed texels (RGB + A); 128 where dropped.
+template <int KIND>
+__device__ __forceinline__ void block_texels(const DevTable& T, const uint8_t* __restrict__ blocks, int64_t g, int k,
+                                             uint32_t (&tx)[16], const DecTables* S) {
+  if (KIND == 7) {
+    const uint4 w = __ldg(reinterpret_cast<const uint4*>(blocks) + g * 16 + k);
+    bc7_block(((uint64_t)w.y << 32) | w.x, ((uint64_t)w.w << 32) | w.z, tx, S);
+  } else if (KIND == 1) {
+    bc1_block(__ldg(reinterpret_cast<const uint2*>(blocks) + g * 16 + k), tx);
+  } else {
+    const int si = stream_of(T, g);
+    const BlockLoc L = locate(T, si, g, k);
+    if (L.kind == 7) {
+      const uint2* p = reinterpret_cast<const uint2*>(blocks + L.off);
+      const uint2 w0 = __ldg(p), w1 = __ldg(p + 1);
+      bc7_block(((uint64_t)w0.y << 32) | w0.x, ((uint64_t)w1.y << 32) | w1.x, tx, S);
+    } else if (L.kind == 1) {
+      bc1_block(__ldg(reinterpret_cast<const uint2*>(blocks + L.off)), tx);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 16; t++) tx[t] = 0xFF808080u;
+    }
+  }
+}
+
+__device__ __forceinline__ int table_kind(const DevTable& T) {
+  if (T.n_streams == 1 && T.bands[0] == 16 && T.bc7[0] == 16 && T.byte_offset[0] == 0) return 7;
+  if (T.n_streams == 1 && T.bands[0] == 16 && T.bc7[0] == 0 && T.byte_offset[0] == 0) return 1;
+  return 0;
+}
+
+// exact (q - 128) as float: 0x4B0000qq is 2^23 + q
+__device__ __forceinline__ float byte_m128(uint32_t v, int c) {
+  return __uint_as_float(__byte_perm(v, 0x4B000000u, 0x7650u | (uint32_t)c)) - 8388736.0f;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_decode2(DevTable T, const uint8_t* __restrict__ blocks,
+                                                 const int32_t* __restrict__ perm, uint8_t* __restrict__ texels) {
+  __shared__ DecTables S;
+  __shared__ uint32_t tile[8][WTILE];
+  load_tables(&S);
+  __syncthreads();
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, gw = l >> 4, kt = l & 15;
+  const int64_t npairs = ((int64_t)T.n_groups + 1) / 2;
+  uint32_t* my = tile[w] + gw * 272;
+  for (int64_t pr = (int64_t)blockIdx.x * 8 + w; pr < npairs; pr += (int64_t)gridDim.x * 8) {
+    const int64_t g = pr * 2 + gw;
+    const bool live = g < T.n_groups;
+    uint32_t tx[16];
+    if (live) block_texels<KIND>(T, blocks, g, kt, tx, &S);
+#pragma unroll
+    for (int t = 0; t < 16; t++) my[17 * kt + t] = live ? tx[t] : 0u;
+    __syncwarp();
+    const int32_t o = live ? __ldg(perm + g * 16 + kt) : -1;
+    if (o >= 0) {
+      uint32_t wv[12];
+#pragma unroll
+      for (int i = 0; i < 12; i++) wv[i] = 0;
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        const uint32_t px = my[17 * k + kt];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          const int byte = 3 * k + c;
+          wv[byte >> 2] |= ((px >> (8 * c)) & 255u) << (8 * (byte & 3));
+        }
+      }
+      uint4* dst = reinterpret_cast<uint4*>(texels + (int64_t)o * 48);
+      dst[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+      dst[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+      dst[2] = make_uint4(wv[8], wv[9], wv[10], wv[11]);
+    }
+    __syncwarp();
+  }
+}
+
+// SH basis polynomials without their constants; the constants (with signs) are folded
+// into the per-coefficient dequantisation factors s_k / 255 * C_k.
+__device__ __forceinline__ void sh_poly2(float2 x, float2 y, float2 z, float2 (&P)[16]) {
+  const float2 xx = __fmul2_rn(x, x), yy = __fmul2_rn(y, y), zz = __fmul2_rn(z, z);
+  const float2 xy = __fmul2_rn(x, y), yz = __fmul2_rn(y, z), xz = __fmul2_rn(x, z);
+  const float2 two = make_float2(2.f, 2.f), three = make_float2(3.f, 3.f), four = make_float2(4.f, 4.f);
+  const float2 xpy = __fadd2_rn(xx, yy);
+  const float2 xmy = __fadd2_rn(xx, make_float2(-yy.x, -yy.y));
+  const float2 t2 = __ffma2_rn(two, zz, make_float2(-xpy.x, -xpy.y));           // 2zz - xx - yy
+  const float2 t4 = __ffma2_rn(four, zz, make_float2(-xpy.x, -xpy.y));          // 4zz - xx - yy
+  const float2 t3 = __ffma2_rn(make_float2(-3.f, -3.f), xpy, __fmul2_rn(two, zz));  // 2zz - 3xx - 3yy
+  P[0] = make_float2(1.f, 1.f);
+  P[1] = y; P[2] = z; P[3] = x;
+  P[4] = xy; P[5] = yz; P[6] = t2; P[7] = xz; P[8] = xmy;
+  P[9] = __fmul2_rn(y, __ffma2_rn(three, xx, make_float2(-yy.x, -yy.y)));        // y (3xx - yy)
+  P[10] = __fmul2_rn(xy, z);
+  P[11] = __fmul2_rn(y, t4);
+  P[12] = __fmul2_rn(z, t3);
+  P[13] = __fmul2_rn(x, t4);
+  P[14] = __fmul2_rn(z, xmy);
+  P[15] = __fmul2_rn(x, __ffma2_rn(make_float2(-3.f, -3.f), yy, xx));           // x (xx - 3yy)
+}
+
+__constant__ float c_shc[16] = {SH_C0, -SH_C1, SH_C1, -SH_C1, SH_C2A, -SH_C2A, SH_C2B, -SH_C2A, SH_C2C,
+                                -SH_C3A, SH_C3B, -SH_C3C, SH_C3D, -SH_C3C, SH_C3E, -SH_C3A};
+
+template <int KIND, bool CAMS>
+__global__ void __launch_bounds__(256) k_eval2(DevTable T, const uint8_t* __restrict__ blocks,
+                                               const int32_t* __restrict__ perm, const float* __restrict__ dirs,
+                                               const float* __restrict__ pos, const float* __restrict__ cams, int V,
+                                               int out_order, float* __restrict__ rgb) {
+  __shared__ DecTables S;
+  __shared__ uint32_t tile[8][WTILE];
+  __shared__ float s_view[3][64];
+  __shared__ float s_deq[16];
+  load_tables(&S);
+  for (int i = threadIdx.x; i < V; i += blockDim.x) {
+    const float* src = CAMS ? cams : dirs;
+    s_view[0][i] = src[3 * i]; s_view[1][i] = src[3 * i + 1]; s_view[2][i] = src[3 * i + 2];
+  }
+  if (threadIdx.x < 16) s_deq[threadIdx.x] = __fmul_rn(__fdiv_rn(T.scales[threadIdx.x], 255.0f), c_shc[threadIdx.x]);
+  __syncthreads();
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, gw = l >> 4, kt = l & 15;
+  const int64_t npairs = ((int64_t)T.n_groups + 1) / 2;
+  const int64_t n = T.n, ns = (int64_t)T.n_groups * 16;
+  uint32_t* my = tile[w] + gw * 272;
+  for (int64_t pr = (int64_t)blockIdx.x * 8 + w; pr < npairs; pr += (int64_t)gridDim.x * 8) {
+    const int64_t g = pr * 2 + gw;
+    const bool live = g < T.n_groups;
+    {
+      uint32_t tx[16];
+      if (live) block_texels<KIND>(T, blocks, g, kt, tx, &S);
+#pragma unroll
+      for (int t = 0; t < 16; t++) my[17 * kt + t] = live ? tx[t] : 0u;
+    }
+    __syncwarp();
+    const int64_t s = g * 16 + kt;
+    const int32_t o = live ? __ldg(perm + s) : -1;
+    if (o >= 0) {
+      // dequantised coefficients with the SH constants folded in
+      float xr[16], xg[16], xb[16];
+#pragma unroll
+      for (int k = 0; k < 16; k++) {
+        const uint32_t px = my[17 * k + kt];
+        const float f = s_deq[k];
+        xr[k] = byte_m128(px, 0) * f; xg[k] = byte_m128(px, 1) * f; xb[k] = byte_m128(px, 2) * f;
+      }
+      float2 p0 = make_float2(0.f, 0.f), p1 = p0, p2 = p0;
+      if (CAMS) { const float px = __ldg(pos + 3 * (int64_t)o), py = __ldg(pos + 3 * (int64_t)o + 1), pz = __ldg(pos + 3 * (int64_t)o + 2);
+                  p0 = make_float2(px, px); p1 = make_float2(py, py); p2 = make_float2(pz, pz); }
+      for (int v = 0; v < V; v += 2) {
+        const int v1 = v + 1 < V ? v + 1 : v;
+        float2 dx = make_float2(s_view[0][v], s_view[0][v1]);
+        float2 dy = make_float2(s_view[1][v], s_view[1][v1]);
+        float2 dz = make_float2(s_view[2][v], s_view[2][v1]);
+        if (CAMS) {
+          dx = __fadd2_rn(dx, make_float2(-p0.x, -p0.y));
+          dy = __fadd2_rn(dy, make_float2(-p1.x, -p1.y));
+          dz = __fadd2_rn(dz, make_float2(-p2.x, -p2.y));
+        }
+        const float2 n2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        float2 r;
+        r.x = n2.x > 0.f ? rsqrtf(n2.x) : 0.f;
+        r.y = n2.y > 0.f ? rsqrtf(n2.y) : 0.f;
+        dx = __fmul2_rn(dx, r); dy = __fmul2_rn(dy, r); dz = __fmul2_rn(dz, r);
+        if (n2.x <= 0.f) { dx.x = 0.f; dy.x = 0.f; dz.x = 1.f; }
+        if (n2.y <= 0.f) { dx.y = 0.f; dy.y = 0.f; dz.y = 1.f; }
+        float2 P[16];
+        sh_poly2(dx, dy, dz, P);
+        float2 ar = make_float2(xr[0], xr[0]), ag = make_float2(xg[0], xg[0]), ab = make_float2(xb[0], xb[0]);
+#pragma unroll
+        for (int k = 1; k < 16; k++) {
+          ar = __ffma2_rn(make_float2(xr[k], xr[k]), P[k], ar);
+          ag = __ffma2_rn(make_float2(xg[k], xg[k]), P[k], ag);
+          ab = __ffma2_rn(make_float2(xb[k], xb[k]), P[k], ab);
+        }
+        if (out_order == GSC_OUT_GAUSS_MAJOR) {
+          float* d = rgb + ((int64_t)o * V + v) * 3;
+          d[0] = ar.x; d[1] = ag.x; d[2] = ab.x;
+          if (v + 1 < V) { d[3] = ar.y; d[4] = ag.y; d[5] = ab.y; }
+        } else {
+          const int64_t idx = out_order == GSC_OUT_VIEW_MAJOR ? o : s;
+          const int64_t stride = out_order == GSC_OUT_VIEW_MAJOR ? n : ns;
+          float* d = rgb + ((int64_t)v * stride + idx) * 3;
+          d[0] = ar.x; d[1] = ag.x; d[2] = ab.x;
+          if (v + 1 < V) { d += stride * 3; d[0] = ar.y; d[1] = ag.y; d[2] = ab.y; }
+        }
+      }
+    } else if (live && out_order == GSC_OUT_SLOT_ORDER) {
+      for (int v = 0; v < V; v++) { float* d = rgb + ((int64_t)v * ns + s) * 3; d[0] = d[1] = d[2] = 0.f; }
+    }
+    __syncwarp();
+  }
+}
+
+static int kind_of(const DevTable& T) {
+  if (T.n_streams == 1 && T.bands[0] == 16 && T.byte_offset[0] == 0) return T.bc7[0] == 16 ? 7 : (T.bc7[0] == 0 ? 1 : 0);
+  return 0;
+}
+
+static int eval_grid(int64_t n_groups, int sm_count) {
+  int64_t pairs = (n_groups + 1) / 2;
+  int64_t g = ceil_div64(pairs, 8);
+  int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * 8;
+  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+cudaError_t launch_decode(const DevTable& T, const uint8_t* blocks, const int32_t* perm, uint8_t* texels,
+                          cudaStream_t st) {
+  if (T.n_groups == 0) return cudaSuccess;
+  const int grid = eval_grid(T.n_groups, 152);
+  switch (kind_of(T)) {
+    case 7: gsc_count_launch(); k_decode2<7><<<grid, 256, 0, st>>>(T, blocks, perm, texels); break;
+    case 1: gsc_count_launch(); k_decode2<1><<<grid, 256, 0, st>>>(T, blocks, perm, texels); break;
+    default: gsc_count_launch(); k_decode2<0><<<grid, 256, 0, st>>>(T, blocks, perm, texels); break;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_decode_eval(const DevTable& T, const uint8_t* blocks, const int32_t* perm, const float* dirs,
                                const float* pos, const float* cams, int V, int out_order, float* rgb, int sm_count,
                                cudaStream_t st) {
-  const int64_t ns = (int64_t)T.n_groups * 16;
-  if (ns == 0) return cudaSuccess;
-  int64_t grid = ceil_div64(ns, 256);
-  int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * 8;
-  if (grid > cap) grid = cap;
-  gsc_count_launch(); k_decode_eval<<<(int)grid, 256, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order, rgb);
+  if (T.n_groups == 0) return cudaSuccess;
+  const int grid = eval_grid(T.n_groups, sm_count);
+  const int kind = kind_of(T);
+#define EVAL_LAUNCH(K, C) \
+  do { gsc_count_launch(); k_eval2<K, C><<<grid, 256, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order, rgb); } while (0)
+  if (cams) {
+    if (kind == 7) EVAL_LAUNCH(7, true); else if (kind == 1) EVAL_LAUNCH(1, true); else EVAL_LAUNCH(0, true);
+  } else {
+    if (kind == 7) EVAL_LAUNCH(7, false); else if (kind == 1) EVAL_LAUNCH(1, false); else EVAL_LAUNCH(0, false);
+  }
+#undef EVAL_LAUNCH
   return cudaGetLastError();
 }
 
@@ -340,7 +576,7 @@ struct TexImg {
   cudaTextureObject_t tex = 0;
 };
 
-static cudaError_t make_tex(const uint8_t* d_lin, int64_t nblk, int bc7, TexImg* out) {
+static cudaError_t make_tex(const uint8_t* d_lin, int64_t nblk, int bc7, TexImg* out, cudaStream_t st) {
   const int64_t w = nblk < TEXW ? (nblk > 0 ? nblk : 1) : TEXW;
   const int64_t h = nblk > 0 ? ceil_div64(nblk, w) : 1;
   const int bpb = bc7 ? 16 : 8;
@@ -351,13 +587,13 @@ static cudaError_t make_tex(const uint8_t* d_lin, int64_t nblk, int bc7, TexImg*
   if (nblk > 0) {
     const int64_t full_rows = nblk / w, rem = nblk % w;
     if (full_rows > 0) {
-      e = cudaMemcpy2DToArray(out->arr, 0, 0, d_lin, (size_t)(w * bpb), (size_t)(w * bpb), (size_t)full_rows,
-                              cudaMemcpyDeviceToDevice);
+      e = cudaMemcpy2DToArrayAsync(out->arr, 0, 0, d_lin, (size_t)(w * bpb), (size_t)(w * bpb),
+                                   (size_t)full_rows, cudaMemcpyDeviceToDevice, st);
       if (e != cudaSuccess) return e;
     }
     if (rem > 0) {
-      e = cudaMemcpy2DToArray(out->arr, 0, (size_t)full_rows, d_lin + full_rows * w * bpb, (size_t)(rem * bpb),
-                              (size_t)(rem * bpb), 1, cudaMemcpyDeviceToDevice);
+      e = cudaMemcpy2DToArrayAsync(out->arr, 0, (size_t)full_rows, d_lin + full_rows * w * bpb,
+                                   (size_t)(rem * bpb), (size_t)(rem * bpb), 1, cudaMemcpyDeviceToDevice, st);
       if (e != cudaSuccess) return e;
     }
   }
@@ -404,7 +640,7 @@ gsc_status decode_blocks_tex_run(gsc_ctx* ctx, const uint8_t* blocks, int64_t nb
   if (nblk <= 0) return GSC_OK;
   TexImg img;
   GSC_CUDA(cudaStreamSynchronize(st));
-  cudaError_t e = make_tex(blocks, nblk, format == GSC_FMT_BC7, &img);
+  cudaError_t e = make_tex(blocks, nblk, format == GSC_FMT_BC7, &img, st);
   if (e == cudaSuccess) {
     int64_t grid = ceil_div64(nblk * 16, 256);
     if (grid > 152 * 16) grid = 152 * 16;
@@ -416,10 +652,11 @@ gsc_status decode_blocks_tex_run(gsc_ctx* ctx, const uint8_t* blocks, int64_t nb
   return e == cudaSuccess ? GSC_OK : GSC_ERR_CUDA;
 }
 
+struct TexBases { int64_t b7[GSC_MODES], b1[GSC_MODES]; };
+
 // Gathers every kept block of the streams into one linear buffer per format.
-__global__ void k_gather_streams(DevTable T, const uint8_t* __restrict__ blocks, const int64_t* __restrict__ base7,
-                                 const int64_t* __restrict__ base1, uint8_t* __restrict__ lin7,
-                                 uint8_t* __restrict__ lin1) {
+__global__ void k_gather_streams(DevTable T, TexBases B, const uint8_t* __restrict__ blocks,
+                                 uint8_t* __restrict__ lin7, uint8_t* __restrict__ lin1) {
   const int64_t total = (int64_t)T.n_groups * 16;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t g = i >> 4;
@@ -430,17 +667,16 @@ __global__ void k_gather_streams(DevTable T, const uint8_t* __restrict__ blocks,
     const int64_t gi = g - T.first_group[si];
     if (L.kind == 7) {
       const uint2* src = reinterpret_cast<const uint2*>(blocks + L.off);
-      uint2* dst = reinterpret_cast<uint2*>(lin7 + (base7[si] + gi * j + k) * 16);
+      uint2* dst = reinterpret_cast<uint2*>(lin7 + (B.b7[si] + gi * j + k) * 16);
       dst[0] = src[0]; dst[1] = src[1];
     } else if (L.kind == 1) {
-      *reinterpret_cast<uint2*>(lin1 + (base1[si] + gi * (b - j) + (k - j)) * 8) =
+      *reinterpret_cast<uint2*>(lin1 + (B.b1[si] + gi * (b - j) + (k - j)) * 8) =
           *reinterpret_cast<const uint2*>(blocks + L.off);
     }
   }
 }
 
-__global__ void k_tex_streams(DevTable T, cudaTextureObject_t tex7, cudaTextureObject_t tex1,
-                              const int64_t* __restrict__ base7, const int64_t* __restrict__ base1,
+__global__ void k_tex_streams(DevTable T, TexBases B, cudaTextureObject_t tex7, cudaTextureObject_t tex1,
                               const int32_t* __restrict__ perm, uint8_t* __restrict__ texels) {
   const int64_t total = (int64_t)T.n_groups * 16 * 16;  // (slot, k)
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -454,54 +690,105 @@ __global__ void k_tex_streams(DevTable T, cudaTextureObject_t tex7, cudaTextureO
     const int j = T.bc7[si], b = T.bands[si];
     const int64_t gi = g - T.first_group[si];
     uint32_t px;
-    if (k < j) px = tex_fetch(tex7, base7[si] + gi * j + k, t);
-    else if (k < b) px = tex_fetch(tex1, base1[si] + gi * (b - j) + (k - j), t);
+    if (k < j) px = tex_fetch(tex7, B.b7[si] + gi * j + k, t);
+    else if (k < b) px = tex_fetch(tex1, B.b1[si] + gi * (b - j) + (k - j), t);
     else px = 0x808080u;
     uint8_t* d = texels + (int64_t)o * 48 + 3 * k;
     d[0] = px & 255; d[1] = (px >> 8) & 255; d[2] = (px >> 16) & 255;
   }
 }
 
+void tex_cache_free(gsc_ctx* c) {
+  for (int f = 0; f < 2; f++) {
+    TexImg img;
+    img.arr = c->tex[f].arr;
+    img.tex = c->tex[f].tex;
+    free_tex(&img);
+    c->tex[f].arr = nullptr;
+    c->tex[f].tex = 0;
+    c->tex[f].nblk = -1;
+    if (c->tex_lin[f]) cudaFree(c->tex_lin[f]);
+    c->tex_lin[f] = nullptr;
+    c->tex_lin_bytes[f] = 0;
+  }
+}
+
+// Staging buffer and texture of one format, reused while the block count is unchanged.
+static cudaError_t tex_slot(gsc_ctx* c, int f, int64_t nblk, cudaStream_t st, bool* fresh) {
+  const size_t need = (size_t)(nblk > 0 ? nblk : 1) * (f ? 16 : 8);
+  *fresh = false;
+  if (c->tex_lin_bytes[f] < need) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    if (c->tex_lin[f]) cudaFree(c->tex_lin[f]);
+    c->tex_lin[f] = nullptr;
+    c->tex_lin_bytes[f] = 0;
+    e = cudaMalloc(&c->tex_lin[f], need);
+    if (e != cudaSuccess) return e;
+    c->tex_lin_bytes[f] = need;
+  }
+  if (c->tex[f].nblk != nblk || !c->tex[f].arr) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    TexImg old;
+    old.arr = c->tex[f].arr;
+    old.tex = c->tex[f].tex;
+    free_tex(&old);
+    c->tex[f].arr = nullptr;
+    c->tex[f].tex = 0;
+    c->tex[f].nblk = -1;
+    *fresh = true;
+  }
+  return cudaSuccess;
+}
+
 gsc_status decode_tex_run(gsc_ctx* ctx, const DevTable& T, const uint8_t* blocks, const int32_t* perm,
                           uint8_t* texels, cudaStream_t st) {
-  (void)ctx;
   if (T.n_groups == 0) return GSC_OK;
-  int64_t h7[GSC_MODES], h1[GSC_MODES], n7 = 0, n1 = 0;
+  TexBases B;
+  int64_t n7 = 0, n1 = 0;
+  for (int i = 0; i < GSC_MODES; i++) { B.b7[i] = 0; B.b1[i] = 0; }
   for (int i = 0; i < T.n_streams; i++) {
-    h7[i] = n7; h1[i] = n1;
-    int64_t ng = T.stream_groups[i];
-    n7 += ng * T.bc7[i];
-    n1 += ng * (T.bands[i] - T.bc7[i]);
+    B.b7[i] = n7; B.b1[i] = n1;
+    n7 += T.stream_groups[i] * T.bc7[i];
+    n1 += T.stream_groups[i] * (T.bands[i] - T.bc7[i]);
   }
-  uint8_t *lin7 = nullptr, *lin1 = nullptr;
-  int64_t* d_base = nullptr;
-  TexImg i7, i1;
-  cudaError_t e = cudaMalloc(&d_base, sizeof(int64_t) * 2 * GSC_MODES);
-  if (e == cudaSuccess) e = cudaMalloc(&lin7, (size_t)(n7 > 0 ? n7 : 1) * 16);
-  if (e == cudaSuccess) e = cudaMalloc(&lin1, (size_t)(n1 > 0 ? n1 : 1) * 8);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_base, h7, sizeof(int64_t) * GSC_MODES, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_base + GSC_MODES, h1, sizeof(int64_t) * GSC_MODES, cudaMemcpyHostToDevice, st);
+  bool fresh7 = false, fresh1 = false;
+  cudaError_t e = tex_slot(ctx, 1, n7, st, &fresh7);
+  if (e == cudaSuccess) e = tex_slot(ctx, 0, n1, st, &fresh1);
+  if (e != cudaSuccess) return GSC_ERR_CUDA;
+  int64_t grid = ceil_div64(T.n_groups * 16, 256);
+  if (grid > 152 * 16) grid = 152 * 16;
+  gsc_count_launch(); k_gather_streams<<<(int)grid, 256, 0, st>>>(T, B, blocks, ctx->tex_lin[1], ctx->tex_lin[0]);
+  e = cudaGetLastError();
+  // (re)create the arrays if the sizes changed, then copy the staged blocks in stream order
+  for (int f = 1; f >= 0 && e == cudaSuccess; f--) {
+    const int64_t nb = f ? n7 : n1;
+    const bool fresh = f ? fresh7 : fresh1;
+    TexImg img;
+    img.arr = ctx->tex[f].arr;
+    img.tex = ctx->tex[f].tex;
+    if (fresh) {
+      e = make_tex(ctx->tex_lin[f], nb, f, &img, st);
+      ctx->tex[f].arr = img.arr;
+      ctx->tex[f].tex = img.tex;
+      ctx->tex[f].nblk = nb;
+    } else if (nb > 0) {
+      const int64_t w = nb < TEXW ? nb : TEXW, bpb = f ? 16 : 8;
+      const int64_t full_rows = nb / w, rem = nb % w;
+      if (full_rows > 0)
+        e = cudaMemcpy2DToArrayAsync(img.arr, 0, 0, ctx->tex_lin[f], (size_t)(w * bpb), (size_t)(w * bpb),
+                                     (size_t)full_rows, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess && rem > 0)
+        e = cudaMemcpy2DToArrayAsync(img.arr, 0, (size_t)full_rows, ctx->tex_lin[f] + full_rows * w * bpb,
+                                     (size_t)(rem * bpb), (size_t)(rem * bpb), 1, cudaMemcpyDeviceToDevice, st);
+    }
+  }
   if (e == cudaSuccess) {
-    int64_t grid = ceil_div64(T.n_groups * 16, 256);
-    if (grid > 152 * 16) grid = 152 * 16;
-    gsc_count_launch(); k_gather_streams<<<(int)grid, 256, 0, st>>>(T, blocks, d_base, d_base + GSC_MODES, lin7, lin1);
+    int64_t g2 = ceil_div64(T.n_groups * 256, 256);
+    if (g2 > 152 * 16) g2 = 152 * 16;
+    gsc_count_launch(); k_tex_streams<<<(int)g2, 256, 0, st>>>(T, B, ctx->tex[1].tex, ctx->tex[0].tex, perm, texels);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess) e = make_tex(lin7, n7, 1, &i7);
-  if (e == cudaSuccess) e = make_tex(lin1, n1, 0, &i1);
-  if (e == cudaSuccess) {
-    int64_t grid = ceil_div64(T.n_groups * 256, 256);
-    if (grid > 152 * 16) grid = 152 * 16;
-    gsc_count_launch(); k_tex_streams<<<(int)grid, 256, 0, st>>>(T, i7.tex, i1.tex, d_base, d_base + GSC_MODES, perm, texels);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  free_tex(&i7);
-  free_tex(&i1);
-  if (lin7) cudaFree(lin7);
-  if (lin1) cudaFree(lin1);
-  if (d_base) cudaFree(d_base);
   return e == cudaSuccess ? GSC_OK : GSC_ERR_CUDA;
 }

@@ -13,8 +13,17 @@ enum { T_PLAN = 0, T_BC1, T_BC7, T_RATE, T_DECODE, T_EVAL, T_TEX, T_COUNT };
 
 struct gsc_timer_rec { int id; cudaEvent_t a, b; };
 
+struct gsc_tex_slot {
+  cudaArray_t arr;
+  cudaTextureObject_t tex;
+  int64_t nblk;
+};
+
 struct gsc_ctx {
   int device;
+  gsc_tex_slot tex[2];        // texture path: [0] BC1, [1] BC7, kept between calls
+  uint8_t* tex_lin[2];
+  size_t tex_lin_bytes[2];
   int sm_count;
   int timing;                 // record events around kernels
   gsc_timer_rec* recs;        // pending records
@@ -127,5 +136,6 @@ cudaError_t launch_decode_eval(const DevTable& t, const uint8_t* blocks, const i
 cudaError_t launch_decode_blocks(const uint8_t* blocks, int64_t nblk, int format, uint8_t* rgba, cudaStream_t st);
 gsc_status decode_tex_run(gsc_ctx* ctx, const DevTable& t, const uint8_t* blocks, const int32_t* perm,
                           uint8_t* texels, cudaStream_t st);
+void tex_cache_free(gsc_ctx* ctx);
 gsc_status decode_blocks_tex_run(gsc_ctx* ctx, const uint8_t* blocks, int64_t nblk, int format, uint8_t* rgba,
                                  cudaStream_t st);

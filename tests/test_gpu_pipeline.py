@@ -94,6 +94,61 @@ def test_rate_streams_bit_exact(ctx, O, target_x4):
     ctx.sync()
     assert np.array_equal(tex.cpu().numpy(), tex_ref)
     assert np.array_equal(tex_hw.cpu().numpy(), tex_ref)
+    # fused evaluation of the mixed streams (dropped coefficients decode to zero)
+    dirs = S.make_dirs(5, 703)
+    rgb = gsc.gsc_decode_eval_sh(ctx, tab, blocks, perm_out, dirs=_dev(dirs))
+    out, ab = O.eval_sh(tex_ref, ref["scales"], dirs=dirs, want_abs=True)
+    ctx.sync()
+    _check_sh(rgb.cpu().numpy(), out, ab)
+
+
+@pytest.mark.parametrize("fmt,n", [(1, 300_000), (7, 40_000)])
+def test_texture_path_spans_rows(ctx, O, fmt, n):
+    # more blocks than one texture row (16384 blocks): the texture unit and the software
+    # decoder agree on every texel, twice in a row (the cached arrays are reused), and
+    # sampled groups match the oracle block for block
+    from paper_2607_14513_gb300 import gsc
+    sc = S.make_scene(n, 950 + fmt, heavy_frac=0.1)
+    perm, scales = gsc.gsc_plan_reorder(ctx, _dev(sc.pos), _dev(sc.sh))
+    blocks, perm_out, tab = gsc.gsc_encode(ctx, _dev(sc.sh), perm, scales, fmt)
+    for _ in range(2):
+        tex = gsc.gsc_decode(ctx, tab, blocks, perm_out)
+        tex_hw = gsc.gsc_decode_tex(ctx, tab, blocks, perm_out)
+        ctx.sync()
+        assert torch.equal(tex, tex_hw)
+    q = O.quantise(sc.sh, scales.cpu().numpy())
+    pc = perm_out.cpu().numpy()
+    ng = pc.size // 16
+    rng = np.random.default_rng(951)
+    groups = np.unique(np.concatenate([[0, ng - 1], rng.integers(0, ng, size=14)]))
+    st = O.stage(q, np.concatenate([pc[16 * g:16 * g + 16] for g in groups]))
+    ob, _ = O.encode_blocks(st.reshape(-1, 16, 3), fmt)
+    bpb = 16 if fmt == 7 else 8
+    gb = blocks.cpu().numpy().reshape(ng, 16, bpb)[groups].reshape(-1, bpb)
+    assert np.array_equal(gb, ob)
+
+
+def test_decode_eval_at_scale(ctx, O):
+    # 200k Gaussians, 8 cameras, every output order: FP32 against FP64 evaluated from the
+    # GPU-decoded texels (the decode itself is pinned bit for bit elsewhere)
+    from paper_2607_14513_gb300 import gsc
+    n = 200_000
+    sc = S.make_scene(n, 960, clusters=16)
+    cams = S.make_cams(8, 961)
+    perm, scales = gsc.gsc_plan_reorder(ctx, _dev(sc.pos), _dev(sc.sh))
+    blocks, perm_out, tab = gsc.gsc_encode(ctx, _dev(sc.sh), perm, scales, 1)
+    tex = gsc.gsc_decode(ctx, tab, blocks, perm_out).cpu().numpy()
+    sel = np.random.default_rng(962).choice(n, 3000, replace=False)
+    out, ab = O.eval_sh(tex[sel], scales.cpu().numpy(), pos=sc.pos[sel], cams=cams, want_abs=True)
+    pc = perm_out.cpu().numpy()
+    slot_of = np.empty(n, np.int64)
+    slot_of[pc[pc >= 0]] = np.nonzero(pc >= 0)[0]
+    for order in (0, 1, 2):
+        rgb = gsc.gsc_decode_eval_sh(ctx, tab, blocks, perm_out, pos=_dev(sc.pos), cams=_dev(cams), out_order=order)
+        ctx.sync()
+        g = rgb.cpu().numpy()
+        got = {0: lambda: g[:, sel], 1: lambda: g[:, slot_of[sel]], 2: lambda: g[sel].transpose(1, 0, 2)}[order]()
+        _check_sh(got, out, ab)
 
 
 def test_rate_budget_error(ctx):
