@@ -119,6 +119,23 @@ size_t gsc_workspace_bytes(int64_t n, const gsc_encode_params* ep);
 gsc_status gsc_plan_reorder(gsc_ctx* ctx, const float* d_pos, const float* d_sh, const gsc_plan_params* pp,
                             int32_t* d_perm, float* d_scales, void* d_ws, size_t ws_bytes, void* stream);
 
+/* Allocation-free form of gsc_plan_reorder (the paper has no counterpart: this is a
+ * service for callers that cannot call cudaMalloc, e.g. a host framework that owns all
+ * device memory and forbids foreign allocations, or a latency-bound loop that must not
+ * pay for cudaMalloc's implicit synchronisation or risk an out-of-memory failure there).
+ * Same arguments and results as gsc_plan_reorder without d_ws / ws_bytes: its scratch is
+ * a 2 MiB array inside the library that every GPU loading the library keeps until the
+ * process exits. Limits: 0 <= n <= GSC_PLAN_STATIC_MAX_N (65536) Gaussians; larger n
+ * returns GSC_ERR_INVALID_ARG and launches nothing. It calls no cudaMalloc, cudaFree or
+ * allocating library routine. The first call on a device looks up the array's device
+ * address (with that device current); make that first call before any stream capture.
+ * All calls share the one array, which keeps the last call's contents (the call clears
+ * what it needs): calls that overlap on the GPU, from any stream or context of the
+ * process, race on it and must be serialised by the caller. */
+#define GSC_PLAN_STATIC_MAX_N 65536
+gsc_status gsc_plan_reorder_static(gsc_ctx* ctx, const float* d_pos, const float* d_sh, const gsc_plan_params* pp,
+                                   int32_t* d_perm, float* d_scales, void* stream);
+
 /* Sec. V-A: q = clamp(128 + rint(fl(fl(x / s_k) * 255)), 0, 255), round half to even.
  * d_sh [n][16][3] float -> d_q [n][16][3] uint8. */
 gsc_status gsc_quantise(gsc_ctx* ctx, const float* d_sh, int64_t n, const float* d_scales, uint8_t* d_q, void* stream);

@@ -1,6 +1,8 @@
 // plan.cu -- per-scene scales, quantisation and the reorder plan (Sec. V-A; Sec. III-C,
 // Fig. Bit4Scan), plus the device-wide radix sort and scan the plan and the rate
 // control share. No host synchronisation: everything is queued on the caller's stream.
+#include <mutex>
+
 #include "gsc_internal.cuh"
 
 // ---- scan (exclusive, 64-bit) -------------------------------------------------------------
@@ -435,4 +437,39 @@ gsc_status plan_run(gsc_ctx* ctx, const float* pos, const float* sh, const gsc_p
   gsc_count_launch(); k_finish_perm<<<grid_stride(ns, 256), 256, 0, st>>>(vals, n, ns, 0, perm);
   GSC_CUDA(cudaGetLastError());
   return GSC_OK;
+}
+
+// ---- allocation-free variant of gsc_plan_reorder ------------------------------------------
+// Scratch lives in this file-scope device array instead of a caller workspace. Every GPU
+// that loads the library holds it (2 MiB) until the process exits. Its device address is
+// looked up once per device, with that device current, on the first call there.
+#define GSC_PLAN_STATIC_BYTES (2u << 20)
+#define GSC_MAX_DEVICES 64
+static __device__ __align__(256) uint8_t g_plan_scratch[GSC_PLAN_STATIC_BYTES];
+static std::mutex g_plan_scratch_mu;
+static void* g_plan_scratch_ptr[GSC_MAX_DEVICES];
+
+extern "C" gsc_status gsc_plan_reorder_static(gsc_ctx* c, const float* d_pos, const float* d_sh,
+                                              const gsc_plan_params* pp, int32_t* d_perm, float* d_scales,
+                                              void* stream) {
+  if (!c || !pp || pp->n < 0 || pp->n > GSC_PLAN_STATIC_MAX_N) return GSC_ERR_INVALID_ARG;
+  if (pp->group_size < 0 || pp->group_size % 16 != 0) return GSC_ERR_INVALID_ARG;
+  if (pp->quantile_permille == 0 || pp->quantile_permille > 1000) return GSC_ERR_INVALID_ARG;
+  if (pp->sort != 0 && pp->sort != 1) return GSC_ERR_INVALID_ARG;
+  if (!d_scales || (pp->n > 0 && (!d_sh || !d_perm || (pp->sort && !d_pos)))) return GSC_ERR_INVALID_ARG;
+  if (((uintptr_t)d_sh % 16) != 0) return GSC_ERR_INVALID_ARG;
+  if (c->device < 0 || c->device >= GSC_MAX_DEVICES) return GSC_ERR_UNSUPPORTED;
+  if (plan_ws_bytes(pp->n) > GSC_PLAN_STATIC_BYTES) return GSC_ERR_OOM;
+  GSC_CUDA(cudaSetDevice(c->device));
+  void* ws = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_plan_scratch_mu);
+    if (!g_plan_scratch_ptr[c->device]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_plan_scratch) != cudaSuccess || !p) return GSC_ERR_CUDA;
+      g_plan_scratch_ptr[c->device] = p;
+    }
+    ws = g_plan_scratch_ptr[c->device];
+  }
+  return plan_run(c, d_pos, d_sh, pp, d_perm, d_scales, ws, GSC_PLAN_STATIC_BYTES, (cudaStream_t)stream);
 }

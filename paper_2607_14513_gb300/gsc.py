@@ -64,6 +64,7 @@ _SIGS = {
     "gsc_status_string": [C.c_int],
     "gsc_workspace_bytes": [C.c_int64, C.POINTER(EncodeParams)],
     "gsc_plan_reorder": [_P, _P, _P, C.POINTER(PlanParams), _P, _P, _P, C.c_size_t, _P],
+    "gsc_plan_reorder_static": [_P, _P, _P, C.POINTER(PlanParams), _P, _P, _P],
     "gsc_quantise": [_P, _P, C.c_int64, _P, _P, _P],
     "gsc_encode": [_P, _P, C.c_int64, _P, _P, C.POINTER(EncodeParams), _P, _P, C.POINTER(StreamTable), _P,
                    C.c_size_t, _P],
