@@ -83,41 +83,50 @@ struct FitOut {
   uint32_t idx_lo, idx_hi;  // 4 bits per texel, texel t at bits 4t of the 64-bit pair
 };
 
-__device__ __forceinline__ void set_idx(FitOut* o, int t, int j) {
-  if (t < 8) o->idx_lo |= (uint32_t)j << (4 * t); else o->idx_hi |= (uint32_t)j << (4 * (t - 8));
+// Texels of the thread's block: tex[t * STAGE_STRIDE], packed r | g << 8 | b << 16 (top byte 0).
+// Palette search (exact): with pk_j = 16 |p_j|^2 + j, the key pk_j - 32 dot(v, p_j) equals
+// 16 (|v - p_j|^2 - |v|^2) + j, so its minimum gives the first index of least error
+// (key & 15) and that error minus |v|^2 (key >> 4, an exact floor shift).
+__device__ __forceinline__ uint32_t pack_rgb(int r, int g, int b) { return (uint32_t)r | ((uint32_t)g << 8) | ((uint32_t)b << 16); }
+
+template <int F>
+__device__ __forceinline__ int best_key(uint32_t v, const uint32_t (&pal)[F], const int (&pk)[F]) {
+  int key = 0x7FFFFFFF;
+#pragma unroll
+  for (int j = 0; j < F; j++) key = min(key, pk[j] - 32 * (int)__dp4a(v, pal[j], 0u));
+  return key;
 }
 
 // Fits subset s of partition `part` (2 bits per texel) over the channels in CHMASK.
 template <int IB, int CHMASK, int PT, int BITS, bool OUT>
-__device__ __forceinline__ uint32_t fit_subset(const uint32_t (&tx)[16], uint32_t part, int s, FitOut* out) {
+__device__ __forceinline__ uint32_t fit_subset(const uint32_t* __restrict__ tex, uint32_t part, int s, FitOut* out,
+                                               const uint16_t* __restrict__ sq) {
   constexpr int F = 1 << IB;
   constexpr int NCH = ((CHMASK >> 0) & 1) + ((CHMASK >> 1) & 1) + ((CHMASK >> 2) & 1);
-  int ch[3];
+  constexpr uint32_t CM = ((CHMASK & 1) ? 0xFFu : 0u) | ((CHMASK & 2) ? 0xFF00u : 0u) | ((CHMASK & 4) ? 0xFF0000u : 0u);
+  int ch[3] = {0, 0, 0};
   {
     int k = 0;
 #pragma unroll
     for (int c = 0; c < 3; c++) if ((CHMASK >> c) & 1) ch[k++] = c;
   }
-  int n = 0, lo[NCH], hi[NCH], s1[NCH], s2[NCH][NCH];
+  int n = 0, lo[NCH], hi[NCH], s1[NCH], s2[3];
 #pragma unroll
-  for (int i = 0; i < NCH; i++) {
-    lo[i] = 255; hi[i] = 0; s1[i] = 0;
-#pragma unroll
-    for (int j = 0; j < NCH; j++) s2[i][j] = 0;
-  }
-#pragma unroll
+  for (int i = 0; i < NCH; i++) { lo[i] = 255; hi[i] = 0; s1[i] = 0; }
+  s2[0] = s2[1] = s2[2] = 0;  // channel pairs (0,1), (0,2), (1,2) of the coded channels
+#pragma unroll 4
   for (int t = 0; t < 16; t++) {
     if ((int)((part >> (2 * t)) & 3) != s) continue;
+    const uint32_t v = tex[t * STAGE_STRIDE];
     n++;
-    int v[NCH];
-#pragma unroll
-    for (int i = 0; i < NCH; i++) v[i] = chan(tx[t], ch[i]);
+    int c[NCH];
 #pragma unroll
     for (int i = 0; i < NCH; i++) {
-      lo[i] = min(lo[i], v[i]); hi[i] = max(hi[i], v[i]); s1[i] += v[i];
-#pragma unroll
-      for (int j = i + 1; j < NCH; j++) s2[i][j] += v[i] * v[j];
+      c[i] = (v >> (8 * ch[i])) & 255;
+      lo[i] = min(lo[i], c[i]); hi[i] = max(hi[i], c[i]); s1[i] += c[i];
     }
+    if (NCH >= 2) s2[0] += c[0] * c[NCH >= 2 ? 1 : 0];
+    if (NCH >= 3) { s2[1] += c[0] * c[NCH >= 3 ? 2 : 0]; s2[2] += c[NCH >= 2 ? 1 : 0] * c[NCH >= 3 ? 2 : 0]; }
   }
   if (OUT) { out->idx_lo = 0; out->idx_hi = 0; out->p[0] = out->p[1] = 0;
 #pragma unroll
@@ -131,48 +140,40 @@ __device__ __forceinline__ uint32_t fit_subset(const uint32_t (&tx)[16], uint32_
   for (int i = 0; i < NCH; i++) {
     bool flip = false;
     if (i != ref) {
-      int cross = 0;
-#pragma unroll
-      for (int a = 0; a < NCH; a++)
-#pragma unroll
-        for (int b = a + 1; b < NCH; b++)
-          if ((a == ref && b == i) || (a == i && b == ref)) cross = s2[a][b];
+      const int a = min(i, ref), b = max(i, ref);
+      const int cross = (a == 0 && b == 1) ? s2[0] : ((a == 0 && b == 2) ? s2[1] : s2[2]);
       flip = (n * cross - s1[ref] * s1[i]) < 0;
     }
     e0[i] = flip ? lo[i] : hi[i];
     e1[i] = flip ? hi[i] : lo[i];
   }
-  // initial indices against the unquantised endpoints, accumulated straight into LS sums
+  // initial indices against the unquantised endpoints, accumulated straight into the LS sums
   int saa = 0, sbb = 0, sab = 0, sav[NCH], sbv[NCH];
   {
-    int pal[F][NCH];
+    uint32_t pal[F];
+    int pk[F];
 #pragma unroll
-    for (int j = 0; j < F; j++)
+    for (int j = 0; j < F; j++) {
+      int cc[3] = {0, 0, 0};
 #pragma unroll
-      for (int i = 0; i < NCH; i++) pal[j][i] = interp64(e0[i], e1[i], wgt<IB>(j));
+      for (int i = 0; i < NCH; i++) cc[ch[i]] = interp64(e0[i], e1[i], wgt<IB>(j));
+      pal[j] = pack_rgb(cc[0], cc[1], cc[2]);
+      pk[j] = 16 * (int)__dp4a(pal[j], pal[j], 0u) + j;
+    }
 #pragma unroll
     for (int i = 0; i < NCH; i++) { sav[i] = 0; sbv[i] = 0; }
-#pragma unroll
+#pragma unroll 2
     for (int t = 0; t < 16; t++) {
       if ((int)((part >> (2 * t)) & 3) != s) continue;
-      int v[NCH];
-#pragma unroll
-      for (int i = 0; i < NCH; i++) v[i] = chan(tx[t], ch[i]);
-      int best = 0x7FFFFFFF, bj = 0;
-#pragma unroll
-      for (int j = 0; j < F; j++) {
-        int e = 0;
-#pragma unroll
-        for (int i = 0; i < NCH; i++) { int d = v[i] - pal[j][i]; e += d * d; }
-        if (e < best) { best = e; bj = j; }
-      }
-      int w = wgt<IB>(bj), a = 64 - w;
+      const uint32_t v = tex[t * STAGE_STRIDE] & CM;
+      const int bj = best_key<F>(v, pal, pk) & 15;
+      const int w = wgt<IB>(bj), a = 64 - w;
       saa += a * a; sbb += w * w; sab += a * w;
 #pragma unroll
-      for (int i = 0; i < NCH; i++) { sav[i] += a * v[i]; sbv[i] += w * v[i]; }
+      for (int i = 0; i < NCH; i++) { const int c = (v >> (8 * ch[i])) & 255; sav[i] += a * c; sbv[i] += w * c; }
     }
   }
-  long long det = (long long)saa * sbb - (long long)sab * sab;
+  const long long det = (long long)saa * sbb - (long long)sab * sab;
   if (det != 0) {
 #pragma unroll
     for (int i = 0; i < NCH; i++) {
@@ -187,37 +188,35 @@ __device__ __forceinline__ uint32_t fit_subset(const uint32_t (&tx)[16], uint32_
   for (int cmb = 0; cmb < NCOMBO; cmb++) {
     const int p0 = PT == PT_UNIQUE ? (cmb & 1) : (PT == PT_SHARED ? cmb : 0);
     const int p1 = PT == PT_UNIQUE ? (cmb >> 1) : (PT == PT_SHARED ? cmb : 0);
-    const uint16_t* q0 = g_qtab[qid(BITS, HP, p0)];
-    const uint16_t* q1 = g_qtab[qid(BITS, HP, p1)];
-    int c0[NCH], c1[NCH], pal[F][NCH];
+    const uint16_t* q0 = sq + 256 * qid(BITS, HP, p0);
+    const uint16_t* q1 = sq + 256 * qid(BITS, HP, p1);
+    int c0[NCH], c1[NCH], v0[3] = {0, 0, 0}, v1[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < NCH; i++) {
-      uint32_t a = __ldg(q0 + e0[i]), b = __ldg(q1 + e1[i]);
+      const uint32_t a = q0[e0[i]], b = q1[e1[i]];
       c0[i] = a & 255; c1[i] = b & 255;
-      int v0 = a >> 8, v1 = b >> 8;
-#pragma unroll
-      for (int j = 0; j < F; j++) pal[j][i] = interp64(v0, v1, wgt<IB>(j));
+      v0[ch[i]] = a >> 8; v1[ch[i]] = b >> 8;
     }
-    uint32_t sse = 0, il = 0, ih = 0;
+    uint32_t pal[F];
+    int pk[F];
 #pragma unroll
+    for (int j = 0; j < F; j++) {
+      const int w = wgt<IB>(j);
+      pal[j] = pack_rgb(interp64(v0[0], v1[0], w), interp64(v0[1], v1[1], w), interp64(v0[2], v1[2], w)) & CM;
+      pk[j] = 16 * (int)__dp4a(pal[j], pal[j], 0u) + j;
+    }
+    int sse = 0;
+    uint32_t il = 0, ih = 0;
+#pragma unroll 2
     for (int t = 0; t < 16; t++) {
       if ((int)((part >> (2 * t)) & 3) != s) continue;
-      int v[NCH];
-#pragma unroll
-      for (int i = 0; i < NCH; i++) v[i] = chan(tx[t], ch[i]);
-      int best = 0x7FFFFFFF, bj = 0;
-#pragma unroll
-      for (int j = 0; j < F; j++) {
-        int e = 0;
-#pragma unroll
-        for (int i = 0; i < NCH; i++) { int d = v[i] - pal[j][i]; e += d * d; }
-        if (e < best) { best = e; bj = j; }
-      }
-      sse += best;
-      if (OUT) { if (t < 8) il |= (uint32_t)bj << (4 * t); else ih |= (uint32_t)bj << (4 * (t - 8)); }
+      const uint32_t v = tex[t * STAGE_STRIDE] & CM;
+      const int key = best_key<F>(v, pal, pk);
+      sse += (int)__dp4a(v, v, 0u) + (key >> 4);
+      if (OUT) { if (t < 8) il |= (uint32_t)(key & 15) << (4 * t); else ih |= (uint32_t)(key & 15) << (4 * (t - 8)); }
     }
-    if (sse < best_sse) {
-      best_sse = sse;
+    if ((uint32_t)sse < best_sse) {
+      best_sse = (uint32_t)sse;
       if (OUT) {
         out->idx_lo = il; out->idx_hi = ih; out->p[0] = p0; out->p[1] = p1;
 #pragma unroll
@@ -230,32 +229,32 @@ __device__ __forceinline__ uint32_t fit_subset(const uint32_t (&tx)[16], uint32_
 
 // ---- candidate scoring (search phase) ----------------------------------------------
 template <int NS, int IB, int PT, int BITS>
-__device__ __forceinline__ uint32_t score_part(const uint32_t (&tx)[16], uint32_t part) {
-  uint32_t s = fit_subset<IB, 7, PT, BITS, false>(tx, part, 0, nullptr);
-  if (NS > 1) s += fit_subset<IB, 7, PT, BITS, false>(tx, part, 1, nullptr);
-  if (NS > 2) s += fit_subset<IB, 7, PT, BITS, false>(tx, part, 2, nullptr);
+__device__ __forceinline__ uint32_t score_part(const uint32_t* tex, uint32_t part, const uint16_t* sq) {
+  uint32_t s = fit_subset<IB, 7, PT, BITS, false>(tex, part, 0, nullptr, sq);
+  if (NS > 1) s += fit_subset<IB, 7, PT, BITS, false>(tex, part, 1, nullptr, sq);
+  if (NS > 2) s += fit_subset<IB, 7, PT, BITS, false>(tex, part, 2, nullptr, sq);
   return s;
 }
 
 // modes 4 / 5: colour over the channels other than rot-1, scalar channel rot-1 in the alpha slot
 template <int MODE, int ROT, int ISB>
-__device__ __forceinline__ uint32_t score_rot(const uint32_t (&tx)[16], FitOut* oc, FitOut* oa) {
+__device__ __forceinline__ uint32_t score_rot(const uint32_t* tex, FitOut* oc, FitOut* oa, const uint16_t* sq) {
   constexpr int CB = MODE == 4 ? 5 : 7, AB = MODE == 4 ? 6 : 8;
   constexpr int CIB = MODE == 4 ? (ISB ? 3 : 2) : 2, AIB = MODE == 4 ? (ISB ? 2 : 3) : 2;
   constexpr int CM = ROT == 0 ? 7 : (7 & ~(1 << (ROT - 1)));
   const bool out = oc != nullptr;
   uint32_t s;
-  if (out) s = fit_subset<CIB, CM, PT_NONE, CB, true>(tx, 0u, 0, oc);
-  else s = fit_subset<CIB, CM, PT_NONE, CB, false>(tx, 0u, 0, nullptr);
+  if (out) s = fit_subset<CIB, CM, PT_NONE, CB, true>(tex, 0u, 0, oc, sq);
+  else s = fit_subset<CIB, CM, PT_NONE, CB, false>(tex, 0u, 0, nullptr, sq);
   if constexpr (ROT != 0) {
     constexpr int AM = 1 << (ROT > 0 ? ROT - 1 : 0);
-    if (out) s += fit_subset<AIB, AM, PT_NONE, AB, true>(tx, 0u, 0, oa);
-    else s += fit_subset<AIB, AM, PT_NONE, AB, false>(tx, 0u, 0, nullptr);
+    if (out) s += fit_subset<AIB, AM, PT_NONE, AB, true>(tex, 0u, 0, oa, sq);
+    else s += fit_subset<AIB, AM, PT_NONE, AB, false>(tex, 0u, 0, nullptr, sq);
   }
   return s;
 }
 
-__device__ __noinline__ int search_best(const uint32_t (&tx)[16], uint32_t* best_sse) {
+__device__ __noinline__ int search_best(const uint32_t* tex, uint32_t* best_sse, const uint16_t* sq) {
   uint32_t best = 0xFFFFFFFFu;
   int be = 0, e = 0;
 #define CAND(expr)                 \
@@ -264,24 +263,24 @@ __device__ __noinline__ int search_best(const uint32_t (&tx)[16], uint32_t* best
     if (s_ < best) { best = s_; be = e; } \
     e++;                           \
   } while (0)
-  for (int p = 0; p < 16; p++) CAND((score_part<3, 3, PT_UNIQUE, 4>(tx, c_part3[p])));
-  for (int p = 0; p < 64; p++) CAND((score_part<2, 3, PT_SHARED, 6>(tx, c_part2[p])));
-  for (int p = 0; p < 64; p++) CAND((score_part<3, 2, PT_NONE, 5>(tx, c_part3[p])));
-  for (int p = 0; p < 64; p++) CAND((score_part<2, 2, PT_UNIQUE, 7>(tx, c_part2[p])));
-  CAND((score_rot<4, 0, 0>(tx, nullptr, nullptr)));
-  CAND((score_rot<4, 0, 1>(tx, nullptr, nullptr)));
-  CAND((score_rot<4, 1, 0>(tx, nullptr, nullptr)));
-  CAND((score_rot<4, 1, 1>(tx, nullptr, nullptr)));
-  CAND((score_rot<4, 2, 0>(tx, nullptr, nullptr)));
-  CAND((score_rot<4, 2, 1>(tx, nullptr, nullptr)));
-  CAND((score_rot<4, 3, 0>(tx, nullptr, nullptr)));
-  CAND((score_rot<4, 3, 1>(tx, nullptr, nullptr)));
-  CAND((score_rot<5, 0, 0>(tx, nullptr, nullptr)));
-  CAND((score_rot<5, 1, 0>(tx, nullptr, nullptr)));
-  CAND((score_rot<5, 2, 0>(tx, nullptr, nullptr)));
-  CAND((score_rot<5, 3, 0>(tx, nullptr, nullptr)));
-  CAND((score_part<1, 4, PT_UNIQUE, 7>(tx, 0u)));
-  for (int p = 0; p < 64; p++) CAND((score_part<2, 2, PT_UNIQUE, 5>(tx, c_part2[p])));
+  for (int p = 0; p < 16; p++) CAND((score_part<3, 3, PT_UNIQUE, 4>(tex, c_part3[p], sq)));
+  for (int p = 0; p < 64; p++) CAND((score_part<2, 3, PT_SHARED, 6>(tex, c_part2[p], sq)));
+  for (int p = 0; p < 64; p++) CAND((score_part<3, 2, PT_NONE, 5>(tex, c_part3[p], sq)));
+  for (int p = 0; p < 64; p++) CAND((score_part<2, 2, PT_UNIQUE, 7>(tex, c_part2[p], sq)));
+  CAND((score_rot<4, 0, 0>(tex, nullptr, nullptr, sq)));
+  CAND((score_rot<4, 0, 1>(tex, nullptr, nullptr, sq)));
+  CAND((score_rot<4, 1, 0>(tex, nullptr, nullptr, sq)));
+  CAND((score_rot<4, 1, 1>(tex, nullptr, nullptr, sq)));
+  CAND((score_rot<4, 2, 0>(tex, nullptr, nullptr, sq)));
+  CAND((score_rot<4, 2, 1>(tex, nullptr, nullptr, sq)));
+  CAND((score_rot<4, 3, 0>(tex, nullptr, nullptr, sq)));
+  CAND((score_rot<4, 3, 1>(tex, nullptr, nullptr, sq)));
+  CAND((score_rot<5, 0, 0>(tex, nullptr, nullptr, sq)));
+  CAND((score_rot<5, 1, 0>(tex, nullptr, nullptr, sq)));
+  CAND((score_rot<5, 2, 0>(tex, nullptr, nullptr, sq)));
+  CAND((score_rot<5, 3, 0>(tex, nullptr, nullptr, sq)));
+  CAND((score_part<1, 4, PT_UNIQUE, 7>(tex, 0u, sq)));
+  for (int p = 0; p < 64; p++) CAND((score_part<2, 2, PT_UNIQUE, 5>(tex, c_part2[p], sq)));
 #undef CAND
   *best_sse = best;
   return be;
@@ -325,7 +324,7 @@ __device__ __forceinline__ int anchor_of(int ns, int p, int s) {
 }
 
 // Solves candidate e into per-subset fits, fixes anchors and packs the 128 bits.
-__device__ __noinline__ uint4 solve_pack(const uint32_t (&tx)[16], int e) {
+__device__ __noinline__ uint4 solve_pack(const uint32_t* tx, int e, const uint16_t* sq) {
   int mode, part = 0, rot = 0, isb = 0;
   if (e < 16) { mode = 0; part = e; }
   else if (e < 208) { mode = 1 + (e - 16) / 64; part = (e - 16) % 64; }
@@ -339,30 +338,30 @@ __device__ __noinline__ uint4 solve_pack(const uint32_t (&tx)[16], int e) {
   int acode[3][2];
   for (int s = 0; s < 3; s++) acode[s][0] = acode[s][1] = (1 << M.ab) - 1;
   switch (mode) {
-    case 0: for (int s = 0; s < 3; s++) fit_subset<3, 7, PT_UNIQUE, 4, true>(tx, pm, s, &f[s]); break;
-    case 1: for (int s = 0; s < 2; s++) fit_subset<3, 7, PT_SHARED, 6, true>(tx, pm, s, &f[s]); break;
-    case 2: for (int s = 0; s < 3; s++) fit_subset<2, 7, PT_NONE, 5, true>(tx, pm, s, &f[s]); break;
-    case 3: for (int s = 0; s < 2; s++) fit_subset<2, 7, PT_UNIQUE, 7, true>(tx, pm, s, &f[s]); break;
-    case 6: fit_subset<4, 7, PT_UNIQUE, 7, true>(tx, 0u, 0, &f[0]); break;
-    case 7: for (int s = 0; s < 2; s++) fit_subset<2, 7, PT_UNIQUE, 5, true>(tx, pm, s, &f[s]); break;
+    case 0: for (int s = 0; s < 3; s++) fit_subset<3, 7, PT_UNIQUE, 4, true>(tx, pm, s, &f[s], sq); break;
+    case 1: for (int s = 0; s < 2; s++) fit_subset<3, 7, PT_SHARED, 6, true>(tx, pm, s, &f[s], sq); break;
+    case 2: for (int s = 0; s < 3; s++) fit_subset<2, 7, PT_NONE, 5, true>(tx, pm, s, &f[s], sq); break;
+    case 3: for (int s = 0; s < 2; s++) fit_subset<2, 7, PT_UNIQUE, 7, true>(tx, pm, s, &f[s], sq); break;
+    case 6: fit_subset<4, 7, PT_UNIQUE, 7, true>(tx, 0u, 0, &f[0], sq); break;
+    case 7: for (int s = 0; s < 2; s++) fit_subset<2, 7, PT_UNIQUE, 5, true>(tx, pm, s, &f[s], sq); break;
     case 4:
       switch (rot * 2 + isb) {
-        case 0: score_rot<4, 0, 0>(tx, &f[0], &fa); break;
-        case 1: score_rot<4, 0, 1>(tx, &f[0], &fa); break;
-        case 2: score_rot<4, 1, 0>(tx, &f[0], &fa); break;
-        case 3: score_rot<4, 1, 1>(tx, &f[0], &fa); break;
-        case 4: score_rot<4, 2, 0>(tx, &f[0], &fa); break;
-        case 5: score_rot<4, 2, 1>(tx, &f[0], &fa); break;
-        case 6: score_rot<4, 3, 0>(tx, &f[0], &fa); break;
-        default: score_rot<4, 3, 1>(tx, &f[0], &fa); break;
+        case 0: score_rot<4, 0, 0>(tx, &f[0], &fa, sq); break;
+        case 1: score_rot<4, 0, 1>(tx, &f[0], &fa, sq); break;
+        case 2: score_rot<4, 1, 0>(tx, &f[0], &fa, sq); break;
+        case 3: score_rot<4, 1, 1>(tx, &f[0], &fa, sq); break;
+        case 4: score_rot<4, 2, 0>(tx, &f[0], &fa, sq); break;
+        case 5: score_rot<4, 2, 1>(tx, &f[0], &fa, sq); break;
+        case 6: score_rot<4, 3, 0>(tx, &f[0], &fa, sq); break;
+        default: score_rot<4, 3, 1>(tx, &f[0], &fa, sq); break;
       }
       break;
     default:
       switch (rot) {
-        case 0: score_rot<5, 0, 0>(tx, &f[0], &fa); break;
-        case 1: score_rot<5, 1, 0>(tx, &f[0], &fa); break;
-        case 2: score_rot<5, 2, 0>(tx, &f[0], &fa); break;
-        default: score_rot<5, 3, 0>(tx, &f[0], &fa); break;
+        case 0: score_rot<5, 0, 0>(tx, &f[0], &fa, sq); break;
+        case 1: score_rot<5, 1, 0>(tx, &f[0], &fa, sq); break;
+        case 2: score_rot<5, 2, 0>(tx, &f[0], &fa, sq); break;
+        default: score_rot<5, 3, 0>(tx, &f[0], &fa, sq); break;
       }
       break;
   }
@@ -435,41 +434,40 @@ __device__ __noinline__ uint4 solve_pack(const uint32_t (&tx)[16], int e) {
 }
 
 // One kernel for both sources: staged layout-D groups (sh / perm / scales) or raw
-// texels [nblk][16][3] (texin != nullptr), so the search is compiled once.
-__global__ void __launch_bounds__(STAGE_THREADS) k_bc7(const float* __restrict__ sh, const int32_t* __restrict__ perm,
+// texels [nblk][16][3] (texin != nullptr), so the search is compiled once. Each thread's
+// texels stay in the shared tile (column threadIdx.x) for the whole search.
+__global__ void __launch_bounds__(STAGE_THREADS, 4) k_bc7(const float* __restrict__ sh, const int32_t* __restrict__ perm,
                                                        const float* __restrict__ scales, int64_t n_groups,
                                                        const uint8_t* __restrict__ texin, int64_t nblk,
                                                        uint4* __restrict__ blocks, uint32_t* __restrict__ sse7,
                                                        uint64_t* __restrict__ sse64) {
   __shared__ uint32_t tex[16][STAGE_STRIDE];
   __shared__ float s_scale[16];
-  if (!texin) {
-    if (threadIdx.x < 16) s_scale[threadIdx.x] = scales[threadIdx.x];
-    __syncthreads();
-  }
+  __shared__ uint16_t sq[12 * 256];
+  for (int i = threadIdx.x; i < 12 * 256; i += blockDim.x) sq[i] = (&g_qtab[0][0])[i];
+  if (!texin && threadIdx.x < 16) s_scale[threadIdx.x] = scales[threadIdx.x];
+  __syncthreads();
   const int64_t total = texin ? nblk : n_groups * 16;
   for (int64_t b0 = (int64_t)blockIdx.x * STAGE_THREADS; b0 < total; b0 += (int64_t)gridDim.x * STAGE_THREADS) {
     const int64_t blk = b0 + threadIdx.x;
-    uint32_t tx[16];
     if (!texin) {
       stage_groups(sh, perm, s_scale, b0 / 16, n_groups, tex);
-      __syncthreads();
-#pragma unroll
-      for (int t = 0; t < 16; t++) tx[t] = tex[t][threadIdx.x];
-      __syncthreads();
     } else if (blk < total) {
       const uint8_t* p = texin + blk * 48;
 #pragma unroll
       for (int t = 0; t < 16; t++)
-        tx[t] = (uint32_t)p[3 * t] | ((uint32_t)p[3 * t + 1] << 8) | ((uint32_t)p[3 * t + 2] << 16);
+        tex[t][threadIdx.x] = (uint32_t)p[3 * t] | ((uint32_t)p[3 * t + 1] << 8) | ((uint32_t)p[3 * t + 2] << 16);
     }
+    __syncthreads();
     if (blk < total) {
       uint32_t best;
-      int e = search_best(tx, &best);
-      blocks[blk] = solve_pack(tx, e);
+      const uint32_t* my = &tex[0][threadIdx.x];
+      const int e = search_best(my, &best, sq);
+      blocks[blk] = solve_pack(my, e, sq);
       if (sse7) sse7[blk] = best;
       if (sse64) sse64[blk] = best;
     }
+    __syncthreads();
   }
 }
 
