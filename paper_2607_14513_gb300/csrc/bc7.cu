@@ -91,16 +91,20 @@ __device__ __forceinline__ uint32_t pack_rgb(int r, int g, int b) { return (uint
 
 template <int F>
 __device__ __forceinline__ int best_key(uint32_t v, const uint32_t (&pal)[F], const int (&pk)[F]) {
-  int key = 0x7FFFFFFF;
+  int k[F];
 #pragma unroll
-  for (int j = 0; j < F; j++) key = min(key, pk[j] - 32 * (int)__dp4a(v, pal[j], 0u));
-  return key;
+  for (int j = 0; j < F; j++) k[j] = pk[j] - 32 * (int)__dp4a(v, pal[j], 0u);
+#pragma unroll
+  for (int w = F / 2; w >= 1; w /= 2)
+#pragma unroll
+    for (int j = 0; j < w; j++) k[j] = min(k[j], k[j + w]);
+  return k[0];
 }
 
-// Fits subset s of partition `part` (2 bits per texel) over the channels in CHMASK.
-template <int IB, int CHMASK, int PT, int BITS, bool OUT>
-__device__ __forceinline__ uint32_t fit_subset(const uint32_t* __restrict__ tex, uint32_t part, int s, FitOut* out,
-                                               const uint16_t* __restrict__ sq) {
+// Stage 1 of a subset fit: bounding-box diagonal oriented by covariance signs, indices
+// against the unquantised palette, one least-squares refinement. Returns the member count.
+template <int IB, int CHMASK>
+__device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t part, int s, int (&e0)[3], int (&e1)[3]) {
   constexpr int F = 1 << IB;
   constexpr int NCH = ((CHMASK >> 0) & 1) + ((CHMASK >> 1) & 1) + ((CHMASK >> 2) & 1);
   constexpr uint32_t CM = ((CHMASK & 1) ? 0xFFu : 0u) | ((CHMASK & 2) ? 0xFF00u : 0u) | ((CHMASK & 4) ? 0xFF0000u : 0u);
@@ -128,14 +132,10 @@ __device__ __forceinline__ uint32_t fit_subset(const uint32_t* __restrict__ tex,
     if (NCH >= 2) s2[0] += c[0] * c[NCH >= 2 ? 1 : 0];
     if (NCH >= 3) { s2[1] += c[0] * c[NCH >= 3 ? 2 : 0]; s2[2] += c[NCH >= 2 ? 1 : 0] * c[NCH >= 3 ? 2 : 0]; }
   }
-  if (OUT) { out->idx_lo = 0; out->idx_hi = 0; out->p[0] = out->p[1] = 0;
-#pragma unroll
-    for (int i = 0; i < 3; i++) out->code[0][i] = out->code[1][i] = 0; }
   if (n == 0) return 0;
   int ref = 0;
 #pragma unroll
   for (int i = 1; i < NCH; i++) if (hi[i] - lo[i] > hi[ref] - lo[ref]) ref = i;
-  int e0[NCH], e1[NCH];
 #pragma unroll
   for (int i = 0; i < NCH; i++) {
     bool flip = false;
@@ -147,7 +147,6 @@ __device__ __forceinline__ uint32_t fit_subset(const uint32_t* __restrict__ tex,
     e0[i] = flip ? lo[i] : hi[i];
     e1[i] = flip ? hi[i] : lo[i];
   }
-  // initial indices against the unquantised endpoints, accumulated straight into the LS sums
   int saa = 0, sbb = 0, sab = 0, sav[NCH], sbv[NCH];
   {
     uint32_t pal[F];
@@ -180,6 +179,24 @@ __device__ __forceinline__ uint32_t fit_subset(const uint32_t* __restrict__ tex,
       e0[i] = round_div_clamp255(64LL * ((long long)sbb * sav[i] - (long long)sab * sbv[i]), det);
       e1[i] = round_div_clamp255(64LL * ((long long)saa * sbv[i] - (long long)sab * sav[i]), det);
     }
+  }
+  return n;
+}
+
+// Stage 2: every p-bit combination quantised to the nearest codes and re-indexed; the best
+// combination (first on ties) scores the subset.
+template <int IB, int CHMASK, int PT, int BITS, bool OUT>
+__device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex, uint32_t part, int s,
+                                               const int (&e0)[3], const int (&e1)[3], FitOut* out,
+                                               const uint16_t* __restrict__ sq) {
+  constexpr int F = 1 << IB;
+  constexpr int NCH = ((CHMASK >> 0) & 1) + ((CHMASK >> 1) & 1) + ((CHMASK >> 2) & 1);
+  constexpr uint32_t CM = ((CHMASK & 1) ? 0xFFu : 0u) | ((CHMASK & 2) ? 0xFF00u : 0u) | ((CHMASK & 4) ? 0xFF0000u : 0u);
+  int ch[3] = {0, 0, 0};
+  {
+    int k = 0;
+#pragma unroll
+    for (int c = 0; c < 3; c++) if ((CHMASK >> c) & 1) ch[k++] = c;
   }
   constexpr int NCOMBO = PT == PT_NONE ? 1 : (PT == PT_UNIQUE ? 4 : 2);
   constexpr int HP = PT == PT_NONE ? 0 : 1;
@@ -227,6 +244,18 @@ __device__ __forceinline__ uint32_t fit_subset(const uint32_t* __restrict__ tex,
   return best_sse;
 }
 
+// Full subset fit = prefit + quant_eval.
+template <int IB, int CHMASK, int PT, int BITS, bool OUT>
+__device__ __forceinline__ uint32_t fit_subset(const uint32_t* __restrict__ tex, uint32_t part, int s, FitOut* out,
+                                               const uint16_t* __restrict__ sq) {
+  if (OUT) { out->idx_lo = 0; out->idx_hi = 0; out->p[0] = out->p[1] = 0;
+#pragma unroll
+    for (int i = 0; i < 3; i++) out->code[0][i] = out->code[1][i] = 0; }
+  int e0[3] = {0, 0, 0}, e1[3] = {0, 0, 0};
+  if (prefit<IB, CHMASK>(tex, part, s, e0, e1) == 0) return 0;
+  return quant_eval<IB, CHMASK, PT, BITS, OUT>(tex, part, s, e0, e1, out, sq);
+}
+
 // ---- candidate scoring (search phase) ----------------------------------------------
 template <int NS, int IB, int PT, int BITS>
 __device__ __forceinline__ uint32_t score_part(const uint32_t* tex, uint32_t part, const uint16_t* sq) {
@@ -256,31 +285,44 @@ __device__ __forceinline__ uint32_t score_rot(const uint32_t* tex, FitOut* oc, F
 
 __device__ __noinline__ int search_best(const uint32_t* tex, uint32_t* best_sse, const uint16_t* sq) {
   uint32_t best = 0xFFFFFFFFu;
-  int be = 0, e = 0;
-#define CAND(expr)                 \
-  do {                             \
-    uint32_t s_ = (expr);          \
-    if (s_ < best) { best = s_; be = e; } \
-    e++;                           \
+  int be = 0;
+  // the block takes the least error, ties to the lowest enumeration index
+#define CAND(expr, idx)                                      \
+  do {                                                       \
+    const uint32_t s_ = (expr);                              \
+    const int e_ = (idx);                                    \
+    if (s_ < best || (s_ == best && e_ < be)) { best = s_; be = e_; } \
   } while (0)
-  for (int p = 0; p < 16; p++) CAND((score_part<3, 3, PT_UNIQUE, 4>(tex, c_part3[p], sq)));
-  for (int p = 0; p < 64; p++) CAND((score_part<2, 3, PT_SHARED, 6>(tex, c_part2[p], sq)));
-  for (int p = 0; p < 64; p++) CAND((score_part<3, 2, PT_NONE, 5>(tex, c_part3[p], sq)));
-  for (int p = 0; p < 64; p++) CAND((score_part<2, 2, PT_UNIQUE, 7>(tex, c_part2[p], sq)));
-  CAND((score_rot<4, 0, 0>(tex, nullptr, nullptr, sq)));
-  CAND((score_rot<4, 0, 1>(tex, nullptr, nullptr, sq)));
-  CAND((score_rot<4, 1, 0>(tex, nullptr, nullptr, sq)));
-  CAND((score_rot<4, 1, 1>(tex, nullptr, nullptr, sq)));
-  CAND((score_rot<4, 2, 0>(tex, nullptr, nullptr, sq)));
-  CAND((score_rot<4, 2, 1>(tex, nullptr, nullptr, sq)));
-  CAND((score_rot<4, 3, 0>(tex, nullptr, nullptr, sq)));
-  CAND((score_rot<4, 3, 1>(tex, nullptr, nullptr, sq)));
-  CAND((score_rot<5, 0, 0>(tex, nullptr, nullptr, sq)));
-  CAND((score_rot<5, 1, 0>(tex, nullptr, nullptr, sq)));
-  CAND((score_rot<5, 2, 0>(tex, nullptr, nullptr, sq)));
-  CAND((score_rot<5, 3, 0>(tex, nullptr, nullptr, sq)));
-  CAND((score_part<1, 4, PT_UNIQUE, 7>(tex, 0u, sq)));
-  for (int p = 0; p < 64; p++) CAND((score_part<2, 2, PT_UNIQUE, 5>(tex, c_part2[p], sq)));
+  for (int p = 0; p < 16; p++) CAND((score_part<3, 3, PT_UNIQUE, 4>(tex, c_part3[p], sq)), p);
+  for (int p = 0; p < 64; p++) CAND((score_part<2, 3, PT_SHARED, 6>(tex, c_part2[p], sq)), 16 + p);
+  for (int p = 0; p < 64; p++) CAND((score_part<3, 2, PT_NONE, 5>(tex, c_part3[p], sq)), 80 + p);
+  // modes 3 and 7: same partitions and 2-bit weights, so one prefit per subset serves both
+  for (int p = 0; p < 64; p++) {
+    const uint32_t part = c_part2[p];
+    uint32_t s3 = 0, s7 = 0;
+#pragma unroll
+    for (int sub = 0; sub < 2; sub++) {
+      int e0[3] = {0, 0, 0}, e1[3] = {0, 0, 0};
+      if (prefit<2, 7>(tex, part, sub, e0, e1) == 0) continue;
+      s3 += quant_eval<2, 7, PT_UNIQUE, 7, false>(tex, part, sub, e0, e1, nullptr, sq);
+      s7 += quant_eval<2, 7, PT_UNIQUE, 5, false>(tex, part, sub, e0, e1, nullptr, sq);
+    }
+    CAND(s3, 144 + p);
+    CAND(s7, 221 + p);
+  }
+  CAND((score_rot<4, 0, 0>(tex, nullptr, nullptr, sq)), 208);
+  CAND((score_rot<4, 0, 1>(tex, nullptr, nullptr, sq)), 209);
+  CAND((score_rot<4, 1, 0>(tex, nullptr, nullptr, sq)), 210);
+  CAND((score_rot<4, 1, 1>(tex, nullptr, nullptr, sq)), 211);
+  CAND((score_rot<4, 2, 0>(tex, nullptr, nullptr, sq)), 212);
+  CAND((score_rot<4, 2, 1>(tex, nullptr, nullptr, sq)), 213);
+  CAND((score_rot<4, 3, 0>(tex, nullptr, nullptr, sq)), 214);
+  CAND((score_rot<4, 3, 1>(tex, nullptr, nullptr, sq)), 215);
+  CAND((score_rot<5, 0, 0>(tex, nullptr, nullptr, sq)), 216);
+  CAND((score_rot<5, 1, 0>(tex, nullptr, nullptr, sq)), 217);
+  CAND((score_rot<5, 2, 0>(tex, nullptr, nullptr, sq)), 218);
+  CAND((score_rot<5, 3, 0>(tex, nullptr, nullptr, sq)), 219);
+  CAND((score_part<1, 4, PT_UNIQUE, 7>(tex, 0u, sq)), 220);
 #undef CAND
   *best_sse = best;
   return be;
