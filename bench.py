@@ -160,8 +160,11 @@ def run_gsc(args, world, rank, local):
     rgb = torch.empty((3, n, N_CAMS, 3), dtype=torch.float32, device=dev)
     ok = torch.ones((), dtype=torch.bool, device=dev)
 
+    last_perm = [None]
+
     def step(pos_d, sh_d):
         perm, scales = gsc.gsc_plan_reorder(ctx, pos_d, sh_d, ws=ws, stream=stream)
+        last_perm[0] = perm
         rblk, rperm, rtab = gsc.gsc_encode(ctx, sh_d, perm, scales, gsc.FMT_RATE, RATE_TARGET_X4, ws=ws,
                                            out=rate_buf, perm_out=rate_perm, stream=stream, bc1_all=bc1, bc7_all=bc7)
         t1, t7 = gsc.forced_table(rtab, gsc.FMT_BC1), gsc.forced_table(rtab, gsc.FMT_BC7)
@@ -193,6 +196,7 @@ def run_gsc(args, world, rank, local):
     for _ in range(args.steps):
         rtab, rblk, rperm = step(pos, sh)
     e1.record(stream)
+    perm_last = last_perm[0]
     stream.synchronize()
     launches = gsc.launch_count() - launches0
     barrier(world)
@@ -235,6 +239,10 @@ def run_gsc(args, world, rank, local):
     stages["decode_eval_GB_s"] = round(ev_gbs, 1)
     stages["rate_bits_per_texel"] = round(rtab.used_bits / (16.0 * n), 4)
 
+    # the same evaluation on resident texture scenes (blocks decoded by the texture unit)
+    tex_stats = time_tex_eval(args, ctx, gsc, stream, dev, rtab, bc1, bc7, perm_last, pos, cams, n, ns)
+    stages.update(tex_stats["stages"])
+
     # end to end through the public API with host buffers
     e2e = run_e2e(args, ctx, gsc, stream, dev, sc, step, world)
 
@@ -247,7 +255,8 @@ def run_gsc(args, world, rank, local):
                                   % (n, cfg["clusters"], int(cfg["heavy_frac"] * 100), N_CAMS),
                       "n_gaussians": n, "parallelism": "weak, one scene per GPU" if world > 1 else "single GPU",
                       "l2": "inputs larger than L2 (SH 192 B/Gaussian)", "texture_path_bit_exact": match},
-           "roofline": roofline, "roofline_decode_eval": roofline_eval, "stages": stages,
+           "roofline": roofline, "roofline_decode_eval": roofline_eval,
+           "roofline_decode_eval_tex": tex_stats["roofline"], "stages": stages,
            "clocks": clk, "e2e": e2e, "gpu_launches": int(launches)}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
@@ -257,6 +266,42 @@ def run_gsc(args, world, rank, local):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def time_tex_eval(args, ctx, gsc, stream, dev, rtab, bc1, bc7, perm, pos, cams, n, ns):
+    """Fused evaluation of the all-BC7 and all-BC1 codings kept resident as texture objects."""
+    import torch
+    out = torch.empty((n, N_CAMS, 3), dtype=torch.float32, device=dev)
+    res = {"stages": {}}
+    hbm, hbm_src = peaks()
+    for name, fmt, blk, bpg in [("bc7", gsc.FMT_BC7, bc7, 16), ("bc1", gsc.FMT_BC1, bc1, 8)]:
+        tab = gsc.forced_table(rtab, fmt)
+        scene = gsc.TexScene(ctx, tab, blk, perm=perm, pos=pos, stream=stream)
+        for _ in range(3):
+            gsc.gsc_decode_eval_sh_tex(ctx, scene, perm, cams=cams, out_order=gsc.OUT_GAUSS_MAJOR, out=out,
+                                       stream=stream)
+        stream.synchronize()
+        gsc.set_timing(ctx, True)
+        for _ in range(max(5, args.steps)):
+            gsc.gsc_decode_eval_sh_tex(ctx, scene, perm, cams=cams, out_order=gsc.OUT_GAUSS_MAJOR, out=out,
+                                       stream=stream)
+        ms, cnt = gsc.kernel_time(ctx, "decode_eval_tex")
+        gsc.set_timing(ctx, False)
+        scene.close()
+        ms /= max(1, cnt)
+        by = (bpg + 4 + 12 + N_CAMS * 12) * n
+        gbs = by / (ms * 1e-3) / 1e9
+        res["stages"]["decode_eval_tex_%s_ms" % name] = round(ms, 4)
+        res["stages"]["decode_eval_tex_%s_GB_s" % name] = round(gbs, 1)
+        res["stages"]["decode_eval_tex_%s_MGauss_s" % name] = round(n / (ms * 1e-3) / 1e6, 1)
+        if name == "bc7":
+            res["roofline"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                               "frac": round(gbs / hbm, 4), "traffic": None, "peak_source": hbm_src,
+                               "kernel": "k_eval_tex (texture-unit decode + SH eval, all-BC7, %d cameras, "
+                                         "Gaussian-major output)" % N_CAMS,
+                               "algorithmic": "16 B block + 4 B perm + 12 B position + %d x 12 B output per Gaussian"
+                                              % N_CAMS}
+    return res
 
 
 def run_e2e(args, ctx, gsc, stream, dev, sc, step, world):

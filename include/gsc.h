@@ -164,7 +164,8 @@ gsc_status gsc_decode(gsc_ctx* ctx, const gsc_stream_table* table, const uint8_t
  * (k = l*l + l + m, Condon-Shortley phase), no offset and no clamp. Directions: either
  * d_dirs [V][3] unit vectors shared by all Gaussians, or d_cams [V][3] camera centres
  * with d = (cam - p) / |cam - p| from d_pos [n][3] ((0, 0, 1) if the camera sits on p).
- * Exactly one of d_dirs, d_cams is non-NULL. 1 <= V <= 64. out_order: gsc_out_order. */
+ * Exactly one of d_dirs, d_cams is non-NULL. 1 <= V <= 64. out_order: gsc_out_order.
+ * d_rgb must be 16-byte aligned. */
 gsc_status gsc_decode_eval_sh(gsc_ctx* ctx, const gsc_stream_table* table, const uint8_t* d_blocks,
                               const int32_t* d_perm, const float* d_dirs, const float* d_pos, const float* d_cams,
                               int32_t V, int32_t out_order, float* d_rgb, void* stream);
@@ -177,6 +178,26 @@ gsc_status gsc_decode_eval_sh(gsc_ctx* ctx, const gsc_stream_table* table, const
  * asynchronous. Calls on one context must not overlap on different streams. */
 gsc_status gsc_decode_tex(gsc_ctx* ctx, const gsc_stream_table* table, const uint8_t* d_blocks,
                           const int32_t* d_perm, uint8_t* d_texels, void* stream);
+
+/* Sec. I (blocks decoded by the GPU's fixed-function texture unit) and Sec. II. A coded
+ * scene kept resident as BC1/BC7 texture objects: gsc_tex_scene_create gathers every
+ * stream's blocks into 2-D CUDA arrays (16384 blocks per row) and, when d_perm and d_pos
+ * [n][3] are given, keeps the positions in slot order (Sec. III-C: positions move with
+ * the Gaussians, so no side data is needed). It allocates the arrays, the positions and a
+ * temporary staging buffer, and synchronises `stream`; the scene owns its memory until
+ * gsc_tex_scene_destroy. The inputs may be freed or overwritten after create returns. */
+typedef struct gsc_tex_scene gsc_tex_scene;
+gsc_status gsc_tex_scene_create(gsc_ctx* ctx, const gsc_stream_table* table, const uint8_t* d_blocks,
+                                const int32_t* d_perm, const float* d_pos, gsc_tex_scene** out, void* stream);
+gsc_status gsc_tex_scene_destroy(gsc_tex_scene* scene);
+/* gsc_decode_eval_sh with the texels fetched through the texture unit from a resident
+ * scene (same arguments otherwise; d_perm is the scene's slot order; d_pos may be NULL
+ * when the scene holds positions). The dequantisation
+ * recovers q - 128 exactly from the UNORM8 sample and the SH evaluation is the same code,
+ * so the colours equal gsc_decode_eval_sh's bit for bit. */
+gsc_status gsc_decode_eval_sh_tex(gsc_ctx* ctx, const gsc_tex_scene* scene, const int32_t* d_perm,
+                                  const float* d_dirs, const float* d_pos, const float* d_cams, int32_t V,
+                                  int32_t out_order, float* d_rgb, void* stream);
 
 /* Block-level codecs (Sec. III-B): nblk independent 4x4 blocks.
  * d_tex [nblk][16][3] uint8 -> d_out [nblk][8 or 16] bytes; d_sse [nblk] (optional)
@@ -200,7 +221,8 @@ gsc_status gsc_probe_int_peak(gsc_ctx* ctx, double* ops_per_s, void* stream);
 /* Kernel timing: when enabled, each call records CUDA events on its own stream around its
  * main kernels. gsc_kernel_time waits for the recorded events and returns the summed
  * milliseconds and launch count of one kernel ("plan", "bc1_encode", "bc7_encode",
- * "rate_select", "decode", "decode_eval", "decode_tex") since timing was last enabled. */
+ * "rate_select", "decode", "decode_eval", "decode_tex", "decode_eval_tex") since timing
+ * was last enabled. */
 gsc_status gsc_ctx_set_timing(gsc_ctx* ctx, int enable);
 gsc_status gsc_kernel_time(gsc_ctx* ctx, const char* name, double* ms, int64_t* launches);
 

@@ -14,7 +14,7 @@ void gsc_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 extern "C" uint64_t gsc_launch_count(void) { return g_launches.load(); }
 
 static const char* kTimerNames[T_COUNT] = {"plan", "bc1_encode", "bc7_encode", "rate_select", "decode",
-                                           "decode_eval", "decode_tex"};
+                                           "decode_eval", "decode_tex", "decode_eval_tex"};
 
 int gsc_timer_begin(gsc_ctx* c, int id, cudaStream_t st) {
   if (!c || !c->timing) return -1;
@@ -356,7 +356,7 @@ extern "C" gsc_status gsc_decode_eval_sh(gsc_ctx* c, const gsc_stream_table* tab
   if ((d_dirs == nullptr) == (d_cams == nullptr)) return GSC_ERR_INVALID_ARG;
   if (d_cams && !d_pos && T.n > 0) return GSC_ERR_INVALID_ARG;
   if (T.n_groups > 0 && (!d_blocks || !d_perm || !d_rgb)) return GSC_ERR_INVALID_ARG;
-  if (!aligned(d_blocks, 8) || !aligned(d_rgb, 4)) return GSC_ERR_INVALID_ARG;
+  if (!aligned(d_blocks, 8) || !aligned(d_rgb, 16)) return GSC_ERR_INVALID_ARG;
   GSC_CUDA(cudaSetDevice(c->device));
   GscTimed tm(c, T_EVAL, (cudaStream_t)stream);
   GSC_CUDA(launch_decode_eval(T, d_blocks, d_perm, d_dirs, d_pos, d_cams, V, out_order, d_rgb, c->sm_count,

@@ -410,6 +410,83 @@ __device__ __forceinline__ void sh_poly2(float2 x, float2 y, float2 z, float2 (&
 __constant__ float c_shc[16] = {SH_C0, -SH_C1, SH_C1, -SH_C1, SH_C2A, -SH_C2A, SH_C2B, -SH_C2A, SH_C2C,
                                 -SH_C3A, SH_C3B, -SH_C3C, SH_C3D, -SH_C3C, SH_C3E, -SH_C3A};
 
+// SH evaluation of one Gaussian for V views and the store in the requested order. x holds
+// the dequantised coefficients with the SH constants folded in; both decoders share this
+// code, so their colours agree bit for bit when their texels do.
+template <bool CAMS>
+__device__ __forceinline__ void eval_store(const float (&xr)[16], const float (&xg)[16], const float (&xb)[16],
+                                           int64_t o, int64_t s, float3 p, const float (*s_view)[64], int V,
+                                           int out_order, int64_t n, int64_t ns, float* __restrict__ rgb) {
+  const float2 p0 = make_float2(p.x, p.x), p1 = make_float2(p.y, p.y), p2 = make_float2(p.z, p.z);
+  // views in chunks of 8: accumulate in registers, then store (16-byte vectors for whole
+  // Gaussian-major rows when V is a multiple of 4)
+  for (int v0 = 0; v0 < V; v0 += 8) {
+    float res[24];
+#pragma unroll
+    for (int pr = 0; pr < 4; pr++) {
+      const int v = v0 + 2 * pr;
+      if (v >= V) break;
+      const int v1 = v + 1 < V ? v + 1 : v;
+      float2 dx = make_float2(s_view[0][v], s_view[0][v1]);
+      float2 dy = make_float2(s_view[1][v], s_view[1][v1]);
+      float2 dz = make_float2(s_view[2][v], s_view[2][v1]);
+      if (CAMS) {
+        dx = __fadd2_rn(dx, make_float2(-p0.x, -p0.y));
+        dy = __fadd2_rn(dy, make_float2(-p1.x, -p1.y));
+        dz = __fadd2_rn(dz, make_float2(-p2.x, -p2.y));
+      }
+      const float2 n2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+      float2 r;
+      r.x = n2.x > 0.f ? rsqrtf(n2.x) : 0.f;
+      r.y = n2.y > 0.f ? rsqrtf(n2.y) : 0.f;
+      dx = __fmul2_rn(dx, r); dy = __fmul2_rn(dy, r); dz = __fmul2_rn(dz, r);
+      if (n2.x <= 0.f) { dx.x = 0.f; dy.x = 0.f; dz.x = 1.f; }
+      if (n2.y <= 0.f) { dx.y = 0.f; dy.y = 0.f; dz.y = 1.f; }
+      float2 P[16];
+      sh_poly2(dx, dy, dz, P);
+      float2 ar = make_float2(xr[0], xr[0]), ag = make_float2(xg[0], xg[0]), ab = make_float2(xb[0], xb[0]);
+#pragma unroll
+      for (int k = 1; k < 16; k++) {
+        ar = __ffma2_rn(make_float2(xr[k], xr[k]), P[k], ar);
+        ag = __ffma2_rn(make_float2(xg[k], xg[k]), P[k], ag);
+        ab = __ffma2_rn(make_float2(xb[k], xb[k]), P[k], ab);
+      }
+      res[6 * pr + 0] = ar.x; res[6 * pr + 1] = ag.x; res[6 * pr + 2] = ab.x;
+      res[6 * pr + 3] = ar.y; res[6 * pr + 4] = ag.y; res[6 * pr + 5] = ab.y;
+    }
+    const int nv = V - v0 < 8 ? V - v0 : 8;
+    if (out_order == GSC_OUT_GAUSS_MAJOR && (V & 3) == 0) {
+      float4* d = reinterpret_cast<float4*>(rgb + (o * V + v0) * 3);
+#pragma unroll
+      for (int q = 0; q < 6; q++)
+        if (4 * q < 3 * nv) d[q] = make_float4(res[4 * q], res[4 * q + 1], res[4 * q + 2], res[4 * q + 3]);
+    } else if (out_order == GSC_OUT_GAUSS_MAJOR) {
+      float* d = rgb + (o * V + v0) * 3;
+#pragma unroll
+      for (int q = 0; q < 24; q++)
+        if (q < 3 * nv) d[q] = res[q];
+    } else {
+      const int64_t idx = out_order == GSC_OUT_VIEW_MAJOR ? o : s;
+      const int64_t stride = out_order == GSC_OUT_VIEW_MAJOR ? n : ns;
+#pragma unroll
+      for (int q = 0; q < 8; q++)
+        if (q < nv) {
+          float* d = rgb + ((int64_t)(v0 + q) * stride + idx) * 3;
+          d[0] = res[3 * q]; d[1] = res[3 * q + 1]; d[2] = res[3 * q + 2];
+        }
+    }
+  }
+}
+
+__device__ __forceinline__ void load_views(float (*s_view)[64], float* s_deq, const float* dirs, const float* cams,
+                                           int V, const DevTable& T) {
+  for (int i = threadIdx.x; i < V; i += blockDim.x) {
+    const float* src = cams ? cams : dirs;
+    s_view[0][i] = src[3 * i]; s_view[1][i] = src[3 * i + 1]; s_view[2][i] = src[3 * i + 2];
+  }
+  if (threadIdx.x < 16) s_deq[threadIdx.x] = __fmul_rn(__fdiv_rn(T.scales[threadIdx.x], 255.0f), c_shc[threadIdx.x]);
+}
+
 template <int KIND, bool CAMS>
 __global__ void __launch_bounds__(256) k_eval2(DevTable T, const uint8_t* __restrict__ blocks,
                                                const int32_t* __restrict__ perm, const float* __restrict__ dirs,
@@ -420,11 +497,7 @@ __global__ void __launch_bounds__(256) k_eval2(DevTable T, const uint8_t* __rest
   __shared__ float s_view[3][64];
   __shared__ float s_deq[16];
   load_tables(&S);
-  for (int i = threadIdx.x; i < V; i += blockDim.x) {
-    const float* src = CAMS ? cams : dirs;
-    s_view[0][i] = src[3 * i]; s_view[1][i] = src[3 * i + 1]; s_view[2][i] = src[3 * i + 2];
-  }
-  if (threadIdx.x < 16) s_deq[threadIdx.x] = __fmul_rn(__fdiv_rn(T.scales[threadIdx.x], 255.0f), c_shc[threadIdx.x]);
+  load_views(s_view, s_deq, dirs, cams, V, T);
   __syncthreads();
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, gw = l >> 4, kt = l & 15;
   const int64_t npairs = ((int64_t)T.n_groups + 1) / 2;
@@ -443,7 +516,6 @@ __global__ void __launch_bounds__(256) k_eval2(DevTable T, const uint8_t* __rest
     const int64_t s = g * 16 + kt;
     const int32_t o = live ? __ldg(perm + s) : -1;
     if (o >= 0) {
-      // dequantised coefficients with the SH constants folded in
       float xr[16], xg[16], xb[16];
 #pragma unroll
       for (int k = 0; k < 16; k++) {
@@ -451,47 +523,9 @@ __global__ void __launch_bounds__(256) k_eval2(DevTable T, const uint8_t* __rest
         const float f = s_deq[k];
         xr[k] = byte_m128(px, 0) * f; xg[k] = byte_m128(px, 1) * f; xb[k] = byte_m128(px, 2) * f;
       }
-      float2 p0 = make_float2(0.f, 0.f), p1 = p0, p2 = p0;
-      if (CAMS) { const float px = __ldg(pos + 3 * (int64_t)o), py = __ldg(pos + 3 * (int64_t)o + 1), pz = __ldg(pos + 3 * (int64_t)o + 2);
-                  p0 = make_float2(px, px); p1 = make_float2(py, py); p2 = make_float2(pz, pz); }
-      for (int v = 0; v < V; v += 2) {
-        const int v1 = v + 1 < V ? v + 1 : v;
-        float2 dx = make_float2(s_view[0][v], s_view[0][v1]);
-        float2 dy = make_float2(s_view[1][v], s_view[1][v1]);
-        float2 dz = make_float2(s_view[2][v], s_view[2][v1]);
-        if (CAMS) {
-          dx = __fadd2_rn(dx, make_float2(-p0.x, -p0.y));
-          dy = __fadd2_rn(dy, make_float2(-p1.x, -p1.y));
-          dz = __fadd2_rn(dz, make_float2(-p2.x, -p2.y));
-        }
-        const float2 n2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-        float2 r;
-        r.x = n2.x > 0.f ? rsqrtf(n2.x) : 0.f;
-        r.y = n2.y > 0.f ? rsqrtf(n2.y) : 0.f;
-        dx = __fmul2_rn(dx, r); dy = __fmul2_rn(dy, r); dz = __fmul2_rn(dz, r);
-        if (n2.x <= 0.f) { dx.x = 0.f; dy.x = 0.f; dz.x = 1.f; }
-        if (n2.y <= 0.f) { dx.y = 0.f; dy.y = 0.f; dz.y = 1.f; }
-        float2 P[16];
-        sh_poly2(dx, dy, dz, P);
-        float2 ar = make_float2(xr[0], xr[0]), ag = make_float2(xg[0], xg[0]), ab = make_float2(xb[0], xb[0]);
-#pragma unroll
-        for (int k = 1; k < 16; k++) {
-          ar = __ffma2_rn(make_float2(xr[k], xr[k]), P[k], ar);
-          ag = __ffma2_rn(make_float2(xg[k], xg[k]), P[k], ag);
-          ab = __ffma2_rn(make_float2(xb[k], xb[k]), P[k], ab);
-        }
-        if (out_order == GSC_OUT_GAUSS_MAJOR) {
-          float* d = rgb + ((int64_t)o * V + v) * 3;
-          d[0] = ar.x; d[1] = ag.x; d[2] = ab.x;
-          if (v + 1 < V) { d[3] = ar.y; d[4] = ag.y; d[5] = ab.y; }
-        } else {
-          const int64_t idx = out_order == GSC_OUT_VIEW_MAJOR ? o : s;
-          const int64_t stride = out_order == GSC_OUT_VIEW_MAJOR ? n : ns;
-          float* d = rgb + ((int64_t)v * stride + idx) * 3;
-          d[0] = ar.x; d[1] = ag.x; d[2] = ab.x;
-          if (v + 1 < V) { d += stride * 3; d[0] = ar.y; d[1] = ag.y; d[2] = ab.y; }
-        }
-      }
+      float3 p = make_float3(0.f, 0.f, 0.f);
+      if (CAMS) p = make_float3(__ldg(pos + 3 * (int64_t)o), __ldg(pos + 3 * (int64_t)o + 1), __ldg(pos + 3 * (int64_t)o + 2));
+      eval_store<CAMS>(xr, xg, xb, o, s, p, s_view, V, out_order, n, ns, rgb);
     } else if (live && out_order == GSC_OUT_SLOT_ORDER) {
       for (int v = 0; v < V; v++) { float* d = rgb + ((int64_t)v * ns + s) * 3; d[0] = d[1] = d[2] = 0.f; }
     }
@@ -791,4 +825,181 @@ gsc_status decode_tex_run(gsc_ctx* ctx, const DevTable& T, const uint8_t* blocks
     e = cudaGetLastError();
   }
   return e == cudaSuccess ? GSC_OK : GSC_ERR_CUDA;
+}
+
+// ---- resident texture scene and texture-decoded fused evaluation ----------------------------
+// Sec. I: the GPU's fixed-function texture unit decodes BC blocks; a coded scene kept
+// resident as BC1/BC7 texture objects is evaluated without a software block decoder.
+struct gsc_tex_scene {
+  int device;
+  DevTable T;
+  TexBases B;
+  TexImg img[2];       // [0] BC1, [1] BC7
+  float4* pos_slot;    // positions in slot order (x, y, z, 0), or null
+};
+
+__global__ void k_pos_slot(const float* __restrict__ pos, const int32_t* __restrict__ perm, int64_t ns,
+                           float4* __restrict__ out) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t o = perm[s];
+    out[s] = o >= 0 ? make_float4(pos[3 * (int64_t)o], pos[3 * (int64_t)o + 1], pos[3 * (int64_t)o + 2], 0.f)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// exact (q - 128) from a UNORM8 sample f = q / 255: f * 255 + 1.5 * 2^23 lands on 1.5 * 2^23 + q
+__device__ __forceinline__ float unorm_m128(float f) { return fmaf(f, 255.0f, 12582912.0f) - 12583040.0f; }
+
+template <int KIND, bool CAMS>
+__global__ void __launch_bounds__(256) k_eval_tex(DevTable T, TexBases B, cudaTextureObject_t tex7,
+                                                  cudaTextureObject_t tex1, const int32_t* __restrict__ perm,
+                                                  const float* __restrict__ dirs, const float* __restrict__ pos,
+                                                  const float* __restrict__ cams, int V, int out_order,
+                                                  float* __restrict__ rgb, const float4* __restrict__ pos_slot) {
+  __shared__ float s_view[3][64];
+  __shared__ float s_deq[16];
+  load_views(s_view, s_deq, dirs, cams, V, T);
+  __syncthreads();
+  const int64_t n = T.n, ns = (int64_t)T.n_groups * 16;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t o = __ldg(perm + s);
+    if (o < 0) {
+      if (out_order == GSC_OUT_SLOT_ORDER)
+        for (int v = 0; v < V; v++) { float* d = rgb + ((int64_t)v * ns + s) * 3; d[0] = d[1] = d[2] = 0.f; }
+      continue;
+    }
+    const int64_t g = s >> 4;
+    const int t = (int)(s & 15);
+    int si = 0, j = 16, b = 16;
+    int64_t gi = g;
+    if (KIND == 0) { si = stream_of(T, g); j = T.bc7[si]; b = T.bands[si]; gi = g - T.first_group[si]; }
+    float xr[16], xg[16], xb[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+      float4 f;
+      if (KIND == 7) f = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (KIND == 7 || (KIND == 0 && k < j)) {
+        const int64_t bi = KIND == 7 ? g * 16 + k : B.b7[si] + gi * j + k;
+        const int x = (int)(bi % TEXW) * 4 + (t & 3), y = (int)(bi / TEXW) * 4 + (t >> 2);
+        f = tex2D<float4>(tex7, (float)x + 0.5f, (float)y + 0.5f);
+      } else if (KIND == 1 || (KIND == 0 && k < b)) {
+        const int64_t bi = KIND == 1 ? g * 16 + k : B.b1[si] + gi * (b - j) + (k - j);
+        const int x = (int)(bi % TEXW) * 4 + (t & 3), y = (int)(bi / TEXW) * 4 + (t >> 2);
+        f = tex2D<float4>(tex1, (float)x + 0.5f, (float)y + 0.5f);
+      } else {
+        f = make_float4(128.f / 255.f, 128.f / 255.f, 128.f / 255.f, 1.f);
+      }
+      const float q = s_deq[k];
+      xr[k] = unorm_m128(f.x) * q; xg[k] = unorm_m128(f.y) * q; xb[k] = unorm_m128(f.z) * q;
+    }
+    float3 p = make_float3(0.f, 0.f, 0.f);
+    if (CAMS) {
+      if (pos_slot) { const float4 q4 = __ldg(pos_slot + s); p = make_float3(q4.x, q4.y, q4.z); }
+      else p = make_float3(__ldg(pos + 3 * (int64_t)o), __ldg(pos + 3 * (int64_t)o + 1), __ldg(pos + 3 * (int64_t)o + 2));
+    }
+    eval_store<CAMS>(xr, xg, xb, o, s, p, s_view, V, out_order, n, ns, rgb);
+  }
+}
+
+extern "C" gsc_status gsc_tex_scene_create(gsc_ctx* c, const gsc_stream_table* table, const uint8_t* d_blocks,
+                                           const int32_t* d_perm, const float* d_pos, gsc_tex_scene** out,
+                                           void* stream) {
+  if (!c || !out) return GSC_ERR_INVALID_ARG;
+  *out = nullptr;
+  DevTable T;
+  gsc_status st = make_dev_table(table, &T);
+  if (st != GSC_OK) return st;
+  if (T.n_groups > 0 && !d_blocks) return GSC_ERR_INVALID_ARG;
+  if (((uintptr_t)d_blocks % 8) != 0) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  gsc_tex_scene* sc = new gsc_tex_scene();
+  sc->device = c->device;
+  sc->T = T;
+  int64_t n7 = 0, n1 = 0;
+  for (int i = 0; i < GSC_MODES; i++) { sc->B.b7[i] = 0; sc->B.b1[i] = 0; }
+  for (int i = 0; i < T.n_streams; i++) {
+    sc->B.b7[i] = n7; sc->B.b1[i] = n1;
+    n7 += T.stream_groups[i] * T.bc7[i];
+    n1 += T.stream_groups[i] * (T.bands[i] - T.bc7[i]);
+  }
+  uint8_t *lin7 = nullptr, *lin1 = nullptr;
+  cudaError_t e = cudaMalloc(&lin7, (size_t)(n7 > 0 ? n7 : 1) * 16);
+  if (e == cudaSuccess) e = cudaMalloc(&lin1, (size_t)(n1 > 0 ? n1 : 1) * 8);
+  if (e == cudaSuccess && T.n_groups > 0) {
+    int64_t grid = ceil_div64(T.n_groups * 16, 256);
+    if (grid > 152 * 16) grid = 152 * 16;
+    gsc_count_launch(); k_gather_streams<<<(int)grid, 256, 0, s>>>(T, sc->B, d_blocks, lin7, lin1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = make_tex(lin7, n7, 1, &sc->img[1], s);
+  if (e == cudaSuccess) e = make_tex(lin1, n1, 0, &sc->img[0], s);
+  sc->pos_slot = nullptr;
+  if (e == cudaSuccess && d_pos && d_perm && T.n_groups > 0) {
+    const int64_t ns = (int64_t)T.n_groups * 16;
+    e = cudaMalloc(&sc->pos_slot, sizeof(float4) * ns);
+    if (e == cudaSuccess) {
+      int64_t grid = ceil_div64(ns, 256);
+      if (grid > 152 * 16) grid = 152 * 16;
+      gsc_count_launch(); k_pos_slot<<<(int)grid, 256, 0, s>>>(d_pos, d_perm, ns, sc->pos_slot);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (lin7) cudaFree(lin7);
+  if (lin1) cudaFree(lin1);
+  if (e != cudaSuccess) {
+    free_tex(&sc->img[0]);
+    free_tex(&sc->img[1]);
+    if (sc->pos_slot) cudaFree(sc->pos_slot);
+    delete sc;
+    return GSC_ERR_CUDA;
+  }
+  *out = sc;
+  return GSC_OK;
+}
+
+extern "C" gsc_status gsc_tex_scene_destroy(gsc_tex_scene* sc) {
+  if (!sc) return GSC_ERR_INVALID_ARG;
+  cudaSetDevice(sc->device);
+  free_tex(&sc->img[0]);
+  free_tex(&sc->img[1]);
+  if (sc->pos_slot) cudaFree(sc->pos_slot);
+  delete sc;
+  return GSC_OK;
+}
+
+extern "C" gsc_status gsc_decode_eval_sh_tex(gsc_ctx* c, const gsc_tex_scene* sc, const int32_t* d_perm,
+                                             const float* d_dirs, const float* d_pos, const float* d_cams, int32_t V,
+                                             int32_t out_order, float* d_rgb, void* stream) {
+  if (!c || !sc || sc->device != c->device) return GSC_ERR_INVALID_ARG;
+  const DevTable& T = sc->T;
+  if (V < 1 || V > 64 || out_order < 0 || out_order > 2) return GSC_ERR_INVALID_ARG;
+  if ((d_dirs == nullptr) == (d_cams == nullptr)) return GSC_ERR_INVALID_ARG;
+  if (d_cams && !d_pos && !sc->pos_slot && T.n > 0) return GSC_ERR_INVALID_ARG;
+  if (T.n_groups > 0 && (!d_perm || !d_rgb)) return GSC_ERR_INVALID_ARG;
+  if (((uintptr_t)d_rgb % 16) != 0) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  if (T.n_groups == 0) return GSC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  GscTimed tm(c, T_EVAL_TEX, st);
+  const int64_t ns = (int64_t)T.n_groups * 16;
+  int64_t grid = ceil_div64(ns, 256);
+  const int64_t cap = (int64_t)(c->sm_count > 0 ? c->sm_count : 152) * 8;
+  if (grid > cap) grid = cap;
+  const int kind = kind_of(T);
+#define TEX_LAUNCH(K, C)                                                                                       \
+  do {                                                                                                         \
+    gsc_count_launch();                                                                                        \
+    k_eval_tex<K, C><<<(int)grid, 256, 0, st>>>(T, sc->B, sc->img[1].tex, sc->img[0].tex, d_perm, d_dirs, d_pos, \
+                                                d_cams, V, out_order, d_rgb, sc->pos_slot);                    \
+  } while (0)
+  if (d_cams) {
+    if (kind == 7) TEX_LAUNCH(7, true); else if (kind == 1) TEX_LAUNCH(1, true); else TEX_LAUNCH(0, true);
+  } else {
+    if (kind == 7) TEX_LAUNCH(7, false); else if (kind == 1) TEX_LAUNCH(1, false); else TEX_LAUNCH(0, false);
+  }
+#undef TEX_LAUNCH
+  GSC_CUDA(cudaGetLastError());
+  return GSC_OK;
 }

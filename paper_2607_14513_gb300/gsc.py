@@ -71,6 +71,9 @@ _SIGS = {
     "gsc_decode": [_P, C.POINTER(StreamTable), _P, _P, _P, _P],
     "gsc_decode_eval_sh": [_P, C.POINTER(StreamTable), _P, _P, _P, _P, _P, C.c_int32, C.c_int32, _P, _P],
     "gsc_decode_tex": [_P, C.POINTER(StreamTable), _P, _P, _P, _P],
+    "gsc_tex_scene_create": [_P, C.POINTER(StreamTable), _P, _P, _P, C.POINTER(C.c_void_p), _P],
+    "gsc_tex_scene_destroy": [_P],
+    "gsc_decode_eval_sh_tex": [_P, _P, _P, _P, _P, _P, C.c_int32, C.c_int32, _P, _P],
     "gsc_encode_blocks": [_P, _P, C.c_int64, C.c_int32, _P, _P, _P],
     "gsc_decode_blocks": [_P, _P, C.c_int64, C.c_int32, _P, _P],
     "gsc_decode_blocks_tex": [_P, _P, C.c_int64, C.c_int32, _P, _P],
@@ -260,6 +263,43 @@ def gsc_decode_tex(ctx, table, blocks, perm, stream=None):
     _check(ctx.lib.gsc_decode_tex(ctx.h, C.byref(table), _ptr(blocks), _ptr(perm), _ptr(tex), _stream(stream)),
            "gsc_decode_tex")
     return tex
+
+
+class TexScene:
+    """A coded scene resident as BC1/BC7 texture objects (gsc_tex_scene)."""
+
+    def __init__(self, ctx, table, blocks, perm=None, pos=None, stream=None):
+        self.ctx = ctx
+        self.table = table
+        h = C.c_void_p()
+        _check(ctx.lib.gsc_tex_scene_create(ctx.h, C.byref(table), _ptr(blocks), _ptr(perm), _ptr(pos), C.byref(h),
+                                            _stream(stream)), "gsc_tex_scene_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.gsc_tex_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gsc_decode_eval_sh_tex(ctx, scene, perm, dirs=None, pos=None, cams=None, out_order=OUT_VIEW_MAJOR, out=None,
+                           stream=None):
+    import torch
+    src = dirs if dirs is not None else cams
+    V = src.shape[0]
+    table = scene.table
+    n, ns = table.n, table.n_groups * 16
+    shape = {OUT_VIEW_MAJOR: (V, n, 3), OUT_SLOT_ORDER: (V, ns, 3), OUT_GAUSS_MAJOR: (n, V, 3)}[out_order]
+    rgb = out if out is not None else torch.empty(shape, dtype=torch.float32, device=perm.device)
+    _check(ctx.lib.gsc_decode_eval_sh_tex(ctx.h, scene.h, _ptr(perm), _ptr(dirs), _ptr(pos), _ptr(cams), V,
+                                          out_order, _ptr(rgb), _stream(stream)), "gsc_decode_eval_sh_tex")
+    return rgb
 
 
 def gsc_encode_blocks(ctx, tex, fmt, stream=None):

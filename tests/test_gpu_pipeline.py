@@ -151,6 +151,36 @@ def test_decode_eval_at_scale(ctx, O):
         _check_sh(got, out, ab)
 
 
+@pytest.mark.parametrize("fmt,n", [(1, 50_000), (7, 20_000), (0, 6_000)])
+def test_eval_through_texture_unit_equals_software(ctx, fmt, n):
+    # texels fetched through the texture unit, dequantised exactly, same SH code: the colours
+    # equal the software-decoded fused kernel bit for bit, in every order and direction mode
+    from paper_2607_14513_gb300 import gsc
+    sc = S.make_scene(n, 970 + fmt, heavy_frac=0.1)
+    perm, scales = gsc.gsc_plan_reorder(ctx, _dev(sc.pos), _dev(sc.sh))
+    blocks, perm_out, tab = gsc.gsc_encode(ctx, _dev(sc.sh), perm, scales, fmt, 16 if fmt == 0 else 0)
+    dirs, cams, pos = _dev(S.make_dirs(3, 971)), _dev(S.make_cams(8, 972)), _dev(sc.pos)
+    scene = gsc.TexScene(ctx, tab, blocks)                       # positions gathered per call
+    scene_p = gsc.TexScene(ctx, tab, blocks, perm_out, pos)      # positions resident in slot order
+    for order in (0, 1, 2):
+        for kw in (dict(dirs=dirs), dict(pos=pos, cams=cams)):
+            a = gsc.gsc_decode_eval_sh(ctx, tab, blocks, perm_out, out_order=order, **kw)
+            b = gsc.gsc_decode_eval_sh_tex(ctx, scene, perm_out, out_order=order, **kw)
+            kw2 = dict(kw)
+            kw2.pop("pos", None)
+            c = gsc.gsc_decode_eval_sh_tex(ctx, scene_p, perm_out, out_order=order, **kw2)
+            ctx.sync()
+            assert torch.equal(a, b)
+            assert torch.equal(a, c)
+    # odd view counts take the unvectorised store path
+    a = gsc.gsc_decode_eval_sh(ctx, tab, blocks, perm_out, dirs=_dev(S.make_dirs(5, 973)), out_order=2)
+    b = gsc.gsc_decode_eval_sh_tex(ctx, scene_p, perm_out, dirs=_dev(S.make_dirs(5, 973)), out_order=2)
+    ctx.sync()
+    assert torch.equal(a, b)
+    scene.close()
+    scene_p.close()
+
+
 def test_rate_budget_error(ctx):
     from paper_2607_14513_gb300 import gsc
     sc = S.make_scene(500, 701)                    # 32 groups: the cheapest coding needs 2048 bits > 4 * 500
