@@ -344,6 +344,289 @@ def run_e2e(args, ctx, gsc, stream, dev, sc, step, world):
 
 
 # ------------------------------------------------------------------------------------------------
+def run_batch(args, world, rank, local):
+    """64 scenes of uneven sizes: one persistent encode launch + one captured evaluation graph,
+    against per-scene plain calls (plan, encode, decode + SH eval per scene) on the same data."""
+    import torch
+    from paper_2607_14513_gb300 import gsc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    mix = S.batch_mix(**dict(S.BATCH, seed=S.BATCH["seed"] + 1000 * rank))
+    fmt_of = {"bc1": gsc.FMT_BC1, "bc7": gsc.FMT_BC7, "rate": gsc.FMT_RATE}
+    ctx = gsc.Context(local)
+    stream = torch.cuda.Stream(dev)
+    cams = torch.from_numpy(S.make_cams(N_CAMS, 1100 + rank)).to(dev)
+    scenes, host = [], []
+    for n, seed, f, t4 in mix:
+        sc = S.make_scene(n, seed, clusters=S.SCENE["clusters"], heavy_frac=S.SCENE["heavy_frac"])
+        pos_h = torch.from_numpy(sc.pos).pin_memory()
+        sh_h = torch.from_numpy(sc.sh).pin_memory()
+        host.append((pos_h, sh_h))
+        scenes.append((pos_h.to(dev), sh_h.to(dev), fmt_of[f], t4))
+    total_n = sum(m[0] for m in mix)
+    batch = gsc.Batch(ctx, scenes, group_size=4096)
+    torch.cuda.synchronize()
+    tuning, proxy_ms = batch.autotune(stream=stream)
+    outs = [torch.empty((n, N_CAMS, 3), dtype=torch.float32, device=dev) for n, _, _, _ in mix]
+    outs_plain = [torch.empty((n, N_CAMS, 3), dtype=torch.float32, device=dev) for n, _, _, _ in mix]
+    batch.encode(tuning, stream=stream)
+    graph = batch.eval_graph(cams, outs, stream=stream)
+
+    def batched():
+        batch.encode(tuning, stream=stream)
+        graph.launch(stream=stream)
+
+    n_max = max(m[0] for m in mix)
+    ws = ctx.workspace(n_max, gsc.FMT_RATE, 32)
+    ng_max = (n_max + 15) // 16
+    blk = torch.empty(ng_max * 256, dtype=torch.uint8, device=dev)
+    po = torch.empty(ng_max * 16, dtype=torch.int32, device=dev)
+
+    def plain():
+        for (pos, sh, fmt, t4), out in zip(scenes, outs_plain):
+            perm, scales = gsc.gsc_plan_reorder(ctx, pos, sh, ws=ws, stream=stream)
+            b, p, tab = gsc.gsc_encode(ctx, sh, perm, scales, fmt, t4, ws=ws, out=blk, perm_out=po, stream=stream)
+            gsc.gsc_decode_eval_sh(ctx, tab, b, p, pos=pos, cams=cams, out_order=gsc.OUT_GAUSS_MAJOR, out=out,
+                                   stream=stream)
+
+    def timed(fn, steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    for _ in range(args.warmup):
+        batched()
+        plain()
+    stream.synchronize()
+    same = all(torch.equal(a, b) for a, b in zip(outs, outs_plain))
+    barrier(world)
+    torch.cuda.synchronize()
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    gsc.set_timing(ctx, True)
+    launches0 = gsc.launch_count()
+    ms_batched = timed(batched, args.steps)
+    launches = gsc.launch_count() - launches0
+    kb_ms, kb_cnt = gsc.kernel_time(ctx, "batch_encode")
+    gsc.set_timing(ctx, False)
+    ms_plain = timed(plain, args.steps)
+    clk = clocks.stop()
+    ms_step = max_over_ranks(ms_batched, world, dev)
+    ms_plain = max_over_ranks(ms_plain, world, dev)
+    ms_graph = timed(lambda: graph.launch(stream=stream), max(5, args.steps))
+
+    # the persistent encode launch: BC7 candidate search of every BC7-searched block
+    nb7 = sum(((m[0] + 15) // 16) * 16 for m in mix if m[2] != "bc1")
+    kb_ms /= max(1, kb_cnt)
+    int_peak = gsc.int_peak(ctx, stream=stream)
+    ach = BC7_EVALS_PER_BLOCK * OPS_PER_EVAL * nb7 / (kb_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(ach, 3), "peak": round(int_peak / 1e12, 3), "unit": "Tops/s",
+                "frac": round(ach / (int_peak / 1e12), 4), "traffic": None,
+                "kernel": "k_batch (persistent BC1/BC7 search over all scenes, schedule %d, %d CTAs/SM, "
+                          "BC1 tiles of %d groups)" % (tuning.schedule, tuning.ctas_per_sm, tuning.bc1_tile_groups),
+                "peak_source": "measured on this GPU by gsc_probe_int_peak",
+                "algorithmic": "%d palette evaluations x %d int ops per BC7-searched block, %d blocks (BC1 work "
+                               "not counted)" % (BC7_EVALS_PER_BLOCK, OPS_PER_EVAL, nb7)}
+    hbm, hbm_src = peaks()
+    ev_bytes = 0
+    for i, (n, _, f, _) in enumerate(mix):
+        ns = (n + 15) // 16 * 16
+        ev_bytes += batch.result(i)[4].total_bytes + 4 * ns + 12 * n + N_CAMS * 12 * n
+    ev_gbs = ev_bytes / (ms_graph * 1e-3) / 1e9
+    roofline_eval = {"bound": "hbm", "achieved": round(ev_gbs, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(ev_gbs / hbm, 4), "traffic": None, "peak_source": hbm_src,
+                     "kernel": "captured graph of k_eval2 over 64 scenes (%d cameras, Gaussian-major)" % N_CAMS}
+
+    # end to end: pinned host scenes in, every scene's blocks and slot order out
+    blocks_h = [torch.empty(max(1, batch.result(i)[2].numel()), dtype=torch.uint8).pin_memory()
+                for i in range(len(mix))]
+    perm_h = [torch.empty(max(1, batch.result(i)[3].numel()), dtype=torch.int32).pin_memory()
+              for i in range(len(mix))]
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            for (pos_h, sh_h), (pos, sh, _, _) in zip(host, scenes):
+                pos.copy_(pos_h, non_blocking=True)
+                sh.copy_(sh_h, non_blocking=True)
+        batched()
+        with torch.cuda.stream(stream):
+            for i in range(len(mix)):
+                _, _, b, p, _ = batch.result(i)
+                blocks_h[i][:b.numel()].copy_(b, non_blocking=True)
+                perm_h[i][:p.numel()].copy_(p, non_blocking=True)
+        return sum(batch.result(i)[2].numel() + 4 * batch.result(i)[3].numel() for i in range(len(mix)))
+
+    e2e_step()
+    stream.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        bo = e2e_step()
+    stream.synchronize()
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
+
+    out = {"metric": METRIC, "value": round(world * total_n / (ms_step * 1e-3) / 1e6, 3), "unit": UNIT,
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u8 texels / int32 search / f32 SH eval", "data": "synthetic (seeded)",
+           "config": {"workload": "batched form: %d scenes, %d..%d Gaussians log-uniform (%d total), formats "
+                                  "cycling BC1 / BC7 / rate 3-4-6-8 bpt; one persistent encode launch + one "
+                                  "captured evaluation graph (%d cameras)" % (len(mix), S.BATCH["lo"],
+                                                                             S.BATCH["hi"], total_n, N_CAMS),
+                      "n_gaussians": total_n, "parallelism": "weak, one batch per GPU" if world > 1 else "single GPU",
+                      "l2": "inputs larger than L2", "bit_exact_vs_per_scene": same},
+           "batched_vs_per_scene": {"batched_ms": round(ms_step, 3), "per_scene_ms": round(ms_plain, 3),
+                                    "speedup": round(ms_plain / ms_step, 3),
+                                    "tuning": {"schedule": tuning.schedule, "ctas_per_sm": tuning.ctas_per_sm,
+                                               "bc1_tile_groups": tuning.bc1_tile_groups,
+                                               "proxy_ms": round(proxy_ms, 3)}},
+           "roofline": roofline, "roofline_decode_eval": roofline_eval,
+           "stages": {"batch_encode_ms": round(kb_ms, 3), "eval_graph_ms": round(ms_graph, 3)},
+           "clocks": clk,
+           "e2e": {"value": round(world * total_n / t_e2e / 1e6, 3), "unit": UNIT,
+                   "h2d_bytes_per_step": int(total_n * (12 + 192)), "d2h_bytes_per_step": int(bo),
+                   "ms_per_step": round(t_e2e * 1e3, 3)},
+           "gpu_launches": int(launches)}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_mix(mix, budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    graph.close()
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_serve(args, world, rank, local):
+    """A Poisson stream of encode and evaluation requests against the request loop: continuous
+    batching (4 slots, merged evaluations, high-priority evaluation streams) and, on the same
+    trace, a plain queue (one slot, no merging). Latency is the server's submit-to-done time."""
+    import queue
+    import torch
+    from paper_2607_14513_gb300 import gsc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = dict(S.SERVE, seed=S.SERVE["seed"] + 1000 * rank)
+    pool, reqs = S.serve_trace(**cfg, seconds=args.serve_seconds)
+    fmt_of = {"bc1": gsc.FMT_BC1, "bc7": gsc.FMT_BC7}
+    ctx = gsc.Context(local)
+    host = []
+    for n, seed, f in pool:
+        sc = S.make_scene(n, seed, clusters=S.SCENE["clusters"], heavy_frac=S.SCENE["heavy_frac"])
+        host.append((torch.from_numpy(sc.pos).pin_memory(), torch.from_numpy(sc.sh).pin_memory(), fmt_of[f]))
+    cams = [torch.from_numpy(S.make_cams(V, cs)).to(dev) for _, _, _, V, cs in reqs]
+    budget = 120 * (1 << 30)
+
+    def play(n_slots, merge, priority):
+        srv = gsc.Server(ctx, budget, n_slots=n_slots, merge=merge, priority=priority)
+        ts = [srv.encode(i, h[0], h[1], h[2]) for i, h in enumerate(host)]
+        for t in ts:
+            assert srv.wait(t).status == 0
+        done = []
+        q = queue.Queue()
+
+        def waiter():
+            while True:
+                item = q.get()
+                if item is None:
+                    return
+                t, kind, n, V = item
+                done.append((kind, srv.wait(t), n, V))
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        lag = 0.0
+        t0 = time.perf_counter()
+        for k, (ta, kind, i, V, _) in enumerate(reqs):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            lag = max(lag, time.perf_counter() - t0 - ta)
+            n = pool[i][0]
+            if kind == "encode":
+                q.put((srv.encode(i, host[i][0], host[i][1], host[i][2]), kind, n, 0))
+            else:
+                out = torch.empty((n, V, 3), dtype=torch.float32, device=dev)
+                q.put((srv.eval(i, n, out, cams=cams[k]), kind, n, V))
+        q.put(None)
+        th.join()
+        span = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        lat = {kd: np.array([r.t_done_ms - r.t_submit_ms for k2, r, _, _ in done if kd in (k2, "all")])
+               for kd in ("all", "encode", "eval")}
+        bad = sum(r.status != 0 for _, r, _, _ in done)
+        gauss = sum(n for _, r, n, _ in done)
+        pct = {}
+        for kd, a in lat.items():
+            if a.size:
+                pct[kd] = {"p50_ms": round(float(np.percentile(a, 50)), 3),
+                           "p99_ms": round(float(np.percentile(a, 99)), 3), "count": int(a.size)}
+        return {"latency": pct, "served_req_s": round(len(done) / span, 2), "MGauss_s": round(gauss / span / 1e6, 3),
+                "span_s": round(span, 3), "failed": int(bad), "merged": int(st.merged), "evictions": int(st.evictions),
+                "peak_bytes": int(st.peak_bytes), "max_submit_lag_ms": round(lag * 1e3, 3),
+                "slots": n_slots, "merge": bool(merge), "priority": bool(priority)}
+
+    barrier(world)
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    launches0 = gsc.launch_count()
+    cb = play(4, True, True)
+    launches = gsc.launch_count() - launches0
+    clk = clocks.stop()
+    plain = play(1, False, False)
+    value = max_over_ranks(-cb["MGauss_s"], world, dev) * -1 * world
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 1,
+           "ms_per_step": round(cb["span_s"] * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u8 texels / int32 search / f32 SH eval", "data": "synthetic (seeded)",
+           "config": {"workload": "served form: Poisson %.0f req/s for %.0f s, %.0f%% re-encodes of a pool of %d "
+                                  "scenes (%d..%d Gaussians log-uniform, half BC1 / half BC7), the rest decode + SH "
+                                  "eval of 1..32 camera centres; 120 GB HBM admission budget"
+                                  % (cfg["rate_hz"], args.serve_seconds, 100 * cfg["encode_frac"], cfg["n_scenes"],
+                                     cfg["lo"], cfg["hi"]),
+                      "requests": len(reqs), "pool_gaussians": int(sum(p[0] for p in pool))},
+           "serving": {"continuous_batching": cb, "plain_queue": plain},
+           "clocks": clk, "gpu_launches": int(launches),
+           "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": 0,
+                   "note": "requests carry pinned host scenes (encode) and device outputs (eval)"}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline_mix(mix, budget_s=20.0):
+    """The oracle's per-Gaussian stage times (scene-scale sample) charged to each scene of a
+    batch by its format: plan + its coding(s) + one decode + SH evaluation."""
+    b = cpu_baseline("scene3m", budget_s=budget_s)
+    st = {k: v * 1e-6 for k, v in b["stage_us_per_gaussian"].items()}
+    enc = {"bc1": st["bc1"], "bc7": st["bc7"], "rate": st["bc1"] + st["bc7"]}
+    t = sum(n * (st["plan"] + enc[f] + st["decode_eval"]) for n, _, f, _ in mix)
+    return {"value": round(sum(m[0] for m in mix) / t / 1e6, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": b["sample"] + "; charged per scene by format"}
+
+
+# ------------------------------------------------------------------------------------------------
 def cpu_baseline(workload, budget_s=20.0):
     """The oracle, as it stands, single-threaded on a bounded sample of the workload.
 
@@ -419,13 +702,20 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gsc", choices=["gsc", "reference"])
-    ap.add_argument("--workload", default="scene3m", choices=["scene3m", "medium262k", "tiny4k"])
+    ap.add_argument("--workload", default="scene3m", choices=["scene3m", "medium262k", "tiny4k", "batch64", "serve"])
+    ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload == "batch64":
+        run_batch(args, world, rank, local)
+        return
+    if args.workload == "serve":
+        run_serve(args, world, rank, local)
         return
     run_gsc(args, world, rank, local)
 

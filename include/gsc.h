@@ -199,6 +199,159 @@ gsc_status gsc_decode_eval_sh_tex(gsc_ctx* ctx, const gsc_tex_scene* scene, cons
                                   const float* d_dirs, const float* d_pos, const float* d_cams, int32_t V,
                                   int32_t out_order, float* d_rgb, void* stream);
 
+/* Batched form: many scenes of uneven sizes (the paper codes one scene at a time; this packages
+ * the same steps for throughput). Per scene the results equal the single-scene calls bit for bit:
+ * the plan of gsc_plan_reorder (quantile 995), then the blocks, slot order and stream table of
+ * gsc_encode with the scene's format. All BC1/BC7 block searches of all scenes run in one
+ * persistent launch whose CTAs claim tiles of groups (Sec. IV-B layout D); rate scenes then
+ * select their streams one by one. At most 1024 scenes (else GSC_ERR_INVALID_ARG). The caller
+ * owns every buffer; the call synchronises `stream`. */
+typedef struct {
+  const float* d_pos;       /* [n][3] (needed when sort = 1 and for evaluation) */
+  const float* d_sh;        /* [n][16][3], 16-byte aligned */
+  int64_t n;
+  int64_t group_size;       /* as gsc_plan_params */
+  int32_t sort;
+  int32_t format;           /* GSC_FMT_BC1, GSC_FMT_BC7 or GSC_FMT_RATE */
+  uint32_t target_bpt_x4;   /* rate scenes */
+  int32_t* d_perm;          /* out: planned slot order [n_groups*16] */
+  float* d_scales;          /* out: [16] */
+  uint8_t* d_blocks;        /* out: n_groups*256 bytes of capacity, 16-byte aligned */
+  int32_t* d_perm_out;      /* out: final slot order [n_groups*16] */
+  gsc_stream_table table;   /* out */
+} gsc_batch_scene;
+
+/* How the persistent launch hands out work: schedule 0 = static round robin over tiles,
+ * 1 = atomic work queue, 2 = atomic queue over scenes ordered by decreasing cost; CTAs per
+ * SM 1..4; groups per BC1 tile (multiple of 8; BC7 tiles are 8 groups). */
+typedef struct {
+  int32_t schedule;
+  int32_t ctas_per_sm;
+  int32_t bc1_tile_groups;
+} gsc_batch_tuning;
+
+size_t gsc_batch_workspace_bytes(const gsc_batch_scene* scenes, int32_t n_scenes);
+gsc_status gsc_batch_encode(gsc_ctx* ctx, gsc_batch_scene* scenes, int32_t n_scenes, const gsc_batch_tuning* tune,
+                            void* d_ws, size_t ws_bytes, void* stream);
+/* Times every tuning (3 schedules x 3 occupancies x 2 BC1 tile sizes) on a 1/32-scale proxy
+ * of the same batch (each scene's first groups) and returns the fastest. It writes the
+ * scenes' plans and partial blocks (gsc_batch_encode overwrites them). */
+gsc_status gsc_batch_autotune(gsc_ctx* ctx, gsc_batch_scene* scenes, int32_t n_scenes, gsc_batch_tuning* out,
+                              double* proxy_ms, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Decode + SH evaluation (gsc_decode_eval_sh with camera centres) of every scene of an encoded
+ * batch, captured once into a CUDA graph on `stream` (a created stream, not the legacy one)
+ * and replayed with gsc_graph_launch. d_rgb[i] is scene i's output (16-byte aligned). The
+ * graph reads the scenes' buffers at launch time but keeps each scene's stream table as it
+ * was at capture: capture again after a re-encode that changes a table. */
+typedef struct gsc_graph gsc_graph;
+gsc_status gsc_batch_eval_graph(gsc_ctx* ctx, const gsc_batch_scene* scenes, int32_t n_scenes, const float* d_cams,
+                                int32_t V, int32_t out_order, float* const* d_rgb, gsc_graph** out, void* stream);
+gsc_status gsc_graph_launch(gsc_graph* graph, void* stream);
+gsc_status gsc_graph_destroy(gsc_graph* graph);
+
+/* Request loop (serving form; the paper codes scenes offline, this keeps the same calls
+ * behind a queue). Encode and evaluation requests are submitted at any time from any host
+ * thread; coded scenes stay resident on the device; n_slots worker threads each own a
+ * context and two CUDA streams (evaluations on the high-priority one) and take the next
+ * admissible request as soon as they are free, so the work of several requests overlaps on
+ * the device. A request is admitted when a slot is free and its device memory fits in
+ * hbm_budget_bytes (resident scenes + running requests' buffers), evicting idle resident
+ * scenes least recently used first when that makes it fit. Requests on one scene keep their
+ * submission order around encodes. Queued evaluations of one scene with the same output
+ * order and view kind merge into one launch of up to max_views views. Every result equals
+ * the single calls' bit for bit: an encode is gsc_plan_reorder (quantile 995) + gsc_encode,
+ * an evaluation is gsc_decode_eval_sh of the scene's resident coding. */
+typedef struct {
+  uint64_t hbm_budget_bytes;
+  int32_t n_slots;            /* 1..16 */
+  int32_t merge;              /* 0 or 1 */
+  int32_t max_views;          /* 1..64: views of one evaluation request and of one merged launch */
+  int32_t priority;           /* 1: evaluations on high-priority streams */
+  int64_t hold_us;            /* a request older than this that does not fit holds back later ones */
+} gsc_server_params;
+
+enum { GSC_REQ_ENCODE = 0, GSC_REQ_EVAL = 1 };
+
+/* Pointers may be host (pinned or pageable) or device memory and must stay valid until the
+ * request completes. Encode: pos [n][3], sh [n][16][3] (16-byte aligned), format, rate target,
+ * group_size and sort as in gsc_plan_reorder / gsc_encode. Evaluation: n = the resident scene's
+ * Gaussian count (the request fails with GSC_ERR_INVALID_ARG if the scene is not resident or has
+ * another size), exactly one of dirs / cams [V][3], out [n][V][3] / [V][n][3] / [V][ns][3] by
+ * out_order, 16-byte aligned. */
+typedef struct {
+  int32_t kind;
+  int32_t scene;              /* caller's id, >= 0 */
+  const float* pos;
+  const float* sh;
+  int64_t n;
+  int32_t format;
+  uint32_t target_bpt_x4;
+  int64_t group_size;
+  int32_t sort;
+  int32_t V;
+  const float* dirs;
+  const float* cams;
+  int32_t out_order;
+  float* out;
+} gsc_request;
+
+typedef struct {
+  int32_t status;             /* gsc_status of the request */
+  int32_t kind;
+  int32_t scene;
+  int32_t merged;             /* requests in its launch */
+  int64_t n;
+  double t_submit_ms, t_admit_ms, t_done_ms;  /* since gsc_server_create */
+} gsc_request_result;
+
+typedef struct {
+  uint64_t submitted, done, failed, merged, evictions;
+  uint64_t resident_bytes, used_bytes, peak_bytes;
+  int32_t queued, resident_versions;
+} gsc_server_stats;
+
+typedef struct gsc_server gsc_server;
+gsc_status gsc_server_create(gsc_ctx* ctx, const gsc_server_params* p, gsc_server** out);
+/* GSC_ERR_BUDGET when the request could never fit; otherwise queued, *ticket identifies it. */
+gsc_status gsc_server_submit(gsc_server* srv, const gsc_request* req, uint64_t* ticket);
+/* Waits for a ticket (timeout_ms < 0: no limit; GSC_ERR_TIMEOUT when it runs out) and
+ * consumes it. The request's own outcome is res->status. */
+gsc_status gsc_server_wait(gsc_server* srv, uint64_t ticket, int64_t timeout_ms, gsc_request_result* res);
+gsc_status gsc_server_drain(gsc_server* srv, int64_t timeout_ms);
+/* Copies a resident scene's table, blocks and slot order out (host or device buffers). */
+gsc_status gsc_server_read_scene(gsc_server* srv, int32_t scene, gsc_stream_table* table, uint8_t* blocks,
+                                 size_t blocks_cap, int32_t* perm, size_t perm_bytes_cap);
+/* Frees a resident scene that no queued or running request uses (else GSC_ERR_INVALID_ARG). */
+gsc_status gsc_server_evict(gsc_server* srv, int32_t scene);
+gsc_status gsc_server_get_stats(gsc_server* srv, gsc_server_stats* st);
+/* Drains, stops the workers and frees every resident scene. */
+gsc_status gsc_server_destroy(gsc_server* srv);
+
+/* The admission policy of the request loop run on the host against a trace: arrivals in ms,
+ * a service time per request (a merged launch takes the sum of its requests'), n_slots
+ * launches at a time. No device work; the memory figures are the server's. */
+typedef struct {
+  int32_t kind, scene;
+  int64_t n;
+  int32_t format;
+  uint32_t target_bpt_x4;
+  int32_t V, out_order, cams, out_device, host_input;
+  double t_arrival_ms, service_ms;
+} gsc_sim_request;
+
+typedef struct {
+  int32_t status;             /* GSC_OK, GSC_ERR_INVALID_ARG (rejected), GSC_ERR_BUDGET (never fits) */
+  int32_t merged;
+  int32_t evictions;          /* scenes evicted to admit it */
+  int32_t pad;
+  double t_admit_ms, t_done_ms;
+  uint64_t used_bytes_at_admit;
+} gsc_sim_result;
+
+gsc_status gsc_server_simulate(const gsc_server_params* p, const gsc_sim_request* reqs, int32_t n,
+                               gsc_sim_result* res, uint64_t* peak_bytes);
+
 /* Block-level codecs (Sec. III-B): nblk independent 4x4 blocks.
  * d_tex [nblk][16][3] uint8 -> d_out [nblk][8 or 16] bytes; d_sse [nblk] (optional)
  * receives each block's squared error. format: GSC_FMT_BC1 or GSC_FMT_BC7. */
@@ -221,8 +374,8 @@ gsc_status gsc_probe_int_peak(gsc_ctx* ctx, double* ops_per_s, void* stream);
 /* Kernel timing: when enabled, each call records CUDA events on its own stream around its
  * main kernels. gsc_kernel_time waits for the recorded events and returns the summed
  * milliseconds and launch count of one kernel ("plan", "bc1_encode", "bc7_encode",
- * "rate_select", "decode", "decode_eval", "decode_tex", "decode_eval_tex") since timing
- * was last enabled. */
+ * "rate_select", "decode", "decode_eval", "decode_tex", "decode_eval_tex", "batch_encode")
+ * since timing was last enabled. */
 gsc_status gsc_ctx_set_timing(gsc_ctx* ctx, int enable);
 gsc_status gsc_kernel_time(gsc_ctx* ctx, const char* name, double* ms, int64_t* launches);
 

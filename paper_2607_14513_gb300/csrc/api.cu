@@ -14,7 +14,7 @@ void gsc_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 extern "C" uint64_t gsc_launch_count(void) { return g_launches.load(); }
 
 static const char* kTimerNames[T_COUNT] = {"plan", "bc1_encode", "bc7_encode", "rate_select", "decode",
-                                           "decode_eval", "decode_tex", "decode_eval_tex"};
+                                           "decode_eval", "decode_tex", "decode_eval_tex", "batch_encode"};
 
 int gsc_timer_begin(gsc_ctx* c, int id, cudaStream_t st) {
   if (!c || !c->timing) return -1;
@@ -136,7 +136,9 @@ extern "C" const char* gsc_status_string(gsc_status s) {
   }
 }
 
-extern "C" gsc_status gsc_ctx_create(gsc_ctx** out, int device) {
+extern "C" gsc_status gsc_ctx_create(gsc_ctx** out, int device) { return ctx_new(device, true, out); }
+
+gsc_status ctx_new(int device, bool init_tables, gsc_ctx** out) {
   if (!out) return GSC_ERR_INVALID_ARG;
   *out = nullptr;
   int count = 0;
@@ -157,10 +159,12 @@ extern "C" gsc_status gsc_ctx_create(gsc_ctx** out, int device) {
   if (e == cudaSuccess) { c->d_diag = c->d_status + 1; e = cudaMemset(c->d_status, 0, 2 * sizeof(int)); }
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_pinned, PINNED_BYTES);
   c->h_pinned_bytes = PINNED_BYTES;
-  if (e == cudaSuccess) e = bc1_init_tables();
-  if (e == cudaSuccess) e = bc7_init_tables();
-  if (e == cudaSuccess) e = decode_init_tables();
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (init_tables) {
+    if (e == cudaSuccess) e = bc1_init_tables();
+    if (e == cudaSuccess) e = bc7_init_tables();
+    if (e == cudaSuccess) e = decode_init_tables();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
   if (e != cudaSuccess) {
     if (c->d_status) cudaFree(c->d_status);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -232,7 +236,7 @@ extern "C" gsc_status gsc_quantise(gsc_ctx* c, const float* d_sh, int64_t n, con
   return GSC_OK;
 }
 
-static void host_weights(const float* scales, uint32_t* w) {
+void host_weights(const float* scales, uint32_t* w) {
   double mx = 0.0;
   for (int k = 0; k < GSC_SH; k++) { double s = scales[k]; if (s * s > mx) mx = s * s; }
   for (int k = 0; k < GSC_SH; k++) {

@@ -10,12 +10,8 @@
 //  565 quantisation; two least-squares refinements on the current indices; then up to
 //  four rounds of the best strictly improving +-1 step on the six endpoint channels.
 //  Every candidate is scored with the four-colour palette of the GB300 texture unit.
-#include "gsc_internal.cuh"
-#include "stage.cuh"
+#include "bc1_dev.cuh"
 
-// Per channel value: best (a, b) code pair for a constant block, packed a | b << 8.
-__constant__ uint16_t c_const5[256];
-__constant__ uint16_t c_const6[256];
 
 static int h_ex5(int x) { return (x << 3) | (x >> 2); }
 static int h_ex6(int x) { return (x << 2) | (x >> 4); }
@@ -26,8 +22,7 @@ static int h_third(int a, int b, int bits) {
   return A + (num >= 0 ? num / 1024 : -((-num + 1023) / 1024));
 }
 
-cudaError_t bc1_init_tables() {
-  uint16_t t5[256], t6[256];
+void bc1_const_tables(uint16_t* t5, uint16_t* t6) {
   for (int v = 0; v < 256; v++) {
     for (int bits = 5; bits <= 6; bits++) {
       int lim = 1 << bits, be = -1, ba = 0, bb = 0;
@@ -39,166 +34,15 @@ cudaError_t bc1_init_tables() {
       (bits == 5 ? t5 : t6)[v] = (uint16_t)(ba | (bb << 8));
     }
   }
+}
+
+cudaError_t bc1_init_tables() {
+  uint16_t t5[256], t6[256];
+  bc1_const_tables(t5, t6);
   (void)h_ex5;
   cudaError_t e = cudaMemcpyToSymbol(c_const5, t5, sizeof(t5));
   if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_const6, t6, sizeof(t6));
-}
-
-__device__ __forceinline__ int ex5(int x) { return (x << 3) | (x >> 2); }
-__device__ __forceinline__ int ex6(int x) { return (x << 2) | (x >> 4); }
-// Interior entries: measured GB300 texture-unit rule (5-bit on codes, 6-bit on expansions).
-__device__ __forceinline__ int third5(int a, int b) { return ((2 * a + b) * 11) >> 2; }
-__device__ __forceinline__ int third6(int a, int b) {
-  int A = ex6(a), B = ex6(b);
-  return A + (((B - A) * 321 + 512) >> 10);
-}
-
-struct Bc1Res {
-  uint32_t sse;
-  uint32_t idx;   // 2 bits per texel
-  uint16_t c0, c1;
-};
-
-__device__ __forceinline__ Bc1Res bc1_eval(const uint32_t (&tx)[16], uint32_t a, uint32_t b) {
-  Bc1Res r;
-  r.c0 = (uint16_t)max(a, b);
-  r.c1 = (uint16_t)min(a, b);
-  r.sse = 0;
-  r.idx = 0;
-  const int ra = r.c0 >> 11, ga = (r.c0 >> 5) & 63, ba = r.c0 & 31;
-  const int rb = r.c1 >> 11, gb = (r.c1 >> 5) & 63, bb = r.c1 & 31;
-  const int p0r = ex5(ra), p0g = ex6(ga), p0b = ex5(ba);
-  if (r.c0 == r.c1) {
-#pragma unroll
-    for (int t = 0; t < 16; t++) {
-      int dr = tex_r(tx[t]) - p0r, dg = tex_g(tx[t]) - p0g, db = tex_b(tx[t]) - p0b;
-      r.sse += dr * dr + dg * dg + db * db;
-    }
-    return r;
-  }
-  const int p1r = ex5(rb), p1g = ex6(gb), p1b = ex5(bb);
-  const int p2r = third5(ra, rb), p2g = third6(ga, gb), p2b = third5(ba, bb);
-  const int p3r = third5(rb, ra), p3g = third6(gb, ga), p3b = third5(bb, ba);
-#pragma unroll
-  for (int t = 0; t < 16; t++) {
-    const int vr = tex_r(tx[t]), vg = tex_g(tx[t]), vb = tex_b(tx[t]);
-    int d, best, j = 0;
-    d = vr - p0r; best = d * d; d = vg - p0g; best += d * d; d = vb - p0b; best += d * d;
-    int e1, e2, e3;
-    d = vr - p1r; e1 = d * d; d = vg - p1g; e1 += d * d; d = vb - p1b; e1 += d * d;
-    d = vr - p2r; e2 = d * d; d = vg - p2g; e2 += d * d; d = vb - p2b; e2 += d * d;
-    d = vr - p3r; e3 = d * d; d = vg - p3g; e3 += d * d; d = vb - p3b; e3 += d * d;
-    if (e1 < best) { best = e1; j = 1; }
-    if (e2 < best) { best = e2; j = 2; }
-    if (e3 < best) { best = e3; j = 3; }
-    r.sse += best;
-    r.idx |= (uint32_t)j << (2 * t);
-  }
-  return r;
-}
-
-__device__ __forceinline__ int q5(int v) { return (v * 31 + 127) / 255; }
-__device__ __forceinline__ int q6(int v) { return (v * 63 + 127) / 255; }
-__device__ __forceinline__ uint32_t pack565(int r, int g, int b) { return (q5(r) << 11) | (q6(g) << 5) | q5(b); }
-
-// Encodes one block; returns the palette choice and writes sse0 (error of texel 128) if asked.
-__device__ Bc1Res bc1_encode(const uint32_t (&tx)[16]) {
-  bool constant = true;
-#pragma unroll
-  for (int t = 1; t < 16; t++) constant &= (tx[t] == tx[0]);
-  if (constant) {
-    uint32_t pr = c_const5[tex_r(tx[0])], pg = c_const6[tex_g(tx[0])], pb = c_const5[tex_b(tx[0])];
-    uint32_t c0 = ((pr & 255) << 11) | ((pg & 255) << 5) | (pb & 255);
-    uint32_t c1 = ((pr >> 8) << 11) | ((pg >> 8) << 5) | (pb >> 8);
-    return bc1_eval(tx, c0, c1);
-  }
-  int lo[3] = {255, 255, 255}, hi[3] = {0, 0, 0}, s1[3] = {0, 0, 0};
-  int s2rg = 0, s2rb = 0, s2gb = 0;
-#pragma unroll
-  for (int t = 0; t < 16; t++) {
-    int v[3] = {tex_r(tx[t]), tex_g(tx[t]), tex_b(tx[t])};
-#pragma unroll
-    for (int c = 0; c < 3; c++) { lo[c] = min(lo[c], v[c]); hi[c] = max(hi[c], v[c]); s1[c] += v[c]; }
-    s2rg += v[0] * v[1]; s2rb += v[0] * v[2]; s2gb += v[1] * v[2];
-  }
-  int ref = 0;
-  if (hi[1] - lo[1] > hi[ref] - lo[ref]) ref = 1;
-  if (hi[2] - lo[2] > hi[ref] - lo[ref]) ref = 2;
-  // covariance of the reference channel with each other channel (scaled by 16)
-  int cov[3];
-  cov[0] = ref == 1 ? 16 * s2rg - s1[1] * s1[0] : (ref == 2 ? 16 * s2rb - s1[2] * s1[0] : 0);
-  cov[1] = ref == 0 ? 16 * s2rg - s1[0] * s1[1] : (ref == 2 ? 16 * s2gb - s1[2] * s1[1] : 0);
-  cov[2] = ref == 0 ? 16 * s2rb - s1[0] * s1[2] : (ref == 1 ? 16 * s2gb - s1[1] * s1[2] : 0);
-  int e0[3], e1[3];
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    bool flip = (c != ref) && cov[c] < 0;
-    e0[c] = flip ? lo[c] : hi[c];
-    e1[c] = flip ? hi[c] : lo[c];
-    int d = (hi[c] - lo[c]) >> 4;
-    if (e0[c] >= e1[c]) { e0[c] -= d; e1[c] += d; } else { e0[c] += d; e1[c] -= d; }
-  }
-  Bc1Res best = bc1_eval(tx, pack565(e0[0], e0[1], e0[2]), pack565(e1[0], e1[1], e1[2]));
-  // two least-squares refinements: weights (3,0,2,1)/3 on c0 for indices 0..3
-  for (int it = 0; it < 2; it++) {
-    if (best.c0 == best.c1) break;
-    int saa = 0, sbb = 0, sab = 0, sav[3] = {0, 0, 0}, sbv[3] = {0, 0, 0};
-#pragma unroll
-    for (int t = 0; t < 16; t++) {
-      int j = (best.idx >> (2 * t)) & 3;
-      int a = (0x1203 >> (4 * j)) & 15;  // j: 0 -> 3, 1 -> 0, 2 -> 2, 3 -> 1
-      int b = 3 - a;
-      saa += a * a; sbb += b * b; sab += a * b;
-      int v[3] = {tex_r(tx[t]), tex_g(tx[t]), tex_b(tx[t])};
-#pragma unroll
-      for (int c = 0; c < 3; c++) { sav[c] += a * v[c]; sbv[c] += b * v[c]; }
-    }
-    int det = saa * sbb - sab * sab;
-    if (det == 0) break;
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-      e0[c] = round_div_clamp255(3LL * (sbb * sav[c] - sab * sbv[c]), det);
-      e1[c] = round_div_clamp255(3LL * (saa * sbv[c] - sab * sav[c]), det);
-    }
-    Bc1Res r = bc1_eval(tx, pack565(e0[0], e0[1], e0[2]), pack565(e1[0], e1[1], e1[2]));
-    if (r.sse < best.sse) best = r; else break;
-  }
-  // +-1 neighbourhood, order: endpoint (c0, c1) x channel (R, G, B) x step (+1, -1)
-  for (int round = 0; round < 4; round++) {
-    Bc1Res nb;
-    nb.sse = 0xFFFFFFFFu;
-    bool found = false;
-#pragma unroll
-    for (int q = 0; q < 12; q++) {
-      const int ep = q / 6, c = (q / 2) % 3, sgn = q & 1;
-      const int shift = c == 0 ? 11 : (c == 1 ? 5 : 0), mask = c == 1 ? 63 : 31;
-      uint32_t cc0 = best.c0, cc1 = best.c1;
-      uint32_t cur = ep ? cc1 : cc0;
-      int v = (int)((cur >> shift) & mask) + (sgn ? -1 : 1);
-      if (v < 0 || v > mask) continue;
-      cur = (cur & ~((uint32_t)mask << shift)) | ((uint32_t)v << shift);
-      if (ep) cc1 = cur; else cc0 = cur;
-      Bc1Res r = bc1_eval(tx, cc0, cc1);
-      if (!found || r.sse < nb.sse) { nb = r; found = true; }
-    }
-    if (found && nb.sse < best.sse) best = nb; else break;
-  }
-  return best;
-}
-
-__device__ __forceinline__ uint2 bc1_bits(const Bc1Res& r) {
-  return make_uint2((uint32_t)r.c0 | ((uint32_t)r.c1 << 16), r.idx);
-}
-
-__device__ __forceinline__ uint32_t sse_zero(const uint32_t (&tx)[16]) {
-  uint32_t s = 0;
-#pragma unroll
-  for (int t = 0; t < 16; t++) {
-    int dr = tex_r(tx[t]) - 128, dg = tex_g(tx[t]) - 128, db = tex_b(tx[t]) - 128;
-    s += dr * dr + dg * dg + db * db;
-  }
-  return s;
 }
 
 __global__ void __launch_bounds__(STAGE_THREADS) k_bc1_groups(const float* __restrict__ sh,

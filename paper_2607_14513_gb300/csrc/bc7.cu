@@ -13,6 +13,7 @@
 // error, first on ties) scores the subset. The block takes the first candidate of
 // least total error; the winner is solved again, anchors are fixed losslessly by
 // swapping endpoints and inverting indices, and the fields are packed LSB first.
+#include "bc1_dev.cuh"
 #include "bc7_tables.h"
 #include "gsc_internal.cuh"
 #include "stage.cuh"
@@ -53,6 +54,10 @@ cudaError_t bc7_init_tables() {
     }
   }
   cudaError_t e;
+  uint16_t t5[256], t6[256];
+  bc1_const_tables(t5, t6);
+  if ((e = cudaMemcpyToSymbol(c_const5, t5, sizeof(t5))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_const6, t6, sizeof(t6))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_part2, p2, sizeof(p2))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_part3, p3, sizeof(p3))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_anc2, a2, sizeof(a2))) != cudaSuccess) return e;
@@ -531,5 +536,73 @@ cudaError_t launch_bc7_blocks(const uint8_t* tex, int64_t nblk, uint8_t* out, ui
   if (nblk <= 0) return cudaSuccess;
   gsc_count_launch(); k_bc7<<<grid_for7(nblk, STAGE_THREADS), STAGE_THREADS, 0, st>>>(nullptr, nullptr, nullptr, 0, tex, nblk,
                                                                 reinterpret_cast<uint4*>(out), nullptr, sse);
+  return cudaGetLastError();
+}
+
+// ---- persistent multi-scene encode -----------------------------------------------------------
+// Tiles are claimed round robin (schedule 0) or from an atomic work queue (1, and 2 when the
+// host listed the scenes by decreasing cost); a tile finds its scene by binary search over
+// the scene list. Each tile stages 8 groups at a time and codes them BC1 (kind 1) or BC7
+// (kind 7); a scene that needs both codings is listed twice. The bits equal the single-scene
+// kernels'.
+__global__ void __launch_bounds__(STAGE_THREADS, 4) k_batch(const BatchSceneDev* __restrict__ scenes, int n_scenes,
+                                                            int64_t n_tiles, int schedule, int* __restrict__ counter) {
+  __shared__ uint32_t tex[16][STAGE_STRIDE];
+  __shared__ float s_scale[16];
+  __shared__ uint16_t sq[12 * 256];
+  __shared__ long long s_tile;
+  for (int i = threadIdx.x; i < 12 * 256; i += blockDim.x) sq[i] = (&g_qtab[0][0])[i];
+  for (int64_t it = 0;; it++) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_tile = schedule == 0 ? (long long)(blockIdx.x + it * gridDim.x) : (long long)atomicAdd(counter, 1);
+    __syncthreads();
+    const int64_t ti = s_tile;
+    if (ti >= n_tiles) break;
+    int lo = 0, hi = n_scenes - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (scenes[mid].tile0 <= ti) lo = mid; else hi = mid - 1;
+    }
+    const BatchSceneDev& S = scenes[lo];
+    const int64_t gbeg = (ti - S.tile0) * S.tile_groups;
+    const int64_t gend = min(gbeg + (int64_t)S.tile_groups, S.work_groups);
+    if (threadIdx.x < 16) s_scale[threadIdx.x] = S.scales[threadIdx.x];
+    __syncthreads();
+    for (int64_t g0 = gbeg; g0 < gend; g0 += STAGE_GROUPS) {
+      stage_groups(S.sh, S.perm, s_scale, g0, S.n_groups, tex);
+      __syncthreads();
+      const int64_t blk = g0 * 16 + threadIdx.x;
+      if (blk < S.n_groups * 16) {
+        if (S.kind == 1) {
+          uint32_t tx[16];
+#pragma unroll
+          for (int t = 0; t < 16; t++) tx[t] = tex[t][threadIdx.x];
+          const Bc1Res r = bc1_encode(tx);
+          reinterpret_cast<uint2*>(S.b1)[blk] = bc1_bits(r);
+          if (S.sse1) S.sse1[blk] = r.sse;
+          if (S.sse0) S.sse0[blk] = sse_zero(tx);
+        } else {
+          uint32_t best;
+          const uint32_t* my = &tex[0][threadIdx.x];
+          const int e = search_best(my, &best, sq);
+          reinterpret_cast<uint4*>(S.b7)[blk] = solve_pack(my, e, sq);
+          if (S.sse7) S.sse7[blk] = best;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+cudaError_t launch_batch_encode(const BatchSceneDev* scenes, int n_scenes, int64_t n_tiles, int schedule,
+                                int ctas_per_sm, int sm_count, int* counter, cudaStream_t st) {
+  if (n_tiles <= 0 || n_scenes <= 0) return cudaSuccess;
+  int64_t grid = (int64_t)(sm_count > 0 ? sm_count : 152) * (ctas_per_sm > 0 ? ctas_per_sm : 4);
+  if (grid > n_tiles) grid = n_tiles;
+  if (schedule != 0) {
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+  }
+  gsc_count_launch(); k_batch<<<(int)grid, STAGE_THREADS, 0, st>>>(scenes, n_scenes, n_tiles, schedule, counter);
   return cudaGetLastError();
 }

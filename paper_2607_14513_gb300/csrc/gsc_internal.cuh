@@ -9,7 +9,7 @@
 #define GSC_SH 16
 #define GSC_MODES 14
 
-enum { T_PLAN = 0, T_BC1, T_BC7, T_RATE, T_DECODE, T_EVAL, T_TEX, T_EVAL_TEX, T_COUNT };
+enum { T_PLAN = 0, T_BC1, T_BC7, T_RATE, T_DECODE, T_EVAL, T_TEX, T_EVAL_TEX, T_BATCH, T_COUNT };
 
 struct gsc_timer_rec { int id; cudaEvent_t a, b; };
 
@@ -79,7 +79,12 @@ struct Carve {
     off += sizeof(T) * (size_t)(count > 0 ? count : 1);
     return p;
   }
+  bool ok() const { return off <= cap; }
 };
+
+// A context on `device`; init_tables = false skips the constant tables (already loaded by an
+// earlier context in this process), as the request loop's per-slot contexts do.
+gsc_status ctx_new(int device, bool init_tables, gsc_ctx** out);
 
 // ---- launchers implemented by the translation units ------------------------------
 // plan.cu
@@ -109,9 +114,31 @@ cudaError_t bc7_init_tables();
 cudaError_t launch_bc7_groups(const float* sh, const int32_t* perm, const float* scales, int64_t n_groups,
                               uint8_t* blocks, uint32_t* sse7, cudaStream_t st);
 cudaError_t launch_bc7_blocks(const uint8_t* tex, int64_t nblk, uint8_t* out, uint64_t* sse, cudaStream_t st);
+// Persistent multi-scene encode. Scenes are listed in schedule order; scene i owns tiles
+// [tile0, tile0 + n_tiles) of tile_groups groups each (a multiple of 8) over its first
+// work_groups groups, coded BC1 (kind 1, optionally with the per-block errors of BC1 and of
+// the zero coding that the rate control needs) or BC7 (kind 7, optionally with its errors).
+struct BatchSceneDev {
+  const float* sh;
+  const int32_t* perm;
+  const float* scales;
+  int64_t n_groups, work_groups;
+  int64_t tile0, n_tiles;
+  int32_t kind, tile_groups;
+  uint8_t* b1;
+  uint8_t* b7;
+  uint32_t *sse1, *sse7, *sse0;
+};
+cudaError_t launch_batch_encode(const BatchSceneDev* scenes, int n_scenes, int64_t n_tiles, int schedule,
+                                int ctas_per_sm, int sm_count, int* counter, cudaStream_t st);
 
 // rate.cu
 size_t rate_ws_bytes(int64_t n_groups);
+size_t rate_select_ws_bytes(int64_t n_groups);
+gsc_status rate_select(gsc_ctx* ctx, int64_t n, const int32_t* perm, const float* scales, uint32_t target_x4,
+                       const uint8_t* b1, const uint8_t* b7, const uint32_t* sse1, const uint32_t* sse7,
+                       const uint32_t* sse0, uint8_t* blocks, int32_t* perm_out, gsc_stream_table* table, void* ws,
+                       size_t ws_bytes, cudaStream_t st);
 gsc_status rate_run(gsc_ctx* ctx, const float* sh, int64_t n, const int32_t* perm, const float* scales,
                     uint32_t target_x4, uint8_t* blocks, int32_t* perm_out, gsc_stream_table* table, void* ws,
                     size_t ws_bytes, uint8_t* bc1_all, uint8_t* bc7_all, cudaStream_t st);
@@ -127,6 +154,8 @@ struct DevTable {
   int64_t first_group[GSC_MODES], stream_groups[GSC_MODES], byte_offset[GSC_MODES];
   float scales[GSC_SH];
 };
+// Band weights of the rate-distortion objective from the 16 scales (fp64, Sec. IV-B).
+void host_weights(const float* scales, uint32_t* w);
 gsc_status make_dev_table(const gsc_stream_table* t, DevTable* d);
 cudaError_t launch_decode(const DevTable& t, const uint8_t* blocks, const int32_t* perm, uint8_t* texels,
                           cudaStream_t st);

@@ -281,39 +281,20 @@ __global__ void k_assemble(const uint64_t* __restrict__ keys, const uint32_t* __
   }
 }
 
-size_t rate_ws_bytes(int64_t ng) {
-  const int64_t nb = ng * 16;
-  size_t b = 0;
-  b += align_up(8 * (size_t)nb, 256) + align_up(16 * (size_t)nb, 256);        // BC1, BC7 blocks
-  b += 3 * align_up(4 * (size_t)nb, 256);                                     // sse1, sse7, sse0
-  b += align_up(8 * (size_t)ng * GSC_MODES, 256);                             // D
-  b += align_up(8 * (size_t)ng * GSC_MODES, 256) + align_up((size_t)ng * GSC_MODES, 256);  // steps
-  b += 3 * align_up((size_t)ng, 256);                                         // n_steps, mode, alt
-  b += 2 * align_up(8 * (size_t)ng, 256);                                     // delta, prefix
-  b += align_up(8 * (size_t)ng, 256) + align_up(4 * (size_t)ng, 256);         // keys, vals
-  b += align_up(sizeof(RateState), 256) + align_up(sizeof(StreamInfo), 256) + align_up(64, 256);
-  b += radix_ws_bytes(ng) + scan_ws_bytes(ng);
-  return b + 8192;
-}
-
 static int gsz(int64_t n, int threads, int cap) {
   int64_t g = ceil_div64(n > 0 ? n : 1, threads);
   return (int)(g > cap ? cap : g);
 }
 
-gsc_status rate_run(gsc_ctx* ctx, const float* sh, int64_t n, const int32_t* perm, const float* scales,
-                    uint32_t target_x4, uint8_t* blocks, int32_t* perm_out, gsc_stream_table* table, void* ws,
-                    size_t ws_bytes, uint8_t* bc1_all, uint8_t* bc7_all, cudaStream_t st) {
+// Stream selection from the per-block codings and errors of every block: D table,
+// lambda search, fill, stable partition, assembly; fills *table (synchronises st).
+gsc_status rate_select(gsc_ctx* ctx, int64_t n, const int32_t* perm, const float* scales, uint32_t target_x4,
+                       const uint8_t* b1, const uint8_t* b7, const uint32_t* sse1, const uint32_t* sse7,
+                       const uint32_t* sse0, uint8_t* blocks, int32_t* perm_out, gsc_stream_table* table, void* ws,
+                       size_t ws_bytes, cudaStream_t st) {
   const int64_t ng = ceil_div64(n, 16);
-  if (ws_bytes < rate_ws_bytes(ng)) return GSC_ERR_OOM;
+  if (ws_bytes < rate_select_ws_bytes(ng)) return GSC_ERR_OOM;
   Carve c{reinterpret_cast<uint8_t*>(ws), 0, ws_bytes};
-  uint8_t* b1 = c.take<uint8_t>(8 * ng * 16);
-  uint8_t* b7 = c.take<uint8_t>(16 * ng * 16);
-  if (bc1_all) b1 = bc1_all;   // the caller keeps the all-BC1 / all-BC7 codings
-  if (bc7_all) b7 = bc7_all;
-  uint32_t* sse1 = c.take<uint32_t>(ng * 16);
-  uint32_t* sse7 = c.take<uint32_t>(ng * 16);
-  uint32_t* sse0 = c.take<uint32_t>(ng * 16);
   uint64_t* dtab = c.take<uint64_t>(ng * GSC_MODES);
   uint64_t* step_l = c.take<uint64_t>(ng * GSC_MODES);
   uint8_t* step_m = c.take<uint8_t>(ng * GSC_MODES);
@@ -331,18 +312,9 @@ gsc_status rate_run(gsc_ctx* ctx, const float* sh, int64_t n, const int32_t* per
   void* sws = c.take<uint8_t>((int64_t)scan_ws_bytes(ng));
   const uint64_t budget = (uint64_t)target_x4 * 4ull * (uint64_t)n;
   const int cap = ctx->sm_count * 8;
-
+  GscTimed tm_rate(ctx, T_RATE, st);
   GSC_CUDA(cudaMemsetAsync(S, 0, sizeof(RateState), st));
   gsc_count_launch(); k_weights<<<1, 32, 0, st>>>(scales, w);
-  {
-    GscTimed tm(ctx, T_BC1, st);
-    GSC_CUDA(launch_bc1_groups(sh, perm, scales, ng, b1, sse1, sse0, st));
-  }
-  {
-    GscTimed tm(ctx, T_BC7, st);
-    GSC_CUDA(launch_bc7_groups(sh, perm, scales, ng, b7, sse7, st));
-  }
-  GscTimed tm_rate(ctx, T_RATE, st);
   gsc_count_launch(); k_dtable<<<gsz(ng, 128, cap), 128, 0, st>>>(sse1, sse7, sse0, w, ng, dtab, step_l, step_m, n_steps, S);
   gsc_count_launch(); k_search_init<<<1, 32, 0, st>>>(S, budget);
   for (int p = 0; p < N_PASSES; p++) {
@@ -382,4 +354,48 @@ gsc_status rate_run(gsc_ctx* ctx, const float* sh, int64_t n, const int32_t* per
     table->s[m].byte_offset = h->offset[m];
   }
   return GSC_OK;
+}
+
+size_t rate_select_ws_bytes(int64_t ng) {
+  size_t b = 0;
+  b += align_up(8 * (size_t)ng * GSC_MODES, 256);                             // D
+  b += align_up(8 * (size_t)ng * GSC_MODES, 256) + align_up((size_t)ng * GSC_MODES, 256);  // steps
+  b += 3 * align_up((size_t)ng, 256);                                         // n_steps, mode, alt
+  b += 2 * align_up(8 * (size_t)ng, 256);                                     // delta, prefix
+  b += align_up(8 * (size_t)ng, 256) + align_up(4 * (size_t)ng, 256);         // keys, vals
+  b += align_up(sizeof(RateState), 256) + align_up(sizeof(StreamInfo), 256) + align_up(64, 256);
+  b += radix_ws_bytes(ng) + scan_ws_bytes(ng);
+  return b + 8192;
+}
+
+gsc_status rate_run(gsc_ctx* ctx, const float* sh, int64_t n, const int32_t* perm, const float* scales,
+                    uint32_t target_x4, uint8_t* blocks, int32_t* perm_out, gsc_stream_table* table, void* ws,
+                    size_t ws_bytes, uint8_t* bc1_all, uint8_t* bc7_all, cudaStream_t st) {
+  const int64_t ng = ceil_div64(n, 16);
+  if (ws_bytes < rate_ws_bytes(ng)) return GSC_ERR_OOM;
+  Carve c{reinterpret_cast<uint8_t*>(ws), 0, ws_bytes};
+  uint8_t* b1 = c.take<uint8_t>(8 * ng * 16);
+  uint8_t* b7 = c.take<uint8_t>(16 * ng * 16);
+  if (bc1_all) b1 = bc1_all;   // the caller keeps the all-BC1 / all-BC7 codings
+  if (bc7_all) b7 = bc7_all;
+  uint32_t* sse1 = c.take<uint32_t>(ng * 16);
+  uint32_t* sse7 = c.take<uint32_t>(ng * 16);
+  uint32_t* sse0 = c.take<uint32_t>(ng * 16);
+  const size_t used = align_up(c.off, 256);
+  {
+    GscTimed tm(ctx, T_BC1, st);
+    GSC_CUDA(launch_bc1_groups(sh, perm, scales, ng, b1, sse1, sse0, st));
+  }
+  {
+    GscTimed tm(ctx, T_BC7, st);
+    GSC_CUDA(launch_bc7_groups(sh, perm, scales, ng, b7, sse7, st));
+  }
+  return rate_select(ctx, n, perm, scales, target_x4, b1, b7, sse1, sse7, sse0, blocks, perm_out, table,
+                     reinterpret_cast<uint8_t*>(ws) + used, ws_bytes - used, st);
+}
+
+size_t rate_ws_bytes(int64_t ng) {
+  const int64_t nb = ng * 16;
+  return align_up(8 * (size_t)nb, 256) + align_up(16 * (size_t)nb, 256) + 3 * align_up(4 * (size_t)nb, 256) + 1024 +
+         rate_select_ws_bytes(ng);
 }

@@ -53,6 +53,55 @@ class StreamTable(C.Structure):
                      n_groups=self.s[i].n_groups, byte_offset=self.s[i].byte_offset) for i in range(self.n_streams)]
 
 
+class BatchScene(C.Structure):
+    _fields_ = [("d_pos", C.c_void_p), ("d_sh", C.c_void_p), ("n", C.c_int64), ("group_size", C.c_int64),
+                ("sort", C.c_int32), ("format", C.c_int32), ("target_bpt_x4", C.c_uint32), ("d_perm", C.c_void_p),
+                ("d_scales", C.c_void_p), ("d_blocks", C.c_void_p), ("d_perm_out", C.c_void_p),
+                ("table", StreamTable)]
+
+
+class BatchTuning(C.Structure):
+    _fields_ = [("schedule", C.c_int32), ("ctas_per_sm", C.c_int32), ("bc1_tile_groups", C.c_int32)]
+
+
+REQ_ENCODE, REQ_EVAL = 0, 1
+
+
+class ServerParams(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_uint64), ("n_slots", C.c_int32), ("merge", C.c_int32),
+                ("max_views", C.c_int32), ("priority", C.c_int32), ("hold_us", C.c_int64)]
+
+
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("scene", C.c_int32), ("pos", C.c_void_p), ("sh", C.c_void_p),
+                ("n", C.c_int64), ("format", C.c_int32), ("target_bpt_x4", C.c_uint32), ("group_size", C.c_int64),
+                ("sort", C.c_int32), ("V", C.c_int32), ("dirs", C.c_void_p), ("cams", C.c_void_p),
+                ("out_order", C.c_int32), ("out", C.c_void_p)]
+
+
+class RequestResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("kind", C.c_int32), ("scene", C.c_int32), ("merged", C.c_int32),
+                ("n", C.c_int64), ("t_submit_ms", C.c_double), ("t_admit_ms", C.c_double), ("t_done_ms", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("done", C.c_uint64), ("failed", C.c_uint64), ("merged", C.c_uint64),
+                ("evictions", C.c_uint64), ("resident_bytes", C.c_uint64), ("used_bytes", C.c_uint64),
+                ("peak_bytes", C.c_uint64), ("queued", C.c_int32), ("resident_versions", C.c_int32)]
+
+
+class SimRequest(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("scene", C.c_int32), ("n", C.c_int64), ("format", C.c_int32),
+                ("target_bpt_x4", C.c_uint32), ("V", C.c_int32), ("out_order", C.c_int32), ("cams", C.c_int32),
+                ("out_device", C.c_int32), ("host_input", C.c_int32), ("t_arrival_ms", C.c_double),
+                ("service_ms", C.c_double)]
+
+
+class SimResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("merged", C.c_int32), ("evictions", C.c_int32), ("pad", C.c_int32),
+                ("t_admit_ms", C.c_double), ("t_done_ms", C.c_double), ("used_bytes_at_admit", C.c_uint64)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -77,6 +126,24 @@ _SIGS = {
     "gsc_encode_blocks": [_P, _P, C.c_int64, C.c_int32, _P, _P, _P],
     "gsc_decode_blocks": [_P, _P, C.c_int64, C.c_int32, _P, _P],
     "gsc_decode_blocks_tex": [_P, _P, C.c_int64, C.c_int32, _P, _P],
+    "gsc_batch_workspace_bytes": [C.POINTER(BatchScene), C.c_int32],
+    "gsc_batch_encode": [_P, C.POINTER(BatchScene), C.c_int32, C.POINTER(BatchTuning), _P, C.c_size_t, _P],
+    "gsc_batch_autotune": [_P, C.POINTER(BatchScene), C.c_int32, C.POINTER(BatchTuning), C.POINTER(C.c_double), _P,
+                           C.c_size_t, _P],
+    "gsc_batch_eval_graph": [_P, C.POINTER(BatchScene), C.c_int32, _P, C.c_int32, C.c_int32, C.POINTER(C.c_void_p),
+                             C.POINTER(C.c_void_p), _P],
+    "gsc_graph_launch": [_P, _P],
+    "gsc_graph_destroy": [_P],
+    "gsc_server_create": [_P, C.POINTER(ServerParams), C.POINTER(C.c_void_p)],
+    "gsc_server_submit": [_P, C.POINTER(Request), C.POINTER(C.c_uint64)],
+    "gsc_server_wait": [_P, C.c_uint64, C.c_int64, C.POINTER(RequestResult)],
+    "gsc_server_drain": [_P, C.c_int64],
+    "gsc_server_read_scene": [_P, C.c_int32, C.POINTER(StreamTable), _P, C.c_size_t, _P, C.c_size_t],
+    "gsc_server_evict": [_P, C.c_int32],
+    "gsc_server_get_stats": [_P, C.POINTER(ServerStats)],
+    "gsc_server_destroy": [_P],
+    "gsc_server_simulate": [C.POINTER(ServerParams), C.POINTER(SimRequest), C.c_int32, C.POINTER(SimResult),
+                            C.POINTER(C.c_uint64)],
     "gsc_launch_count": [],
     "gsc_probe_int_peak": [_P, C.POINTER(C.c_double), _P],
     "gsc_ctx_set_timing": [_P, C.c_int],
@@ -107,6 +174,7 @@ def load(path: str | None = None):
             lib.gsc_status_string.restype = C.c_char_p
             lib.gsc_workspace_bytes.restype = C.c_size_t
             lib.gsc_launch_count.restype = C.c_uint64
+            lib.gsc_batch_workspace_bytes.restype = C.c_size_t
             _lib = lib
     return _lib
 
@@ -120,6 +188,10 @@ def _ptr(t):
     if t is None:
         return None
     return C.c_void_p(t.data_ptr())
+
+
+def _addr(t):
+    return None if t is None else t.data_ptr()
 
 
 def _stream(stream):
@@ -330,3 +402,156 @@ def gsc_decode_blocks_tex(ctx, blocks, fmt, stream=None):
     _check(ctx.lib.gsc_decode_blocks_tex(ctx.h, _ptr(blocks.contiguous()), nb, fmt, _ptr(rgba), _stream(stream)),
            "gsc_decode_blocks_tex")
     return rgba
+
+
+class Batch:
+    """Many scenes coded through one persistent launch (gsc_batch_*). Holds the device
+    buffers of every scene; `scenes` are (pos, sh, format, target_x4) device tensors."""
+
+    def __init__(self, ctx, scenes, group_size=4096, sort=1):
+        import torch
+        self.ctx = ctx
+        n = len(scenes)
+        self.arr = (BatchScene * n)()
+        self.keep = []
+        for i, (pos, sh, fmt, t4) in enumerate(scenes):
+            m = sh.shape[0]
+            ng = (m + 15) // 16
+            perm = torch.empty(max(ng * 16, 1), dtype=torch.int32, device=sh.device)
+            scales = torch.empty(16, dtype=torch.float32, device=sh.device)
+            blocks = torch.empty(max(ng * 256, 16), dtype=torch.uint8, device=sh.device)
+            perm_out = torch.empty(max(ng * 16, 1), dtype=torch.int32, device=sh.device)
+            self.keep.append((pos, sh, perm, scales, blocks, perm_out))
+            self.arr[i] = BatchScene(_ptr(pos), _ptr(sh), m, group_size, sort, fmt, t4, _ptr(perm), _ptr(scales),
+                                     _ptr(blocks), _ptr(perm_out), StreamTable())
+        nb = ctx.lib.gsc_batch_workspace_bytes(self.arr, n)
+        if nb == 0:
+            raise GscError(1, "gsc_batch_workspace_bytes")
+        self.ws = torch.empty(int(nb), dtype=torch.uint8, device="cuda:%d" % ctx.device)
+        self.n = n
+
+    def autotune(self, stream=None):
+        t = BatchTuning()
+        ms = C.c_double(0.0)
+        _check(self.ctx.lib.gsc_batch_autotune(self.ctx.h, self.arr, self.n, C.byref(t), C.byref(ms), _ptr(self.ws),
+                                               self.ws.numel(), _stream(stream)), "gsc_batch_autotune")
+        return t, ms.value
+
+    def encode(self, tuning, stream=None):
+        _check(self.ctx.lib.gsc_batch_encode(self.ctx.h, self.arr, self.n, C.byref(tuning), _ptr(self.ws),
+                                             self.ws.numel(), _stream(stream)), "gsc_batch_encode")
+
+    def result(self, i):
+        """(perm, scales, blocks, perm_out, table) of scene i."""
+        pos, sh, perm, scales, blocks, perm_out = self.keep[i]
+        t = self.arr[i].table
+        return perm, scales, blocks[:t.total_bytes], perm_out[:t.n_groups * 16], t
+
+    def eval_graph(self, cams, outs, out_order=OUT_GAUSS_MAJOR, stream=None):
+        ptrs = (C.c_void_p * self.n)(*[o.data_ptr() for o in outs])
+        g = C.c_void_p()
+        _check(self.ctx.lib.gsc_batch_eval_graph(self.ctx.h, self.arr, self.n, _ptr(cams), cams.shape[0], out_order,
+                                                 ptrs, C.byref(g), _stream(stream)), "gsc_batch_eval_graph")
+        return Graph(self.ctx, g)
+
+
+class Graph:
+    def __init__(self, ctx, h):
+        self.ctx = ctx
+        self.h = h
+
+    def launch(self, stream=None):
+        _check(self.ctx.lib.gsc_graph_launch(self.h, _stream(stream)), "gsc_graph_launch")
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.gsc_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def simulate(params, reqs):
+    """Runs the request loop's admission policy on the host over a trace of SimRequest."""
+    lib = load()
+    n = len(reqs)
+    arr = (SimRequest * max(n, 1))(*reqs)
+    res = (SimResult * max(n, 1))()
+    peak = C.c_uint64(0)
+    _check(lib.gsc_server_simulate(C.byref(params), arr, n, res, C.byref(peak)), "gsc_server_simulate")
+    return list(res)[:n], peak.value
+
+
+class Server:
+    """The request loop (gsc_server_*). Tensors passed to submit() must stay alive until the
+    request completes; the object keeps a reference to them until wait() returns."""
+
+    def __init__(self, ctx, budget_bytes, n_slots=4, merge=True, max_views=64, priority=True, hold_us=200_000):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self.params = ServerParams(int(budget_bytes), n_slots, int(merge), max_views, int(priority), hold_us)
+        h = C.c_void_p()
+        _check(self.lib.gsc_server_create(ctx.h, C.byref(self.params), C.byref(h)), "gsc_server_create")
+        self.h = h
+        self.keep = {}
+
+    def encode(self, scene, pos, sh, fmt, target_x4=0, group_size=4096, sort=1):
+        r = Request(REQ_ENCODE, scene, _addr(pos), _addr(sh), sh.shape[0], fmt, target_x4, group_size, sort, 0,
+                    None, None, 0, None)
+        return self._submit(r, (pos, sh))
+
+    def eval(self, scene, n, out, dirs=None, cams=None, out_order=OUT_GAUSS_MAJOR):
+        src = dirs if dirs is not None else cams
+        r = Request(REQ_EVAL, scene, None, None, n, 0, 0, 0, 0, src.shape[0], _addr(dirs), _addr(cams), out_order,
+                    _addr(out))
+        return self._submit(r, (src, out))
+
+    def _submit(self, r, refs):
+        t = C.c_uint64(0)
+        _check(self.lib.gsc_server_submit(self.h, C.byref(r), C.byref(t)), "gsc_server_submit")
+        self.keep[t.value] = refs
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        res = RequestResult()
+        _check(self.lib.gsc_server_wait(self.h, ticket, timeout_ms, C.byref(res)), "gsc_server_wait")
+        self.keep.pop(ticket, None)
+        return res
+
+    def drain(self, timeout_ms=-1):
+        _check(self.lib.gsc_server_drain(self.h, timeout_ms), "gsc_server_drain")
+
+    def read_scene(self, scene):
+        """(table, blocks uint8, perm int32) of a resident scene, as host tensors."""
+        import torch
+        t = StreamTable()
+        _check(self.lib.gsc_server_read_scene(self.h, scene, C.byref(t), None, 0, None, 0), "gsc_server_read_scene")
+        blocks = torch.empty(max(t.total_bytes, 1), dtype=torch.uint8)
+        perm = torch.empty(max(t.n_groups * 16, 1), dtype=torch.int32)
+        _check(self.lib.gsc_server_read_scene(self.h, scene, C.byref(t), _ptr(blocks), blocks.numel(), _ptr(perm),
+                                              4 * perm.numel()), "gsc_server_read_scene")
+        return t, blocks[:t.total_bytes], perm[:t.n_groups * 16]
+
+    def evict(self, scene):
+        _check(self.lib.gsc_server_evict(self.h, scene), "gsc_server_evict")
+
+    def stats(self):
+        st = ServerStats()
+        _check(self.lib.gsc_server_get_stats(self.h, C.byref(st)), "gsc_server_get_stats")
+        return st
+
+    def close(self):
+        if self.h:
+            self.lib.gsc_server_destroy(self.h)
+            self.h = None
+            self.keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

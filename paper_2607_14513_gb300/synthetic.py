@@ -81,3 +81,41 @@ def batch_sizes(n_scenes: int, seed: int, lo: int, hi: int) -> np.ndarray:
     """Scene sizes log-uniform in [lo, hi] (batched and served workloads)."""
     rng = np.random.default_rng(seed)
     return np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_scenes)).astype(np.int64)
+
+
+# Batched workload: 64 scenes, sizes log-uniform in [50,000, 2,000,000], the scene-scale
+# value distributions; formats cycle BC1, BC7, rate-controlled, the rate targets cycle
+# 3, 4, 6, 8 bits per texel (given x4).
+BATCH = dict(n_scenes=64, seed=2000, lo=50_000, hi=2_000_000)
+
+
+def batch_mix(n_scenes: int, seed: int, lo: int, hi: int):
+    """[(n, scene seed, format name, rate target x4)] of the batched workload."""
+    sizes = batch_sizes(n_scenes, seed, lo, hi)
+    out = []
+    for i, n in enumerate(sizes):
+        fmt = ("bc1", "bc7", "rate")[i % 3]
+        out.append((int(n), seed + 1 + i, fmt, (12, 16, 24, 32)[(i // 3) % 4] if fmt == "rate" else 0))
+    return out
+
+
+# Served workload: a pool of scenes of 10,000..4,000,000 Gaussians (log-uniform), half BC1 and
+# half BC7, and a Poisson stream of requests (mean 200 per second): a re-encode of a pool scene
+# with probability encode_frac, else a decode + SH evaluation of a pool scene for 1..32 camera
+# centres (uniform).
+SERVE = dict(n_scenes=32, seed=3000, lo=10_000, hi=4_000_000, rate_hz=200.0, encode_frac=0.1)
+
+
+def serve_trace(n_scenes: int, seed: int, lo: int, hi: int, rate_hz: float, encode_frac: float, seconds: float):
+    """(pool [(n, scene seed, format name)], requests [(t_arrival_s, kind, scene, V, cams seed)])."""
+    sizes = batch_sizes(n_scenes, seed, lo, hi)
+    pool = [(int(n), seed + 1 + i, ("bc1", "bc7")[i % 2]) for i, n in enumerate(sizes)]
+    rng = np.random.default_rng(seed + 999)
+    reqs, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate_hz)
+        if t >= seconds:
+            break
+        kind = "encode" if rng.random() < encode_frac else "eval"
+        reqs.append((t, kind, int(rng.integers(n_scenes)), int(rng.integers(1, 33)), int(rng.integers(1 << 30))))
+    return pool, reqs
