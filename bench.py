@@ -426,6 +426,15 @@ def run_batch(args, world, rank, local):
     ms_step = max_over_ranks(ms_batched, world, dev)
     ms_plain = max_over_ranks(ms_plain, world, dev)
     ms_graph = timed(lambda: graph.launch(stream=stream), max(5, args.steps))
+    res_tabs = [batch.result(i) for i in range(len(mix))]
+
+    def eval_per_scene():
+        for i, (pos, _, _, _) in enumerate(scenes):
+            _, _, b, p, tab = res_tabs[i]
+            gsc.gsc_decode_eval_sh(ctx, tab, b, p, pos=pos, cams=cams, out_order=gsc.OUT_GAUSS_MAJOR, out=outs_plain[i],
+                                   stream=stream)
+
+    ms_eval_plain = timed(eval_per_scene, max(5, args.steps))
 
     # the persistent encode launch: BC7 candidate search of every BC7-searched block
     nb7 = sum(((m[0] + 15) // 16) * 16 for m in mix if m[2] != "bc1")
@@ -492,7 +501,8 @@ def run_batch(args, world, rank, local):
                                                "bc1_tile_groups": tuning.bc1_tile_groups,
                                                "proxy_ms": round(proxy_ms, 3)}},
            "roofline": roofline, "roofline_decode_eval": roofline_eval,
-           "stages": {"batch_encode_ms": round(kb_ms, 3), "eval_graph_ms": round(ms_graph, 3)},
+           "stages": {"batch_encode_ms": round(kb_ms, 3), "eval_graph_ms": round(ms_graph, 3),
+                      "eval_per_scene_ms": round(ms_eval_plain, 3)},
            "clocks": clk,
            "e2e": {"value": round(world * total_n / t_e2e / 1e6, 3), "unit": UNIT,
                    "h2d_bytes_per_step": int(total_n * (12 + 192)), "d2h_bytes_per_step": int(bo),

@@ -221,9 +221,11 @@ typedef struct {
   gsc_stream_table table;   /* out */
 } gsc_batch_scene;
 
-/* How the persistent launch hands out work: schedule 0 = static round robin over tiles,
- * 1 = atomic work queue, 2 = atomic queue over scenes ordered by decreasing cost; CTAs per
- * SM 1..4; groups per BC1 tile (multiple of 8; BC7 tiles are 8 groups). */
+/* How the encode launch hands out work: schedule 0 = static round robin over tiles, 1 = atomic
+ * work queue, 2 = atomic queue, 3 = one CTA per tile; schedules other than 1 list the scenes by
+ * decreasing cost. CTAs per SM 1..32 (schedules 0-2; above the 4 that fit, the grid is
+ * oversubscribed and the hardware block scheduler balances); groups per BC1 tile (multiple of
+ * 8; BC7 tiles are 8 groups). The plans of the scenes run on 4 streams at once. */
 typedef struct {
   int32_t schedule;
   int32_t ctas_per_sm;
@@ -233,8 +235,9 @@ typedef struct {
 size_t gsc_batch_workspace_bytes(const gsc_batch_scene* scenes, int32_t n_scenes);
 gsc_status gsc_batch_encode(gsc_ctx* ctx, gsc_batch_scene* scenes, int32_t n_scenes, const gsc_batch_tuning* tune,
                             void* d_ws, size_t ws_bytes, void* stream);
-/* Times every tuning (3 schedules x 3 occupancies x 2 BC1 tile sizes) on a 1/32-scale proxy
- * of the same batch (each scene's first groups) and returns the fastest. It writes the
+/* Times 9 tunings (work queues on resident grids, oversubscribed round robin, one CTA per
+ * tile) on a 1/8-scale proxy of the same batch (each scene's first groups) and returns the
+ * fastest. It writes the
  * scenes' plans and partial blocks (gsc_batch_encode overwrites them). */
 gsc_status gsc_batch_autotune(gsc_ctx* ctx, gsc_batch_scene* scenes, int32_t n_scenes, gsc_batch_tuning* out,
                               double* proxy_ms, void* d_ws, size_t ws_bytes, void* stream);
@@ -268,6 +271,8 @@ typedef struct {
   int32_t merge;              /* 0 or 1 */
   int32_t max_views;          /* 1..64: views of one evaluation request and of one merged launch */
   int32_t priority;           /* 1: evaluations on high-priority streams */
+  int32_t encode_slots;       /* encodes running at once, 1..n_slots (0: n_slots - 1, at least 1), so
+                               * that evaluations keep a slot while long encodes run */
   int64_t hold_us;            /* a request older than this that does not fit holds back later ones */
 } gsc_server_params;
 

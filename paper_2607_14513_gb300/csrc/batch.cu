@@ -34,6 +34,11 @@ static bool batch_args_ok(const gsc_batch_scene* sc, int n) {
 
 static int64_t groups_of(int64_t n) { return ceil_div64(n, 16); }
 
+static const int kPlanLanes = 4;
+// The autotuner's proxy: every scene's first 1/8 of the groups. Smaller proxies leave too few
+// tiles per CTA and favour launch shapes that lose at full size.
+static const int64_t kProxyDiv = 8;
+
 struct BatchLayout {
   size_t plan_ws, select_ws, per_rate, total;
 };
@@ -49,7 +54,8 @@ static BatchLayout layout(const gsc_batch_scene* sc, int n) {
     }
   }
   // the device scene list holds up to two entries per scene (a rate scene codes BC1 and BC7)
-  L.total = align_up(L.plan_ws, 256) + align_up(L.select_ws, 256) + L.per_rate +
+  L.plan_ws = align_up(L.plan_ws, 256);
+  L.total = L.plan_ws * (size_t)std::min(n, kPlanLanes) + align_up(L.select_ws, 256) + L.per_rate +
             align_up(sizeof(BatchSceneDev) * 2 * (size_t)n, 256) + 256 + 4096;
   return L;
 }
@@ -74,7 +80,7 @@ static BatchBufs carve(const gsc_batch_scene* sc, int n, void* ws) {
   const BatchLayout L = layout(sc, n);
   Carve c{reinterpret_cast<uint8_t*>(ws), 0, L.total};
   BatchBufs B;
-  B.plan_ws = c.take<uint8_t>((int64_t)L.plan_ws);
+  B.plan_ws = c.take<uint8_t>((int64_t)(L.plan_ws * (size_t)std::min(n, kPlanLanes)));
   B.select_ws = c.take<uint8_t>((int64_t)L.select_ws);
   B.d_list = c.take<BatchSceneDev>(2 * (int64_t)n);
   B.list_cap = 2 * (size_t)n;
@@ -94,22 +100,59 @@ static BatchBufs carve(const gsc_batch_scene* sc, int n, void* ws) {
   return B;
 }
 
+// The plans are short, latency-bound launch sequences with no host synchronisation: run them
+// on kPlanLanes streams at once (each with its own workspace), forked from and joined back
+// into the caller's stream; scenes go to the lane with the least work so far.
 static gsc_status run_plans(gsc_ctx* c, gsc_batch_scene* sc, int n, const BatchBufs& B, cudaStream_t st) {
-  for (int i = 0; i < n; i++) {
-    gsc_plan_params pp;
-    pp.n = sc[i].n;
-    pp.group_size = sc[i].group_size;
-    pp.sort = sc[i].sort;
-    pp.quantile_permille = 995;
-    gsc_status s = plan_run(c, sc[i].d_pos, sc[i].d_sh, &pp, sc[i].d_perm, sc[i].d_scales, B.plan_ws,
-                            layout(sc, n).plan_ws, st);
-    if (s != GSC_OK) return s;
+  const int lanes = std::min(n, kPlanLanes);
+  const size_t pws = layout(sc, n).plan_ws;
+  cudaStream_t ls[kPlanLanes] = {};
+  cudaEvent_t fork = nullptr, join[kPlanLanes] = {};
+  gsc_status s = GSC_OK;
+  cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  for (int l = 0; l < lanes && e == cudaSuccess; l++) {
+    e = cudaStreamCreateWithFlags(&ls[l], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[l], cudaEventDisableTiming);
   }
-  return GSC_OK;
+  if (e == cudaSuccess) e = cudaEventRecord(fork, st);
+  for (int l = 0; l < lanes && e == cudaSuccess; l++) e = cudaStreamWaitEvent(ls[l], fork, 0);
+  if (e == cudaSuccess) {
+    std::vector<int> order(n);
+    for (int i = 0; i < n; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sc[a].n > sc[b].n; });
+    int64_t load[kPlanLanes] = {};
+    for (int i : order) {
+      int l = 0;
+      for (int k = 1; k < lanes; k++) if (load[k] < load[l]) l = k;
+      load[l] += sc[i].n + 20000;  // a plan's fixed launch cost counts like ~20k Gaussians
+      gsc_plan_params pp;
+      pp.n = sc[i].n;
+      pp.group_size = sc[i].group_size;
+      pp.sort = sc[i].sort;
+      pp.quantile_permille = 995;
+      s = plan_run(c, sc[i].d_pos, sc[i].d_sh, &pp, sc[i].d_perm, sc[i].d_scales,
+                   static_cast<uint8_t*>(B.plan_ws) + (size_t)l * pws, pws, ls[l]);
+      if (s != GSC_OK) break;
+    }
+  }
+  for (int l = 0; l < lanes; l++) {
+    if (ls[l] && join[l]) {
+      if (e == cudaSuccess) e = cudaEventRecord(join[l], ls[l]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join[l], 0);
+    }
+  }
+  for (int l = 0; l < lanes; l++) {
+    if (join[l]) cudaEventDestroy(join[l]);
+    if (ls[l]) cudaStreamDestroy(ls[l]);
+  }
+  if (fork) cudaEventDestroy(fork);
+  if (e != cudaSuccess) { cudaGetLastError(); return GSC_ERR_CUDA; }
+  return s;
 }
 
 // Scene list in schedule order with tile ranges; work_div shrinks every scene's work
 // (the autotuner's proxy), 1 = the real batch.
+// n_tiles[0] / [1]: tiles of the BC7 and of the BC1 entries.
 static std::vector<BatchSceneDev> scene_list(const gsc_batch_scene* sc, int n, const BatchBufs& B,
                                              const gsc_batch_tuning& tune, int64_t work_div, int64_t* n_tiles) {
   std::vector<BatchSceneDev> v;
@@ -144,31 +187,41 @@ static std::vector<BatchSceneDev> scene_list(const gsc_batch_scene* sc, int n, c
       v.push_back(e);
     }
   }
-  if (tune.schedule == 2) {
-    // decreasing cost: a BC7 block costs ~40 BC1 blocks
-    auto cost = [](const BatchSceneDev& d) { return d.work_groups * (d.kind == 1 ? 1 : 40); };
-    std::stable_sort(v.begin(), v.end(), [&](const BatchSceneDev& a, const BatchSceneDev& b) { return cost(a) > cost(b); });
+  // BC7 entries first, then BC1 entries (one launch each); within a kind, schedules other than
+  // the plain work queue list the scenes by decreasing size
+  std::stable_sort(v.begin(), v.end(), [&](const BatchSceneDev& a, const BatchSceneDev& b) {
+    if (a.kind != b.kind) return a.kind > b.kind;
+    return tune.schedule != 1 && a.work_groups > b.work_groups;
+  });
+  int64_t t7 = 0, t1 = 0;
+  for (auto& d : v) {
+    int64_t& t = d.kind == 7 ? t7 : t1;
+    d.tile0 = t;
+    t += d.n_tiles;
   }
-  int64_t t = 0;
-  for (auto& d : v) { d.tile0 = t; t += d.n_tiles; }
-  *n_tiles = t;
+  n_tiles[0] = t7;
+  n_tiles[1] = t1;
   return v;
 }
 
-static gsc_status launch_list(gsc_ctx* c, const std::vector<BatchSceneDev>& v, int64_t n_tiles, const BatchBufs& B,
-                              const gsc_batch_tuning& tune, cudaStream_t st) {
+static gsc_status launch_list(gsc_ctx* c, const std::vector<BatchSceneDev>& v, const int64_t* n_tiles,
+                              const BatchBufs& B, const gsc_batch_tuning& tune, cudaStream_t st) {
   if (v.empty()) return GSC_OK;
   if (v.size() > B.list_cap) return GSC_ERR_INVALID_ARG;
-  if (n_tiles >= (int64_t)0x7F000000) return GSC_ERR_INVALID_ARG;  // the work queue counts tiles in 32 bits
+  if (n_tiles[0] >= (int64_t)0x7F000000 || n_tiles[1] >= (int64_t)0x7F000000) return GSC_ERR_INVALID_ARG;
+  int n7 = 0;
+  while (n7 < (int)v.size() && v[n7].kind == 7) n7++;
+  // a pageable source: the copy is staged before cudaMemcpyAsync returns
   GSC_CUDA(cudaMemcpyAsync(B.d_list, v.data(), sizeof(BatchSceneDev) * v.size(), cudaMemcpyHostToDevice, st));
-  GSC_CUDA(launch_batch_encode(B.d_list, (int)v.size(), n_tiles, tune.schedule, tune.ctas_per_sm, c->sm_count,
-                               B.counter, st));
-  // the host list must outlive the copy: pageable source, so the copy is staged before return
+  GSC_CUDA(launch_batch_encode(7, B.d_list, n7, n_tiles[0], tune.schedule, tune.ctas_per_sm, c->sm_count, B.counter,
+                               st));
+  GSC_CUDA(launch_batch_encode(1, B.d_list + n7, (int)v.size() - n7, n_tiles[1], tune.schedule, tune.ctas_per_sm,
+                               c->sm_count, B.counter + 32, st));
   return GSC_OK;
 }
 
 static bool tune_ok(const gsc_batch_tuning* t) {
-  return t && t->schedule >= 0 && t->schedule <= 2 && t->ctas_per_sm >= 1 && t->ctas_per_sm <= 4 &&
+  return t && t->schedule >= 0 && t->schedule <= 3 && t->ctas_per_sm >= 1 && t->ctas_per_sm <= 32 &&
          t->bc1_tile_groups >= 8 && t->bc1_tile_groups <= 4096;
 }
 
@@ -182,8 +235,8 @@ extern "C" gsc_status gsc_batch_encode(gsc_ctx* c, gsc_batch_scene* sc, int32_t 
   if (!B.fits) return GSC_ERR_INVALID_ARG;
   gsc_status s = run_plans(c, sc, n, B, st);
   if (s != GSC_OK) return s;
-  int64_t n_tiles = 0;
-  std::vector<BatchSceneDev> v = scene_list(sc, n, B, *tune, 1, &n_tiles);
+  int64_t n_tiles[2] = {0, 0};
+  std::vector<BatchSceneDev> v = scene_list(sc, n, B, *tune, 1, n_tiles);
   {
     GscTimed tm(c, T_BATCH, st);
     s = launch_list(c, v, n_tiles, B, *tune, st);
@@ -245,27 +298,27 @@ extern "C" gsc_status gsc_batch_autotune(gsc_ctx* c, gsc_batch_scene* sc, int32_
   GSC_CUDA(cudaEventCreate(&e1));
   double best = 1e30;
   gsc_batch_tuning bt = {1, 4, 8};
-  static const int kSched[3] = {0, 1, 2}, kCtas[3] = {2, 3, 4}, kTile[2] = {8, 32};
-  for (int a = 0; a < 3; a++)
-    for (int b = 0; b < 3; b++)
-      for (int d = 0; d < 2; d++) {
-        gsc_batch_tuning t = {kSched[a], kCtas[b], kTile[d]};
-        int64_t n_tiles = 0;
-        std::vector<BatchSceneDev> v = scene_list(sc, n, B, t, 32, &n_tiles);
-        double ms = 1e30;
-        for (int rep = 0; rep < 2; rep++) {
-          cudaEventRecord(e0, st);
-          s = launch_list(c, v, n_tiles, B, t, st);
-          if (s != GSC_OK) break;
-          cudaEventRecord(e1, st);
-          if (cudaEventSynchronize(e1) != cudaSuccess) { s = GSC_ERR_CUDA; break; }
-          float f = 0.f;
-          cudaEventElapsedTime(&f, e0, e1);
-          if (rep > 0) ms = std::min(ms, (double)f);
-        }
-        if (s != GSC_OK) break;
-        if (ms < best) { best = ms; bt = t; }
-      }
+  // candidates: resident grids (1..4 CTAs per SM) with work queues, oversubscribed round-robin
+  // grids (8..32 CTAs per SM, the hardware balances), one CTA per tile; BC1 tiles of 8 or 32
+  static const gsc_batch_tuning kCand[] = {{1, 4, 8}, {2, 4, 8}, {2, 3, 8}, {2, 4, 32}, {0, 8, 8},
+                                           {0, 16, 8}, {0, 32, 8}, {0, 32, 32}, {3, 4, 8}};
+  for (const gsc_batch_tuning& t : kCand) {
+    int64_t n_tiles[2] = {0, 0};
+    std::vector<BatchSceneDev> v = scene_list(sc, n, B, t, kProxyDiv, n_tiles);
+    double ms = 1e30;
+    for (int rep = 0; rep < 2; rep++) {
+      cudaEventRecord(e0, st);
+      s = launch_list(c, v, n_tiles, B, t, st);
+      if (s != GSC_OK) break;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { s = GSC_ERR_CUDA; break; }
+      float f = 0.f;
+      cudaEventElapsedTime(&f, e0, e1);
+      if (rep > 0) ms = std::min(ms, (double)f);
+    }
+    if (s != GSC_OK) break;
+    if (ms < best) { best = ms; bt = t; }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != GSC_OK) return s;
@@ -296,14 +349,44 @@ extern "C" gsc_status gsc_batch_eval_graph(gsc_ctx* c, const gsc_batch_scene* sc
   for (int i = 0; i < n; i++) g->kernels += T[i].n_groups > 0;
   g->graph = nullptr;
   g->exec = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  // the graph forks into kPlanLanes branches (scenes by decreasing size, each to the branch
+  // with the least work) so that evaluations of small scenes overlap
+  const int lanes = std::min(n, kPlanLanes);
+  cudaStream_t ls[kPlanLanes] = {};
+  cudaEvent_t fork = nullptr, join[kPlanLanes] = {};
+  cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  for (int l = 0; l < lanes && e == cudaSuccess; l++) {
+    e = cudaStreamCreateWithFlags(&ls[l], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[l], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    for (int i = 0; i < n && e == cudaSuccess; i++)
+    e = cudaEventRecord(fork, st);
+    for (int l = 0; l < lanes && e == cudaSuccess; l++) e = cudaStreamWaitEvent(ls[l], fork, 0);
+    std::vector<int> order(n);
+    for (int i = 0; i < n; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sc[a].n > sc[b].n; });
+    int64_t load[kPlanLanes] = {};
+    for (int i : order) {
+      if (e != cudaSuccess) break;
+      int l = 0;
+      for (int k = 1; k < lanes; k++) if (load[k] < load[l]) l = k;
+      load[l] += sc[i].n + 20000;
       e = launch_decode_eval(T[i], sc[i].d_blocks, sc[i].d_perm_out, nullptr, sc[i].d_pos, d_cams, V, out_order,
-                             d_rgb[i], c->sm_count, st);
+                             d_rgb[i], c->sm_count, ls[l]);
+    }
+    for (int l = 0; l < lanes; l++) {
+      if (e == cudaSuccess) e = cudaEventRecord(join[l], ls[l]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join[l], 0);
+    }
     cudaError_t e2 = cudaStreamEndCapture(st, &g->graph);
     if (e == cudaSuccess) e = e2;
   }
+  for (int l = 0; l < lanes; l++) {
+    if (join[l]) cudaEventDestroy(join[l]);
+    if (ls[l]) cudaStreamDestroy(ls[l]);
+  }
+  if (fork) cudaEventDestroy(fork);
   if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
   if (e != cudaSuccess) {
     if (g->exec) cudaGraphExecDestroy(g->exec);

@@ -540,21 +540,24 @@ cudaError_t launch_bc7_blocks(const uint8_t* tex, int64_t nblk, uint8_t* out, ui
 }
 
 // ---- persistent multi-scene encode -----------------------------------------------------------
-// Tiles are claimed round robin (schedule 0) or from an atomic work queue (1, and 2 when the
-// host listed the scenes by decreasing cost); a tile finds its scene by binary search over
-// the scene list. Each tile stages 8 groups at a time and codes them BC1 (kind 1) or BC7
-// (kind 7); a scene that needs both codings is listed twice. The bits equal the single-scene
-// kernels'.
+// One launch per coding (KIND 1 = BC1, 7 = BC7) over the tiles of every listed scene. Tiles
+// are claimed round robin (schedule 0), from an atomic work queue (1, 2), or one per CTA (3, a
+// grid of all tiles); a tile finds its scene by binary search over the list. Each tile stages
+// 8 groups at a time; the bits equal the single-scene kernels'.
+template <int KIND>
 __global__ void __launch_bounds__(STAGE_THREADS, 4) k_batch(const BatchSceneDev* __restrict__ scenes, int n_scenes,
                                                             int64_t n_tiles, int schedule, int* __restrict__ counter) {
   __shared__ uint32_t tex[16][STAGE_STRIDE];
   __shared__ float s_scale[16];
-  __shared__ uint16_t sq[12 * 256];
+  __shared__ uint16_t sq[KIND == 7 ? 12 * 256 : 1];
   __shared__ long long s_tile;
-  for (int i = threadIdx.x; i < 12 * 256; i += blockDim.x) sq[i] = (&g_qtab[0][0])[i];
+  if (KIND == 7)
+    for (int i = threadIdx.x; i < 12 * 256; i += blockDim.x) sq[i] = (&g_qtab[0][0])[i];
   for (int64_t it = 0;; it++) {
     __syncthreads();
-    if (threadIdx.x == 0) s_tile = schedule == 0 ? (long long)(blockIdx.x + it * gridDim.x) : (long long)atomicAdd(counter, 1);
+    if (threadIdx.x == 0)
+      s_tile = (schedule == 0 || schedule == 3) ? (long long)(blockIdx.x + it * gridDim.x)
+                                                : (long long)atomicAdd(counter, 1);
     __syncthreads();
     const int64_t ti = s_tile;
     if (ti >= n_tiles) break;
@@ -563,7 +566,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, 4) k_batch(const BatchSceneDev*
       const int mid = (lo + hi + 1) >> 1;
       if (scenes[mid].tile0 <= ti) lo = mid; else hi = mid - 1;
     }
-    const BatchSceneDev& S = scenes[lo];
+    const BatchSceneDev S = scenes[lo];
     const int64_t gbeg = (ti - S.tile0) * S.tile_groups;
     const int64_t gend = min(gbeg + (int64_t)S.tile_groups, S.work_groups);
     if (threadIdx.x < 16) s_scale[threadIdx.x] = S.scales[threadIdx.x];
@@ -573,7 +576,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, 4) k_batch(const BatchSceneDev*
       __syncthreads();
       const int64_t blk = g0 * 16 + threadIdx.x;
       if (blk < S.n_groups * 16) {
-        if (S.kind == 1) {
+        if (KIND == 1) {
           uint32_t tx[16];
 #pragma unroll
           for (int t = 0; t < 16; t++) tx[t] = tex[t][threadIdx.x];
@@ -594,15 +597,19 @@ __global__ void __launch_bounds__(STAGE_THREADS, 4) k_batch(const BatchSceneDev*
   }
 }
 
-cudaError_t launch_batch_encode(const BatchSceneDev* scenes, int n_scenes, int64_t n_tiles, int schedule,
+cudaError_t launch_batch_encode(int kind, const BatchSceneDev* scenes, int n_scenes, int64_t n_tiles, int schedule,
                                 int ctas_per_sm, int sm_count, int* counter, cudaStream_t st) {
   if (n_tiles <= 0 || n_scenes <= 0) return cudaSuccess;
-  int64_t grid = (int64_t)(sm_count > 0 ? sm_count : 152) * (ctas_per_sm > 0 ? ctas_per_sm : 4);
+  // schedule 3: one CTA per tile, left to the hardware block scheduler
+  int64_t grid = schedule == 3 ? n_tiles : (int64_t)(sm_count > 0 ? sm_count : 152) * (ctas_per_sm > 0 ? ctas_per_sm : 4);
   if (grid > n_tiles) grid = n_tiles;
-  if (schedule != 0) {
+  if (grid > 0x7FFFFFFF) grid = 0x7FFFFFFF;
+  if (schedule == 1 || schedule == 2) {
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
   }
-  gsc_count_launch(); k_batch<<<(int)grid, STAGE_THREADS, 0, st>>>(scenes, n_scenes, n_tiles, schedule, counter);
+  gsc_count_launch();
+  if (kind == 7) k_batch<7><<<(int)grid, STAGE_THREADS, 0, st>>>(scenes, n_scenes, n_tiles, schedule, counter);
+  else k_batch<1><<<(int)grid, STAGE_THREADS, 0, st>>>(scenes, n_scenes, n_tiles, schedule, counter);
   return cudaGetLastError();
 }

@@ -487,23 +487,26 @@ __device__ __forceinline__ void load_views(float (*s_view)[64], float* s_deq, co
   if (threadIdx.x < 16) s_deq[threadIdx.x] = __fmul_rn(__fdiv_rn(T.scales[threadIdx.x], 255.0f), c_shc[threadIdx.x]);
 }
 
+// CTAs of 4 warps (128 threads x at most 128 registers): one fits where one BC7-search CTA
+// retired, so an evaluation launched beside an encode on a higher-priority stream starts early.
+#define EVAL_THREADS 128
 template <int KIND, bool CAMS>
-__global__ void __launch_bounds__(256) k_eval2(DevTable T, const uint8_t* __restrict__ blocks,
+__global__ void __launch_bounds__(EVAL_THREADS) k_eval2(DevTable T, const uint8_t* __restrict__ blocks,
                                                const int32_t* __restrict__ perm, const float* __restrict__ dirs,
                                                const float* __restrict__ pos, const float* __restrict__ cams, int V,
                                                int out_order, float* __restrict__ rgb) {
   __shared__ DecTables S;
-  __shared__ uint32_t tile[8][WTILE];
+  __shared__ uint32_t tile[EVAL_THREADS / 32][WTILE];
   __shared__ float s_view[3][64];
   __shared__ float s_deq[16];
   load_tables(&S);
   load_views(s_view, s_deq, dirs, cams, V, T);
   __syncthreads();
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, gw = l >> 4, kt = l & 15;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, gw = l >> 4, kt = l & 15, nw = blockDim.x >> 5;
   const int64_t npairs = ((int64_t)T.n_groups + 1) / 2;
   const int64_t n = T.n, ns = (int64_t)T.n_groups * 16;
   uint32_t* my = tile[w] + gw * 272;
-  for (int64_t pr = (int64_t)blockIdx.x * 8 + w; pr < npairs; pr += (int64_t)gridDim.x * 8) {
+  for (int64_t pr = (int64_t)blockIdx.x * nw + w; pr < npairs; pr += (int64_t)gridDim.x * nw) {
     const int64_t g = pr * 2 + gw;
     const bool live = g < T.n_groups;
     {
@@ -538,10 +541,11 @@ static int kind_of(const DevTable& T) {
   return 0;
 }
 
-static int eval_grid(int64_t n_groups, int sm_count) {
+// CTAs of `warps` warps, one pair of groups per warp per step; at most 64 warps per SM.
+static int eval_grid(int64_t n_groups, int sm_count, int warps = 8) {
   int64_t pairs = (n_groups + 1) / 2;
-  int64_t g = ceil_div64(pairs, 8);
-  int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * 8;
+  int64_t g = ceil_div64(pairs, warps);
+  int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * (64 / warps);
   return (int)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
@@ -561,10 +565,10 @@ cudaError_t launch_decode_eval(const DevTable& T, const uint8_t* blocks, const i
                                const float* pos, const float* cams, int V, int out_order, float* rgb, int sm_count,
                                cudaStream_t st) {
   if (T.n_groups == 0) return cudaSuccess;
-  const int grid = eval_grid(T.n_groups, sm_count);
+  const int grid = eval_grid(T.n_groups, sm_count, EVAL_THREADS / 32);
   const int kind = kind_of(T);
 #define EVAL_LAUNCH(K, C) \
-  do { gsc_count_launch(); k_eval2<K, C><<<grid, 256, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order, rgb); } while (0)
+  do { gsc_count_launch(); k_eval2<K, C><<<grid, EVAL_THREADS, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order, rgb); } while (0)
   if (cams) {
     if (kind == 7) EVAL_LAUNCH(7, true); else if (kind == 1) EVAL_LAUNCH(1, true); else EVAL_LAUNCH(0, true);
   } else {

@@ -129,7 +129,8 @@ struct BatchSceneDev {
   uint8_t* b7;
   uint32_t *sse1, *sse7, *sse0;
 };
-cudaError_t launch_batch_encode(const BatchSceneDev* scenes, int n_scenes, int64_t n_tiles, int schedule,
+// kind 1 or 7: every listed scene must be of that kind.
+cudaError_t launch_batch_encode(int kind, const BatchSceneDev* scenes, int n_scenes, int64_t n_tiles, int schedule,
                                 int ctas_per_sm, int sm_count, int* counter, cudaStream_t st);
 
 // rate.cu

@@ -65,7 +65,12 @@ void encode_bytes(int64_t n, int fmt, uint32_t t4, bool host_sh, uint64_t* temp,
 
 bool params_ok(const gsc_server_params* p) {
   return p && p->hbm_budget_bytes > 0 && p->n_slots >= 1 && p->n_slots <= 16 && p->max_views >= 1 &&
-         p->max_views <= 64 && p->hold_us >= 0 && (p->merge == 0 || p->merge == 1);
+         p->max_views <= 64 && p->hold_us >= 0 && (p->merge == 0 || p->merge == 1) && p->encode_slots >= 0 &&
+         p->encode_slots <= p->n_slots;
+}
+
+int encode_slots(const gsc_server_params& p) {
+  return p.encode_slots > 0 ? p.encode_slots : (p.n_slots > 1 ? p.n_slots - 1 : 1);
 }
 
 }  // namespace
@@ -85,7 +90,7 @@ struct gsc_server {
   std::chrono::steady_clock::time_point t0;
 
   explicit gsc_server(const gsc_server_params& p)
-      : prm(p), sched(p.hbm_budget_bytes, p.merge != 0, p.max_views, 16, p.hold_us * 1000) {}
+      : prm(p), sched(p.hbm_budget_bytes, p.merge != 0, p.max_views, 16, p.hold_us * 1000, encode_slots(p)) {}
 
   int64_t now() const {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0).count();
@@ -467,7 +472,7 @@ extern "C" gsc_status gsc_server_destroy(gsc_server* s) {
 extern "C" gsc_status gsc_server_simulate(const gsc_server_params* p, const gsc_sim_request* rq, int32_t n,
                                           gsc_sim_result* res, uint64_t* peak_bytes) {
   if (!params_ok(p) || n < 0 || (n > 0 && (!rq || !res))) return GSC_ERR_INVALID_ARG;
-  Sched sc(p->hbm_budget_bytes, p->merge != 0, p->max_views, 16, p->hold_us * 1000);
+  Sched sc(p->hbm_budget_bytes, p->merge != 0, p->max_views, 16, p->hold_us * 1000, encode_slots(*p));
   std::vector<int> order(n);
   for (int i = 0; i < n; i++) order[i] = i;
   std::stable_sort(order.begin(), order.end(),

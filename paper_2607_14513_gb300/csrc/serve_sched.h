@@ -51,8 +51,9 @@ static inline uint64_t sched_eval_bytes(int64_t n, int V, int out_order) {
 
 class Sched {
  public:
-  Sched(uint64_t budget, bool merge, int max_views, int max_merge, int64_t hold_ns)
-      : budget_(budget), merge_(merge), max_views_(max_views), max_merge_(max_merge), hold_ns_(hold_ns) {}
+  Sched(uint64_t budget, bool merge, int max_views, int max_merge, int64_t hold_ns, int max_encodes)
+      : budget_(budget), merge_(merge), max_views_(max_views), max_merge_(max_merge), hold_ns_(hold_ns),
+        max_encodes_(max_encodes) {}
 
   // False when the request could never run within the budget.
   bool submit(const SchedReq& r) {
@@ -133,6 +134,7 @@ class Sched {
         return true;
       }
       // encode
+      if (encoding_ >= max_encodes_) continue;
       if (!fits(L.temp_bytes + L.keep_bytes, r.scene, &L.evict)) {
         if (now - r.t_submit > hold_ns_) return false;
         continue;
@@ -140,6 +142,7 @@ class Sched {
       take(i);
       apply_evictions(L.evict);
       S.encoding = true;
+      encoding_++;
       L.version = S.next_version++;
       used_ += L.temp_bytes + L.keep_bytes;
       peak_ = std::max(peak_, used_);
@@ -161,6 +164,7 @@ class Sched {
     used_ -= L.temp_bytes;
     if (L.kind == SLAUNCH_ENCODE) {
       S.encoding = false;
+      encoding_--;
       if (!ok) {
         used_ -= L.keep_bytes;
         return freed;
@@ -290,5 +294,6 @@ class Sched {
   bool merge_;
   int max_views_, max_merge_;
   int64_t hold_ns_;
-  int running_ = 0;
+  int max_encodes_;
+  int running_ = 0, encoding_ = 0;
 };

@@ -69,7 +69,7 @@ REQ_ENCODE, REQ_EVAL = 0, 1
 
 class ServerParams(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_uint64), ("n_slots", C.c_int32), ("merge", C.c_int32),
-                ("max_views", C.c_int32), ("priority", C.c_int32), ("hold_us", C.c_int64)]
+                ("max_views", C.c_int32), ("priority", C.c_int32), ("encode_slots", C.c_int32), ("hold_us", C.c_int64)]
 
 
 class Request(C.Structure):
@@ -490,10 +490,12 @@ class Server:
     """The request loop (gsc_server_*). Tensors passed to submit() must stay alive until the
     request completes; the object keeps a reference to them until wait() returns."""
 
-    def __init__(self, ctx, budget_bytes, n_slots=4, merge=True, max_views=64, priority=True, hold_us=200_000):
+    def __init__(self, ctx, budget_bytes, n_slots=4, merge=True, max_views=64, priority=True, hold_us=200_000,
+                 encode_slots=0):
         self.ctx = ctx
         self.lib = ctx.lib
-        self.params = ServerParams(int(budget_bytes), n_slots, int(merge), max_views, int(priority), hold_us)
+        self.params = ServerParams(int(budget_bytes), n_slots, int(merge), max_views, int(priority), encode_slots,
+                                   hold_us)
         h = C.c_void_p()
         _check(self.lib.gsc_server_create(ctx.h, C.byref(self.params), C.byref(h)), "gsc_server_create")
         self.h = h

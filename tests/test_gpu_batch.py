@@ -53,7 +53,7 @@ def _single(ctx, pos, sh, fmt, t4, gs):
     return perm, scales, blocks, perm_out, tab
 
 
-@pytest.mark.parametrize("schedule,ctas,tile", [(0, 4, 8), (1, 3, 32), (2, 2, 64)])
+@pytest.mark.parametrize("schedule,ctas,tile", [(0, 4, 8), (1, 3, 32), (2, 2, 64), (3, 4, 16)])
 def test_batch_equals_single_scene_calls(ctx, schedule, ctas, tile):
     from paper_2607_14513_gb300 import gsc
     sc = _scenes(MIX, 3100)
@@ -90,7 +90,7 @@ def test_batch_autotune_picks_a_valid_tuning(ctx):
     sc = _scenes(MIX[:6], 3200)
     b = gsc.Batch(ctx, [(p, s, f, t) for p, s, f, t, _ in sc], group_size=1024)
     t, ms = b.autotune()
-    assert t.schedule in (0, 1, 2) and t.ctas_per_sm in (2, 3, 4) and t.bc1_tile_groups in (8, 32)
+    assert t.schedule in (0, 1, 2, 3) and 1 <= t.ctas_per_sm <= 32 and t.bc1_tile_groups in (8, 32)
     assert ms > 0.0
     b.encode(t)
     ctx.sync()
@@ -127,9 +127,11 @@ def test_batch_invalid_arguments(ctx):
     sc = _scenes([(100, 1, 0)], 3500)
     b = gsc.Batch(ctx, [(p, s, f, t) for p, s, f, t, _ in sc])
     with pytest.raises(gsc.GscError):
-        b.encode(gsc.BatchTuning(3, 4, 8))          # no such schedule
+        b.encode(gsc.BatchTuning(4, 4, 8))          # no such schedule
     with pytest.raises(gsc.GscError):
         b.encode(gsc.BatchTuning(0, 0, 8))          # zero CTAs per SM
+    with pytest.raises(gsc.GscError):
+        b.encode(gsc.BatchTuning(0, 33, 8))         # more than 32 CTAs per SM
     bad = (gsc.BatchScene * 1)()
     bad[0] = b.arr[0]
     bad[0].format = 2

@@ -135,7 +135,7 @@ def test_budget_eviction_and_refusals(ctx):
     dev = [(torch.from_numpy(s.pos).cuda(), torch.from_numpy(s.sh).cuda()) for s in scs]
     # find the footprint of one BC1 encode of this size with the host-side policy
     req = gsc.SimRequest(0, 0, n, 1, 0, 0, 0, 0, 1, 0, 0.0, 1.0)
-    res, peak = gsc.simulate(gsc.ServerParams(64 * GiB, 1, 1, 64, 1, 0), [req])
+    res, peak = gsc.simulate(gsc.ServerParams(64 * GiB, 1, 1, 64, 1, 0, 0), [req])
     e = res[0].used_bytes_at_admit
     keep = (n + 15) // 16 * 128 + 4 * ((n + 15) // 16 * 16) + 12 * n
     budget = e + keep + keep // 2

@@ -10,8 +10,8 @@ OK, INVALID, BUDGET = 0, 1, 4
 GiB = 1 << 30
 
 
-def P(budget=64 * GiB, slots=4, merge=1, max_views=64, hold_us=10_000_000):
-    return gsc.ServerParams(budget, slots, merge, max_views, 1, hold_us)
+def P(budget=64 * GiB, slots=4, merge=1, max_views=64, hold_us=10_000_000, encode_slots=0):
+    return gsc.ServerParams(budget, slots, merge, max_views, 1, encode_slots, hold_us)
 
 
 def enc(t, scene, n=16000, fmt=1, service=10.0, t4=0):
@@ -119,8 +119,8 @@ def test_hold_time_stops_overtaking():
     # evaluations of scene 2 (resident) need staging memory (host output)
     tr = [enc(0.0, 2, service=1.0), enc(5.0, 0, service=20.0), enc(6.0, 1, service=1.0),
           ev(10.0, 2, V=1, out_device=0), ev(11.0, 2, V=1, out_device=0)]
-    res_hold, _ = gsc.simulate(P(budget=budget, slots=2, hold_us=1000, merge=0), tr)
-    res_free, _ = gsc.simulate(P(budget=budget, slots=2, hold_us=10**9, merge=0), tr)
+    res_hold, _ = gsc.simulate(P(budget=budget, slots=2, hold_us=1000, merge=0, encode_slots=2), tr)
+    res_free, _ = gsc.simulate(P(budget=budget, slots=2, hold_us=10**9, merge=0, encode_slots=2), tr)
     # without a hold the evaluations overtake the waiting encode; with a 1 ms hold they queue behind it
     assert res_free[3].t_admit_ms < res_free[2].t_admit_ms
     assert res_hold[3].t_admit_ms >= res_hold[2].t_admit_ms
@@ -132,3 +132,15 @@ def test_one_slot_runs_requests_one_at_a_time():
     spans = sorted((r.t_admit_ms, r.t_done_ms) for r in res)
     for (a0, d0), (a1, d1) in zip(spans, spans[1:]):
         assert a1 >= d0
+
+
+def test_encode_slots_keep_a_slot_for_evaluations():
+    # three long encodes and an evaluation of a resident scene; with 3 slots and the default
+    # of n_slots - 1 encode slots, the evaluation does not wait for an encode to finish
+    tr = [enc(0.0, 9, service=1.0), enc(2.0, 0, service=50.0), enc(2.1, 1, service=50.0), enc(2.2, 2, service=50.0),
+          ev(3.0, 9)]
+    res, _ = gsc.simulate(P(slots=3), tr)
+    assert res[4].t_admit_ms == pytest.approx(3.0)
+    assert res[3].t_admit_ms >= res[1].t_done_ms - 1e-9      # the third encode waited for an encode slot
+    res_all, _ = gsc.simulate(P(slots=3, encode_slots=3), tr)
+    assert res_all[4].t_admit_ms >= 52.0 - 1e-9              # all slots busy with encodes
