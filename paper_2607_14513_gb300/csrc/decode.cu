@@ -228,8 +228,23 @@ __device__ __forceinline__ void bc1_block(uint2 w, uint32_t (&tx)[16]) {
   }
 }
 
+// A zero bit inserted at position p (0..63): the index of an anchor texel is stored one bit
+// short (its top bit is 0), so this gives every texel the full index width.
+__device__ __forceinline__ uint64_t ins0(uint64_t x, int p) {
+  const uint64_t m = (1ull << p) - 1ull;
+  return (x & m) | ((x & ~m) << 1);
+}
+
 // Whole BC7 block, uniform control flow across modes (fields located from the mode descriptor).
-__device__ __forceinline__ void bc7_block(uint64_t lo, uint64_t hi, uint32_t (&tx)[16], const DecTables* S) {
+// Texel t comes out as r | g << 8 | b << 16 (the alpha byte is unspecified). The block is
+// parsed once: endpoints per subset go to this lane's slot `ep` in shared memory as 16-bit
+// lanes scaled by 4 (e0 r|g, e0 b|a, e1 r|g, e1 b|a), so that the interpolation
+// ((64 - w) e0 + w e1 + 32) >> 6 of two channels is two multiply-adds whose result bytes 1
+// and 3 are the two channels; the index streams are re-spaced to a fixed width per texel.
+// A rotation (modes 4 and 5) puts the alpha-index interpolation of the alpha endpoints into
+// the rotated channel.
+__device__ __forceinline__ void bc7_block(uint64_t lo, uint64_t hi, uint32_t (&tx)[16], const DecTables* S,
+                                          uint4* ep) {
   const uint32_t b0 = (uint32_t)(lo & 0xFF);
   const int mode = b0 ? __ffs(b0) - 1 : 0;
   const uint32_t d = S->desc[mode];
@@ -248,72 +263,122 @@ __device__ __forceinline__ void bc7_block(uint64_t lo, uint64_t hi, uint32_t (&t
   const int istart = pstart + (epb ? 2 * ns : (spb ? ns : 0));
   const int hp = epb | spb, nb = cb + hp, na = ab + epb;
   const uint64_t pbits = shr128(lo, hi, pstart);
-  uint32_t E0rg[3], E0ba[3], E1rg[3], E1ba[3];
+  // one window per channel: the 2 ns endpoint fields of a channel span at most 30 bits
+  const uint32_t fr = (uint32_t)shr128(lo, hi, cstart), fg = (uint32_t)shr128(lo, hi, cstart + 2 * ns * cb);
+  const uint32_t fb = (uint32_t)shr128(lo, hi, cstart + 4 * ns * cb), fa = (uint32_t)shr128(lo, hi, astart);
+  const uint32_t cm = (1u << cb) - 1u, amk = (1u << ab) - 1u;
+  // bit replication to 8 bits, (v << (8 - n)) | (v >> (2n - 8)), exact also for n = 8
+  const int cl8 = 8 - nb, cr8 = 2 * nb - 8, al8 = 8 - na, ar8 = 2 * na - 8;
 #pragma unroll
   for (int s = 0; s < 3; s++) {
-    E0rg[s] = E0ba[s] = E1rg[s] = E1ba[s] = 0;
     if (s < ns) {
-      const int p0 = epb ? (int)((pbits >> (2 * s)) & 1) : (spb ? (int)((pbits >> s) & 1) : 0);
-      const int p1 = epb ? (int)((pbits >> (2 * s + 1)) & 1) : p0;
-      int v0[4], v1[4];
+      const uint32_t p0 = epb ? (uint32_t)((pbits >> (2 * s)) & 1) : (spb ? (uint32_t)((pbits >> s) & 1) : 0u);
+      const uint32_t p1 = epb ? (uint32_t)((pbits >> (2 * s + 1)) & 1) : p0;
+      const int sh0 = 2 * s * cb, sh1 = sh0 + cb;
+      uint32_t v0[3], v1[3];
+      const uint32_t f3[3] = {fr, fg, fb};
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        const uint64_t f = shr128(lo, hi, cstart + (c * ns + s) * 2 * cb);
-        const int c0 = (int)(f & ((1u << cb) - 1u)), c1 = (int)((f >> cb) & ((1u << cb) - 1u));
-        v0[c] = d_expand(hp ? (c0 << 1) | p0 : c0, nb);
-        v1[c] = d_expand(hp ? (c1 << 1) | p1 : c1, nb);
+        const uint32_t c0 = ((f3[c] >> sh0) & cm) << hp | (p0 & hp), c1 = ((f3[c] >> sh1) & cm) << hp | (p1 & hp);
+        v0[c] = (c0 << cl8) | (c0 >> cr8);
+        v1[c] = (c1 << cl8) | (c1 >> cr8);
       }
+      uint32_t a0 = 255u, a1 = 255u;
       if (ab) {
-        const uint64_t f = shr128(lo, hi, astart + 2 * s * ab);
-        const int c0 = (int)(f & ((1u << ab) - 1u)), c1 = (int)((f >> ab) & ((1u << ab) - 1u));
-        v0[3] = d_expand(epb ? (c0 << 1) | p0 : c0, na);
-        v1[3] = d_expand(epb ? (c1 << 1) | p1 : c1, na);
-      } else {
-        v0[3] = v1[3] = 255;
+        const uint32_t c0 = ((fa >> (2 * s * ab)) & amk) << epb | (p0 & epb), c1 = ((fa >> ((2 * s + 1) * ab)) & amk) << epb | (p1 & epb);
+        a0 = (c0 << al8) | (c0 >> ar8);
+        a1 = (c1 << al8) | (c1 >> ar8);
       }
-      E0rg[s] = v0[0] | (v0[1] << 16); E0ba[s] = v0[2] | (v0[3] << 16);
-      E1rg[s] = v1[0] | (v1[1] << 16); E1ba[s] = v1[2] | (v1[3] << 16);
+      ep[s] = make_uint4((v0[0] | (v0[1] << 16)) << 2, (v0[2] | (a0 << 16)) << 2, (v1[0] | (v1[1] << 16)) << 2,
+                         (v1[2] | (a1 << 16)) << 2);
     }
   }
-  uint64_t prim = shr128(lo, hi, istart);
-  uint64_t sec = ib2 ? shr128(lo, hi, istart + 16 * ib - 1) : 0;
-  const int cib = (ib2 && isbv) ? ib2 : ib, aib = ib2 ? (isbv ? ib : ib2) : ib;
-  const uint32_t rsel = rot == 0 ? 0x3210u : (rot == 1 ? 0x0213u : (rot == 2 ? 0x1230u : 0x2310u));
+  // index streams at a fixed width per texel (anchor texels: texel 0, and a1, a2 in the primary)
+  uint64_t pa = ins0(shr128(lo, hi, istart), ib - 1);
+  const int alo = min(a1, a2), ahi = max(a1, a2);
+  if (alo < 16) pa = ins0(pa, alo * ib + ib - 1);
+  if (ahi < 16) pa = ins0(pa, ahi * ib + ib - 1);
+  uint64_t sa = ib2 ? ins0(shr128(lo, hi, istart + 16 * ib - 1), ib2 - 1) : 0ull;
+  const bool swap = ib2 && isbv;  // mode 4 with the index selection bit: colour from the 3-bit stream
+  const uint64_t cs = swap ? sa : pa, as = swap ? pa : sa;
+  const int cbits = swap ? ib2 : ib, abits = ib2 ? (swap ? ib : ib2) : 0;
+  const uint32_t cmask = (1u << cbits) - 1u, amask = (1u << abits) - 1u;
+  const uint8_t* wc = S->wt + (cbits - 2) * 16;
+  const uint8_t* wa = S->wt + (abits ? abits - 2 : 0) * 16;
+  // rotation: the alpha result (byte 3 of `al`, operand byte 7) replaces channel rot - 1
+  const uint32_t rsel = rot == 0 ? 0x3210u : (rot == 1 ? 0x3217u : (rot == 2 ? 0x3270u : 0x3710u));
+  // the reserved mode (first byte 0) decodes to 0: zero endpoints give exactly that below
+  if (!b0) ep[0] = ep[1] = ep[2] = make_uint4(0u, 0u, 0u, 0u);
+  const uint32_t bias = 0x00800080u;
+  // both streams as 32-bit halves, advanced by funnel shifts (widths are at most 4 bits)
+  uint32_t cl = (uint32_t)cs, ch = (uint32_t)(cs >> 32), al32 = (uint32_t)as, ah = (uint32_t)(as >> 32);
 #pragma unroll
   for (int t = 0; t < 16; t++) {
-    const int anc = (t == 0) | (t == a1) | (t == a2);
-    const int n1 = ib - anc;
-    const int pi = (int)(prim & ((1u << n1) - 1u));
-    prim >>= n1;
-    int si = pi;
-    if (ib2) {
-      const int n2 = ib2 - (t == 0);
-      si = (int)(sec & ((1u << n2) - 1u));
-      sec >>= n2;
+    const uint32_t ci = cl & cmask, ai = al32 & amask;
+    cl = __funnelshift_r(cl, ch, cbits);
+    ch >>= cbits;
+    al32 = __funnelshift_r(al32, ah, abits);
+    ah >>= abits;
+    const uint4 e = ep[(pm >> (2 * t)) & 3];
+    const uint32_t cw = wc[ci], aw = wa[ai];
+    const uint32_t rg = (64u - cw) * e.x + cw * e.z + bias;
+    const uint32_t ba = (64u - cw) * e.y + cw * e.w + bias;
+    const uint32_t al = (64u - aw) * e.y + aw * e.w + bias;
+    tx[t] = __byte_perm(__byte_perm(rg, ba, 0x0531u), al, rsel);
+  }
+}
+
+// The raw words of block k of group g (kind 0: dropped, 1: BC1 in w.x/w.y, 7: BC7), loaded
+// ahead of their decode.
+struct RawBlock {
+  uint4 w;
+  int kind;
+};
+
+template <int KIND>
+__device__ __forceinline__ RawBlock fetch_block(const DevTable& T, const uint8_t* __restrict__ blocks, int64_t g, int k) {
+  RawBlock r;
+  r.w = make_uint4(0u, 0u, 0u, 0u);
+  if (KIND == 7) {
+    r.w = __ldg(reinterpret_cast<const uint4*>(blocks) + g * 16 + k);
+    r.kind = 7;
+  } else if (KIND == 1) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(blocks) + g * 16 + k);
+    r.w.x = v.x; r.w.y = v.y;
+    r.kind = 1;
+  } else {
+    const int si = stream_of(T, g);
+    const BlockLoc L = locate(T, si, g, k);
+    r.kind = L.kind;
+    if (L.kind != 0) {
+      const uint2* p = reinterpret_cast<const uint2*>(blocks + L.off);
+      const uint2 w0 = __ldg(p);
+      r.w.x = w0.x; r.w.y = w0.y;
+      if (L.kind == 7) { const uint2 w1 = __ldg(p + 1); r.w.z = w1.x; r.w.w = w1.y; }
     }
-    const int ci = (ib2 && isbv) ? si : pi;
-    const int ai = ib2 ? (isbv ? pi : si) : pi;
-    const int cw = S->wt[(cib - 2) * 16 + ci], aw = S->wt[(aib - 2) * 16 + ai];
-    const int s = (pm >> (2 * t)) & 3;
-    const uint32_t e0rg = s == 0 ? E0rg[0] : (s == 1 ? E0rg[1] : E0rg[2]);
-    const uint32_t e1rg = s == 0 ? E1rg[0] : (s == 1 ? E1rg[1] : E1rg[2]);
-    const uint32_t e0ba = s == 0 ? E0ba[0] : (s == 1 ? E0ba[1] : E0ba[2]);
-    const uint32_t e1ba = s == 0 ? E1ba[0] : (s == 1 ? E1ba[1] : E1ba[2]);
-    const uint32_t rg = (((64 - cw) * e0rg + cw * e1rg + 0x00200020u) >> 6) & 0x00FF00FFu;
-    const uint32_t bb = (((64 - cw) * (e0ba & 0xFFFF) + cw * (e1ba & 0xFFFF) + 32) >> 6);
-    const uint32_t aa = (((64 - aw) * (e0ba >> 16) + aw * (e1ba >> 16) + 32) >> 6);
-    const uint32_t px = (rg & 0xFF) | ((rg >> 16) << 8) | (bb << 16) | (aa << 24);
-    tx[t] = b0 ? __byte_perm(px, 0, rsel) : 0u;
+  }
+  return r;
+}
+
+template <int KIND>
+__device__ __forceinline__ void decode_raw(const RawBlock& r, uint32_t (&tx)[16], const DecTables* S, uint4* ep) {
+  if (KIND == 7 || (KIND == 0 && r.kind == 7)) {
+    bc7_block(((uint64_t)r.w.y << 32) | r.w.x, ((uint64_t)r.w.w << 32) | r.w.z, tx, S, ep);
+  } else if (KIND == 1 || (KIND == 0 && r.kind == 1)) {
+    bc1_block(make_uint2(r.w.x, r.w.y), tx);
+  } else {
+#pragma unroll
+    for (int t = 0; t < 16; t++) tx[t] = 0xFF808080u;
   }
 }
 
 // Block k of group g of the stream table into 16 packed texels (RGB + A); 128 where dropped.
 template <int KIND>
 __device__ __forceinline__ void block_texels(const DevTable& T, const uint8_t* __restrict__ blocks, int64_t g, int k,
-                                             uint32_t (&tx)[16], const DecTables* S) {
+                                             uint32_t (&tx)[16], const DecTables* S, uint4* ep) {
   if (KIND == 7) {
     const uint4 w = __ldg(reinterpret_cast<const uint4*>(blocks) + g * 16 + k);
-    bc7_block(((uint64_t)w.y << 32) | w.x, ((uint64_t)w.w << 32) | w.z, tx, S);
+    bc7_block(((uint64_t)w.y << 32) | w.x, ((uint64_t)w.w << 32) | w.z, tx, S, ep);
   } else if (KIND == 1) {
     bc1_block(__ldg(reinterpret_cast<const uint2*>(blocks) + g * 16 + k), tx);
   } else {
@@ -322,7 +387,7 @@ __device__ __forceinline__ void block_texels(const DevTable& T, const uint8_t* _
     if (L.kind == 7) {
       const uint2* p = reinterpret_cast<const uint2*>(blocks + L.off);
       const uint2 w0 = __ldg(p), w1 = __ldg(p + 1);
-      bc7_block(((uint64_t)w0.y << 32) | w0.x, ((uint64_t)w1.y << 32) | w1.x, tx, S);
+      bc7_block(((uint64_t)w0.y << 32) | w0.x, ((uint64_t)w1.y << 32) | w1.x, tx, S, ep);
     } else if (L.kind == 1) {
       bc1_block(__ldg(reinterpret_cast<const uint2*>(blocks + L.off)), tx);
     } else {
@@ -338,9 +403,9 @@ __device__ __forceinline__ int table_kind(const DevTable& T) {
   return 0;
 }
 
-// exact (q - 128) as float: 0x4B0000qq is 2^23 + q
-__device__ __forceinline__ float byte_m128(uint32_t v, int c) {
-  return __uint_as_float(__byte_perm(v, 0x4B000000u, 0x7650u | (uint32_t)c)) - 8388736.0f;
+// 2^23 + q as float for byte c of v (0x4B0000qq)
+__device__ __forceinline__ float u23(uint32_t v, int c) {
+  return __uint_as_float(__byte_perm(v, 0x4B000000u, 0x7650u | (uint32_t)c));
 }
 
 template <int KIND>
@@ -348,6 +413,7 @@ __global__ void __launch_bounds__(256) k_decode2(DevTable T, const uint8_t* __re
                                                  const int32_t* __restrict__ perm, uint8_t* __restrict__ texels) {
   __shared__ DecTables S;
   __shared__ uint32_t tile[8][WTILE];
+  __shared__ uint4 s_ep[256][3];
   load_tables(&S);
   __syncthreads();
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, gw = l >> 4, kt = l & 15;
@@ -357,7 +423,7 @@ __global__ void __launch_bounds__(256) k_decode2(DevTable T, const uint8_t* __re
     const int64_t g = pr * 2 + gw;
     const bool live = g < T.n_groups;
     uint32_t tx[16];
-    if (live) block_texels<KIND>(T, blocks, g, kt, tx, &S);
+    if (live) block_texels<KIND>(T, blocks, g, kt, tx, &S, s_ep[threadIdx.x]);
 #pragma unroll
     for (int t = 0; t < 16; t++) my[17 * kt + t] = live ? tx[t] : 0u;
     __syncwarp();
@@ -384,57 +450,52 @@ __global__ void __launch_bounds__(256) k_decode2(DevTable T, const uint8_t* __re
   }
 }
 
-// SH basis polynomials without their constants; the constants (with signs) are folded
-// into the per-coefficient dequantisation factors s_k / 255 * C_k.
+// SH basis polynomials without their constants (the constants, with their signs, are folded
+// into the per-coefficient dequantisation factors s_k / 255 * C_k), for two views at once.
 __device__ __forceinline__ void sh_poly2(float2 x, float2 y, float2 z, float2 (&P)[16]) {
   const float2 xx = __fmul2_rn(x, x), yy = __fmul2_rn(y, y), zz = __fmul2_rn(z, z);
   const float2 xy = __fmul2_rn(x, y), yz = __fmul2_rn(y, z), xz = __fmul2_rn(x, z);
   const float2 two = make_float2(2.f, 2.f), three = make_float2(3.f, 3.f), four = make_float2(4.f, 4.f);
   const float2 xpy = __fadd2_rn(xx, yy);
-  const float2 xmy = __fadd2_rn(xx, make_float2(-yy.x, -yy.y));
-  const float2 t2 = __ffma2_rn(two, zz, make_float2(-xpy.x, -xpy.y));           // 2zz - xx - yy
-  const float2 t4 = __ffma2_rn(four, zz, make_float2(-xpy.x, -xpy.y));          // 4zz - xx - yy
-  const float2 t3 = __ffma2_rn(make_float2(-3.f, -3.f), xpy, __fmul2_rn(two, zz));  // 2zz - 3xx - 3yy
+  const float2 nxpy = make_float2(-xpy.x, -xpy.y), nyy = make_float2(-yy.x, -yy.y);
+  const float2 xmy = __fadd2_rn(xx, nyy);
+  const float2 t4 = __ffma2_rn(four, zz, nxpy);                                  // 4zz - xx - yy
   P[0] = make_float2(1.f, 1.f);
   P[1] = y; P[2] = z; P[3] = x;
-  P[4] = xy; P[5] = yz; P[6] = t2; P[7] = xz; P[8] = xmy;
-  P[9] = __fmul2_rn(y, __ffma2_rn(three, xx, make_float2(-yy.x, -yy.y)));        // y (3xx - yy)
+  P[4] = xy; P[5] = yz; P[6] = __ffma2_rn(two, zz, nxpy); P[7] = xz; P[8] = xmy; // 2zz - xx - yy
+  P[9] = __fmul2_rn(y, __ffma2_rn(three, xx, nyy));                              // y (3xx - yy)
   P[10] = __fmul2_rn(xy, z);
   P[11] = __fmul2_rn(y, t4);
-  P[12] = __fmul2_rn(z, t3);
+  P[12] = __fmul2_rn(z, __ffma2_rn(make_float2(-3.f, -3.f), xpy, __fmul2_rn(two, zz)));  // z (2zz - 3xx - 3yy)
   P[13] = __fmul2_rn(x, t4);
   P[14] = __fmul2_rn(z, xmy);
-  P[15] = __fmul2_rn(x, __ffma2_rn(make_float2(-3.f, -3.f), yy, xx));           // x (xx - 3yy)
+  P[15] = __fmul2_rn(x, __ffma2_rn(make_float2(-3.f, -3.f), yy, xx));            // x (xx - 3yy)
 }
 
 __constant__ float c_shc[16] = {SH_C0, -SH_C1, SH_C1, -SH_C1, SH_C2A, -SH_C2A, SH_C2B, -SH_C2A, SH_C2C,
                                 -SH_C3A, SH_C3B, -SH_C3C, SH_C3D, -SH_C3C, SH_C3E, -SH_C3A};
 
-// SH evaluation of one Gaussian for V views and the store in the requested order. x holds
-// the dequantised coefficients with the SH constants folded in; both decoders share this
-// code, so their colours agree bit for bit when their texels do.
+// SH evaluation of one Gaussian for V views and the store in the requested order. x holds the
+// dequantised coefficients with the SH constants folded in; both decoders share this code, so
+// their colours agree bit for bit when their texels do. Views go in pairs through the
+// two-lane multiply-adds (one coefficient against the basis of two views), four views at a
+// time (three 16-byte stores of a Gaussian-major row when V is a multiple of 4).
 template <bool CAMS>
 __device__ __forceinline__ void eval_store(const float (&xr)[16], const float (&xg)[16], const float (&xb)[16],
                                            int64_t o, int64_t s, float3 p, const float (*s_view)[64], int V,
                                            int out_order, int64_t n, int64_t ns, float* __restrict__ rgb) {
-  const float2 p0 = make_float2(p.x, p.x), p1 = make_float2(p.y, p.y), p2 = make_float2(p.z, p.z);
-  // views in chunks of 8: accumulate in registers, then store (16-byte vectors for whole
-  // Gaussian-major rows when V is a multiple of 4)
-  for (int v0 = 0; v0 < V; v0 += 8) {
-    float res[24];
+  const float2 np0 = make_float2(-p.x, -p.x), np1 = make_float2(-p.y, -p.y), np2 = make_float2(-p.z, -p.z);
+  for (int v0 = 0; v0 < V; v0 += 4) {
+    float res[12];
 #pragma unroll
-    for (int pr = 0; pr < 4; pr++) {
+    for (int pr = 0; pr < 2; pr++) {
       const int v = v0 + 2 * pr;
       if (v >= V) break;
       const int v1 = v + 1 < V ? v + 1 : v;
       float2 dx = make_float2(s_view[0][v], s_view[0][v1]);
       float2 dy = make_float2(s_view[1][v], s_view[1][v1]);
       float2 dz = make_float2(s_view[2][v], s_view[2][v1]);
-      if (CAMS) {
-        dx = __fadd2_rn(dx, make_float2(-p0.x, -p0.y));
-        dy = __fadd2_rn(dy, make_float2(-p1.x, -p1.y));
-        dz = __fadd2_rn(dz, make_float2(-p2.x, -p2.y));
-      }
+      if (CAMS) { dx = __fadd2_rn(dx, np0); dy = __fadd2_rn(dy, np1); dz = __fadd2_rn(dz, np2); }
       const float2 n2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
       float2 r;
       r.x = n2.x > 0.f ? rsqrtf(n2.x) : 0.f;
@@ -454,22 +515,22 @@ __device__ __forceinline__ void eval_store(const float (&xr)[16], const float (&
       res[6 * pr + 0] = ar.x; res[6 * pr + 1] = ag.x; res[6 * pr + 2] = ab.x;
       res[6 * pr + 3] = ar.y; res[6 * pr + 4] = ag.y; res[6 * pr + 5] = ab.y;
     }
-    const int nv = V - v0 < 8 ? V - v0 : 8;
+    const int nv = V - v0 < 4 ? V - v0 : 4;
     if (out_order == GSC_OUT_GAUSS_MAJOR && (V & 3) == 0) {
       float4* d = reinterpret_cast<float4*>(rgb + (o * V + v0) * 3);
-#pragma unroll
-      for (int q = 0; q < 6; q++)
-        if (4 * q < 3 * nv) d[q] = make_float4(res[4 * q], res[4 * q + 1], res[4 * q + 2], res[4 * q + 3]);
+      d[0] = make_float4(res[0], res[1], res[2], res[3]);
+      d[1] = make_float4(res[4], res[5], res[6], res[7]);
+      d[2] = make_float4(res[8], res[9], res[10], res[11]);
     } else if (out_order == GSC_OUT_GAUSS_MAJOR) {
       float* d = rgb + (o * V + v0) * 3;
 #pragma unroll
-      for (int q = 0; q < 24; q++)
+      for (int q = 0; q < 12; q++)
         if (q < 3 * nv) d[q] = res[q];
     } else {
       const int64_t idx = out_order == GSC_OUT_VIEW_MAJOR ? o : s;
       const int64_t stride = out_order == GSC_OUT_VIEW_MAJOR ? n : ns;
 #pragma unroll
-      for (int q = 0; q < 8; q++)
+      for (int q = 0; q < 4; q++)
         if (q < nv) {
           float* d = rgb + ((int64_t)(v0 + q) * stride + idx) * 3;
           d[0] = res[3 * q]; d[1] = res[3 * q + 1]; d[2] = res[3 * q + 2];
@@ -497,8 +558,9 @@ __global__ void __launch_bounds__(EVAL_THREADS) k_eval2(DevTable T, const uint8_
                                                int out_order, float* __restrict__ rgb) {
   __shared__ DecTables S;
   __shared__ uint32_t tile[EVAL_THREADS / 32][WTILE];
+  __shared__ uint4 s_ep[EVAL_THREADS][3];
   __shared__ float s_view[3][64];
-  __shared__ float s_deq[16];
+  __shared__ __align__(8) float s_deq[16];
   load_tables(&S);
   load_views(s_view, s_deq, dirs, cams, V, T);
   __syncthreads();
@@ -506,33 +568,65 @@ __global__ void __launch_bounds__(EVAL_THREADS) k_eval2(DevTable T, const uint8_
   const int64_t npairs = ((int64_t)T.n_groups + 1) / 2;
   const int64_t n = T.n, ns = (int64_t)T.n_groups * 16;
   uint32_t* my = tile[w] + gw * 272;
-  for (int64_t pr = (int64_t)blockIdx.x * nw + w; pr < npairs; pr += (int64_t)gridDim.x * nw) {
-    const int64_t g = pr * 2 + gw;
+  const int64_t step = (int64_t)gridDim.x * nw;
+  // software pipeline: slot order entries two iterations ahead, blocks and positions one ahead
+  auto group_of = [&](int64_t pr) { return pr * 2 + gw; };
+  auto perm_at = [&](int64_t pr) -> int32_t {
+    const int64_t g = group_of(pr);
+    return (pr < npairs && g < T.n_groups) ? __ldg(perm + g * 16 + kt) : -1;
+  };
+  auto pos_at = [&](int32_t o) -> float3 {
+    if (!CAMS || o < 0) return make_float3(0.f, 0.f, 0.f);
+    return make_float3(__ldg(pos + 3 * (int64_t)o), __ldg(pos + 3 * (int64_t)o + 1), __ldg(pos + 3 * (int64_t)o + 2));
+  };
+  int64_t pr = (int64_t)blockIdx.x * nw + w;
+  RawBlock raw;
+  raw.kind = 0;
+  raw.w = make_uint4(0u, 0u, 0u, 0u);
+  if (pr < npairs && group_of(pr) < T.n_groups) raw = fetch_block<KIND>(T, blocks, group_of(pr), kt);
+  int32_t o = perm_at(pr), o1 = perm_at(pr + step);
+  float3 p = pos_at(o);
+  for (; pr < npairs; pr += step) {
+    const int64_t g = group_of(pr);
     const bool live = g < T.n_groups;
+    // loads for the next iterations
+    const int64_t prn = pr + step;
+    RawBlock rawn;
+    rawn.kind = 0;
+    rawn.w = make_uint4(0u, 0u, 0u, 0u);
+    if (prn < npairs && group_of(prn) < T.n_groups) rawn = fetch_block<KIND>(T, blocks, group_of(prn), kt);
+    const float3 pn = pos_at(o1);
+    const int32_t o2 = perm_at(prn + step);
     {
       uint32_t tx[16];
-      if (live) block_texels<KIND>(T, blocks, g, kt, tx, &S);
+      decode_raw<KIND>(raw, tx, &S, s_ep[threadIdx.x]);  // past the last group: never read back
 #pragma unroll
-      for (int t = 0; t < 16; t++) my[17 * kt + t] = live ? tx[t] : 0u;
+      for (int t = 0; t < 16; t++) my[17 * kt + t] = tx[t];
     }
     __syncwarp();
     const int64_t s = g * 16 + kt;
-    const int32_t o = live ? __ldg(perm + s) : -1;
     if (o >= 0) {
+      // (q - 128) * f_k for two consecutive k at once: 0x4B0000qq is 2^23 + q exactly
       float xr[16], xg[16], xb[16];
+      const float2 m = make_float2(-8388736.0f, -8388736.0f);
 #pragma unroll
-      for (int k = 0; k < 16; k++) {
-        const uint32_t px = my[17 * k + kt];
-        const float f = s_deq[k];
-        xr[k] = byte_m128(px, 0) * f; xg[k] = byte_m128(px, 1) * f; xb[k] = byte_m128(px, 2) * f;
+      for (int j = 0; j < 8; j++) {
+        const uint32_t p0 = my[17 * (2 * j) + kt], p1 = my[17 * (2 * j + 1) + kt];
+        const float2 f = *reinterpret_cast<const float2*>(s_deq + 2 * j);
+        const float2 r = __fmul2_rn(__fadd2_rn(make_float2(u23(p0, 0), u23(p1, 0)), m), f);
+        const float2 gg = __fmul2_rn(__fadd2_rn(make_float2(u23(p0, 1), u23(p1, 1)), m), f);
+        const float2 b = __fmul2_rn(__fadd2_rn(make_float2(u23(p0, 2), u23(p1, 2)), m), f);
+        xr[2 * j] = r.x; xr[2 * j + 1] = r.y; xg[2 * j] = gg.x; xg[2 * j + 1] = gg.y; xb[2 * j] = b.x; xb[2 * j + 1] = b.y;
       }
-      float3 p = make_float3(0.f, 0.f, 0.f);
-      if (CAMS) p = make_float3(__ldg(pos + 3 * (int64_t)o), __ldg(pos + 3 * (int64_t)o + 1), __ldg(pos + 3 * (int64_t)o + 2));
       eval_store<CAMS>(xr, xg, xb, o, s, p, s_view, V, out_order, n, ns, rgb);
     } else if (live && out_order == GSC_OUT_SLOT_ORDER) {
       for (int v = 0; v < V; v++) { float* d = rgb + ((int64_t)v * ns + s) * 3; d[0] = d[1] = d[2] = 0.f; }
     }
     __syncwarp();
+    raw = rawn;
+    p = pn;
+    o = o1;
+    o1 = o2;
   }
 }
 
@@ -861,12 +955,27 @@ __global__ void __launch_bounds__(256) k_eval_tex(DevTable T, TexBases B, cudaTe
                                                   const float* __restrict__ cams, int V, int out_order,
                                                   float* __restrict__ rgb, const float4* __restrict__ pos_slot) {
   __shared__ float s_view[3][64];
-  __shared__ float s_deq[16];
+  __shared__ __align__(8) float s_deq[16];
   load_views(s_view, s_deq, dirs, cams, V, T);
   __syncthreads();
   const int64_t n = T.n, ns = (int64_t)T.n_groups * 16;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t o = __ldg(perm + s);
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  // the slot's Gaussian and position are loaded one iteration ahead
+  auto pos_of = [&](int64_t s, int32_t o) -> float3 {
+    if (!CAMS || o < 0) return make_float3(0.f, 0.f, 0.f);
+    if (pos_slot) { const float4 q4 = __ldg(pos_slot + s); return make_float3(q4.x, q4.y, q4.z); }
+    return make_float3(__ldg(pos + 3 * (int64_t)o), __ldg(pos + 3 * (int64_t)o + 1), __ldg(pos + 3 * (int64_t)o + 2));
+  };
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int32_t o_n = s < ns ? __ldg(perm + s) : -1;
+  float3 p_n = pos_of(s, o_n);
+  for (; s < ns; s += step) {
+    const int32_t o = o_n;
+    const float3 p = p_n;
+    if (s + step < ns) {
+      o_n = __ldg(perm + s + step);
+      p_n = pos_of(s + step, o_n);
+    }
     if (o < 0) {
       if (out_order == GSC_OUT_SLOT_ORDER)
         for (int v = 0; v < V; v++) { float* d = rgb + ((int64_t)v * ns + s) * 3; d[0] = d[1] = d[2] = 0.f; }
@@ -893,13 +1002,9 @@ __global__ void __launch_bounds__(256) k_eval_tex(DevTable T, TexBases B, cudaTe
       } else {
         f = make_float4(128.f / 255.f, 128.f / 255.f, 128.f / 255.f, 1.f);
       }
+      // exact q - 128 from the unorm value, into the pair slot of k
       const float q = s_deq[k];
-      xr[k] = unorm_m128(f.x) * q; xg[k] = unorm_m128(f.y) * q; xb[k] = unorm_m128(f.z) * q;
-    }
-    float3 p = make_float3(0.f, 0.f, 0.f);
-    if (CAMS) {
-      if (pos_slot) { const float4 q4 = __ldg(pos_slot + s); p = make_float3(q4.x, q4.y, q4.z); }
-      else p = make_float3(__ldg(pos + 3 * (int64_t)o), __ldg(pos + 3 * (int64_t)o + 1), __ldg(pos + 3 * (int64_t)o + 2));
+      xr[k] = __fmul_rn(unorm_m128(f.x), q); xg[k] = __fmul_rn(unorm_m128(f.y), q); xb[k] = __fmul_rn(unorm_m128(f.z), q);
     }
     eval_store<CAMS>(xr, xg, xb, o, s, p, s_view, V, out_order, n, ns, rgb);
   }
