@@ -138,17 +138,20 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
     if (NCH >= 3) { s2[1] += c[0] * c[NCH >= 3 ? 2 : 0]; s2[2] += c[NCH >= 2 ? 1 : 0] * c[NCH >= 3 ? 2 : 0]; }
   }
   if (n == 0) return 0;
-  int ref = 0;
+  // reference channel = widest range (first on ties); selects, not indexing, keep the
+  // per-channel sums in registers
+  int ref = 0, rw = hi[0] - lo[0], s1r = s1[0];
 #pragma unroll
-  for (int i = 1; i < NCH; i++) if (hi[i] - lo[i] > hi[ref] - lo[ref]) ref = i;
+  for (int i = 1; i < NCH; i++)
+    if (hi[i] - lo[i] > rw) { rw = hi[i] - lo[i]; ref = i; s1r = s1[i]; }
 #pragma unroll
   for (int i = 0; i < NCH; i++) {
-    bool flip = false;
-    if (i != ref) {
-      const int a = min(i, ref), b = max(i, ref);
-      const int cross = (a == 0 && b == 1) ? s2[0] : ((a == 0 && b == 2) ? s2[1] : s2[2]);
-      flip = (n * cross - s1[ref] * s1[i]) < 0;
-    }
+    // cross sum of channels i and ref: pairs (0,1), (0,2), (1,2) are s2[0], s2[1], s2[2]
+    int cross;
+    if (i == 0) cross = ref == 1 ? s2[0] : s2[1];
+    else if (i == 1) cross = ref == 0 ? s2[0] : s2[2];
+    else cross = ref == 0 ? s2[1] : s2[2];
+    const bool flip = i != ref && (n * cross - s1r * s1[i]) < 0;
     e0[i] = flip ? lo[i] : hi[i];
     e1[i] = flip ? hi[i] : lo[i];
   }
