@@ -108,8 +108,11 @@ __device__ __forceinline__ int best_key(uint32_t v, const uint32_t (&pal)[F], co
 
 // Stage 1 of a subset fit: bounding-box diagonal oriented by covariance signs, indices
 // against the unquantised palette, one least-squares refinement. Returns the member count.
+// `sel` permutes each texel's bytes on load (identity by default); the rotation search uses it
+// to move the rotated channel to byte 2, keeping the other two in their order.
 template <int IB, int CHMASK>
-__device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t part, int s, int (&e0)[3], int (&e1)[3]) {
+__device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t part, int s, int (&e0)[3], int (&e1)[3],
+                                      uint32_t sel = 0x3210u) {
   constexpr int F = 1 << IB;
   constexpr int NCH = ((CHMASK >> 0) & 1) + ((CHMASK >> 1) & 1) + ((CHMASK >> 2) & 1);
   constexpr uint32_t CM = ((CHMASK & 1) ? 0xFFu : 0u) | ((CHMASK & 2) ? 0xFF00u : 0u) | ((CHMASK & 4) ? 0xFF0000u : 0u);
@@ -126,7 +129,7 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
 #pragma unroll 4
   for (int t = 0; t < 16; t++) {
     if ((int)((part >> (2 * t)) & 3) != s) continue;
-    const uint32_t v = tex[t * STAGE_STRIDE];
+    const uint32_t v = __byte_perm(tex[t * STAGE_STRIDE], 0u, sel);
     n++;
     int c[NCH];
 #pragma unroll
@@ -172,7 +175,7 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
 #pragma unroll 2
     for (int t = 0; t < 16; t++) {
       if ((int)((part >> (2 * t)) & 3) != s) continue;
-      const uint32_t v = tex[t * STAGE_STRIDE] & CM;
+      const uint32_t v = __byte_perm(tex[t * STAGE_STRIDE], 0u, sel) & CM;
       const int bj = best_key<F>(v, pal, pk) & 15;
       const int w = wgt<IB>(bj), a = 64 - w;
       saa += a * a; sbb += w * w; sab += a * w;
@@ -196,7 +199,7 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
 template <int IB, int CHMASK, int PT, int BITS, bool OUT>
 __device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex, uint32_t part, int s,
                                                const int (&e0)[3], const int (&e1)[3], FitOut* out,
-                                               const uint16_t* __restrict__ sq) {
+                                               const uint16_t* __restrict__ sq, uint32_t sel = 0x3210u) {
   constexpr int F = 1 << IB;
   constexpr int NCH = ((CHMASK >> 0) & 1) + ((CHMASK >> 1) & 1) + ((CHMASK >> 2) & 1);
   constexpr uint32_t CM = ((CHMASK & 1) ? 0xFFu : 0u) | ((CHMASK & 2) ? 0xFF00u : 0u) | ((CHMASK & 4) ? 0xFF0000u : 0u);
@@ -235,7 +238,7 @@ __device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex,
 #pragma unroll 2
     for (int t = 0; t < 16; t++) {
       if ((int)((part >> (2 * t)) & 3) != s) continue;
-      const uint32_t v = tex[t * STAGE_STRIDE] & CM;
+      const uint32_t v = __byte_perm(tex[t * STAGE_STRIDE], 0u, sel) & CM;
       const int key = best_key<F>(v, pal, pk);
       sse += (int)__dp4a(v, v, 0u) + (key >> 4);
       if (OUT) { if (t < 8) il |= (uint32_t)(key & 15) << (4 * t); else ih |= (uint32_t)(key & 15) << (4 * (t - 8)); }
@@ -255,21 +258,23 @@ __device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex,
 // Full subset fit = prefit + quant_eval.
 template <int IB, int CHMASK, int PT, int BITS, bool OUT>
 __device__ __forceinline__ uint32_t fit_subset(const uint32_t* __restrict__ tex, uint32_t part, int s, FitOut* out,
-                                               const uint16_t* __restrict__ sq) {
+                                               const uint16_t* __restrict__ sq, uint32_t sel = 0x3210u) {
   if (OUT) { out->idx_lo = 0; out->idx_hi = 0; out->p[0] = out->p[1] = 0;
 #pragma unroll
     for (int i = 0; i < 3; i++) out->code[0][i] = out->code[1][i] = 0; }
   int e0[3] = {0, 0, 0}, e1[3] = {0, 0, 0};
-  if (prefit<IB, CHMASK>(tex, part, s, e0, e1) == 0) return 0;
-  return quant_eval<IB, CHMASK, PT, BITS, OUT>(tex, part, s, e0, e1, out, sq);
+  if (prefit<IB, CHMASK>(tex, part, s, e0, e1, sel) == 0) return 0;
+  return quant_eval<IB, CHMASK, PT, BITS, OUT>(tex, part, s, e0, e1, out, sq, sel);
 }
 
 // ---- candidate scoring (search phase) ----------------------------------------------
+// Subsets in a rolled loop: one copy of the fit code per mode keeps the search's instruction
+// footprint small (warps at different candidates share the instruction cache).
 template <int NS, int IB, int PT, int BITS>
 __device__ __forceinline__ uint32_t score_part(const uint32_t* tex, uint32_t part, const uint16_t* sq) {
-  uint32_t s = fit_subset<IB, 7, PT, BITS, false>(tex, part, 0, nullptr, sq);
-  if (NS > 1) s += fit_subset<IB, 7, PT, BITS, false>(tex, part, 1, nullptr, sq);
-  if (NS > 2) s += fit_subset<IB, 7, PT, BITS, false>(tex, part, 2, nullptr, sq);
+  uint32_t s = 0;
+#pragma unroll 1
+  for (int sub = 0; sub < NS; sub++) s += fit_subset<IB, 7, PT, BITS, false>(tex, part, sub, nullptr, sq);
   return s;
 }
 
@@ -291,6 +296,23 @@ __device__ __forceinline__ uint32_t score_rot(const uint32_t* tex, FitOut* oc, F
   return s;
 }
 
+// Search-only form of score_rot for rotations 1-3: the texels' bytes are permuted so that
+// the rotated channel sits in byte 2 and the colour channels keep their order in bytes 0-1;
+// the errors equal score_rot's (every step of the fit is symmetric in the channel positions,
+// and the order of the colour channels, which decides ties, is kept).
+template <int MODE, int ISB>
+__device__ __forceinline__ uint32_t score_rot_n(const uint32_t* tex, uint32_t sel, const uint16_t* sq) {
+  constexpr int CB = MODE == 4 ? 5 : 7, AB = MODE == 4 ? 6 : 8;
+  constexpr int CIB = MODE == 4 ? (ISB ? 3 : 2) : 2, AIB = MODE == 4 ? (ISB ? 2 : 3) : 2;
+  return fit_subset<CIB, 3, PT_NONE, CB, false>(tex, 0u, 0, nullptr, sq, sel) +
+         fit_subset<AIB, 4, PT_NONE, AB, false>(tex, 0u, 0, nullptr, sq, sel);
+}
+
+__device__ __forceinline__ uint32_t rot_sel(int rot) {
+  // byte 2 <- rotated channel; bytes 0-1 <- the other two in order; byte 3 <- 0
+  return rot == 1 ? 0x4021u : (rot == 2 ? 0x4120u : 0x4210u);
+}
+
 __device__ __noinline__ int search_best(const uint32_t* tex, uint32_t* best_sse, const uint16_t* sq) {
   uint32_t best = 0xFFFFFFFFu;
   int be = 0;
@@ -308,7 +330,7 @@ __device__ __noinline__ int search_best(const uint32_t* tex, uint32_t* best_sse,
   for (int p = 0; p < 64; p++) {
     const uint32_t part = c_part2[p];
     uint32_t s3 = 0, s7 = 0;
-#pragma unroll
+#pragma unroll 1
     for (int sub = 0; sub < 2; sub++) {
       int e0[3] = {0, 0, 0}, e1[3] = {0, 0, 0};
       if (prefit<2, 7>(tex, part, sub, e0, e1) == 0) continue;
@@ -320,16 +342,14 @@ __device__ __noinline__ int search_best(const uint32_t* tex, uint32_t* best_sse,
   }
   CAND((score_rot<4, 0, 0>(tex, nullptr, nullptr, sq)), 208);
   CAND((score_rot<4, 0, 1>(tex, nullptr, nullptr, sq)), 209);
-  CAND((score_rot<4, 1, 0>(tex, nullptr, nullptr, sq)), 210);
-  CAND((score_rot<4, 1, 1>(tex, nullptr, nullptr, sq)), 211);
-  CAND((score_rot<4, 2, 0>(tex, nullptr, nullptr, sq)), 212);
-  CAND((score_rot<4, 2, 1>(tex, nullptr, nullptr, sq)), 213);
-  CAND((score_rot<4, 3, 0>(tex, nullptr, nullptr, sq)), 214);
-  CAND((score_rot<4, 3, 1>(tex, nullptr, nullptr, sq)), 215);
   CAND((score_rot<5, 0, 0>(tex, nullptr, nullptr, sq)), 216);
-  CAND((score_rot<5, 1, 0>(tex, nullptr, nullptr, sq)), 217);
-  CAND((score_rot<5, 2, 0>(tex, nullptr, nullptr, sq)), 218);
-  CAND((score_rot<5, 3, 0>(tex, nullptr, nullptr, sq)), 219);
+#pragma unroll 1
+  for (int rot = 1; rot <= 3; rot++) {
+    const uint32_t sel = rot_sel(rot);
+    CAND((score_rot_n<4, 0>(tex, sel, sq)), 208 + 2 * rot);
+    CAND((score_rot_n<4, 1>(tex, sel, sq)), 209 + 2 * rot);
+    CAND((score_rot_n<5, 0>(tex, sel, sq)), 216 + rot);
+  }
   CAND((score_part<1, 4, PT_UNIQUE, 7>(tex, 0u, sq)), 220);
 #undef CAND
   *best_sse = best;
