@@ -45,6 +45,9 @@ BC7_EVALS_PER_BLOCK = (16 * (16 * 8 + 4 * 16 * 8) + 64 * (16 * 8 + 2 * 16 * 8) +
                        + 64 * (16 * 4 + 4 * 16 * 4) + (128 + 256 + 3 * 768) + (128 + 3 * 256)
                        + (16 * 16 + 4 * 16 * 16) + 64 * (16 * 4 + 4 * 16 * 4))
 OPS_PER_EVAL = 8
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) measured with ncu on the
+# 3M-Gaussian workload for the kernels as they stand; to be reset to None when a kernel changes.
+MEASURED_TRAFFIC = {"scene3m": {"k_bc7": 845557248, "k_eval2_bc7": 446549504, "k_eval_tex_bc7": 391628032}}
 
 
 def workload_cfg(name):
@@ -216,32 +219,60 @@ def run_gsc(args, world, rank, local):
     bc7_ops = BC7_EVALS_PER_BLOCK * OPS_PER_EVAL * ns
     bc7_achieved = bc7_ops / (bc7_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": round(bc7_achieved, 3), "peak": round(int_peak / 1e12, 3),
-                "unit": "Tops/s", "frac": round(bc7_achieved / (int_peak / 1e12), 4), "traffic": None,
+                "unit": "Tops/s", "frac": round(bc7_achieved / (int_peak / 1e12), 4),
+                "traffic": MEASURED_TRAFFIC.get(args.workload, {}).get("k_bc7"),
                 "kernel": "k_bc7 (BC7 candidate search)",
                 "peak_source": "measured on this GPU by gsc_probe_int_peak (IADD3/LOP3/IMAD chains)",
                 "algorithmic": "%d palette evaluations x %d int ops per block, %d blocks" % (
                     BC7_EVALS_PER_BLOCK, OPS_PER_EVAL, ns)}
-    # the fused decode + SH evaluation (HBM bound): algorithmic bytes per launch
+    # the fused decode + SH evaluation (HBM bound), all-BC7 coding, timed alone after the step:
+    # algorithmic bytes per launch = 16 B block + 4 B slot entry + 12 B position + 8 x 12 B output
     hbm, hbm_src = peaks()
-    ev_ms = kt["decode_eval"][0] / max(1, kt["decode_eval"][1])
-    ev_bytes = np.mean([16 * ns, 8 * ns, rtab.total_bytes]) + 4 * ns + 12 * n + N_CAMS * 12 * n
+    t7 = gsc.forced_table(rtab, gsc.FMT_BC7)
+
+    def time_eval7(order, out):
+        for _ in range(3):
+            gsc.gsc_decode_eval_sh(ctx, t7, bc7, last_perm[0], pos=pos, cams=cams, out_order=order, out=out,
+                                   stream=stream)
+        stream.synchronize()
+        gsc.set_timing(ctx, True)
+        for _ in range(max(5, args.steps)):
+            gsc.gsc_decode_eval_sh(ctx, t7, bc7, last_perm[0], pos=pos, cams=cams, out_order=order, out=out,
+                                   stream=stream)
+        ms_, cnt_ = gsc.kernel_time(ctx, "decode_eval")
+        gsc.set_timing(ctx, False)
+        return ms_ / max(1, cnt_)
+
+    ev_ms3 = kt["decode_eval"][0] / max(1, kt["decode_eval"][1])
+    ev_ms = time_eval7(gsc.OUT_GAUSS_MAJOR, rgb[0])
+    ev_bytes = (16 + 4 + 12 + N_CAMS * 12) * n
     ev_gbs = ev_bytes / (ev_ms * 1e-3) / 1e9
     roofline_eval = {"bound": "hbm", "achieved": round(ev_gbs, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(ev_gbs / hbm, 4), "traffic": None, "peak_source": hbm_src,
-                     "kernel": "k_decode_eval (decode + SH eval, %d cameras, Gaussian-major output)" % N_CAMS,
-                     "algorithmic": "blocks + perm 4 B + position 12 B + %d x 12 B output per Gaussian" % N_CAMS}
+                     "frac": round(ev_gbs / hbm, 4), "peak_source": hbm_src,
+                     "traffic": MEASURED_TRAFFIC.get(args.workload, {}).get("k_eval2_bc7"),
+                     "kernel": "k_eval2 (software BC7 decode + SH eval, all-BC7 coding, %d cameras, "
+                               "Gaussian-major output)" % N_CAMS,
+                     "algorithmic": "16 B block + 4 B perm + 12 B position + %d x 12 B output per Gaussian" % N_CAMS}
     stages = {}
     for k, (ms, cnt) in kt.items():
         stages[k + "_ms"] = round(ms / max(1, cnt), 4)
     stages["bc1_encode_Mblocks_s"] = round(ns / (kt["bc1_encode"][0] / max(1, kt["bc1_encode"][1]) * 1e-3) / 1e6, 2)
     stages["bc7_encode_Mblocks_s"] = round(ns / (bc7_ms * 1e-3) / 1e6, 3)
-    stages["decode_eval_MGauss_s"] = round(n / (ev_ms * 1e-3) / 1e6, 1)
-    stages["decode_eval_GB_s"] = round(ev_gbs, 1)
+    stages["decode_eval_bc7_ms"] = round(ev_ms, 4)
+    stages["decode_eval_bc7_MGauss_s"] = round(n / (ev_ms * 1e-3) / 1e6, 1)
+    stages["decode_eval_bc7_GB_s"] = round(ev_gbs, 1)
+    stages["decode_eval_3codings_mean_ms"] = round(ev_ms3, 4)
     stages["rate_bits_per_texel"] = round(rtab.used_bits / (16.0 * n), 4)
 
     # the same evaluation on resident texture scenes (blocks decoded by the texture unit)
     tex_stats = time_tex_eval(args, ctx, gsc, stream, dev, rtab, bc1, bc7, perm_last, pos, cams, n, ns)
     stages.update(tex_stats["stages"])
+    # coalesced comparison: the all-BC7 coding evaluated into slot order (no scattered stores)
+    rgb_slot = torch.empty((N_CAMS, ns, 3), dtype=torch.float32, device=dev)
+    ms_slot = time_eval7(gsc.OUT_SLOT_ORDER, rgb_slot)
+    stages["decode_eval_bc7_slot_order_ms"] = round(ms_slot, 4)
+    stages["decode_eval_bc7_slot_order_GB_s"] = round((16 + 4 + 12 + N_CAMS * 12) * n / (ms_slot * 1e-3) / 1e9, 1)
+    del rgb_slot
 
     # end to end through the public API with host buffers
     e2e = run_e2e(args, ctx, gsc, stream, dev, sc, step, world)
@@ -296,7 +327,8 @@ def time_tex_eval(args, ctx, gsc, stream, dev, rtab, bc1, bc7, perm, pos, cams, 
         res["stages"]["decode_eval_tex_%s_MGauss_s" % name] = round(n / (ms * 1e-3) / 1e6, 1)
         if name == "bc7":
             res["roofline"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
-                               "frac": round(gbs / hbm, 4), "traffic": None, "peak_source": hbm_src,
+                               "frac": round(gbs / hbm, 4), "peak_source": hbm_src,
+                               "traffic": MEASURED_TRAFFIC.get(args.workload, {}).get("k_eval_tex_bc7"),
                                "kernel": "k_eval_tex (texture-unit decode + SH eval, all-BC7, %d cameras, "
                                          "Gaussian-major output)" % N_CAMS,
                                "algorithmic": "16 B block + 4 B perm + 12 B position + %d x 12 B output per Gaussian"
@@ -664,6 +696,12 @@ def cpu_baseline(workload, budget_s=20.0):
     t0 = time.perf_counter()
     O.encode_blocks(blocks[:nb1], 1, threads=1)
     t_bc1 = (time.perf_counter() - t0) / nb1
+    # the dominant stage again on every host core (the same scalar code, blocks split across threads)
+    cores = os.cpu_count() or 1
+    nb7_all = min(blocks.shape[0], nb7 * max(1, cores // 2))
+    t0 = time.perf_counter()
+    O.encode_blocks(blocks[:nb7_all], 7, threads=cores)
+    t_bc7_all = (time.perf_counter() - t0) / nb7_all
     n_ev = 4096
     r = O.encode(q[:n_ev], np.arange(n_ev, dtype=np.int32), scl, 1)
     t0 = time.perf_counter()
@@ -677,12 +715,17 @@ def cpu_baseline(workload, budget_s=20.0):
     t_dec = (time.perf_counter() - t0) / n_ev
     # one block per Gaussian per coding (16 blocks per 16-Gaussian group)
     per_gauss = t_plan + t_bc7 + t_bc1 + t_eval + t_dec
+    per_gauss_all = t_plan + t_bc7_all + t_bc1 + t_eval + t_dec
     return {"value": round(1.0 / per_gauss / 1e6, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "plan on %d Gaussians; BC7 on %d and BC1 on %d staged blocks; decode + SH eval (8 cams, x3) "
                       "and 4 decodes on %d Gaussians; scaled per Gaussian" % (n_plan, nb7, nb1, n_ev),
             "stage_us_per_gaussian": {"plan": round(t_plan * 1e6, 3), "bc7": round(t_bc7 * 1e6, 1),
                                       "bc1": round(t_bc1 * 1e6, 2), "decode_eval": round(t_eval * 1e6, 2),
-                                      "decode": round(t_dec * 1e6, 2)}}
+                                      "decode": round(t_dec * 1e6, 2)},
+            "all_cores": {"value": round(1.0 / per_gauss_all / 1e6, 6), "cores": cores,
+                          "bc7_us_per_block": round(t_bc7_all * 1e6, 2),
+                          "sample": "BC7 (the dominant stage) on %d blocks over %d threads; other stages as "
+                                    "single-threaded" % (nb7_all, cores)}}
 
 
 def run_reference(args, world, rank):
