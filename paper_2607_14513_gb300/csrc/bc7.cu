@@ -94,6 +94,23 @@ struct FitOut {
 // (key & 15) and that error minus |v|^2 (key >> 4, an exact floor shift).
 __device__ __forceinline__ uint32_t pack_rgb(int r, int g, int b) { return (uint32_t)r | ((uint32_t)g << 8) | ((uint32_t)b << 16); }
 
+// Palette of F entries between endpoints a and b (R, G, B; uncoded channels 0) with BC7 weights,
+// and its keys. Two channels share one multiply-add in 16-bit lanes scaled by 4, so byte 1 of
+// each lane is ((64 - w) a + w b + 32) >> 6 exactly.
+template <int IB>
+__device__ __forceinline__ void build_pal(const int (&a)[3], const int (&b)[3], uint32_t (&pal)[1 << IB],
+                                          int (&pk)[1 << IB]) {
+  const uint32_t A = ((uint32_t)a[0] | ((uint32_t)a[1] << 16)) << 2, B = ((uint32_t)b[0] | ((uint32_t)b[1] << 16)) << 2;
+  const uint32_t Ab = (uint32_t)a[2] << 2, Bb = (uint32_t)b[2] << 2;
+#pragma unroll
+  for (int j = 0; j < (1 << IB); j++) {
+    const uint32_t w = (uint32_t)wgt<IB>(j);
+    const uint32_t rg = (64u - w) * A + w * B + 0x00800080u, bb = (64u - w) * Ab + w * Bb + 0x80u;
+    pal[j] = __byte_perm(rg, bb, 0x7531u);
+    pk[j] = 16 * (int)__dp4a(pal[j], pal[j], 0u) + j;
+  }
+}
+
 template <int F>
 __device__ __forceinline__ int best_key(uint32_t v, const uint32_t (&pal)[F], const int (&pk)[F]) {
   int k[F];
@@ -162,13 +179,11 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
   {
     uint32_t pal[F];
     int pk[F];
+    {
+      int a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
 #pragma unroll
-    for (int j = 0; j < F; j++) {
-      int cc[3] = {0, 0, 0};
-#pragma unroll
-      for (int i = 0; i < NCH; i++) cc[ch[i]] = interp64(e0[i], e1[i], wgt<IB>(j));
-      pal[j] = pack_rgb(cc[0], cc[1], cc[2]);
-      pk[j] = 16 * (int)__dp4a(pal[j], pal[j], 0u) + j;
+      for (int i = 0; i < NCH; i++) { a[ch[i]] = e0[i]; b[ch[i]] = e1[i]; }
+      build_pal<IB>(a, b, pal, pk);
     }
 #pragma unroll
     for (int i = 0; i < NCH; i++) { sav[i] = 0; sbv[i] = 0; }
@@ -227,12 +242,7 @@ __device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex,
     }
     uint32_t pal[F];
     int pk[F];
-#pragma unroll
-    for (int j = 0; j < F; j++) {
-      const int w = wgt<IB>(j);
-      pal[j] = pack_rgb(interp64(v0[0], v1[0], w), interp64(v0[1], v1[1], w), interp64(v0[2], v1[2], w)) & CM;
-      pk[j] = 16 * (int)__dp4a(pal[j], pal[j], 0u) + j;
-    }
+    build_pal<IB>(v0, v1, pal, pk);  // uncoded channels have zero endpoints, so their bytes are 0
     int sse = 0;
     uint32_t il = 0, ih = 0;
 #pragma unroll 2

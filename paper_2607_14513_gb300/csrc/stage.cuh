@@ -60,9 +60,12 @@ __device__ __forceinline__ int round_div_clamp255(long long num, long long den) 
   if (num < 0) return 0;
   long long N = 2 * num + den, D = 2 * den;
   if (N >= 256 * D) return 255;
-  int q = (int)__fdiv_rn((float)N, (float)D);
+  // N / D < 256 and both conversions and the approximate quotient carry a relative error of a few
+  // 2^-24, so the estimate is within 1e-3 of the true quotient: its floor is off by at most one,
+  // and one exact step each way lands on floor(N / D)
+  int q = (int)__fdividef((float)N, (float)D);
   q = min(max(q, 0), 255);
-  while (q > 0 && (long long)q * D > N) q--;
-  while (q < 255 && (long long)(q + 1) * D <= N) q++;
+  if (q > 0 && (long long)q * D > N) q--;
+  if (q < 255 && (long long)(q + 1) * D <= N) q++;
   return q;
 }
