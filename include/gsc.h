@@ -223,7 +223,7 @@ typedef struct {
 
 /* How the encode launch hands out work: schedule 0 = static round robin over tiles, 1 = atomic
  * work queue, 2 = atomic queue, 3 = one CTA per tile; schedules other than 1 list the scenes by
- * decreasing cost. CTAs per SM 1..32 (schedules 0-2; above the 4 that fit, the grid is
+ * decreasing cost. CTAs per SM 1..32 (schedules 0-2; above the 5 that fit, the grid is
  * oversubscribed and the hardware block scheduler balances); groups per BC1 tile (multiple of
  * 8; BC7 tiles are 8 groups). The plans of the scenes run on 4 streams at once. */
 typedef struct {

@@ -297,11 +297,11 @@ extern "C" gsc_status gsc_batch_autotune(gsc_ctx* c, gsc_batch_scene* sc, int32_
   GSC_CUDA(cudaEventCreate(&e0));
   GSC_CUDA(cudaEventCreate(&e1));
   double best = 1e30;
-  gsc_batch_tuning bt = {1, 4, 8};
+  gsc_batch_tuning bt = {1, 5, 8};
   // candidates: resident grids (1..4 CTAs per SM) with work queues, oversubscribed round-robin
   // grids (8..32 CTAs per SM, the hardware balances), one CTA per tile; BC1 tiles of 8 or 32
-  static const gsc_batch_tuning kCand[] = {{1, 4, 8}, {2, 4, 8}, {2, 3, 8}, {2, 4, 32}, {0, 8, 8},
-                                           {0, 16, 8}, {0, 32, 8}, {0, 32, 32}, {3, 4, 8}};
+  static const gsc_batch_tuning kCand[] = {{1, 5, 8}, {2, 5, 8}, {2, 4, 8}, {2, 5, 32}, {0, 10, 8},
+                                           {0, 16, 8}, {0, 32, 8}, {0, 32, 32}, {3, 5, 8}};
   for (const gsc_batch_tuning& t : kCand) {
     int64_t n_tiles[2] = {0, 0};
     std::vector<BatchSceneDev> v = scene_list(sc, n, B, t, kProxyDiv, n_tiles);
