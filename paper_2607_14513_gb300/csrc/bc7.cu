@@ -123,6 +123,12 @@ __device__ __forceinline__ int best_key(uint32_t v, const uint32_t (&pal)[F], co
   return k[0];
 }
 
+// Bit 2t set for every texel t of subset s of a partition (2 bits per texel).
+__device__ __forceinline__ uint32_t member_mask(uint32_t part, int s) {
+  const uint32_t x = part ^ ((uint32_t)s * 0x55555555u);
+  return ~(x | (x >> 1)) & 0x55555555u;
+}
+
 // Stage 1 of a subset fit: bounding-box diagonal oriented by covariance signs, indices
 // against the unquantised palette, one least-squares refinement. Returns the member count.
 // `sel` permutes each texel's bytes on load (identity by default); the rotation search uses it
@@ -143,9 +149,10 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
 #pragma unroll
   for (int i = 0; i < NCH; i++) { lo[i] = 255; hi[i] = 0; s1[i] = 0; }
   s2[0] = s2[1] = s2[2] = 0;  // channel pairs (0,1), (0,2), (1,2) of the coded channels
-#pragma unroll 4
-  for (int t = 0; t < 16; t++) {
-    if ((int)((part >> (2 * t)) & 3) != s) continue;
+  // member texels only, in increasing order (the mask is the same for every lane)
+  const uint32_t mm = member_mask(part, s);
+  for (uint32_t m = mm; m; m &= m - 1) {
+    const int t = (__ffs(m) - 1) >> 1;
     const uint32_t v = __byte_perm(tex[t * STAGE_STRIDE], 0u, sel);
     n++;
     int c[NCH];
@@ -187,9 +194,8 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
     }
 #pragma unroll
     for (int i = 0; i < NCH; i++) { sav[i] = 0; sbv[i] = 0; }
-#pragma unroll 2
-    for (int t = 0; t < 16; t++) {
-      if ((int)((part >> (2 * t)) & 3) != s) continue;
+    for (uint32_t m = mm; m; m &= m - 1) {
+      const int t = (__ffs(m) - 1) >> 1;
       const uint32_t v = __byte_perm(tex[t * STAGE_STRIDE], 0u, sel) & CM;
       const int bj = best_key<F>(v, pal, pk) & 15;
       const int w = wgt<IB>(bj), a = 64 - w;
@@ -245,9 +251,8 @@ __device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex,
     build_pal<IB>(v0, v1, pal, pk);  // uncoded channels have zero endpoints, so their bytes are 0
     int sse = 0;
     uint32_t il = 0, ih = 0;
-#pragma unroll 2
-    for (int t = 0; t < 16; t++) {
-      if ((int)((part >> (2 * t)) & 3) != s) continue;
+    for (uint32_t m = member_mask(part, s); m; m &= m - 1) {
+      const int t = (__ffs(m) - 1) >> 1;
       const uint32_t v = __byte_perm(tex[t * STAGE_STRIDE], 0u, sel) & CM;
       const int key = best_key<F>(v, pal, pk);
       sse += (int)__dp4a(v, v, 0u) + (key >> 4);
