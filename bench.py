@@ -47,7 +47,7 @@ BC7_EVALS_PER_BLOCK = (16 * (16 * 8 + 4 * 16 * 8) + 64 * (16 * 8 + 2 * 16 * 8) +
 OPS_PER_EVAL = 8
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) measured with ncu on the
 # 3M-Gaussian workload for the kernels as they stand; to be reset to None when a kernel changes.
-MEASURED_TRAFFIC = {"scene3m": {"k_bc7": None, "k_eval2_bc7": 446549504, "k_eval_tex_bc7": 391628032}}
+MEASURED_TRAFFIC = {"scene3m": {"k_bc7": 870084864, "k_eval2_bc7": 446549504, "k_eval_tex_bc7": 391628032}}
 
 
 def workload_cfg(name):
@@ -602,10 +602,10 @@ def run_serve(args, world, rank, local):
             lag = max(lag, time.perf_counter() - t0 - ta)
             n = pool[i][0]
             if kind == "encode":
-                q.put((srv.encode(i, host[i][0], host[i][1], host[i][2]), kind, n, 0))
+                q.put((srv.encode(i, host[i][0], host[i][1], host[i][2]), kind, n, i))
             else:
                 out = torch.empty((n, V, 3), dtype=torch.float32, device=dev)
-                q.put((srv.eval(i, n, out, cams=cams[k]), kind, n, V))
+                q.put((srv.eval(i, n, out, cams=cams[k]), kind, n, i))
         q.put(None)
         th.join()
         span = time.perf_counter() - t0
@@ -613,6 +613,21 @@ def run_serve(args, world, rank, local):
         srv.close()
         lat = {kd: np.array([r.t_done_ms - r.t_submit_ms for k2, r, _, _ in done if kd in (k2, "all")])
                for kd in ("all", "encode", "eval")}
+        # evaluations that had to wait for an earlier re-encode of their scene (submission order)
+        enc_spans = {}
+        for k2, r, _, sc in done:
+            if k2 == "encode":
+                enc_spans.setdefault(sc, []).append((r.t_submit_ms, r.t_done_ms))
+        free, dep = [], []
+        for k2, r, _, sc in done:
+            if k2 != "eval":
+                continue
+            waited = any(a < r.t_submit_ms < b for a, b in enc_spans.get(sc, []))
+            (dep if waited else free).append(r.t_done_ms - r.t_submit_ms)
+        lat["eval_no_pending_encode"] = np.array(free)
+        lat["eval_behind_encode"] = np.array(dep)
+        lat["queue_wait"] = np.array([r.t_admit_ms - r.t_submit_ms for _, r, _, _ in done])
+        lat["service"] = np.array([r.t_done_ms - r.t_admit_ms for _, r, _, _ in done])
         bad = sum(r.status != 0 for _, r, _, _ in done)
         gauss = sum(n for _, r, n, _ in done)
         pct = {}
