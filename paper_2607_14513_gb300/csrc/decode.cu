@@ -551,8 +551,13 @@ __device__ __forceinline__ void load_views(float (*s_view)[64], float* s_deq, co
 // CTAs of 4 warps (128 threads x at most 128 registers): one fits where one BC7-search CTA
 // retired, so an evaluation launched beside an encode on a higher-priority stream starts early.
 #define EVAL_THREADS 128
+// No register cap: capping at 5 or 6 resident CTAs per SM spills in the evaluation loop and
+// measured slower (3M Gaussians, all-BC7, 8 cameras: 0.205 ms uncapped, 0.225 ms and 0.260 ms).
+#ifndef EVAL_MIN_BLOCKS
+#define EVAL_MIN_BLOCKS 1
+#endif
 template <int KIND, bool CAMS>
-__global__ void __launch_bounds__(EVAL_THREADS) k_eval2(DevTable T, const uint8_t* __restrict__ blocks,
+__global__ void __launch_bounds__(EVAL_THREADS, EVAL_MIN_BLOCKS) k_eval2(DevTable T, const uint8_t* __restrict__ blocks,
                                                const int32_t* __restrict__ perm, const float* __restrict__ dirs,
                                                const float* __restrict__ pos, const float* __restrict__ cams, int V,
                                                int out_order, float* __restrict__ rgb) {
