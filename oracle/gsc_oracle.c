@@ -27,6 +27,8 @@
  */
 #include "gsc_oracle.h"
 
+#include <pthread.h>
+
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -871,9 +873,20 @@ int or_encode(const uint8_t* q, int64_t n, const int32_t* perm, const float* sca
   uint8_t* b1 = (uint8_t*)malloc((size_t)(ng * 16 * 8 + 1));
   uint8_t* b7 = (uint8_t*)malloc((size_t)(ng * 16 * 16 + 1));
   uint64_t* D = dtab ? dtab : (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(ng * OR_MODES + 1));
-  uint8_t* mode = (uint8_t*)malloc((size_t)(ng + 1));
-  if (!b1 || !b7 || !D || !mode) return -2;
-  for (int64_t g = 0; g < ng; g++) {
+  if (!b1 || !b7 || !D) return -2;
+  or_code_groups(q, n, perm, scales, b1, b7, D);
+  int rc = or_rate_assemble(n, perm, scales, target_x4, b1, b7, D, blocks, perm_out, t);
+  free(b1); free(b7);
+  if (!dtab) free(D);
+  return rc;
+}
+
+/* Groups g0..g1-1 of the rate path: both codings of every block, and D[g][m] = sum over the
+ * 16 coefficients of w_k times the error of the coding mode m gives coefficient k. */
+static void code_group_range(const uint8_t* q, const int32_t* perm, const uint32_t* w, uint8_t* b1, uint8_t* b7,
+                             uint64_t* D, int64_t g0, int64_t g1) {
+  uint8_t tex[16 * 16 * 3];
+  for (int64_t g = g0; g < g1; g++) {
     uint64_t e1[16], e7[16], e0[16];
     uint8_t rgba[64];
     or_stage_group(q, perm, g, tex);
@@ -892,11 +905,68 @@ int or_encode(const uint8_t* q, int64_t n, const int32_t* perm, const float* sca
       uint64_t d = 0;
       for (int k = 0; k < OR_SH; k++) {
         uint64_t e = k < MODE_J[m] ? e7[k] : (k < MODE_B[m] ? e1[k] : e0[k]);
-        d += (uint64_t)t->weights[k] * e;
+        d += (uint64_t)w[k] * e;
       }
       D[g * OR_MODES + m] = d;
     }
   }
+}
+
+struct code_job {
+  const uint8_t* q;
+  const int32_t* perm;
+  const uint32_t* w;
+  uint8_t *b1, *b7;
+  uint64_t* D;
+  int64_t g0, g1;
+};
+
+static void* code_job_run(void* arg) {
+  struct code_job* j = (struct code_job*)arg;
+  code_group_range(j->q, j->perm, j->w, j->b1, j->b7, j->D, j->g0, j->g1);
+  return NULL;
+}
+
+static int g_threads = 1;
+
+void or_set_threads(int threads) { g_threads = threads < 1 ? 1 : (threads > 256 ? 256 : threads); }
+
+/* Both codings and the D table of every group. Groups are independent and write disjoint
+ * memory, so they may be split over threads (or_set_threads) with identical results. */
+void or_code_groups(const uint8_t* q, int64_t n, const int32_t* perm, const float* scales, uint8_t* b1, uint8_t* b7,
+                    uint64_t* D) {
+  int64_t ng = (n + 15) / 16;
+  uint32_t w[OR_SH];
+  or_weights(scales, w);
+  int nt = g_threads;
+  if ((int64_t)nt > ng) nt = ng > 0 ? (int)ng : 1;
+  if (nt <= 1) {
+    code_group_range(q, perm, w, b1, b7, D, 0, ng);
+    return;
+  }
+  pthread_t th[256];
+  struct code_job jobs[256];
+  int started = 0;
+  for (int i = 0; i < nt; i++) {
+    jobs[i] = (struct code_job){q, perm, w, b1, b7, D, ng * i / nt, ng * (i + 1) / nt};
+    if (pthread_create(&th[i], NULL, code_job_run, &jobs[i]) == 0) started = i + 1;
+    else { code_group_range(q, perm, w, b1, b7, D, jobs[i].g0, jobs[i].g1); }
+  }
+  for (int i = 0; i < started; i++) pthread_join(th[i], NULL);
+}
+
+/* Rate control at target_x4 / 4 bits per texel over coded groups, then the 14 streams: the
+ * stable partition of groups by mode id, each group's kept blocks back to back. */
+int or_rate_assemble(int64_t n, const int32_t* perm, const float* scales, uint32_t target_x4, const uint8_t* b1,
+                     const uint8_t* b7, const uint64_t* D, uint8_t* blocks, int32_t* perm_out, or_table* t) {
+  int64_t ng = (n + 15) / 16;
+  memset(t, 0, sizeof(*t));
+  t->n = n; t->n_groups = ng; t->format = 0;
+  for (int k = 0; k < OR_SH; k++) t->scales[k] = scales[k];
+  or_weights(scales, t->weights);
+  if (target_x4 == 0) return -1;
+  uint8_t* mode = (uint8_t*)malloc((size_t)(ng + 1));
+  if (!mode) return -2;
   uint64_t budget = (uint64_t)target_x4 * 4u * (uint64_t)n;
   t->budget_bits = budget;
   int rc = or_rate_control(D, ng, budget, mode, &t->lambda);
@@ -923,8 +993,7 @@ int or_encode(const uint8_t* q, int64_t n, const int32_t* perm, const float* sca
     t->total_bytes = off;
     t->used_bits = (uint64_t)off * 8;
   }
-  free(b1); free(b7); free(mode);
-  if (!dtab) free(D);
+  free(mode);
   return rc;
 }
 

@@ -55,6 +55,14 @@ void or_mode_table(int32_t* bands, int32_t* bc7);
 void or_weights(const float* scales, uint32_t* w);
 int or_rate_choose(const uint64_t* D, int64_t ng, uint64_t lambda, uint8_t* mode);
 int or_rate_control(const uint64_t* D, int64_t ng, uint64_t budget, uint8_t* mode, uint64_t* lambda);
+/* The rate path in two steps (or_encode with format 0 runs both): both codings of every
+ * group with the D table [ng][14], then rate control and stream assembly for one target.
+ * or_set_threads splits the coding step over threads (default 1); results are identical. */
+void or_set_threads(int threads);
+void or_code_groups(const uint8_t* q, int64_t n, const int32_t* perm, const float* scales, uint8_t* b1, uint8_t* b7,
+                    uint64_t* D);
+int or_rate_assemble(int64_t n, const int32_t* perm, const float* scales, uint32_t target_x4, const uint8_t* b1,
+                     const uint8_t* b7, const uint64_t* D, uint8_t* blocks, int32_t* perm_out, or_table* t);
 int or_encode(const uint8_t* q, int64_t n, const int32_t* perm, const float* scales, int format,
               uint32_t target_x4, uint8_t* blocks, int32_t* perm_out, or_table* t, uint64_t* dtab);
 int or_decode(const or_table* t, const uint8_t* blocks, const int32_t* perm, uint8_t* texels);

@@ -33,7 +33,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
             os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "gsc_oracle.h"))):
         tmp = LIB + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-pthread",
                                "-fPIC", "-shared", "-o", tmp, SRC, "-lm"])
         os.replace(tmp, LIB)
     return LIB
@@ -82,6 +82,9 @@ def lib():
                 "or_rate_choose": (i32, [P, i64, u64, P]),
                 "or_rate_control": (i32, [P, i64, u64, P, P]),
                 "or_encode": (i32, [P, i64, P, P, i32, u32, P, P, P, P]),
+                "or_set_threads": (None, [i32]),
+                "or_code_groups": (None, [P, i64, P, P, P, P, P]),
+                "or_rate_assemble": (i32, [i64, P, P, u32, P, P, P, P, P, P]),
                 "or_decode": (i32, [P, P, P, P]),
                 "or_sh_basis": (None, [C.c_double, C.c_double, C.c_double, P]),
                 "or_eval_sh": (None, [P, i64, P, P, P, P, i32, P, P]),
@@ -289,6 +292,35 @@ def encode(q, perm, sc, fmt, target_x4=0, want_dtab=False):
     if want_dtab:
         res["dtab"] = dtab[:ng]
     return res
+
+
+def encode_rates(q, perm, sc, targets_x4, threads=1):
+    """Rate-controlled encode at several targets from one coding pass (the coding step split
+    over `threads`; results equal encode(q, perm, sc, 0, t) for each target t)."""
+    q = _c(q, np.uint8)
+    perm = _c(perm, np.int32)
+    sc = _c(sc, np.float32)
+    n = q.shape[0]
+    ng = (n + 15) // 16
+    b1 = np.zeros(max(ng * 128, 1), np.uint8)
+    b7 = np.zeros(max(ng * 256, 1), np.uint8)
+    D = np.zeros((max(ng, 1), MODES), np.uint64)
+    lib().or_set_threads(int(threads))
+    try:
+        lib().or_code_groups(_p(q), n, _p(perm), _p(sc), _p(b1), _p(b7), _p(D))
+    finally:
+        lib().or_set_threads(1)
+    out = []
+    for t4 in targets_x4:
+        blocks = np.zeros(max(ng * 256, 1), np.uint8)
+        perm_out = np.full(max(ng * 16, 1), -1, np.int32)
+        t = Table()
+        rc = lib().or_rate_assemble(n, _p(perm), _p(sc), int(t4), _p(b1), _p(b7), _p(D), _p(blocks), _p(perm_out),
+                                    C.byref(t))
+        if rc != 0:
+            raise ValueError("or_rate_assemble failed: %d" % rc)
+        out.append(dict(blocks=blocks[:t.total_bytes], perm=perm_out[:ng * 16], table=t))
+    return out
 
 
 def decode(table: Table, blocks, perm):

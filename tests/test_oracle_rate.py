@@ -117,3 +117,24 @@ def test_rate_targets_respect_budget(O, target_x4):
         g += s.n_groups
         off += s.n_groups * (16 * s.bc7_blocks + 8 * (s.bands - s.bc7_blocks))
     assert g == t.n_groups and off == t.total_bytes
+
+
+def test_rate_path_split_and_threads_change_nothing():
+    # coding all groups once (over several threads) and assembling per target gives exactly the
+    # single-call serial encode at every target
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2607_14513_gb300 import synthetic as S
+    O.lib()
+    sc = S.make_scene(1500, 711, heavy_frac=0.1)
+    osc = O.scales(sc.sh)
+    q = O.quantise(sc.sh, osc)
+    perm = O.plan(sc.pos, q, 256, 1)
+    targets = (12, 24)
+    outs = O.encode_rates(q, perm, osc, targets, threads=4)
+    for t4, o in zip(targets, outs):
+        r = O.encode(q, perm, osc, 0, t4)
+        assert np.array_equal(r["blocks"], o["blocks"]) and np.array_equal(r["perm"], o["perm"])
+        assert (r["table"].lambda_, r["table"].used_bits, r["table"].budget_bits) == \
+            (o["table"].lambda_, o["table"].used_bits, o["table"].budget_bits)
+        assert [r["table"].s[i].n_groups for i in range(14)] == [o["table"].s[i].n_groups for i in range(14)]
