@@ -46,7 +46,8 @@ typedef enum {
   GSC_ERR_BUDGET = 4,      /* rate target below the cheapest coding of the scene */
   GSC_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
   GSC_ERR_UNSUPPORTED = 6, /* no usable sm_103 device, or a feature the device lacks */
-  GSC_ERR_DEVICE = 7       /* an index check inside a kernel failed (record in the context) */
+  GSC_ERR_DEVICE = 7,      /* an index check inside a kernel failed (record in the context) */
+  GSC_ERR_CANCELLED = 8    /* a queued request of the request loop was cancelled */
 } gsc_status;
 
 typedef enum { GSC_FMT_RATE = 0, GSC_FMT_BC1 = 1, GSC_FMT_BC7 = 7 } gsc_format;
@@ -276,7 +277,7 @@ typedef struct {
   int64_t hold_us;            /* a request older than this that does not fit holds back later ones */
 } gsc_server_params;
 
-enum { GSC_REQ_ENCODE = 0, GSC_REQ_EVAL = 1 };
+enum { GSC_REQ_ENCODE = 0, GSC_REQ_EVAL = 1, GSC_REQ_LOAD = 2 };
 
 /* Pointers may be host (pinned or pageable) or device memory and must stay valid until the
  * request completes. Encode: pos [n][3], sh [n][16][3] (16-byte aligned), format, rate target,
@@ -299,6 +300,8 @@ typedef struct {
   const float* cams;
   int32_t out_order;
   float* out;
+  const char* path;           /* load: a checkpoint file written with positions (gsc_scene_write); n = its
+                               * Gaussian count. The load is ordered and admitted like an encode. */
 } gsc_request;
 
 typedef struct {
@@ -327,6 +330,12 @@ gsc_status gsc_server_drain(gsc_server* srv, int64_t timeout_ms);
 /* Copies a resident scene's table, blocks and slot order out (host or device buffers). */
 gsc_status gsc_server_read_scene(gsc_server* srv, int32_t scene, gsc_stream_table* table, uint8_t* blocks,
                                  size_t blocks_cap, int32_t* perm, size_t perm_bytes_cap);
+/* Cancels a queued request: it completes with GSC_ERR_CANCELLED (collect it with
+ * gsc_server_wait). A request already admitted or completed cannot be cancelled
+ * (GSC_ERR_INVALID_ARG). */
+gsc_status gsc_server_cancel(gsc_server* srv, uint64_t ticket);
+/* Writes a resident scene (with its positions) to a checkpoint file (gsc_scene_write). */
+gsc_status gsc_server_save_scene(gsc_server* srv, int32_t scene, const char* path);
 /* Frees a resident scene that no queued or running request uses (else GSC_ERR_INVALID_ARG). */
 gsc_status gsc_server_evict(gsc_server* srv, int32_t scene);
 gsc_status gsc_server_get_stats(gsc_server* srv, gsc_server_stats* st);
@@ -356,6 +365,18 @@ typedef struct {
 
 gsc_status gsc_server_simulate(const gsc_server_params* p, const gsc_sim_request* reqs, int32_t n,
                                gsc_sim_result* res, uint64_t* peak_bytes);
+
+/* Checkpoint file of a coded scene (the paper stores scenes as these streams; the file format is
+ * this codec's own): a versioned header with the stream table, section sizes and an FNV-1a 64
+ * checksum, then the blocks (table->total_bytes), the final slot order (n_groups * 16 int32) and
+ * optionally the positions (n * 3 float). Buffers may be host or device memory. Reading checks the
+ * magic, version, sizes against the table and the checksum (GSC_ERR_INVALID_ARG on any mismatch or
+ * a capacity too small); the bytes read back equal the bytes written. */
+gsc_status gsc_scene_write(const char* path, const gsc_stream_table* table, const uint8_t* blocks,
+                           const int32_t* perm, const float* pos);
+gsc_status gsc_scene_read_info(const char* path, gsc_stream_table* table, int32_t* has_pos);
+gsc_status gsc_scene_read(const char* path, gsc_stream_table* table, uint8_t* blocks, size_t blocks_cap,
+                          int32_t* perm, size_t perm_bytes_cap, float* pos, size_t pos_bytes_cap);
 
 /* Block-level codecs (Sec. III-B): nblk independent 4x4 blocks.
  * d_tex [nblk][16][3] uint8 -> d_out [nblk][8 or 16] bytes; d_sse [nblk] (optional)

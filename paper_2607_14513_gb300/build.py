@@ -10,7 +10,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "lib", "libgsc.so")
-SOURCES = ["api.cu", "plan.cu", "bc1.cu", "bc7.cu", "rate.cu", "decode.cu", "batch.cu", "serve.cu"]
+SOURCES = ["api.cu", "plan.cu", "bc1.cu", "bc7.cu", "rate.cu", "decode.cu", "batch.cu", "serve.cu", "scene_file.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -132,6 +132,7 @@ extern "C" const char* gsc_status_string(gsc_status s) {
     case GSC_ERR_TIMEOUT: return "device-side wait timed out";
     case GSC_ERR_UNSUPPORTED: return "no usable sm_103 device";
     case GSC_ERR_DEVICE: return "device-side check failed";
+    case GSC_ERR_CANCELLED: return "request cancelled";
     default: return "unknown status";
   }
 }
@@ -215,6 +216,7 @@ static bool n_ok(int64_t n) { return n >= 0 && n < (int64_t)0x7FFFFFF0; }
 
 extern "C" gsc_status gsc_plan_reorder(gsc_ctx* c, const float* d_pos, const float* d_sh, const gsc_plan_params* pp,
                                        int32_t* d_perm, float* d_scales, void* d_ws, size_t ws_bytes, void* stream) {
+  GscRange gsc_range_("gsc_plan_reorder");
   if (!c || !pp || !n_ok(pp->n)) return GSC_ERR_INVALID_ARG;
   if (pp->group_size < 0 || pp->group_size % 16 != 0) return GSC_ERR_INVALID_ARG;
   if (pp->quantile_permille == 0 || pp->quantile_permille > 1000) return GSC_ERR_INVALID_ARG;
@@ -229,6 +231,7 @@ extern "C" gsc_status gsc_plan_reorder(gsc_ctx* c, const float* d_pos, const flo
 
 extern "C" gsc_status gsc_quantise(gsc_ctx* c, const float* d_sh, int64_t n, const float* d_scales, uint8_t* d_q,
                                    void* stream) {
+  GscRange gsc_range_("gsc_quantise");
   if (!c || !n_ok(n) || !d_scales || (n > 0 && (!d_sh || !d_q))) return GSC_ERR_INVALID_ARG;
   if (!aligned(d_sh, 16) || !aligned(d_q, 4)) return GSC_ERR_INVALID_ARG;
   GSC_CUDA(cudaSetDevice(c->device));
@@ -250,6 +253,7 @@ extern "C" gsc_status gsc_encode(gsc_ctx* c, const float* d_sh, int64_t n, const
                                  const float* d_scales, const gsc_encode_params* ep, uint8_t* d_blocks,
                                  int32_t* d_perm_out, gsc_stream_table* h_table, void* d_ws, size_t ws_bytes,
                                  void* stream) {
+  GscRange gsc_range_("gsc_encode");
   if (!c || !ep || !h_table || !n_ok(n) || !d_scales) return GSC_ERR_INVALID_ARG;
   if (ep->format != GSC_FMT_BC1 && ep->format != GSC_FMT_BC7 && ep->format != GSC_FMT_RATE) return GSC_ERR_INVALID_ARG;
   if (ep->format == GSC_FMT_RATE && (ep->target_bpt_x4 == 0 || ep->target_bpt_x4 > 64)) return GSC_ERR_INVALID_ARG;
@@ -336,6 +340,7 @@ gsc_status make_dev_table(const gsc_stream_table* t, DevTable* d) {
 
 extern "C" gsc_status gsc_decode(gsc_ctx* c, const gsc_stream_table* table, const uint8_t* d_blocks,
                                  const int32_t* d_perm, uint8_t* d_texels, void* stream) {
+  GscRange gsc_range_("gsc_decode");
   if (!c) return GSC_ERR_INVALID_ARG;
   DevTable T;
   gsc_status s = make_dev_table(table, &T);
@@ -352,6 +357,7 @@ extern "C" gsc_status gsc_decode_eval_sh(gsc_ctx* c, const gsc_stream_table* tab
                                          const int32_t* d_perm, const float* d_dirs, const float* d_pos,
                                          const float* d_cams, int32_t V, int32_t out_order, float* d_rgb,
                                          void* stream) {
+  GscRange gsc_range_("gsc_decode_eval_sh");
   if (!c) return GSC_ERR_INVALID_ARG;
   DevTable T;
   gsc_status s = make_dev_table(table, &T);
@@ -370,6 +376,7 @@ extern "C" gsc_status gsc_decode_eval_sh(gsc_ctx* c, const gsc_stream_table* tab
 
 extern "C" gsc_status gsc_decode_tex(gsc_ctx* c, const gsc_stream_table* table, const uint8_t* d_blocks,
                                      const int32_t* d_perm, uint8_t* d_texels, void* stream) {
+  GscRange gsc_range_("gsc_decode_tex");
   if (!c) return GSC_ERR_INVALID_ARG;
   DevTable T;
   gsc_status s = make_dev_table(table, &T);
@@ -385,6 +392,7 @@ static bool fmt_ok(int f) { return f == GSC_FMT_BC1 || f == GSC_FMT_BC7; }
 
 extern "C" gsc_status gsc_encode_blocks(gsc_ctx* c, const uint8_t* d_tex, int64_t nblk, int32_t format,
                                         uint8_t* d_out, uint64_t* d_sse, void* stream) {
+  GscRange gsc_range_("gsc_encode_blocks");
   if (!c || nblk < 0 || !fmt_ok(format) || (nblk > 0 && (!d_tex || !d_out))) return GSC_ERR_INVALID_ARG;
   if (!aligned(d_out, format == GSC_FMT_BC7 ? 16 : 8) || !aligned(d_sse, 8)) return GSC_ERR_INVALID_ARG;
   GSC_CUDA(cudaSetDevice(c->device));
@@ -395,6 +403,7 @@ extern "C" gsc_status gsc_encode_blocks(gsc_ctx* c, const uint8_t* d_tex, int64_
 
 extern "C" gsc_status gsc_decode_blocks(gsc_ctx* c, const uint8_t* d_blocks, int64_t nblk, int32_t format,
                                         uint8_t* d_rgba, void* stream) {
+  GscRange gsc_range_("gsc_decode_blocks");
   if (!c || nblk < 0 || !fmt_ok(format) || (nblk > 0 && (!d_blocks || !d_rgba))) return GSC_ERR_INVALID_ARG;
   if (!aligned(d_blocks, format == GSC_FMT_BC7 ? 16 : 8) || !aligned(d_rgba, 4)) return GSC_ERR_INVALID_ARG;
   GSC_CUDA(cudaSetDevice(c->device));
@@ -404,6 +413,7 @@ extern "C" gsc_status gsc_decode_blocks(gsc_ctx* c, const uint8_t* d_blocks, int
 
 extern "C" gsc_status gsc_decode_blocks_tex(gsc_ctx* c, const uint8_t* d_blocks, int64_t nblk, int32_t format,
                                             uint8_t* d_rgba, void* stream) {
+  GscRange gsc_range_("gsc_decode_blocks_tex");
   if (!c || nblk < 0 || !fmt_ok(format) || (nblk > 0 && (!d_blocks || !d_rgba))) return GSC_ERR_INVALID_ARG;
   if (!aligned(d_blocks, 8) || !aligned(d_rgba, 4)) return GSC_ERR_INVALID_ARG;
   GSC_CUDA(cudaSetDevice(c->device));

@@ -227,6 +227,7 @@ static bool tune_ok(const gsc_batch_tuning* t) {
 
 extern "C" gsc_status gsc_batch_encode(gsc_ctx* c, gsc_batch_scene* sc, int32_t n, const gsc_batch_tuning* tune,
                                        void* d_ws, size_t ws_bytes, void* stream) {
+  GscRange gsc_range_("gsc_batch_encode");
   if (!c || !batch_args_ok(sc, n) || !tune_ok(tune) || ((uintptr_t)d_ws % 256) != 0) return GSC_ERR_INVALID_ARG;
   if (ws_bytes < layout(sc, n).total) return GSC_ERR_OOM;
   GSC_CUDA(cudaSetDevice(c->device));
@@ -285,6 +286,7 @@ extern "C" gsc_status gsc_batch_encode(gsc_ctx* c, gsc_batch_scene* sc, int32_t 
 
 extern "C" gsc_status gsc_batch_autotune(gsc_ctx* c, gsc_batch_scene* sc, int32_t n, gsc_batch_tuning* out,
                                          double* ms_best, void* d_ws, size_t ws_bytes, void* stream) {
+  GscRange gsc_range_("gsc_batch_autotune");
   if (!c || !out || !batch_args_ok(sc, n) || ((uintptr_t)d_ws % 256) != 0) return GSC_ERR_INVALID_ARG;
   if (ws_bytes < layout(sc, n).total) return GSC_ERR_OOM;
   GSC_CUDA(cudaSetDevice(c->device));
@@ -330,6 +332,7 @@ extern "C" gsc_status gsc_batch_autotune(gsc_ctx* c, gsc_batch_scene* sc, int32_
 extern "C" gsc_status gsc_batch_eval_graph(gsc_ctx* c, const gsc_batch_scene* sc, int32_t n, const float* d_cams,
                                            int32_t V, int32_t out_order, float* const* d_rgb, gsc_graph** out,
                                            void* stream) {
+  GscRange gsc_range_("gsc_batch_eval_graph");
   if (!c || !sc || n <= 0 || !out || !d_rgb || !d_cams || V < 1 || V > 64 || out_order < 0 || out_order > 2)
     return GSC_ERR_INVALID_ARG;
   *out = nullptr;
@@ -400,6 +403,7 @@ extern "C" gsc_status gsc_batch_eval_graph(gsc_ctx* c, const gsc_batch_scene* sc
 }
 
 extern "C" gsc_status gsc_graph_launch(gsc_graph* g, void* stream) {
+  GscRange gsc_range_("gsc_graph_launch");
   if (!g) return GSC_ERR_INVALID_ARG;
   GSC_CUDA(cudaSetDevice(g->device));
   for (int i = 0; i < g->kernels; i++) gsc_count_launch();

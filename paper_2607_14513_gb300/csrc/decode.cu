@@ -1018,6 +1018,7 @@ __global__ void __launch_bounds__(256) k_eval_tex(DevTable T, TexBases B, cudaTe
 extern "C" gsc_status gsc_tex_scene_create(gsc_ctx* c, const gsc_stream_table* table, const uint8_t* d_blocks,
                                            const int32_t* d_perm, const float* d_pos, gsc_tex_scene** out,
                                            void* stream) {
+  GscRange gsc_range_("gsc_tex_scene_create");
   if (!c || !out) return GSC_ERR_INVALID_ARG;
   *out = nullptr;
   DevTable T;
@@ -1086,6 +1087,7 @@ extern "C" gsc_status gsc_tex_scene_destroy(gsc_tex_scene* sc) {
 extern "C" gsc_status gsc_decode_eval_sh_tex(gsc_ctx* c, const gsc_tex_scene* sc, const int32_t* d_perm,
                                              const float* d_dirs, const float* d_pos, const float* d_cams, int32_t V,
                                              int32_t out_order, float* d_rgb, void* stream) {
+  GscRange gsc_range_("gsc_decode_eval_sh_tex");
   if (!c || !sc || sc->device != c->device) return GSC_ERR_INVALID_ARG;
   const DevTable& T = sc->T;
   if (V < 1 || V > 64 || out_order < 0 || out_order > 2) return GSC_ERR_INVALID_ARG;

@@ -1,6 +1,7 @@
 // gsc_internal.cuh -- shared declarations of the CUDA library's translation units.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -54,6 +55,13 @@ struct GscTimed {
   gsc_ctx* c; int rec; cudaStream_t st;
   GscTimed(gsc_ctx* c_, int id, cudaStream_t st_) : c(c_), rec(gsc_timer_begin(c_, id, st_)), st(st_) {}
   ~GscTimed() { gsc_timer_end(c, rec, st); }
+};
+
+// NVTX range over one C-ABI call (header-only NVTX 3: a no-op unless a profiler is attached), so
+// timelines show each call with its kernels.
+struct GscRange {
+  explicit GscRange(const char* name) { nvtxRangePushA(name); }
+  ~GscRange() { nvtxRangePop(); }
 };
 
 // Records the first device-detected error into the context status word.

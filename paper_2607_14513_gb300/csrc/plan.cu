@@ -452,6 +452,7 @@ static void* g_plan_scratch_ptr[GSC_MAX_DEVICES];
 extern "C" gsc_status gsc_plan_reorder_static(gsc_ctx* c, const float* d_pos, const float* d_sh,
                                               const gsc_plan_params* pp, int32_t* d_perm, float* d_scales,
                                               void* stream) {
+  GscRange gsc_range_("gsc_plan_reorder_static");
   if (!c || !pp || pp->n < 0 || pp->n > GSC_PLAN_STATIC_MAX_N) return GSC_ERR_INVALID_ARG;
   if (pp->group_size < 0 || pp->group_size % 16 != 0) return GSC_ERR_INVALID_ARG;
   if (pp->quantile_permille == 0 || pp->quantile_permille > 1000) return GSC_ERR_INVALID_ARG;

@@ -118,6 +118,7 @@ cudaError_t pool_alloc(gsc_server* s, T** p, uint64_t bytes, cudaStream_t st) {
 
 // One encode on the slot's low-priority stream; the coded scene goes to *out.
 gsc_status run_encode(gsc_server* s, Slot& w, const gsc_request& r, SceneRes* out) {
+  GscRange range("serve_encode");
   cudaStream_t st = w.lo;
   const int64_t n = r.n, ng = ceil_div64(n, 16), ns = ng * 16;
   const bool host_sh = !on_device(r.sh);
@@ -163,9 +164,41 @@ gsc_status run_encode(gsc_server* s, Slot& w, const gsc_request& r, SceneRes* ou
   return rc;
 }
 
+// A coded scene read back from a checkpoint file into resident memory (with its positions).
+gsc_status run_load(gsc_server* s, Slot& w, const gsc_request& r, SceneRes* out) {
+  cudaStream_t st = w.lo;
+  gsc_stream_table t;
+  int32_t has_pos = 0;
+  gsc_status rc = gsc_scene_read_info(r.path, &t, &has_pos);
+  if (rc != GSC_OK) return rc;
+  if (!has_pos || t.n != r.n) return GSC_ERR_INVALID_ARG;
+  const int64_t ns = t.n_groups * 16;
+  cudaError_t e = pool_alloc(s, &out->blocks, (uint64_t)t.total_bytes, st);
+  if (e == cudaSuccess) e = pool_alloc(s, &out->perm, 4 * (uint64_t)ns, st);
+  if (e == cudaSuccess) e = pool_alloc(s, &out->pos, 12 * (uint64_t)t.n, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the allocations exist before the copies
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    rc = e == cudaErrorMemoryAllocation ? GSC_ERR_OOM : GSC_ERR_CUDA;
+  } else {
+    rc = gsc_scene_read(r.path, &out->table, out->blocks, (size_t)t.total_bytes, out->perm, 4 * (size_t)ns, out->pos,
+                        12 * (size_t)t.n);
+  }
+  out->n = t.n;
+  if (rc != GSC_OK) {
+    cudaFreeAsync(out->blocks, st);
+    cudaFreeAsync(out->perm, st);
+    cudaFreeAsync(out->pos, st);
+    out->blocks = nullptr;
+    cudaStreamSynchronize(st);
+  }
+  return rc;
+}
+
 // One evaluation launch (one or several merged requests) on the slot's high-priority stream.
 gsc_status run_eval(gsc_server* s, Slot& w, const SceneRes& sc, std::vector<Rec*>& rs, int V_total,
                     uint64_t stage_bytes) {
+  GscRange range("serve_eval");
   cudaStream_t st = s->prm.priority ? w.hi : w.lo;
   const gsc_request& r0 = rs[0]->req;
   const bool cams = r0.cams != nullptr;
@@ -240,7 +273,7 @@ void slot_main(gsc_server* s, int k) {
       const gsc_request req = rs[0]->req;
       lk.unlock();
       SceneRes res;
-      rc = run_encode(s, w, req, &res);
+      rc = req.kind == GSC_REQ_LOAD ? run_load(s, w, req, &res) : run_encode(s, w, req, &res);
       lk.lock();
       if (rc == GSC_OK) s->scenes[{L.scene, L.version}] = res;
     } else {
@@ -273,6 +306,10 @@ gsc_status request_ok(const gsc_request* r, const gsc_server_params& p) {
     if (((uintptr_t)r->sh % 16) != 0) return GSC_ERR_INVALID_ARG;
     return GSC_OK;
   }
+  if (r->kind == GSC_REQ_LOAD) {
+    if (!r->path || r->n <= 0) return GSC_ERR_INVALID_ARG;
+    return GSC_OK;
+  }
   if (r->kind == GSC_REQ_EVAL) {
     if (r->n <= 0 || r->V < 1 || r->V > p.max_views || !r->out || (!r->dirs == !r->cams)) return GSC_ERR_INVALID_ARG;
     if (r->out_order < 0 || r->out_order > 2 || ((uintptr_t)r->out % 16) != 0) return GSC_ERR_INVALID_ARG;
@@ -284,7 +321,7 @@ gsc_status request_ok(const gsc_request* r, const gsc_server_params& p) {
 SchedReq sched_req(const gsc_request& r, uint64_t ticket, int64_t t, bool host_sh, bool out_device) {
   SchedReq q;
   q.ticket = ticket;
-  q.kind = r.kind == GSC_REQ_ENCODE ? SREQ_ENCODE : SREQ_EVAL;
+  q.kind = r.kind == GSC_REQ_EVAL ? SREQ_EVAL : SREQ_ENCODE;  // a load installs a version like an encode
   q.scene = r.scene;
   q.n = r.n;
   q.V = r.V;
@@ -294,6 +331,14 @@ SchedReq sched_req(const gsc_request& r, uint64_t ticket, int64_t t, bool host_s
   q.t_submit = t;
   if (r.kind == GSC_REQ_ENCODE) encode_bytes(r.n, r.format, r.target_bpt_x4, host_sh, &q.temp_bytes, &q.keep_bytes);
   return q;
+}
+
+// Resident bytes of a checkpoint file's scene (0 when the file cannot serve as one).
+uint64_t load_bytes(const gsc_request& r) {
+  gsc_stream_table t;
+  int32_t has_pos = 0;
+  if (gsc_scene_read_info(r.path, &t, &has_pos) != GSC_OK || !has_pos || t.n != r.n) return 0;
+  return sched_align((uint64_t)t.total_bytes) + sched_align(4 * (uint64_t)t.n_groups * 16) + sched_align(12 * (uint64_t)t.n);
 }
 
 }  // namespace
@@ -345,16 +390,24 @@ extern "C" gsc_status gsc_server_create(gsc_ctx* c, const gsc_server_params* p, 
 }
 
 extern "C" gsc_status gsc_server_submit(gsc_server* s, const gsc_request* r, uint64_t* ticket) {
+  GscRange gsc_range_("gsc_server_submit");
   if (!s || !ticket) return GSC_ERR_INVALID_ARG;
   gsc_status rc = request_ok(r, s->prm);
   if (rc != GSC_OK) return rc;
   const bool host_sh = r->kind == GSC_REQ_ENCODE && !on_device(r->sh);
   const bool out_dev = r->kind == GSC_REQ_EVAL && on_device(r->out);
+  SchedReq q0 = sched_req(*r, 0, 0, host_sh, out_dev);
+  if (r->kind == GSC_REQ_LOAD) {
+    q0.keep_bytes = load_bytes(*r);  // the file is read once here to size the request
+    if (q0.keep_bytes == 0) return GSC_ERR_INVALID_ARG;
+  }
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stop) return GSC_ERR_INVALID_ARG;
   const uint64_t t = s->next_ticket++;
   const int64_t now = s->now();
-  if (!s->sched.submit(sched_req(*r, t, now, host_sh, out_dev))) return GSC_ERR_BUDGET;
+  q0.ticket = t;
+  q0.t_submit = now;
+  if (!s->sched.submit(q0)) return GSC_ERR_BUDGET;
   Rec& rec = s->recs[t];
   rec.req = *r;
   rec.t_submit = now;
@@ -365,6 +418,7 @@ extern "C" gsc_status gsc_server_submit(gsc_server* s, const gsc_request* r, uin
 }
 
 extern "C" gsc_status gsc_server_wait(gsc_server* s, uint64_t ticket, int64_t timeout_ms, gsc_request_result* res) {
+  GscRange gsc_range_("gsc_server_wait");
   if (!s || !res) return GSC_ERR_INVALID_ARG;
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->recs.find(ticket);
@@ -409,6 +463,33 @@ extern "C" gsc_status gsc_server_read_scene(gsc_server* s, int32_t scene, gsc_st
   if (blocks) GSC_CUDA(cudaMemcpy(blocks, r.blocks, nb, cudaMemcpyDefault));
   if (perm) GSC_CUDA(cudaMemcpy(perm, r.perm, np, cudaMemcpyDefault));
   return GSC_OK;
+}
+
+extern "C" gsc_status gsc_server_cancel(gsc_server* s, uint64_t ticket) {
+  if (!s) return GSC_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->recs.find(ticket);
+  if (it == s->recs.end() || it->second.done || !s->sched.cancel(ticket)) return GSC_ERR_INVALID_ARG;
+  Rec& r = it->second;
+  r.status = GSC_ERR_CANCELLED;
+  r.t_admit = r.t_done = s->now();
+  r.done = true;
+  s->done++;
+  s->failed++;
+  s->cv_done.notify_all();
+  s->cv_work.notify_all();  // a request held back behind it may be admissible now
+  return GSC_OK;
+}
+
+extern "C" gsc_status gsc_server_save_scene(gsc_server* s, int32_t scene, const char* path) {
+  if (!s || !path) return GSC_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  const int v = s->sched.current(scene);
+  auto it = s->scenes.find({scene, v});
+  if (v < 0 || it == s->scenes.end()) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(s->device));
+  const SceneRes& r = it->second;
+  return gsc_scene_write(path, &r.table, r.blocks, r.perm, r.pos);
 }
 
 extern "C" gsc_status gsc_server_evict(gsc_server* s, int32_t scene) {

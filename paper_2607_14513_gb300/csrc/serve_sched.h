@@ -182,6 +182,13 @@ class Sched {
     return freed;
   }
 
+  // Removes a queued request; false when it is not queued (already admitted, or unknown).
+  bool cancel(uint64_t ticket) {
+    for (size_t i = 0; i < q_.size(); i++)
+      if (q_[i].ticket == ticket) { take(i); return true; }
+    return false;
+  }
+
   // Frees a scene's current version when nothing queued or running uses it.
   bool evict(int scene, std::vector<std::pair<int, int>>* freed) {
     auto it = scenes_.find(scene);

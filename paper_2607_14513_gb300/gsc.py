@@ -17,7 +17,7 @@ HEADER = os.path.join(PKG, "..", "include", "gsc.h")
 
 GSC_OK = 0
 STATUS = {0: "GSC_OK", 1: "GSC_ERR_INVALID_ARG", 2: "GSC_ERR_CUDA", 3: "GSC_ERR_OOM", 4: "GSC_ERR_BUDGET",
-          5: "GSC_ERR_TIMEOUT", 6: "GSC_ERR_UNSUPPORTED", 7: "GSC_ERR_DEVICE"}
+          5: "GSC_ERR_TIMEOUT", 6: "GSC_ERR_UNSUPPORTED", 7: "GSC_ERR_DEVICE", 8: "GSC_ERR_CANCELLED"}
 FMT_RATE, FMT_BC1, FMT_BC7 = 0, 1, 7
 OUT_VIEW_MAJOR, OUT_SLOT_ORDER, OUT_GAUSS_MAJOR = 0, 1, 2
 
@@ -64,7 +64,7 @@ class BatchTuning(C.Structure):
     _fields_ = [("schedule", C.c_int32), ("ctas_per_sm", C.c_int32), ("bc1_tile_groups", C.c_int32)]
 
 
-REQ_ENCODE, REQ_EVAL = 0, 1
+REQ_ENCODE, REQ_EVAL, REQ_LOAD = 0, 1, 2
 
 
 class ServerParams(C.Structure):
@@ -76,7 +76,7 @@ class Request(C.Structure):
     _fields_ = [("kind", C.c_int32), ("scene", C.c_int32), ("pos", C.c_void_p), ("sh", C.c_void_p),
                 ("n", C.c_int64), ("format", C.c_int32), ("target_bpt_x4", C.c_uint32), ("group_size", C.c_int64),
                 ("sort", C.c_int32), ("V", C.c_int32), ("dirs", C.c_void_p), ("cams", C.c_void_p),
-                ("out_order", C.c_int32), ("out", C.c_void_p)]
+                ("out_order", C.c_int32), ("out", C.c_void_p), ("path", C.c_char_p)]
 
 
 class RequestResult(C.Structure):
@@ -140,6 +140,11 @@ _SIGS = {
     "gsc_server_drain": [_P, C.c_int64],
     "gsc_server_read_scene": [_P, C.c_int32, C.POINTER(StreamTable), _P, C.c_size_t, _P, C.c_size_t],
     "gsc_server_evict": [_P, C.c_int32],
+    "gsc_server_save_scene": [_P, C.c_int32, C.c_char_p],
+    "gsc_server_cancel": [_P, C.c_uint64],
+    "gsc_scene_write": [C.c_char_p, C.POINTER(StreamTable), _P, _P, _P],
+    "gsc_scene_read_info": [C.c_char_p, C.POINTER(StreamTable), C.POINTER(C.c_int32)],
+    "gsc_scene_read": [C.c_char_p, C.POINTER(StreamTable), _P, C.c_size_t, _P, C.c_size_t, _P, C.c_size_t],
     "gsc_server_get_stats": [_P, C.POINTER(ServerStats)],
     "gsc_server_destroy": [_P],
     "gsc_server_simulate": [C.POINTER(ServerParams), C.POINTER(SimRequest), C.c_int32, C.POINTER(SimResult),
@@ -506,6 +511,14 @@ class Server:
                     None, None, 0, None)
         return self._submit(r, (pos, sh))
 
+    def load(self, scene, path, n):
+        """Install a checkpoint file (written with positions) as the scene's next version."""
+        r = Request(REQ_LOAD, scene, None, None, n, 0, 0, 0, 0, 0, None, None, 0, None, os.fsencode(path))
+        return self._submit(r, ())
+
+    def save(self, scene, path):
+        _check(self.lib.gsc_server_save_scene(self.h, scene, os.fsencode(path)), "gsc_server_save_scene")
+
     def eval(self, scene, n, out, dirs=None, cams=None, out_order=OUT_GAUSS_MAJOR):
         src = dirs if dirs is not None else cams
         r = Request(REQ_EVAL, scene, None, None, n, 0, 0, 0, 0, src.shape[0], _addr(dirs), _addr(cams), out_order,
@@ -523,6 +536,9 @@ class Server:
         _check(self.lib.gsc_server_wait(self.h, ticket, timeout_ms, C.byref(res)), "gsc_server_wait")
         self.keep.pop(ticket, None)
         return res
+
+    def cancel(self, ticket):
+        _check(self.lib.gsc_server_cancel(self.h, ticket), "gsc_server_cancel")
 
     def drain(self, timeout_ms=-1):
         _check(self.lib.gsc_server_drain(self.h, timeout_ms), "gsc_server_drain")
@@ -557,3 +573,26 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def scene_write(path, table, blocks, perm, pos=None):
+    """Checkpoint file of a coded scene (host or device tensors)."""
+    _check(load().gsc_scene_write(os.fsencode(path), C.byref(table), _ptr(blocks), _ptr(perm), _ptr(pos)),
+           "gsc_scene_write")
+
+
+def scene_read(path, device=None):
+    """(table, blocks, perm, pos or None) read back from a checkpoint file, as tensors on `device`
+    (host when None)."""
+    import torch
+    lib = load()
+    t = StreamTable()
+    has = C.c_int32(0)
+    _check(lib.gsc_scene_read_info(os.fsencode(path), C.byref(t), C.byref(has)), "gsc_scene_read_info")
+    dev = device if device is not None else "cpu"
+    blocks = torch.empty(max(t.total_bytes, 1), dtype=torch.uint8, device=dev)
+    perm = torch.empty(max(t.n_groups * 16, 1), dtype=torch.int32, device=dev)
+    pos = torch.empty((max(t.n, 1), 3), dtype=torch.float32, device=dev) if has.value else None
+    _check(lib.gsc_scene_read(os.fsencode(path), C.byref(t), _ptr(blocks), blocks.numel(), _ptr(perm),
+                              4 * perm.numel(), _ptr(pos), 0 if pos is None else 4 * pos.numel()), "gsc_scene_read")
+    return t, blocks[:t.total_bytes], perm[:t.n_groups * 16], (pos[:t.n] if pos is not None else None)

@@ -161,3 +161,66 @@ def test_budget_eviction_and_refusals(ctx):
             srv.encode(5, torch.zeros((2_000_000, 3), device="cuda"), big, gsc.FMT_BC7)  # never fits
     finally:
         srv.close()
+
+
+def test_checkpoint_round_trip_and_server_reload(ctx, tmp_path):
+    # a coded scene written from device buffers reads back byte for byte; a server scene saved,
+    # evicted and reloaded from its file evaluates exactly as before
+    from paper_2607_14513_gb300 import gsc
+    n = 30000
+    sc = S.make_scene(n, 4300, clusters=5, heavy_frac=0.1)
+    pos, sh = torch.from_numpy(sc.pos).cuda(), torch.from_numpy(sc.sh).cuda()
+    blocks, perm_out, tab = _single_encode(ctx, pos, sh, gsc.FMT_RATE, 24)
+    f = str(tmp_path / "s.gsc")
+    gsc.scene_write(f, tab, blocks, perm_out, pos)
+    t2, b2, p2, q2 = gsc.scene_read(f, device="cuda")
+    assert torch.equal(b2, blocks) and torch.equal(p2, perm_out) and torch.equal(q2, pos)
+    cams = torch.from_numpy(S.make_cams(8, 88)).cuda()
+    ref = _single_eval(ctx, (blocks, perm_out, tab), pos, cams, True, gsc.OUT_GAUSS_MAJOR)
+    got = _single_eval(ctx, (b2, p2, t2), q2, cams, True, gsc.OUT_GAUSS_MAJOR)
+    assert torch.equal(ref, got)
+    srv = gsc.Server(ctx, 8 * GiB, n_slots=2)
+    try:
+        assert srv.wait(srv.encode(3, pos, sh, gsc.FMT_RATE, target_x4=24)).status == 0
+        out0 = torch.empty((n, 8, 3), device="cuda")
+        assert srv.wait(srv.eval(3, n, out0, cams=cams)).status == 0
+        g = str(tmp_path / "srv.gsc")
+        srv.save(3, g)
+        srv.evict(3)
+        assert srv.wait(srv.eval(3, n, out0, cams=cams)).status == 1      # no longer resident
+        assert srv.wait(srv.load(3, g, n)).status == 0
+        out1 = torch.empty((n, 8, 3), device="cuda")
+        assert srv.wait(srv.eval(3, n, out1, cams=cams)).status == 0
+        assert torch.equal(out1, ref)
+        with pytest.raises(gsc.GscError):
+            srv.load(4, g, n + 1)                                          # the file holds another size
+    finally:
+        srv.close()
+
+
+def test_wait_timeout_and_cancel(ctx):
+    # failure handling on the host: a bounded wait returns GSC_ERR_TIMEOUT and the request still
+    # completes; a queued request can be cancelled, an admitted or finished one cannot
+    from paper_2607_14513_gb300 import gsc
+    a = S.make_scene(600_000, 4400, clusters=8)
+    b = S.make_scene(5_000, 4401, clusters=2)
+    pa, sa = torch.from_numpy(a.pos).cuda(), torch.from_numpy(a.sh).cuda()
+    pb, sb = torch.from_numpy(b.pos).cuda(), torch.from_numpy(b.sh).cuda()
+    srv = gsc.Server(ctx, 8 * GiB, n_slots=1)
+    try:
+        t1 = srv.encode(0, pa, sa, gsc.FMT_BC7)          # ~30 ms of BC7 search on the only slot
+        t2 = srv.encode(1, pb, sb, gsc.FMT_BC1)          # queued behind it
+        with pytest.raises(gsc.GscError) as e:
+            srv.wait(t1, timeout_ms=0)
+        assert e.value.code == 5
+        srv.cancel(t2)
+        assert srv.wait(t2).status == 8
+        assert srv.wait(t1).status == 0
+        with pytest.raises(gsc.GscError):
+            srv.cancel(t1)                                # already completed and collected
+        st = srv.stats()
+        assert st.failed == 1 and st.done == 2
+        out = torch.empty((5000, 1, 3), device="cuda")
+        assert srv.wait(srv.eval(1, 5000, out, cams=torch.zeros((1, 3), device="cuda"))).status == 1
+    finally:
+        srv.close()
