@@ -366,6 +366,12 @@ typedef struct {
 gsc_status gsc_server_simulate(const gsc_server_params* p, const gsc_sim_request* reqs, int32_t n,
                                gsc_sim_result* res, uint64_t* peak_bytes);
 
+/* 1 in the checked build (libgsc_checked.so, selected with GSC_CHECKED=1 by the binding): every
+ * slot-order entry the decoders read is checked against [-1, n); entries outside are treated as
+ * empty slots (never used for an access) and the first one is reported by the next
+ * gsc_ctx_sync as GSC_ERR_DEVICE. 0 in the normal build, which trusts the slot order. */
+int32_t gsc_build_checked(void);
+
 /* Checkpoint file of a coded scene (the paper stores scenes as these streams; the file format is
  * this codec's own): a versioned header with the stream table, section sizes and an FNV-1a 64
  * checksum, then the blocks (table->total_bytes), the final slot order (n_groups * 16 int32) and

@@ -199,6 +199,9 @@ extern "C" gsc_status gsc_ctx_sync(gsc_ctx* c, void* stream) {
     GSC_CUDA(cudaMemset(c->d_status, 0, sizeof(st)));
     return (gsc_status)st[0];
   }
+  int where = 0;
+  const int chk = gsc_check_take(&where);  // checked build: a slot entry outside [-1, n)
+  if (chk != 0) return (gsc_status)chk;
   return GSC_OK;
 }
 

@@ -21,6 +21,44 @@ cudaError_t decode_init_tables() {
   return cudaMemcpyToSymbol(d_anc3b, kBC7Anchor3b, 64);
 }
 
+// ---- checked build ------------------------------------------------------------------------
+// With GSC_CHECKED every slot entry read from the caller's slot order is checked against
+// [-1, n): the first entry outside is recorded (status, slot) and every bad entry is treated as
+// an empty slot, so no access uses it. gsc_ctx_sync reports the record as GSC_ERR_DEVICE.
+#ifdef GSC_CHECKED
+static __device__ int g_check[2];
+__device__ __forceinline__ int32_t checked_slot(int32_t o, int64_t n, int64_t s) {
+  if (o < -1 || (int64_t)o >= n) {
+    if (atomicCAS(&g_check[0], 0, (int)GSC_ERR_DEVICE) == 0) g_check[1] = (int)(s < 0x7FFFFFFF ? s : 0x7FFFFFFF);
+    return -1;
+  }
+  return o;
+}
+int gsc_check_take(int* where) {
+  int h[2] = {0, 0};
+  if (cudaMemcpyFromSymbol(h, g_check, sizeof(h)) != cudaSuccess) { cudaGetLastError(); return 0; }
+  if (h[0]) {
+    const int z[2] = {0, 0};
+    cudaMemcpyToSymbol(g_check, z, sizeof(z));
+  }
+  if (where) *where = h[1];
+  return h[0];
+}
+#else
+__device__ __forceinline__ int32_t checked_slot(int32_t o, int64_t, int64_t) { return o; }
+int gsc_check_take(int* where) {
+  if (where) *where = 0;
+  return 0;
+}
+#endif
+extern "C" int32_t gsc_build_checked(void) {
+#ifdef GSC_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
 // ---- BC1 -----------------------------------------------------------------------------
 __device__ __forceinline__ int dx5(int x) { return (x << 3) | (x >> 2); }
 __device__ __forceinline__ int dx6(int x) { return (x << 2) | (x >> 4); }
@@ -427,7 +465,7 @@ __global__ void __launch_bounds__(256) k_decode2(DevTable T, const uint8_t* __re
 #pragma unroll
     for (int t = 0; t < 16; t++) my[17 * kt + t] = live ? tx[t] : 0u;
     __syncwarp();
-    const int32_t o = live ? __ldg(perm + g * 16 + kt) : -1;
+    const int32_t o = live ? checked_slot(__ldg(perm + g * 16 + kt), T.n, g * 16 + kt) : -1;
     if (o >= 0) {
       uint32_t wv[12];
 #pragma unroll
@@ -578,7 +616,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, EVAL_MIN_BLOCKS) k_eval2(DevTabl
   auto group_of = [&](int64_t pr) { return pr * 2 + gw; };
   auto perm_at = [&](int64_t pr) -> int32_t {
     const int64_t g = group_of(pr);
-    return (pr < npairs && g < T.n_groups) ? __ldg(perm + g * 16 + kt) : -1;
+    return (pr < npairs && g < T.n_groups) ? checked_slot(__ldg(perm + g * 16 + kt), T.n, g * 16 + kt) : -1;
   };
   auto pos_at = [&](int32_t o) -> float3 {
     if (!CAMS || o < 0) return make_float3(0.f, 0.f, 0.f);
@@ -819,7 +857,7 @@ __global__ void k_tex_streams(DevTable T, TexBases B, cudaTextureObject_t tex7, 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = i >> 4;
     const int k = (int)(i & 15);
-    const int32_t o = perm[s];
+    const int32_t o = checked_slot(perm[s], T.n, s);
     if (o < 0) continue;
     const int64_t g = s >> 4;
     const int t = (int)(s & 15);
@@ -941,10 +979,10 @@ struct gsc_tex_scene {
   float4* pos_slot;    // positions in slot order (x, y, z, 0), or null
 };
 
-__global__ void k_pos_slot(const float* __restrict__ pos, const int32_t* __restrict__ perm, int64_t ns,
+__global__ void k_pos_slot(const float* __restrict__ pos, const int32_t* __restrict__ perm, int64_t n, int64_t ns,
                            float4* __restrict__ out) {
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t o = perm[s];
+    const int32_t o = checked_slot(perm[s], n, s);
     out[s] = o >= 0 ? make_float4(pos[3 * (int64_t)o], pos[3 * (int64_t)o + 1], pos[3 * (int64_t)o + 2], 0.f)
                     : make_float4(0.f, 0.f, 0.f, 0.f);
   }
@@ -972,13 +1010,13 @@ __global__ void __launch_bounds__(256) k_eval_tex(DevTable T, TexBases B, cudaTe
     return make_float3(__ldg(pos + 3 * (int64_t)o), __ldg(pos + 3 * (int64_t)o + 1), __ldg(pos + 3 * (int64_t)o + 2));
   };
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int32_t o_n = s < ns ? __ldg(perm + s) : -1;
+  int32_t o_n = s < ns ? checked_slot(__ldg(perm + s), n, s) : -1;
   float3 p_n = pos_of(s, o_n);
   for (; s < ns; s += step) {
     const int32_t o = o_n;
     const float3 p = p_n;
     if (s + step < ns) {
-      o_n = __ldg(perm + s + step);
+      o_n = checked_slot(__ldg(perm + s + step), n, s + step);
       p_n = pos_of(s + step, o_n);
     }
     if (o < 0) {
@@ -1056,7 +1094,7 @@ extern "C" gsc_status gsc_tex_scene_create(gsc_ctx* c, const gsc_stream_table* t
     if (e == cudaSuccess) {
       int64_t grid = ceil_div64(ns, 256);
       if (grid > 152 * 16) grid = 152 * 16;
-      gsc_count_launch(); k_pos_slot<<<(int)grid, 256, 0, s>>>(d_pos, d_perm, ns, sc->pos_slot);
+      gsc_count_launch(); k_pos_slot<<<(int)grid, 256, 0, s>>>(d_pos, d_perm, (int64_t)T.n, ns, sc->pos_slot);
       e = cudaGetLastError();
     }
   }

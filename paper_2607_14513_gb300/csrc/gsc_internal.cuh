@@ -90,6 +90,10 @@ struct Carve {
   bool ok() const { return off <= cap; }
 };
 
+// Checked build (GSC_CHECKED): takes and clears the first slot-order check failure recorded by
+// the decode kernels on the current device (GSC_ERR_DEVICE and the slot), or 0.
+int gsc_check_take(int* where);
+
 // A context on `device`; init_tables = false skips the constant tables (already loaded by an
 // earlier context in this process), as the request loop's per-slot contexts do.
 gsc_status ctx_new(int device, bool init_tables, gsc_ctx** out);

@@ -13,6 +13,7 @@ import threading
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "lib", "libgsc.so")
+LIB_CHECKED_PATH = os.path.join(PKG, "lib", "libgsc_checked.so")  # GSC_CHECKED=1 selects it
 HEADER = os.path.join(PKG, "..", "include", "gsc.h")
 
 GSC_OK = 0
@@ -149,6 +150,7 @@ _SIGS = {
     "gsc_server_destroy": [_P],
     "gsc_server_simulate": [C.POINTER(ServerParams), C.POINTER(SimRequest), C.c_int32, C.POINTER(SimResult),
                             C.POINTER(C.c_uint64)],
+    "gsc_build_checked": [],
     "gsc_launch_count": [],
     "gsc_probe_int_peak": [_P, C.POINTER(C.c_double), _P],
     "gsc_ctx_set_timing": [_P, C.c_int],
@@ -168,7 +170,7 @@ def load(path: str | None = None):
     global _lib
     with _lock:
         if _lib is None:
-            p = path or LIB_PATH
+            p = path or (LIB_CHECKED_PATH if os.environ.get("GSC_CHECKED") == "1" else LIB_PATH)
             if not os.path.exists(p):
                 raise RuntimeError("libgsc.so not built (%s); run __graft_entry__.build()" % p)
             lib = C.CDLL(p)
