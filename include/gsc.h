@@ -26,7 +26,13 @@
  *  - Arrays are C-contiguous: float positions [n][3]; float SH [n][16][3] with the
  *    RGB triple innermost; texels uint8 [n][16][3]; perm int32 [n_groups * 16].
  *  - There is no CPU fallback: without a usable GB300 every call returns
- *    GSC_ERR_UNSUPPORTED.
+ *    GSC_ERR_UNSUPPORTED (except the host-only calls: gsc_server_simulate and the
+ *    checkpoint file calls on host buffers).
+ *  - A context serves one host thread at a time (it holds a pinned staging buffer and the
+ *    kernel timers); use one context per thread, as the request loop does per worker. The
+ *    request loop's own calls (gsc_server_*) may be made from any thread.
+ *  - Beyond the texture path, the batched form, the request loop and the allocation-free plan
+ *    allocate what their calls say (graphs, a memory pool, a static array).
  */
 #ifndef GSC_H
 #define GSC_H
