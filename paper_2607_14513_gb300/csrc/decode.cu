@@ -518,10 +518,13 @@ __constant__ float c_shc[16] = {SH_C0, -SH_C1, SH_C1, -SH_C1, SH_C2A, -SH_C2A, S
 // their colours agree bit for bit when their texels do. Views go in pairs through the
 // two-lane multiply-adds (one coefficient against the basis of two views), four views at a
 // time (three 16-byte stores of a Gaussian-major row when V is a multiple of 4).
-template <bool CAMS>
+// VF > 0: a launch of exactly VF views into Gaussian-major rows, known at compile time.
+template <bool CAMS, int VF>
 __device__ __forceinline__ void eval_store(const float (&xr)[16], const float (&xg)[16], const float (&xb)[16],
-                                           int64_t o, int64_t s, float3 p, const float (*s_view)[64], int V,
-                                           int out_order, int64_t n, int64_t ns, float* __restrict__ rgb) {
+                                           int64_t o, int64_t s, float3 p, const float (*s_view)[64], int V_,
+                                           int out_order_, int64_t n, int64_t ns, float* __restrict__ rgb) {
+  const int V = VF > 0 ? VF : V_;
+  const int out_order = VF > 0 ? (int)GSC_OUT_GAUSS_MAJOR : out_order_;
   const float2 np0 = make_float2(-p.x, -p.x), np1 = make_float2(-p.y, -p.y), np2 = make_float2(-p.z, -p.z);
   for (int v0 = 0; v0 < V; v0 += 4) {
     float res[12];
@@ -539,8 +542,9 @@ __device__ __forceinline__ void eval_store(const float (&xr)[16], const float (&
       r.x = n2.x > 0.f ? rsqrtf(n2.x) : 0.f;
       r.y = n2.y > 0.f ? rsqrtf(n2.y) : 0.f;
       dx = __fmul2_rn(dx, r); dy = __fmul2_rn(dy, r); dz = __fmul2_rn(dz, r);
-      if (n2.x <= 0.f) { dx.x = 0.f; dy.x = 0.f; dz.x = 1.f; }
-      if (n2.y <= 0.f) { dx.y = 0.f; dy.y = 0.f; dz.y = 1.f; }
+      // a camera on the Gaussian: r = 0 already zeroes x and y; the direction is (0, 0, 1)
+      if (n2.x <= 0.f) dz.x = 1.f;
+      if (n2.y <= 0.f) dz.y = 1.f;
       float2 P[16];
       sh_poly2(dx, dy, dz, P);
       float2 ar = make_float2(xr[0], xr[0]), ag = make_float2(xg[0], xg[0]), ab = make_float2(xb[0], xb[0]);
@@ -594,7 +598,7 @@ __device__ __forceinline__ void load_views(float (*s_view)[64], float* s_deq, co
 #ifndef EVAL_MIN_BLOCKS
 #define EVAL_MIN_BLOCKS 1
 #endif
-template <int KIND, bool CAMS>
+template <int KIND, bool CAMS, int VF>
 __global__ void __launch_bounds__(EVAL_THREADS, EVAL_MIN_BLOCKS) k_eval2(DevTable T, const uint8_t* __restrict__ blocks,
                                                const int32_t* __restrict__ perm, const float* __restrict__ dirs,
                                                const float* __restrict__ pos, const float* __restrict__ cams, int V,
@@ -661,7 +665,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, EVAL_MIN_BLOCKS) k_eval2(DevTabl
         const float2 b = __fmul2_rn(__fadd2_rn(make_float2(u23(p0, 2), u23(p1, 2)), m), f);
         xr[2 * j] = r.x; xr[2 * j + 1] = r.y; xg[2 * j] = gg.x; xg[2 * j + 1] = gg.y; xb[2 * j] = b.x; xb[2 * j + 1] = b.y;
       }
-      eval_store<CAMS>(xr, xg, xb, o, s, p, s_view, V, out_order, n, ns, rgb);
+      eval_store<CAMS, VF>(xr, xg, xb, o, s, p, s_view, V, out_order, n, ns, rgb);
     } else if (live && out_order == GSC_OUT_SLOT_ORDER) {
       for (int v = 0; v < V; v++) { float* d = rgb + ((int64_t)v * ns + s) * 3; d[0] = d[1] = d[2] = 0.f; }
     }
@@ -704,8 +708,13 @@ cudaError_t launch_decode_eval(const DevTable& T, const uint8_t* blocks, const i
   if (T.n_groups == 0) return cudaSuccess;
   const int grid = eval_grid(T.n_groups, sm_count, EVAL_THREADS / 32);
   const int kind = kind_of(T);
-#define EVAL_LAUNCH(K, C) \
-  do { gsc_count_launch(); k_eval2<K, C><<<grid, EVAL_THREADS, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order, rgb); } while (0)
+  // runtime view count only: a compile-time 8-view form raised this kernel to 140 registers (one
+  // resident CTA fewer) and measured no faster (the texture kernel does use one)
+#define EVAL_LAUNCH(K, C)                                                                                        \
+  do {                                                                                                           \
+    gsc_count_launch();                                                                                          \
+    k_eval2<K, C, 0><<<grid, EVAL_THREADS, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order, rgb);        \
+  } while (0)
   if (cams) {
     if (kind == 7) EVAL_LAUNCH(7, true); else if (kind == 1) EVAL_LAUNCH(1, true); else EVAL_LAUNCH(0, true);
   } else {
@@ -991,7 +1000,7 @@ __global__ void k_pos_slot(const float* __restrict__ pos, const int32_t* __restr
 // exact (q - 128) from a UNORM8 sample f = q / 255: f * 255 + 1.5 * 2^23 lands on 1.5 * 2^23 + q
 __device__ __forceinline__ float unorm_m128(float f) { return fmaf(f, 255.0f, 12582912.0f) - 12583040.0f; }
 
-template <int KIND, bool CAMS>
+template <int KIND, bool CAMS, int VF>
 __global__ void __launch_bounds__(256) k_eval_tex(DevTable T, TexBases B, cudaTextureObject_t tex7,
                                                   cudaTextureObject_t tex1, const int32_t* __restrict__ perm,
                                                   const float* __restrict__ dirs, const float* __restrict__ pos,
@@ -1049,7 +1058,7 @@ __global__ void __launch_bounds__(256) k_eval_tex(DevTable T, TexBases B, cudaTe
       const float q = s_deq[k];
       xr[k] = __fmul_rn(unorm_m128(f.x), q); xg[k] = __fmul_rn(unorm_m128(f.y), q); xb[k] = __fmul_rn(unorm_m128(f.z), q);
     }
-    eval_store<CAMS>(xr, xg, xb, o, s, p, s_view, V, out_order, n, ns, rgb);
+    eval_store<CAMS, VF>(xr, xg, xb, o, s, p, s_view, V, out_order, n, ns, rgb);
   }
 }
 
@@ -1142,11 +1151,17 @@ extern "C" gsc_status gsc_decode_eval_sh_tex(gsc_ctx* c, const gsc_tex_scene* sc
   const int64_t cap = (int64_t)(c->sm_count > 0 ? c->sm_count : 152) * 8;
   if (grid > cap) grid = cap;
   const int kind = kind_of(T);
-#define TEX_LAUNCH(K, C)                                                                                       \
-  do {                                                                                                         \
-    gsc_count_launch();                                                                                        \
-    k_eval_tex<K, C><<<(int)grid, 256, 0, st>>>(T, sc->B, sc->img[1].tex, sc->img[0].tex, d_perm, d_dirs, d_pos, \
-                                                d_cams, V, out_order, d_rgb, sc->pos_slot);                    \
+  // 8 views into Gaussian-major rows (the camera-pose workload) run a compile-time view count
+  const bool v8 = V == 8 && out_order == GSC_OUT_GAUSS_MAJOR;
+#define TEX_LAUNCH(K, C)                                                                                          \
+  do {                                                                                                            \
+    gsc_count_launch();                                                                                           \
+    if (v8)                                                                                                       \
+      k_eval_tex<K, C, 8><<<(int)grid, 256, 0, st>>>(T, sc->B, sc->img[1].tex, sc->img[0].tex, d_perm, d_dirs,    \
+                                                     d_pos, d_cams, V, out_order, d_rgb, sc->pos_slot);           \
+    else                                                                                                          \
+      k_eval_tex<K, C, 0><<<(int)grid, 256, 0, st>>>(T, sc->B, sc->img[1].tex, sc->img[0].tex, d_perm, d_dirs,    \
+                                                     d_pos, d_cams, V, out_order, d_rgb, sc->pos_slot);           \
   } while (0)
   if (d_cams) {
     if (kind == 7) TEX_LAUNCH(7, true); else if (kind == 1) TEX_LAUNCH(1, true); else TEX_LAUNCH(0, true);
