@@ -327,8 +327,11 @@ __device__ __forceinline__ void bc7_block(uint64_t lo, uint64_t hi, uint32_t (&t
         a0 = (c0 << al8) | (c0 >> ar8);
         a1 = (c1 << al8) | (c1 >> ar8);
       }
-      ep[s] = make_uint4((v0[0] | (v0[1] << 16)) << 2, (v0[2] | (a0 << 16)) << 2, (v1[0] | (v1[1] << 16)) << 2,
-                         (v1[2] | (a1 << 16)) << 2);
+      // (64 - w) E0 + w E1 + bias = (64 E0 + bias) + w (E1 - E0) modulo 2^32, and the true value of
+      // each 16-bit lane stays below 2^16, so base + w * diff gives the same 32 bits in one multiply-add
+      const uint32_t e0rg = (v0[0] | (v0[1] << 16)) << 2, e0ba = (v0[2] | (a0 << 16)) << 2;
+      const uint32_t e1rg = (v1[0] | (v1[1] << 16)) << 2, e1ba = (v1[2] | (a1 << 16)) << 2;
+      ep[s] = make_uint4(64u * e0rg + 0x00800080u, e1rg - e0rg, 64u * e0ba + 0x00800080u, e1ba - e0ba);
     }
   }
   // index streams at a fixed width per texel (anchor texels: texel 0, and a1, a2 in the primary)
@@ -346,8 +349,7 @@ __device__ __forceinline__ void bc7_block(uint64_t lo, uint64_t hi, uint32_t (&t
   // rotation: the alpha result (byte 3 of `al`, operand byte 7) replaces channel rot - 1
   const uint32_t rsel = rot == 0 ? 0x3210u : (rot == 1 ? 0x3217u : (rot == 2 ? 0x3270u : 0x3710u));
   // the reserved mode (first byte 0) decodes to 0: zero endpoints give exactly that below
-  if (!b0) ep[0] = ep[1] = ep[2] = make_uint4(0u, 0u, 0u, 0u);
-  const uint32_t bias = 0x00800080u;
+  if (!b0) ep[0] = ep[1] = ep[2] = make_uint4(0x00800080u, 0u, 0x00800080u, 0u);
   // both streams as 32-bit halves, advanced by funnel shifts (widths are at most 4 bits)
   uint32_t cl = (uint32_t)cs, ch = (uint32_t)(cs >> 32), al32 = (uint32_t)as, ah = (uint32_t)(as >> 32);
 #pragma unroll
@@ -357,11 +359,11 @@ __device__ __forceinline__ void bc7_block(uint64_t lo, uint64_t hi, uint32_t (&t
     ch >>= cbits;
     al32 = __funnelshift_r(al32, ah, abits);
     ah >>= abits;
-    const uint4 e = ep[(pm >> (2 * t)) & 3];
+    const uint4 e = ep[(pm >> (2 * t)) & 3];  // (base rg, diff rg, base ba, diff ba)
     const uint32_t cw = wc[ci], aw = wa[ai];
-    const uint32_t rg = (64u - cw) * e.x + cw * e.z + bias;
-    const uint32_t ba = (64u - cw) * e.y + cw * e.w + bias;
-    const uint32_t al = (64u - aw) * e.y + aw * e.w + bias;
+    const uint32_t rg = cw * e.y + e.x;
+    const uint32_t ba = cw * e.w + e.z;
+    const uint32_t al = aw * e.w + e.z;
     tx[t] = __byte_perm(__byte_perm(rg, ba, 0x0531u), al, rsel);
   }
 }
