@@ -54,6 +54,9 @@ def workload_cfg(name):
     return {"scene3m": S.SCENE, "medium262k": S.MEDIUM, "tiny4k": S.TINY}[name]
 
 
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e nominal, reported beside the measured copy bandwidth
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -249,6 +252,7 @@ def run_gsc(args, world, rank, local):
     ev_gbs = ev_bytes / (ev_ms * 1e-3) / 1e9
     roofline_eval = {"bound": "hbm", "achieved": round(ev_gbs, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(ev_gbs / hbm, 4), "peak_source": hbm_src,
+                     "frac_of_nominal": round(ev_gbs / HBM_NOMINAL_GBS, 4),
                      "traffic": MEASURED_TRAFFIC.get(args.workload, {}).get("k_eval2_bc7"),
                      "kernel": "k_eval2 (software BC7 decode + SH eval, all-BC7 coding, %d cameras, "
                                "Gaussian-major output)" % N_CAMS,
@@ -328,6 +332,7 @@ def time_tex_eval(args, ctx, gsc, stream, dev, rtab, bc1, bc7, perm, pos, cams, 
         if name == "bc7":
             res["roofline"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                                "frac": round(gbs / hbm, 4), "peak_source": hbm_src,
+                               "frac_of_nominal": round(gbs / HBM_NOMINAL_GBS, 4),
                                "traffic": MEASURED_TRAFFIC.get(args.workload, {}).get("k_eval_tex_bc7"),
                                "kernel": "k_eval_tex (texture-unit decode + SH eval, all-BC7, %d cameras, "
                                          "Gaussian-major output)" % N_CAMS,
