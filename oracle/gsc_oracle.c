@@ -16,6 +16,9 @@
  *    done independently inside larger spatial groups. Reading: spatial groups are
  *    chunks of G consecutive Gaussians in 30-bit Morton order.
  *  - Sec. IV-B, Fig. SetupD: block k of a group holds coefficient k of 16 Gaussians.
+ *    Fig. SetupA / SetupB (Table I's other rows): one Gaussian per block, or four
+ *    Gaussians' coefficients 4b..4b+3 in block b of four; texel placement inside a
+ *    block (raster order, row = Gaussian in B) is this codec's reading.
  *  - Sec. III-A/B: BTC, BC1, BC7 (D3D11 / Khronos BC7 format definitions). The paper
  *    uses a third-party encoder; the encoder here is the codec's own deterministic
  *    integer search (ties go to the lowest enumeration index).
@@ -180,6 +183,59 @@ void or_stage_group(const uint8_t* q, const int32_t* perm, int64_t g, uint8_t* t
     for (int k = 0; k < OR_SH; k++)
       for (int c = 0; c < 3; c++) tex[(k * 16 + t) * 3 + c] = (last >= 0) ? q[(last * OR_SH + k) * 3 + c] : 128;
   }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Block layouts (Sec. IV-B). A group is slots 16g..16g+15 and 16 blocks of     */
+/* 4 x 4 texels (texel t in raster order, row t / 4, column t % 4).             */
+/*  D, Fig. SetupD: block k, texel t = coefficient k of slot t.                 */
+/*  A, Fig. SetupA: one Gaussian per block: block k, texel t = coefficient t of */
+/*     slot k.                                                                  */
+/*  B, Fig. SetupB: four Gaussians in four blocks: the group is 4 quads of 4    */
+/*     slots; block b of quad v (k = 4v + b), row i, column j holds coefficient */
+/*     4b + j of slot 4v + i, so block 0 of a quad carries the first four       */
+/*     coefficients (bands 0 and 1) of its Gaussians.                           */
+/* ------------------------------------------------------------------------- */
+void or_layout_map(int layout, int k, int t, int* u, int* c) {
+  if (layout == OR_LAYOUT_A) { *u = k; *c = t; }
+  else if (layout == OR_LAYOUT_B) {
+    int v = k / 4, b = k % 4, i = t / 4, j = t % 4;
+    *u = 4 * v + i; *c = 4 * b + j;
+  } else { *u = t; *c = k; }
+}
+
+/* A fixed coding of a layout gives j of each group's 16 blocks to BC7 and the rest to
+ * BC1 (Table I: BC7 on the first block of each quad in layout B, on block 0 in D). D: the
+ * first j blocks; A: all or none; B: the first j / 4 blocks of every quad. */
+int or_layout_ok(int layout, int j) {
+  if (layout == OR_LAYOUT_D) return j >= 0 && j <= 16;
+  if (layout == OR_LAYOUT_A) return j == 0 || j == 16;
+  if (layout == OR_LAYOUT_B) return j >= 0 && j <= 16 && j % 4 == 0;
+  return 0;
+}
+
+int or_layout_bc7(int layout, int j, int k) {
+  if (layout == OR_LAYOUT_A) return j == 16;
+  if (layout == OR_LAYOUT_B) return (k % 4) < j / 4;
+  return k < j;
+}
+
+/* Texels of group g in a layout: tex[k][t][c]. A padding slot repeats the last valid slot
+ * before it in its group (128 if there is none), as in layout D. */
+void or_stage_layout(const uint8_t* q, const int32_t* perm, int layout, int64_t g, uint8_t* tex) {
+  int64_t src[16];
+  int64_t last = -1;
+  for (int u = 0; u < 16; u++) {
+    if (perm[16 * g + u] >= 0) last = perm[16 * g + u];
+    src[u] = last;
+  }
+  for (int k = 0; k < 16; k++)
+    for (int t = 0; t < 16; t++) {
+      int u, c;
+      or_layout_map(layout, k, t, &u, &c);
+      for (int ch = 0; ch < 3; ch++)
+        tex[(k * 16 + t) * 3 + ch] = src[u] >= 0 ? q[(src[u] * OR_SH + c) * 3 + ch] : 128;
+    }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -1000,28 +1056,64 @@ int or_rate_assemble(int64_t n, const int32_t* perm, const float* scales, uint32
 /* Decode every stream back to texels [n][16][3] in original order (inverse
  * permutation); coefficients a stream does not keep decode to 128 (zero). */
 int or_decode(const or_table* t, const uint8_t* blocks, const int32_t* perm, uint8_t* texels) {
-  uint8_t rgba[64];
+  uint8_t rgba[16][64];
+  const int layout = t->layout;
   for (int si = 0; si < t->n_streams; si++) {
     const or_stream* S = &t->s[si];
     int64_t gbytes = 16 * S->bc7_blocks + 8 * (S->bands - S->bc7_blocks);
     for (int64_t gi = 0; gi < S->n_groups; gi++) {
       int64_t g = S->first_group + gi;
       const uint8_t* src = blocks + S->byte_offset + gi * gbytes;
+      /* a group's BC7 blocks come first, then its BC1 blocks, each in block order;
+         blocks past the kept coefficients (layout D only) decode to 128 */
       for (int k = 0; k < OR_SH; k++) {
-        if (k < S->bands) {
-          if (k < S->bc7_blocks) { or_bc7_decode(src, rgba); src += 16; }
-          else { or_bc1_decode(src, rgba); src += 8; }
-        } else {
-          memset(rgba, 128, sizeof(rgba));
-        }
-        for (int u = 0; u < 16; u++) {
+        if (k < S->bands && or_layout_bc7(layout, S->bc7_blocks, k)) { or_bc7_decode(src, rgba[k]); src += 16; }
+      }
+      for (int k = 0; k < OR_SH; k++) {
+        if (k >= S->bands) memset(rgba[k], 128, sizeof(rgba[k]));
+        else if (!or_layout_bc7(layout, S->bc7_blocks, k)) { or_bc1_decode(src, rgba[k]); src += 8; }
+      }
+      for (int k = 0; k < OR_SH; k++)
+        for (int tt = 0; tt < 16; tt++) {
+          int u, c;
+          or_layout_map(layout, k, tt, &u, &c);
           int32_t o = perm[16 * g + u];
           if (o < 0) continue;
-          for (int c = 0; c < 3; c++) texels[((int64_t)o * OR_SH + k) * 3 + c] = rgba[4 * u + c];
+          for (int ch = 0; ch < 3; ch++) texels[((int64_t)o * OR_SH + c) * 3 + ch] = rgba[k][4 * tt + ch];
         }
-      }
     }
   }
+  return 0;
+}
+
+/* Fixed coding of a layout (Sec. IV-B, Table I): j = bc7_blocks of each group's blocks in
+ * BC7 (which ones: or_layout_bc7), the rest in BC1, one stream; each group's bytes are its
+ * BC7 blocks then its BC1 blocks, in block order. The slot order is the caller's. */
+int or_encode_layout(const uint8_t* q, int64_t n, const int32_t* perm, const float* scales, int layout,
+                     int bc7_blocks, uint8_t* blocks, or_table* t) {
+  if (!or_layout_ok(layout, bc7_blocks)) return -1;
+  int64_t ng = (n + 15) / 16;
+  const int j = bc7_blocks;
+  const int64_t gbytes = 16 * j + 8 * (16 - j);
+  memset(t, 0, sizeof(*t));
+  t->n = n; t->n_groups = ng; t->layout = layout;
+  t->format = j == 16 ? 7 : (j == 0 ? 1 : 2);
+  for (int k = 0; k < OR_SH; k++) t->scales[k] = scales[k];
+  or_weights(scales, t->weights);
+  uint8_t tex[16 * 16 * 3];
+  for (int64_t g = 0; g < ng; g++) {
+    or_stage_layout(q, perm, layout, g, tex);
+    uint8_t* dst = blocks + g * gbytes;
+    for (int k = 0; k < OR_SH; k++)
+      if (or_layout_bc7(layout, j, k)) { or_bc7_encode(tex + 48 * k, dst); dst += 16; }
+    for (int k = 0; k < OR_SH; k++)
+      if (!or_layout_bc7(layout, j, k)) { or_bc1_encode(tex + 48 * k, dst); dst += 8; }
+  }
+  t->n_streams = 1;
+  t->s[0].bands = 16; t->s[0].bc7_blocks = j;
+  t->s[0].first_group = 0; t->s[0].n_groups = ng; t->s[0].byte_offset = 0;
+  t->total_bytes = ng * gbytes;
+  t->used_bits = (uint64_t)t->total_bytes * 8;
   return 0;
 }
 

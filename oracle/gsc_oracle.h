@@ -22,13 +22,19 @@ typedef struct {
 
 typedef struct {
   int32_t n_streams;
-  int32_t format;      /* 1 BC1, 7 BC7, 0 rate-controlled */
+  int32_t format;      /* 1 BC1, 7 BC7, 0 rate-controlled, 2 a fixed BC7 / BC1 mix */
   int64_t n, n_groups, total_bytes;
   uint64_t budget_bits, used_bits, lambda;
   float scales[OR_SH];
   uint32_t weights[OR_SH];
   or_stream s[OR_MODES];
+  int32_t layout;      /* OR_LAYOUT_D, _A or _B */
 } or_table;
+
+/* Block layouts (Sec. IV-B): a group is 16 slots and 16 blocks in every layout. */
+#define OR_LAYOUT_D 0 /* Fig. SetupD: block k holds coefficient k of the 16 Gaussians */
+#define OR_LAYOUT_A 1 /* Fig. SetupA: block k holds the 16 coefficients of one Gaussian */
+#define OR_LAYOUT_B 2 /* Fig. SetupB: 4 blocks hold the 16 coefficients of 4 Gaussians */
 
 int or_scales(const float* sh, int64_t n, uint32_t permille, float* scales);
 uint8_t or_quant1(float x, float s);
@@ -37,6 +43,12 @@ uint32_t or_morton30(uint32_t x, uint32_t y, uint32_t z);
 uint32_t or_colour_key(uint32_t r, uint32_t g, uint32_t b);
 int or_plan(const float* pos, const uint8_t* q, int64_t n, int64_t group_size, int sort, int32_t* perm);
 void or_stage_group(const uint8_t* q, const int32_t* perm, int64_t g, uint8_t* tex /*[16 blocks][16 texels][3]*/);
+void or_layout_map(int layout, int k, int t, int* u, int* c);
+int or_layout_ok(int layout, int bc7_blocks);
+int or_layout_bc7(int layout, int bc7_blocks, int k);
+void or_stage_layout(const uint8_t* q, const int32_t* perm, int layout, int64_t g, uint8_t* tex /*[16][16][3]*/);
+int or_encode_layout(const uint8_t* q, int64_t n, const int32_t* perm, const float* scales, int layout,
+                     int bc7_blocks, uint8_t* blocks, or_table* t);
 
 void or_bc1_palette(uint16_t c0, uint16_t c1, uint8_t* pal /*[4][4] RGBA*/);
 void or_bc1_decode(const uint8_t* blk, uint8_t* out /*[16][4]*/);

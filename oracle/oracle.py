@@ -48,7 +48,9 @@ class Table(C.Structure):
     _fields_ = [("n_streams", C.c_int32), ("format", C.c_int32), ("n", C.c_int64), ("n_groups", C.c_int64),
                 ("total_bytes", C.c_int64), ("budget_bits", C.c_uint64), ("used_bits", C.c_uint64),
                 ("lambda_", C.c_uint64), ("scales", C.c_float * SH), ("weights", C.c_uint32 * SH),
-                ("s", Stream * MODES)]
+                ("s", Stream * MODES), ("layout", C.c_int32)]
+
+LAYOUT_D, LAYOUT_A, LAYOUT_B = 0, 1, 2
 
 
 def lib():
@@ -66,6 +68,11 @@ def lib():
                 "or_colour_key": (u32, [u32, u32, u32]),
                 "or_plan": (i32, [P, P, i64, i64, i32, P]),
                 "or_stage_group": (None, [P, P, i64, P]),
+                "or_layout_map": (None, [i32, i32, i32, P, P]),
+                "or_layout_ok": (i32, [i32, i32]),
+                "or_layout_bc7": (i32, [i32, i32, i32]),
+                "or_stage_layout": (None, [P, P, i32, i64, P]),
+                "or_encode_layout": (i32, [P, i64, P, P, i32, i32, P, P]),
                 "or_bc1_palette": (None, [C.c_uint16, C.c_uint16, P]),
                 "or_bc1_decode": (None, [P, P]),
                 "or_bc1_candidate_sse": (u64, [P, C.c_uint16, C.c_uint16]),
@@ -266,8 +273,50 @@ def rate_control(D, budget):
     return rc, mode, lam.value
 
 
+def layout_map(layout, k, t):
+    """(slot in group, coefficient) held by texel t of block k (Sec. IV-B, Figs. SetupA/B/D)."""
+    u, c = C.c_int(0), C.c_int(0)
+    lib().or_layout_map(layout, k, t, C.byref(u), C.byref(c))
+    return u.value, c.value
+
+
+def layout_ok(layout, bc7_blocks):
+    return bool(lib().or_layout_ok(layout, bc7_blocks))
+
+
+def layout_bc7(layout, bc7_blocks, k):
+    return bool(lib().or_layout_bc7(layout, bc7_blocks, k))
+
+
+def stage_layout(q, perm, layout):
+    """Texels of every group in a layout: [n_groups, 16 blocks, 16 texels, 3]."""
+    q = _c(q, np.uint8)
+    perm = _c(perm, np.int32)
+    ng = perm.shape[0] // 16
+    out = np.zeros((ng, 16, 16, 3), np.uint8)
+    for g in range(ng):
+        lib().or_stage_layout(_p(q), _p(perm), layout, g, _p(out[g]))
+    return out
+
+
+def encode_layout(q, perm, sc, layout, bc7_blocks):
+    """Fixed coding of a layout: bc7_blocks BC7 blocks per group, the rest BC1 (one stream)."""
+    q = _c(q, np.uint8)
+    perm = _c(perm, np.int32)
+    sc = _c(sc, np.float32)
+    n = q.shape[0]
+    ng = (n + 15) // 16
+    blocks = np.zeros(max(ng * 256, 1), np.uint8)
+    t = Table()
+    rc = lib().or_encode_layout(_p(q), n, _p(perm), _p(sc), layout, bc7_blocks, _p(blocks), C.byref(t))
+    if rc != 0:
+        raise ValueError("or_encode_layout failed: %d" % rc)
+    return dict(blocks=blocks[:t.total_bytes], perm=perm[:ng * 16].copy(), table=t)
+
+
 def table_dict(t: Table):
     return dict(n_streams=t.n_streams, format=t.format, n=t.n, n_groups=t.n_groups, total_bytes=t.total_bytes,
+                layout=t.layout,
                 budget_bits=t.budget_bits, used_bits=t.used_bits, lambda_=t.lambda_,
                 scales=np.array(t.scales[:], np.float32), weights=np.array(t.weights[:], np.uint32),
                 streams=[dict(bands=t.s[i].bands, bc7_blocks=t.s[i].bc7_blocks, first_group=t.s[i].first_group,
