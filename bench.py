@@ -51,7 +51,13 @@ MEASURED_TRAFFIC = {"scene3m": {"k_bc7": 870084864, "k_eval2_bc7": None, "k_eval
 
 
 def workload_cfg(name):
-    return {"scene3m": S.SCENE, "medium262k": S.MEDIUM, "tiny4k": S.TINY}[name]
+    return {"scene3m": S.SCENE, "medium262k": S.MEDIUM, "tiny4k": S.TINY, "layouts3m": S.SCENE}[name]
+
+
+# Table I's fixed codings of the other block layouts (Figs. SetupA / SetupB), and layout D's
+# "BC7 on the first block" mix: (name, layout, format, BC7 blocks per group, bytes per Gaussian)
+LAYOUT_CODINGS = [("A_bc1", 1, 1, 0, 8.0), ("A_bc7", 1, 7, 16, 16.0), ("B_bc7_first", 2, 2, 4, 10.0),
+                  ("D_bc7_first", 0, 2, 1, 8.5)]
 
 
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e nominal, reported beside the measured copy bandwidth
@@ -381,6 +387,178 @@ def run_e2e(args, ctx, gsc, stream, dev, sc, step, world):
 
 
 # ------------------------------------------------------------------------------------------------
+def run_layouts(args, world, rank, local):
+    """One step: the reorder plan, then every coding of LAYOUT_CODINGS (encode, then fused decode +
+    SH evaluation of 8 cameras into Gaussian-major rows) of the 3M-Gaussian scene."""
+    import torch
+    from paper_2607_14513_gb300 import gsc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = dict(S.SCENE)
+    cfg["seed"] = cfg["seed"] + 1000 * rank
+    n = cfg["n"]
+    ng = (n + 15) // 16
+    ns = ng * 16
+    sc = S.make_scene(**cfg)
+    ctx = gsc.Context(local)
+    stream = torch.cuda.Stream(dev)
+    pos = torch.from_numpy(sc.pos).to(dev)
+    sh = torch.from_numpy(sc.sh).to(dev)
+    cams = torch.from_numpy(S.make_cams(N_CAMS, 1100 + rank)).to(dev)
+    ws_bytes = max(int(ctx.lib.gsc_workspace_bytes(n, C_ref(gsc.EncodeParams(f, 0, None, None, lay, j))))
+                   for _, lay, f, j, _ in LAYOUT_CODINGS)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    bufs = {c[0]: torch.empty(ng * 256, dtype=torch.uint8, device=dev) for c in LAYOUT_CODINGS}
+    perms = {c[0]: torch.empty(ns, dtype=torch.int32, device=dev) for c in LAYOUT_CODINGS}
+    rgb = torch.empty((n, N_CAMS, 3), dtype=torch.float32, device=dev)
+    ev = {c[0]: [torch.cuda.Event(enable_timing=True) for _ in range(3)] for c in LAYOUT_CODINGS}
+    acc = {c[0]: [0.0, 0.0] for c in LAYOUT_CODINGS}
+    tables = {}
+
+    def step(pos_d, sh_d, record=False):
+        perm, scales = gsc.gsc_plan_reorder(ctx, pos_d, sh_d, ws=ws, stream=stream)
+        out = []
+        for name, lay, fmt, j, _ in LAYOUT_CODINGS:
+            e = ev[name]
+            e[0].record(stream)
+            blk, po, tab = gsc.gsc_encode(ctx, sh_d, perm, scales, fmt, ws=ws, out=bufs[name], perm_out=perms[name],
+                                          stream=stream, layout=lay, bc7_blocks=j)
+            e[1].record(stream)
+            gsc.gsc_decode_eval_sh(ctx, tab, blk, po, pos=pos_d, cams=cams, out_order=gsc.OUT_GAUSS_MAJOR, out=rgb,
+                                   stream=stream)
+            e[2].record(stream)
+            tables[name] = tab
+            out.append((tab, blk, po))
+        if record:
+            stream.synchronize()
+            for name in acc:
+                acc[name][0] += ev[name][0].elapsed_time(ev[name][1])
+                acc[name][1] += ev[name][1].elapsed_time(ev[name][2])
+        return out
+
+    for _ in range(args.warmup):
+        step(pos, sh)
+    stream.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    gsc.set_timing(ctx, True)
+    launches0 = gsc.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(pos, sh)
+    e1.record(stream)
+    stream.synchronize()
+    launches = gsc.launch_count() - launches0
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    kt = {k: gsc.kernel_time(ctx, k) for k in ["plan", "bc1_encode", "bc7_encode", "decode_eval"]}
+    gsc.set_timing(ctx, False)
+    ms_step = max_over_ranks(ms_total / args.steps, world, dev)
+    value = world * n / (ms_step * 1e-3) / 1e6
+    # per-coding times (event pairs around each call; a separate pass so the timed loop has no extra syncs)
+    for _ in range(args.steps):
+        step(pos, sh, record=True)
+
+    hbm, hbm_src = peaks()
+    bc7_blocks_step = sum(ng * j for _, _, _, j, _ in LAYOUT_CODINGS)
+    bc7_ms = kt["bc7_encode"][0] / max(1, args.steps)
+    int_peak = gsc.int_peak(ctx, stream=stream)
+    bc7_achieved = BC7_EVALS_PER_BLOCK * OPS_PER_EVAL * bc7_blocks_step / (bc7_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(bc7_achieved, 3), "peak": round(int_peak / 1e12, 3),
+                "unit": "Tops/s", "frac": round(bc7_achieved / (int_peak / 1e12), 4), "traffic": None,
+                "kernel": "k_bc7 on staged texels (every BC7 block of the step's codings)",
+                "peak_source": "measured on this GPU by gsc_probe_int_peak (IADD3/LOP3/IMAD chains)",
+                "algorithmic": "%d palette evaluations x %d int ops per block, %d BC7 blocks per step" % (
+                    BC7_EVALS_PER_BLOCK, OPS_PER_EVAL, bc7_blocks_step)}
+    stages, rooflines = {}, {}
+    for name, lay, fmt, j, bpg in LAYOUT_CODINGS:
+        enc_ms, ev_ms = acc[name][0] / args.steps, acc[name][1] / args.steps
+        tab = tables[name]
+        by = (tab.total_bytes / n + 4 + 12 + N_CAMS * 12) * n
+        gbs = by / (ev_ms * 1e-3) / 1e9
+        stages[name] = {"bytes_per_gaussian": round(tab.total_bytes / n, 4), "table_one_bytes": bpg,
+                        "encode_ms": round(enc_ms, 3), "encode_MGauss_s": round(n / (enc_ms * 1e-3) / 1e6, 2),
+                        "decode_eval_ms": round(ev_ms, 4), "decode_eval_GB_s": round(gbs, 1),
+                        "decode_eval_frac_hbm": round(gbs / hbm, 4)}
+        if name == "A_bc7":
+            rooflines = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(gbs / hbm, 4), "peak_source": hbm_src,
+                         "frac_of_nominal": round(gbs / HBM_NOMINAL_GBS, 4), "traffic": None,
+                         "kernel": "k_eval2 layout A, all-BC7 (16 B block + 4 B perm + 12 B position + %d x 12 B "
+                                   "output per Gaussian)" % N_CAMS}
+    stages["plan_ms"] = round(kt["plan"][0] / max(1, args.steps), 4)
+
+    # end to end: pinned host inputs in, every coding's blocks and slot order back to the host
+    pos_h = torch.from_numpy(sc.pos).pin_memory()
+    sh_h = torch.from_numpy(sc.sh).pin_memory()
+    pos_d, sh_d = torch.empty_like(pos_h, device=dev), torch.empty_like(sh_h, device=dev)
+    host_out = {c[0]: torch.empty(ng * 256, dtype=torch.uint8).pin_memory() for c in LAYOUT_CODINGS}
+    host_perm = torch.empty(ns, dtype=torch.int32).pin_memory()
+    bo = [0]
+
+    def one():
+        with torch.cuda.stream(stream):
+            pos_d.copy_(pos_h, non_blocking=True)
+            sh_d.copy_(sh_h, non_blocking=True)
+        res = step(pos_d, sh_d)
+        bo[0] = 4 * ns
+        with torch.cuda.stream(stream):
+            for (name, _, _, _, _), (tab, blk, po) in zip(LAYOUT_CODINGS, res):
+                host_out[name][:tab.total_bytes].copy_(blk, non_blocking=True)
+                bo[0] += tab.total_bytes
+            host_perm.copy_(res[-1][2], non_blocking=True)
+
+    one()
+    stream.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    stream.synchronize()
+    t = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
+    e2e = {"value": round(world * n / t / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": int(n * (12 + 192)),
+           "d2h_bytes_per_step": int(bo[0]), "ms_per_step": round(t * 1e3, 3),
+           "path": "pinned host pos+SH -> plan, four codings, their decode + SH eval -> every coding's blocks "
+                   "and the slot order to host"}
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u8 texels / int32 search / f32 SH eval",
+           "data": "synthetic (seeded; stands in for the paper's trained scenes)",
+           "config": {"workload": "layouts: %d Gaussians; Table I codings of layout A (BC1, BC7), layout B (BC7 on "
+                                  "the first block of each quad, BC1 on the rest) and layout D (BC7 on block 0); "
+                                  "each decoded + SH-evaluated for %d camera poses" % (n, N_CAMS),
+                      "n_gaussians": n, "parallelism": "weak, one scene per GPU" if world > 1 else "single GPU",
+                      "l2": "inputs larger than L2 (SH 192 B/Gaussian)"},
+           "roofline": roofline, "roofline_decode_eval": rooflines, "stages": stages, "clocks": clk, "e2e": e2e,
+           "gpu_launches": int(launches)}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline("layouts3m", budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def C_ref(x):
+    import ctypes
+    return ctypes.byref(x)
+
+
+# ------------------------------------------------------------------------------------------------
 def run_batch(args, world, rank, local):
     """64 scenes of uneven sizes: one persistent encode launch + one captured evaluation graph,
     against per-scene plain calls (plan, encode, decode + SH eval per scene) on the same data."""
@@ -690,6 +868,24 @@ def cpu_baseline_mix(mix, budget_s=20.0):
 
 # ------------------------------------------------------------------------------------------------
 def cpu_baseline(workload, budget_s=20.0):
+    if workload == "layouts3m":
+        return cpu_baseline_layouts(budget_s)
+    return cpu_baseline_d(workload, budget_s)
+
+
+def cpu_baseline_layouts(budget_s=20.0):
+    """The oracle's per-block coding times (scene-scale sample of layout D's blocks) charged per
+    Gaussian to the layout codings of one step: BC7 / BC1 blocks per Gaussian of each coding, plus
+    the plan and one decode + SH evaluation per coding."""
+    b = cpu_baseline_d("scene3m", budget_s=budget_s)
+    st = {k: v * 1e-6 for k, v in b["stage_us_per_gaussian"].items()}
+    per_g = st["plan"] + sum((j / 16.0) * st["bc7"] + (1 - j / 16.0) * st["bc1"] + st["decode_eval"]
+                             for _, _, _, j, _ in LAYOUT_CODINGS)
+    return {"value": round(1.0 / per_g / 1e6, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": b["sample"] + "; charged per Gaussian by each coding's BC7 / BC1 block counts"}
+
+
+def cpu_baseline_d(workload, budget_s=20.0):
     """The oracle, as it stands, single-threaded on a bounded sample of the workload.
 
     Per stage it codes a sample and charges the per-Gaussian time; the stages are the
@@ -775,7 +971,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gsc", choices=["gsc", "reference"])
-    ap.add_argument("--workload", default="scene3m", choices=["scene3m", "medium262k", "tiny4k", "batch64", "serve"])
+    ap.add_argument("--workload", default="scene3m",
+                    choices=["scene3m", "medium262k", "tiny4k", "layouts3m", "batch64", "serve"])
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -789,6 +986,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args, world, rank, local)
+        return
+    if args.workload == "layouts3m":
+        run_layouts(args, world, rank, local)
         return
     run_gsc(args, world, rank, local)
 

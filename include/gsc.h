@@ -56,7 +56,18 @@ typedef enum {
   GSC_ERR_CANCELLED = 8    /* a queued request of the request loop was cancelled */
 } gsc_status;
 
-typedef enum { GSC_FMT_RATE = 0, GSC_FMT_BC1 = 1, GSC_FMT_BC7 = 7 } gsc_format;
+/* GSC_FMT_MIXED: a fixed number of BC7 blocks per group (gsc_encode_params.bc7_blocks), the
+ * rest BC1 (Table I's "BC7 on the first block(s), BC1 on the rest" rows). */
+typedef enum { GSC_FMT_RATE = 0, GSC_FMT_BC1 = 1, GSC_FMT_MIXED = 2, GSC_FMT_BC7 = 7 } gsc_format;
+
+/* Block layouts (Sec. IV-B). A group is 16 slots (16g..16g+15) and 16 blocks of 4x4 texels
+ * (texel t in raster order) in every layout:
+ *  D (Fig. SetupD): block k holds coefficient k of the 16 Gaussians, texel t = slot 16g + t.
+ *  A (Fig. SetupA): block k holds the 16 coefficients of slot 16g + k, texel t = coefficient t.
+ *  B (Fig. SetupB): quads of 4 slots and 4 blocks; block b of quad v (k = 4v + b), row i,
+ *    column j holds coefficient 4b + j of slot 16g + 4v + i (block 0 of a quad carries the
+ *    first four coefficients of its Gaussians). */
+typedef enum { GSC_LAYOUT_D = 0, GSC_LAYOUT_A = 1, GSC_LAYOUT_B = 2 } gsc_layout;
 
 typedef enum {
   GSC_OUT_VIEW_MAJOR = 0,  /* rgb [V][n][3], original Gaussian order (through the inverse permutation) */
@@ -84,11 +95,19 @@ typedef struct {
    * GSC_FMT_BC1 and GSC_FMT_BC7 would write for d_perm. */
   uint8_t* d_bc1_blocks;
   uint8_t* d_bc7_blocks;
+  /* Block layout (gsc_layout; 0 = D). Layouts A and B take BC1, BC7 and GSC_FMT_MIXED, not the
+   * rate control (its streams drop coefficients, which layout D's blocks make possible). */
+  int32_t layout;
+  /* GSC_FMT_MIXED only: BC7 blocks per group, j. D: 0..16, the first j blocks; B: 0, 4, 8, 12 or
+   * 16, the first j / 4 blocks of every quad (j = 4 is Table I's 10 bytes per Gaussian); A: 0 or 16. */
+  int32_t bc7_blocks;
 } gsc_encode_params;
 
-/* One fixed-rate stream: every group in it keeps `bands` coefficients, the first
- * `bc7_blocks` coded BC7 (16 B) and the rest BC1 (8 B); coefficients not kept
- * decode to zero (texel 128). Group bytes = 16 * bc7_blocks + 8 * (bands - bc7_blocks). */
+/* One fixed-rate stream: every group in it keeps `bands` coefficients, `bc7_blocks` of its
+ * blocks coded BC7 (16 B) and the rest BC1 (8 B); coefficients not kept decode to zero
+ * (texel 128). Group bytes = 16 * bc7_blocks + 8 * (bands - bc7_blocks): the group's BC7
+ * blocks in block order, then its BC1 blocks in block order. Which blocks are BC7 follows the
+ * layout (gsc_encode_params.bc7_blocks); layouts A and B keep all 16 coefficients. */
 typedef struct {
   int32_t bands, bc7_blocks;
   int64_t first_group, n_groups, byte_offset;
@@ -102,6 +121,7 @@ typedef struct {
   float scales[16];     /* s_k: x' = (q - 128) / 255 * s_k */
   uint32_t weights[16]; /* w_k used by the rate control */
   gsc_stream s[14];
+  int32_t layout;       /* gsc_layout of the blocks */
 } gsc_stream_table;
 
 /* Context on one device (made current by every call). */
@@ -147,11 +167,13 @@ gsc_status gsc_plan_reorder_static(gsc_ctx* ctx, const float* d_pos, const float
  * d_sh [n][16][3] float -> d_q [n][16][3] uint8. */
 gsc_status gsc_quantise(gsc_ctx* ctx, const float* d_sh, int64_t n, const float* d_scales, uint8_t* d_q, void* stream);
 
-/* Sec. IV-B (Fig. SetupD), Sec. III-B, Sec. IV-B rate control. Group g = slots
- * 16g..16g+15; block k of group g holds coefficient k of those 16 Gaussians, texel t
- * in raster order = slot 16g + t (a padding slot repeats the group's last valid
- * slot). BC1 / BC7 formats code all 16 blocks of every group; GSC_FMT_RATE picks one
- * of 14 stream modes per group under the budget floor(target_bpt_x4 * 4 * n) bits.
+/* Sec. IV-B (Figs. SetupD, SetupA, SetupB), Sec. III-B, Sec. IV-B rate control. Group g =
+ * slots 16g..16g+15; its 16 blocks hold those Gaussians' coefficients as the layout says (a
+ * padding slot repeats the group's last valid slot). BC1 / BC7 formats code all 16 blocks
+ * of every group; GSC_FMT_MIXED codes ep->bc7_blocks of them BC7 and the rest BC1 (one
+ * stream); GSC_FMT_RATE (layout D) picks one of 14 stream modes per group under the budget
+ * floor(target_bpt_x4 * 4 * n) bits. Layouts A and B and GSC_FMT_MIXED stage the texels in
+ * the workspace and need ws_bytes >= gsc_workspace_bytes(n, ep).
  * d_blocks receives the streams back to back (capacity n_groups * 256 bytes),
  * d_perm_out the final slot order, *h_table the stream table. Synchronises `stream`
  * before returning (the table carries the scales and, in GSC_FMT_RATE, device results);

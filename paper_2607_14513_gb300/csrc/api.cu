@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include "gsc_internal.cuh"
+#include "layout.cuh"
 
 #include <atomic>
 
@@ -205,12 +206,32 @@ extern "C" gsc_status gsc_ctx_sync(gsc_ctx* c, void* stream) {
   return GSC_OK;
 }
 
+// BC7 blocks per group of a fixed coding, or -1 if the request is not one
+static int fixed_bc7_blocks(const gsc_encode_params* ep) {
+  if (ep->format == GSC_FMT_BC1) return 0;
+  if (ep->format == GSC_FMT_BC7) return 16;
+  if (ep->format == GSC_FMT_MIXED) return ep->bc7_blocks;
+  return -1;
+}
+
+// fixed codings that stage texels in the workspace: every coding of layouts A and B, and the mix
+static bool staged_coding(const gsc_encode_params* ep) {
+  return ep->layout != GSC_LAYOUT_D || ep->format == GSC_FMT_MIXED;
+}
+
 extern "C" size_t gsc_workspace_bytes(int64_t n, const gsc_encode_params* ep) {
   if (n < 0) return 0;
   size_t b = plan_ws_bytes(n);
   if (ep && ep->format == GSC_FMT_RATE) {
     size_t r = rate_ws_bytes(ceil_div64(n, 16));
     if (r > b) b = r;
+  }
+  if (ep && staged_coding(ep)) {
+    const int j = fixed_bc7_blocks(ep);
+    if (j >= 0 && j <= 16) {
+      size_t r = layout_ws_bytes(ceil_div64(n, 16), j);
+      if (r > b) b = r;
+    }
   }
   return b;
 }
@@ -258,7 +279,12 @@ extern "C" gsc_status gsc_encode(gsc_ctx* c, const float* d_sh, int64_t n, const
                                  void* stream) {
   GscRange gsc_range_("gsc_encode");
   if (!c || !ep || !h_table || !n_ok(n) || !d_scales) return GSC_ERR_INVALID_ARG;
-  if (ep->format != GSC_FMT_BC1 && ep->format != GSC_FMT_BC7 && ep->format != GSC_FMT_RATE) return GSC_ERR_INVALID_ARG;
+  if (ep->format != GSC_FMT_BC1 && ep->format != GSC_FMT_BC7 && ep->format != GSC_FMT_RATE &&
+      ep->format != GSC_FMT_MIXED)
+    return GSC_ERR_INVALID_ARG;
+  if (ep->layout != GSC_LAYOUT_D && ep->layout != GSC_LAYOUT_A && ep->layout != GSC_LAYOUT_B) return GSC_ERR_INVALID_ARG;
+  if (staged_coding(ep) && (ep->format == GSC_FMT_RATE || !lay_ok(ep->layout, fixed_bc7_blocks(ep))))
+    return GSC_ERR_INVALID_ARG;
   if (ep->format == GSC_FMT_RATE && (ep->target_bpt_x4 == 0 || ep->target_bpt_x4 > 64)) return GSC_ERR_INVALID_ARG;
   if (n > 0 && (!d_sh || !d_perm || !d_blocks || !d_perm_out)) return GSC_ERR_INVALID_ARG;
   if (!aligned(d_sh, 16) || !aligned(d_blocks, 16) || !aligned(d_ws, 256)) return GSC_ERR_INVALID_ARG;
@@ -285,7 +311,12 @@ extern "C" gsc_status gsc_encode(gsc_ctx* c, const float* d_sh, int64_t n, const
     memcpy(h_table->scales, scales, sizeof(scales));
     return s;
   }
-  if (ep->format == GSC_FMT_BC1) {
+  const int j = fixed_bc7_blocks(ep);
+  if (staged_coding(ep)) {
+    if (n > 0 && (!d_ws || ws_bytes < layout_ws_bytes(ng, j))) return GSC_ERR_OOM;
+    const gsc_status s = layout_encode_run(c, d_sh, n, d_perm, d_scales, ep->layout, j, d_blocks, d_ws, ws_bytes, st);
+    if (s != GSC_OK) return s;
+  } else if (ep->format == GSC_FMT_BC1) {
     GscTimed tm(c, T_BC1, st);
     GSC_CUDA(launch_bc1_groups(d_sh, d_perm, d_scales, ng, d_blocks, nullptr, nullptr, st));
   } else {
@@ -295,17 +326,17 @@ extern "C" gsc_status gsc_encode(gsc_ctx* c, const float* d_sh, int64_t n, const
   if (ng > 0 && d_perm_out != d_perm)
     GSC_CUDA(cudaMemcpyAsync(d_perm_out, d_perm, sizeof(int32_t) * ng * 16, cudaMemcpyDeviceToDevice, st));
   GSC_CUDA(cudaStreamSynchronize(st));
-  const int bpb = ep->format == GSC_FMT_BC7 ? 16 : 8;
   h_table->n_streams = 1;
   h_table->format = ep->format;
+  h_table->layout = ep->layout;
   h_table->n = n;
   h_table->n_groups = ng;
-  h_table->total_bytes = ng * 16 * bpb;
+  h_table->total_bytes = ng * (16 * j + 8 * (16 - j));
   h_table->used_bits = (uint64_t)h_table->total_bytes * 8;
   memcpy(h_table->scales, hs, sizeof(float) * GSC_SH);
   host_weights(h_table->scales, h_table->weights);
   h_table->s[0].bands = 16;
-  h_table->s[0].bc7_blocks = ep->format == GSC_FMT_BC7 ? 16 : 0;
+  h_table->s[0].bc7_blocks = j;
   h_table->s[0].first_group = 0;
   h_table->s[0].n_groups = ng;
   h_table->s[0].byte_offset = 0;
@@ -316,7 +347,12 @@ gsc_status make_dev_table(const gsc_stream_table* t, DevTable* d) {
   if (!t || !d) return GSC_ERR_INVALID_ARG;
   if (t->n_streams < 1 || t->n_streams > GSC_MODES || !n_ok(t->n)) return GSC_ERR_INVALID_ARG;
   if (t->n_groups != ceil_div64(t->n, 16)) return GSC_ERR_INVALID_ARG;
+  if (t->layout != GSC_LAYOUT_D && t->layout != GSC_LAYOUT_A && t->layout != GSC_LAYOUT_B) return GSC_ERR_INVALID_ARG;
+  // layouts A and B: one stream of whole groups (all 16 coefficients) with a valid BC7 count
+  if (t->layout != GSC_LAYOUT_D && (t->n_streams != 1 || t->s[0].bands != 16 || !lay_ok(t->layout, t->s[0].bc7_blocks)))
+    return GSC_ERR_INVALID_ARG;
   memset(d, 0, sizeof(*d));
+  d->layout = t->layout;
   d->n_streams = t->n_streams;
   d->n = (int32_t)t->n;
   d->n_groups = (int32_t)t->n_groups;

@@ -3,6 +3,7 @@
 // Sec. II: c(f) = H w(f - p); Sec. III-B: BC1 / BC7 formats).
 #include "bc7_tables.h"
 #include "gsc_internal.cuh"
+#include "layout.cuh"
 
 __constant__ uint32_t d_part2[64];
 __constant__ uint32_t d_part3[64];
@@ -182,15 +183,26 @@ __device__ __forceinline__ int stream_of(const DevTable& T, int64_t g) {
   return si;
 }
 
+// Block k of group g: a group's BC7 blocks come first, then its BC1 blocks, each in block
+// order (which blocks are BC7 follows the layout); blocks past the kept coefficients (layout D
+// streams only) are dropped.
 __device__ __forceinline__ BlockLoc locate(const DevTable& T, int si, int64_t g, int k) {
   const int b = T.bands[si], j = T.bc7[si];
   const int64_t gbytes = 16 * j + 8 * (b - j);
   const int64_t base = T.byte_offset[si] + (g - T.first_group[si]) * gbytes;
   BlockLoc L;
-  if (k < j) { L.off = base + 16 * k; L.kind = 7; }
-  else if (k < b) { L.off = base + 16 * j + 8 * (k - j); L.kind = 1; }
-  else { L.off = 0; L.kind = 0; }
+  if (k >= b) { L.off = 0; L.kind = 0; }
+  else if (lay_bc7(T.layout, j, k)) { L.off = base + 16 * lay_rank(T.layout, j, k); L.kind = 7; }
+  else { L.off = base + 16 * j + 8 * lay_rank(T.layout, j, k); L.kind = 1; }
   return L;
+}
+
+// Index in a decoded tile (block k's texel t at 17 k + t) of coefficient c of slot u.
+template <int LAYOUT>
+__device__ __forceinline__ int tile_at(int u, int c) {
+  int k, t;
+  lay_inv(LAYOUT, u, c, k, t);
+  return 17 * k + t;
 }
 
 __device__ __forceinline__ uint32_t decode_at(const uint8_t* __restrict__ blocks, const BlockLoc& L, int t) {
@@ -448,7 +460,7 @@ __device__ __forceinline__ float u23(uint32_t v, int c) {
   return __uint_as_float(__byte_perm(v, 0x4B000000u, 0x7650u | (uint32_t)c));
 }
 
-template <int KIND>
+template <int KIND, int LAYOUT>
 __global__ void __launch_bounds__(256) k_decode2(DevTable T, const uint8_t* __restrict__ blocks,
                                                  const int32_t* __restrict__ perm, uint8_t* __restrict__ texels) {
   __shared__ DecTables S;
@@ -474,7 +486,7 @@ __global__ void __launch_bounds__(256) k_decode2(DevTable T, const uint8_t* __re
       for (int i = 0; i < 12; i++) wv[i] = 0;
 #pragma unroll
       for (int k = 0; k < 16; k++) {
-        const uint32_t px = my[17 * k + kt];
+        const uint32_t px = my[tile_at<LAYOUT>(kt, k)];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
           const int byte = 3 * k + c;
@@ -600,7 +612,7 @@ __device__ __forceinline__ void load_views(float (*s_view)[64], float* s_deq, co
 #ifndef EVAL_MIN_BLOCKS
 #define EVAL_MIN_BLOCKS 1
 #endif
-template <int KIND, bool CAMS, int VF>
+template <int KIND, bool CAMS, int VF, int LAYOUT>
 __global__ void __launch_bounds__(EVAL_THREADS, EVAL_MIN_BLOCKS) k_eval2(DevTable T, const uint8_t* __restrict__ blocks,
                                                const int32_t* __restrict__ perm, const float* __restrict__ dirs,
                                                const float* __restrict__ pos, const float* __restrict__ cams, int V,
@@ -660,7 +672,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, EVAL_MIN_BLOCKS) k_eval2(DevTabl
       const float2 m = make_float2(-8388736.0f, -8388736.0f);
 #pragma unroll
       for (int j = 0; j < 8; j++) {
-        const uint32_t p0 = my[17 * (2 * j) + kt], p1 = my[17 * (2 * j + 1) + kt];
+        const uint32_t p0 = my[tile_at<LAYOUT>(kt, 2 * j)], p1 = my[tile_at<LAYOUT>(kt, 2 * j + 1)];
         const float2 f = *reinterpret_cast<const float2*>(s_deq + 2 * j);
         const float2 r = __fmul2_rn(__fadd2_rn(make_float2(u23(p0, 0), u23(p1, 0)), m), f);
         const float2 gg = __fmul2_rn(__fadd2_rn(make_float2(u23(p0, 1), u23(p1, 1)), m), f);
@@ -696,11 +708,19 @@ cudaError_t launch_decode(const DevTable& T, const uint8_t* blocks, const int32_
                           cudaStream_t st) {
   if (T.n_groups == 0) return cudaSuccess;
   const int grid = eval_grid(T.n_groups, 152);
-  switch (kind_of(T)) {
-    case 7: gsc_count_launch(); k_decode2<7><<<grid, 256, 0, st>>>(T, blocks, perm, texels); break;
-    case 1: gsc_count_launch(); k_decode2<1><<<grid, 256, 0, st>>>(T, blocks, perm, texels); break;
-    default: gsc_count_launch(); k_decode2<0><<<grid, 256, 0, st>>>(T, blocks, perm, texels); break;
-  }
+#define DEC_LAUNCH(L)                                                                              \
+  do {                                                                                             \
+    gsc_count_launch();                                                                            \
+    switch (kind_of(T)) {                                                                          \
+      case 7: k_decode2<7, L><<<grid, 256, 0, st>>>(T, blocks, perm, texels); break;               \
+      case 1: k_decode2<1, L><<<grid, 256, 0, st>>>(T, blocks, perm, texels); break;               \
+      default: k_decode2<0, L><<<grid, 256, 0, st>>>(T, blocks, perm, texels); break;              \
+    }                                                                                              \
+  } while (0)
+  if (T.layout == GSC_LAYOUT_A) DEC_LAUNCH(GSC_LAYOUT_A);
+  else if (T.layout == GSC_LAYOUT_B) DEC_LAUNCH(GSC_LAYOUT_B);
+  else DEC_LAUNCH(GSC_LAYOUT_D);
+#undef DEC_LAUNCH
   return cudaGetLastError();
 }
 
@@ -712,16 +732,25 @@ cudaError_t launch_decode_eval(const DevTable& T, const uint8_t* blocks, const i
   const int kind = kind_of(T);
   // runtime view count only: a compile-time 8-view form raised this kernel to 140 registers (one
   // resident CTA fewer) and measured no faster (the texture kernel does use one)
-#define EVAL_LAUNCH(K, C)                                                                                        \
+#define EVAL_LAUNCH(K, C, L)                                                                                     \
   do {                                                                                                           \
     gsc_count_launch();                                                                                          \
-    k_eval2<K, C, 0><<<grid, EVAL_THREADS, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order, rgb);        \
+    k_eval2<K, C, 0, L><<<grid, EVAL_THREADS, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order, rgb);     \
   } while (0)
-  if (cams) {
-    if (kind == 7) EVAL_LAUNCH(7, true); else if (kind == 1) EVAL_LAUNCH(1, true); else EVAL_LAUNCH(0, true);
-  } else {
-    if (kind == 7) EVAL_LAUNCH(7, false); else if (kind == 1) EVAL_LAUNCH(1, false); else EVAL_LAUNCH(0, false);
-  }
+#define EVAL_KINDS(C, L)                                                                                         \
+  do {                                                                                                           \
+    if (kind == 7) EVAL_LAUNCH(7, C, L); else if (kind == 1) EVAL_LAUNCH(1, C, L); else EVAL_LAUNCH(0, C, L);    \
+  } while (0)
+#define EVAL_LAYOUTS(C)                                                                                          \
+  do {                                                                                                           \
+    if (T.layout == GSC_LAYOUT_A) EVAL_KINDS(C, GSC_LAYOUT_A);                                                   \
+    else if (T.layout == GSC_LAYOUT_B) EVAL_KINDS(C, GSC_LAYOUT_B);                                              \
+    else EVAL_KINDS(C, GSC_LAYOUT_D);                                                                            \
+  } while (0)
+  if (cams) EVAL_LAYOUTS(true);
+  else EVAL_LAYOUTS(false);
+#undef EVAL_LAYOUTS
+#undef EVAL_KINDS
 #undef EVAL_LAUNCH
   return cudaGetLastError();
 }
@@ -851,13 +880,13 @@ __global__ void k_gather_streams(DevTable T, TexBases B, const uint8_t* __restri
     BlockLoc L = locate(T, si, g, k);
     const int j = T.bc7[si], b = T.bands[si];
     const int64_t gi = g - T.first_group[si];
+    const int r = lay_rank(T.layout, j, k);
     if (L.kind == 7) {
       const uint2* src = reinterpret_cast<const uint2*>(blocks + L.off);
-      uint2* dst = reinterpret_cast<uint2*>(lin7 + (B.b7[si] + gi * j + k) * 16);
+      uint2* dst = reinterpret_cast<uint2*>(lin7 + (B.b7[si] + gi * j + r) * 16);
       dst[0] = src[0]; dst[1] = src[1];
     } else if (L.kind == 1) {
-      *reinterpret_cast<uint2*>(lin1 + (B.b1[si] + gi * (b - j) + (k - j)) * 8) =
-          *reinterpret_cast<const uint2*>(blocks + L.off);
+      *reinterpret_cast<uint2*>(lin1 + (B.b1[si] + gi * (b - j) + r) * 8) = *reinterpret_cast<const uint2*>(blocks + L.off);
     }
   }
 }
@@ -871,14 +900,16 @@ __global__ void k_tex_streams(DevTable T, TexBases B, cudaTextureObject_t tex7, 
     const int32_t o = checked_slot(perm[s], T.n, s);
     if (o < 0) continue;
     const int64_t g = s >> 4;
-    const int t = (int)(s & 15);
+    int blk, t;
+    lay_inv(T.layout, (int)(s & 15), k, blk, t);
     const int si = stream_of(T, g);
     const int j = T.bc7[si], b = T.bands[si];
     const int64_t gi = g - T.first_group[si];
+    const int r = lay_rank(T.layout, j, blk);
     uint32_t px;
-    if (k < j) px = tex_fetch(tex7, B.b7[si] + gi * j + k, t);
-    else if (k < b) px = tex_fetch(tex1, B.b1[si] + gi * (b - j) + (k - j), t);
-    else px = 0x808080u;
+    if (blk >= b) px = 0x808080u;
+    else if (lay_bc7(T.layout, j, blk)) px = tex_fetch(tex7, B.b7[si] + gi * j + r, t);
+    else px = tex_fetch(tex1, B.b1[si] + gi * (b - j) + r, t);
     uint8_t* d = texels + (int64_t)o * 48 + 3 * k;
     d[0] = px & 255; d[1] = (px >> 8) & 255; d[2] = (px >> 16) & 255;
   }
@@ -1002,7 +1033,7 @@ __global__ void k_pos_slot(const float* __restrict__ pos, const int32_t* __restr
 // exact (q - 128) from a UNORM8 sample f = q / 255: f * 255 + 1.5 * 2^23 lands on 1.5 * 2^23 + q
 __device__ __forceinline__ float unorm_m128(float f) { return fmaf(f, 255.0f, 12582912.0f) - 12583040.0f; }
 
-template <int KIND, bool CAMS, int VF>
+template <int KIND, bool CAMS, int VF, int LAYOUT>
 __global__ void __launch_bounds__(256) k_eval_tex(DevTable T, TexBases B, cudaTextureObject_t tex7,
                                                   cudaTextureObject_t tex1, const int32_t* __restrict__ perm,
                                                   const float* __restrict__ dirs, const float* __restrict__ pos,
@@ -1036,21 +1067,24 @@ __global__ void __launch_bounds__(256) k_eval_tex(DevTable T, TexBases B, cudaTe
       continue;
     }
     const int64_t g = s >> 4;
-    const int t = (int)(s & 15);
+    const int u = (int)(s & 15);
     int si = 0, j = 16, b = 16;
     int64_t gi = g;
     if (KIND == 0) { si = stream_of(T, g); j = T.bc7[si]; b = T.bands[si]; gi = g - T.first_group[si]; }
     float xr[16], xg[16], xb[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) {
+      // coefficient k of slot u sits in block blk, texel t of the group
+      int blk, t;
+      lay_inv(LAYOUT, u, k, blk, t);
       float4 f;
       if (KIND == 7) f = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (KIND == 7 || (KIND == 0 && k < j)) {
-        const int64_t bi = KIND == 7 ? g * 16 + k : B.b7[si] + gi * j + k;
+      if (KIND == 7 || (KIND == 0 && blk < b && lay_bc7(LAYOUT, j, blk))) {
+        const int64_t bi = KIND == 7 ? g * 16 + blk : B.b7[si] + gi * j + lay_rank(LAYOUT, j, blk);
         const int x = (int)(bi % TEXW) * 4 + (t & 3), y = (int)(bi / TEXW) * 4 + (t >> 2);
         f = tex2D<float4>(tex7, (float)x + 0.5f, (float)y + 0.5f);
-      } else if (KIND == 1 || (KIND == 0 && k < b)) {
-        const int64_t bi = KIND == 1 ? g * 16 + k : B.b1[si] + gi * (b - j) + (k - j);
+      } else if (KIND == 1 || (KIND == 0 && blk < b)) {
+        const int64_t bi = KIND == 1 ? g * 16 + blk : B.b1[si] + gi * (b - j) + lay_rank(LAYOUT, j, blk);
         const int x = (int)(bi % TEXW) * 4 + (t & 3), y = (int)(bi / TEXW) * 4 + (t >> 2);
         f = tex2D<float4>(tex1, (float)x + 0.5f, (float)y + 0.5f);
       } else {
@@ -1155,21 +1189,24 @@ extern "C" gsc_status gsc_decode_eval_sh_tex(gsc_ctx* c, const gsc_tex_scene* sc
   const int kind = kind_of(T);
   // 8 views into Gaussian-major rows (the camera-pose workload) run a compile-time view count
   const bool v8 = V == 8 && out_order == GSC_OUT_GAUSS_MAJOR;
-#define TEX_LAUNCH(K, C)                                                                                          \
+  // (layouts A and B run the runtime view count)
+#define TEX_LAUNCH(K, C, VF, L)                                                                                   \
+  k_eval_tex<K, C, VF, L><<<(int)grid, 256, 0, st>>>(T, sc->B, sc->img[1].tex, sc->img[0].tex, d_perm, d_dirs,   \
+                                                     d_pos, d_cams, V, out_order, d_rgb, sc->pos_slot)
+#define TEX_LAYOUTS(K, C)                                                                                         \
   do {                                                                                                            \
     gsc_count_launch();                                                                                           \
-    if (v8)                                                                                                       \
-      k_eval_tex<K, C, 8><<<(int)grid, 256, 0, st>>>(T, sc->B, sc->img[1].tex, sc->img[0].tex, d_perm, d_dirs,    \
-                                                     d_pos, d_cams, V, out_order, d_rgb, sc->pos_slot);           \
-    else                                                                                                          \
-      k_eval_tex<K, C, 0><<<(int)grid, 256, 0, st>>>(T, sc->B, sc->img[1].tex, sc->img[0].tex, d_perm, d_dirs,    \
-                                                     d_pos, d_cams, V, out_order, d_rgb, sc->pos_slot);           \
+    if (T.layout == GSC_LAYOUT_A) TEX_LAUNCH(K, C, 0, GSC_LAYOUT_A);                                              \
+    else if (T.layout == GSC_LAYOUT_B) TEX_LAUNCH(K, C, 0, GSC_LAYOUT_B);                                         \
+    else if (v8) TEX_LAUNCH(K, C, 8, GSC_LAYOUT_D);                                                               \
+    else TEX_LAUNCH(K, C, 0, GSC_LAYOUT_D);                                                                       \
   } while (0)
   if (d_cams) {
-    if (kind == 7) TEX_LAUNCH(7, true); else if (kind == 1) TEX_LAUNCH(1, true); else TEX_LAUNCH(0, true);
+    if (kind == 7) TEX_LAYOUTS(7, true); else if (kind == 1) TEX_LAYOUTS(1, true); else TEX_LAYOUTS(0, true);
   } else {
-    if (kind == 7) TEX_LAUNCH(7, false); else if (kind == 1) TEX_LAUNCH(1, false); else TEX_LAUNCH(0, false);
+    if (kind == 7) TEX_LAYOUTS(7, false); else if (kind == 1) TEX_LAYOUTS(1, false); else TEX_LAYOUTS(0, false);
   }
+#undef TEX_LAYOUTS
 #undef TEX_LAUNCH
   GSC_CUDA(cudaGetLastError());
   return GSC_OK;

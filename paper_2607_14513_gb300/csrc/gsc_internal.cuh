@@ -156,6 +156,11 @@ gsc_status rate_run(gsc_ctx* ctx, const float* sh, int64_t n, const int32_t* per
                     uint32_t target_x4, uint8_t* blocks, int32_t* perm_out, gsc_stream_table* table, void* ws,
                     size_t ws_bytes, uint8_t* bc1_all, uint8_t* bc7_all, cudaStream_t st);
 
+// layout.cu: fixed codings of any layout with j BC7 blocks per group (texels staged in ws)
+size_t layout_ws_bytes(int64_t n_groups, int j);
+gsc_status layout_encode_run(gsc_ctx* ctx, const float* sh, int64_t n, const int32_t* perm, const float* scales,
+                             int layout, int j, uint8_t* blocks, void* ws, size_t ws_bytes, cudaStream_t st);
+
 // decode.cu
 cudaError_t decode_init_tables();
 // Flattened stream table for kernels (passed by value).
@@ -166,6 +171,7 @@ struct DevTable {
   int32_t bands[GSC_MODES], bc7[GSC_MODES];
   int64_t first_group[GSC_MODES], stream_groups[GSC_MODES], byte_offset[GSC_MODES];
   float scales[GSC_SH];
+  int32_t layout;  // gsc_layout
 };
 // Band weights of the rate-distortion objective from the 16 scales (fp64, Sec. IV-B).
 void host_weights(const float* scales, uint32_t* w);

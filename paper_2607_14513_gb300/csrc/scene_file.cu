@@ -12,7 +12,7 @@
 namespace {
 
 const char kMagic[8] = {'G', 'S', 'C', 'S', 'C', 'E', 'N', 'E'};
-const uint32_t kVersion = 1;
+const uint32_t kVersion = 2;  // 2: the stream table carries the block layout
 
 struct FileHeader {
   char magic[8];

@@ -19,7 +19,8 @@ HEADER = os.path.join(PKG, "..", "include", "gsc.h")
 GSC_OK = 0
 STATUS = {0: "GSC_OK", 1: "GSC_ERR_INVALID_ARG", 2: "GSC_ERR_CUDA", 3: "GSC_ERR_OOM", 4: "GSC_ERR_BUDGET",
           5: "GSC_ERR_TIMEOUT", 6: "GSC_ERR_UNSUPPORTED", 7: "GSC_ERR_DEVICE", 8: "GSC_ERR_CANCELLED"}
-FMT_RATE, FMT_BC1, FMT_BC7 = 0, 1, 7
+FMT_RATE, FMT_BC1, FMT_MIXED, FMT_BC7 = 0, 1, 2, 7
+LAYOUT_D, LAYOUT_A, LAYOUT_B = 0, 1, 2
 OUT_VIEW_MAJOR, OUT_SLOT_ORDER, OUT_GAUSS_MAJOR = 0, 1, 2
 
 
@@ -35,7 +36,7 @@ class PlanParams(C.Structure):
 
 class EncodeParams(C.Structure):
     _fields_ = [("format", C.c_int32), ("target_bpt_x4", C.c_uint32), ("d_bc1_blocks", C.c_void_p),
-                ("d_bc7_blocks", C.c_void_p)]
+                ("d_bc7_blocks", C.c_void_p), ("layout", C.c_int32), ("bc7_blocks", C.c_int32)]
 
 
 class Stream(C.Structure):
@@ -47,7 +48,7 @@ class StreamTable(C.Structure):
     _fields_ = [("n_streams", C.c_int32), ("format", C.c_int32), ("n", C.c_int64), ("n_groups", C.c_int64),
                 ("total_bytes", C.c_int64), ("budget_bits", C.c_uint64), ("used_bits", C.c_uint64),
                 ("lambda_", C.c_uint64), ("scales", C.c_float * 16), ("weights", C.c_uint32 * 16),
-                ("s", Stream * 14)]
+                ("s", Stream * 14), ("layout", C.c_int32)]
 
     def streams(self):
         return [dict(bands=self.s[i].bands, bc7_blocks=self.s[i].bc7_blocks, first_group=self.s[i].first_group,
@@ -231,9 +232,9 @@ class Context:
     def sync(self, stream=None):
         _check(self.lib.gsc_ctx_sync(self.h, _stream(stream)), "gsc_ctx_sync")
 
-    def workspace(self, n, fmt=FMT_BC1, target_x4=0):
+    def workspace(self, n, fmt=FMT_BC1, target_x4=0, layout=LAYOUT_D, bc7_blocks=0):
         import torch
-        ep = EncodeParams(fmt, target_x4, None, None)
+        ep = EncodeParams(fmt, target_x4, None, None, layout, bc7_blocks)
         nb = self.lib.gsc_workspace_bytes(n, C.byref(ep))
         return torch.empty(max(int(nb), 256), dtype=torch.uint8, device="cuda:%d" % self.device)
 
@@ -261,19 +262,20 @@ def gsc_quantise(ctx, sh, scales, stream=None):
 
 
 def gsc_encode(ctx, sh, perm, scales, fmt, target_x4=0, ws=None, out=None, perm_out=None, stream=None,
-               bc1_all=None, bc7_all=None):
+               bc1_all=None, bc7_all=None, layout=LAYOUT_D, bc7_blocks=0):
     """-> (blocks uint8 [total_bytes], perm_out int32, StreamTable).
 
     In rate mode, bc1_all / bc7_all (optional uint8 device tensors of n_groups*128 and
-    n_groups*256 bytes) receive the all-BC1 and all-BC7 codings of the planned order."""
+    n_groups*256 bytes) receive the all-BC1 and all-BC7 codings of the planned order.
+    layout: LAYOUT_D / _A / _B; FMT_MIXED codes bc7_blocks blocks of every group BC7."""
     import torch
     n = sh.shape[0]
     ng = (n + 15) // 16
     dev = sh.device
     blocks = out if out is not None else torch.empty(max(ng * 256, 16), dtype=torch.uint8, device=dev)
     po = perm_out if perm_out is not None else torch.empty(max(ng * 16, 1), dtype=torch.int32, device=dev)
-    ws = ws if ws is not None else ctx.workspace(n, fmt, target_x4)
-    ep = EncodeParams(fmt, target_x4, _ptr(bc1_all), _ptr(bc7_all))
+    ws = ws if ws is not None else ctx.workspace(n, fmt, target_x4, layout, bc7_blocks)
+    ep = EncodeParams(fmt, target_x4, _ptr(bc1_all), _ptr(bc7_all), layout, bc7_blocks)
     tab = StreamTable()
     _check(ctx.lib.gsc_encode(ctx.h, _ptr(sh), n, _ptr(perm), _ptr(scales), C.byref(ep), _ptr(blocks), _ptr(po),
                               C.byref(tab), _ptr(ws), ws.numel(), _stream(stream)), "gsc_encode")
@@ -281,9 +283,10 @@ def gsc_encode(ctx, sh, perm, scales, fmt, target_x4=0, ws=None, out=None, perm_
 
 
 def forced_table(table, fmt):
-    """Stream table of the all-BC1 / all-BC7 layout that shares `table`'s scene and scales."""
+    """Stream table of the all-BC1 / all-BC7 coding that shares `table`'s scene, scales and layout."""
     t = StreamTable()
     t.n_streams, t.format, t.n, t.n_groups = 1, fmt, table.n, table.n_groups
+    t.layout = table.layout
     bpb = 16 if fmt == FMT_BC7 else 8
     t.total_bytes = table.n_groups * 16 * bpb
     t.used_bits = t.total_bytes * 8

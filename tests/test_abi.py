@@ -42,3 +42,38 @@ def test_host_side_sizes_and_strings():
     assert lib.gsc_workspace_bytes(3_000_000, ctypes.byref(ep)) > 3_000_000 * 16
     assert lib.gsc_workspace_bytes(-1, ctypes.byref(ep)) == 0
     assert lib.gsc_status_string(4) == b"rate target below the cheapest coding of the scene"
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # the binding's ctypes structures against the C compiler's view of include/gsc.h
+    import shutil
+    import subprocess
+    from paper_2607_14513_gb300 import gsc
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gsc.h"\nint main(void) {\n'
+                   '  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(gsc_stream_table), offsetof(gsc_stream_table, layout),'
+                   ' sizeof(gsc_encode_params), offsetof(gsc_encode_params, layout),'
+                   ' offsetof(gsc_encode_params, bc7_blocks), sizeof(gsc_stream));\n  return 0;\n}\n')
+    exe = tmp_path / "abi"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.check_call([cc, "-I", inc, str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(gsc.StreamTable), gsc.StreamTable.layout.offset, ctypes.sizeof(gsc.EncodeParams),
+            gsc.EncodeParams.layout.offset, gsc.EncodeParams.bc7_blocks.offset, ctypes.sizeof(gsc.Stream)]
+    assert got == want
+
+
+def test_layout_workspace_sizes():
+    from paper_2607_14513_gb300 import gsc
+    lib = gsc.load()
+    n = 1_000_000
+    ng = (n + 15) // 16
+    # layout B with BC7 on the first block of every quad stages 48 B texels per block and the two
+    # coded arrays before the interleave
+    ep = gsc.EncodeParams(gsc.FMT_MIXED, 0, None, None, gsc.LAYOUT_B, 4)
+    assert lib.gsc_workspace_bytes(n, ctypes.byref(ep)) >= ng * 16 * 48 + ng * (4 * 16 + 12 * 8)
+    ep = gsc.EncodeParams(gsc.FMT_BC7, 0, None, None, gsc.LAYOUT_A, 0)
+    assert lib.gsc_workspace_bytes(n, ctypes.byref(ep)) >= ng * 16 * 48
