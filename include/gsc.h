@@ -7,7 +7,8 @@
  * p in R^3 and opacity-premultiplied SH colour coefficients H~ = mu H (Eq. premult),
  * 16 RGB coefficients each (k = l*l + l + m, degree 3). The codec quantises H~ to
  * 8-bit texels, reorders the Gaussians by colour inside spatial groups (Sec. III-C),
- * packs coefficient k of 16 Gaussians into one 4x4 block (Sec. IV-B, Fig. SetupD),
+ * packs coefficient k of 16 Gaussians into one 4x4 block (Sec. IV-B, Fig. SetupD; or one
+ * Gaussian per block, Fig. SetupA, or four Gaussians in four blocks, Fig. SetupB),
  * codes every block with BC1 (8 bytes) or BC7 (16 bytes) (Sec. III-B), optionally
  * spreading groups over several fixed-rate streams (Sec. IV-B), and decodes the
  * blocks back, evaluating the view-dependent colour c(f) = H w(f - p) (Sec. II).
@@ -233,7 +234,8 @@ gsc_status gsc_decode_eval_sh_tex(gsc_ctx* ctx, const gsc_tex_scene* scene, cons
  * the plan of gsc_plan_reorder (quantile 995), then the blocks, slot order and stream table of
  * gsc_encode with the scene's format. All BC1/BC7 block searches of all scenes run in one
  * persistent launch whose CTAs claim tiles of groups (Sec. IV-B layout D); rate scenes then
- * select their streams one by one. At most 1024 scenes (else GSC_ERR_INVALID_ARG). The caller
+ * select their streams one by one. At most 1024 scenes (else GSC_ERR_INVALID_ARG). Scenes are
+ * coded in layout D (the layouts of Figs. SetupA / SetupB go through gsc_encode). The caller
  * owns every buffer; the call synchronises `stream`. */
 typedef struct {
   const float* d_pos;       /* [n][3] (needed when sort = 1 and for evaluation) */
@@ -292,7 +294,8 @@ gsc_status gsc_graph_destroy(gsc_graph* graph);
  * scenes least recently used first when that makes it fit. Requests on one scene keep their
  * submission order around encodes. Queued evaluations of one scene with the same output
  * order and view kind merge into one launch of up to max_views views. Every result equals
- * the single calls' bit for bit: an encode is gsc_plan_reorder (quantile 995) + gsc_encode,
+ * the single calls' bit for bit: an encode is gsc_plan_reorder (quantile 995) + gsc_encode
+ * (layout D; a loaded checkpoint keeps the layout its table names),
  * an evaluation is gsc_decode_eval_sh of the scene's resident coding. */
 typedef struct {
   uint64_t hbm_budget_bytes;
