@@ -1187,3 +1187,143 @@ void or_eval_sh(const uint8_t* texels, int64_t n, const float* scales, const flo
       }
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Splatting renderer (Sec. II: Eq. sigmoid, Eq. covar, Eq. opac, Eq. blend /   */
+/* Eq. preblend with the premultiplied H~ of Eq. premult; Fig. GSRend).         */
+/* The paper gives the 3-D opacity g(x) of Eq. opac; the screen-space form here */
+/* is the EWA splat of the cited method: the Gaussian projected with the       */
+/* Jacobian of the pinhole projection at its centre, plus a 0.3 px^2 low-pass,  */
+/* and limited to the 16 x 16 pixel tiles that its 3-sigma square touches.      */
+/* Every decision (culling, tile rectangle, depth order) is taken in float      */
+/* with the fixed operation order below, so that every implementation takes it */
+/* the same way; the blending itself is accumulated in double.                 */
+/* ------------------------------------------------------------------------- */
+void or_camera_centre(const or_camera* cam, float* f) {
+  for (int k = 0; k < 3; k++) {
+    double v = ((double)cam->R[k] * cam->t[0] + (double)cam->R[3 + k] * cam->t[1]) + (double)cam->R[6 + k] * cam->t[2];
+    f[k] = (float)(-v);
+  }
+}
+
+int or_splat_setup(const float* p, const float* s, const float* q, const or_camera* cam, or_splat* o) {
+  const float* R = cam->R;
+  memset(o, 0, sizeof(*o));
+  /* camera coordinates */
+  float x = ((R[0] * p[0] + R[1] * p[1]) + R[2] * p[2]) + cam->t[0];
+  float y = ((R[3] * p[0] + R[4] * p[1]) + R[5] * p[2]) + cam->t[1];
+  float z = ((R[6] * p[0] + R[7] * p[1]) + R[8] * p[2]) + cam->t[2];
+  if (!(z > cam->near_z)) return 0;
+  /* Eq. covar: Sigma = R(q) D(s) D(s)^T R(q)^T, q = (w, x, y, z) normalised */
+  float nq = sqrtf(((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]) + q[3] * q[3]);
+  if (!(nq > 0.0f)) return 0;
+  float qw = q[0] / nq, qx = q[1] / nq, qy = q[2] / nq, qz = q[3] / nq;
+  float r[9];
+  r[0] = 1.0f - 2.0f * (qy * qy + qz * qz); r[1] = 2.0f * (qx * qy - qw * qz); r[2] = 2.0f * (qx * qz + qw * qy);
+  r[3] = 2.0f * (qx * qy + qw * qz); r[4] = 1.0f - 2.0f * (qx * qx + qz * qz); r[5] = 2.0f * (qy * qz - qw * qx);
+  r[6] = 2.0f * (qx * qz - qw * qy); r[7] = 2.0f * (qy * qz + qw * qx); r[8] = 1.0f - 2.0f * (qx * qx + qy * qy);
+  float m[9];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) m[3 * i + j] = r[3 * i + j] * s[j];
+  float S[9];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) S[3 * i + j] = (m[3 * i] * m[3 * j] + m[3 * i + 1] * m[3 * j + 1]) + m[3 * i + 2] * m[3 * j + 2];
+  /* Jacobian of (fx x / z + cx, fy y / z + cy) at the centre, times the view rotation */
+  float iz = 1.0f / z;
+  float J[6] = {cam->fx * iz, 0.0f, -(cam->fx * x) * (iz * iz), 0.0f, cam->fy * iz, -(cam->fy * y) * (iz * iz)};
+  float T[6];
+  for (int a = 0; a < 2; a++)
+    for (int j = 0; j < 3; j++) T[3 * a + j] = (J[3 * a] * R[j] + J[3 * a + 1] * R[3 + j]) + J[3 * a + 2] * R[6 + j];
+  float U[6];
+  for (int a = 0; a < 2; a++)
+    for (int j = 0; j < 3; j++) U[3 * a + j] = (T[3 * a] * S[j] + T[3 * a + 1] * S[3 + j]) + T[3 * a + 2] * S[6 + j];
+  float c00 = (U[0] * T[0] + U[1] * T[1]) + U[2] * T[2];
+  float c01 = (U[0] * T[3] + U[1] * T[4]) + U[2] * T[5];
+  float c11 = (U[3] * T[3] + U[4] * T[4]) + U[5] * T[5];
+  float a = c00 + 0.3f, b = c01, c = c11 + 0.3f;
+  float det = a * c - b * b;
+  if (!(det > 0.0f)) return 0;
+  float mid = 0.5f * (a + c);
+  float disc = mid * mid - det;
+  float lam = mid + sqrtf(disc > 0.1f ? disc : 0.1f);
+  float rad = ceilf(3.0f * sqrtf(lam));
+  float u = cam->fx * (x / z) + cam->cx, v = cam->fy * (y / z) + cam->cy;
+  int tx = (cam->width + 15) / 16, ty = (cam->height + 15) / 16;
+  float fx0 = floorf((u - rad) / 16.0f), fx1 = floorf((u + rad) / 16.0f) + 1.0f;
+  float fy0 = floorf((v - rad) / 16.0f), fy1 = floorf((v + rad) / 16.0f) + 1.0f;
+  int x0 = fx0 < 0.0f ? 0 : (fx0 > (float)tx ? tx : (int)fx0), x1 = fx1 < 0.0f ? 0 : (fx1 > (float)tx ? tx : (int)fx1);
+  int y0 = fy0 < 0.0f ? 0 : (fy0 > (float)ty ? ty : (int)fy0), y1 = fy1 < 0.0f ? 0 : (fy1 > (float)ty ? ty : (int)fy1);
+  if (x1 <= x0 || y1 <= y0) return 0;
+  o->u = u; o->v = v; o->depth = z;
+  o->a = a; o->b = b; o->c = c;
+  o->x0 = x0; o->y0 = y0; o->x1 = x1; o->y1 = y1;
+  o->visible = 1;
+  return 1;
+}
+
+typedef struct { uint32_t depth_bits; int64_t i; } depth_key;
+static int cmp_depth(const void* pa, const void* pb) {
+  const depth_key* a = (const depth_key*)pa;
+  const depth_key* b = (const depth_key*)pb;
+  if (a->depth_bits != b->depth_bits) return a->depth_bits < b->depth_bits ? -1 : 1;
+  return a->i < b->i ? -1 : (a->i > b->i ? 1 : 0);
+}
+
+/* Eq. preblend, pixel (x, y) with centre (x + 0.5, y + 0.5): a = sum_i g_i c~_i prod_{j<i} (1 - mu_j g_j)
+ * over the Gaussians whose tile rectangle holds the pixel's tile, nearest first (camera depth, then
+ * index); c~ = H~ w(f - p) is the premultiplied colour (Eq. premult), mu = sigmoid(t) (Eq. sigmoid).
+ * tiles: the tile ids (ty * tiles_x + tx) to render, or NULL for all. trans gets the final
+ * prod (1 - mu g); abs_sum the sum of |g c~ prod| per channel (for error bounds). */
+int or_render(int64_t n, const float* pos, const float* scale, const float* rot, const float* logit,
+              const double* colour, const or_camera* cam, const int32_t* tiles, int64_t n_tiles, double* image,
+              double* trans, double* abs_sum) {
+  const int W = cam->width, H = cam->height, tx = (W + 15) / 16, ty = (H + 15) / 16;
+  or_splat* sp = (or_splat*)malloc(sizeof(or_splat) * (size_t)(n > 0 ? n : 1));
+  depth_key* list = (depth_key*)malloc(sizeof(depth_key) * (size_t)(n > 0 ? n : 1));
+  if (!sp || !list) { free(sp); free(list); return -1; }
+  for (int64_t i = 0; i < n; i++) or_splat_setup(pos + 3 * i, scale + 3 * i, rot + 4 * i, cam, &sp[i]);
+  int64_t nt = tiles ? n_tiles : (int64_t)tx * ty;
+  for (int64_t ti = 0; ti < nt; ti++) {
+    int tile = tiles ? tiles[ti] : (int)ti;
+    int bx = tile % tx, by = tile / tx;
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; i++) {
+      const or_splat* g = &sp[i];
+      if (g->visible && bx >= g->x0 && bx < g->x1 && by >= g->y0 && by < g->y1) {
+        uint32_t bits;
+        memcpy(&bits, &g->depth, 4);
+        list[m].depth_bits = bits; list[m].i = i; m++;
+      }
+    }
+    qsort(list, (size_t)m, sizeof(depth_key), cmp_depth);
+    for (int py = by * 16; py < by * 16 + 16 && py < H; py++)
+      for (int px = bx * 16; px < bx * 16 + 16 && px < W; px++) {
+        double T = 1.0, acc[3] = {0.0, 0.0, 0.0}, ab[3] = {0.0, 0.0, 0.0};
+        for (int64_t k = 0; k < m; k++) {
+          const int64_t i = list[k].i;
+          const or_splat* g = &sp[i];
+          double a = g->a, b = g->b, c = g->c;
+          double det = a * c - b * b;
+          double ca = c / det, cb = -b / det, cc = a / det;
+          double dx = (px + 0.5) - (double)g->u, dy = (py + 0.5) - (double)g->v;
+          double gv = exp(-0.5 * (ca * dx * dx + cc * dy * dy) - cb * dx * dy);
+          double mu = 1.0 / (1.0 + exp(-(double)logit[i]));
+          for (int ch = 0; ch < 3; ch++) {
+            double term = gv * colour[3 * i + ch] * T;
+            acc[ch] += term;
+            ab[ch] += fabs(term);
+          }
+          T *= 1.0 - mu * gv;
+        }
+        int64_t pix = (int64_t)py * W + px;
+        for (int ch = 0; ch < 3; ch++) {
+          image[3 * pix + ch] = acc[ch];
+          if (abs_sum) abs_sum[3 * pix + ch] = ab[ch];
+        }
+        if (trans) trans[pix] = T;
+      }
+  }
+  free(sp);
+  free(list);
+  return 0;
+}

@@ -79,6 +79,26 @@ int or_encode(const uint8_t* q, int64_t n, const int32_t* perm, const float* sca
               uint32_t target_x4, uint8_t* blocks, int32_t* perm_out, or_table* t, uint64_t* dtab);
 int or_decode(const or_table* t, const uint8_t* blocks, const int32_t* perm, uint8_t* texels);
 
+/* Splatting renderer (Sec. II, Eqs. sigmoid, covar, opac, preblend; Fig. GSRend). */
+typedef struct {
+  float R[9];        /* world -> camera rotation, row-major: x_cam = R x + t */
+  float t[3];
+  float fx, fy, cx, cy; /* pinhole intrinsics in pixels; pixel (x, y) covers [x, x+1) x [y, y+1) */
+  int32_t width, height;
+  float near_z;      /* Gaussians at camera depth <= near_z are culled */
+} or_camera;
+typedef struct {
+  float u, v, depth;      /* projected centre (pixels), camera depth */
+  float a, b, c;          /* 2-D covariance (with the 0.3 px^2 low-pass) */
+  int32_t x0, y0, x1, y1; /* tile rectangle [x0, x1) x [y0, y1) of 16 x 16 pixel tiles */
+  int32_t visible;
+} or_splat;
+void or_camera_centre(const or_camera* cam, float* f /*[3]*/);
+int or_splat_setup(const float* p, const float* s, const float* q, const or_camera* cam, or_splat* out);
+int or_render(int64_t n, const float* pos, const float* scale, const float* rot, const float* logit,
+              const double* colour /*[n][3]*/, const or_camera* cam, const int32_t* tiles, int64_t n_tiles,
+              double* image /*[H][W][3]*/, double* trans /*[H][W] or NULL*/, double* abs_sum /*or NULL*/);
+
 void or_sh_basis(double x, double y, double z, double* Y /*[16]*/);
 void or_eval_sh(const uint8_t* texels, int64_t n, const float* scales, const float* pos,
                 const float* dirs, const float* cams, int V, double* out /*[V][n][3]*/,

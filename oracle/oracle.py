@@ -93,6 +93,9 @@ def lib():
                 "or_code_groups": (None, [P, i64, P, P, P, P, P]),
                 "or_rate_assemble": (i32, [i64, P, P, u32, P, P, P, P, P, P]),
                 "or_decode": (i32, [P, P, P, P]),
+                "or_camera_centre": (None, [P, P]),
+                "or_splat_setup": (i32, [P, P, P, P, P]),
+                "or_render": (i32, [i64, P, P, P, P, P, P, P, i64, P, P, P]),
                 "or_sh_basis": (None, [C.c_double, C.c_double, C.c_double, P]),
                 "or_eval_sh": (None, [P, i64, P, P, P, P, i32, P, P]),
             }
@@ -379,6 +382,58 @@ def decode(table: Table, blocks, perm):
     buf = blocks if blocks.size else np.zeros(1, np.uint8)
     lib().or_decode(C.byref(table), _p(buf), _p(perm), _p(tex))
     return tex
+
+
+# --- splatting renderer (Sec. II, Eqs. sigmoid / covar / opac / preblend) -----------------
+class Camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("near_z", C.c_float)]
+
+
+class Splat(C.Structure):
+    _fields_ = [("u", C.c_float), ("v", C.c_float), ("depth", C.c_float), ("a", C.c_float), ("b", C.c_float),
+                ("c", C.c_float), ("x0", C.c_int32), ("y0", C.c_int32), ("x1", C.c_int32), ("y1", C.c_int32),
+                ("visible", C.c_int32)]
+
+
+def camera(d):
+    cam = Camera()
+    cam.R[:] = [float(x) for x in d["R"]]
+    cam.t[:] = [float(x) for x in d["t"]]
+    cam.fx, cam.fy, cam.cx, cam.cy = float(d["fx"]), float(d["fy"]), float(d["cx"]), float(d["cy"])
+    cam.width, cam.height, cam.near_z = int(d["width"]), int(d["height"]), float(d["near_z"])
+    return cam
+
+
+def camera_centre(d):
+    f = np.zeros(3, np.float32)
+    lib().or_camera_centre(C.byref(camera(d)), _p(f))
+    return f
+
+
+def splat_setup(p, s, q, d):
+    sp = Splat()
+    lib().or_splat_setup(_p(_c(p, np.float32)), _p(_c(s, np.float32)), _p(_c(q, np.float32)), C.byref(camera(d)),
+                         C.byref(sp))
+    return sp
+
+
+def render(pos, scale, rot, logit, colour, cam, tiles=None, want_abs=False):
+    """Eq. preblend image [H, W, 3] (float64), final transmittance [H, W] and optionally the sum of
+    absolute terms; tiles: tile ids to render (others stay 0)."""
+    pos, scale, rot = _c(pos, np.float32), _c(scale, np.float32), _c(rot, np.float32)
+    logit, colour = _c(logit, np.float32), _c(colour, np.float64)
+    c = camera(cam)
+    img = np.zeros((c.height, c.width, 3), np.float64)
+    tr = np.zeros((c.height, c.width), np.float64)
+    ab = np.zeros((c.height, c.width, 3), np.float64) if want_abs else None
+    tl = _c(tiles, np.int32) if tiles is not None else None
+    rc = lib().or_render(pos.shape[0], _p(pos), _p(scale), _p(rot), _p(logit), _p(colour), C.byref(c), _p(tl),
+                         0 if tl is None else tl.shape[0], _p(img), _p(tr), _p(ab))
+    if rc != 0:
+        raise ValueError("or_render failed: %d" % rc)
+    return (img, tr, ab) if want_abs else (img, tr)
 
 
 # --- SH evaluation (Sec. II) --------------------------------------------------------------

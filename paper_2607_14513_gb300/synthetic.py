@@ -16,7 +16,11 @@ What is generated stands in for the trained scenes of the paper's experiments
   DC (k = 0) ~ N(0, 0.8), band l >= 1 ~ N(0, 0.15 / (l + 1)) (standard deviations);
   optionally a heavy-tailed fraction whose bands 2-3 are Laplace(0, 0.3);
 * view directions uniform on the unit sphere, and camera centres uniform on a
-  sphere of radius 2 around (0.5, 0.5, 0.5).
+  sphere of radius 2 around (0.5, 0.5, 0.5);
+* for rendering (Sec. II), per-Gaussian geometry: scales ``s`` (log-normal around a
+  given size, per axis), rotation quaternions ``q`` (normal draws, not normalised)
+  and opacity logits ``t`` ~ N(0, 1.5); and pinhole cameras on the same sphere
+  looking at (0.5, 0.5, 0.5).
 """
 from __future__ import annotations
 
@@ -119,3 +123,51 @@ def serve_trace(n_scenes: int, seed: int, lo: int, hi: int, rate_hz: float, enco
         kind = "encode" if rng.random() < encode_frac else "eval"
         reqs.append((t, kind, int(rng.integers(n_scenes)), int(rng.integers(1, 33)), int(rng.integers(1 << 30))))
     return pool, reqs
+
+
+@dataclass
+class Geometry:
+    scale: np.ndarray  # [N, 3] float32, linear axis scales s (Eq. covar)
+    rot: np.ndarray    # [N, 4] float32, rotation quaternion (w, x, y, z), not normalised
+    logit: np.ndarray  # [N] float32, opacity logits t (Eq. sigmoid)
+
+
+def make_geometry(n: int, seed: int, scale: float = 0.004) -> Geometry:
+    """Per-Gaussian shape and opacity parameters for rendering."""
+    rng = np.random.default_rng(seed)
+    s = np.exp(rng.normal(np.log(scale), 0.35, size=(n, 3)))
+    q = rng.standard_normal(size=(n, 4))
+    t = rng.normal(0.0, 1.5, size=n)
+    return Geometry(scale=s.astype(np.float32), rot=q.astype(np.float32), logit=t.astype(np.float32))
+
+
+def look_at(eye, target, width: int, height: int, fov_x_deg: float = 50.0, near: float = 0.2) -> dict:
+    """A pinhole camera at ``eye`` looking at ``target``: world -> camera rotation R (rows: image
+    right, image down, viewing direction) and translation t = -R eye; focal length from the
+    horizontal field of view, principal point at the image centre."""
+    eye = np.asarray(eye, np.float64)
+    fwd = np.asarray(target, np.float64) - eye
+    fwd /= np.linalg.norm(fwd)
+    up = np.array([0.0, 0.0, 1.0]) if abs(fwd[2]) < 0.95 else np.array([0.0, 1.0, 0.0])
+    right = np.cross(fwd, up)
+    right /= np.linalg.norm(right)
+    down = np.cross(fwd, right)
+    R = np.stack([right, down, fwd])
+    t = -R @ eye
+    f = 0.5 * width / np.tan(np.radians(fov_x_deg) / 2)
+    return dict(R=R.astype(np.float32).reshape(9), t=t.astype(np.float32), fx=np.float32(f), fy=np.float32(f),
+                cx=np.float32(width / 2), cy=np.float32(height / 2), width=int(width), height=int(height),
+                near_z=np.float32(near))
+
+
+def make_views(count: int, seed: int, width: int, height: int, radius: float = 2.0, fov_x_deg: float = 50.0):
+    """``count`` cameras on a sphere of ``radius`` around (0.5, 0.5, 0.5), looking at it."""
+    rng = np.random.default_rng(seed)
+    d = rng.standard_normal(size=(count, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    c = np.array([0.5, 0.5, 0.5])
+    return [look_at(c + radius * d[i], c, width, height, fov_x_deg) for i in range(count)]
+
+
+RENDER = dict(n=3000000, seed=1003, clusters=64, heavy_frac=0.10, geom_seed=1103, scale=0.004,
+              width=1920, height=1080, views=4, view_seed=1203)    # the 3M scene rendered at 1080p
