@@ -229,6 +229,38 @@ gsc_status gsc_decode_eval_sh_tex(gsc_ctx* ctx, const gsc_tex_scene* scene, cons
                                   const float* d_dirs, const float* d_pos, const float* d_cams, int32_t V,
                                   int32_t out_order, float* d_rgb, void* stream);
 
+/* Splatting renderer (Sec. II: Eq. sigmoid mu = 1 / (1 + e^-t), Eq. covar Sigma = R(q) D(s) D(s)^T
+ * R(q)^T, Eq. opac, Eq. preblend a = sum_i g_i c~_i prod_{j<i} (1 - mu_j g_j) with the premultiplied
+ * c~ = H~ w(f - p) of Eq. premult; Fig. GSRend). Pinhole camera: x_cam = R x + t; pixel (x, y)
+ * covers [x, x+1) x [y, y+1) and is sampled at its centre; Gaussians at camera depth <= near_z are
+ * culled. g is the EWA screen-space splat: the Gaussian projected with the pinhole Jacobian at its
+ * centre plus a 0.3 px^2 low-pass, evaluated on the 16 x 16 pixel tiles that its 3-sigma square
+ * touches; Gaussians are blended nearest first (camera depth, then index), with no early stop. */
+typedef struct {
+  float R[9];           /* world -> camera rotation, row-major (rows: image right, image down, view) */
+  float t[3];           /* world -> camera translation */
+  float fx, fy, cx, cy; /* focal lengths and principal point, pixels */
+  int32_t width, height; /* 1..16384 */
+  float near_z;         /* > 0 */
+} gsc_camera;
+
+/* Workspace bytes of gsc_render for n Gaussians and up to max_pairs (Gaussian, tile) overlaps. */
+size_t gsc_render_workspace_bytes(int64_t n, const gsc_camera* cam, int64_t max_pairs);
+
+/* Renders a coded scene (any layout and coding) for one camera into d_image [height][width][3]
+ * float (background 0) and, if d_trans is not NULL, the final transmittance prod (1 - mu g)
+ * [height][width]. Per Gaussian, in original order: d_pos [n][3], d_scale [n][3] (axis scales s),
+ * d_rot [n][4] (quaternion w, x, y, z; normalised here; 16-byte aligned), d_logit [n] (opacity
+ * logit t). The colour of every Gaussian is decoded from the blocks and evaluated for the camera
+ * centre f = -R^T t in one fused pass. The call synchronises `stream` once, to size the sort: it
+ * writes the number of (Gaussian, tile) overlaps to *h_pairs (if not NULL) and returns
+ * GSC_ERR_OOM, with nothing rendered, when ws_bytes is below gsc_render_workspace_bytes(n, cam,
+ * that number). */
+gsc_status gsc_render(gsc_ctx* ctx, const gsc_stream_table* table, const uint8_t* d_blocks, const int32_t* d_perm,
+                      const float* d_pos, const float* d_scale, const float* d_rot, const float* d_logit,
+                      const gsc_camera* cam, float* d_image, float* d_trans, int64_t* h_pairs, void* d_ws,
+                      size_t ws_bytes, void* stream);
+
 /* Batched form: many scenes of uneven sizes (the paper codes one scene at a time; this packages
  * the same steps for throughput). Per scene the results equal the single-scene calls bit for bit:
  * the plan of gsc_plan_reorder (quantile 995), then the blocks, slot order and stream table of

@@ -15,7 +15,8 @@ void gsc_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 extern "C" uint64_t gsc_launch_count(void) { return g_launches.load(); }
 
 static const char* kTimerNames[T_COUNT] = {"plan", "bc1_encode", "bc7_encode", "rate_select", "decode",
-                                           "decode_eval", "decode_tex", "decode_eval_tex", "batch_encode"};
+                                           "decode_eval", "decode_tex", "decode_eval_tex", "batch_encode", "render",
+                                           "render_blend"};
 
 int gsc_timer_begin(gsc_ctx* c, int id, cudaStream_t st) {
   if (!c || !c->timing) return -1;

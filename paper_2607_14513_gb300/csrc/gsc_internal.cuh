@@ -10,7 +10,7 @@
 #define GSC_SH 16
 #define GSC_MODES 14
 
-enum { T_PLAN = 0, T_BC1, T_BC7, T_RATE, T_DECODE, T_EVAL, T_TEX, T_EVAL_TEX, T_BATCH, T_COUNT };
+enum { T_PLAN = 0, T_BC1, T_BC7, T_RATE, T_DECODE, T_EVAL, T_TEX, T_EVAL_TEX, T_BATCH, T_RENDER, T_BLEND, T_COUNT };
 
 struct gsc_timer_rec { int id; cudaEvent_t a, b; };
 

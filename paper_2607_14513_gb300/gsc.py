@@ -55,6 +55,22 @@ class StreamTable(C.Structure):
                      n_groups=self.s[i].n_groups, byte_offset=self.s[i].byte_offset) for i in range(self.n_streams)]
 
 
+class Camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("near_z", C.c_float)]
+
+
+def camera(d):
+    """gsc_camera from a dict with R (9), t (3), fx, fy, cx, cy, width, height, near_z."""
+    cam = Camera()
+    cam.R[:] = [float(x) for x in d["R"]]
+    cam.t[:] = [float(x) for x in d["t"]]
+    cam.fx, cam.fy, cam.cx, cam.cy = float(d["fx"]), float(d["fy"]), float(d["cx"]), float(d["cy"])
+    cam.width, cam.height, cam.near_z = int(d["width"]), int(d["height"]), float(d["near_z"])
+    return cam
+
+
 class BatchScene(C.Structure):
     _fields_ = [("d_pos", C.c_void_p), ("d_sh", C.c_void_p), ("n", C.c_int64), ("group_size", C.c_int64),
                 ("sort", C.c_int32), ("format", C.c_int32), ("target_bpt_x4", C.c_uint32), ("d_perm", C.c_void_p),
@@ -125,6 +141,9 @@ _SIGS = {
     "gsc_tex_scene_create": [_P, C.POINTER(StreamTable), _P, _P, _P, C.POINTER(C.c_void_p), _P],
     "gsc_tex_scene_destroy": [_P],
     "gsc_decode_eval_sh_tex": [_P, _P, _P, _P, _P, _P, C.c_int32, C.c_int32, _P, _P],
+    "gsc_render_workspace_bytes": [C.c_int64, C.POINTER(Camera), C.c_int64],
+    "gsc_render": [_P, C.POINTER(StreamTable), _P, _P, _P, _P, _P, _P, C.POINTER(Camera), _P, _P,
+                   C.POINTER(C.c_int64), _P, C.c_size_t, _P],
     "gsc_encode_blocks": [_P, _P, C.c_int64, C.c_int32, _P, _P, _P],
     "gsc_decode_blocks": [_P, _P, C.c_int64, C.c_int32, _P, _P],
     "gsc_decode_blocks_tex": [_P, _P, C.c_int64, C.c_int32, _P, _P],
@@ -183,6 +202,7 @@ def load(path: str | None = None):
             lib.gsc_workspace_bytes.restype = C.c_size_t
             lib.gsc_launch_count.restype = C.c_uint64
             lib.gsc_batch_workspace_bytes.restype = C.c_size_t
+            lib.gsc_render_workspace_bytes.restype = C.c_size_t
             _lib = lib
     return _lib
 
@@ -382,6 +402,37 @@ def gsc_decode_eval_sh_tex(ctx, scene, perm, dirs=None, pos=None, cams=None, out
     _check(ctx.lib.gsc_decode_eval_sh_tex(ctx.h, scene.h, _ptr(perm), _ptr(dirs), _ptr(pos), _ptr(cams), V,
                                           out_order, _ptr(rgb), _stream(stream)), "gsc_decode_eval_sh_tex")
     return rgb
+
+
+class Renderer:
+    """gsc_render with a workspace that grows to the (Gaussian, tile) overlap count it needs."""
+
+    def __init__(self, ctx):
+        self.ctx = ctx
+        self.ws = None
+
+    def render(self, table, blocks, perm, pos, scale, rot, logit, cam, image=None, trans=None, stream=None):
+        """-> (image float32 [H, W, 3], transmittance [H, W] or None, overlap count)."""
+        import torch
+        c = camera(cam)
+        dev = perm.device
+        img = image if image is not None else torch.empty((c.height, c.width, 3), dtype=torch.float32, device=dev)
+        pairs = C.c_int64(0)
+        n = table.n
+        for _ in range(2):
+            if self.ws is None:
+                nb = self.ctx.lib.gsc_render_workspace_bytes(n, C.byref(c), max(16 * n, 1 << 16))
+                self.ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+            code = self.ctx.lib.gsc_render(self.ctx.h, C.byref(table), _ptr(blocks), _ptr(perm), _ptr(pos),
+                                           _ptr(scale), _ptr(rot), _ptr(logit), C.byref(c), _ptr(img), _ptr(trans),
+                                           C.byref(pairs), _ptr(self.ws), self.ws.numel(), _stream(stream))
+            if code == 3 and pairs.value > 0:        # GSC_ERR_OOM: grow to the overlap count, once
+                nb = self.ctx.lib.gsc_render_workspace_bytes(n, C.byref(c), int(pairs.value * 5 // 4))
+                self.ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+                continue
+            _check(code, "gsc_render")
+            return img, trans, pairs.value
+        raise GscError(3, "gsc_render")
 
 
 def gsc_encode_blocks(ctx, tex, fmt, stream=None):
