@@ -51,7 +51,8 @@ MEASURED_TRAFFIC = {"scene3m": {"k_bc7": 870084864, "k_eval2_bc7": 444865024, "k
 
 
 def workload_cfg(name):
-    return {"scene3m": S.SCENE, "medium262k": S.MEDIUM, "tiny4k": S.TINY, "layouts3m": S.SCENE}[name]
+    return {"scene3m": S.SCENE, "medium262k": S.MEDIUM, "tiny4k": S.TINY, "layouts3m": S.SCENE,
+            "render3m": S.SCENE}[name]
 
 
 # Table I's fixed codings of the other block layouts (Figs. SetupA / SetupB), and layout D's
@@ -553,6 +554,150 @@ def run_layouts(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_render(args, world, rank, local):
+    """One step: the 3M-Gaussian scene, coded all-BC7 (layout D), rendered for 4 cameras at
+    1920 x 1080 (fused decode + SH colour, splat setup, tile sort, per-tile blending)."""
+    import torch
+    from paper_2607_14513_gb300 import gsc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    cfg = dict(S.RENDER)
+    n, W, H, V = cfg["n"], cfg["width"], cfg["height"], cfg["views"]
+    sc = S.make_scene(n=n, seed=cfg["seed"] + 1000 * rank, clusters=cfg["clusters"], heavy_frac=cfg["heavy_frac"])
+    geo = S.make_geometry(n, cfg["geom_seed"] + 1000 * rank, scale=cfg["scale"])
+    cams = S.make_views(V, cfg["view_seed"] + rank, W, H)
+    ctx = gsc.Context(local)
+    stream = torch.cuda.Stream(dev)
+    pos, sh = torch.from_numpy(sc.pos).to(dev), torch.from_numpy(sc.sh).to(dev)
+    scale, rot = torch.from_numpy(geo.scale).to(dev), torch.from_numpy(geo.rot).to(dev)
+    logit = torch.from_numpy(geo.logit).to(dev)
+    perm, scales = gsc.gsc_plan_reorder(ctx, pos, sh, stream=stream)
+    blk, po, tab = gsc.gsc_encode(ctx, sh, perm, scales, gsc.FMT_BC7, stream=stream)
+    r = gsc.Renderer(ctx)
+    imgs = torch.empty((V, H, W, 3), dtype=torch.float32, device=dev)
+    pairs = [0] * V
+
+    def step(blk_d, po_d, pos_d, scale_d, rot_d, logit_d):
+        for v in range(V):
+            _, _, pairs[v] = r.render(tab, blk_d, po_d, pos_d, scale_d, rot_d, logit_d, cams[v], image=imgs[v],
+                                      stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        step(blk, po, pos, scale, rot, logit)
+    stream.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    gsc.set_timing(ctx, True)
+    launches0 = gsc.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(blk, po, pos, scale, rot, logit)
+    e1.record(stream)
+    stream.synchronize()
+    launches = gsc.launch_count() - launches0
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    kt = {k: gsc.kernel_time(ctx, k) for k in ["render", "render_blend"]}
+    gsc.set_timing(ctx, False)
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
+    value = world * n * V / (ms_step * 1e-3) / 1e6
+    frames = args.steps * V
+    blend_ms = kt["render_blend"][0] / max(1, frames)
+    call_ms = kt["render"][0] / max(1, frames)
+    # the blending kernel: every pixel of a tile evaluates every splat of the tile's list
+    # (20 FP32 flops per evaluation: offset 2, quadratic form 8, weight 1, colour 6, transmittance 3;
+    # plus one exp2 on the special-function unit); peak = SMs x 128 FP32 lanes x 2 flops x SM clock
+    evals = 256 * sum(pairs) / V
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_mhz") or 2070.0
+    peak = sm * 128 * 2 * mhz * 1e6 / 1e12
+    achieved = evals * 20 / (blend_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "k_render (per-tile front-to-back blending, one thread per pixel)",
+                "peak_source": "FP32 FMA peak from the SM count, 128 lanes/SM and the sampled SM clock",
+                "algorithmic": "256 pixels x %d (Gaussian, tile) pairs per frame (mean) x 20 flops" % (sum(pairs) // V)}
+    stages = {"frame_ms": round(ms_step / V, 3), "render_call_ms": round(call_ms, 3),
+              "blend_kernel_ms": round(blend_ms, 3), "pairs_per_frame": int(sum(pairs) // V),
+              "frames_per_s": round(V / (ms_step * 1e-3), 1)}
+
+    # end to end: the coded scene and the geometry from pinned host memory, the frames back to the host
+    hosts = [t.cpu().pin_memory() for t in (blk, po, pos, scale, rot, logit)]
+    devs = [torch.empty_like(h, device=dev) for h in hosts]
+    out_h = torch.empty((V, H, W, 3), dtype=torch.float32).pin_memory()
+
+    def one():
+        with torch.cuda.stream(stream):
+            for d_, h_ in zip(devs, hosts):
+                d_.copy_(h_, non_blocking=True)
+        step(*devs)
+        with torch.cuda.stream(stream):
+            out_h.copy_(imgs, non_blocking=True)
+
+    one()
+    stream.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    stream.synchronize()
+    t = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
+    e2e = {"value": round(world * n * V / t / 1e6, 3), "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(h.numel() * h.element_size() for h in hosts)),
+           "d2h_bytes_per_step": int(out_h.numel() * 4), "ms_per_step": round(t * 1e3, 3),
+           "path": "pinned host BC7 blocks + slot order + geometry -> %d frames -> frames to host" % V}
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": max(3, args.warmup), "ms_per_step": round(ms_step, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u8 texels / f32 splatting",
+           "data": "synthetic (seeded; stands in for the paper's trained scenes)",
+           "config": {"workload": "render: %d Gaussians coded all-BC7 (8 bpt), %d cameras at %d x %d, splat scale "
+                                  "%.3f" % (n, V, W, H, cfg["scale"]),
+                      "n_gaussians": n, "parallelism": "weak, one scene per GPU" if world > 1 else "single GPU",
+                      "l2": "scene larger than L2 (BC7 blocks 48 MB, geometry 96 MB)"},
+           "roofline": roofline, "stages": stages, "clocks": clk, "e2e": e2e, "gpu_launches": int(launches)}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_render(budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline_render(budget_s=20.0):
+    """The oracle renderer on a bounded sample: a 20,000-Gaussian piece of the scene coded and
+    rendered at 480 x 270 for one camera, charged per Gaussian per frame."""
+    from oracle import oracle as O
+    cfg = S.RENDER
+    n = 20000
+    sc = S.make_scene(n=n, seed=cfg["seed"], clusters=cfg["clusters"], heavy_frac=cfg["heavy_frac"])
+    geo = S.make_geometry(n, cfg["geom_seed"], scale=cfg["scale"] * 4)
+    cam = S.make_views(1, cfg["view_seed"], 480, 270)[0]
+    osc = O.scales(sc.sh)
+    q = O.quantise(sc.sh, osc)
+    r = O.encode(q, np.arange(n, dtype=np.int32), osc, 1)      # coding is outside the timed frame
+    t0 = time.perf_counter()
+    tex = O.decode(r["table"], r["blocks"], r["perm"])
+    colour = O.eval_sh(tex, osc, pos=sc.pos, cams=O.camera_centre(cam)[None, :])[0]
+    O.render(sc.pos, geo.scale, geo.rot, geo.logit, colour, cam)
+    t = time.perf_counter() - t0
+    return {"value": round(n / t / 1e6, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "decode + SH colour + splatting of %d Gaussians for one 480 x 270 frame (BC1-coded sample), "
+                      "per Gaussian per frame" % n}
+
+
 def C_ref(x):
     import ctypes
     return ctypes.byref(x)
@@ -870,6 +1015,8 @@ def cpu_baseline_mix(mix, budget_s=20.0):
 def cpu_baseline(workload, budget_s=20.0):
     if workload == "layouts3m":
         return cpu_baseline_layouts(budget_s)
+    if workload == "render3m":
+        return cpu_baseline_render(budget_s)
     return cpu_baseline_d(workload, budget_s)
 
 
@@ -972,7 +1119,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gsc", choices=["gsc", "reference"])
     ap.add_argument("--workload", default="scene3m",
-                    choices=["scene3m", "medium262k", "tiny4k", "layouts3m", "batch64", "serve"])
+                    choices=["scene3m", "medium262k", "tiny4k", "layouts3m", "render3m", "batch64", "serve"])
     ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -989,6 +1136,9 @@ def main():
         return
     if args.workload == "layouts3m":
         run_layouts(args, world, rank, local)
+        return
+    if args.workload == "render3m":
+        run_render(args, world, rank, local)
         return
     run_gsc(args, world, rank, local)
 
