@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_bc1_groups(const float* __res
   if (threadIdx.x < 16) s_scale[threadIdx.x] = scales[threadIdx.x];
   __syncthreads();
   for (int64_t g0 = (int64_t)blockIdx.x * STAGE_GROUPS; g0 < n_groups; g0 += (int64_t)gridDim.x * STAGE_GROUPS) {
-    stage_groups(sh, perm, s_scale, g0, n_groups, tex);
+    stage_groups(sh, perm, s_scale, g0, n_groups, tex, threadIdx.x);
     __syncthreads();
     const int64_t blk = g0 * 16 + threadIdx.x;
     if (blk < n_groups * 16) {

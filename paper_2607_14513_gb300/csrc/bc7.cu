@@ -328,6 +328,10 @@ __device__ __forceinline__ uint32_t rot_sel(int rot) {
   return rot == 1 ? 0x4021u : (rot == 2 ? 0x4120u : 0x4210u);
 }
 
+// SYNC: every thread of the CTA calls the search, and a barrier after each mode's candidates
+// keeps the CTA's warps in the same part of the (large) search code, so they share the
+// instruction cache.
+template <bool SYNC>
 __device__ __noinline__ int search_best(const uint32_t* tex, uint32_t* best_sse, const uint16_t* sq) {
   uint32_t best = 0xFFFFFFFFu;
   int be = 0;
@@ -339,8 +343,11 @@ __device__ __noinline__ int search_best(const uint32_t* tex, uint32_t* best_sse,
     if (s_ < best || (s_ == best && e_ < be)) { best = s_; be = e_; } \
   } while (0)
   for (int p = 0; p < 16; p++) CAND((score_part<3, 3, PT_UNIQUE, 4>(tex, c_part3[p], sq)), p);
+  if (SYNC) __syncthreads();
   for (int p = 0; p < 64; p++) CAND((score_part<2, 3, PT_SHARED, 6>(tex, c_part2[p], sq)), 16 + p);
+  if (SYNC) __syncthreads();
   for (int p = 0; p < 64; p++) CAND((score_part<3, 2, PT_NONE, 5>(tex, c_part3[p], sq)), 80 + p);
+  if (SYNC) __syncthreads();
   // modes 3 and 7: same partitions and 2-bit weights, so one prefit per subset serves both
   for (int p = 0; p < 64; p++) {
     const uint32_t part = c_part2[p];
@@ -355,6 +362,7 @@ __device__ __noinline__ int search_best(const uint32_t* tex, uint32_t* best_sse,
     CAND(s3, 144 + p);
     CAND(s7, 221 + p);
   }
+  if (SYNC) __syncthreads();
   CAND((score_rot<4, 0, 0>(tex, nullptr, nullptr, sq)), 208);
   CAND((score_rot<4, 0, 1>(tex, nullptr, nullptr, sq)), 209);
   CAND((score_rot<5, 0, 0>(tex, nullptr, nullptr, sq)), 216);
@@ -519,40 +527,51 @@ __device__ __noinline__ uint4 solve_pack(const uint32_t* tx, int e, const uint16
 }
 
 // One kernel for both sources: staged layout-D groups (sh / perm / scales) or raw
-// texels [nblk][16][3] (texin != nullptr), so the search is compiled once. Each thread's
-// texels stay in the shared tile (column threadIdx.x) for the whole search.
-// 5 resident CTAs per SM (at most 102 registers, a few spills) measured fastest: 24.7 Mblocks/s
-// against 23.0 at 4 and 24.3 at 6.
-#ifndef BC7_MIN_BLOCKS
-#define BC7_MIN_BLOCKS 5
+// texels [nblk][16][3] (texin != nullptr), so the search is compiled once. A CTA is BC7_SUBS
+// staging units of 128 threads (one block per thread); each thread's texels stay in its unit's
+// shared tile (column threadIdx.x % 128) for the whole search. Every thread searches (threads
+// past the last block on texels of 128) so that the barriers between the search's modes are
+// reached by the whole CTA.
+// 5 units (20 warps, at most 102 registers) per SM: 5 resident 128-thread CTAs measured fastest
+// before the barriers (24.7 Mblocks/s against 23.0 at 4 and 24.3 at 6).
+#ifndef BC7_SUBS
+#define BC7_SUBS 5
 #endif
-__global__ void __launch_bounds__(STAGE_THREADS, BC7_MIN_BLOCKS) k_bc7(const float* __restrict__ sh, const int32_t* __restrict__ perm,
-                                                       const float* __restrict__ scales, int64_t n_groups,
-                                                       const uint8_t* __restrict__ texin, int64_t nblk,
-                                                       uint4* __restrict__ blocks, uint32_t* __restrict__ sse7,
-                                                       uint64_t* __restrict__ sse64) {
-  __shared__ uint32_t tex[16][STAGE_STRIDE];
+// the persistent multi-scene kernel keeps 128-thread CTAs, 5 per SM
+#define BC7_MIN_BLOCKS 5
+#define BC7_THREADS (BC7_SUBS * STAGE_THREADS)
+__global__ void __launch_bounds__(BC7_THREADS, 1) k_bc7(const float* __restrict__ sh, const int32_t* __restrict__ perm,
+                                                        const float* __restrict__ scales, int64_t n_groups,
+                                                        const uint8_t* __restrict__ texin, int64_t nblk,
+                                                        uint4* __restrict__ blocks, uint32_t* __restrict__ sse7,
+                                                        uint64_t* __restrict__ sse64) {
+  __shared__ uint32_t tex[BC7_SUBS][16][STAGE_STRIDE];
   __shared__ float s_scale[16];
   __shared__ uint16_t sq[12 * 256];
   for (int i = threadIdx.x; i < 12 * 256; i += blockDim.x) sq[i] = (&g_qtab[0][0])[i];
   if (!texin && threadIdx.x < 16) s_scale[threadIdx.x] = scales[threadIdx.x];
   __syncthreads();
+  const int sub = threadIdx.x / STAGE_THREADS, lt = threadIdx.x % STAGE_THREADS;
   const int64_t total = texin ? nblk : n_groups * 16;
-  for (int64_t b0 = (int64_t)blockIdx.x * STAGE_THREADS; b0 < total; b0 += (int64_t)gridDim.x * STAGE_THREADS) {
-    const int64_t blk = b0 + threadIdx.x;
+  for (int64_t b0 = (int64_t)blockIdx.x * BC7_THREADS; b0 < total; b0 += (int64_t)gridDim.x * BC7_THREADS) {
+    const int64_t bs = b0 + sub * STAGE_THREADS;  // first block of this thread's staging unit
+    const int64_t blk = bs + lt;
     if (!texin) {
-      stage_groups(sh, perm, s_scale, b0 / 16, n_groups, tex);
+      stage_groups(sh, perm, s_scale, bs / 16, n_groups, tex[sub], lt);
     } else if (blk < total) {
       const uint8_t* p = texin + blk * 48;
 #pragma unroll
       for (int t = 0; t < 16; t++)
-        tex[t][threadIdx.x] = (uint32_t)p[3 * t] | ((uint32_t)p[3 * t + 1] << 8) | ((uint32_t)p[3 * t + 2] << 16);
+        tex[sub][t][lt] = (uint32_t)p[3 * t] | ((uint32_t)p[3 * t + 1] << 8) | ((uint32_t)p[3 * t + 2] << 16);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 16; t++) tex[sub][t][lt] = 0x808080u;
     }
     __syncthreads();
+    uint32_t best;
+    const uint32_t* my = &tex[sub][0][lt];
+    const int e = search_best<true>(my, &best, sq);
     if (blk < total) {
-      uint32_t best;
-      const uint32_t* my = &tex[0][threadIdx.x];
-      const int e = search_best(my, &best, sq);
       blocks[blk] = solve_pack(my, e, sq);
       if (sse7) sse7[blk] = best;
       if (sse64) sse64[blk] = best;
@@ -570,14 +589,14 @@ static int grid_for7(int64_t work, int per_cta) {
 cudaError_t launch_bc7_groups(const float* sh, const int32_t* perm, const float* scales, int64_t n_groups,
                               uint8_t* blocks, uint32_t* sse7, cudaStream_t st) {
   if (n_groups <= 0) return cudaSuccess;
-  gsc_count_launch(); k_bc7<<<grid_for7(n_groups, STAGE_GROUPS), STAGE_THREADS, 0, st>>>(
+  gsc_count_launch(); k_bc7<<<grid_for7(n_groups, STAGE_GROUPS * BC7_SUBS), BC7_THREADS, 0, st>>>(
       sh, perm, scales, n_groups, nullptr, 0, reinterpret_cast<uint4*>(blocks), sse7, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bc7_blocks(const uint8_t* tex, int64_t nblk, uint8_t* out, uint64_t* sse, cudaStream_t st) {
   if (nblk <= 0) return cudaSuccess;
-  gsc_count_launch(); k_bc7<<<grid_for7(nblk, STAGE_THREADS), STAGE_THREADS, 0, st>>>(nullptr, nullptr, nullptr, 0, tex, nblk,
+  gsc_count_launch(); k_bc7<<<grid_for7(nblk, BC7_THREADS), BC7_THREADS, 0, st>>>(nullptr, nullptr, nullptr, 0, tex, nblk,
                                                                 reinterpret_cast<uint4*>(out), nullptr, sse);
   return cudaGetLastError();
 }
@@ -615,7 +634,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, BC7_MIN_BLOCKS) k_batch(const B
     if (threadIdx.x < 16) s_scale[threadIdx.x] = S.scales[threadIdx.x];
     __syncthreads();
     for (int64_t g0 = gbeg; g0 < gend; g0 += STAGE_GROUPS) {
-      stage_groups(S.sh, S.perm, s_scale, g0, S.n_groups, tex);
+      stage_groups(S.sh, S.perm, s_scale, g0, S.n_groups, tex, threadIdx.x);
       __syncthreads();
       const int64_t blk = g0 * 16 + threadIdx.x;
       if (blk < S.n_groups * 16) {
@@ -630,7 +649,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, BC7_MIN_BLOCKS) k_batch(const B
         } else {
           uint32_t best;
           const uint32_t* my = &tex[0][threadIdx.x];
-          const int e = search_best(my, &best, sq);
+          const int e = search_best<false>(my, &best, sq);
           reinterpret_cast<uint4*>(S.b7)[blk] = solve_pack(my, e, sq);
           if (S.sse7) S.sse7[blk] = best;
         }

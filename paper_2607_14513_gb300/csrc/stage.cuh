@@ -13,10 +13,11 @@
 #define STAGE_THREADS 128
 #define STAGE_STRIDE 129
 
+// i: the thread's index inside its 128-thread staging unit (a multiple of 32 apart from
+// threadIdx.x, so the warp-level ballots below see the same lanes)
 __device__ __forceinline__ void stage_groups(const float* __restrict__ sh, const int32_t* __restrict__ perm,
                                              const float* s_scale, int64_t g0, int64_t n_groups,
-                                             uint32_t (*tex)[STAGE_STRIDE]) {
-  const int i = threadIdx.x;
+                                             uint32_t (*tex)[STAGE_STRIDE], int i) {
   const int lg = i >> 4, t = i & 15;
   const int64_t g = g0 + lg;
   const bool live = g < n_groups;
