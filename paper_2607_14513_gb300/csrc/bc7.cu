@@ -603,53 +603,81 @@ cudaError_t launch_bc7_blocks(const uint8_t* tex, int64_t nblk, uint8_t* out, ui
 
 // ---- persistent multi-scene encode -----------------------------------------------------------
 // One launch per coding (KIND 1 = BC1, 7 = BC7) over the tiles of every listed scene. Tiles
-// are claimed round robin (schedule 0), from an atomic work queue (1, 2), or one per CTA (3, a
-// grid of all tiles); a tile finds its scene by binary search over the list. Each tile stages
-// 8 groups at a time; the bits equal the single-scene kernels'.
+// are claimed round robin (schedule 0), from an atomic work queue (1, 2), or one per CTA unit
+// (3, a grid of all tiles); a tile finds its scene by binary search over the list. A BC7 CTA is
+// BC7_SUBS staging units of 128 threads, each claiming its own tile, that step through their
+// tiles 8 groups at a time in lockstep (units past their tile's end search texels of 128), so
+// the search's barriers are reached by the whole CTA, as in k_bc7. The bits equal the
+// single-scene kernels'.
 template <int KIND>
-__global__ void __launch_bounds__(STAGE_THREADS, BC7_MIN_BLOCKS) k_batch(const BatchSceneDev* __restrict__ scenes, int n_scenes,
-                                                            int64_t n_tiles, int schedule, int* __restrict__ counter) {
-  __shared__ uint32_t tex[16][STAGE_STRIDE];
-  __shared__ float s_scale[16];
+__global__ void __launch_bounds__((KIND == 7 ? BC7_SUBS : 1) * STAGE_THREADS, KIND == 7 ? 1 : BC7_MIN_BLOCKS)
+    k_batch(const BatchSceneDev* __restrict__ scenes, int n_scenes, int64_t n_tiles, int schedule,
+            int* __restrict__ counter) {
+  constexpr int SUBS = KIND == 7 ? BC7_SUBS : 1;
+  __shared__ uint32_t tex[SUBS][16][STAGE_STRIDE];
+  __shared__ float s_scale[SUBS][16];
   __shared__ uint16_t sq[KIND == 7 ? 12 * 256 : 1];
-  __shared__ long long s_tile;
+  __shared__ long long s_tile[SUBS];
+  __shared__ int s_iters;
   if (KIND == 7)
     for (int i = threadIdx.x; i < 12 * 256; i += blockDim.x) sq[i] = (&g_qtab[0][0])[i];
+  const int sub = threadIdx.x / STAGE_THREADS, lt = threadIdx.x % STAGE_THREADS;
   for (int64_t it = 0;; it++) {
     __syncthreads();
-    if (threadIdx.x == 0)
-      s_tile = (schedule == 0 || schedule == 3) ? (long long)(blockIdx.x + it * gridDim.x)
-                                                : (long long)atomicAdd(counter, 1);
+    if (lt == 0)
+      s_tile[sub] = (schedule == 0 || schedule == 3) ? (long long)((blockIdx.x + it * gridDim.x) * SUBS + sub)
+                                                     : (long long)atomicAdd(counter, 1);
+    if (threadIdx.x == 0) s_iters = 0;
     __syncthreads();
-    const int64_t ti = s_tile;
-    if (ti >= n_tiles) break;
-    int lo = 0, hi = n_scenes - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (scenes[mid].tile0 <= ti) lo = mid; else hi = mid - 1;
+    bool any = false;
+#pragma unroll
+    for (int u = 0; u < SUBS; u++) any |= s_tile[u] < n_tiles;
+    if (!any) break;
+    const int64_t ti = s_tile[sub];
+    const bool has = ti < n_tiles;
+    BatchSceneDev S;
+    int64_t gbeg = 0, gend = 0;
+    if (has) {
+      int lo = 0, hi = n_scenes - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (scenes[mid].tile0 <= ti) lo = mid; else hi = mid - 1;
+      }
+      S = scenes[lo];
+      gbeg = (ti - S.tile0) * S.tile_groups;
+      gend = min(gbeg + (int64_t)S.tile_groups, S.work_groups);
+      if (lt < 16) s_scale[sub][lt] = S.scales[lt];
+      if (lt == 0) atomicMax(&s_iters, (int)((gend - gbeg + STAGE_GROUPS - 1) / STAGE_GROUPS));
     }
-    const BatchSceneDev S = scenes[lo];
-    const int64_t gbeg = (ti - S.tile0) * S.tile_groups;
-    const int64_t gend = min(gbeg + (int64_t)S.tile_groups, S.work_groups);
-    if (threadIdx.x < 16) s_scale[threadIdx.x] = S.scales[threadIdx.x];
     __syncthreads();
-    for (int64_t g0 = gbeg; g0 < gend; g0 += STAGE_GROUPS) {
-      stage_groups(S.sh, S.perm, s_scale, g0, S.n_groups, tex, threadIdx.x);
+    const int iters = s_iters;  // the longest tile of the CTA's units, in staging steps
+    for (int k = 0; k < iters; k++) {
+      const int64_t g0 = gbeg + (int64_t)k * STAGE_GROUPS;
+      const bool live = has && g0 < gend;
+      if (live) {
+        stage_groups(S.sh, S.perm, s_scale[sub], g0, S.n_groups, tex[sub], lt);
+      } else {
+#pragma unroll
+        for (int t = 0; t < 16; t++) tex[sub][t][lt] = 0x808080u;
+      }
       __syncthreads();
-      const int64_t blk = g0 * 16 + threadIdx.x;
-      if (blk < S.n_groups * 16) {
-        if (KIND == 1) {
+      const int64_t blk = g0 * 16 + lt;
+      const bool write = live && blk < S.n_groups * 16;
+      if (KIND == 1) {
+        if (write) {
           uint32_t tx[16];
 #pragma unroll
-          for (int t = 0; t < 16; t++) tx[t] = tex[t][threadIdx.x];
+          for (int t = 0; t < 16; t++) tx[t] = tex[sub][t][lt];
           const Bc1Res r = bc1_encode(tx);
           reinterpret_cast<uint2*>(S.b1)[blk] = bc1_bits(r);
           if (S.sse1) S.sse1[blk] = r.sse;
           if (S.sse0) S.sse0[blk] = sse_zero(tx);
-        } else {
-          uint32_t best;
-          const uint32_t* my = &tex[0][threadIdx.x];
-          const int e = search_best<false>(my, &best, sq);
+        }
+      } else {
+        uint32_t best;
+        const uint32_t* my = &tex[sub][0][lt];
+        const int e = search_best<true>(my, &best, sq);
+        if (write) {
           reinterpret_cast<uint4*>(S.b7)[blk] = solve_pack(my, e, sq);
           if (S.sse7) S.sse7[blk] = best;
         }
@@ -662,16 +690,19 @@ __global__ void __launch_bounds__(STAGE_THREADS, BC7_MIN_BLOCKS) k_batch(const B
 cudaError_t launch_batch_encode(int kind, const BatchSceneDev* scenes, int n_scenes, int64_t n_tiles, int schedule,
                                 int ctas_per_sm, int sm_count, int* counter, cudaStream_t st) {
   if (n_tiles <= 0 || n_scenes <= 0) return cudaSuccess;
-  // schedule 3: one CTA per tile, left to the hardware block scheduler
-  int64_t grid = schedule == 3 ? n_tiles : (int64_t)(sm_count > 0 ? sm_count : 152) * (ctas_per_sm > 0 ? ctas_per_sm : BC7_MIN_BLOCKS);
-  if (grid > n_tiles) grid = n_tiles;
+  // schedule 3: one CTA unit per tile, left to the hardware block scheduler; a BC7 CTA holds
+  // BC7_SUBS units
+  const int64_t units = kind == 7 ? BC7_SUBS : 1;
+  const int64_t cta_tiles = ceil_div64(n_tiles, units);
+  int64_t grid = schedule == 3 ? cta_tiles : (int64_t)(sm_count > 0 ? sm_count : 152) * (ctas_per_sm > 0 ? ctas_per_sm : BC7_MIN_BLOCKS);
+  if (grid > cta_tiles) grid = cta_tiles;
   if (grid > 0x7FFFFFFF) grid = 0x7FFFFFFF;
   if (schedule == 1 || schedule == 2) {
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
   }
   gsc_count_launch();
-  if (kind == 7) k_batch<7><<<(int)grid, STAGE_THREADS, 0, st>>>(scenes, n_scenes, n_tiles, schedule, counter);
+  if (kind == 7) k_batch<7><<<(int)grid, BC7_THREADS, 0, st>>>(scenes, n_scenes, n_tiles, schedule, counter);
   else k_batch<1><<<(int)grid, STAGE_THREADS, 0, st>>>(scenes, n_scenes, n_tiles, schedule, counter);
   return cudaGetLastError();
 }
