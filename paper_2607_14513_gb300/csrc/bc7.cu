@@ -194,14 +194,28 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
     }
 #pragma unroll
     for (int i = 0; i < NCH; i++) { sav[i] = 0; sbv[i] = 0; }
-    for (uint32_t m = mm; m; m &= m - 1) {
-      const int t = (__ffs(m) - 1) >> 1;
-      const uint32_t v = __byte_perm(tex[t * STAGE_STRIDE], 0u, sel) & CM;
-      const int bj = best_key<F>(v, pal, pk) & 15;
-      const int w = wgt<IB>(bj), a = 64 - w;
+    auto accumulate = [&](uint32_t v, int key) {
+      const int w = wgt<IB>(key & 15), a = 64 - w;
       saa += a * a; sbb += w * w; sab += a * w;
 #pragma unroll
       for (int i = 0; i < NCH; i++) { const int c = (v >> (8 * ch[i])) & 255; sav[i] += a * c; sbv[i] += w * c; }
+    };
+    // two member texels per step (independent palette searches; integer sums, order-free)
+    uint32_t m = mm;
+    while (m) {
+      const int ta = (__ffs(m) - 1) >> 1;
+      m &= m - 1;
+      const uint32_t va = __byte_perm(tex[ta * STAGE_STRIDE], 0u, sel) & CM;
+      if (m) {
+        const int tb = (__ffs(m) - 1) >> 1;
+        m &= m - 1;
+        const uint32_t vb = __byte_perm(tex[tb * STAGE_STRIDE], 0u, sel) & CM;
+        const int ka = best_key<F>(va, pal, pk), kb = best_key<F>(vb, pal, pk);
+        accumulate(va, ka);
+        accumulate(vb, kb);
+      } else {
+        accumulate(va, best_key<F>(va, pal, pk));
+      }
     }
   }
   const long long det = (long long)saa * sbb - (long long)sab * sab;
@@ -251,12 +265,33 @@ __device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex,
     build_pal<IB>(v0, v1, pal, pk);  // uncoded channels have zero endpoints, so their bytes are 0
     int sse = 0;
     uint32_t il = 0, ih = 0;
-    for (uint32_t m = member_mask(part, s); m; m &= m - 1) {
-      const int t = (__ffs(m) - 1) >> 1;
-      const uint32_t v = __byte_perm(tex[t * STAGE_STRIDE], 0u, sel) & CM;
-      const int key = best_key<F>(v, pal, pk);
-      sse += (int)__dp4a(v, v, 0u) + (key >> 4);
-      if (OUT) { if (t < 8) il |= (uint32_t)(key & 15) << (4 * t); else ih |= (uint32_t)(key & 15) << (4 * (t - 8)); }
+    if (OUT) {
+      for (uint32_t m = member_mask(part, s); m; m &= m - 1) {
+        const int t = (__ffs(m) - 1) >> 1;
+        const uint32_t v = __byte_perm(tex[t * STAGE_STRIDE], 0u, sel) & CM;
+        const int key = best_key<F>(v, pal, pk);
+        sse += (int)__dp4a(v, v, 0u) + (key >> 4);
+        if (t < 8) il |= (uint32_t)(key & 15) << (4 * t); else ih |= (uint32_t)(key & 15) << (4 * (t - 8));
+      }
+    } else {
+      // two member texels per step: their palette searches are independent chains (the error is
+      // an integer sum, so the order of the additions does not matter)
+      uint32_t m = member_mask(part, s);
+      while (m) {
+        const int ta = (__ffs(m) - 1) >> 1;
+        m &= m - 1;
+        const uint32_t va = __byte_perm(tex[ta * STAGE_STRIDE], 0u, sel) & CM;
+        if (m) {
+          const int tb = (__ffs(m) - 1) >> 1;
+          m &= m - 1;
+          const uint32_t vb = __byte_perm(tex[tb * STAGE_STRIDE], 0u, sel) & CM;
+          const int ka = best_key<F>(va, pal, pk), kb = best_key<F>(vb, pal, pk);
+          sse += ((int)__dp4a(va, va, 0u) + (ka >> 4)) + ((int)__dp4a(vb, vb, 0u) + (kb >> 4));
+        } else {
+          const int ka = best_key<F>(va, pal, pk);
+          sse += (int)__dp4a(va, va, 0u) + (ka >> 4);
+        }
+      }
     }
     if ((uint32_t)sse < best_sse) {
       best_sse = (uint32_t)sse;
