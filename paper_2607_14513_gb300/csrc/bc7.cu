@@ -25,6 +25,7 @@ __constant__ uint8_t c_anc3a[64];
 __constant__ uint8_t c_anc3b[64];
 // nearest endpoint code per 8-bit target: code | expanded value << 8, 12 configurations
 __device__ uint16_t g_qtab[12][256];
+cudaError_t bc7_kernel_attributes();
 
 static int h_expand(int v, int n) { return n >= 8 ? v : ((v << (8 - n)) | (v >> (2 * n - 8))); }
 
@@ -63,7 +64,8 @@ cudaError_t bc7_init_tables() {
   if ((e = cudaMemcpyToSymbol(c_anc2, a2, sizeof(a2))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_anc3a, a3a, sizeof(a3a))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_anc3b, a3b, sizeof(a3b))) != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(g_qtab, q, sizeof(q));
+  if ((e = cudaMemcpyToSymbol(g_qtab, q, sizeof(q))) != cudaSuccess) return e;
+  return bc7_kernel_attributes();
 }
 
 // table ids: (bits, p-bit present, p)
@@ -567,20 +569,23 @@ __device__ __noinline__ uint4 solve_pack(const uint32_t* tx, int e, const uint16
 // shared tile (column threadIdx.x % 128) for the whole search. Every thread searches (threads
 // past the last block on texels of 128) so that the barriers between the search's modes are
 // reached by the whole CTA.
-// 5 units (20 warps, at most 102 registers) per SM: 5 resident 128-thread CTAs measured fastest
-// before the barriers (24.7 Mblocks/s against 23.0 at 4 and 24.3 at 6).
+// 5 units (20 warps, at most 102 registers) per CTA and SM measured fastest: 100.9 ms for 3M
+// blocks against 107.7 ms with 4 units (128 registers) and 101.4 ms with 6 (80 registers).
 #ifndef BC7_SUBS
 #define BC7_SUBS 5
 #endif
 // the persistent multi-scene kernel keeps 128-thread CTAs, 5 per SM
 #define BC7_MIN_BLOCKS 5
 #define BC7_THREADS (BC7_SUBS * STAGE_THREADS)
+#define BC7_DYN_SMEM (BC7_SUBS * 16 * STAGE_STRIDE * 4)
 __global__ void __launch_bounds__(BC7_THREADS, 1) k_bc7(const float* __restrict__ sh, const int32_t* __restrict__ perm,
                                                         const float* __restrict__ scales, int64_t n_groups,
                                                         const uint8_t* __restrict__ texin, int64_t nblk,
                                                         uint4* __restrict__ blocks, uint32_t* __restrict__ sse7,
                                                         uint64_t* __restrict__ sse64) {
-  __shared__ uint32_t tex[BC7_SUBS][16][STAGE_STRIDE];
+  // the units' texel tiles live in dynamic shared memory (more than 48 KB for six units)
+  extern __shared__ uint32_t k_bc7_dyn[];
+  uint32_t(*tex)[16][STAGE_STRIDE] = reinterpret_cast<uint32_t(*)[16][STAGE_STRIDE]>(k_bc7_dyn);
   __shared__ float s_scale[16];
   __shared__ uint16_t sq[12 * 256];
   for (int i = threadIdx.x; i < 12 * 256; i += blockDim.x) sq[i] = (&g_qtab[0][0])[i];
@@ -615,6 +620,11 @@ __global__ void __launch_bounds__(BC7_THREADS, 1) k_bc7(const float* __restrict_
   }
 }
 
+// allows the dynamic shared memory of k_bc7 above 48 KB (called once with the tables)
+cudaError_t bc7_kernel_attributes() {
+  return cudaFuncSetAttribute(k_bc7, cudaFuncAttributeMaxDynamicSharedMemorySize, BC7_DYN_SMEM);
+}
+
 static int grid_for7(int64_t work, int per_cta) {
   int64_t g = ceil_div64(work, per_cta);
   if (g > 152 * 32) g = 152 * 32;
@@ -624,14 +634,14 @@ static int grid_for7(int64_t work, int per_cta) {
 cudaError_t launch_bc7_groups(const float* sh, const int32_t* perm, const float* scales, int64_t n_groups,
                               uint8_t* blocks, uint32_t* sse7, cudaStream_t st) {
   if (n_groups <= 0) return cudaSuccess;
-  gsc_count_launch(); k_bc7<<<grid_for7(n_groups, STAGE_GROUPS * BC7_SUBS), BC7_THREADS, 0, st>>>(
+  gsc_count_launch(); k_bc7<<<grid_for7(n_groups, STAGE_GROUPS * BC7_SUBS), BC7_THREADS, BC7_DYN_SMEM, st>>>(
       sh, perm, scales, n_groups, nullptr, 0, reinterpret_cast<uint4*>(blocks), sse7, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bc7_blocks(const uint8_t* tex, int64_t nblk, uint8_t* out, uint64_t* sse, cudaStream_t st) {
   if (nblk <= 0) return cudaSuccess;
-  gsc_count_launch(); k_bc7<<<grid_for7(nblk, BC7_THREADS), BC7_THREADS, 0, st>>>(nullptr, nullptr, nullptr, 0, tex, nblk,
+  gsc_count_launch(); k_bc7<<<grid_for7(nblk, BC7_THREADS), BC7_THREADS, BC7_DYN_SMEM, st>>>(nullptr, nullptr, nullptr, 0, tex, nblk,
                                                                 reinterpret_cast<uint4*>(out), nullptr, sse);
   return cudaGetLastError();
 }
