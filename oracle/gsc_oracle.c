@@ -1327,3 +1327,152 @@ int or_render(int64_t n, const float* pos, const float* scale, const float* rot,
   free(list);
   return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Geometry streams and the chunk hierarchy (Sec. IV-A: position and shape are  */
+/* coded apart from appearance, each parameter simply quantised to a fixed     */
+/* number of bits and kept in its own fixed-rate bitstream; a hierarchical     */
+/* organisation lets a view use only the primitives of the part it sees).      */
+/* Readings (the paper gives no bit allocation): slot order (positions move    */
+/* with the Gaussians, so no index is stored); chunks of C consecutive slots;  */
+/* per chunk the bounding box of its centres and its largest scale; position   */
+/* 3 x 16 bits over the chunk box; scale 3 x bfloat16; rotation as the        */
+/* "smallest three" of the unit quaternion (2-bit index of the largest         */
+/* component, made positive, and three 10-bit codes of 1022 steps over         */
+/* [-1/sqrt2, 1/sqrt2]); opacity logit 8 bits over [-8, 8]. 17 bytes per slot.  */
+/* ------------------------------------------------------------------------- */
+static uint16_t bf16_rne(float x) {
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+static float bf16_val(uint16_t h) {
+  uint32_t u = (uint32_t)h << 16;
+  float x;
+  memcpy(&x, &u, 4);
+  return x;
+}
+static uint32_t quant_unit(float t, float levels) { /* round(t * levels), t clamped to [0, 1] */
+  float c = t < 0.0f ? 0.0f : (t > 1.0f ? 1.0f : t);
+  return (uint32_t)rintf(c * levels);
+}
+
+int64_t or_chunks(int64_t n_slots, int64_t chunk_slots) { return (n_slots + chunk_slots - 1) / chunk_slots; }
+
+/* chunk[c] = lo[3], hi[3] (bounds of the chunk's centres), largest decoded scale, 0 */
+void or_chunk_table(const float* pos, const float* scale, const int32_t* perm, int64_t n_slots, int64_t chunk_slots,
+                    float* chunk) {
+  int64_t nc = or_chunks(n_slots, chunk_slots);
+  for (int64_t c = 0; c < nc; c++) {
+    float* e = chunk + 8 * c;
+    int any = 0;
+    for (int a = 0; a < 8; a++) e[a] = 0.0f;
+    for (int64_t s = c * chunk_slots; s < (c + 1) * chunk_slots && s < n_slots; s++) {
+      int32_t o = perm[s];
+      if (o < 0) continue;
+      for (int a = 0; a < 3; a++) {
+        float p = pos[3 * (int64_t)o + a];
+        if (!any || p < e[a]) e[a] = p;
+        if (!any || p > e[3 + a]) e[3 + a] = p;
+        float sv = bf16_val(bf16_rne(scale[3 * (int64_t)o + a]));
+        if (!any || sv > e[6]) e[6] = sv;
+        if (a == 2) any = 1;
+      }
+    }
+  }
+}
+
+/* Codes of slot s (Gaussian o = perm[s]) into the streams; padding slots get zero codes. */
+void or_geometry_encode(const float* pos, const float* scale, const float* rot, const float* logit,
+                        const int32_t* perm, int64_t n_slots, int64_t chunk_slots, const float* chunk,
+                        uint16_t* qpos, uint16_t* qscale, uint32_t* qrot, uint8_t* qlogit) {
+  for (int64_t s = 0; s < n_slots; s++) {
+    int32_t o = perm[s];
+    if (o < 0) {
+      for (int a = 0; a < 3; a++) { qpos[3 * s + a] = 0; qscale[3 * s + a] = 0; }
+      qrot[s] = 0; qlogit[s] = 0;
+      continue;
+    }
+    const float* e = chunk + 8 * (s / chunk_slots);
+    for (int a = 0; a < 3; a++) {
+      float ext = e[3 + a] - e[a];
+      float t = ext > 0.0f ? (pos[3 * (int64_t)o + a] - e[a]) / ext : 0.0f;
+      qpos[3 * s + a] = (uint16_t)quant_unit(t, 65535.0f);
+      qscale[3 * s + a] = bf16_rne(scale[3 * (int64_t)o + a]);
+    }
+    /* smallest three: normalise, largest |component| first on ties, made non-negative */
+    const float* q = rot + 4 * (int64_t)o;
+    float nq = sqrtf(((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]) + q[3] * q[3]);
+    float u[4];
+    for (int a = 0; a < 4; a++) u[a] = nq > 0.0f ? q[a] / nq : (a == 0 ? 1.0f : 0.0f);
+    int m = 0;
+    for (int a = 1; a < 4; a++) if (fabsf(u[a]) > fabsf(u[m])) m = a;
+    float sg = u[m] < 0.0f ? -1.0f : 1.0f;
+    uint32_t code = (uint32_t)m, sh = 2;
+    for (int a = 0; a < 4; a++) {
+      if (a == m) continue;
+      float c = sg * u[a];                                 /* in [-1/sqrt2, 1/sqrt2] */
+      float t = c * 0.70710678f + 0.5f;                    /* [-1/sqrt2, 1/sqrt2] -> [0, 1] */
+      code |= quant_unit(t, 1022.0f) << sh;                /* 1022 steps: 0 is code 511 exactly */
+      sh += 10;
+    }
+    qrot[s] = code;
+    float lt = (logit[o] + 8.0f) / 16.0f;
+    qlogit[s] = (uint8_t)quant_unit(lt, 255.0f);
+  }
+}
+
+/* Decoded geometry of slot s in float, with the fixed operation order every decoder uses. */
+void or_geometry_decode_slot(const uint16_t* qpos, const uint16_t* qscale, const uint32_t* qrot, const uint8_t* qlogit,
+                             int64_t s, int64_t chunk_slots, const float* chunk, float* p, float* sc, float* q,
+                             float* t) {
+  const float* e = chunk + 8 * (s / chunk_slots);
+  for (int a = 0; a < 3; a++) {
+    float ext = e[3 + a] - e[a];
+    p[a] = e[a] + ((float)qpos[3 * s + a] / 65535.0f) * ext;
+    sc[a] = bf16_val(qscale[3 * s + a]);
+  }
+  uint32_t code = qrot[s];
+  int m = (int)(code & 3u);
+  float ss = 0.0f;
+  int sh = 2;
+  for (int a = 0; a < 4; a++) {
+    if (a == m) continue;
+    float c = (((float)((code >> sh) & 1023u) / 1022.0f) - 0.5f) * 1.41421356f;
+    q[a] = c;
+    ss = ss + c * c;
+    sh += 10;
+  }
+  float r = 1.0f - ss;
+  q[m] = sqrtf(r > 0.0f ? r : 0.0f);
+  *t = ((float)qlogit[s] / 255.0f) * 16.0f - 8.0f;
+}
+
+/* Chunk visibility (a reading of the hierarchy's view test): a chunk is kept unless its box of
+ * centres, grown by 6 times its largest scale, lies entirely at camera depth <= near_z / 2, or is
+ * entirely in front of the camera and projects entirely beyond one image side by more than
+ * 64 pixels. Corners are projected in float with a fixed operation order. */
+int or_chunk_visible(const float* e, const or_camera* cam) {
+  float g = 6.0f * e[6];
+  const float* R = cam->R;
+  int behind = 1, front = 1, left = 1, right = 1, top = 1, bottom = 1;
+  float W = (float)cam->width, H = (float)cam->height;
+  for (int k = 0; k < 8; k++) {
+    float c[3];
+    for (int a = 0; a < 3; a++) c[a] = ((k >> a) & 1) ? e[3 + a] + g : e[a] - g;
+    float x = ((R[0] * c[0] + R[1] * c[1]) + R[2] * c[2]) + cam->t[0];
+    float y = ((R[3] * c[0] + R[4] * c[1]) + R[5] * c[2]) + cam->t[1];
+    float z = ((R[6] * c[0] + R[7] * c[1]) + R[8] * c[2]) + cam->t[2];
+    if (z > 0.5f * cam->near_z) behind = 0;
+    if (!(z > 0.5f * cam->near_z)) { front = 0; continue; }
+    float u = cam->fx * (x / z) + cam->cx, v = cam->fy * (y / z) + cam->cy;
+    if (!(u < -64.0f)) left = 0;
+    if (!(u > W + 64.0f)) right = 0;
+    if (!(v < -64.0f)) top = 0;
+    if (!(v > H + 64.0f)) bottom = 0;
+  }
+  if (behind) return 0;
+  if (front && (left || right || top || bottom)) return 0;
+  return 1;
+}

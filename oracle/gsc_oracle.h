@@ -99,6 +99,18 @@ int or_render(int64_t n, const float* pos, const float* scale, const float* rot,
               const double* colour /*[n][3]*/, const or_camera* cam, const int32_t* tiles, int64_t n_tiles,
               double* image /*[H][W][3]*/, double* trans /*[H][W] or NULL*/, double* abs_sum /*or NULL*/);
 
+/* Geometry streams and chunk hierarchy (Sec. IV-A); 17 bytes per slot. */
+int64_t or_chunks(int64_t n_slots, int64_t chunk_slots);
+void or_chunk_table(const float* pos, const float* scale, const int32_t* perm, int64_t n_slots, int64_t chunk_slots,
+                    float* chunk /*[n_chunks][8]*/);
+void or_geometry_encode(const float* pos, const float* scale, const float* rot, const float* logit,
+                        const int32_t* perm, int64_t n_slots, int64_t chunk_slots, const float* chunk,
+                        uint16_t* qpos, uint16_t* qscale, uint32_t* qrot, uint8_t* qlogit);
+void or_geometry_decode_slot(const uint16_t* qpos, const uint16_t* qscale, const uint32_t* qrot, const uint8_t* qlogit,
+                             int64_t s, int64_t chunk_slots, const float* chunk, float* p, float* sc, float* q,
+                             float* t);
+int or_chunk_visible(const float* chunk_entry, const or_camera* cam);
+
 void or_sh_basis(double x, double y, double z, double* Y /*[16]*/);
 void or_eval_sh(const uint8_t* texels, int64_t n, const float* scales, const float* pos,
                 const float* dirs, const float* cams, int V, double* out /*[V][n][3]*/,

@@ -96,6 +96,11 @@ def lib():
                 "or_camera_centre": (None, [P, P]),
                 "or_splat_setup": (i32, [P, P, P, P, P]),
                 "or_render": (i32, [i64, P, P, P, P, P, P, P, i64, P, P, P]),
+                "or_chunks": (i64, [i64, i64]),
+                "or_chunk_table": (None, [P, P, P, i64, i64, P]),
+                "or_geometry_encode": (None, [P, P, P, P, P, i64, i64, P, P, P, P, P]),
+                "or_geometry_decode_slot": (None, [P, P, P, P, i64, i64, P, P, P, P, P]),
+                "or_chunk_visible": (i32, [P, P]),
                 "or_sh_basis": (None, [C.c_double, C.c_double, C.c_double, P]),
                 "or_eval_sh": (None, [P, i64, P, P, P, P, i32, P, P]),
             }
@@ -434,6 +439,39 @@ def render(pos, scale, rot, logit, colour, cam, tiles=None, want_abs=False):
     if rc != 0:
         raise ValueError("or_render failed: %d" % rc)
     return (img, tr, ab) if want_abs else (img, tr)
+
+
+# --- geometry streams and chunk hierarchy (Sec. IV-A) ---------------------------------------
+def geometry_encode(pos, scale, rot, logit, perm, chunk_slots=4096):
+    """Fixed-rate geometry codes in slot order and the chunk table."""
+    pos, scale, rot = _c(pos, np.float32), _c(scale, np.float32), _c(rot, np.float32)
+    logit, perm = _c(logit, np.float32), _c(perm, np.int32)
+    ns = perm.shape[0]
+    nc = lib().or_chunks(ns, chunk_slots)
+    chunk = np.zeros((nc, 8), np.float32)
+    lib().or_chunk_table(_p(pos), _p(scale), _p(perm), ns, chunk_slots, _p(chunk))
+    qpos = np.zeros((ns, 3), np.uint16)
+    qscale = np.zeros((ns, 3), np.uint16)
+    qrot = np.zeros(ns, np.uint32)
+    qlogit = np.zeros(ns, np.uint8)
+    lib().or_geometry_encode(_p(pos), _p(scale), _p(rot), _p(logit), _p(perm), ns, chunk_slots, _p(chunk), _p(qpos),
+                             _p(qscale), _p(qrot), _p(qlogit))
+    return dict(qpos=qpos, qscale=qscale, qrot=qrot, qlogit=qlogit, chunk=chunk, chunk_slots=chunk_slots)
+
+
+def geometry_decode(g):
+    """Decoded (position, scale, quaternion, logit) of every slot, in slot order (float32)."""
+    ns = g["qrot"].shape[0]
+    P_, S_, Q_, T_ = (np.zeros((ns, 3), np.float32), np.zeros((ns, 3), np.float32), np.zeros((ns, 4), np.float32),
+                      np.zeros(ns, np.float32))
+    for s in range(ns):
+        lib().or_geometry_decode_slot(_p(g["qpos"]), _p(g["qscale"]), _p(g["qrot"]), _p(g["qlogit"]), s,
+                                      g["chunk_slots"], _p(g["chunk"]), _p(P_[s]), _p(S_[s]), _p(Q_[s]), _p(T_[s:s + 1]))
+    return P_, S_, Q_, T_
+
+
+def chunk_visible(entry, cam):
+    return bool(lib().or_chunk_visible(_p(_c(entry, np.float32)), C.byref(camera(cam))))
 
 
 # --- SH evaluation (Sec. II) --------------------------------------------------------------
