@@ -1360,7 +1360,8 @@ static uint32_t quant_unit(float t, float levels) { /* round(t * levels), t clam
 
 int64_t or_chunks(int64_t n_slots, int64_t chunk_slots) { return (n_slots + chunk_slots - 1) / chunk_slots; }
 
-/* chunk[c] = lo[3], hi[3] (bounds of the chunk's centres), largest decoded scale, 0 */
+/* chunk[c] = lo[3], hi[3] (bounds of the chunk's centres), largest decoded scale, 0; a chunk of
+ * padding slots only is all zero */
 void or_chunk_table(const float* pos, const float* scale, const int32_t* perm, int64_t n_slots, int64_t chunk_slots,
                     float* chunk) {
   int64_t nc = or_chunks(n_slots, chunk_slots);
@@ -1373,12 +1374,12 @@ void or_chunk_table(const float* pos, const float* scale, const int32_t* perm, i
       if (o < 0) continue;
       for (int a = 0; a < 3; a++) {
         float p = pos[3 * (int64_t)o + a];
+        float sv = bf16_val(bf16_rne(scale[3 * (int64_t)o + a]));
         if (!any || p < e[a]) e[a] = p;
         if (!any || p > e[3 + a]) e[3 + a] = p;
-        float sv = bf16_val(bf16_rne(scale[3 * (int64_t)o + a]));
-        if (!any || sv > e[6]) e[6] = sv;
-        if (a == 2) any = 1;
+        if ((!any && a == 0) || sv > e[6]) e[6] = sv;
       }
+      any = 1;
     }
   }
 }

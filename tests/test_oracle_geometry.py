@@ -82,6 +82,7 @@ def test_rotation_smallest_three(O):
 
 def test_chunk_table_and_byte_count(O):
     sc, geo, perm = _scene(n=1000)
+    geo.scale[perm[0]] = [0.001, 0.5, 0.002]          # the chunk's first Gaussian holds its largest scale
     g = O.geometry_encode(sc.pos, geo.scale, geo.rot, geo.logit, perm, 256)
     _, Sc, _, _ = O.geometry_decode(g)
     for c in range(g["chunk"].shape[0]):
