@@ -632,6 +632,52 @@ def run_render(args, world, rank, local):
               "blend_kernel_ms": round(blend_ms, 3), "pairs_per_frame": int(sum(pairs) // V),
               "frames_per_s": round(V / (ms_step * 1e-3), 1)}
 
+    # the fully coded scene: geometry streams (17 B per slot) and chunks of 4096 slots culled by the
+    # view test; the same cameras, and a close view of one corner that keeps part of the scene
+    chunk_slots = 4096
+    perm2, scales2 = gsc.gsc_plan_reorder(ctx, pos, sh, group_size=chunk_slots, stream=stream)
+    blk2, po2, tab2 = gsc.gsc_encode(ctx, sh, perm2, scales2, gsc.FMT_BC7, stream=stream)
+    geom = gsc.gsc_geometry_encode(ctx, pos, scale, rot, logit, po2, chunk_slots, stream=stream)
+    close = S.look_at([0.3, 0.3, 0.3], [0.9, 0.9, 0.6], W, H, fov_x_deg=50.0)
+
+    def coded_ms(cam_list, reps):
+        kept = 0
+        for cam in cam_list:
+            r.render_coded(tab2, blk2, po2, geom, chunk_slots, cam, image=imgs[0], stream=stream)
+        stream.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            for cam in cam_list:
+                _, _, _, kept = r.render_coded(tab2, blk2, po2, geom, chunk_slots, cam, image=imgs[0], stream=stream)
+        b.record(stream)
+        stream.synchronize()
+        return a.elapsed_time(b) / (reps * len(cam_list)), kept
+
+    def float_ms(cam_list, reps):
+        for cam in cam_list:
+            r.render(tab2, blk2, po2, pos, scale, rot, logit, cam, image=imgs[0], stream=stream)
+        stream.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            for cam in cam_list:
+                r.render(tab2, blk2, po2, pos, scale, rot, logit, cam, image=imgs[0], stream=stream)
+        b.record(stream)
+        stream.synchronize()
+        return a.elapsed_time(b) / (reps * len(cam_list))
+
+    n_chunks = (po2.shape[0] + chunk_slots - 1) // chunk_slots
+    ms_c, kept_all = coded_ms(cams, max(2, args.steps))
+    ms_cc, kept_close = coded_ms([close], max(2, args.steps))
+    ms_fc = float_ms([close], max(2, args.steps))
+    stages["coded"] = {"frame_ms": round(ms_c, 3), "geometry_bytes_per_gaussian": 17,
+                       "colour_bytes_per_gaussian": 16, "chunks": int(n_chunks), "kept_chunks_last_view": int(kept_all),
+                       "close_view_frame_ms": round(ms_cc, 3), "close_view_kept_chunks": int(kept_close),
+                       "close_view_float_geometry_frame_ms": round(ms_fc, 3)}
+
     # end to end: the coded scene and the geometry from pinned host memory, the frames back to the host
     hosts = [t.cpu().pin_memory() for t in (blk, po, pos, scale, rot, logit)]
     devs = [torch.empty_like(h, device=dev) for h in hosts]

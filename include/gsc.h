@@ -261,6 +261,41 @@ gsc_status gsc_render(gsc_ctx* ctx, const gsc_stream_table* table, const uint8_t
                       const gsc_camera* cam, float* d_image, float* d_trans, int64_t* h_pairs, void* d_ws,
                       size_t ws_bytes, void* stream);
 
+/* Geometry streams and chunk hierarchy (Sec. IV-A: position and shape are coded apart from
+ * appearance, each parameter quantised to a fixed number of bits in its own bitstream; a
+ * hierarchy lets a view use only the primitives of the part it sees). In slot order (the
+ * positions move with the Gaussians, so no index is stored), 17 bytes per slot: position 3 x 16
+ * bits over the box of its chunk (chunk_slots consecutive slots, a multiple of 16), scale 3 x
+ * bfloat16 (round to nearest even), rotation as the smallest three of the unit quaternion (2-bit
+ * index of the largest component, made non-negative; three 10-bit codes of 1022 steps over
+ * [-1/sqrt2, 1/sqrt2]), opacity logit 8 bits over [-8, 8]. Per chunk a gsc_chunk: the box of its
+ * centres and its largest decoded scale (a chunk of padding only is zero). Decoding: position
+ * lo + (code / 65535) (hi - lo), rotation component (code / 1022 - 1/2) sqrt2 and the largest
+ * sqrt(1 - sum of the other squares), logit (code / 255) 16 - 8. One buffer holds the streams at
+ * 256-byte aligned offsets: qpos u16 [n_slots][3], qscale u16 [n_slots][3], qrot u32 [n_slots],
+ * qlogit u8 [n_slots], chunks [n_chunks]. */
+typedef struct {
+  float lo[3], hi[3];
+  float max_scale;
+  float pad;
+} gsc_chunk;
+size_t gsc_geometry_bytes(int64_t n_slots, int64_t chunk_slots);
+/* Codes the geometry of a planned scene (d_perm [n_slots], n_slots a multiple of 16; geometry in
+ * original order as gsc_render takes it) into d_geom (256-byte aligned, gsc_geometry_bytes). */
+gsc_status gsc_geometry_encode(gsc_ctx* ctx, const float* d_pos, const float* d_scale, const float* d_rot,
+                               const float* d_logit, const int32_t* d_perm, int64_t n_slots, int64_t chunk_slots,
+                               uint8_t* d_geom, void* stream);
+/* gsc_render from a fully coded scene: colour from the blocks, geometry from d_geom. Chunks are
+ * culled first (kept unless the box of their centres, grown by 6 times their largest scale, lies
+ * entirely at camera depth <= near_z / 2, or entirely in front of the camera and more than 64
+ * pixels beyond one image side, corners projected in float in a fixed order), and only the kept
+ * chunks' groups are decoded and splatted; *h_chunks (if not NULL) receives the kept count. The
+ * image equals gsc_render's of the decoded geometry restricted to the kept chunks. */
+gsc_status gsc_render_coded(gsc_ctx* ctx, const gsc_stream_table* table, const uint8_t* d_blocks,
+                            const int32_t* d_perm, const uint8_t* d_geom, int64_t chunk_slots, const gsc_camera* cam,
+                            float* d_image, float* d_trans, int64_t* h_pairs, int64_t* h_chunks, void* d_ws,
+                            size_t ws_bytes, void* stream);
+
 /* Batched form: many scenes of uneven sizes (the paper codes one scene at a time; this packages
  * the same steps for throughput). Per scene the results equal the single-scene calls bit for bit:
  * the plan of gsc_plan_reorder (quantile 995), then the blocks, slot order and stream table of

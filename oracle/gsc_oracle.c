@@ -1477,3 +1477,11 @@ int or_chunk_visible(const float* e, const or_camera* cam) {
   if (front && (left || right || top || bottom)) return 0;
   return 1;
 }
+
+/* Every slot's decoded geometry (or_geometry_decode_slot for s = 0 .. n_slots - 1). */
+void or_geometry_decode_all(const uint16_t* qpos, const uint16_t* qscale, const uint32_t* qrot, const uint8_t* qlogit,
+                            int64_t n_slots, int64_t chunk_slots, const float* chunk, float* p, float* sc, float* q,
+                            float* t) {
+  for (int64_t s = 0; s < n_slots; s++)
+    or_geometry_decode_slot(qpos, qscale, qrot, qlogit, s, chunk_slots, chunk, p + 3 * s, sc + 3 * s, q + 4 * s, t + s);
+}

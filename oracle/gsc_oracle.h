@@ -109,6 +109,9 @@ void or_geometry_encode(const float* pos, const float* scale, const float* rot, 
 void or_geometry_decode_slot(const uint16_t* qpos, const uint16_t* qscale, const uint32_t* qrot, const uint8_t* qlogit,
                              int64_t s, int64_t chunk_slots, const float* chunk, float* p, float* sc, float* q,
                              float* t);
+void or_geometry_decode_all(const uint16_t* qpos, const uint16_t* qscale, const uint32_t* qrot, const uint8_t* qlogit,
+                            int64_t n_slots, int64_t chunk_slots, const float* chunk, float* p, float* sc, float* q,
+                            float* t);
 int or_chunk_visible(const float* chunk_entry, const or_camera* cam);
 
 void or_sh_basis(double x, double y, double z, double* Y /*[16]*/);

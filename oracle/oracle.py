@@ -101,6 +101,7 @@ def lib():
                 "or_geometry_encode": (None, [P, P, P, P, P, i64, i64, P, P, P, P, P]),
                 "or_geometry_decode_slot": (None, [P, P, P, P, i64, i64, P, P, P, P, P]),
                 "or_chunk_visible": (i32, [P, P]),
+                "or_geometry_decode_all": (None, [P, P, P, P, i64, i64, P, P, P, P, P]),
                 "or_sh_basis": (None, [C.c_double, C.c_double, C.c_double, P]),
                 "or_eval_sh": (None, [P, i64, P, P, P, P, i32, P, P]),
             }
@@ -464,9 +465,10 @@ def geometry_decode(g):
     ns = g["qrot"].shape[0]
     P_, S_, Q_, T_ = (np.zeros((ns, 3), np.float32), np.zeros((ns, 3), np.float32), np.zeros((ns, 4), np.float32),
                       np.zeros(ns, np.float32))
-    for s in range(ns):
-        lib().or_geometry_decode_slot(_p(g["qpos"]), _p(g["qscale"]), _p(g["qrot"]), _p(g["qlogit"]), s,
-                                      g["chunk_slots"], _p(g["chunk"]), _p(P_[s]), _p(S_[s]), _p(Q_[s]), _p(T_[s:s + 1]))
+    q = [_c(g[k], t) for k, t in (("qpos", np.uint16), ("qscale", np.uint16), ("qrot", np.uint32),
+                                   ("qlogit", np.uint8))]
+    lib().or_geometry_decode_all(_p(q[0]), _p(q[1]), _p(q[2]), _p(q[3]), ns, g["chunk_slots"],
+                                 _p(_c(g["chunk"], np.float32)), _p(P_), _p(S_), _p(Q_), _p(T_))
     return P_, S_, Q_, T_
 
 

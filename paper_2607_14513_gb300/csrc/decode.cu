@@ -612,11 +612,14 @@ __device__ __forceinline__ void load_views(float (*s_view)[64], float* s_deq, co
 #ifndef EVAL_MIN_BLOCKS
 #define EVAL_MIN_BLOCKS 1
 #endif
-template <int KIND, bool CAMS, int VF, int LAYOUT>
+// LIST: only the groups listed in glist[0, n_list) (-1 entries skipped), e.g. those of the chunks a
+// view keeps.
+template <int KIND, bool CAMS, int VF, int LAYOUT, bool LIST>
 __global__ void __launch_bounds__(EVAL_THREADS, EVAL_MIN_BLOCKS) k_eval2(DevTable T, const uint8_t* __restrict__ blocks,
                                                const int32_t* __restrict__ perm, const float* __restrict__ dirs,
                                                const float* __restrict__ pos, const float* __restrict__ cams, int V,
-                                               int out_order, float* __restrict__ rgb) {
+                                               int out_order, float* __restrict__ rgb,
+                                               const int32_t* __restrict__ glist, int64_t n_list) {
   __shared__ DecTables S;
   __shared__ uint32_t tile[EVAL_THREADS / 32][WTILE];
   __shared__ uint4 s_ep[EVAL_THREADS][3];
@@ -626,15 +629,21 @@ __global__ void __launch_bounds__(EVAL_THREADS, EVAL_MIN_BLOCKS) k_eval2(DevTabl
   load_views(s_view, s_deq, dirs, cams, V, T);
   __syncthreads();
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, gw = l >> 4, kt = l & 15, nw = blockDim.x >> 5;
-  const int64_t npairs = ((int64_t)T.n_groups + 1) / 2;
+  const int64_t npairs = ((LIST ? n_list : (int64_t)T.n_groups) + 1) / 2;
   const int64_t n = T.n, ns = (int64_t)T.n_groups * 16;
   uint32_t* my = tile[w] + gw * 272;
   const int64_t step = (int64_t)gridDim.x * nw;
   // software pipeline: slot order entries two iterations ahead, blocks and positions one ahead
-  auto group_of = [&](int64_t pr) { return pr * 2 + gw; };
+  auto group_of = [&](int64_t pr) -> int64_t {
+    if (!LIST) return pr * 2 + gw;
+    const int64_t i = pr * 2 + gw;
+    return i < n_list ? (int64_t)__ldg(glist + i) : -1;
+  };
+  auto valid = [&](int64_t g) { return LIST ? g >= 0 : g < T.n_groups; };
   auto perm_at = [&](int64_t pr) -> int32_t {
+    if (pr >= npairs) return -1;
     const int64_t g = group_of(pr);
-    return (pr < npairs && g < T.n_groups) ? checked_slot(__ldg(perm + g * 16 + kt), T.n, g * 16 + kt) : -1;
+    return valid(g) ? checked_slot(__ldg(perm + g * 16 + kt), T.n, g * 16 + kt) : -1;
   };
   auto pos_at = [&](int32_t o) -> float3 {
     if (!CAMS || o < 0) return make_float3(0.f, 0.f, 0.f);
@@ -644,18 +653,18 @@ __global__ void __launch_bounds__(EVAL_THREADS, EVAL_MIN_BLOCKS) k_eval2(DevTabl
   RawBlock raw;
   raw.kind = 0;
   raw.w = make_uint4(0u, 0u, 0u, 0u);
-  if (pr < npairs && group_of(pr) < T.n_groups) raw = fetch_block<KIND>(T, blocks, group_of(pr), kt);
+  if (pr < npairs && valid(group_of(pr))) raw = fetch_block<KIND>(T, blocks, group_of(pr), kt);
   int32_t o = perm_at(pr), o1 = perm_at(pr + step);
   float3 p = pos_at(o);
   for (; pr < npairs; pr += step) {
     const int64_t g = group_of(pr);
-    const bool live = g < T.n_groups;
+    const bool live = valid(g);
     // loads for the next iterations
     const int64_t prn = pr + step;
     RawBlock rawn;
     rawn.kind = 0;
     rawn.w = make_uint4(0u, 0u, 0u, 0u);
-    if (prn < npairs && group_of(prn) < T.n_groups) rawn = fetch_block<KIND>(T, blocks, group_of(prn), kt);
+    if (prn < npairs && valid(group_of(prn))) rawn = fetch_block<KIND>(T, blocks, group_of(prn), kt);
     const float3 pn = pos_at(o1);
     const int32_t o2 = perm_at(prn + step);
     {
@@ -726,16 +735,21 @@ cudaError_t launch_decode(const DevTable& T, const uint8_t* blocks, const int32_
 
 cudaError_t launch_decode_eval(const DevTable& T, const uint8_t* blocks, const int32_t* perm, const float* dirs,
                                const float* pos, const float* cams, int V, int out_order, float* rgb, int sm_count,
-                               cudaStream_t st) {
-  if (T.n_groups == 0) return cudaSuccess;
-  const int grid = eval_grid(T.n_groups, sm_count, EVAL_THREADS / 32);
+                               cudaStream_t st, const int32_t* glist, int64_t n_list) {
+  if (T.n_groups == 0 || (glist && n_list == 0)) return cudaSuccess;
+  const int grid = eval_grid(glist ? n_list : T.n_groups, sm_count, EVAL_THREADS / 32);
   const int kind = kind_of(T);
   // runtime view count only: a compile-time 8-view form raised this kernel to 140 registers (one
   // resident CTA fewer) and measured no faster (the texture kernel does use one)
 #define EVAL_LAUNCH(K, C, L)                                                                                     \
   do {                                                                                                           \
     gsc_count_launch();                                                                                          \
-    k_eval2<K, C, 0, L><<<grid, EVAL_THREADS, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order, rgb);     \
+    if (glist)                                                                                                   \
+      k_eval2<K, C, 0, L, true><<<grid, EVAL_THREADS, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order,   \
+                                                               rgb, glist, n_list);                              \
+    else                                                                                                         \
+      k_eval2<K, C, 0, L, false><<<grid, EVAL_THREADS, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order,  \
+                                                                rgb, nullptr, 0);                                \
   } while (0)
 #define EVAL_KINDS(C, L)                                                                                         \
   do {                                                                                                           \

@@ -178,9 +178,10 @@ void host_weights(const float* scales, uint32_t* w);
 gsc_status make_dev_table(const gsc_stream_table* t, DevTable* d);
 cudaError_t launch_decode(const DevTable& t, const uint8_t* blocks, const int32_t* perm, uint8_t* texels,
                           cudaStream_t st);
+// glist (optional): evaluate only the groups glist[0, n_list) (-1 entries skipped)
 cudaError_t launch_decode_eval(const DevTable& t, const uint8_t* blocks, const int32_t* perm, const float* dirs,
                                const float* pos, const float* cams, int V, int out_order, float* rgb, int sm_count,
-                               cudaStream_t st);
+                               cudaStream_t st, const int32_t* glist = nullptr, int64_t n_list = 0);
 cudaError_t launch_decode_blocks(const uint8_t* blocks, int64_t nblk, int format, uint8_t* rgba, cudaStream_t st);
 gsc_status decode_tex_run(gsc_ctx* ctx, const DevTable& t, const uint8_t* blocks, const int32_t* perm,
                           uint8_t* texels, cudaStream_t st);

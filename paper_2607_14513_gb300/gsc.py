@@ -142,6 +142,10 @@ _SIGS = {
     "gsc_tex_scene_destroy": [_P],
     "gsc_decode_eval_sh_tex": [_P, _P, _P, _P, _P, _P, C.c_int32, C.c_int32, _P, _P],
     "gsc_render_workspace_bytes": [C.c_int64, C.POINTER(Camera), C.c_int64],
+    "gsc_geometry_bytes": [C.c_int64, C.c_int64],
+    "gsc_geometry_encode": [_P, _P, _P, _P, _P, _P, C.c_int64, C.c_int64, _P, _P],
+    "gsc_render_coded": [_P, C.POINTER(StreamTable), _P, _P, _P, C.c_int64, C.POINTER(Camera), _P, _P,
+                         C.POINTER(C.c_int64), C.POINTER(C.c_int64), _P, C.c_size_t, _P],
     "gsc_render": [_P, C.POINTER(StreamTable), _P, _P, _P, _P, _P, _P, C.POINTER(Camera), _P, _P,
                    C.POINTER(C.c_int64), _P, C.c_size_t, _P],
     "gsc_encode_blocks": [_P, _P, C.c_int64, C.c_int32, _P, _P, _P],
@@ -203,6 +207,7 @@ def load(path: str | None = None):
             lib.gsc_launch_count.restype = C.c_uint64
             lib.gsc_batch_workspace_bytes.restype = C.c_size_t
             lib.gsc_render_workspace_bytes.restype = C.c_size_t
+            lib.gsc_geometry_bytes.restype = C.c_size_t
             _lib = lib
     return _lib
 
@@ -404,6 +409,29 @@ def gsc_decode_eval_sh_tex(ctx, scene, perm, dirs=None, pos=None, cams=None, out
     return rgb
 
 
+def geometry_layout(n_slots, chunk_slots):
+    """Byte offsets of (qpos, qscale, qrot, qlogit, chunks) in a geometry buffer and its size, as
+    include/gsc.h lays them out (each 256-byte aligned)."""
+    al = lambda v: (v + 255) // 256 * 256
+    nc = (n_slots + chunk_slots - 1) // chunk_slots
+    off, b = [], 0
+    for size in (6 * n_slots, 6 * n_slots, 4 * n_slots, n_slots, 32 * max(nc, 1)):
+        off.append(b)
+        b = al(b + size)
+    return off, b
+
+
+def gsc_geometry_encode(ctx, pos, scale, rot, logit, perm, chunk_slots=4096, out=None, stream=None):
+    """-> uint8 device buffer with the geometry streams of the planned slot order `perm`."""
+    import torch
+    ns = perm.shape[0]
+    nb = ctx.lib.gsc_geometry_bytes(ns, chunk_slots)
+    geom = out if out is not None else torch.empty(max(nb, 256), dtype=torch.uint8, device=perm.device)
+    _check(ctx.lib.gsc_geometry_encode(ctx.h, _ptr(pos), _ptr(scale), _ptr(rot), _ptr(logit), _ptr(perm), ns,
+                                       chunk_slots, _ptr(geom), _stream(stream)), "gsc_geometry_encode")
+    return geom
+
+
 class Renderer:
     """gsc_render with a workspace that grows to the (Gaussian, tile) overlap count it needs."""
 
@@ -433,6 +461,29 @@ class Renderer:
             _check(code, "gsc_render")
             return img, trans, pairs.value
         raise GscError(3, "gsc_render")
+
+    def render_coded(self, table, blocks, perm, geom, chunk_slots, cam, image=None, trans=None, stream=None):
+        """gsc_render_coded -> (image, transmittance or None, overlap count, kept chunks)."""
+        import torch
+        c = camera(cam)
+        dev = perm.device
+        img = image if image is not None else torch.empty((c.height, c.width, 3), dtype=torch.float32, device=dev)
+        pairs, chunks = C.c_int64(0), C.c_int64(0)
+        n = table.n
+        for _ in range(2):
+            if self.ws is None:
+                nb = self.ctx.lib.gsc_render_workspace_bytes(n, C.byref(c), max(16 * n, 1 << 16))
+                self.ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+            code = self.ctx.lib.gsc_render_coded(self.ctx.h, C.byref(table), _ptr(blocks), _ptr(perm), _ptr(geom),
+                                                 chunk_slots, C.byref(c), _ptr(img), _ptr(trans), C.byref(pairs),
+                                                 C.byref(chunks), _ptr(self.ws), self.ws.numel(), _stream(stream))
+            if code == 3 and pairs.value > 0:
+                nb = self.ctx.lib.gsc_render_workspace_bytes(n, C.byref(c), int(pairs.value * 5 // 4))
+                self.ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+                continue
+            _check(code, "gsc_render_coded")
+            return img, trans, pairs.value, chunks.value
+        raise GscError(3, "gsc_render_coded")
 
 
 def gsc_encode_blocks(ctx, tex, fmt, stream=None):
