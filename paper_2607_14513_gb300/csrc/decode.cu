@@ -205,15 +205,6 @@ __device__ __forceinline__ int tile_at(int u, int c) {
   return 17 * k + t;
 }
 
-__device__ __forceinline__ uint32_t decode_at(const uint8_t* __restrict__ blocks, const BlockLoc& L, int t) {
-  if (L.kind == 0) return 0x80808080u | 0xFF000000u;
-  const uint2* p = reinterpret_cast<const uint2*>(blocks + L.off);
-  uint2 w0 = __ldg(p);
-  if (L.kind == 1) return bc1_texel(w0, t);
-  uint2 w1 = __ldg(p + 1);
-  return bc7_texel(((uint64_t)w0.y << 32) | w0.x, ((uint64_t)w1.y << 32) | w1.x, t);
-}
-
 #define SH_C0 0.28209479177387814f   /* sqrt(1/(4 pi)) */
 #define SH_C1 0.4886025119029199f    /* sqrt(3/(4 pi)) */
 #define SH_C2A 1.0925484305920792f   /* sqrt(15/(4 pi)) */
@@ -449,11 +440,6 @@ __device__ __forceinline__ void block_texels(const DevTable& T, const uint8_t* _
   }
 }
 
-__device__ __forceinline__ int table_kind(const DevTable& T) {
-  if (T.n_streams == 1 && T.bands[0] == 16 && T.bc7[0] == 16 && T.byte_offset[0] == 0) return 7;
-  if (T.n_streams == 1 && T.bands[0] == 16 && T.bc7[0] == 0 && T.byte_offset[0] == 0) return 1;
-  return 0;
-}
 
 // 2^23 + q as float for byte c of v (0x4B0000qq)
 __device__ __forceinline__ float u23(uint32_t v, int c) {
