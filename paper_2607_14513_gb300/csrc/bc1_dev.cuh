@@ -130,12 +130,13 @@ __device__ __forceinline__ Bc1Res bc1_encode(const uint32_t (&tx)[16]) {
     Bc1Res r = bc1_eval(tx, pack565(e0[0], e0[1], e0[2]), pack565(e1[0], e1[1], e1[2]));
     if (r.sse < best.sse) best = r; else break;
   }
-  // +-1 neighbourhood, order: endpoint (c0, c1) x channel (R, G, B) x step (+1, -1)
+  // +-1 neighbourhood, order: endpoint (c0, c1) x channel (R, G, B) x step (+1, -1); one copy of
+  // the candidate evaluation in a rolled loop keeps the code small enough for the instruction cache
   for (int round = 0; round < 4; round++) {
     Bc1Res nb;
     nb.sse = 0xFFFFFFFFu;
     bool found = false;
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < 12; q++) {
       const int ep = q / 6, c = (q / 2) % 3, sgn = q & 1;
       const int shift = c == 0 ? 11 : (c == 1 ? 5 : 0), mask = c == 1 ? 63 : 31;
