@@ -574,7 +574,8 @@ __device__ __noinline__ uint4 solve_pack(const uint32_t* tx, int e, const uint16
 #ifndef BC7_SUBS
 #define BC7_SUBS 5
 #endif
-// the persistent multi-scene kernel keeps 128-thread CTAs, 5 per SM
+// the multi-scene BC1 kernel keeps 128-thread CTAs, 5 per SM (and the default CTAs per SM of the
+// multi-scene launches)
 #define BC7_MIN_BLOCKS 5
 #define BC7_THREADS (BC7_SUBS * STAGE_THREADS)
 #define BC7_DYN_SMEM (BC7_SUBS * 16 * STAGE_STRIDE * 4)
