@@ -320,10 +320,11 @@ typedef struct {
 } gsc_batch_scene;
 
 /* How the encode launch hands out work: schedule 0 = static round robin over tiles, 1 = atomic
- * work queue, 2 = atomic queue, 3 = one CTA per tile; schedules other than 1 list the scenes by
- * decreasing cost. CTAs per SM 1..32 (schedules 0-2; above the 5 that fit, the grid is
- * oversubscribed and the hardware block scheduler balances); groups per BC1 tile (multiple of
- * 8; BC7 tiles are 8 groups). The plans of the scenes run on 4 streams at once. */
+ * work queue, 2 = atomic queue, 3 = one CTA unit per tile; schedules other than 1 list the scenes
+ * by decreasing cost. CTAs per SM 1..32 (schedules 0-2; a BC1 CTA is 128 threads, 5 fit per SM; a
+ * BC7 CTA is five 128-thread units that claim their own tiles, 1 fits per SM; above what fits the
+ * grid is oversubscribed and the hardware block scheduler balances); groups per BC1 tile (multiple
+ * of 8; BC7 tiles are 8 groups). The plans of the scenes run on 4 streams at once. */
 typedef struct {
   int32_t schedule;
   int32_t ctas_per_sm;
