@@ -151,11 +151,10 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
 #pragma unroll
   for (int i = 0; i < NCH; i++) { lo[i] = 255; hi[i] = 0; s1[i] = 0; }
   s2[0] = s2[1] = s2[2] = 0;  // channel pairs (0,1), (0,2), (1,2) of the coded channels
-  // member texels only, in increasing order (the mask is the same for every lane)
+  // member texels only (the mask is the same for every lane); box and sums are order-free, so
+  // two texels per step: both shared-memory reads are in flight together
   const uint32_t mm = member_mask(part, s);
-  for (uint32_t m = mm; m; m &= m - 1) {
-    const int t = (__ffs(m) - 1) >> 1;
-    const uint32_t v = __byte_perm(tex[t * STAGE_STRIDE], 0u, sel);
+  auto box = [&](uint32_t v) {
     n++;
     int c[NCH];
 #pragma unroll
@@ -165,6 +164,20 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
     }
     if (NCH >= 2) s2[0] += c[0] * c[NCH >= 2 ? 1 : 0];
     if (NCH >= 3) { s2[1] += c[0] * c[NCH >= 3 ? 2 : 0]; s2[2] += c[NCH >= 2 ? 1 : 0] * c[NCH >= 3 ? 2 : 0]; }
+  };
+  for (uint32_t m = mm; m;) {
+    const int ta = (__ffs(m) - 1) >> 1;
+    m &= m - 1;
+    const uint32_t va = __byte_perm(tex[ta * STAGE_STRIDE], 0u, sel);
+    if (m) {
+      const int tb = (__ffs(m) - 1) >> 1;
+      m &= m - 1;
+      const uint32_t vb = __byte_perm(tex[tb * STAGE_STRIDE], 0u, sel);
+      box(va);
+      box(vb);
+    } else {
+      box(va);
+    }
   }
   if (n == 0) return 0;
   // reference channel = widest range (first on ties); selects, not indexing, keep the
