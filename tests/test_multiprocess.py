@@ -90,4 +90,7 @@ def test_reference_arm_prints_once_under_two_ranks():
     d = json.loads(lines0[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+    # the same workload config as the GPU arm prints for this workload
+    import bench
+    assert d["config"] == bench.scene_config(bench.workload_cfg("tiny4k"), 2)
     assert outs[1][0].strip() == ""
