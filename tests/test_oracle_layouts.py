@@ -1,8 +1,8 @@
 """Pins of the oracle's block layouts A and B (Sec. IV-B, Figs. SetupA and SetupB, Table I).
 
 Fig. SetupA moves the 16 RGB vectors of one Gaussian into one 4x4 block; Fig. SetupB moves the
-64 RGB vectors of four Gaussians into four blocks, and Table I codes "the 4 first SH
-coefficients" of that layout in BC7 and the rest in BC1 at 10 bytes per Gaussian. The texel
+64 RGB vectors of four Gaussians into four blocks, and Table I codes the first four SH
+coefficients of that layout in BC7 and the rest in BC1 at 10 bytes per Gaussian. The texel
 placement inside a block is not printed (raster order, row = Gaussian in B, is the reading).
 The pins: the captions' content per block, the byte column of Table I, lossless BC7 round trips of
 data that is constant inside every block of the layout (exactly representable, so the least-error
@@ -50,6 +50,7 @@ def test_fixed_codings_match_table_one_bytes(O):
     n = 256
     q = O.quantise(sc.sh[:n], O.scales(sc.sh[:n]))
     perm = np.arange(n, dtype=np.int32)
+    # (layout D, BC7 first: the block bytes; Table I prints one block per group more, 9)
     for lay, j, want in ((A, 0, 8.0), (A, 16, 16.0), (B, 4, 10.0), (B, 0, 8.0), (B, 16, 16.0), (D, 1, 8.5)):
         r = O.encode_layout(q, perm, O.scales(sc.sh[:n]), lay, j)
         assert r["table"].total_bytes / n == want, (lay, j)

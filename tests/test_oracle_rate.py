@@ -20,7 +20,8 @@ def test_mode_rates_match_table_one_arithmetic(O):
                                                  (9, 9), (16, 0), (16, 1), (16, 4), (16, 9), (16, 16)]
     bytes_per_gaussian = {(int(bb), int(jj)): (16 * jj + 8 * (bb - jj)) / 16 for bb, jj in zip(b, j)}
     # Table I, Setup D rows: all BC1 -> 8 B, BC7 first + BC1 rest -> 8.5 B, all BC7 -> 16 B per primitive
-    # (8 B per BC1 block, 16 B per BC7 block; the table prints 8.5 / 9 / 17, a uniform 17/16 factor)
+    # (8 B per BC1 block, 16 B per BC7 block; the table prints 8.5 / 9 / 17, one more block per group
+    # of 16 primitives in the format of the group's other blocks)
     assert bytes_per_gaussian[(16, 0)] == 8.0
     assert bytes_per_gaussian[(16, 1)] == 8.5
     assert bytes_per_gaussian[(16, 16)] == 16.0
