@@ -45,24 +45,38 @@ def test_host_side_sizes_and_strings():
 
 
 def test_struct_layouts_match_the_header(tmp_path):
-    # the binding's ctypes structures against the C compiler's view of include/gsc.h
+    # every ctypes structure of the binding against the C compiler's view of include/gsc.h: the
+    # size and the offset of every field
     import shutil
     import subprocess
     from paper_2607_14513_gb300 import gsc
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
+    pairs = [(gsc.PlanParams, "gsc_plan_params"), (gsc.EncodeParams, "gsc_encode_params"),
+             (gsc.Stream, "gsc_stream"), (gsc.StreamTable, "gsc_stream_table"), (gsc.Camera, "gsc_camera"),
+             (gsc.BatchScene, "gsc_batch_scene"), (gsc.BatchTuning, "gsc_batch_tuning"),
+             (gsc.ServerParams, "gsc_server_params"), (gsc.Request, "gsc_request"),
+             (gsc.RequestResult, "gsc_request_result"), (gsc.ServerStats, "gsc_server_stats"),
+             (gsc.SimRequest, "gsc_sim_request"), (gsc.SimResult, "gsc_sim_result")]
+    rename = {"lambda_": "lambda"}
+    lines, want = [], []
+    for py, c in pairs:
+        lines.append('  printf("%%zu\\n", sizeof(%s));' % c)
+        want.append(ctypes.sizeof(py))
+        for name, _ in py._fields_:
+            lines.append('  printf("%%zu\\n", offsetof(%s, %s));' % (c, rename.get(name, name)))
+            want.append(getattr(py, name).offset)
+    # the chunk table entry is read as eight floats per chunk (box low, box high, largest scale, pad)
+    lines.append('  printf("%zu\\n", sizeof(gsc_chunk));')
+    want.append(32)
     src = tmp_path / "abi.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gsc.h"\nint main(void) {\n'
-                   '  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(gsc_stream_table), offsetof(gsc_stream_table, layout),'
-                   ' sizeof(gsc_encode_params), offsetof(gsc_encode_params, layout),'
-                   ' offsetof(gsc_encode_params, bc7_blocks), sizeof(gsc_stream));\n  return 0;\n}\n')
+                   + "\n".join(lines) + "\n  return 0;\n}\n")
     exe = tmp_path / "abi"
     inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
     subprocess.check_call([cc, "-I", inc, str(src), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
-    want = [ctypes.sizeof(gsc.StreamTable), gsc.StreamTable.layout.offset, ctypes.sizeof(gsc.EncodeParams),
-            gsc.EncodeParams.layout.offset, gsc.EncodeParams.bc7_blocks.offset, ctypes.sizeof(gsc.Stream)]
     assert got == want
 
 
