@@ -91,3 +91,82 @@ def test_layout_workspace_sizes():
     assert lib.gsc_workspace_bytes(n, ctypes.byref(ep)) >= ng * 16 * 48 + ng * (4 * 16 + 12 * 8)
     ep = gsc.EncodeParams(gsc.FMT_BC7, 0, None, None, gsc.LAYOUT_A, 0)
     assert lib.gsc_workspace_bytes(n, ctypes.byref(ep)) >= ng * 16 * 48
+
+
+def test_constants_match_the_header(tmp_path):
+    # the binding's enum values against the header's, through the C compiler
+    import shutil
+    import subprocess
+    from paper_2607_14513_gb300 import gsc
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = {"GSC_FMT_RATE": gsc.FMT_RATE, "GSC_FMT_BC1": gsc.FMT_BC1, "GSC_FMT_MIXED": gsc.FMT_MIXED,
+             "GSC_FMT_BC7": gsc.FMT_BC7, "GSC_LAYOUT_D": gsc.LAYOUT_D, "GSC_LAYOUT_A": gsc.LAYOUT_A,
+             "GSC_LAYOUT_B": gsc.LAYOUT_B, "GSC_OUT_VIEW_MAJOR": gsc.OUT_VIEW_MAJOR,
+             "GSC_OUT_SLOT_ORDER": gsc.OUT_SLOT_ORDER, "GSC_OUT_GAUSS_MAJOR": gsc.OUT_GAUSS_MAJOR,
+             "GSC_REQ_ENCODE": gsc.REQ_ENCODE, "GSC_REQ_EVAL": gsc.REQ_EVAL, "GSC_REQ_LOAD": gsc.REQ_LOAD}
+    names.update({v: k for k, v in gsc.STATUS.items()})
+    src = tmp_path / "enums.c"
+    src.write_text('#include <stdio.h>\n#include "gsc.h"\nint main(void) {\n'
+                   + "\n".join('  printf("%%d\\n", (int)%s);' % k for k in names) + "\n  return 0;\n}\n")
+    exe = tmp_path / "enums"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.check_call([cc, "-I", inc, str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert got == list(names.values())
+
+
+def _prototypes():
+    """(name, return type, [parameter type]) of every function include/gsc.h declares."""
+    import re
+    from paper_2607_14513_gb300 import gsc
+    txt = re.sub(r"/\*.*?\*/", "", open(gsc.HEADER).read(), flags=re.S)
+    txt = re.sub(r"#[^\n]*", "", txt)
+    out = []
+    for m in re.finditer(r"([A-Za-z_][A-Za-z0-9_ ]*[ *]+)\b(gsc_[a-z0-9_]+)\s*\(([^()]*)\)\s*;", txt):
+        ret = m.group(1).strip()
+        ret = ret.split(";")[-1].split("}")[-1].strip()
+        params = [p.strip() for p in m.group(3).split(",") if p.strip()]
+        if params == ["void"]:
+            params = []
+        types = []
+        for p in params:
+            t = re.sub(r"\b[A-Za-z_][A-Za-z0-9_]*\s*$", "", p).strip()   # drop the parameter's name
+            types.append(t if t else p)
+        out.append((m.group(2), ret, types))
+    return out
+
+
+def test_binding_argument_widths_match_the_prototypes(tmp_path):
+    # every argument's size as ctypes passes it against the C type's size (a 32/64-bit mismatch
+    # shifts the arguments after it once they go on the stack), the argument counts, and the size of
+    # the return value the binding reads
+    import shutil
+    import subprocess
+    from paper_2607_14513_gb300 import gsc
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    protos = _prototypes()
+    assert {n for n, _, _ in protos} == set(gsc._SIGS)
+    lib = gsc.load()
+    lines, want, where = [], [], []
+    for name, ret, types in protos:
+        assert len(types) == len(gsc._SIGS[name]), name
+        lines.append('  printf("%%zu\\n", sizeof(%s));' % ret)
+        want.append(ctypes.sizeof(getattr(lib, name).restype))
+        where.append((name, "return", ret))
+        for i, (t, a) in enumerate(zip(types, gsc._SIGS[name])):
+            lines.append('  printf("%%zu\\n", sizeof(%s));' % t)
+            want.append(ctypes.sizeof(a))
+            where.append((name, i, t))
+    src = tmp_path / "args.c"
+    src.write_text('#include <stdio.h>\n#include "gsc.h"\nint main(void) {\n' + "\n".join(lines)
+                   + "\n  return 0;\n}\n")
+    exe = tmp_path / "args"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.check_call([cc, "-I", inc, str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    bad = [w for w, g, e in zip(where, got, want) if g != e]
+    assert not bad, bad
