@@ -244,7 +244,8 @@ typedef struct {
   float near_z;         /* > 0 */
 } gsc_camera;
 
-/* Workspace bytes of gsc_render for n Gaussians and up to max_pairs (Gaussian, tile) overlaps. */
+/* Workspace bytes of gsc_render for n Gaussians and up to max_pairs (Gaussian, tile) overlaps; 0
+ * when n or max_pairs is negative or the camera is missing or invalid. */
 size_t gsc_render_workspace_bytes(int64_t n, const gsc_camera* cam, int64_t max_pairs);
 
 /* Renders a coded scene (any layout and coding) for one camera into d_image [height][width][3]
@@ -279,6 +280,8 @@ typedef struct {
   float max_scale;
   float pad;
 } gsc_chunk;
+/* Bytes of the geometry buffer for n_slots slots in chunks of chunk_slots; 0 when n_slots < 0 or
+ * chunk_slots is not a positive multiple of 16. */
 size_t gsc_geometry_bytes(int64_t n_slots, int64_t chunk_slots);
 /* Codes the geometry of a planned scene (d_perm [n_slots], n_slots a multiple of 16; geometry in
  * original order as gsc_render takes it) into d_geom (256-byte aligned, gsc_geometry_bytes). */

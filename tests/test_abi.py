@@ -170,3 +170,25 @@ def test_binding_argument_widths_match_the_prototypes(tmp_path):
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     bad = [w for w, g, e in zip(where, got, want) if g != e]
     assert not bad, bad
+
+
+def test_host_size_queries():
+    # pure host functions: the geometry buffer size equals the binding's offsets, the render
+    # workspace grows with the scene and the overlap count, and invalid arguments give 0
+    from paper_2607_14513_gb300 import gsc
+    from paper_2607_14513_gb300 import synthetic as S
+    lib = gsc.load()
+    for ns in (0, 16, 4096, 4112, 3_000_016):
+        for cs in (16, 128, 4096):
+            assert lib.gsc_geometry_bytes(ns, cs) == gsc.geometry_layout(ns, cs)[1], (ns, cs)
+    for ns, cs in ((-16, 16), (16, 0), (16, 8), (16, 24), (16, -16)):
+        assert lib.gsc_geometry_bytes(ns, cs) == 0, (ns, cs)
+    cam = gsc.camera(S.look_at([0.5, 0.5, -1.5], [0.5, 0.5, 0.5], 1920, 1080))
+    sizes = [lib.gsc_render_workspace_bytes(n, ctypes.byref(cam), p)
+             for n, p in ((0, 0), (1000, 0), (1000, 10**6), (10**6, 10**6), (3 * 10**6, 3 * 10**7))]
+    assert all(a < b for a, b in zip(sizes, sizes[1:])) and sizes[0] > 0
+    assert lib.gsc_render_workspace_bytes(-1, ctypes.byref(cam), 0) == 0
+    assert lib.gsc_render_workspace_bytes(10, ctypes.byref(cam), -1) == 0
+    assert lib.gsc_render_workspace_bytes(10, None, 0) == 0
+    bad = gsc.camera(S.look_at([0.5, 0.5, -1.5], [0.5, 0.5, 0.5], 0, 1080))
+    assert lib.gsc_render_workspace_bytes(10, ctypes.byref(bad), 0) == 0
