@@ -1149,11 +1149,18 @@ def cpu_baseline_d(workload, budget_s=20.0):
 def run_reference(args, world, rank):
     if rank != 0:
         return
+    if args.workload == "serve":
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle has no request loop; the served "
+                          "form's per-request work is the batch64 and scene3m reference arms' work"}), flush=True)
+        return
     times = []
     base = None
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        base = cpu_baseline(args.workload, budget_s=5.0)
+        if args.workload == "batch64":
+            base = cpu_baseline_mix(S.batch_mix(**S.BATCH), budget_s=5.0)
+        else:
+            base = cpu_baseline(args.workload, budget_s=5.0)
         if i >= args.warmup:
             times.append(time.perf_counter() - t0)
     v = base["value"]
