@@ -127,10 +127,12 @@ typedef struct {
 
 /* Context on one device (made current by every call). */
 gsc_status gsc_ctx_create(gsc_ctx** out, int device);
+/* Waits for the device, then frees the context's own buffers (not the caller's). */
 gsc_status gsc_ctx_destroy(gsc_ctx* ctx);
 /* Waits for `stream` and returns the first error a kernel recorded since the last
  * sync (then clears it). */
 gsc_status gsc_ctx_sync(gsc_ctx* ctx, void* stream);
+/* A static description of a status code (never NULL). */
 const char* gsc_status_string(gsc_status s);
 
 /* Bytes of scratch that gsc_plan_reorder and gsc_encode need for n Gaussians. */
@@ -334,6 +336,7 @@ typedef struct {
   int32_t bc1_tile_groups;
 } gsc_batch_tuning;
 
+/* Workspace bytes of gsc_batch_encode / gsc_batch_autotune for these scenes (0 if invalid). */
 size_t gsc_batch_workspace_bytes(const gsc_batch_scene* scenes, int32_t n_scenes);
 gsc_status gsc_batch_encode(gsc_ctx* ctx, gsc_batch_scene* scenes, int32_t n_scenes, const gsc_batch_tuning* tune,
                             void* d_ws, size_t ws_bytes, void* stream);
@@ -428,6 +431,7 @@ gsc_status gsc_server_submit(gsc_server* srv, const gsc_request* req, uint64_t* 
 /* Waits for a ticket (timeout_ms < 0: no limit; GSC_ERR_TIMEOUT when it runs out) and
  * consumes it. The request's own outcome is res->status. */
 gsc_status gsc_server_wait(gsc_server* srv, uint64_t ticket, int64_t timeout_ms, gsc_request_result* res);
+/* Waits until no request is queued or running (timeout_ms < 0: no limit; GSC_ERR_TIMEOUT). */
 gsc_status gsc_server_drain(gsc_server* srv, int64_t timeout_ms);
 /* Copies a resident scene's table, blocks and slot order out (host or device buffers). */
 gsc_status gsc_server_read_scene(gsc_server* srv, int32_t scene, gsc_stream_table* table, uint8_t* blocks,
@@ -440,6 +444,7 @@ gsc_status gsc_server_cancel(gsc_server* srv, uint64_t ticket);
 gsc_status gsc_server_save_scene(gsc_server* srv, int32_t scene, const char* path);
 /* Frees a resident scene that no queued or running request uses (else GSC_ERR_INVALID_ARG). */
 gsc_status gsc_server_evict(gsc_server* srv, int32_t scene);
+/* Counters since creation and the current memory figures. */
 gsc_status gsc_server_get_stats(gsc_server* srv, gsc_server_stats* st);
 /* Drains, stops the workers and frees every resident scene. */
 gsc_status gsc_server_destroy(gsc_server* srv);
@@ -482,6 +487,8 @@ int32_t gsc_build_checked(void);
  * a capacity too small); the bytes read back equal the bytes written. */
 gsc_status gsc_scene_write(const char* path, const gsc_stream_table* table, const uint8_t* blocks,
                            const int32_t* perm, const float* pos);
+/* Reads and checks the header only: the table and whether positions are stored, to size the
+ * buffers of gsc_scene_read. */
 gsc_status gsc_scene_read_info(const char* path, gsc_stream_table* table, int32_t* has_pos);
 gsc_status gsc_scene_read(const char* path, gsc_stream_table* table, uint8_t* blocks, size_t blocks_cap,
                           int32_t* perm, size_t perm_bytes_cap, float* pos, size_t pos_bytes_cap);
@@ -508,8 +515,8 @@ gsc_status gsc_probe_int_peak(gsc_ctx* ctx, double* ops_per_s, void* stream);
 /* Kernel timing: when enabled, each call records CUDA events on its own stream around its
  * main kernels. gsc_kernel_time waits for the recorded events and returns the summed
  * milliseconds and launch count of one kernel ("plan", "bc1_encode", "bc7_encode",
- * "rate_select", "decode", "decode_eval", "decode_tex", "decode_eval_tex", "batch_encode")
- * since timing was last enabled. */
+ * "rate_select", "decode", "decode_eval", "decode_tex", "decode_eval_tex", "batch_encode",
+ * "render" (a whole frame), "render_blend") since timing was last enabled. */
 gsc_status gsc_ctx_set_timing(gsc_ctx* ctx, int enable);
 gsc_status gsc_kernel_time(gsc_ctx* ctx, const char* name, double* ms, int64_t* launches);
 
