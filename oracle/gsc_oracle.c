@@ -45,6 +45,7 @@ static int cmp_float(const void* a, const void* b) {
   return (x > y) - (x < y);
 }
 
+/* Sec. V-A: the per-coefficient scale factors. */
 int or_scales(const float* sh, int64_t n, uint32_t permille, float* scales) {
   if (permille == 0 || permille > 1000) return -1;
   if (n <= 0) {
@@ -79,6 +80,7 @@ uint8_t or_quant1(float x, float s) {
   return (uint8_t)q;
 }
 
+/* Sec. V-A: 8-bit quantisation of the scaled coefficients. */
 void or_quantise(const float* sh, int64_t n, const float* scales, uint8_t* q) {
   for (int64_t i = 0; i < n; i++)
     for (int k = 0; k < OR_SH; k++)
@@ -127,7 +129,7 @@ static uint32_t grid10(float p, float lo, float ext) {
   return u > 1023 ? 1023 : u;
 }
 
-/* perm[s] = original index of slot s; slots padded to a multiple of 16 with -1.
+/* Sec. III-C, Sec. V-A. perm[s] = original index of slot s; slots padded to a multiple of 16 with -1.
  * sort = 0 keeps the original order; sort = 1 sorts by (chunk, colour key, spatial rank),
  * chunk = spatial rank / group_size (group_size 0 = whole scene). */
 int or_plan(const float* pos, const uint8_t* q, int64_t n, int64_t group_size, int sort, int32_t* perm) {
@@ -214,13 +216,15 @@ int or_layout_ok(int layout, int j) {
   return 0;
 }
 
+/* Sec. IV-B, Table I: whether block k of a layout's group is BC7 in a fixed mix. */
 int or_layout_bc7(int layout, int j, int k) {
   if (layout == OR_LAYOUT_A) return j == 16;
   if (layout == OR_LAYOUT_B) return (k % 4) < j / 4;
   return k < j;
 }
 
-/* Texels of group g in a layout: tex[k][t][c]. A padding slot repeats the last valid slot
+/* Sec. IV-B, Figs. SetupA/B/D.
+ * Texels of group g in a layout: tex[k][t][c]. A padding slot repeats the last valid slot
  * before it in its group (128 if there is none), as in layout D. */
 void or_stage_layout(const uint8_t* q, const int32_t* perm, int layout, int64_t g, uint8_t* tex) {
   int64_t src[16];
@@ -275,6 +279,7 @@ static int bc1_half(int a, int b, int bits) {
   return A + floor_div((B - A) * 257 + 256, 512);
 }
 
+/* Sec. III-A; BC1 format: the four-entry palette of two endpoints. */
 void or_bc1_palette(uint16_t c0, uint16_t c1, uint8_t* pal) {
   int a[3] = {c0 >> 11, (c0 >> 5) & 63, c0 & 31};
   int b[3] = {c1 >> 11, (c1 >> 5) & 63, c1 & 31};
@@ -294,6 +299,7 @@ void or_bc1_palette(uint16_t c0, uint16_t c1, uint8_t* pal) {
   pal[3 * 4 + 3] = (c0 > c1) ? 255 : 0;
 }
 
+/* Sec. III-A; BC1 format: a block to its 16 texels. */
 void or_bc1_decode(const uint8_t* blk, uint8_t* out) {
   uint16_t c0 = (uint16_t)(blk[0] | (blk[1] << 8));
   uint16_t c1 = (uint16_t)(blk[2] | (blk[3] << 8));
@@ -344,6 +350,7 @@ static void bc1_write(const bc1_sol* s, uint8_t* out) {
   out[4] = ix & 255; out[5] = (ix >> 8) & 255; out[6] = (ix >> 16) & 255; out[7] = ix >> 24;
 }
 
+/* Sec. III-A/B; BC1 format: the least-error block under the encoder specification. */
 uint64_t or_bc1_encode(const uint8_t* tex, uint8_t* out) {
   int constant = 1;
   for (int t = 1; t < 16; t++)
@@ -494,10 +501,12 @@ static const int* wtab(int ib) { return ib == 2 ? WT2 : (ib == 3 ? WT3 : WT4); }
 static int interp7(int e0, int e1, int w) { return ((64 - w) * e0 + w * e1 + 32) >> 6; }
 static int expand_bits(int v, int n) { return n >= 8 ? v : ((v << (8 - n)) | (v >> (2 * n - 8))); }
 
+/* Sec. III-B; BC7 format: the subset of texel t in partition part. */
 int or_bc7_subset(int ns, int part, int t) {
   if (ns == 1) return 0;
   return (ns == 2 ? PART2[part][t] : PART3[part][t]) - '0';
 }
+/* Sec. III-B; BC7 format: the anchor texel of subset s. */
 int or_bc7_anchor(int ns, int part, int s) {
   if (s == 0) return 0;
   if (ns == 2) return ANCH2[part];
@@ -520,6 +529,7 @@ static uint32_t br_get(bitr* r, int n) {
   return v;
 }
 
+/* Sec. III-B; BC7 format: a block of any mode to its 16 texels. */
 void or_bc7_decode(const uint8_t* blk, uint8_t* out) {
   int m = 0;
   while (m < 8 && !((blk[0] >> m) & 1)) m++;
@@ -789,6 +799,7 @@ static void bc7_pack(bc7_sol* S, uint8_t* out) {
   memcpy(out, w.b, 16);
 }
 
+/* Sec. III-B; BC7 format: the error and block of one enumerated candidate. */
 uint64_t or_bc7_candidate(const uint8_t* tex, int e, uint8_t* out) {
   bc7_cand c;
   if (cand_of(e, &c)) return UINT64_MAX;
@@ -798,6 +809,7 @@ uint64_t or_bc7_candidate(const uint8_t* tex, int e, uint8_t* out) {
   return S.sse;
 }
 
+/* Sec. III-B; BC7 format: the least-error candidate, first on ties. */
 uint64_t or_bc7_encode(const uint8_t* tex, uint8_t* out) {
   int ne = or_bc7_n_candidates(), best_e = 0;
   uint64_t best = UINT64_MAX;
@@ -824,11 +836,12 @@ static const int MODE_B[OR_MODES] = {1, 1, 4, 4, 4, 9, 9, 9, 9, 16, 16, 16, 16, 
 static const int MODE_J[OR_MODES] = {0, 1, 0, 1, 4, 0, 1, 4, 9, 0, 1, 4, 9, 16};
 static uint64_t mode_rate(int m) { return 64u * (uint64_t)(MODE_B[m] + MODE_J[m]); }
 
+/* Sec. IV-B, Table I: the 14 fixed-rate codings of a group (bands kept, BC7 blocks). */
 void or_mode_table(int32_t* bands, int32_t* bc7) {
   for (int m = 0; m < OR_MODES; m++) { bands[m] = MODE_B[m]; bc7[m] = MODE_J[m]; }
 }
 
-/* w_k = max(1, rint(65536 s_k^2 / max s^2)) in double precision. */
+/* Sec. IV-B. w_k = max(1, rint(65536 s_k^2 / max s^2)) in double precision. */
 void or_weights(const float* scales, uint32_t* w) {
   double mx = 0.0;
   for (int k = 0; k < OR_SH; k++) { double s = scales[k]; if (s * s > mx) mx = s * s; }
@@ -856,12 +869,13 @@ static uint64_t choose_all(const uint64_t* D, int64_t ng, uint64_t lambda, uint8
   return total;
 }
 
+/* Sec. IV-B: every group's coding at one Lagrange multiplier. */
 int or_rate_choose(const uint64_t* D, int64_t ng, uint64_t lambda, uint8_t* mode) {
   choose_all(D, ng, lambda, mode);
   return 0;
 }
 
-/* Smallest integer lambda in [0, 2^62] whose choice fits the budget, then a fill
+/* Sec. IV-B. Smallest integer lambda in [0, 2^62] whose choice fits the budget, then a fill
  * step: groups whose choice differs at lambda - 1 take that choice, in group order,
  * until the first one that would exceed the budget. */
 int or_rate_control(const uint64_t* D, int64_t ng, uint64_t budget, uint8_t* mode, uint64_t* lambda_out) {
@@ -987,7 +1001,7 @@ static int g_threads = 1;
 
 void or_set_threads(int threads) { g_threads = threads < 1 ? 1 : (threads > 256 ? 256 : threads); }
 
-/* Both codings and the D table of every group. Groups are independent and write disjoint
+/* Sec. IV-B. Both codings and the D table of every group. Groups are independent and write disjoint
  * memory, so they may be split over threads (or_set_threads) with identical results. */
 void or_code_groups(const uint8_t* q, int64_t n, const int32_t* perm, const float* scales, uint8_t* b1, uint8_t* b7,
                     uint64_t* D) {
@@ -1011,7 +1025,8 @@ void or_code_groups(const uint8_t* q, int64_t n, const int32_t* perm, const floa
   for (int i = 0; i < started; i++) pthread_join(th[i], NULL);
 }
 
-/* Rate control at target_x4 / 4 bits per texel over coded groups, then the 14 streams: the
+/* Sec. IV-B, Figs. SetupC/D.
+ * Rate control at target_x4 / 4 bits per texel over coded groups, then the 14 streams: the
  * stable partition of groups by mode id, each group's kept blocks back to back. */
 int or_rate_assemble(int64_t n, const int32_t* perm, const float* scales, uint32_t target_x4, const uint8_t* b1,
                      const uint8_t* b7, const uint64_t* D, uint8_t* blocks, int32_t* perm_out, or_table* t) {
@@ -1053,7 +1068,7 @@ int or_rate_assemble(int64_t n, const int32_t* perm, const float* scales, uint32
   return rc;
 }
 
-/* Decode every stream back to texels [n][16][3] in original order (inverse
+/* Sec. I, III; Sec. IV-B. Decode every stream back to texels [n][16][3] in original order (inverse
  * permutation); coefficients a stream does not keep decode to 128 (zero). */
 int or_decode(const or_table* t, const uint8_t* blocks, const int32_t* perm, uint8_t* texels) {
   uint8_t rgba[16][64];
@@ -1141,6 +1156,7 @@ static double assoc_legendre(int l, int m, double z) { /* m >= 0, includes (-1)^
   return pl;
 }
 
+/* Sec. II: the real SH basis to degree 3 at a unit direction. */
 void or_sh_basis(double x, double y, double z, double* Y) {
   const double PI = 3.14159265358979323846;
   double phi = atan2(y, x);
@@ -1157,7 +1173,8 @@ void or_sh_basis(double x, double y, double z, double* Y) {
     }
 }
 
-/* out[v][i][c] = sum_k x'_{i,k,c} Y_k(d), x' = (q - 128) / 255 * s_k, with d the unit
+/* Sec. II, c(f) = H w(f - p).
+ * out[v][i][c] = sum_k x'_{i,k,c} Y_k(d), x' = (q - 128) / 255 * s_k, with d the unit
  * direction dirs[v] (shared) or (cams[v] - pos[i]) / |cams[v] - pos[i]|; a zero
  * vector takes d = (0, 0, 1). abs_sum receives sum_k |x' Y_k(d)| for tolerances. */
 void or_eval_sh(const uint8_t* texels, int64_t n, const float* scales, const float* pos,
@@ -1206,6 +1223,7 @@ void or_camera_centre(const or_camera* cam, float* f) {
   }
 }
 
+/* Sec. II, Eq. covar, Fig. GSRend: the screen-space splat of one Gaussian. */
 int or_splat_setup(const float* p, const float* s, const float* q, const or_camera* cam, or_splat* o) {
   const float* R = cam->R;
   memset(o, 0, sizeof(*o));
@@ -1360,7 +1378,7 @@ static uint32_t quant_unit(float t, float levels) { /* round(t * levels), t clam
 
 int64_t or_chunks(int64_t n_slots, int64_t chunk_slots) { return (n_slots + chunk_slots - 1) / chunk_slots; }
 
-/* chunk[c] = lo[3], hi[3] (bounds of the chunk's centres), largest decoded scale, 0; a chunk of
+/* Sec. IV-A. chunk[c] = lo[3], hi[3] (bounds of the chunk's centres), largest decoded scale, 0; a chunk of
  * padding slots only is all zero */
 void or_chunk_table(const float* pos, const float* scale, const int32_t* perm, int64_t n_slots, int64_t chunk_slots,
                     float* chunk) {
@@ -1450,7 +1468,8 @@ void or_geometry_decode_slot(const uint16_t* qpos, const uint16_t* qscale, const
   *t = ((float)qlogit[s] / 255.0f) * 16.0f - 8.0f;
 }
 
-/* Chunk visibility (a reading of the hierarchy's view test): a chunk is kept unless its box of
+/* Sec. IV-A, Fig. FileHier.
+ * Chunk visibility (a reading of the hierarchy's view test): a chunk is kept unless its box of
  * centres, grown by 6 times its largest scale, lies entirely at camera depth <= near_z / 2, or is
  * entirely in front of the camera and projects entirely beyond one image side by more than
  * 64 pixels. Corners are projected in float with a fixed operation order. */
