@@ -174,7 +174,7 @@ def stage(q, perm):
     return out
 
 
-# --- BC1 / BC7 --------------------------------------------------------------------------
+# --- BC1 / BC7 (Sec. III-A/B; the BC1 and BC7 format definitions) -------------------------
 def bc1_palette(c0, c1):
     pal = np.zeros((4, 4), np.uint8)
     lib().or_bc1_palette(c0, c1, _p(pal))
@@ -282,6 +282,7 @@ def rate_control(D, budget):
     return rc, mode, lam.value
 
 
+# --- block layouts (Sec. IV-B, Figs. SetupA / SetupB / SetupD; Table I) ---------------------
 def layout_map(layout, k, t):
     """(slot in group, coefficient) held by texel t of block k (Sec. IV-B, Figs. SetupA/B/D)."""
     u, c = C.c_int(0), C.c_int(0)
@@ -323,6 +324,7 @@ def encode_layout(q, perm, sc, layout, bc7_blocks):
     return dict(blocks=blocks[:t.total_bytes], perm=perm[:ng * 16].copy(), table=t)
 
 
+# --- stream encode and decode of a scene (Sec. IV-B streams; Sec. I and III decode) --------
 def table_dict(t: Table):
     return dict(n_streams=t.n_streams, format=t.format, n=t.n, n_groups=t.n_groups, total_bytes=t.total_bytes,
                 layout=t.layout,
