@@ -1,5 +1,5 @@
 """The oracle's codings against the byte column that Table I prints (fixture
-`tests/golden/table1_sh_bytes.txt`, every row of the table with its block setup, Sec. VI).
+`tests/golden/table1_sh_bytes.txt`, every row of the table with its block setup, Sec. V-B).
 
 Setups A and B: the bytes of the coded blocks per primitive equal the printed value, in both
 orders. Setup D: the table prints 8.5 / 9 / 17 where the blocks (8 B per BC1 block, 16 B per BC7
