@@ -26,6 +26,8 @@ MODES = 14
 
 _lib = None
 _lock = threading.Lock()
+# A library to load instead of building liboracle.so (the pin tests' planted-mistake copies use it).
+LIB_OVERRIDE = None
 
 
 def build(force: bool = False) -> str:
@@ -57,7 +59,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            _lib = C.CDLL(build())
+            _lib = C.CDLL(LIB_OVERRIDE or build())
             P = C.c_void_p
             i64, u64, i32, u32 = C.c_int64, C.c_uint64, C.c_int, C.c_uint32
             sig = {

@@ -1,0 +1,130 @@
+"""The pins catch plausible mistakes: each case plants one mistake in a copy of the oracle's C
+source (a dropped term, a wrong sign, index or constant, a transposed operand, a reversed order),
+builds that copy apart from the real oracle, and checks that at least one of the named pins fails
+against it. The real oracle passes every one of those pins in the rest of the suite.
+"""
+import importlib.util
+import os
+import subprocess
+
+import pytest
+
+import test_oracle_bc1 as T_BC1
+import test_oracle_bc7 as T_BC7
+import test_oracle_geometry as T_GEO
+import test_oracle_rate as T_RATE
+import test_oracle_render as T_REN
+import test_oracle_reorder as T_REO
+import test_oracle_scales_quant as T_SQ
+import test_oracle_sh as T_SH
+
+ORACLE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle")
+
+# name: ([(text of the oracle, planted replacement)], [pins, at least one of which must fail])
+MUTANTS = {
+    "scale rank off by one (the -1 dropped)": (
+        [("int64_t r = ((int64_t)permille * m + 999) / 1000 - 1;", "int64_t r = ((int64_t)permille * m + 999) / 1000;")],
+        [T_SQ.test_scale_is_exact_order_statistic, T_SQ.test_scale_hand_fixture]),
+    "quantiser truncates instead of rounding": (
+        [("long r = lrintf(t);", "long r = (long)t;")],
+        [T_SQ.test_quantise_against_double_precision, T_SQ.test_quantise_ties_round_half_even]),
+    "quantiser rounds half away from zero": (
+        [("long r = lrintf(t);", "long r = lroundf(t);")],
+        [T_SQ.test_quantise_ties_round_half_even, T_SQ.test_quantise_against_double_precision]),
+    "colour key with R and B exchanged": (
+        [("k |= ((r >> i) & 1u) << (3 * i + 2);", "k |= ((b >> i) & 1u) << (3 * i + 2);"),
+         ("k |= ((b >> i) & 1u) << (3 * i);", "k |= ((r >> i) & 1u) << (3 * i);")],
+        [T_REO.test_colour_key_hand_values]),
+    "Morton code with x and z exchanged": (
+        [("m |= ((x >> i) & 1u) << (3 * i + 2);", "m |= ((z >> i) & 1u) << (3 * i + 2);"),
+         ("m |= ((z >> i) & 1u) << (3 * i);", "m |= ((x >> i) & 1u) << (3 * i);")],
+        [T_REO.test_morton_hand_values]),
+    "BC1 two-thirds entry with its operands transposed": (
+        [("if (bits == 5) return ((2 * a + b) * 11) >> 2;", "if (bits == 5) return ((a + 2 * b) * 11) >> 2;")],
+        [T_BC1.test_hand_built_four_colour_block, T_BC1.test_interpolation_reading_properties]),
+    "BC1 three-colour mode's fourth entry opaque": (
+        [("pal[3 * 4 + 3] = (c0 > c1) ? 255 : 0;", "pal[3 * 4 + 3] = 255;")],
+        [T_BC1.test_hand_built_three_colour_block]),
+    "BC7 interpolation without its rounding bias": (
+        [("static int interp7(int e0, int e1, int w) { return ((64 - w) * e0 + w * e1 + 32) >> 6; }",
+          "static int interp7(int e0, int e1, int w) { return ((64 - w) * e0 + w * e1) >> 6; }")],
+        [T_BC7.test_hand_built_mode6_gradient, T_BC7.test_hand_built_mode1_membership,
+         T_BC7.test_hand_built_mode4_rotation]),
+    "BC7 endpoint expansion without bit replication": (
+        [("static int expand_bits(int v, int n) { return n >= 8 ? v : ((v << (8 - n)) | (v >> (2 * n - 8))); }",
+          "static int expand_bits(int v, int n) { return n >= 8 ? v : (v << (8 - n)); }")],
+        [T_BC7.test_hand_built_mode1_membership, T_BC7.test_hand_built_mode4_rotation, T_BC7.test_constant_colours]),
+    "SH without the Condon-Shortley phase": (
+        [("for (int i = 1; i <= m; i++) pmm *= -(2.0 * i - 1.0) * s;",
+          "for (int i = 1; i <= m; i++) pmm *= (2.0 * i - 1.0) * s;")],
+        [T_SH.test_matches_scipy_complex_sh, T_SH.test_closed_form_values]),
+    "SH view direction p - f instead of f - p": (
+        [("for (int a = 0; a < 3; a++) d[a] = (double)cams[3 * v + a] - (double)pos[3 * i + a];",
+          "for (int a = 0; a < 3; a++) d[a] = (double)pos[3 * i + a] - (double)cams[3 * v + a];")],
+        [T_SH.test_camera_directions]),
+    "renderer blends far to near": (
+        [("if (a->depth_bits != b->depth_bits) return a->depth_bits < b->depth_bits ? -1 : 1;",
+          "if (a->depth_bits != b->depth_bits) return a->depth_bits < b->depth_bits ? 1 : -1;")],
+        [T_REN.test_two_splats_blend_front_to_back]),
+    "renderer transmittance without the opacity": (
+        [("T *= 1.0 - mu * gv;", "T *= 1.0 - gv;")],
+        [T_REN.test_head_on_isotropic_splat_closed_form, T_REN.test_two_splats_blend_front_to_back]),
+    "rate control: a budget met exactly counts as over": (
+        [("if (choose_all(D, ng, mid, NULL) <= budget) hi = mid; else lo = mid + 1;",
+          "if (choose_all(D, ng, mid, NULL) < budget) hi = mid; else lo = mid + 1;")],
+        [T_RATE.test_budget_met_exactly]),
+    "rotation codes over 1023 steps while the decoder uses 1022": (
+        [("code |= quant_unit(t, 1022.0f) << sh;", "code |= quant_unit(t, 1023.0f) << sh;")],
+        [T_GEO.test_rotation_smallest_three]),
+    "chunk test without the scale margin": (
+        [("float g = 6.0f * e[6];", "float g = 0.0f * e[6];")],
+        [T_GEO.test_culling_never_drops_a_drawn_gaussian]),
+    "splat cross term with the wrong sign": (
+        [("float a = c00 + 0.3f, b = c01, c = c11 + 0.3f;", "float a = c00 + 0.3f, b = -c01, c = c11 + 0.3f;")],
+        [T_REN.test_oblique_splat_points_along_its_axis]),
+    "splat without the low-pass": (
+        [("float a = c00 + 0.3f, b = c01, c = c11 + 0.3f;", "float a = c00, b = c01, c = c11;")],
+        [T_REN.test_head_on_isotropic_splat_closed_form]),
+    "rotation matrix with one entry's sign flipped": (
+        [("r[1] = 2.0f * (qx * qy - qw * qz);", "r[1] = 2.0f * (qx * qy + qw * qz);")],
+        [T_REN.test_oblique_splat_points_along_its_axis]),
+    "dequantisation centred on 127": (
+        [("double x = ((double)texels[(i * OR_SH + k) * 3 + c] - 128.0) / 255.0 * (double)scales[k];",
+          "double x = ((double)texels[(i * OR_SH + k) * 3 + c] - 127.0) / 255.0 * (double)scales[k];")],
+        [T_SH.test_degree_zero_and_dequantisation, T_SH.test_camera_directions]),
+    "position codes over 65536 steps while the decoder uses 65535": (
+        [("qpos[3 * s + a] = (uint16_t)quant_unit(t, 65535.0f);", "qpos[3 * s + a] = (uint16_t)quant_unit(t, 65536.0f);")],
+        [T_GEO.test_position_codes_within_half_a_step_of_the_chunk_box]),
+}
+
+
+def _mutant_oracle(tmp_path, patches):
+    src = open(os.path.join(ORACLE, "gsc_oracle.c")).read()
+    for old, new in patches:
+        assert src.count(old) == 1, old
+        src = src.replace(old, new)
+    c = tmp_path / "gsc_oracle_mutant.c"
+    c.write_text(src)
+    so = tmp_path / "liboracle_mutant.so"
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-pthread", "-fPIC",
+                           "-shared", "-I", ORACLE, "-o", str(so), str(c), "-lm"])
+    spec = importlib.util.spec_from_file_location("oracle_mutant_%d" % abs(hash(str(tmp_path))),
+                                                  os.path.join(ORACLE, "oracle.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.LIB_OVERRIDE = str(so)
+    mod.lib()
+    return mod
+
+
+@pytest.mark.parametrize("name", list(MUTANTS))
+def test_a_planted_mistake_fails_a_pin(tmp_path, name):
+    patches, pins = MUTANTS[name]
+    M = _mutant_oracle(tmp_path, patches)
+    failed = []
+    for pin in pins:
+        try:
+            pin(M)
+        except AssertionError:
+            failed.append(pin.__name__)
+    assert failed, "no pin caught: " + name

@@ -68,6 +68,25 @@ def test_lagrangian_choice_is_on_the_hull(O):
         assert np.all(R[mode] >= R[base])
 
 
+def test_budget_met_exactly(O):
+    # a budget equal to the total rate of some multiplier's choice is met exactly: lambda* is the
+    # smallest multiplier whose choice fits (total <= budget), so its total equals the budget
+    rng = np.random.default_rng(24)
+    R = _rates(O)
+    D = _random_D(rng, 12)
+    lams = sorted(set(int(x) for x in np.exp(rng.uniform(0, 40, size=40))))
+    seen = 0
+    for l in lams:
+        budget = int(R[O.rate_choose(D, l)].sum())
+        rc, mode, lam = O.rate_control(D, budget)
+        assert rc == 0
+        assert int(R[O.rate_choose(D, lam)].sum()) == budget
+        assert lam == 0 or int(R[O.rate_choose(D, lam - 1)].sum()) > budget
+        assert int(R[mode].sum()) == budget
+        seen += lam > 0
+    assert seen > 10
+
+
 def test_rate_monotone_in_lambda(O):
     rng = np.random.default_rng(22)
     R = _rates(O)

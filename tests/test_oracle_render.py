@@ -104,6 +104,34 @@ def test_rotation_about_the_view_axis_transposes_an_elongated_splat(O):
     assert np.allclose(b[..., 0], a[..., 0].T, rtol=1e-4, atol=1e-7)
 
 
+def test_oblique_splat_points_along_its_axis(O):
+    # a Gaussian long along a world direction u in the image plane's parallel plane, on the optical
+    # axis: the rendered image's principal axis (second moments) is the camera's image of u, and its
+    # variances are (f s / z)^2 + 0.3 along both axes; at oblique angles a wrong sign anywhere in the
+    # rotation or the projected covariance mirrors the axis
+    cam = _cam()
+    f, z = float(cam["fx"]), 2.0
+    Rm = np.asarray(cam["R"], np.float64).reshape(3, 3)
+    sc = np.array([[0.09, 0.02, 0.02]], np.float32)
+    ys, xs = np.mgrid[0:H, 0:W] + 0.5
+    for deg in (20, 35, 60, 110, 145):
+        th = np.radians(deg)
+        q = [np.cos(th / 2), 0.0, 0.0, np.sin(th / 2)]          # th about world z
+        u = np.array([np.cos(th), np.sin(th), 0.0])              # where the long axis (world x) goes
+        img, _ = O.render([[0.5, 0.5, 0.5]], sc, [q], [2.0], np.array([[1.0, 1.0, 1.0]]), cam)
+        w = img[..., 0]
+        m = w.sum()
+        cx, cy = (w * xs).sum() / m, (w * ys).sum() / m
+        mxx, myy = (w * (xs - cx) ** 2).sum() / m, (w * (ys - cy) ** 2).sum() / m
+        mxy = (w * (xs - cx) * (ys - cy)).sum() / m
+        phi = 0.5 * np.arctan2(2 * mxy, mxx - myy)
+        want = np.arctan2(Rm[1] @ u, Rm[0] @ u)
+        assert abs((phi - want + np.pi / 2) % np.pi - np.pi / 2) < np.radians(0.05), deg
+        ev = np.linalg.eigvalsh([[mxx, mxy], [mxy, myy]])
+        var = (f * sc[0, [2, 0]].astype(np.float64) / z) ** 2 + 0.3
+        assert np.allclose(ev, var, rtol=1e-2), deg
+
+
 def test_culling_and_empty_footprints(O):
     cam = _cam()
     col = np.ones((3, 3))
