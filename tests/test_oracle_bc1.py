@@ -160,6 +160,19 @@ def test_encoder_output_is_canonical_and_consistent(O):
         dec = O.bc1_decode(blocks[i])
         assert int(((dec[:, :3].astype(int) - tex[i].astype(int)) ** 2).sum()) == int(sse[i])
         assert O.bc1_candidate_sse(tex[i], c0, c1) == sse[i]
+    # each texel's index is the first palette entry of least error (the encoder's tie rule)
+    ties = 0
+    for i in range(tex.shape[0]):
+        c0 = int(blocks[i, 0]) | (int(blocks[i, 1]) << 8)
+        c1 = int(blocks[i, 2]) | (int(blocks[i, 3]) << 8)
+        pal = O.bc1_palette(c0, c1).reshape(4, 4)[:, :3].astype(int)
+        nent = 1 if c0 == c1 else 4
+        idx = int.from_bytes(bytes(blocks[i, 4:8]), "little")
+        for t in range(16):
+            e = ((pal[:nent] - tex[i, t].astype(int)) ** 2).sum(axis=1)
+            assert (idx >> (2 * t)) & 3 == int(np.argmin(e)), (i, t)
+            ties += (e == e.min()).sum() > 1
+    assert ties > 0
 
 
 def test_encoder_against_local_brute_force(O):

@@ -153,6 +153,14 @@ def test_encoder_is_the_first_minimum(O):
         blocks, sse = O.encode_blocks(tex[None], 7, threads=1)
         assert int(sse[0]) == min(errs)
         assert np.array_equal(blocks[0], O.bc7_candidate(tex, first)[1])
+    # ties: blocks that many candidates code without error take the first of them
+    ties = [np.tile(np.array([64, 128, 200], np.uint8), (16, 1)),
+            np.where((np.arange(16) % 2)[:, None] == 0, [16, 32, 48], [200, 100, 50]).astype(np.uint8)]
+    for tex in ties:
+        errs = np.array([O.bc7_candidate(tex, e)[0] for e in range(ne)])
+        assert (errs == errs.min()).sum() > 1
+        blocks, _ = O.encode_blocks(tex[None], 7, threads=1)
+        assert np.array_equal(blocks[0], O.bc7_candidate(tex, int(np.argmin(errs)))[1])
 
 
 def test_constant_colours(O):

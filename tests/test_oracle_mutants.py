@@ -95,6 +95,31 @@ MUTANTS = {
     "position codes over 65536 steps while the decoder uses 65535": (
         [("qpos[3 * s + a] = (uint16_t)quant_unit(t, 65535.0f);", "qpos[3 * s + a] = (uint16_t)quant_unit(t, 65536.0f);")],
         [T_GEO.test_position_codes_within_half_a_step_of_the_chunk_box]),
+    "padding repeats the first valid slot of its group": (
+        [("    if (o >= 0) last = o;\n    for (int k = 0; k < OR_SH; k++)\n      for (int c = 0; c < 3; c++) tex[(k * 16 + t) * 3 + c]",
+          "    if (o >= 0 && last < 0) last = o;\n    for (int k = 0; k < OR_SH; k++)\n      for (int c = 0; c < 3; c++) tex[(k * 16 + t) * 3 + c]")],
+        [T_REO.test_stage_layout_d]),
+    "rate weights without the square of the scale": (
+        [("double v = rint((s * s * 65536.0) / mx);", "double v = rint((s * 65536.0) / mx);")],
+        [T_RATE.test_distortion_table_is_dequantised_squared_error]),
+    "distortion table charges BC1 errors to BC7 blocks": (
+        [("uint64_t e = k < MODE_J[m] ? e7[k] : (k < MODE_B[m] ? e1[k] : e0[k]);",
+          "uint64_t e = k < MODE_J[m] ? e1[k] : (k < MODE_B[m] ? e1[k] : e0[k]);")],
+        [T_RATE.test_distortion_table_is_dequantised_squared_error]),
+    "dropped coefficients charged as zero error": (
+        [("for (int u = 0; u < 48; u++) e0[k] += (uint64_t)sq(tk[u] - 128);",
+          "for (int u = 0; u < 48; u++) e0[k] += 0;")],
+        [T_RATE.test_distortion_table_is_dequantised_squared_error]),
+    "BC7 encoder keeps the last of equal errors": (
+        [("if (s < best) { best = s; best_e = e; }", "if (s <= best) { best = s; best_e = e; }")],
+        [T_BC7.test_encoder_is_the_first_minimum]),
+    "BC1 indices take the last of equal palette errors": (
+        [("if (best < 0 || e < best) { best = e; bj = j; }", "if (best < 0 || e <= best) { best = e; bj = j; }")],
+        [T_BC1.test_encoder_output_is_canonical_and_consistent, T_BC1.test_hand_built_four_colour_block,
+         T_BC1.test_encoder_against_local_brute_force]),
+    "bfloat16 scales truncated instead of rounded": (
+        [("u += 0x7FFFu + ((u >> 16) & 1u);", "u += 0u;")],
+        [T_GEO.test_scale_and_opacity_codes]),
 }
 
 

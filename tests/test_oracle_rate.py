@@ -87,6 +87,41 @@ def test_budget_met_exactly(O):
     assert seen > 10
 
 
+def test_distortion_table_is_dequantised_squared_error(O):
+    # Sec. IV-B trades rate against the distortion of the decoded colours. Reading: a group's
+    # distortion under a coding is the squared error of the dequantised coefficients it leaves,
+    # x' = (q - 128) / 255 * s_k (Sec. V-A): BC7 blocks for the first j coefficients, BC1 blocks up
+    # to b, dropped coefficients (x' = 0) after. Checked against block errors computed here from
+    # the block coders, up to one positive factor; the table's integer weights round that factor
+    # per coefficient, which bounds the slack by one unit of weight per unit of block error.
+    sc = S.make_scene(512, 31)
+    scl = O.scales(sc.sh)
+    q = O.quantise(sc.sh, scl)
+    perm = O.plan(sc.pos, q, 256, 1)
+    D = O.encode(q, perm, scl, 0, 24, want_dtab=True)["dtab"].astype(np.float64)
+    tex = O.stage(q, perm).astype(np.int64)                       # [groups, block k, texel, channel]
+    ng = tex.shape[0]
+    flat = tex.reshape(-1, 16, 3).astype(np.uint8)
+    dec = {f: O.decode_blocks(O.encode_blocks(flat, f)[0], f)[..., :3].reshape(ng, 16, 16, 3).astype(np.int64)
+           for f in (1, 7)}
+    e1 = ((dec[1] - tex) ** 2).sum(axis=(2, 3))
+    e7 = ((dec[7] - tex) ** 2).sum(axis=(2, 3))
+    e0 = ((tex - 128) ** 2).sum(axis=(2, 3))
+    b, j = O.mode_table()
+    k = np.arange(16)
+    s2 = scl.astype(np.float64) ** 2
+    E = np.zeros_like(D)
+    U = np.zeros_like(D)
+    for m in range(14):
+        e = np.where(k < j[m], e7, np.where(k < b[m], e1, e0))
+        E[:, m] = (e * s2).sum(axis=1)
+        U[:, m] = e.sum(axis=1)
+    c = (D * E).sum() / (E * E).sum()
+    assert c > 0
+    assert np.all(np.abs(D - c * E) <= U + 1e-9 * D)
+    assert (E > 0).mean() > 0.9
+
+
 def test_rate_monotone_in_lambda(O):
     rng = np.random.default_rng(22)
     R = _rates(O)
