@@ -34,7 +34,7 @@ def test_layout_a_block_is_one_gaussian(O):
 
 def test_layout_b_quad_holds_four_gaussians_first_block_first_coefficients(O):
     # Fig. SetupB: four primitives' 64 vectors in four blocks; Table I: the first of the four blocks
-    # carries "the 4 first SH coefficients" (bands 0 and 1)
+    # carries the first four SH coefficients (bands 0 and 1)
     for v in range(4):
         slots = {O.layout_map(B, 4 * v + b, t)[0] for b in range(4) for t in range(16)}
         assert slots == {4 * v + i for i in range(4)}
@@ -42,6 +42,14 @@ def test_layout_b_quad_holds_four_gaussians_first_block_first_coefficients(O):
             cells = [O.layout_map(B, 4 * v + b, t) for t in range(16)]
             assert {c for _, c in cells} == {4 * b + j for j in range(4)}
             assert sorted(cells) == sorted((u, c) for u in slots for c in range(4 * b, 4 * b + 4))
+
+
+def test_layout_b_placement_rows_are_gaussians(O):
+    # the reading of the placement inside a B block (the figure shows the blocks, not their texel
+    # order): raster order, row i = the quad's Gaussian i, column j = coefficient 4b + j; hand values
+    for k, t, want in ((0, 0, (0, 0)), (0, 3, (0, 3)), (0, 4, (1, 0)), (1, 6, (1, 6)), (5, 6, (5, 6)),
+                       (6, 13, (7, 9)), (15, 15, (15, 15)), (12, 2, (12, 2)), (3, 12, (3, 12))):
+        assert O.layout_map(B, k, t) == want, (k, t)
 
 
 def test_fixed_codings_match_table_one_bytes(O):

@@ -12,6 +12,7 @@ import pytest
 import test_oracle_bc1 as T_BC1
 import test_oracle_bc7 as T_BC7
 import test_oracle_geometry as T_GEO
+import test_oracle_layouts as T_LAY
 import test_oracle_rate as T_RATE
 import test_oracle_render as T_REN
 import test_oracle_reorder as T_REO
@@ -120,6 +121,28 @@ MUTANTS = {
     "bfloat16 scales truncated instead of rounded": (
         [("u += 0x7FFFu + ((u >> 16) & 1u);", "u += 0u;")],
         [T_GEO.test_scale_and_opacity_codes]),
+    "layout B with rows and columns exchanged": (
+        [("*u = 4 * v + i; *c = 4 * b + j;", "*u = 4 * v + j; *c = 4 * b + i;")],
+        [T_LAY.test_layout_b_placement_rows_are_gaussians]),
+    "layout A block read as layout D": (
+        [("if (layout == OR_LAYOUT_A) { *u = k; *c = t; }", "if (layout == OR_LAYOUT_A) { *u = t; *c = k; }")],
+        [T_LAY.test_layout_a_block_is_one_gaussian]),
+    "colour sort ignores the spatial chunks": (
+        [("k[r].a = group_size ? (uint64_t)(r / group_size) : 0;", "k[r].a = 0;")],
+        [lambda O: T_REO.test_plan_matches_independent_restatement(O, 1000, 256)]),
+    "colour ties broken by original index instead of spatial rank": (
+        [("k[r].c = (uint64_t)r;", "k[r].c = (uint64_t)i;")],
+        [T_REO.test_colour_ties_keep_spatial_order]),
+    "pixel centres at integer coordinates": (
+        [("double dx = (px + 0.5) - (double)g->u, dy = (py + 0.5) - (double)g->v;",
+          "double dx = (double)px - (double)g->u, dy = (double)py - (double)g->v;")],
+        [T_REN.test_head_on_isotropic_splat_closed_form]),
+    "splat rectangle of 2 sigma": (
+        [("float rad = ceilf(3.0f * sqrtf(lam));", "float rad = ceilf(2.0f * sqrtf(lam));")],
+        [T_REN.test_tile_rectangle_is_three_sigma]),
+    "chunk scale bound from the last axis only": (
+        [("if ((!any && a == 0) || sv > e[6]) e[6] = sv;", "if (a == 2 && (!any || sv > e[6])) e[6] = sv;")],
+        [T_GEO.test_chunk_table_and_byte_count]),
 }
 
 
@@ -151,5 +174,5 @@ def test_a_planted_mistake_fails_a_pin(tmp_path, name):
         try:
             pin(M)
         except AssertionError:
-            failed.append(pin.__name__)
+            failed.append(getattr(pin, "__name__", "pin"))
     assert failed, "no pin caught: " + name

@@ -132,6 +132,27 @@ def test_oblique_splat_points_along_its_axis(O):
         assert np.allclose(ev, var, rtol=1e-2), deg
 
 
+def test_tile_rectangle_is_three_sigma(O):
+    # the footprint is every 16 x 16 tile that the square of half-width ceil(3 sigma) around the
+    # centre touches (sigma of the larger axis, isotropic here: variance (f s / z)^2 + 0.3 plus the
+    # eigenvalue floor sqrt(0.1)); a head-on splat moved across a tile, inside pixels positive,
+    # outside exactly zero
+    cam = _cam()
+    f, z = float(cam["fx"]), 2.0
+    s = 0.05
+    var = (f * s / z) ** 2 + 0.3
+    r = np.ceil(3 * np.sqrt(var + np.sqrt(0.1)))
+    for du in (-11.0, -7.5, -3.0, 0.0, 2.5, 6.5, 9.25):
+        x = 0.5 - du * z / f                            # image x = -world x
+        img, _ = O.render([[x, 0.5, 0.5]], [[s, s, s]], [[1, 0, 0, 0]], [2.0], np.array([[1.0, 1.0, 1.0]]), cam)
+        u = W / 2 + du
+        t0, t1 = np.floor((u - r) / 16), np.floor((u + r) / 16) + 1
+        v0, v1 = np.floor((H / 2 - r) / 16), np.floor((H / 2 + r) / 16) + 1
+        ys, xs = np.mgrid[0:H, 0:W]
+        inside = (xs >= 16 * t0) & (xs < 16 * t1) & (ys >= 16 * v0) & (ys < 16 * v1)
+        assert np.array_equal(img[..., 0] > 0, inside), du
+
+
 def test_culling_and_empty_footprints(O):
     cam = _cam()
     col = np.ones((3, 3))

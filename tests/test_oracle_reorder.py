@@ -74,6 +74,27 @@ def test_plan_matches_independent_restatement(O, n, gs):
     assert np.all(np.diff(k)[same] >= 0)
 
 
+def test_colour_ties_keep_spatial_order(O):
+    # equal colour keys inside a chunk keep the spatial (Morton) order, not the storage order: a
+    # scene whose DC colours all quantise alike, stored in a shuffled order
+    n = 600
+    sc = S.make_scene(n, 41, clusters=4)
+    sh = sc.sh.copy()
+    sh[:, 0, :] = 0.25                                    # one DC colour for every Gaussian
+    q = O.quantise(sh, O.scales(sh))
+    assert len({tuple(x) for x in q[:, 0, :]}) == 1
+    for gs in (0, 128):
+        perm = O.plan(sc.pos, q, gs, 1)
+        order, _, _ = _np_plan(sc.pos, q, gs)
+        assert np.array_equal(perm[:n], order)
+        # with one colour the colour sort changes nothing: the slot order is the spatial rank
+        lo, hi = sc.pos.min(axis=0), sc.pos.max(axis=0)
+        g = np.minimum(np.floor((sc.pos - lo) / (hi - lo) * 1024).astype(np.int64), 1023)
+        m = np.array([O.morton30(*map(int, r)) for r in g], np.int64)
+        assert np.array_equal(perm[:n], np.lexsort((np.arange(n), m)))
+        assert not np.array_equal(perm[:n], np.arange(n))
+
+
 def test_plan_group16_sorts_each_group(O):
     # G = 16: every group is its own spatial chunk, sorted by colour inside
     sc = S.make_scene(512, 5)
