@@ -89,6 +89,28 @@ def test_hand_built_mode1_membership(O):
             assert tuple(out[t]) == (v, v, v, 255)
 
 
+def test_hand_built_mode1_shared_pbits_and_weights(O):
+    # mode 1, partition 0 (texels 2, 3, 6, 7, 10, 11, 14, 15 in subset 1, anchor 15): 6-bit codes
+    # with one p-bit per subset shared by both endpoints, 3-bit indices (anchors 0 and 15 two bits).
+    # Subset 0: codes 0 / 63, p-bit 1 -> 7-bit 1 / 127 -> 2 / 255; subset 1: codes 10 / 50, p-bit 0
+    # -> 7-bit 20 / 100 -> 40 / 201 (7-bit v expands to v << 1 | v >> 6)
+    W3 = [0, 9, 18, 27, 37, 46, 55, 64]
+    sub1 = {2, 3, 6, 7, 10, 11, 14, 15}
+    idx = [(3 * t) % 8 for t in range(16)]
+    idx[15] = 3
+    b = Bits().put(2, 2).put(0, 6)
+    for _c in range(3):
+        b.put(0, 6).put(63, 6).put(10, 6).put(50, 6)
+    b.put(1, 1).put(0, 1)
+    for t in range(16):
+        b.put(idx[t], 2 if t in (0, 15) else 3)
+    out = O.bc7_decode(b.block())
+    for t in range(16):
+        e0, e1 = (40, 201) if t in sub1 else (2, 255)
+        v = ((64 - W3[idx[t]]) * e0 + W3[idx[t]] * e1 + 32) >> 6
+        assert tuple(out[t]) == (v, v, v, 255), t
+
+
 def test_hand_built_mode4_rotation(O):
     # mode 4, rotation 1 (alpha <-> red), index selection 0: colour codes 0, alpha codes 63 -> 255
     b = Bits().put(1 << 4, 5).put(1, 2).put(0, 1)

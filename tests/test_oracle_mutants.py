@@ -143,6 +143,49 @@ MUTANTS = {
     "chunk scale bound from the last axis only": (
         [("if ((!any && a == 0) || sv > e[6]) e[6] = sv;", "if (a == 2 && (!any || sv > e[6])) e[6] = sv;")],
         [T_GEO.test_chunk_table_and_byte_count]),
+    "BC7 rotation swaps alpha with the wrong channel": (
+        [("if (rot) { int tmp = px[3]; px[3] = px[rot - 1]; px[rot - 1] = tmp; }",
+          "if (rot) { int tmp = px[3]; px[3] = px[rot % 3]; px[rot % 3] = tmp; }")],
+        [T_BC7.test_hand_built_mode4_rotation]),
+    "BC7 index selection bit ignored": (
+        [("if (isb) { ci = sec[t]; cbits = M->ib2; ai = pri[t]; abits = M->ib; }",
+          "if (0) { ci = sec[t]; cbits = M->ib2; ai = pri[t]; abits = M->ib; }")],
+        [T_BC7.test_hand_built_mode4_rotation, T_BC7.test_every_candidate_packs_losslessly]),
+    "BC7 secondary index stream without its anchor bit": (
+        [("for (int t = 0; t < 16; t++) sec[t] = M->ib2 ? (int)br_get(&r, M->ib2 - (t == 0)) : 0;",
+          "for (int t = 0; t < 16; t++) sec[t] = M->ib2 ? (int)br_get(&r, M->ib2) : 0;")],
+        [T_BC7.test_hand_built_mode4_rotation, T_BC7.test_every_candidate_packs_losslessly]),
+    "BC7 shared p-bit applied to one endpoint only": (
+        [("for (int s = 0; s < M->ns; s++) p[s][0] = p[s][1] = (int)br_get(&r, 1);",
+          "for (int s = 0; s < M->ns; s++) p[s][0] = (int)br_get(&r, 1);")],
+        [T_BC7.test_hand_built_mode1_shared_pbits_and_weights]),
+    "BC7 three-subset anchors exchanged": (
+        [("return s == 1 ? ANCH3A[part] : ANCH3B[part];", "return s == 1 ? ANCH3B[part] : ANCH3A[part];")],
+        [T_BC7.test_partition_and_anchor_invariants]),
+    "BC7 opaque modes decode alpha 0": (
+        [("ev[s][e][3] = M->ab ? expand_bits(M->epb ? (code[s][e][3] << 1) | p[s][e] : code[s][e][3], M->ab + M->epb) : 255;",
+          "ev[s][e][3] = M->ab ? expand_bits(M->epb ? (code[s][e][3] << 1) | p[s][e] : code[s][e][3], M->ab + M->epb) : 0;"),
+         ("px[3] = M->ab ? interp7(ev[s][0][3], ev[s][1][3], wtab(abits)[ai]) : 255;",
+          "px[3] = M->ab ? interp7(ev[s][0][3], ev[s][1][3], wtab(abits)[ai]) : 0;")],
+        [T_BC7.test_hand_built_mode1_membership, T_BC7.test_reserved_mode_decodes_to_zero]),
+    "BC1 5-bit expansion without replication": (
+        [("static int ex5(int x) { return (x << 3) | (x >> 2); }", "static int ex5(int x) { return x << 3; }")],
+        [T_BC1.test_hand_built_four_colour_block, T_BC1.test_exact_565_colours_round_trip]),
+    "BC1 three-colour mode's fourth entry white": (
+        [("      pal[3 * 4 + c] = 0;", "      pal[3 * 4 + c] = 255;")],
+        [T_BC1.test_hand_built_three_colour_block]),
+    "SH direction of a camera on the Gaussian is -z": (
+        [("if (nn == 0.0) { d[0] = 0.0; d[1] = 0.0; d[2] = 1.0; }", "if (nn == 0.0) { d[0] = 0.0; d[1] = 0.0; d[2] = -1.0; }")],
+        [T_SH.test_camera_directions]),
+    "opacity logit decoded over 256 steps": (
+        [("*t = ((float)qlogit[s] / 255.0f) * 16.0f - 8.0f;", "*t = ((float)qlogit[s] / 256.0f) * 16.0f - 8.0f;")],
+        [T_GEO.test_scale_and_opacity_codes]),
+    "scales ignore the coverage parameter": (
+        [("int64_t r = ((int64_t)permille * m + 999) / 1000 - 1;", "int64_t r = ((int64_t)995 * m + 999) / 1000 - 1;")],
+        [T_SQ.test_scale_is_exact_order_statistic, T_SQ.test_scale_coverage_property, T_SQ.test_scale_hand_fixture]),
+    "quantiser wraps 256 to 0": (
+        [("if (q > 255) q = 255;", "if (q > 256) q = 255;")],
+        [T_SQ.test_quantise_special_values, T_SQ.test_quantise_against_double_precision]),
 }
 
 
