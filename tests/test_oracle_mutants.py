@@ -186,6 +186,30 @@ MUTANTS = {
     "quantiser wraps 256 to 0": (
         [("if (q > 255) q = 255;", "if (q > 256) q = 255;")],
         [T_SQ.test_quantise_special_values, T_SQ.test_quantise_against_double_precision]),
+    "BC7 fit ignores anti-correlated channels": (
+        [("int flip = (i != ref) && ((int64_t)n * s2[ref][i] - s1[ref] * s1[i] < 0);", "int flip = 0;")],
+        [T_BC7.test_two_subset_partitions_exact, T_BC7.test_three_subset_partitions_exact]),
+    "BC7 fit tries only the first p-bit combination": (
+        [("int ncombo = ptype == 0 ? 1 : (ptype == 1 ? 4 : 2);", "int ncombo = 1;")],
+        [T_BC7.test_constant_colours, T_BC7.test_two_subset_partitions_exact,
+         T_BC7.test_three_subset_partitions_exact]),
+}
+
+# Steps of the encoder's own search heuristic (the encoder specification, not the paper or the BC7
+# format): a change here gives another valid encoder with every format property the pins check
+# (lossless where representable, the first least-error candidate), so no external fact catches it.
+# The GPU encoder, written from the same specification, is compared with the oracle bit for bit,
+# which is what holds these steps. Strict: a pin that starts catching one of them fails this list.
+HEURISTIC_MUTANTS = {
+    "BC7 nearest endpoint code keeps the last of equal distances": (
+        [("    if (be < 0 || d < be) { be = d; best = code; }\n  }\n  return best;",
+          "    if (be < 0 || d <= be) { be = d; best = code; }\n  }\n  return best;")],
+        [T_BC7.test_constant_colours, T_BC7.test_encoder_is_the_first_minimum]),
+    "BC7 fit without its least-squares step": (
+        [("  if (det != 0)\n    for (int i = 0; i < nch; i++) {\n      e0[i] = clampi(",
+          "  if (0)\n    for (int i = 0; i < nch; i++) {\n      e0[i] = clampi(")],
+        [T_BC7.test_constant_colours, T_BC7.test_two_subset_partitions_exact,
+         T_BC7.test_three_subset_partitions_exact, T_BC7.test_encoder_is_the_first_minimum]),
 }
 
 
@@ -211,6 +235,20 @@ def _mutant_oracle(tmp_path, patches):
 @pytest.mark.parametrize("name", list(MUTANTS))
 def test_a_planted_mistake_fails_a_pin(tmp_path, name):
     patches, pins = MUTANTS[name]
+    M = _mutant_oracle(tmp_path, patches)
+    failed = []
+    for pin in pins:
+        try:
+            pin(M)
+        except AssertionError:
+            failed.append(getattr(pin, "__name__", "pin"))
+    assert failed, "no pin caught: " + name
+
+
+@pytest.mark.parametrize("name", list(HEURISTIC_MUTANTS))
+@pytest.mark.xfail(strict=True, reason="a step of the encoder's own heuristic: no pin outside the specification")
+def test_a_heuristic_change_is_not_caught_by_format_pins(tmp_path, name):
+    patches, pins = HEURISTIC_MUTANTS[name]
     M = _mutant_oracle(tmp_path, patches)
     failed = []
     for pin in pins:
