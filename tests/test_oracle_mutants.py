@@ -13,6 +13,7 @@ import test_oracle_bc1 as T_BC1
 import test_oracle_bc7 as T_BC7
 import test_oracle_geometry as T_GEO
 import test_oracle_layouts as T_LAY
+import test_oracle_pipeline as T_PIPE
 import test_oracle_rate as T_RATE
 import test_oracle_render as T_REN
 import test_oracle_reorder as T_REO
@@ -193,6 +194,22 @@ MUTANTS = {
         [("int ncombo = ptype == 0 ? 1 : (ptype == 1 ? 4 : 2);", "int ncombo = 1;")],
         [T_BC7.test_constant_colours, T_BC7.test_two_subset_partitions_exact,
          T_BC7.test_three_subset_partitions_exact]),
+    "decode places a texel with its neighbour slot's Gaussian": (
+        [("          int32_t o = perm[16 * g + u];\n          if (o < 0) continue;",
+          "          int32_t o = perm[16 * g + (u ^ 1)];\n          if (o < 0) continue;")],
+        [lambda O: T_PIPE.test_forced_format_blocks_are_layout_d(O, 1), T_PIPE.test_rate_streams_random_access_and_dropped_bands,
+         lambda O: T_LAY.test_bc7_round_trip_is_lossless_when_blocks_are_constant(O, 1)]),
+    "fixed codings write BC1 blocks before BC7 blocks": (
+        [("    for (int k = 0; k < OR_SH; k++)\n      if (or_layout_bc7(layout, j, k)) { or_bc7_encode(tex + 48 * k, dst); dst += 16; }\n"
+          "    for (int k = 0; k < OR_SH; k++)\n      if (!or_layout_bc7(layout, j, k)) { or_bc1_encode(tex + 48 * k, dst); dst += 8; }\n",
+          "    for (int k = 0; k < OR_SH; k++)\n      if (!or_layout_bc7(layout, j, k)) { or_bc1_encode(tex + 48 * k, dst); dst += 8; }\n"
+          "    for (int k = 0; k < OR_SH; k++)\n      if (or_layout_bc7(layout, j, k)) { or_bc7_encode(tex + 48 * k, dst); dst += 16; }\n")],
+        [T_LAY.test_mixed_b_decodes_each_block_with_its_format]),
+    "rate streams assembled in reverse mode order": (
+        [("    for (int m = 0; m < OR_MODES; m++) {\n      int64_t gbytes",
+          "    for (int m = OR_MODES - 1; m >= 0; m--) {\n      int64_t gbytes")],
+        [T_PIPE.test_rate_streams_random_access_and_dropped_bands,
+         lambda O: T_RATE.test_rate_targets_respect_budget(O, 24)]),
 }
 
 # Steps of the encoder's own search heuristic (the encoder specification, not the paper or the BC7
