@@ -230,29 +230,43 @@ HEURISTIC_MUTANTS = {
 }
 
 
-def _mutant_oracle(tmp_path, patches):
+def _build(path, patches):
     src = open(os.path.join(ORACLE, "gsc_oracle.c")).read()
     for old, new in patches:
         assert src.count(old) == 1, old
         src = src.replace(old, new)
-    c = tmp_path / "gsc_oracle_mutant.c"
+    c = path / "gsc_oracle_mutant.c"
     c.write_text(src)
-    so = tmp_path / "liboracle_mutant.so"
+    so = path / "liboracle_mutant.so"
     subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-pthread", "-fPIC",
                            "-shared", "-I", ORACLE, "-o", str(so), str(c), "-lm"])
-    spec = importlib.util.spec_from_file_location("oracle_mutant_%d" % abs(hash(str(tmp_path))),
-                                                  os.path.join(ORACLE, "oracle.py"))
+    return str(so)
+
+
+@pytest.fixture(scope="module")
+def mutant_libs(tmp_path_factory):
+    """Every planted copy, compiled in parallel once for the module."""
+    from concurrent.futures import ThreadPoolExecutor
+    jobs = {name: patches for name, (patches, _) in list(MUTANTS.items()) + list(HEURISTIC_MUTANTS.items())}
+    dirs = {name: tmp_path_factory.mktemp("mutant") for name in jobs}
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        futs = {name: ex.submit(_build, dirs[name], jobs[name]) for name in jobs}
+        return {name: f.result() for name, f in futs.items()}
+
+
+def _mutant_oracle(so):
+    spec = importlib.util.spec_from_file_location("oracle_mutant_%d" % abs(hash(so)), os.path.join(ORACLE, "oracle.py"))
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
-    mod.LIB_OVERRIDE = str(so)
+    mod.LIB_OVERRIDE = so
     mod.lib()
     return mod
 
 
 @pytest.mark.parametrize("name", list(MUTANTS))
-def test_a_planted_mistake_fails_a_pin(tmp_path, name):
-    patches, pins = MUTANTS[name]
-    M = _mutant_oracle(tmp_path, patches)
+def test_a_planted_mistake_fails_a_pin(mutant_libs, name):
+    _, pins = MUTANTS[name]
+    M = _mutant_oracle(mutant_libs[name])
     failed = []
     for pin in pins:
         try:
@@ -264,9 +278,9 @@ def test_a_planted_mistake_fails_a_pin(tmp_path, name):
 
 @pytest.mark.parametrize("name", list(HEURISTIC_MUTANTS))
 @pytest.mark.xfail(strict=True, reason="a step of the encoder's own heuristic: no pin outside the specification")
-def test_a_heuristic_change_is_not_caught_by_format_pins(tmp_path, name):
-    patches, pins = HEURISTIC_MUTANTS[name]
-    M = _mutant_oracle(tmp_path, patches)
+def test_a_heuristic_change_is_not_caught_by_format_pins(mutant_libs, name):
+    _, pins = HEURISTIC_MUTANTS[name]
+    M = _mutant_oracle(mutant_libs[name])
     failed = []
     for pin in pins:
         try:
