@@ -210,6 +210,16 @@ MUTANTS = {
           "    for (int m = OR_MODES - 1; m >= 0; m--) {\n      int64_t gbytes")],
         [T_PIPE.test_rate_streams_random_access_and_dropped_bands,
          lambda O: T_RATE.test_rate_targets_respect_budget(O, 24)]),
+    "rotation code picks the largest component without its absolute value": (
+        [("for (int a = 1; a < 4; a++) if (fabsf(u[a]) > fabsf(u[m])) m = a;",
+          "for (int a = 1; a < 4; a++) if (u[a] > u[m]) m = a;")],
+        [T_GEO.test_rotation_smallest_three]),
+    "rotation code without making the largest component positive": (
+        [("float sg = u[m] < 0.0f ? -1.0f : 1.0f;", "float sg = 1.0f;")],
+        [T_GEO.test_rotation_smallest_three]),
+    "opacity as the sigmoid of -t": (
+        [("double mu = 1.0 / (1.0 + exp(-(double)logit[i]));", "double mu = 1.0 / (1.0 + exp((double)logit[i]));")],
+        [T_REN.test_head_on_isotropic_splat_closed_form, T_REN.test_two_splats_blend_front_to_back]),
 }
 
 # Steps of the encoder's own search heuristic (the encoder specification, not the paper or the BC7
