@@ -192,3 +192,15 @@ def test_host_size_queries():
     assert lib.gsc_render_workspace_bytes(10, None, 0) == 0
     bad = gsc.camera(S.look_at([0.5, 0.5, -1.5], [0.5, 0.5, 0.5], 0, 1080))
     assert lib.gsc_render_workspace_bytes(10, ctypes.byref(bad), 0) == 0
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # no fallback: without the built library the binding raises instead of computing anything
+    from paper_2607_14513_gb300 import gsc
+    saved = gsc._lib
+    try:
+        gsc._lib = None
+        with pytest.raises(RuntimeError):
+            gsc.load(str(tmp_path / "libgsc.so"))
+    finally:
+        gsc._lib = saved
