@@ -120,6 +120,50 @@ def test_culling_never_drops_a_drawn_gaussian(O):
     assert culled_any > 0
 
 
+def test_culling_keeps_adversarial_chunks(O):
+    # the chunk rule against the renderer's own decision on chunks built to sit at its edges, for
+    # cameras along every axis and an oblique one: tiny splats a few pixels outside a side (only
+    # the pixel band protects them), large splats far outside a side (the box growth must reach
+    # the view from the near side), and chunks straddling the camera plane. A chunk that holds a
+    # Gaussian the renderer draws is never culled.
+    rng = np.random.default_rng(17)
+    centre = [0.5, 0.5, 0.5]
+    drawn = 0
+    for eye in ([0.5, 0.5, -1.5], [0.5, 0.5, 2.5], [-1.5, 0.5, 0.5], [2.5, 0.5, 0.5], [0.5, -1.5, 0.5],
+                [2.0, -1.0, 1.8]):
+        cam = S.look_at(eye, centre, 96, 64, fov_x_deg=60.0)
+        R = np.asarray(cam["R"], np.float64).reshape(3, 3)
+        t = np.asarray(cam["t"], np.float64)
+        f, cx, cy, W, H = float(cam["fx"]), float(cam["cx"]), float(cam["cy"]), cam["width"], cam["height"]
+        for trial in range(3000):
+            kind, side, m = trial % 3, rng.integers(4), 4
+            if kind < 2:
+                if kind == 0:   # tiny splats, 0-5 px outside
+                    scale = np.full((m, 3), np.exp(rng.uniform(np.log(1e-5), np.log(1e-3))))
+                    off, jit = rng.uniform(0, 5), rng.uniform(0, 1e-3)
+                else:           # large splats, 10-250 px outside
+                    scale = np.exp(rng.uniform(np.log(0.02), np.log(1.0), size=(m, 3)))
+                    off, jit = rng.uniform(10, 250), rng.uniform(0, 0.3)
+                z = rng.uniform(0.3, 5.0)
+                u = [-off, W + off, rng.uniform(0, W), rng.uniform(0, W)][side]
+                v = [rng.uniform(0, H), rng.uniform(0, H), -off, H + off][side]
+                camp = np.array([(u - cx) * z / f, (v - cy) * z / f, z])[None, :] + rng.normal(0, jit, size=(m, 3))
+            else:               # straddling the camera plane
+                scale = np.exp(rng.uniform(np.log(1e-3), np.log(0.3), size=(m, 3)))
+                camp = (np.array([rng.uniform(-2, 2), rng.uniform(-1.5, 1.5), rng.uniform(-0.4, 0.6)])[None, :]
+                        + rng.normal(0, rng.uniform(0.05, 0.6), size=(m, 3)))
+            pos = ((camp - t[None, :]) @ R).astype(np.float32)          # world = R^T (camera - t)
+            q = rng.normal(size=(m, 4)).astype(np.float32)
+            sc = scale.astype(np.float32)
+            if not any(O.splat_setup(pos[i], sc[i], q[i], cam).visible for i in range(m)):
+                continue
+            drawn += 1
+            e = np.zeros(8, np.float32)
+            e[0:3], e[3:6], e[6] = pos.min(axis=0), pos.max(axis=0), sc.max()
+            assert O.chunk_visible(e, cam), (eye, trial)
+    assert drawn > 5000
+
+
 def test_culling_cases(O):
     e = np.array([0.4, 0.4, 0.4, 0.6, 0.6, 0.6, 0.01, 0], np.float32)
     cam = S.look_at([0.5, 0.5, -1.5], [0.5, 0.5, 0.5], 64, 64)

@@ -220,6 +220,21 @@ MUTANTS = {
     "opacity as the sigmoid of -t": (
         [("double mu = 1.0 / (1.0 + exp(-(double)logit[i]));", "double mu = 1.0 / (1.0 + exp((double)logit[i]));")],
         [T_REN.test_head_on_isotropic_splat_closed_form, T_REN.test_two_splats_blend_front_to_back]),
+    "chunk box grown on its high side only": (
+        [("for (int a = 0; a < 3; a++) c[a] = ((k >> a) & 1) ? e[3 + a] + g : e[a] - g;",
+          "for (int a = 0; a < 3; a++) c[a] = ((k >> a) & 1) ? e[3 + a] + g : e[a];")],
+        [T_GEO.test_culling_keeps_adversarial_chunks]),
+    "chunk corners from one bit of the corner index": (
+        [("for (int a = 0; a < 3; a++) c[a] = ((k >> a) & 1) ? e[3 + a] + g : e[a] - g;",
+          "for (int a = 0; a < 3; a++) c[a] = ((k >> 1) & 1) ? e[3 + a] + g : e[a] - g;")],
+        [T_GEO.test_culling_keeps_adversarial_chunks]),
+    "chunks straddling the camera plane culled by the side test": (
+        [("if (front && (left || right || top || bottom)) return 0;", "if (left || right || top || bottom) return 0;")],
+        [T_GEO.test_culling_keeps_adversarial_chunks]),
+    "chunk side margin of 0 px": (
+        [("    if (!(u < -64.0f)) left = 0;\n    if (!(u > W + 64.0f)) right = 0;",
+          "    if (!(u < 0.0f)) left = 0;\n    if (!(u > W + 0.0f)) right = 0;")],
+        [T_GEO.test_culling_keeps_adversarial_chunks]),
 }
 
 # Steps of the encoder's own search heuristic (the encoder specification, not the paper or the BC7
