@@ -235,6 +235,12 @@ MUTANTS = {
         [("    if (!(u < -64.0f)) left = 0;\n    if (!(u > W + 64.0f)) right = 0;",
           "    if (!(u < 0.0f)) left = 0;\n    if (!(u > W + 0.0f)) right = 0;")],
         [T_GEO.test_culling_keeps_adversarial_chunks]),
+    "SH tolerance sum of the coefficients without the basis": (
+        [("aa += fabs(x * Y[k]);", "aa += fabs(x);")],
+        [T_SH.test_tolerance_sum_is_the_sum_of_absolute_terms]),
+    "render tolerance sum without the transmittance": (
+        [("ab[ch] += fabs(term);", "ab[ch] += fabs(gv * colour[3 * i + ch]);")],
+        [T_REN.test_two_splats_blend_front_to_back]),
 }
 
 # Steps of the encoder's own search heuristic (the encoder specification, not the paper or the BC7

@@ -56,6 +56,9 @@ def test_two_splats_blend_front_to_back(O):
     want = g[0] * c1 + (1 - _sig(t1) * g[0]) * g[1] * c2
     assert np.allclose(img[px, px], want, rtol=1e-5)
     assert np.isclose(tr[px, px], (1 - _sig(t1) * g[0]) * (1 - _sig(t2) * g[1]), rtol=1e-6)
+    # the error bound the GPU parity tests use: the sum of the blend's absolute terms
+    _, _, ab = O.render(pos, [[s] * 3] * 2, [[1, 0, 0, 0]] * 2, [t1, t2], np.stack([c1, c2]), cam, want_abs=True)
+    assert np.allclose(ab[px, px], g[0] * np.abs(c1) + (1 - _sig(t1) * g[0]) * g[1] * np.abs(c2), rtol=1e-5)
     # swapping the two positions swaps the order: the far splat is now the first colour
     img2, _ = O.render(pos[::-1].copy(), [[s] * 3] * 2, [[1, 0, 0, 0]] * 2, [t1, t2], np.stack([c1, c2]), cam)
     want2 = g[0] * c2 + (1 - _sig(t2) * g[0]) * g[1] * c1

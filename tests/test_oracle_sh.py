@@ -80,6 +80,23 @@ def test_degree_zero_and_dequantisation(O):
         assert np.max(np.abs(out[v] - x0 / (2 * np.sqrt(np.pi)))) < 1e-15
 
 
+def test_tolerance_sum_is_the_sum_of_absolute_terms(O):
+    # the bound the GPU parity tests scale their tolerance by: sum_k |x'_k Y_k(d)| per channel
+    rng = np.random.default_rng(6)
+    n = 30
+    tex = rng.integers(0, 256, size=(n, 16, 3)).astype(np.uint8)
+    sc = rng.uniform(0.1, 2.0, size=16).astype(np.float32)
+    dirs = _dirs(4, 9).astype(np.float32)
+    out, ab = O.eval_sh(tex, sc, dirs=dirs, want_abs=True)
+    x = (tex.astype(np.float64) - 128.0) / 255.0 * sc.astype(np.float64)[None, :, None]
+    for v in range(4):
+        d = dirs[v].astype(np.float64)
+        Y = O.sh_basis(*(d / np.linalg.norm(d)))
+        want = np.abs(x * Y[None, :, None]).sum(axis=1)
+        assert np.allclose(ab[v], want, rtol=1e-12, atol=0)
+        assert np.all(ab[v] >= np.abs(out[v]) - 1e-15)
+
+
 def test_camera_directions(O):
     rng = np.random.default_rng(5)
     n = 20
