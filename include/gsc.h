@@ -202,6 +202,24 @@ gsc_status gsc_decode_eval_sh(gsc_ctx* ctx, const gsc_stream_table* table, const
                               const int32_t* d_perm, const float* d_dirs, const float* d_pos, const float* d_cams,
                               int32_t V, int32_t out_order, float* d_rgb, void* stream);
 
+/* Sec. II and Sec. III-C: gsc_decode_eval_sh with the Gaussians' centres given in slot order.
+ * The reorder moves each Gaussian's position with its colour (Sec. III-C: no side data), so a
+ * coded scene can keep d_pos_slot [n_groups * 16][3] float, row s = the centre of the Gaussian in
+ * slot s (padding rows are not read); the evaluation then reads it contiguously instead of through
+ * the inverse permutation. Same results as gsc_decode_eval_sh with d_pos; d_pos_slot replaces
+ * d_pos (required with d_cams, ignored with d_dirs). Fastest when d_blocks, d_perm and d_pos_slot
+ * are 16-byte aligned (copied to shared memory by TMA bulk copies); 8-, 4- and 4-byte alignment
+ * is the minimum. d_rgb must be 16-byte aligned. */
+gsc_status gsc_decode_eval_sh_slots(gsc_ctx* ctx, const gsc_stream_table* table, const uint8_t* d_blocks,
+                                    const int32_t* d_perm, const float* d_dirs, const float* d_pos_slot,
+                                    const float* d_cams, int32_t V, int32_t out_order, float* d_rgb, void* stream);
+
+/* Centres in slot order for gsc_decode_eval_sh_slots: d_pos_slot[s] = d_pos[d_perm[s]] for the
+ * n_slots = n_groups * 16 slots of a slot order d_perm over n Gaussians (0 for padding slots).
+ * d_pos [n][3] and d_pos_slot [n_slots][3] float, 4-byte aligned. Asynchronous on `stream`. */
+gsc_status gsc_positions_to_slots(gsc_ctx* ctx, const float* d_pos, int64_t n, const int32_t* d_perm,
+                                  int64_t n_slots, float* d_pos_slot, void* stream);
+
 /* Same output as gsc_decode, sampled through CUDA BC1/BC7 texture objects (the GPU's
  * fixed-function block decoders, Sec. I): blocks are gathered into 2-D CUDA arrays
  * (16384 blocks per row) and read with point sampling; texel = rint(255 * f). The

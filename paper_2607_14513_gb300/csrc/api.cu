@@ -166,6 +166,7 @@ gsc_status ctx_new(int device, bool init_tables, gsc_ctx** out) {
     if (e == cudaSuccess) e = bc1_init_tables();
     if (e == cudaSuccess) e = bc7_init_tables();
     if (e == cudaSuccess) e = decode_init_tables();
+    if (e == cudaSuccess) e = eval3_init();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
   if (e != cudaSuccess) {
@@ -204,6 +205,8 @@ extern "C" gsc_status gsc_ctx_sync(gsc_ctx* c, void* stream) {
   int where = 0;
   const int chk = gsc_check_take(&where);  // checked build: a slot entry outside [-1, n)
   if (chk != 0) return (gsc_status)chk;
+  const int chk3 = eval3_err_take(&where);  // the tiled evaluation's checks and bounded waits
+  if (chk3 != 0) return (gsc_status)chk3;
   return GSC_OK;
 }
 
@@ -411,6 +414,38 @@ extern "C" gsc_status gsc_decode_eval_sh(gsc_ctx* c, const gsc_stream_table* tab
   GscTimed tm(c, T_EVAL, (cudaStream_t)stream);
   GSC_CUDA(launch_decode_eval(T, d_blocks, d_perm, d_dirs, d_pos, d_cams, V, out_order, d_rgb, c->sm_count,
                               (cudaStream_t)stream));
+  return GSC_OK;
+}
+
+extern "C" gsc_status gsc_decode_eval_sh_slots(gsc_ctx* c, const gsc_stream_table* table, const uint8_t* d_blocks,
+                                               const int32_t* d_perm, const float* d_dirs, const float* d_pos_slot,
+                                               const float* d_cams, int32_t V, int32_t out_order, float* d_rgb,
+                                               void* stream) {
+  GscRange gsc_range_("gsc_decode_eval_sh_slots");
+  if (!c) return GSC_ERR_INVALID_ARG;
+  DevTable T;
+  gsc_status s = make_dev_table(table, &T);
+  if (s != GSC_OK) return s;
+  if (V < 1 || V > 64 || out_order < 0 || out_order > 2) return GSC_ERR_INVALID_ARG;
+  if ((d_dirs == nullptr) == (d_cams == nullptr)) return GSC_ERR_INVALID_ARG;
+  if (d_cams && !d_pos_slot && T.n > 0) return GSC_ERR_INVALID_ARG;
+  if (T.n_groups > 0 && (!d_blocks || !d_perm || !d_rgb)) return GSC_ERR_INVALID_ARG;
+  if (!aligned(d_blocks, 8) || !aligned(d_rgb, 16) || !aligned(d_pos_slot, 4)) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  GscTimed tm(c, T_EVAL, (cudaStream_t)stream);
+  GSC_CUDA(launch_eval3(T, d_blocks, d_perm, d_dirs, nullptr, d_cams ? d_pos_slot : nullptr, d_cams, V, out_order,
+                        d_rgb, c->sm_count, (cudaStream_t)stream));
+  return GSC_OK;
+}
+
+extern "C" gsc_status gsc_positions_to_slots(gsc_ctx* c, const float* d_pos, int64_t n, const int32_t* d_perm,
+                                             int64_t n_slots, float* d_pos_slot, void* stream) {
+  GscRange gsc_range_("gsc_positions_to_slots");
+  if (!c || !n_ok(n) || n_slots != ceil_div64(n, 16) * 16) return GSC_ERR_INVALID_ARG;
+  if (n_slots > 0 && (!d_pos || !d_perm || !d_pos_slot)) return GSC_ERR_INVALID_ARG;
+  if (!aligned(d_pos, 4) || !aligned(d_pos_slot, 4) || !aligned(d_perm, 4)) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  GSC_CUDA(launch_pos_to_slots(d_pos, d_perm, n, n_slots, d_pos_slot, c->sm_count, (cudaStream_t)stream));
   return GSC_OK;
 }
 

@@ -183,6 +183,17 @@ cudaError_t launch_decode_eval(const DevTable& t, const uint8_t* blocks, const i
                                const float* pos, const float* cams, int V, int out_order, float* rgb, int sm_count,
                                cudaStream_t st, const int32_t* glist = nullptr, int64_t n_list = 0);
 cudaError_t launch_decode_blocks(const uint8_t* blocks, int64_t nblk, int format, uint8_t* rgba, cudaStream_t st);
+// eval.cu: the tiled fused decode + SH evaluation of whole scenes. pos: original order [n][3];
+// pos_slot: slot order [n_groups * 16][3] (one of them when cams are given).
+cudaError_t eval3_init();
+cudaError_t launch_eval3(const DevTable& T, const uint8_t* blocks, const int32_t* perm, const float* dirs,
+                         const float* pos, const float* pos_slot, const float* cams, int V, int out_order, float* rgb,
+                         int sm_count, cudaStream_t st);
+// takes and clears the first error the tiled kernel recorded on the current device (0 = none)
+int eval3_err_take(int* where);
+size_t eval3_smem_bytes();
+cudaError_t launch_pos_to_slots(const float* pos, const int32_t* perm, int64_t n, int64_t ns, float* out, int sm_count,
+                                cudaStream_t st);
 gsc_status decode_tex_run(gsc_ctx* ctx, const DevTable& t, const uint8_t* blocks, const int32_t* perm,
                           uint8_t* texels, cudaStream_t st);
 void tex_cache_free(gsc_ctx* ctx);

@@ -137,6 +137,8 @@ _SIGS = {
                    C.c_size_t, _P],
     "gsc_decode": [_P, C.POINTER(StreamTable), _P, _P, _P, _P],
     "gsc_decode_eval_sh": [_P, C.POINTER(StreamTable), _P, _P, _P, _P, _P, C.c_int32, C.c_int32, _P, _P],
+    "gsc_decode_eval_sh_slots": [_P, C.POINTER(StreamTable), _P, _P, _P, _P, _P, C.c_int32, C.c_int32, _P, _P],
+    "gsc_positions_to_slots": [_P, _P, C.c_int64, _P, C.c_int64, _P, _P],
     "gsc_decode_tex": [_P, C.POINTER(StreamTable), _P, _P, _P, _P],
     "gsc_tex_scene_create": [_P, C.POINTER(StreamTable), _P, _P, _P, C.POINTER(C.c_void_p), _P],
     "gsc_tex_scene_destroy": [_P],
@@ -362,6 +364,31 @@ def gsc_decode_eval_sh(ctx, table, blocks, perm, dirs=None, pos=None, cams=None,
     _check(ctx.lib.gsc_decode_eval_sh(ctx.h, C.byref(table), _ptr(blocks), _ptr(perm), _ptr(dirs), _ptr(pos),
                                       _ptr(cams), V, out_order, _ptr(rgb), _stream(stream)), "gsc_decode_eval_sh")
     return rgb
+
+
+def gsc_decode_eval_sh_slots(ctx, table, blocks, perm, dirs=None, pos_slot=None, cams=None,
+                             out_order=OUT_VIEW_MAJOR, out=None, stream=None):
+    """gsc_decode_eval_sh with centres in slot order (pos_slot [n_groups * 16, 3])."""
+    import torch
+    src = dirs if dirs is not None else cams
+    V = src.shape[0]
+    n, ns = table.n, table.n_groups * 16
+    shape = {OUT_VIEW_MAJOR: (V, n, 3), OUT_SLOT_ORDER: (V, ns, 3), OUT_GAUSS_MAJOR: (n, V, 3)}[out_order]
+    rgb = out if out is not None else torch.empty(shape, dtype=torch.float32, device=blocks.device)
+    _check(ctx.lib.gsc_decode_eval_sh_slots(ctx.h, C.byref(table), _ptr(blocks), _ptr(perm), _ptr(dirs),
+                                            _ptr(pos_slot), _ptr(cams), V, out_order, _ptr(rgb), _stream(stream)),
+           "gsc_decode_eval_sh_slots")
+    return rgb
+
+
+def gsc_positions_to_slots(ctx, pos, perm, out=None, stream=None):
+    """Centres in slot order: out[s] = pos[perm[s]] (zeros for padding slots)."""
+    import torch
+    n, ns = pos.shape[0], perm.shape[0]
+    res = out if out is not None else torch.empty((ns, 3), dtype=torch.float32, device=pos.device)
+    _check(ctx.lib.gsc_positions_to_slots(ctx.h, _ptr(pos), n, _ptr(perm), ns, _ptr(res), _stream(stream)),
+           "gsc_positions_to_slots")
+    return res
 
 
 def gsc_decode_tex(ctx, table, blocks, perm, stream=None):
