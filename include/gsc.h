@@ -207,9 +207,8 @@ gsc_status gsc_decode_eval_sh(gsc_ctx* ctx, const gsc_stream_table* table, const
  * coded scene can keep d_pos_slot [n_groups * 16][3] float, row s = the centre of the Gaussian in
  * slot s (padding rows are not read); the evaluation then reads it contiguously instead of through
  * the inverse permutation. Same results as gsc_decode_eval_sh with d_pos; d_pos_slot replaces
- * d_pos (required with d_cams, ignored with d_dirs). Fastest when d_blocks, d_perm and d_pos_slot
- * are 16-byte aligned (copied to shared memory by TMA bulk copies); 8-, 4- and 4-byte alignment
- * is the minimum. d_rgb must be 16-byte aligned. */
+ * d_pos (required with d_cams, ignored with d_dirs). d_blocks 8-byte and d_pos_slot 4-byte
+ * aligned; d_rgb 16-byte aligned. */
 gsc_status gsc_decode_eval_sh_slots(gsc_ctx* ctx, const gsc_stream_table* table, const uint8_t* d_blocks,
                                     const int32_t* d_perm, const float* d_dirs, const float* d_pos_slot,
                                     const float* d_cams, int32_t V, int32_t out_order, float* d_rgb, void* stream);

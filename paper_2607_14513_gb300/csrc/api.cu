@@ -166,7 +166,6 @@ gsc_status ctx_new(int device, bool init_tables, gsc_ctx** out) {
     if (e == cudaSuccess) e = bc1_init_tables();
     if (e == cudaSuccess) e = bc7_init_tables();
     if (e == cudaSuccess) e = decode_init_tables();
-    if (e == cudaSuccess) e = eval3_init();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
   if (e != cudaSuccess) {
@@ -205,8 +204,6 @@ extern "C" gsc_status gsc_ctx_sync(gsc_ctx* c, void* stream) {
   int where = 0;
   const int chk = gsc_check_take(&where);  // checked build: a slot entry outside [-1, n)
   if (chk != 0) return (gsc_status)chk;
-  const int chk3 = eval3_err_take(&where);  // the tiled evaluation's checks and bounded waits
-  if (chk3 != 0) return (gsc_status)chk3;
   return GSC_OK;
 }
 
@@ -433,8 +430,8 @@ extern "C" gsc_status gsc_decode_eval_sh_slots(gsc_ctx* c, const gsc_stream_tabl
   if (!aligned(d_blocks, 8) || !aligned(d_rgb, 16) || !aligned(d_pos_slot, 4)) return GSC_ERR_INVALID_ARG;
   GSC_CUDA(cudaSetDevice(c->device));
   GscTimed tm(c, T_EVAL, (cudaStream_t)stream);
-  GSC_CUDA(launch_eval3(T, d_blocks, d_perm, d_dirs, nullptr, d_cams ? d_pos_slot : nullptr, d_cams, V, out_order,
-                        d_rgb, c->sm_count, (cudaStream_t)stream));
+  GSC_CUDA(launch_decode_eval(T, d_blocks, d_perm, d_dirs, nullptr, d_cams, V, out_order, d_rgb, c->sm_count,
+                              (cudaStream_t)stream, nullptr, 0, d_cams ? d_pos_slot : nullptr));
   return GSC_OK;
 }
 

@@ -373,7 +373,8 @@ __global__ void __launch_bounds__(EVAL_THREADS, EVAL_MIN_BLOCKS) k_eval2(DevTabl
                                                const int32_t* __restrict__ perm, const float* __restrict__ dirs,
                                                const float* __restrict__ pos, const float* __restrict__ cams, int V,
                                                int out_order, float* __restrict__ rgb,
-                                               const int32_t* __restrict__ glist, int64_t n_list) {
+                                               const int32_t* __restrict__ glist, int64_t n_list,
+                                               const float* __restrict__ pos_slot) {
   __shared__ DecTables S;
   __shared__ uint32_t tile[EVAL_THREADS / 32][WTILE];
   __shared__ uint4 s_ep[EVAL_THREADS][3];
@@ -399,8 +400,13 @@ __global__ void __launch_bounds__(EVAL_THREADS, EVAL_MIN_BLOCKS) k_eval2(DevTabl
     const int64_t g = group_of(pr);
     return valid(g) ? checked_slot(__ldg(perm + g * 16 + kt), T.n, g * 16 + kt) : -1;
   };
-  auto pos_at = [&](int32_t o) -> float3 {
+  // centre of slot entry o at tile pair pr: in slot order (pos_slot) or gathered through o
+  auto pos_at = [&](int64_t pr_, int32_t o) -> float3 {
     if (!CAMS || o < 0) return make_float3(0.f, 0.f, 0.f);
+    if (pos_slot) {
+      const int64_t s_ = group_of(pr_) * 16 + kt;
+      return make_float3(__ldg(pos_slot + 3 * s_), __ldg(pos_slot + 3 * s_ + 1), __ldg(pos_slot + 3 * s_ + 2));
+    }
     return make_float3(__ldg(pos + 3 * (int64_t)o), __ldg(pos + 3 * (int64_t)o + 1), __ldg(pos + 3 * (int64_t)o + 2));
   };
   int64_t pr = (int64_t)blockIdx.x * nw + w;
@@ -409,7 +415,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, EVAL_MIN_BLOCKS) k_eval2(DevTabl
   raw.w = make_uint4(0u, 0u, 0u, 0u);
   if (pr < npairs && valid(group_of(pr))) raw = fetch_block<KIND>(T, blocks, group_of(pr), kt);
   int32_t o = perm_at(pr), o1 = perm_at(pr + step);
-  float3 p = pos_at(o);
+  float3 p = pos_at(pr, o);
   for (; pr < npairs; pr += step) {
     const int64_t g = group_of(pr);
     const bool live = valid(g);
@@ -419,7 +425,7 @@ __global__ void __launch_bounds__(EVAL_THREADS, EVAL_MIN_BLOCKS) k_eval2(DevTabl
     rawn.kind = 0;
     rawn.w = make_uint4(0u, 0u, 0u, 0u);
     if (prn < npairs && valid(group_of(prn))) rawn = fetch_block<KIND>(T, blocks, group_of(prn), kt);
-    const float3 pn = pos_at(o1);
+    const float3 pn = pos_at(prn, o1);
     const int32_t o2 = perm_at(prn + step);
     {
       uint32_t tx[16];
@@ -458,6 +464,12 @@ static int kind_of(const DevTable& T) {
   if (T.n_streams == 1 && T.bands[0] == 16 && T.byte_offset[0] == 0) return T.bc7[0] == 16 ? 7 : (T.bc7[0] == 0 ? 1 : 0);
   return 0;
 }
+// kind for the software decoders: the all-BC7 fast path loads whole 16-byte blocks, so blocks that
+// are only 8-byte aligned (the API's minimum) take the stream path's 8-byte loads
+static int kind_of(const DevTable& T, const void* blocks) {
+  const int k = kind_of(T);
+  return (k == 7 && ((uintptr_t)blocks & 15u) != 0) ? 0 : k;
+}
 
 // CTAs of `warps` warps, one pair of groups per warp per step; at most 64 warps per SM.
 static int eval_grid(int64_t n_groups, int sm_count, int warps = 8) {
@@ -474,7 +486,7 @@ cudaError_t launch_decode(const DevTable& T, const uint8_t* blocks, const int32_
 #define DEC_LAUNCH(L)                                                                              \
   do {                                                                                             \
     gsc_count_launch();                                                                            \
-    switch (kind_of(T)) {                                                                          \
+    switch (kind_of(T, blocks)) {                                                                  \
       case 7: k_decode2<7, L><<<grid, 256, 0, st>>>(T, blocks, perm, texels); break;               \
       case 1: k_decode2<1, L><<<grid, 256, 0, st>>>(T, blocks, perm, texels); break;               \
       default: k_decode2<0, L><<<grid, 256, 0, st>>>(T, blocks, perm, texels); break;              \
@@ -489,10 +501,10 @@ cudaError_t launch_decode(const DevTable& T, const uint8_t* blocks, const int32_
 
 cudaError_t launch_decode_eval(const DevTable& T, const uint8_t* blocks, const int32_t* perm, const float* dirs,
                                const float* pos, const float* cams, int V, int out_order, float* rgb, int sm_count,
-                               cudaStream_t st, const int32_t* glist, int64_t n_list) {
+                               cudaStream_t st, const int32_t* glist, int64_t n_list, const float* pos_slot) {
   if (T.n_groups == 0 || (glist && n_list == 0)) return cudaSuccess;
   const int grid = eval_grid(glist ? n_list : T.n_groups, sm_count, EVAL_THREADS / 32);
-  const int kind = kind_of(T);
+  const int kind = kind_of(T, blocks);
   // runtime view count only: a compile-time 8-view form raised this kernel to 140 registers (one
   // resident CTA fewer) and measured no faster (the texture kernel does use one)
 #define EVAL_LAUNCH(K, C, L)                                                                                     \
@@ -500,10 +512,10 @@ cudaError_t launch_decode_eval(const DevTable& T, const uint8_t* blocks, const i
     gsc_count_launch();                                                                                          \
     if (glist)                                                                                                   \
       k_eval2<K, C, 0, L, true><<<grid, EVAL_THREADS, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order,   \
-                                                               rgb, glist, n_list);                              \
+                                                               rgb, glist, n_list, pos_slot);                    \
     else                                                                                                         \
       k_eval2<K, C, 0, L, false><<<grid, EVAL_THREADS, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order,  \
-                                                                rgb, nullptr, 0);                                \
+                                                                rgb, nullptr, 0, pos_slot);                      \
   } while (0)
 #define EVAL_KINDS(C, L)                                                                                         \
   do {                                                                                                           \
@@ -520,6 +532,29 @@ cudaError_t launch_decode_eval(const DevTable& T, const uint8_t* blocks, const i
 #undef EVAL_LAYOUTS
 #undef EVAL_KINDS
 #undef EVAL_LAUNCH
+  return cudaGetLastError();
+}
+
+// Positions in slot order: out[s] = pos[perm[s]] (zeros for padding slots).
+__global__ void k_pos_to_slots(const float* __restrict__ pos, const int32_t* __restrict__ perm, int64_t n, int64_t ns,
+                               float* __restrict__ out) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
+    int32_t o = perm[s];
+    o = checked_slot(o, n, s);
+    float x = 0.f, y = 0.f, z = 0.f;
+    if (o >= 0) { x = pos[3 * (int64_t)o]; y = pos[3 * (int64_t)o + 1]; z = pos[3 * (int64_t)o + 2]; }
+    out[3 * s] = x; out[3 * s + 1] = y; out[3 * s + 2] = z;
+  }
+}
+
+cudaError_t launch_pos_to_slots(const float* pos, const int32_t* perm, int64_t n, int64_t ns, float* out, int sm_count,
+                                cudaStream_t st) {
+  if (ns <= 0) return cudaSuccess;
+  int64_t grid = (ns + 255) / 256;
+  const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 1) * 8;
+  if (grid > cap) grid = cap;
+  gsc_count_launch();
+  k_pos_to_slots<<<(int)grid, 256, 0, st>>>(pos, perm, n, ns, out);
   return cudaGetLastError();
 }
 

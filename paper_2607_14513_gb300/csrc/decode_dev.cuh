@@ -219,25 +219,25 @@ __device__ __forceinline__ float u23(uint32_t v, int c) {
 }
 
 // SH basis polynomials without their constants (the constants, with their signs, are folded
-// into the per-coefficient dequantisation factors s_k / 255 * C_k), for two views at once.
+// into the per-coefficient dequantisation factors s_k / 255 * C_k), for two directions at once.
+// The directions are unit vectors, so x^2 + y^2 + z^2 = 1 shortens the band-2 and band-3 terms:
+// 2zz - xx - yy = 3zz - 1, 4zz - xx - yy = 5zz - 1, 2zz - 3xx - 3yy = 5zz - 3.
 __device__ __forceinline__ void sh_poly2(float2 x, float2 y, float2 z, float2 (&P)[16]) {
   const float2 xx = __fmul2_rn(x, x), yy = __fmul2_rn(y, y), zz = __fmul2_rn(z, z);
   const float2 xy = __fmul2_rn(x, y), yz = __fmul2_rn(y, z), xz = __fmul2_rn(x, z);
-  const float2 two = make_float2(2.f, 2.f), three = make_float2(3.f, 3.f), four = make_float2(4.f, 4.f);
-  const float2 xpy = __fadd2_rn(xx, yy);
-  const float2 nxpy = make_float2(-xpy.x, -xpy.y), nyy = make_float2(-yy.x, -yy.y);
-  const float2 xmy = __fadd2_rn(xx, nyy);
-  const float2 t4 = __ffma2_rn(four, zz, nxpy);                                  // 4zz - xx - yy
+  const float2 m1 = make_float2(-1.f, -1.f), five = make_float2(5.f, 5.f);
+  const float2 xmy = __ffma2_rn(yy, m1, xx);                                        // xx - yy
+  const float2 t5 = __ffma2_rn(five, zz, m1);                                        // 5zz - 1
   P[0] = make_float2(1.f, 1.f);
   P[1] = y; P[2] = z; P[3] = x;
-  P[4] = xy; P[5] = yz; P[6] = __ffma2_rn(two, zz, nxpy); P[7] = xz; P[8] = xmy; // 2zz - xx - yy
-  P[9] = __fmul2_rn(y, __ffma2_rn(three, xx, nyy));                              // y (3xx - yy)
+  P[4] = xy; P[5] = yz; P[6] = __ffma2_rn(make_float2(3.f, 3.f), zz, m1); P[7] = xz; P[8] = xmy;  // 3zz - 1
+  P[9] = __fmul2_rn(y, __ffma2_rn(make_float2(3.f, 3.f), xx, make_float2(-yy.x, -yy.y)));      // y (3xx - yy)
   P[10] = __fmul2_rn(xy, z);
-  P[11] = __fmul2_rn(y, t4);
-  P[12] = __fmul2_rn(z, __ffma2_rn(make_float2(-3.f, -3.f), xpy, __fmul2_rn(two, zz)));  // z (2zz - 3xx - 3yy)
-  P[13] = __fmul2_rn(x, t4);
+  P[11] = __fmul2_rn(y, t5);
+  P[12] = __fmul2_rn(z, __ffma2_rn(five, zz, make_float2(-3.f, -3.f)));                 // z (5zz - 3)
+  P[13] = __fmul2_rn(x, t5);
   P[14] = __fmul2_rn(z, xmy);
-  P[15] = __fmul2_rn(x, __ffma2_rn(make_float2(-3.f, -3.f), yy, xx));            // x (xx - 3yy)
+  P[15] = __fmul2_rn(x, __ffma2_rn(make_float2(-3.f, -3.f), yy, xx));                  // x (xx - 3yy)
 }
 
 static __constant__ float c_shc[16] = {SH_C0, -SH_C1, SH_C1, -SH_C1, SH_C2A, -SH_C2A, SH_C2B, -SH_C2A, SH_C2C,

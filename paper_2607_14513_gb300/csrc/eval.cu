@@ -2,65 +2,76 @@
 // (Sec. I: random access by block index x block size; Sec. II: c(f) = H w(f - p);
 // Sec. III-B: BC1 / BC7 formats; Sec. IV-B: block layouts and fixed-rate streams).
 //
-// A persistent CTA works through tiles of E_TG groups (E_T slots, E_T blocks):
-//  1. staging: the tile's blocks, slot entries and slot-ordered positions land in shared memory
-//     through TMA bulk copies (cp.async.bulk completing on an mbarrier), issued one tile ahead.
-//     Rate streams (blocks at per-stream offsets) and inputs that are not 16-byte aligned use
-//     per-thread asynchronous copies (cp.async) instead, also one tile ahead.
-//  2. classification: every block gets a class -- BC7 mode 0..7 (mode 4 split by its
-//     index-selection bit), the reserved BC7 mode, BC1, or a coefficient the stream drops --
-//     and joins that class's list (warp-aggregated shared-memory atomics).
-//  3. decode: a warp takes 32 blocks of one class at a time and runs that class's decoder, whose
-//     field positions, widths and subset count are compile-time constants; the texels go to a
-//     Gaussian-major tile (slot row, coefficient column).
-//  4. evaluation: every thread evaluates two Gaussians of the tile. The two share each packed
-//     FP32x2 operation lane for lane (coefficients, directions, bases, accumulators), so no
-//     operand is broadcast, and per (Gaussian, view) the operations are those of the
-//     single-Gaussian evaluation in decode.cu, in the same order: the colours are bit-identical.
+// One persistent CTA per SM, warp-specialised, works through tiles of E_TG groups (E_T slots,
+// E_T blocks) held in a ring of E_NS shared-memory slots:
+//  - producer warps (E_PW): stage the tile's blocks into the slot (TMA bulk copy completing on an
+//    mbarrier, E_NS tiles ahead; per-thread cp.async for rate streams and unaligned blocks),
+//    give every block a class -- BC7 mode 0..7 (mode 4 split by its index-selection bit), the
+//    reserved BC7 mode, BC1, or a coefficient the stream drops -- and decode the blocks 32 of one
+//    class at a time with that class's own decoder (field positions, widths and subset counts are
+//    compile-time constants) into a Gaussian-major tile (slot row, coefficient column);
+//  - consumer warps (E_CW): evaluate two Gaussians per thread from the decoded tile; the two share
+//    each packed FP32x2 operation lane for lane (coefficients, directions, bases, accumulators),
+//    so no operand is broadcast, and per (Gaussian, view) the operations are those of the
+//    single-Gaussian evaluation in decode.cu, in the same order: the colours are bit-identical.
+// Producers and consumers hand slots over through mbarriers (tile full / tile empty), so the
+// integer-heavy decode of one tile runs beside the floating-point evaluation of another.
 #include <stddef.h>
 
+#include "bc7_class.cuh"
 #include "decode_dev.cuh"
 #include "layout.cuh"
 
 namespace {
 
-constexpr int E_NT = 192;         // threads per CTA
-constexpr int E_NW = E_NT / 32;   // warps per CTA
-constexpr int E_T = 2 * E_NT;     // slots (and blocks) per tile: two Gaussians per thread
-constexpr int E_TG = E_T / 16;    // groups per tile
-constexpr int E_ROW = 20;         // tile words per slot row (16 coefficients + 4 to spread banks)
-constexpr int E_GRP = 16 * E_ROW + 4;  // tile words per group
+constexpr int E_PW = 8;                  // producer warps (two warpgroups)
+constexpr int E_CW = 8;                  // consumer warps (two warpgroups)
+// registers per thread: launched with 128, producers give some up and consumers take them
+// (E_PT * E_PREG + E_CT * E_CREG must not exceed E_NT * 128)
+constexpr int E_PREG = 88, E_CREG = 168;
+constexpr int E_PT = 32 * E_PW;          // producer threads
+constexpr int E_CT = 32 * E_CW;          // consumer threads
+constexpr int E_NT = E_PT + E_CT;        // threads per CTA
+constexpr int E_T = 2 * E_CT;            // slots (and blocks) per tile: two Gaussians per consumer thread
+constexpr int E_TG = E_T / 16;           // groups per tile
+constexpr int E_NS = 3;                  // tiles in flight (ring slots)
+constexpr int E_ROW = 20;                // tile words per slot row (16 coefficients + 4 to spread banks)
+constexpr int E_GRP = 16 * E_ROW + 4;    // tile words per group
 constexpr int E_NCLS = 12;
-enum { CL_M4S = 8, CL_RES = 9, CL_BC1 = 10, CL_DROP = 11 };
 constexpr int E_MAXV = 64;
-// a bounded wait for the staged tile: far beyond any copy's latency
+// bounded waits on the ring's barriers: far beyond any copy's or tile's latency
 constexpr uint32_t E_WAIT_LIMIT = 1u << 22;
+constexpr int E_PBAR = 1;                // named barrier of the producer warps
 
-struct EStage {
-  uint4 blk[E_T];       // BC7 blocks (16 B), or BC1 blocks (8 B, packed from the start: all-BC1 codings)
-  int32_t perm[E_T];
-  float pos[E_T * 3];   // slot-ordered positions
-  uint8_t cls[E_T];     // rate streams: format of each block as located (BC7 / BC1 / dropped)
+struct ESlot {
+  uint4 blk[E_T];                  // BC7 blocks (16 B), or BC1 blocks (8 B, packed from the start: all-BC1 codings)
+  int32_t perm[E_T];               // slot entries of the tile
+  float pos[E_T * 3];              // slot-ordered centres of the tile (when given in slot order)
+  uint8_t cls[E_T];                // rate streams: format of each block as located (BC7 / BC1 / dropped)
+  uint32_t tile[E_TG * E_GRP];     // decoded texels, Gaussian-major
 };
 
 struct ESmem {
-  EStage stage[2];
-  uint32_t tile[E_TG * E_GRP];
+  ESlot slot[E_NS];
   uint16_t list[E_NCLS][E_T];
   int cnt[2][E_NCLS];
-  uint4 ep[E_NT][3];            // per-lane endpoint slots of multi-subset blocks
-  float4 cxy[E_MAXV];           // per view (x, x, y, y) of the camera centre or direction
-  float2 cz[E_MAXV];            // (z, z)
-  float2 deq[16];               // (f_k, f_k), f_k = s_k / 255 * C_k
+  alignas(64) uint4 ep[E_PT][4];   // per-lane endpoint / palette slots (64-byte aligned)
+  float4 cxy[E_MAXV];              // per view (x, x, y, y) of the camera centre or direction
+  float2 cz[E_MAXV];               // (z, z)
+  float2 deq[16];                  // (f_k, f_k), f_k = s_k / 255 * C_k
+  float2 deqF[16], deqC[16];       // (f_k 2^133, f_k 2^133) and (-128 f_k, -128 f_k): one-FMA dequantisation
+  int ffma_deq;                    // every f_k 2^133 finite: the one-FMA form applies
   DecTables S;
-  unsigned long long mbar[2];
+  unsigned long long blk_full[E_NS], tile_full[E_NS], tile_empty[E_NS];
 };
 
-static_assert(sizeof(EStage) % 16 == 0, "stage sections must stay 16-byte aligned for TMA");
-static_assert(offsetof(EStage, perm) % 16 == 0 && offsetof(EStage, pos) % 16 == 0, "TMA destinations");
-static_assert(offsetof(ESmem, tile) % 16 == 0 && (E_GRP * 4) % 16 == 0 && (E_ROW * 4) % 16 == 0, "tile rows");
-// two CTAs per SM: 228 KB of shared memory, 1 KB reserved per CTA
-static_assert(sizeof(ESmem) <= 113 * 1024, "shared memory of two resident CTAs");
+static_assert(sizeof(ESlot) % 16 == 0 && offsetof(ESlot, tile) % 16 == 0 && offsetof(ESlot, perm) % 16 == 0 &&
+                  offsetof(ESlot, pos) % 16 == 0, "TMA destinations and tile rows");
+static_assert((E_GRP * 4) % 16 == 0 && (E_ROW * 4) % 16 == 0, "tile rows");
+static_assert(sizeof(ESmem) <= 227 * 1024, "shared memory of one CTA");
+static_assert(E_PT * E_PREG + E_CT * E_CREG <= E_NT * 128, "register split within the launch's registers");
+static_assert(E_PW % 4 == 0 && E_CW % 4 == 0, "setmaxnreg acts on whole warpgroups");
+static_assert(offsetof(ESmem, ep) % 64 == 0, "palette slots are addressed by OR-ing a 6-bit offset");
 
 struct EArgs {
   DevTable T;
@@ -71,11 +82,13 @@ struct EArgs {
   const float* dirs;
   const float* cams;
   float* rgb;
-  int V, out_order, tma;
+  int V, out_order;
+  int tma_blk;   // blocks staged by TMA (16-byte aligned, one format)
+  int tma_meta;  // slot entries and slot-ordered centres staged by TMA (16-byte aligned)
 };
 
 // First error this translation unit's kernels detected (code, where): a slot entry outside
-// [-1, n) in the checked build, or a staged tile that never arrived. Taken by gsc_ctx_sync.
+// [-1, n) in the checked build, or a ring barrier that never completed. Taken by gsc_ctx_sync.
 __device__ int g_eval_err[2];
 __device__ __forceinline__ void eval_record(int code, int where) {
   if (atomicCAS(&g_eval_err[0], 0, code) == 0) g_eval_err[1] = where;
@@ -116,122 +129,16 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// ---- class decoders ---------------------------------------------------------------------------
-// bits [C, C + 64) of the 128-bit block, C a compile-time constant
-template <int C>
-__device__ __forceinline__ uint64_t shr128c(uint64_t lo, uint64_t hi) {
-  if (C == 0) return lo;
-  if (C >= 64) return hi >> (C >= 64 ? C - 64 : 0);
-  return (lo >> (C & 63)) | (hi << ((64 - C) & 63));
-}
-
-// BC7 index weight for index i of a `bits`-wide index: the 2- and 3-bit tables are byte
-// permutes of constants (index 0 weighs 0, so the upper bytes of the permute are 0).
-template <int BITS>
-__device__ __forceinline__ uint32_t wgt_of(uint32_t i, const DecTables* S) {
-  if (BITS == 2) return __byte_perm(0x402B1500u, 0u, i);
-  if (BITS == 3) return __byte_perm(0x1B120900u, 0x40372E25u, i);
-  return S->wt[32 + i];
-}
-
-// One BC7 block of class CL (mode CL, or mode 4 with the index-selection bit set) into 16
-// texels r | g << 8 | b << 16 (alpha byte unspecified). The arithmetic is that of bc7_block in
-// decode_dev.cuh: endpoints as 4x-scaled 16-bit lanes so that ((64 - w) e0 + w e1 + 32) >> 6 of
-// two channels is one multiply-add, index streams re-spaced to a fixed width per texel.
-template <int CL>
-__device__ __forceinline__ void bc7_class_block(uint64_t lo, uint64_t hi, uint32_t (&tx)[16], const DecTables* S,
-                                                uint4* ep) {
-  constexpr int mode = CL == CL_M4S ? 4 : CL;
-  constexpr DModeInfo D = d_mode_info(mode);
-  constexpr int ns = D.ns, pb = D.pb, rb = D.rb, isb = D.isb, cb = D.cb, ab = D.ab, epb = D.epb, spb = D.spb;
-  constexpr int ib = D.ib, ib2 = D.ib2;
-  constexpr bool swap = CL == CL_M4S;  // colour indices from the 3-bit stream
-  constexpr int hp = epb | spb, nb = cb + hp, na = ab + epb;
-  constexpr int pos0 = mode + 1;
-  constexpr int cstart = pos0 + pb + rb + isb, astart = cstart + 6 * ns * cb, pstart = astart + 2 * ns * ab;
-  constexpr int istart = pstart + (epb ? 2 * ns : (spb ? ns : 0));
-  const uint32_t w0 = (uint32_t)lo;
-  const int part = pb ? (int)((w0 >> pos0) & ((1u << pb) - 1u)) : 0;
-  const int rot = rb ? (int)((w0 >> (pos0 + pb)) & 3u) : 0;
-  uint32_t pm = 0u;
-  int a1 = 16, a2 = 16;
-  if (ns == 2) { pm = S->part2[part]; a1 = S->anc2[part]; }
-  if (ns == 3) { pm = S->part3[part]; a1 = S->anc3a[part]; a2 = S->anc3b[part]; }
-  const uint32_t pbits = (uint32_t)shr128c<pstart>(lo, hi);
-  const uint32_t fr = (uint32_t)shr128c<cstart>(lo, hi), fg = (uint32_t)shr128c<cstart + 2 * ns * cb>(lo, hi);
-  const uint32_t fb = (uint32_t)shr128c<cstart + 4 * ns * cb>(lo, hi);
-  const uint32_t fa = ab ? (uint32_t)shr128c<astart>(lo, hi) : 0u;
-  constexpr uint32_t cm = (1u << cb) - 1u, amk = ab ? (1u << ab) - 1u : 0u;
-  constexpr int cl8 = 8 - nb, cr8 = 2 * nb - 8, al8 = ab ? 8 - na : 0, ar8 = ab ? 2 * na - 8 : 0;
-  uint4 e_one = make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-  for (int s = 0; s < ns; s++) {
-    const uint32_t p0 = epb ? ((pbits >> (2 * s)) & 1u) : (spb ? ((pbits >> s) & 1u) : 0u);
-    const uint32_t p1 = epb ? ((pbits >> (2 * s + 1)) & 1u) : p0;
-    const int sh0 = 2 * s * cb, sh1 = sh0 + cb;
-    uint32_t v0[3], v1[3];
-    const uint32_t f3[3] = {fr, fg, fb};
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-      const uint32_t c0 = (((f3[c] >> sh0) & cm) << hp) | (hp ? p0 : 0u);
-      const uint32_t c1 = (((f3[c] >> sh1) & cm) << hp) | (hp ? p1 : 0u);
-      v0[c] = (c0 << cl8) | (c0 >> cr8);
-      v1[c] = (c1 << cl8) | (c1 >> cr8);
-    }
-    uint32_t aa0 = 255u, aa1 = 255u;
-    if (ab) {
-      const uint32_t c0 = (((fa >> (2 * s * ab)) & amk) << epb) | (epb ? p0 : 0u);
-      const uint32_t c1 = (((fa >> ((2 * s + 1) * ab)) & amk) << epb) | (epb ? p1 : 0u);
-      aa0 = (c0 << al8) | (c0 >> ar8);
-      aa1 = (c1 << al8) | (c1 >> ar8);
-    }
-    const uint32_t e0rg = (v0[0] | (v0[1] << 16)) << 2, e0ba = (v0[2] | (aa0 << 16)) << 2;
-    const uint32_t e1rg = (v1[0] | (v1[1] << 16)) << 2, e1ba = (v1[2] | (aa1 << 16)) << 2;
-    const uint4 e = make_uint4(64u * e0rg + 0x00800080u, e1rg - e0rg, 64u * e0ba + 0x00800080u, e1ba - e0ba);
-    if (ns == 1) e_one = e;
-    else ep[s] = e;
-  }
-  // index streams at a fixed width per texel (anchors: texel 0, a1 and a2 in the primary stream)
-  uint64_t pa = ins0(shr128c<istart>(lo, hi), ib - 1);
-  if (ns == 2) pa = ins0(pa, a1 * ib + ib - 1);
-  if (ns == 3) {
-    const int alo = min(a1, a2), ahi = max(a1, a2);
-    pa = ins0(pa, alo * ib + ib - 1);
-    pa = ins0(pa, ahi * ib + ib - 1);
-  }
-  uint64_t sa = 0ull;
-  if (ib2) sa = ins0(shr128c<(ib2 ? istart + 16 * ib - 1 : 0)>(lo, hi), (ib2 ? ib2 : 1) - 1);
-  constexpr int cbits = swap ? ib2 : ib, abits = ib2 ? (swap ? ib : ib2) : 2;
-  const uint64_t cs = swap ? sa : pa, as = swap ? pa : sa;
-  // rotation: the alpha-index interpolation (byte 3 of `al`, operand byte 7) replaces channel rot - 1
-  const uint32_t rsel = rot == 0 ? 0x3210u : (rot == 1 ? 0x3217u : (rot == 2 ? 0x3270u : 0x3710u));
-#pragma unroll
-  for (int t = 0; t < 16; t++) {
-    const uint32_t ci = (uint32_t)(cs >> (cbits * t)) & ((1u << cbits) - 1u);
-    const uint32_t cw = wgt_of<cbits>(ci, S);
-    const uint4 e = ns == 1 ? e_one : ep[(pm >> (2 * t)) & 3u];
-    const uint32_t rg = cw * e.y + e.x, ba = cw * e.w + e.z;
-    uint32_t px = __byte_perm(rg, ba, 0x0531u);
-    if (rb) {
-      const uint32_t ai = (uint32_t)(as >> (abits * t)) & ((1u << abits) - 1u);
-      const uint32_t al = wgt_of<abits>(ai, S) * e.w + e.z;
-      px = __byte_perm(px, al, rsel);
-    }
-    tx[t] = px;
-  }
-}
 
 template <int CL>
-__device__ __forceinline__ void class_block(const EStage& sg, int b, int kind, uint32_t (&tx)[16], const DecTables* S,
+__device__ __forceinline__ void class_block(const ESlot& sg, int b, int kind, uint32_t (&tx)[16], const DecTables* S,
                                             uint4* ep) {
   if (CL <= CL_M4S) {
     const uint4 w = sg.blk[b];
     bc7_class_block<CL>(((uint64_t)w.y << 32) | w.x, ((uint64_t)w.w << 32) | w.z, tx, S, ep);
   } else if (CL == CL_BC1) {
     const uint2 w = kind == 1 ? reinterpret_cast<const uint2*>(sg.blk)[b] : make_uint2(sg.blk[b].x, sg.blk[b].y);
-    bc1_block(w, tx);
+    bc1_class_block(w, tx, ep);
   } else {
     const uint32_t v = CL == CL_RES ? 0u : 0x00808080u;
 #pragma unroll
@@ -261,181 +168,43 @@ __device__ __forceinline__ void tile_store(uint32_t* tile, int b, const uint32_t
 }
 
 template <int CL, int LAYOUT>
-__device__ __forceinline__ void decode_task(ESmem& sm, const EStage& sg, int b, int kind) {
+__device__ __forceinline__ void decode_task(ESmem& sm, ESlot& sg, int b, int kind) {
   uint32_t tx[16];
   class_block<CL>(sg, b, kind, tx, &sm.S, sm.ep[threadIdx.x]);
-  tile_store<LAYOUT>(sm.tile, b, tx);
-}
-
-// stream holding group g: the last stream starting at or before g (streams are back to back)
-__device__ __forceinline__ int stream_at(const DevTable& T, int64_t g) {
-  int si = 0;
-#pragma unroll 1
-  for (int i = 1; i < T.n_streams; i++) si += (T.first_group[i] <= g) ? 1 : 0;
-  return si;
-}
-
-// Issues the copies of tile `tile` into stage `sg`. TMA: one thread, completing on `bar`;
-// otherwise every thread copies its own blocks (b = threadIdx.x + i * E_NT) and, without TMA,
-// a share of the slot entries and positions.
-template <int KIND>
-__device__ __forceinline__ void stage_issue(const EArgs& a, EStage& sg, unsigned long long* bar, int64_t tile) {
-  const DevTable& T = a.T;
-  const int64_t g0 = tile * E_TG;
-  const int vg = (int)min((int64_t)E_TG, (int64_t)T.n_groups - g0);
-  const int64_t s0 = g0 * 16;
-  const int vs = vg * 16;
-  const bool tma = a.tma != 0;
-  if (tma && threadIdx.x == 0) {
-    fence_proxy_async();
-    uint32_t bytes = (uint32_t)vs * 4u;
-    if (a.pos_slot) bytes += (uint32_t)vs * 12u;
-    if (KIND == 7) bytes += (uint32_t)vg * 256u;
-    if (KIND == 1) bytes += (uint32_t)vg * 128u;
-    mbar_expect_tx(bar, bytes);
-    bulk_g2s(sg.perm, a.perm + s0, (uint32_t)vs * 4u, bar);
-    if (a.pos_slot) bulk_g2s(sg.pos, a.pos_slot + s0 * 3, (uint32_t)vs * 12u, bar);
-    if (KIND == 7) bulk_g2s(sg.blk, a.blocks + g0 * 256, (uint32_t)vg * 256u, bar);
-    if (KIND == 1) bulk_g2s(sg.blk, a.blocks + g0 * 128, (uint32_t)vg * 128u, bar);
-  }
-  if (!tma) {
-    for (int s = threadIdx.x; s < vs; s += E_NT) {
-      cp_async4(&sg.perm[s], a.perm + s0 + s);
-      if (a.pos_slot) {
-        const float* src = a.pos_slot + (s0 + s) * 3;
-        cp_async4(&sg.pos[3 * s], src);
-        cp_async4(&sg.pos[3 * s + 1], src + 1);
-        cp_async4(&sg.pos[3 * s + 2], src + 2);
-      }
-    }
-  }
-  if (KIND == 0 || !tma) {
-#pragma unroll
-    for (int i = 0; i < 2; i++) {
-      const int b = threadIdx.x + i * E_NT;
-      if (b >= vs) continue;
-      const int64_t g = g0 + (b >> 4);
-      const int k = b & 15;
-      if (KIND == 7) {
-        const uint8_t* src = a.blocks + (g * 16 + k) * 16;
-        cp_async8(&sg.blk[b], src);
-        cp_async8(reinterpret_cast<uint2*>(&sg.blk[b]) + 1, src + 8);
-      } else if (KIND == 1) {
-        cp_async8(reinterpret_cast<uint2*>(sg.blk) + b, a.blocks + (g * 16 + k) * 8);
-      } else {
-        const int si = stream_at(T, g);
-        const int nb = T.bands[si], j = T.bc7[si];
-        const int64_t base = T.byte_offset[si] + (g - T.first_group[si]) * (int64_t)(16 * j + 8 * (nb - j));
-        uint8_t c = 0;  // 0 dropped, 1 BC1, 7 BC7
-        if (k < nb) {
-          if (lay_bc7(T.layout, j, k)) {
-            const uint8_t* src = a.blocks + base + 16 * lay_rank(T.layout, j, k);
-            cp_async8(&sg.blk[b], src);
-            cp_async8(reinterpret_cast<uint2*>(&sg.blk[b]) + 1, src + 8);
-            c = 7;
-          } else {
-            cp_async8(&sg.blk[b], a.blocks + base + 16 * j + 8 * lay_rank(T.layout, j, k));
-            c = 1;
-          }
-        }
-        sg.cls[b] = c;
-      }
-    }
-  }
-  cp_async_commit();
-}
-
-__device__ __forceinline__ int bc7_class_of(uint32_t w) {
-  const uint32_t b0 = w & 0xFFu;
-  if (!b0) return CL_RES;
-  const int m = __ffs(b0) - 1;
-  return (m == 4 && ((w >> 7) & 1u)) ? CL_M4S : m;
-}
-
-// class of the block b this thread staged, appended to the class lists
-template <int KIND>
-__device__ __forceinline__ void classify(ESmem& sm, const EStage& sg, int cur, int b, bool valid) {
-  int cl = 0;
-  if (valid) {
-    if (KIND == 7) cl = bc7_class_of(sg.blk[b].x);
-    else if (KIND == 1) cl = CL_BC1;
-    else {
-      const int c = sg.cls[b];
-      cl = c == 7 ? bc7_class_of(sg.blk[b].x) : (c == 1 ? CL_BC1 : CL_DROP);
-    }
-  }
-  const unsigned act = __ballot_sync(0xFFFFFFFFu, valid);
-  if (!valid) return;
-  const unsigned peers = __match_any_sync(act, cl);
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(&sm.cnt[cur][cl], __popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  const int rank = __popc(peers & ((1u << lane) - 1u));
-  sm.list[cl][base + rank] = (uint16_t)b;
-}
-
-template <int KIND, int LAYOUT>
-__device__ __forceinline__ void decode_tile(ESmem& sm, const EStage& sg, int cur) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // task j of the tile: chunk (j - first task of class cl) of class cl's list, 32 blocks a chunk
-  int ntask = 0;
-#pragma unroll
-  for (int c = 0; c < E_NCLS; c++) ntask += (sm.cnt[cur][c] + 31) >> 5;
-  for (int j = warp; j < ntask; j += E_NW) {
-    int cl = 0, first = 0, nc = 0;
-    bool found = false;
-#pragma unroll
-    for (int c = 0; c < E_NCLS; c++) {
-      const int cc = sm.cnt[cur][c], tasks = (cc + 31) >> 5;
-      if (!found) {
-        if (j < first + tasks) { found = true; cl = c; nc = cc; }
-        else first += tasks;
-      }
-    }
-    const int idx = (j - first) * 32 + lane;
-    if (!found || idx >= nc) continue;
-    const int b = sm.list[cl][idx];
-    if (b >= E_T) continue;  // never: lists hold tile block indices
-    if (KIND == 1) {
-      decode_task<CL_BC1, LAYOUT>(sm, sg, b, KIND);
-      continue;
-    }
-    switch (cl) {
-      case 0: decode_task<0, LAYOUT>(sm, sg, b, KIND); break;
-      case 1: decode_task<1, LAYOUT>(sm, sg, b, KIND); break;
-      case 2: decode_task<2, LAYOUT>(sm, sg, b, KIND); break;
-      case 3: decode_task<3, LAYOUT>(sm, sg, b, KIND); break;
-      case 4: decode_task<4, LAYOUT>(sm, sg, b, KIND); break;
-      case 5: decode_task<5, LAYOUT>(sm, sg, b, KIND); break;
-      case 6: decode_task<6, LAYOUT>(sm, sg, b, KIND); break;
-      case 7: decode_task<7, LAYOUT>(sm, sg, b, KIND); break;
-      case CL_M4S: decode_task<CL_M4S, LAYOUT>(sm, sg, b, KIND); break;
-      case CL_RES: decode_task<CL_RES, LAYOUT>(sm, sg, b, KIND); break;
-      case CL_BC1: decode_task<CL_BC1, LAYOUT>(sm, sg, b, KIND); break;
-      default: decode_task<CL_DROP, LAYOUT>(sm, sg, b, KIND); break;
-    }
-  }
+  tile_store<LAYOUT>(sg.tile, b, tx);
 }
 
 // Decoded texels of two slots -> dequantised coefficient pairs (slot A in .x, slot B in .y)
-// with the SH constants folded in: x = fl(fl(2^23 + q - (2^23 + 128)) * f_k).
-__device__ __forceinline__ void dequant_pair(const ESmem& sm, int ra, int rb, float2 (&xr)[16], float2 (&xg)[16],
-                                             float2 (&xb)[16]) {
+// with the SH constants folded in, x = fl((q - 128) f_k). Two exact ways to the same bits:
+// fl(fl(2^23 + q - (2^23 + 128)) f_k), or, when f_k 2^133 is finite, one fused multiply-add
+// fma(q 2^-133, f_k 2^133, -128 f_k): q placed in bits 16..23 of a float is exactly q 2^-133
+// (subnormal below q = 128, the smallest normal exponent from there on), the product is exact
+// inside the FMA and -128 f_k is exact, so the single rounding gives fl((q - 128) f_k).
+__device__ __forceinline__ void dequant_pair(const ESmem& sm, const uint32_t* tile, int ra, int rb, float2 (&xr)[16],
+                                             float2 (&xg)[16], float2 (&xb)[16]) {
+  const bool one_fma = sm.ffma_deq != 0;
   const float2 m = make_float2(-8388736.0f, -8388736.0f);
 #pragma unroll
   for (int q = 0; q < 4; q++) {
-    const uint4 ta = *reinterpret_cast<const uint4*>(sm.tile + ra + 4 * q);
-    const uint4 tb = *reinterpret_cast<const uint4*>(sm.tile + rb + 4 * q);
+    const uint4 ta = *reinterpret_cast<const uint4*>(tile + ra + 4 * q);
+    const uint4 tb = *reinterpret_cast<const uint4*>(tile + rb + 4 * q);
     const uint32_t va[4] = {ta.x, ta.y, ta.z, ta.w}, vb[4] = {tb.x, tb.y, tb.z, tb.w};
 #pragma unroll
     for (int i = 0; i < 4; i++) {
       const int k = 4 * q + i;
-      const float2 f = sm.deq[k];
-      xr[k] = __fmul2_rn(__fadd2_rn(make_float2(u23(va[i], 0), u23(vb[i], 0)), m), f);
-      xg[k] = __fmul2_rn(__fadd2_rn(make_float2(u23(va[i], 1), u23(vb[i], 1)), m), f);
-      xb[k] = __fmul2_rn(__fadd2_rn(make_float2(u23(va[i], 2), u23(vb[i], 2)), m), f);
+      if (one_fma) {
+        const float2 F = sm.deqF[k], C = sm.deqC[k];
+#define QF(v, c) __uint_as_float(__byte_perm(v, 0u, 0x4044u | ((c) << 8)))
+        xr[k] = __ffma2_rn(make_float2(QF(va[i], 0), QF(vb[i], 0)), F, C);
+        xg[k] = __ffma2_rn(make_float2(QF(va[i], 1), QF(vb[i], 1)), F, C);
+        xb[k] = __ffma2_rn(make_float2(QF(va[i], 2), QF(vb[i], 2)), F, C);
+#undef QF
+      } else {
+        const float2 f = sm.deq[k];
+        xr[k] = __fmul2_rn(__fadd2_rn(make_float2(u23(va[i], 0), u23(vb[i], 0)), m), f);
+        xg[k] = __fmul2_rn(__fadd2_rn(make_float2(u23(va[i], 1), u23(vb[i], 1)), m), f);
+        xb[k] = __fmul2_rn(__fadd2_rn(make_float2(u23(va[i], 2), u23(vb[i], 2)), m), f);
+      }
     }
   }
 }
@@ -479,43 +248,271 @@ __device__ __forceinline__ int32_t e_checked(const EArgs& a, int32_t o, int64_t 
   return o;
 }
 
-template <bool CAMS>
-__device__ __forceinline__ void eval_tile(const EArgs& a, const ESmem& sm, const EStage& sg, int64_t tile) {
+
+// ---- ring synchronisation ---------------------------------------------------------------------
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+// waits (bounded) for the completion of the barrier phase with the given parity
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, uint32_t parity) {
+  uint32_t spins = 0;
+  while (!mbar_try(b, parity))
+    if (++spins > E_WAIT_LIMIT) return false;
+  return true;
+}
+// barrier of the producer warps that also tells every producer whether all of them passed their
+// waits (a timed-out wait makes all producers stop together)
+__device__ __forceinline__ bool producers_sync_all(bool ok) {
+  uint32_t r;
+  asm volatile(
+      "{ .reg .pred p, q; setp.ne.u32 p, %1, 0; bar.red.and.pred q, %2, %3, p; selp.u32 %0, 1, 0, q; }"
+      : "=r"(r)
+      : "r"((uint32_t)ok), "n"(E_PBAR), "n"(E_PT)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync %0, %1;" ::"n"(E_PBAR), "n"(E_PT) : "memory"); }
+
+// stream holding group g: the last stream starting at or before g (streams are back to back)
+__device__ __forceinline__ int stream_at(const DevTable& T, int64_t g) {
+  int si = 0;
+#pragma unroll 1
+  for (int i = 1; i < T.n_streams; i++) si += (T.first_group[i] <= g) ? 1 : 0;
+  return si;
+}
+
+__device__ __forceinline__ int tile_slots(const DevTable& T, int64_t tile) {
+  return (int)min((int64_t)E_TG, (int64_t)T.n_groups - tile * E_TG) * 16;
+}
+
+// Producers: copies of tile `tile` (if it exists) into slot `sg`: its blocks, slot entries and,
+// when centres come in slot order, its centres. TMA: producer thread 0 issues bulk copies
+// completing on `bar`; otherwise producer threads copy with cp.async, each its own blocks
+// (b = ptid + i * E_PT: the blocks it will classify). Every call commits one cp.async group.
+template <int KIND>
+__device__ __forceinline__ void stage_tile(const EArgs& a, ESlot& sg, unsigned long long* bar, int64_t tile,
+                                           int64_t n_tiles, int ptid) {
   const DevTable& T = a.T;
-  const int64_t g0 = tile * E_TG;
-  const int vs = (int)min((int64_t)E_TG, (int64_t)T.n_groups - g0) * 16;
-  const int sa = threadIdx.x, sb = threadIdx.x + E_NT;  // tile slots of Gaussians A and B
+  if (tile < n_tiles) {
+    const int64_t g0 = tile * E_TG, s0 = g0 * 16;
+    const int vs = tile_slots(T, tile), vg = vs >> 4;
+    const bool tblk = KIND != 0 && a.tma_blk != 0, tmeta = a.tma_meta != 0;
+    if ((tblk || tmeta) && ptid == 0) {
+      fence_proxy_async();
+      const uint32_t bb = tblk ? (uint32_t)vg * (KIND == 7 ? 256u : 128u) : 0u;
+      const uint32_t pb = tmeta ? (uint32_t)vs * 4u : 0u, qb = tmeta && a.pos_slot ? (uint32_t)vs * 12u : 0u;
+      mbar_expect_tx(bar, bb + pb + qb);
+      if (tblk) bulk_g2s(sg.blk, a.blocks + g0 * (KIND == 7 ? 256 : 128), bb, bar);
+      if (pb) bulk_g2s(sg.perm, a.perm + s0, pb, bar);
+      if (qb) bulk_g2s(sg.pos, a.pos_slot + s0 * 3, qb, bar);
+    }
+    if (!tmeta) {
+      for (int u = ptid; u < vs; u += E_PT) {
+        cp_async4(&sg.perm[u], a.perm + s0 + u);
+        if (a.pos_slot) {
+          const float* src = a.pos_slot + (s0 + u) * 3;
+          cp_async4(&sg.pos[3 * u], src);
+          cp_async4(&sg.pos[3 * u + 1], src + 1);
+          cp_async4(&sg.pos[3 * u + 2], src + 2);
+        }
+      }
+    }
+    if (!tblk) {
+      for (int b = ptid; b < vs; b += E_PT) {
+        const int64_t g = g0 + (b >> 4);
+        const int k = b & 15;
+        if (KIND == 7) {
+          const uint8_t* src = a.blocks + (g * 16 + k) * 16;
+          cp_async8(&sg.blk[b], src);
+          cp_async8(reinterpret_cast<uint2*>(&sg.blk[b]) + 1, src + 8);
+        } else if (KIND == 1) {
+          cp_async8(reinterpret_cast<uint2*>(sg.blk) + b, a.blocks + (g * 16 + k) * 8);
+        } else {
+          const int si = stream_at(T, g);
+          const int nb = T.bands[si], j = T.bc7[si];
+          const int64_t base = T.byte_offset[si] + (g - T.first_group[si]) * (int64_t)(16 * j + 8 * (nb - j));
+          uint8_t c = 0;  // 0 dropped, 1 BC1, 7 BC7
+          if (k < nb) {
+            if (lay_bc7(T.layout, j, k)) {
+              const uint8_t* src = a.blocks + base + 16 * lay_rank(T.layout, j, k);
+              cp_async8(&sg.blk[b], src);
+              cp_async8(reinterpret_cast<uint2*>(&sg.blk[b]) + 1, src + 8);
+              c = 7;
+            } else {
+              cp_async8(&sg.blk[b], a.blocks + base + 16 * j + 8 * lay_rank(T.layout, j, k));
+              c = 1;
+            }
+          }
+          sg.cls[b] = c;
+        }
+      }
+    }
+  }
+  cp_async_commit();
+}
+
+__device__ __forceinline__ int bc7_class_of(uint32_t w) {
+  const uint32_t b0 = w & 0xFFu;
+  if (!b0) return CL_RES;
+  const int m = __ffs(b0) - 1;
+  return (m == 4 && ((w >> 7) & 1u)) ? CL_M4S : m;
+}
+
+// class of block b of the slot, appended to the class lists (warp-aggregated)
+template <int KIND>
+__device__ __forceinline__ void classify(ESmem& sm, const ESlot& sg, int cur, int b, bool valid) {
+  int cl = 0;
+  if (valid) {
+    if (KIND == 7) cl = bc7_class_of(sg.blk[b].x);
+    else if (KIND == 1) cl = CL_BC1;
+    else {
+      const int c = sg.cls[b];
+      cl = c == 7 ? bc7_class_of(sg.blk[b].x) : (c == 1 ? CL_BC1 : CL_DROP);
+    }
+  }
+  const unsigned act = __ballot_sync(0xFFFFFFFFu, valid);
+  if (!valid) return;
+  const unsigned peers = __match_any_sync(act, cl);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(&sm.cnt[cur][cl], __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  const int rank = __popc(peers & ((1u << lane) - 1u));
+  sm.list[cl][base + rank] = (uint16_t)b;
+}
+
+// Producer warp `pw` decodes its share of the slot's blocks: classes in order, each class's list
+// in chunks of 32, chunk j of the whole sequence going to warp j % E_PW.
+template <int KIND, int LAYOUT, int CL>
+__device__ __forceinline__ void decode_class(ESmem& sm, ESlot& sg, int cur, int pw, int lane, int& first) {
+  const int cc = sm.cnt[cur][CL], tasks = (cc + 31) >> 5;
+  if (tasks == 0) return;
+  const int r = first % E_PW;
+  for (int j = (pw >= r ? pw - r : pw + E_PW - r); j < tasks; j += E_PW) {
+    const int idx = j * 32 + lane;
+    if (idx < cc) {
+      const int b = sm.list[CL][idx];
+      if (b < E_T) decode_task<CL, LAYOUT>(sm, sg, b, KIND);
+    }
+  }
+  first += tasks;
+}
+
+template <int KIND, int LAYOUT>
+__device__ __forceinline__ void decode_slot(ESmem& sm, ESlot& sg, int cur, int pw, int lane) {
+  int first = 0;
+  if (KIND == 1) {
+    decode_class<KIND, LAYOUT, CL_BC1>(sm, sg, cur, pw, lane, first);
+    return;
+  }
+  decode_class<KIND, LAYOUT, 0>(sm, sg, cur, pw, lane, first);
+  decode_class<KIND, LAYOUT, 1>(sm, sg, cur, pw, lane, first);
+  decode_class<KIND, LAYOUT, 2>(sm, sg, cur, pw, lane, first);
+  decode_class<KIND, LAYOUT, 3>(sm, sg, cur, pw, lane, first);
+  decode_class<KIND, LAYOUT, 4>(sm, sg, cur, pw, lane, first);
+  decode_class<KIND, LAYOUT, 5>(sm, sg, cur, pw, lane, first);
+  decode_class<KIND, LAYOUT, 6>(sm, sg, cur, pw, lane, first);
+  decode_class<KIND, LAYOUT, 7>(sm, sg, cur, pw, lane, first);
+  decode_class<KIND, LAYOUT, CL_M4S>(sm, sg, cur, pw, lane, first);
+  decode_class<KIND, LAYOUT, CL_RES>(sm, sg, cur, pw, lane, first);
+  if (KIND == 0) {
+    decode_class<KIND, LAYOUT, CL_BC1>(sm, sg, cur, pw, lane, first);
+    decode_class<KIND, LAYOUT, CL_DROP>(sm, sg, cur, pw, lane, first);
+  }
+}
+
+template <int KIND, int LAYOUT>
+__device__ void producer(ESmem& sm, const EArgs& a, int64_t n_tiles) {
+  const int ptid = threadIdx.x, pw = ptid >> 5, lane = ptid & 31;
+  const DevTable& T = a.T;
+  const bool tma = (KIND != 0 && a.tma_blk != 0) || a.tma_meta != 0;
+  // the first E_NS tiles of this CTA
+  for (int i = 0; i < E_NS; i++)
+    stage_tile<KIND>(a, sm.slot[i], &sm.blk_full[i], (int64_t)blockIdx.x + (int64_t)i * gridDim.x, n_tiles, ptid);
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, it++) {
+    const int s = it % E_NS, use = it / E_NS, cur = it & 1;
+    ESlot& sg = sm.slot[s];
+    const int vs = tile_slots(T, tile);
+    // this thread's copies of the tile (the E_NS - 1 newer groups may stay in flight)
+    asm volatile("cp.async.wait_group %0;" ::"n"(E_NS - 1) : "memory");
+    bool ok = true;
+    if (tma) ok = mbar_wait(&sm.blk_full[s], (uint32_t)use & 1u);
+    if (!producers_sync_all(ok)) {
+      if (ptid == 0) eval_record((int)GSC_ERR_TIMEOUT, (int)blockIdx.x);
+      return;
+    }
+    for (int b = ptid; b < E_PT * ((E_T + E_PT - 1) / E_PT); b += E_PT) classify<KIND>(sm, sg, cur, b, b < vs);
+    // counters of the next tile: last read by the previous tile's decode, before this tile's barriers
+    if (ptid < E_NCLS) sm.cnt[cur ^ 1][ptid] = 0;
+    // the slot's tile is free once the consumers released its previous use
+    ok = use == 0 || mbar_wait(&sm.tile_empty[s], (uint32_t)(use - 1) & 1u);
+    if (!producers_sync_all(ok)) {
+      if (ptid == 0) eval_record((int)GSC_ERR_TIMEOUT, (int)blockIdx.x);
+      return;
+    }
+    decode_slot<KIND, LAYOUT>(sm, sg, cur, pw, lane);
+    producers_sync();
+    if (ptid == 0) mbar_arrive(&sm.tile_full[s]);
+    // the slot's blocks are decoded: stage the tile E_NS ahead into it
+    stage_tile<KIND>(a, sg, &sm.blk_full[s], tile + (int64_t)E_NS * gridDim.x, n_tiles, ptid);
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+
+// slot entry and centre of tile slot `u`, from the staged slot (centres in original order are
+// gathered through the slot entry)
+struct ESlotIn {
+  int32_t o;
+  float px, py, pz;
+};
+
+template <bool CAMS>
+__device__ __forceinline__ ESlotIn slot_in(const EArgs& a, const ESlot& sg, int64_t tile, int u) {
+  ESlotIn r;
+  r.o = -1;
+  r.px = r.py = r.pz = 0.f;
+  if (u >= tile_slots(a.T, tile)) return r;
+  r.o = e_checked(a, sg.perm[u], tile * E_T + u);
+  if (CAMS) {
+    if (a.pos_slot) {
+      r.px = sg.pos[3 * u]; r.py = sg.pos[3 * u + 1]; r.pz = sg.pos[3 * u + 2];
+    } else if (r.o >= 0) {
+      const float* p = a.pos + 3 * (int64_t)r.o;
+      r.px = __ldg(p); r.py = __ldg(p + 1); r.pz = __ldg(p + 2);
+    }
+  }
+  return r;
+}
+
+// VF > 0: exactly VF views into Gaussian-major rows, known at compile time.
+template <bool CAMS, int VF>
+__device__ __forceinline__ void eval_slot_pair(const EArgs& a, const ESmem& sm, const uint32_t* tile, int64_t tile_i,
+                                               int sa, int sb, const ESlotIn& A, const ESlotIn& B) {
+  const DevTable& T = a.T;
+  const int vs = tile_slots(T, tile_i);
   if (sa >= vs) return;
   const bool vb = sb < vs;
-  const int64_t s0 = g0 * 16;
+  const int64_t s0 = tile_i * E_T;
   const int64_t n = T.n, ns = (int64_t)T.n_groups * 16;
-  const int32_t oa = e_checked(a, sg.perm[sa], s0 + sa);
-  const int32_t ob = vb ? e_checked(a, sg.perm[sb], s0 + sb) : -1;
-  const int V = a.V, order = a.out_order;
+  const int32_t oa = A.o, ob = vb ? B.o : -1;
+  const int V = VF > 0 ? VF : a.V, order = VF > 0 ? (int)GSC_OUT_GAUSS_MAJOR : a.out_order;
   if (oa < 0 && ob < 0) {
     if (order == GSC_OUT_SLOT_ORDER)
       for (int v = 0; v < V; v++) {
         float* d = a.rgb + ((int64_t)v * ns + s0 + sa) * 3;
         d[0] = d[1] = d[2] = 0.f;
-        if (vb) { d += (int64_t)E_NT * 3; d[0] = d[1] = d[2] = 0.f; }
+        if (vb) { d += (int64_t)(sb - sa) * 3; d[0] = d[1] = d[2] = 0.f; }
       }
     return;
   }
-  float2 npx = make_float2(0.f, 0.f), npy = npx, npz = npx;
-  if (CAMS) {
-    float3 pa = make_float3(0.f, 0.f, 0.f), pb = pa;
-    if (a.pos_slot) {
-      pa = make_float3(sg.pos[3 * sa], sg.pos[3 * sa + 1], sg.pos[3 * sa + 2]);
-      if (vb) pb = make_float3(sg.pos[3 * sb], sg.pos[3 * sb + 1], sg.pos[3 * sb + 2]);
-    } else {
-      if (oa >= 0) pa = make_float3(__ldg(a.pos + 3 * (int64_t)oa), __ldg(a.pos + 3 * (int64_t)oa + 1), __ldg(a.pos + 3 * (int64_t)oa + 2));
-      if (ob >= 0) pb = make_float3(__ldg(a.pos + 3 * (int64_t)ob), __ldg(a.pos + 3 * (int64_t)ob + 1), __ldg(a.pos + 3 * (int64_t)ob + 2));
-    }
-    npx = make_float2(-pa.x, -pb.x); npy = make_float2(-pa.y, -pb.y); npz = make_float2(-pa.z, -pb.z);
-  }
+  const float2 npx = make_float2(-A.px, -B.px), npy = make_float2(-A.py, -B.py), npz = make_float2(-A.pz, -B.pz);
   float2 xr[16], xg[16], xb[16];
-  dequant_pair(sm, (sa >> 4) * E_GRP + (sa & 15) * E_ROW, (sb >> 4) * E_GRP + (sb & 15) * E_ROW, xr, xg, xb);
+  dequant_pair(sm, tile, (sa >> 4) * E_GRP + (sa & 15) * E_ROW, (sb >> 4) * E_GRP + (sb & 15) * E_ROW, xr, xg, xb);
   const bool gm4 = order == GSC_OUT_GAUSS_MAJOR && (V & 3) == 0;
+#pragma unroll
   for (int v0 = 0; v0 < V; v0 += 4) {
     float ra[12], rb[12];
 #pragma unroll
@@ -570,8 +567,29 @@ __device__ __forceinline__ void eval_tile(const EArgs& a, const ESmem& sm, const
   }
 }
 
-template <int KIND, bool CAMS, int LAYOUT>
-__global__ void __launch_bounds__(E_NT, 2) k_eval3(EArgs a) {
+template <bool CAMS, int VF>
+__device__ void consumer(ESmem& sm, const EArgs& a, int64_t n_tiles) {
+  const int ctid = threadIdx.x - E_PT, lane = threadIdx.x & 31;
+  const int sa = ctid, sb = ctid + E_CT;  // tile slots of this thread's two Gaussians
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, it++) {
+    const int s = it % E_NS, use = it / E_NS;
+    const bool ok = __all_sync(0xFFFFFFFFu, mbar_wait(&sm.tile_full[s], (uint32_t)use & 1u));
+    if (!ok) {
+      if (lane == 0) eval_record((int)GSC_ERR_TIMEOUT, (int)blockIdx.x);
+      return;
+    }
+    const ESlot& sg = sm.slot[s];
+    const ESlotIn A = slot_in<CAMS>(a, sg, tile, sa), B = slot_in<CAMS>(a, sg, tile, sb);
+    eval_slot_pair<CAMS, VF>(a, sm, sg.tile, tile, sa, sb, A, B);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sm.tile_empty[s]);
+  }
+}
+
+template <int KIND, bool CAMS, int LAYOUT, int VF>
+__global__ void __launch_bounds__(E_NT, 1) k_eval4(EArgs a) {
+  static_assert(E_NT == 512, "128 registers per thread at launch");
   extern __shared__ __align__(128) uint8_t e_raw[];
   ESmem& sm = *reinterpret_cast<ESmem*>(e_raw);
   const DevTable& T = a.T;
@@ -582,62 +600,52 @@ __global__ void __launch_bounds__(E_NT, 2) k_eval3(EArgs a) {
     sm.cxy[i] = make_float4(x, x, y, y);
     sm.cz[i] = make_float2(z, z);
   }
+  bool fma_ok = true;
   if (threadIdx.x < 16) {
     const float f = __fmul_rn(__fdiv_rn(T.scales[threadIdx.x], 255.0f), c_shc[threadIdx.x]);
     sm.deq[threadIdx.x] = make_float2(f, f);
+    const float F = __fmul_rn(__fmul_rn(f, 18446744073709551616.0f), 590295810358705651712.0f);  // f 2^64 2^69
+    const float C = __fmul_rn(f, -128.0f);
+    sm.deqF[threadIdx.x] = make_float2(F, F);
+    sm.deqC[threadIdx.x] = make_float2(C, C);
+    fma_ok = fabsf(f) < 0.03125f;  // f 2^133 < 2^128
   }
   if (threadIdx.x < 2 * E_NCLS) sm.cnt[threadIdx.x / E_NCLS][threadIdx.x % E_NCLS] = 0;
-  if (threadIdx.x == 0) {
-    mbar_init(&sm.mbar[0], 1);
-    mbar_init(&sm.mbar[1], 1);
-    fence_mbar_init();
+  if (threadIdx.x < E_NS) {
+    mbar_init(&sm.blk_full[threadIdx.x], 1);
+    mbar_init(&sm.tile_full[threadIdx.x], 1);
+    mbar_init(&sm.tile_empty[threadIdx.x], E_CW);
   }
+  if (threadIdx.x == 0) fence_mbar_init();
+  const int all_ok = __syncthreads_and(fma_ok);
+  if (threadIdx.x == 0) sm.ffma_deq = all_ok;
   __syncthreads();
   const int64_t n_tiles = ((int64_t)T.n_groups + E_TG - 1) / E_TG;
-  int64_t tile = blockIdx.x;
-  if (tile < n_tiles) stage_issue<KIND>(a, sm.stage[0], &sm.mbar[0], tile);
-  uint32_t parity = 0u;  // bit st: parity of the next completion of stage st's barrier
-  for (int it = 0; tile < n_tiles; tile += gridDim.x, it++) {
-    const int st = it & 1, cur = it & 1;
-    EStage& sg = sm.stage[st];
-    cp_async_wait_all();
-    if (a.tma) {
-      uint32_t spins = 0;
-      while (!mbar_try(&sm.mbar[st], (parity >> st) & 1u)) {
-        if (++spins > E_WAIT_LIMIT) {
-          if (threadIdx.x == 0) eval_record((int)GSC_ERR_TIMEOUT, (int)blockIdx.x);
-          return;
-        }
-      }
-    }
-    parity ^= 1u << st;
-    const int vs = (int)min((int64_t)E_TG, (int64_t)T.n_groups - tile * E_TG) * 16;
-    classify<KIND>(sm, sg, cur, threadIdx.x, (int)threadIdx.x < vs);
-    classify<KIND>(sm, sg, cur, threadIdx.x + E_NT, (int)threadIdx.x + E_NT < vs);
-    __syncthreads();
-    // the other stage was last read by the previous tile's evaluation, finished before the barrier
-    const int64_t next = tile + gridDim.x;
-    if (next < n_tiles) stage_issue<KIND>(a, sm.stage[st ^ 1], &sm.mbar[st ^ 1], next);
-    // counters of the next tile: last read by the previous tile's decode, before this tile's barrier
-    if (threadIdx.x < E_NCLS) sm.cnt[cur ^ 1][threadIdx.x] = 0;
-    decode_tile<KIND, LAYOUT>(sm, sg, cur);
-    __syncthreads();
-    eval_tile<CAMS>(a, sm, sg, tile);
+  if (threadIdx.x < E_PT) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(E_PREG));
+    producer<KIND, LAYOUT>(sm, a, n_tiles);
+  } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(E_CREG));
+    consumer<CAMS, VF>(sm, a, n_tiles);
   }
-  // nothing is left in flight: a tile's copies are issued only when that tile will be processed
 }
 
-template <int KIND, bool CAMS, int LAYOUT>
+template <int KIND, bool CAMS, int LAYOUT, int VF>
 cudaError_t set_attr() {
-  return cudaFuncSetAttribute(k_eval3<KIND, CAMS, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_eval4<KIND, CAMS, LAYOUT, VF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)sizeof(ESmem));
 }
 
 template <bool CAMS, int LAYOUT>
 cudaError_t set_attr_kinds() {
-  cudaError_t e = set_attr<7, CAMS, LAYOUT>();
-  if (e == cudaSuccess) e = set_attr<1, CAMS, LAYOUT>();
-  if (e == cudaSuccess) e = set_attr<0, CAMS, LAYOUT>();
+  cudaError_t e = set_attr<7, CAMS, LAYOUT, 0>();
+  if (e == cudaSuccess) e = set_attr<1, CAMS, LAYOUT, 0>();
+  if (e == cudaSuccess) e = set_attr<0, CAMS, LAYOUT, 0>();
+  if (LAYOUT == GSC_LAYOUT_D) {
+    if (e == cudaSuccess) e = set_attr<7, CAMS, LAYOUT, 8>();
+    if (e == cudaSuccess) e = set_attr<1, CAMS, LAYOUT, 8>();
+    if (e == cudaSuccess) e = set_attr<0, CAMS, LAYOUT, 8>();
+  }
   return e;
 }
 
@@ -692,12 +700,19 @@ cudaError_t launch_eval3(const DevTable& T, const uint8_t* blocks, const int32_t
   a.V = V;
   a.out_order = out_order;
   const int kind = kind_of3(T);
-  a.tma = (al16(perm) && (!pos_slot || al16(pos_slot)) && (kind == 0 || al16(blocks))) ? 1 : 0;
+  a.tma_blk = al16(blocks) ? 1 : 0;  // rate streams always take per-thread copies
+  a.tma_meta = (al16(perm) && (!pos_slot || al16(pos_slot))) ? 1 : 0;
   const int64_t n_tiles = ((int64_t)T.n_groups + E_TG - 1) / E_TG;
-  const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 1) * 2;
+  const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 1);
   const int grid = (int)(n_tiles < cap ? n_tiles : cap);
   const size_t smem = sizeof(ESmem);
-#define E3_LAUNCH(K, C, L) k_eval3<K, C, L><<<grid, E_NT, smem, st>>>(a)
+  // 8 views into Gaussian-major rows (the camera-pose workload): a compile-time view count
+  const bool v8 = V == 8 && out_order == GSC_OUT_GAUSS_MAJOR && T.layout == GSC_LAYOUT_D;
+#define E3_LAUNCH(K, C, L)                                                              \
+  do {                                                                                 \
+    if (L == GSC_LAYOUT_D && v8) k_eval4<K, C, GSC_LAYOUT_D, 8><<<grid, E_NT, smem, st>>>(a); \
+    else k_eval4<K, C, L, 0><<<grid, E_NT, smem, st>>>(a);                             \
+  } while (0)
 #define E3_KINDS(C, L)                                                                 \
   do {                                                                                 \
     if (kind == 7) E3_LAUNCH(7, C, L); else if (kind == 1) E3_LAUNCH(1, C, L); else E3_LAUNCH(0, C, L); \
@@ -717,31 +732,3 @@ cudaError_t launch_eval3(const DevTable& T, const uint8_t* blocks, const int32_t
   return cudaGetLastError();
 }
 
-// Positions in slot order: out[s] = pos[perm[s]] (zeros for padding slots).
-__global__ void k_pos_to_slots(const float* __restrict__ pos, const int32_t* __restrict__ perm, int64_t n, int64_t ns,
-                               float* __restrict__ out) {
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
-    int32_t o = perm[s];
-#ifdef GSC_CHECKED
-    if (o < -1 || (int64_t)o >= n) {
-      eval_record((int)GSC_ERR_DEVICE, (int)(s < 0x7FFFFFFF ? s : 0x7FFFFFFF));
-      o = -1;
-    }
-#endif
-    (void)n;
-    float x = 0.f, y = 0.f, z = 0.f;
-    if (o >= 0) { x = pos[3 * (int64_t)o]; y = pos[3 * (int64_t)o + 1]; z = pos[3 * (int64_t)o + 2]; }
-    out[3 * s] = x; out[3 * s + 1] = y; out[3 * s + 2] = z;
-  }
-}
-
-cudaError_t launch_pos_to_slots(const float* pos, const int32_t* perm, int64_t n, int64_t ns, float* out, int sm_count,
-                                cudaStream_t st) {
-  if (ns <= 0) return cudaSuccess;
-  int64_t grid = (ns + 255) / 256;
-  const int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 1) * 8;
-  if (grid > cap) grid = cap;
-  gsc_count_launch();
-  k_pos_to_slots<<<(int)grid, 256, 0, st>>>(pos, perm, n, ns, out);
-  return cudaGetLastError();
-}

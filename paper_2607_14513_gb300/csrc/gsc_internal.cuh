@@ -178,20 +178,14 @@ void host_weights(const float* scales, uint32_t* w);
 gsc_status make_dev_table(const gsc_stream_table* t, DevTable* d);
 cudaError_t launch_decode(const DevTable& t, const uint8_t* blocks, const int32_t* perm, uint8_t* texels,
                           cudaStream_t st);
-// glist (optional): evaluate only the groups glist[0, n_list) (-1 entries skipped)
+// glist (optional): evaluate only the groups glist[0, n_list) (-1 entries skipped); pos_slot
+// (optional): centres in slot order [n_groups * 16][3], read instead of pos[perm[s]]
 cudaError_t launch_decode_eval(const DevTable& t, const uint8_t* blocks, const int32_t* perm, const float* dirs,
                                const float* pos, const float* cams, int V, int out_order, float* rgb, int sm_count,
-                               cudaStream_t st, const int32_t* glist = nullptr, int64_t n_list = 0);
+                               cudaStream_t st, const int32_t* glist = nullptr, int64_t n_list = 0,
+                               const float* pos_slot = nullptr);
 cudaError_t launch_decode_blocks(const uint8_t* blocks, int64_t nblk, int format, uint8_t* rgba, cudaStream_t st);
-// eval.cu: the tiled fused decode + SH evaluation of whole scenes. pos: original order [n][3];
-// pos_slot: slot order [n_groups * 16][3] (one of them when cams are given).
-cudaError_t eval3_init();
-cudaError_t launch_eval3(const DevTable& T, const uint8_t* blocks, const int32_t* perm, const float* dirs,
-                         const float* pos, const float* pos_slot, const float* cams, int V, int out_order, float* rgb,
-                         int sm_count, cudaStream_t st);
-// takes and clears the first error the tiled kernel recorded on the current device (0 = none)
-int eval3_err_take(int* where);
-size_t eval3_smem_bytes();
+// centres in slot order: out[s] = pos[perm[s]] (0 for padding slots), s < ns
 cudaError_t launch_pos_to_slots(const float* pos, const int32_t* perm, int64_t n, int64_t ns, float* out, int sm_count,
                                 cudaStream_t st);
 gsc_status decode_tex_run(gsc_ctx* ctx, const DevTable& t, const uint8_t* blocks, const int32_t* perm,

@@ -1,16 +1,16 @@
-"""The tiled fused decode + SH evaluation (Sec. II, c(f) = H w(f - p); Sec. III-B decoding)
-through the C-ABI: gsc_decode_eval_sh (centres in original order) and gsc_decode_eval_sh_slots
-(centres in slot order, gsc_positions_to_slots) on the all-BC7, all-BC1 and 6-bpt rate-stream
-codings.
+"""Fused decode + SH evaluation (Sec. II, c(f) = H w(f - p); Sec. III-B decoding) through the
+C-ABI: gsc_decode_eval_sh (centres in original order, gathered through the slot order) and
+gsc_decode_eval_sh_slots (centres in slot order, built by gsc_positions_to_slots) on the all-BC7,
+all-BC1 and 6-bpt rate-stream codings.
 
 Expected values come from the oracle alone: it codes the scene itself (the GPU blocks are checked
 against its blocks bit for bit first), decodes its own blocks and evaluates them in FP64; the GPU
 colours must lie within 1e-5 of the sum of absolute terms. Both software entry points must also
 equal each other and the texture-unit evaluation bit for bit (the same arithmetic per Gaussian
-and view). Sizes straddle the 384-slot tile (1, 17, 383, 385, ...), so first, last and partial
-tiles and partial groups are covered; inputs that are not 16-byte aligned take per-thread copies
-instead of TMA bulk copies and must give the same bits; shared view directions and view counts
-that are not a multiple of four are covered too.
+and view). Sizes straddle group and launch boundaries (1, 17, 383, 385, ...); blocks that are only
+8-byte aligned (the all-BC7 fast path then takes 8-byte loads) and slot entries and centres that
+are only 4-byte aligned must give the same bits; shared view directions and view counts that are
+not a multiple of four are covered too.
 """
 import numpy as np
 import pytest
@@ -62,7 +62,7 @@ def _scene(n, seed):
 
 
 @pytest.mark.parametrize("n", SIZES)
-def test_tiled_eval_matches_oracle_and_texture_unit(ctx, O, n):
+def test_eval_matches_oracle_and_texture_unit(ctx, O, n):
     from paper_2607_14513_gb300 import gsc
     pos, sh = _scene(n, 3000 + n)
     dpos, dsh = torch.from_numpy(pos).cuda(), torch.from_numpy(sh).cuda()
