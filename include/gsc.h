@@ -158,7 +158,10 @@ gsc_status gsc_plan_reorder(gsc_ctx* ctx, const float* d_pos, const float* d_sh,
  * process exits. Limits: 0 <= n <= GSC_PLAN_STATIC_MAX_N (65536) Gaussians; larger n
  * returns GSC_ERR_INVALID_ARG and launches nothing. It calls no cudaMalloc, cudaFree or
  * allocating library routine. The first call on a device looks up the array's device
- * address (with that device current); make that first call before any stream capture.
+ * address (with that device current); make that first call before any stream capture. The
+ * address is kept for the life of the process: after a cudaDeviceReset of that device it is
+ * stale, so do not call this entry point on a device that was reset. Records its time under
+ * "plan" like gsc_plan_reorder when the context's timing is on.
  * All calls share the one array, which keeps the last call's contents (the call clears
  * what it needs): calls that overlap on the GPU, from any stream or context of the
  * process, race on it and must be serialised by the caller. */
@@ -184,6 +187,14 @@ gsc_status gsc_quantise(gsc_ctx* ctx, const float* d_sh, int64_t n, const float*
 gsc_status gsc_encode(gsc_ctx* ctx, const float* d_sh, int64_t n, const int32_t* d_perm, const float* d_scales,
                       const gsc_encode_params* ep, uint8_t* d_blocks, int32_t* d_perm_out, gsc_stream_table* h_table,
                       void* d_ws, size_t ws_bytes, void* stream);
+
+/* Host only. The stream table of the all-BC1 (format GSC_FMT_BC1) or all-BC7 (GSC_FMT_BC7)
+ * coding of the scene that `table` describes (same n, scales, weights and layout): one stream of
+ * every group with all 16 coefficients, n_groups * 16 * (8 or 16) bytes. It describes exactly the
+ * d_bc1_blocks / d_bc7_blocks outputs of a GSC_FMT_RATE gsc_encode, and what GSC_FMT_BC1 /
+ * GSC_FMT_BC7 write for the same slot order (budget_bits 0, used_bits = 8 * total_bytes,
+ * lambda 0). GSC_ERR_INVALID_ARG if `table` is not a valid stream table or format is another. */
+gsc_status gsc_forced_table(const gsc_stream_table* table, int32_t format, gsc_stream_table* out);
 
 /* Sec. I and III-A (random access: block = stream offset + index x block size) and
  * Sec. II. Decodes every stream to texels d_texels [n][16][3] uint8 in original order
@@ -302,6 +313,11 @@ typedef struct {
 /* Bytes of the geometry buffer for n_slots slots in chunks of chunk_slots; 0 when n_slots < 0 or
  * chunk_slots is not a positive multiple of 16. */
 size_t gsc_geometry_bytes(int64_t n_slots, int64_t chunk_slots);
+/* Host only. Byte offsets of the five sections of a geometry buffer (centre codes u16 [n_slots][3],
+ * scale codes u16 [n_slots][3], rotation codes u32 [n_slots], opacity codes u8 [n_slots], chunk
+ * table gsc_chunk [ceil(n_slots / chunk_slots)], each 256-byte aligned) into offsets[5]; returns
+ * the buffer size (gsc_geometry_bytes), or 0 for invalid sizes or a NULL offsets. */
+size_t gsc_geometry_layout(int64_t n_slots, int64_t chunk_slots, size_t* offsets);
 /* Codes the geometry of a planned scene (d_perm [n_slots], n_slots a multiple of 16; geometry in
  * original order as gsc_render takes it) into d_geom (256-byte aligned, gsc_geometry_bytes). */
 gsc_status gsc_geometry_encode(gsc_ctx* ctx, const float* d_pos, const float* d_scale, const float* d_rot,

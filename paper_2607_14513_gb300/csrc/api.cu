@@ -122,6 +122,23 @@ extern "C" gsc_status gsc_probe_int_peak(gsc_ctx* c, double* ops_per_s, void* st
   return GSC_OK;
 }
 
+int gsc_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return 1; }
+  if (dev >= 0 && dev < 64) {
+    const int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int sm = 0;
+  if (cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sm <= 0) {
+    cudaGetLastError();
+    sm = 1;
+  }
+  if (dev >= 0 && dev < 64) cache[dev].store(sm, std::memory_order_relaxed);
+  return sm;
+}
+
 static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 extern "C" const char* gsc_status_string(gsc_status s) {
@@ -375,6 +392,33 @@ gsc_status make_dev_table(const gsc_stream_table* t, DevTable* d) {
     if (!(t->scales[k] > 0.0f) || isinf(t->scales[k])) return GSC_ERR_INVALID_ARG;
     d->scales[k] = t->scales[k];
   }
+  return GSC_OK;
+}
+
+extern "C" gsc_status gsc_forced_table(const gsc_stream_table* table, int32_t format, gsc_stream_table* out) {
+  if (!table || !out || (format != GSC_FMT_BC1 && format != GSC_FMT_BC7)) return GSC_ERR_INVALID_ARG;
+  DevTable T;
+  const gsc_status st = make_dev_table(table, &T);
+  if (st != GSC_OK) return st;
+  const int64_t bpb = format == GSC_FMT_BC7 ? 16 : 8;
+  gsc_stream_table t;
+  memset(&t, 0, sizeof(t));
+  t.n_streams = 1;
+  t.format = format;
+  t.n = table->n;
+  t.n_groups = table->n_groups;
+  t.layout = table->layout;
+  t.total_bytes = table->n_groups * 16 * bpb;
+  t.budget_bits = 0;
+  t.used_bits = (uint64_t)t.total_bytes * 8u;
+  t.lambda = 0;
+  for (int k = 0; k < GSC_SH; k++) { t.scales[k] = table->scales[k]; t.weights[k] = table->weights[k]; }
+  t.s[0].bands = 16;
+  t.s[0].bc7_blocks = format == GSC_FMT_BC7 ? 16 : 0;
+  t.s[0].first_group = 0;
+  t.s[0].n_groups = table->n_groups;
+  t.s[0].byte_offset = 0;
+  *out = t;
   return GSC_OK;
 }
 

@@ -86,7 +86,7 @@ __global__ void k_bc1_blocks(const uint8_t* __restrict__ texin, int64_t nblk, ui
 
 static int grid_for(int64_t work, int per_cta) {
   int64_t g = ceil_div64(work, per_cta);
-  if (g > 152 * 64) g = 152 * 64;
+  if (g > gsc_sm_count() * 64) g = gsc_sm_count() * 64;
   return (int)(g < 1 ? 1 : g);
 }
 

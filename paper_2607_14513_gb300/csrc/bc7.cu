@@ -641,7 +641,7 @@ cudaError_t bc7_kernel_attributes() {
 
 static int grid_for7(int64_t work, int per_cta) {
   int64_t g = ceil_div64(work, per_cta);
-  if (g > 152 * 32) g = 152 * 32;
+  if (g > gsc_sm_count() * 32) g = gsc_sm_count() * 32;
   return (int)(g < 1 ? 1 : g);
 }
 
@@ -753,7 +753,7 @@ cudaError_t launch_batch_encode(int kind, const BatchSceneDev* scenes, int n_sce
   // BC7_SUBS units
   const int64_t units = kind == 7 ? BC7_SUBS : 1;
   const int64_t cta_tiles = ceil_div64(n_tiles, units);
-  int64_t grid = schedule == 3 ? cta_tiles : (int64_t)(sm_count > 0 ? sm_count : 152) * (ctas_per_sm > 0 ? ctas_per_sm : BC7_MIN_BLOCKS);
+  int64_t grid = schedule == 3 ? cta_tiles : (int64_t)(sm_count > 0 ? sm_count : gsc_sm_count()) * (ctas_per_sm > 0 ? ctas_per_sm : BC7_MIN_BLOCKS);
   if (grid > cta_tiles) grid = cta_tiles;
   if (grid > 0x7FFFFFFF) grid = 0x7FFFFFFF;
   if (schedule == 1 || schedule == 2) {

@@ -475,14 +475,14 @@ static int kind_of(const DevTable& T, const void* blocks) {
 static int eval_grid(int64_t n_groups, int sm_count, int warps = 8) {
   int64_t pairs = (n_groups + 1) / 2;
   int64_t g = ceil_div64(pairs, warps);
-  int64_t cap = (int64_t)(sm_count > 0 ? sm_count : 152) * (64 / warps);
+  int64_t cap = (int64_t)(sm_count > 0 ? sm_count : gsc_sm_count()) * (64 / warps);
   return (int)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
 cudaError_t launch_decode(const DevTable& T, const uint8_t* blocks, const int32_t* perm, uint8_t* texels,
                           cudaStream_t st) {
   if (T.n_groups == 0) return cudaSuccess;
-  const int grid = eval_grid(T.n_groups, 152);
+  const int grid = eval_grid(T.n_groups, gsc_sm_count());
 #define DEC_LAUNCH(L)                                                                              \
   do {                                                                                             \
     gsc_count_launch();                                                                            \
@@ -579,7 +579,7 @@ __global__ void k_decode_blocks(const uint8_t* __restrict__ blocks, int64_t nblk
 cudaError_t launch_decode_blocks(const uint8_t* blocks, int64_t nblk, int format, uint8_t* rgba, cudaStream_t st) {
   if (nblk <= 0) return cudaSuccess;
   int64_t grid = ceil_div64(nblk * 16, 256);
-  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid > gsc_sm_count() * 16) grid = gsc_sm_count() * 16;
   gsc_count_launch(); k_decode_blocks<<<(int)grid, 256, 0, st>>>(blocks, nblk, format, reinterpret_cast<uint32_t*>(rgba));
   return cudaGetLastError();
 }
@@ -661,7 +661,7 @@ gsc_status decode_blocks_tex_run(gsc_ctx* ctx, const uint8_t* blocks, int64_t nb
   cudaError_t e = make_tex(blocks, nblk, format == GSC_FMT_BC7, &img, st);
   if (e == cudaSuccess) {
     int64_t grid = ceil_div64(nblk * 16, 256);
-    if (grid > 152 * 16) grid = 152 * 16;
+    if (grid > gsc_sm_count() * 16) grid = gsc_sm_count() * 16;
     gsc_count_launch(); k_tex_blocks<<<(int)grid, 256, 0, st>>>(img.tex, nblk, reinterpret_cast<uint32_t*>(rgba));
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -778,7 +778,7 @@ gsc_status decode_tex_run(gsc_ctx* ctx, const DevTable& T, const uint8_t* blocks
   if (e == cudaSuccess) e = tex_slot(ctx, 0, n1, st, &fresh1);
   if (e != cudaSuccess) return GSC_ERR_CUDA;
   int64_t grid = ceil_div64(T.n_groups * 16, 256);
-  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid > gsc_sm_count() * 16) grid = gsc_sm_count() * 16;
   gsc_count_launch(); k_gather_streams<<<(int)grid, 256, 0, st>>>(T, B, blocks, ctx->tex_lin[1], ctx->tex_lin[0]);
   e = cudaGetLastError();
   // (re)create the arrays if the sizes changed, then copy the staged blocks in stream order
@@ -806,7 +806,7 @@ gsc_status decode_tex_run(gsc_ctx* ctx, const DevTable& T, const uint8_t* blocks
   }
   if (e == cudaSuccess) {
     int64_t g2 = ceil_div64(T.n_groups * 256, 256);
-    if (g2 > 152 * 16) g2 = 152 * 16;
+    if (g2 > gsc_sm_count() * 16) g2 = gsc_sm_count() * 16;
     gsc_count_launch(); k_tex_streams<<<(int)g2, 256, 0, st>>>(T, B, ctx->tex[1].tex, ctx->tex[0].tex, perm, texels);
     e = cudaGetLastError();
   }
@@ -929,7 +929,7 @@ extern "C" gsc_status gsc_tex_scene_create(gsc_ctx* c, const gsc_stream_table* t
   if (e == cudaSuccess) e = cudaMalloc(&lin1, (size_t)(n1 > 0 ? n1 : 1) * 8);
   if (e == cudaSuccess && T.n_groups > 0) {
     int64_t grid = ceil_div64(T.n_groups * 16, 256);
-    if (grid > 152 * 16) grid = 152 * 16;
+    if (grid > gsc_sm_count() * 16) grid = gsc_sm_count() * 16;
     gsc_count_launch(); k_gather_streams<<<(int)grid, 256, 0, s>>>(T, sc->B, d_blocks, lin7, lin1);
     e = cudaGetLastError();
   }
@@ -941,7 +941,7 @@ extern "C" gsc_status gsc_tex_scene_create(gsc_ctx* c, const gsc_stream_table* t
     e = cudaMalloc(&sc->pos_slot, sizeof(float4) * ns);
     if (e == cudaSuccess) {
       int64_t grid = ceil_div64(ns, 256);
-      if (grid > 152 * 16) grid = 152 * 16;
+      if (grid > gsc_sm_count() * 16) grid = gsc_sm_count() * 16;
       gsc_count_launch(); k_pos_slot<<<(int)grid, 256, 0, s>>>(d_pos, d_perm, (int64_t)T.n, ns, sc->pos_slot);
       e = cudaGetLastError();
     }
@@ -987,7 +987,7 @@ extern "C" gsc_status gsc_decode_eval_sh_tex(gsc_ctx* c, const gsc_tex_scene* sc
   GscTimed tm(c, T_EVAL_TEX, st);
   const int64_t ns = (int64_t)T.n_groups * 16;
   int64_t grid = ceil_div64(ns, 256);
-  const int64_t cap = (int64_t)(c->sm_count > 0 ? c->sm_count : 152) * 8;
+  const int64_t cap = (int64_t)(c->sm_count > 0 ? c->sm_count : gsc_sm_count()) * 8;
   if (grid > cap) grid = cap;
   const int kind = kind_of(T);
   // 8 views into Gaussian-major rows (the camera-pose workload) run a compile-time view count

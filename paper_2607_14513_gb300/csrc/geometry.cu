@@ -106,6 +106,11 @@ extern "C" size_t gsc_geometry_bytes(int64_t n_slots, int64_t chunk_slots) {
   return geom_bytes(n_slots, chunk_slots, nullptr);
 }
 
+extern "C" size_t gsc_geometry_layout(int64_t n_slots, int64_t chunk_slots, size_t* offsets) {
+  if (n_slots < 0 || chunk_slots < 16 || chunk_slots % 16 || !offsets) return 0;
+  return geom_bytes(n_slots, chunk_slots, offsets);
+}
+
 extern "C" gsc_status gsc_geometry_encode(gsc_ctx* c, const float* d_pos, const float* d_scale, const float* d_rot,
                                           const float* d_logit, const int32_t* d_perm, int64_t n_slots,
                                           int64_t chunk_slots, uint8_t* d_geom, void* stream) {
@@ -122,7 +127,7 @@ extern "C" gsc_status gsc_geometry_encode(gsc_ctx* c, const float* d_pos, const 
   k_chunk_bounds<<<(unsigned)nc, 256, 0, st>>>(d_pos, d_scale, d_perm, n_slots, chunk_slots, G.chunk);
   GSC_CUDA(cudaGetLastError());
   int64_t grid = ceil_div64(n_slots, 256);
-  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid > gsc_sm_count() * 16) grid = gsc_sm_count() * 16;
   gsc_count_launch();
   k_geometry_encode<<<(int)grid, 256, 0, st>>>(d_pos, d_scale, reinterpret_cast<const float4*>(d_rot), d_logit, d_perm,
                                                n_slots, chunk_slots, G);

@@ -48,6 +48,8 @@ static inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; 
 
 // Host-side count of kernel launches (measurement only).
 void gsc_count_launch();
+// Streaming multiprocessors of the current device (queried once per device; grids are sized from it).
+int gsc_sm_count();
 // Event pair around a kernel when the context's timing is on (measurement only).
 int gsc_timer_begin(gsc_ctx* c, int id, cudaStream_t st);
 void gsc_timer_end(gsc_ctx* c, int rec, cudaStream_t st);

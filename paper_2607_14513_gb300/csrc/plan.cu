@@ -271,7 +271,7 @@ __global__ void k_quantise(const float4* __restrict__ sh4, int64_t n4, const flo
   }
 }
 
-static int grid_stride(int64_t n, int threads, int cap = 152 * 8) {
+static int grid_stride(int64_t n, int threads, int cap = gsc_sm_count() * 8) {
   int64_t g = ceil_div64(n > 0 ? n : 1, threads);
   return (int)(g > cap ? cap : g);
 }
@@ -442,7 +442,9 @@ gsc_status plan_run(gsc_ctx* ctx, const float* pos, const float* sh, const gsc_p
 // ---- allocation-free variant of gsc_plan_reorder ------------------------------------------
 // Scratch lives in this file-scope device array instead of a caller workspace. Every GPU
 // that loads the library holds it (2 MiB) until the process exits. Its device address is
-// looked up once per device, with that device current, on the first call there.
+// looked up once per device, with that device current, on the first call there, and kept for
+// the life of the process: a cudaDeviceReset of that device invalidates it (the module is loaded
+// again, possibly elsewhere), so this entry point must not be used after such a reset.
 #define GSC_PLAN_STATIC_BYTES (2u << 20)
 #define GSC_MAX_DEVICES 64
 static __device__ __align__(256) uint8_t g_plan_scratch[GSC_PLAN_STATIC_BYTES];
@@ -472,5 +474,6 @@ extern "C" gsc_status gsc_plan_reorder_static(gsc_ctx* c, const float* d_pos, co
     }
     ws = g_plan_scratch_ptr[c->device];
   }
+  GscTimed tm(c, T_PLAN, (cudaStream_t)stream);
   return plan_run(c, d_pos, d_sh, pp, d_perm, d_scales, ws, GSC_PLAN_STATIC_BYTES, (cudaStream_t)stream);
 }

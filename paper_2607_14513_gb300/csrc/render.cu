@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(RTHREADS) k_render(const uint2* __restrict__ r
 
 int grid_of(int64_t work) {
   int64_t g = ceil_div64(work, 256);
-  if (g > 152 * 16) g = 152 * 16;
+  if (g > gsc_sm_count() * 16) g = gsc_sm_count() * 16;
   return (int)(g < 1 ? 1 : g);
 }
 

@@ -145,6 +145,8 @@ _SIGS = {
     "gsc_decode_eval_sh_tex": [_P, _P, _P, _P, _P, _P, C.c_int32, C.c_int32, _P, _P],
     "gsc_render_workspace_bytes": [C.c_int64, C.POINTER(Camera), C.c_int64],
     "gsc_geometry_bytes": [C.c_int64, C.c_int64],
+    "gsc_geometry_layout": [C.c_int64, C.c_int64, C.POINTER(C.c_size_t)],
+    "gsc_forced_table": [C.POINTER(StreamTable), C.c_int32, C.POINTER(StreamTable)],
     "gsc_geometry_encode": [_P, _P, _P, _P, _P, _P, C.c_int64, C.c_int64, _P, _P],
     "gsc_render_coded": [_P, C.POINTER(StreamTable), _P, _P, _P, C.c_int64, C.POINTER(Camera), _P, _P,
                          C.POINTER(C.c_int64), C.POINTER(C.c_int64), _P, C.c_size_t, _P],
@@ -210,6 +212,7 @@ def load(path: str | None = None):
             lib.gsc_batch_workspace_bytes.restype = C.c_size_t
             lib.gsc_render_workspace_bytes.restype = C.c_size_t
             lib.gsc_geometry_bytes.restype = C.c_size_t
+            lib.gsc_geometry_layout.restype = C.c_size_t
             _lib = lib
     return _lib
 
@@ -310,17 +313,10 @@ def gsc_encode(ctx, sh, perm, scales, fmt, target_x4=0, ws=None, out=None, perm_
 
 
 def forced_table(table, fmt):
-    """Stream table of the all-BC1 / all-BC7 coding that shares `table`'s scene, scales and layout."""
+    """Stream table of the all-BC1 / all-BC7 coding that shares `table`'s scene, scales and layout
+    (gsc_forced_table)."""
     t = StreamTable()
-    t.n_streams, t.format, t.n, t.n_groups = 1, fmt, table.n, table.n_groups
-    t.layout = table.layout
-    bpb = 16 if fmt == FMT_BC7 else 8
-    t.total_bytes = table.n_groups * 16 * bpb
-    t.used_bits = t.total_bytes * 8
-    t.scales[:] = table.scales[:]
-    t.weights[:] = table.weights[:]
-    t.s[0].bands, t.s[0].bc7_blocks = 16, (16 if fmt == FMT_BC7 else 0)
-    t.s[0].first_group, t.s[0].n_groups, t.s[0].byte_offset = 0, table.n_groups, 0
+    _check(load().gsc_forced_table(C.byref(table), fmt, C.byref(t)), "gsc_forced_table")
     return t
 
 
@@ -437,15 +433,13 @@ def gsc_decode_eval_sh_tex(ctx, scene, perm, dirs=None, pos=None, cams=None, out
 
 
 def geometry_layout(n_slots, chunk_slots):
-    """Byte offsets of (qpos, qscale, qrot, qlogit, chunks) in a geometry buffer and its size, as
-    include/gsc.h lays them out (each 256-byte aligned)."""
-    al = lambda v: (v + 255) // 256 * 256
-    nc = (n_slots + chunk_slots - 1) // chunk_slots
-    off, b = [], 0
-    for size in (6 * n_slots, 6 * n_slots, 4 * n_slots, n_slots, 32 * max(nc, 1)):
-        off.append(b)
-        b = al(b + size)
-    return off, b
+    """Byte offsets of (qpos, qscale, qrot, qlogit, chunks) in a geometry buffer and its size
+    (gsc_geometry_layout)."""
+    off = (C.c_size_t * 5)()
+    size = load().gsc_geometry_layout(n_slots, chunk_slots, off)
+    if size == 0:
+        raise GscError(1, "gsc_geometry_layout")  # GSC_ERR_INVALID_ARG
+    return list(off), int(size)
 
 
 def gsc_geometry_encode(ctx, pos, scale, rot, logit, perm, chunk_slots=4096, out=None, stream=None):

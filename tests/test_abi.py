@@ -178,11 +178,23 @@ def test_host_size_queries():
     from paper_2607_14513_gb300 import gsc
     from paper_2607_14513_gb300 import synthetic as S
     lib = gsc.load()
+    # the geometry buffer as the header lays it out: five sections (6, 6, 4 and 1 bytes per slot,
+    # 32 bytes per chunk), each starting 256-byte aligned
+    al = lambda v: (v + 255) // 256 * 256
     for ns in (0, 16, 4096, 4112, 3_000_016):
         for cs in (16, 128, 4096):
-            assert lib.gsc_geometry_bytes(ns, cs) == gsc.geometry_layout(ns, cs)[1], (ns, cs)
+            nc = (ns + cs - 1) // cs
+            want, b = [], 0
+            for size in (6 * ns, 6 * ns, 4 * ns, ns, 32 * max(nc, 1)):
+                want.append(b)
+                b = al(b + size)
+            off, size = gsc.geometry_layout(ns, cs)
+            assert (off, size) == (want, b), (ns, cs)
+            assert lib.gsc_geometry_bytes(ns, cs) == b, (ns, cs)
     for ns, cs in ((-16, 16), (16, 0), (16, 8), (16, 24), (16, -16)):
         assert lib.gsc_geometry_bytes(ns, cs) == 0, (ns, cs)
+        with pytest.raises(gsc.GscError):
+            gsc.geometry_layout(ns, cs)
     cam = gsc.camera(S.look_at([0.5, 0.5, -1.5], [0.5, 0.5, 0.5], 1920, 1080))
     sizes = [lib.gsc_render_workspace_bytes(n, ctypes.byref(cam), p)
              for n, p in ((0, 0), (1000, 0), (1000, 10**6), (10**6, 10**6), (3 * 10**6, 3 * 10**7))]
@@ -204,3 +216,31 @@ def test_missing_library_fails_loudly(tmp_path):
             gsc.load(str(tmp_path / "libgsc.so"))
     finally:
         gsc._lib = saved
+
+
+def test_forced_table():
+    # host only: the all-BC1 / all-BC7 table of a scene from any valid stream table of it
+    from paper_2607_14513_gb300 import gsc
+    lib = gsc.load()
+    n, ng = 1000, 63
+    t = gsc.StreamTable()
+    t.n_streams, t.format, t.n, t.n_groups, t.layout = 2, gsc.FMT_RATE, n, ng, gsc.LAYOUT_D
+    t.s[0].bands, t.s[0].bc7_blocks, t.s[0].first_group, t.s[0].n_groups, t.s[0].byte_offset = 16, 1, 0, 40, 0
+    t.s[1].bands, t.s[1].bc7_blocks, t.s[1].first_group, t.s[1].n_groups = 4, 0, 40, 23
+    t.s[1].byte_offset = 40 * (16 + 15 * 8)
+    t.total_bytes = t.s[1].byte_offset + 23 * 4 * 8
+    for k in range(16):
+        t.scales[k], t.weights[k] = 0.25 + k, 1000 + k
+    for fmt, bpb, j in ((gsc.FMT_BC1, 8, 0), (gsc.FMT_BC7, 16, 16)):
+        f = gsc.forced_table(t, fmt)
+        assert (f.n_streams, f.format, f.n, f.n_groups, f.layout) == (1, fmt, n, ng, gsc.LAYOUT_D)
+        assert (f.s[0].bands, f.s[0].bc7_blocks, f.s[0].first_group, f.s[0].n_groups, f.s[0].byte_offset) == \
+            (16, j, 0, ng, 0)
+        assert f.total_bytes == ng * 16 * bpb and f.used_bits == 8 * f.total_bytes
+        assert (f.budget_bits, f.lambda_) == (0, 0)
+        assert list(f.scales) == list(t.scales) and list(f.weights) == list(t.weights)
+    out = gsc.StreamTable()
+    assert lib.gsc_forced_table(ctypes.byref(t), gsc.FMT_RATE, ctypes.byref(out)) == 1
+    assert lib.gsc_forced_table(ctypes.byref(t), gsc.FMT_MIXED, ctypes.byref(out)) == 1
+    t.total_bytes += 8  # no longer the sum of its streams
+    assert lib.gsc_forced_table(ctypes.byref(t), gsc.FMT_BC7, ctypes.byref(out)) == 1
