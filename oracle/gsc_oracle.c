@@ -809,8 +809,38 @@ uint64_t or_bc7_candidate(const uint8_t* tex, int e, uint8_t* out) {
   return S.sse;
 }
 
-/* Sec. III-B; BC7 format: the least-error candidate, first on ties. */
+/* Constant blocks (Sec. III-A: the error of a block whose texels are all one colour can go to
+ * zero; the format reaches every constant colour). Mode 5, rotation 0, every colour index 1: the
+ * 2-bit index's weight 21 interpolates two 7-bit endpoint codes, and for every 8-bit value v some
+ * pair (a, b) gives ((64 - 21) ex7(a) + 21 ex7(b) + 32) >> 6 = v. Per channel the pair found first
+ * with a = 0..127 outer, b = 0..127 inner is taken; alpha codes are all ones, alpha indices 0. */
+static void bc7_const_pair(int v, int* a, int* b) {
+  for (int i = 0; i < 128; i++)
+    for (int j = 0; j < 128; j++)
+      if (interp7(expand_bits(i, 7), expand_bits(j, 7), WT2[1]) == v) { *a = i; *b = j; return; }
+  *a = *b = 0; /* not reached: every value has a pair */
+}
+
+static void bc7_const_block(const uint8_t* rgb, uint8_t* out) {
+  bc7_sol S;
+  memset(&S, 0, sizeof(S));
+  S.c.mode = 5;
+  for (int c = 0; c < 3; c++) bc7_const_pair(rgb[c], &S.code[0][0][c], &S.code[0][1][c]);
+  S.code[0][0][3] = S.code[0][1][3] = 255;
+  for (int t = 0; t < 16; t++) { S.cidx[t] = 1; S.aidx[t] = 0; }
+  bc7_pack(&S, out);
+}
+
+/* Sec. III-B; BC7 format: a constant block as above (error 0), otherwise the least-error
+ * candidate, first on ties. */
 uint64_t or_bc7_encode(const uint8_t* tex, uint8_t* out) {
+  int constant = 1;
+  for (int t = 1; t < 16; t++)
+    if (tex[3 * t] != tex[0] || tex[3 * t + 1] != tex[1] || tex[3 * t + 2] != tex[2]) constant = 0;
+  if (constant) {
+    if (out) bc7_const_block(tex, out);
+    return 0;
+  }
   int ne = or_bc7_n_candidates(), best_e = 0;
   uint64_t best = UINT64_MAX;
   for (int e = 0; e < ne; e++) {

@@ -25,6 +25,8 @@ __constant__ uint8_t c_anc3a[64];
 __constant__ uint8_t c_anc3b[64];
 // nearest endpoint code per 8-bit target: code | expanded value << 8, 12 configurations
 __device__ uint16_t g_qtab[12][256];
+// constant blocks: per 8-bit value the 7-bit code pair a | b << 8 of mode 5 at weight 21
+__constant__ uint16_t c_const7[256];
 cudaError_t bc7_kernel_attributes();
 
 static int h_expand(int v, int n) { return n >= 8 ? v : ((v << (8 - n)) | (v >> (2 * n - 8))); }
@@ -54,7 +56,18 @@ cudaError_t bc7_init_tables() {
       q[c][e] = (uint16_t)(best | (bv << 8));
     }
   }
+  // Constant blocks: every 8-bit value v is ((64 - 21) ex7(a) + 21 ex7(b) + 32) >> 6 for some 7-bit
+  // pair; the first with a outer and b inner is taken.
+  uint16_t c7[256];
+  for (int v = 0; v < 256; v++) {
+    c7[v] = 0;
+    bool found = false;
+    for (int a = 0; a < 128 && !found; a++)
+      for (int b = 0; b < 128 && !found; b++)
+        if (((64 - 21) * h_expand(a, 7) + 21 * h_expand(b, 7) + 32) >> 6 == v) { c7[v] = (uint16_t)(a | (b << 8)); found = true; }
+  }
   cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(c_const7, c7, sizeof(c7))) != cudaSuccess) return e;
   uint16_t t5[256], t6[256];
   bc1_const_tables(t5, t6);
   if ((e = cudaMemcpyToSymbol(c_const5, t5, sizeof(t5))) != cudaSuccess) return e;
@@ -576,6 +589,36 @@ __device__ __noinline__ uint4 solve_pack(const uint32_t* tx, int e, const uint16
   return make_uint4(w.w[0], w.w[1], w.w[2], w.w[3]);
 }
 
+// Constant blocks (Sec. III-A: a block of one colour can be coded without error; the format
+// reaches every constant colour): mode 5, rotation 0, every colour index 1 (weight 21), per
+// channel the code pair of c_const7, alpha codes all ones and alpha indices 0. Texel t of the
+// thread's block is tx[t * STAGE_STRIDE]; returns whether the block is constant.
+__device__ __forceinline__ bool const_block(const uint32_t* tx, uint4* out) {
+  const uint32_t c = tx[0];
+  bool same = true;
+#pragma unroll
+  for (int t = 1; t < 16; t++) same &= tx[t * STAGE_STRIDE] == c;
+  if (!same) return false;
+  BitW w;
+  w.w[0] = w.w[1] = w.w[2] = w.w[3] = 0;
+  w.pos = 0;
+  w.put(1u << 5, 6);  // mode 5
+  w.put(0u, 2);       // rotation 0
+  for (int ch = 0; ch < 3; ch++) {
+    const uint32_t ab = c_const7[(c >> (8 * ch)) & 255u];
+    w.put(ab & 255u, 7);
+    w.put(ab >> 8, 7);
+  }
+  w.put(255u, 8);
+  w.put(255u, 8);
+  w.put(1u, 1);  // texel 0's colour index (anchor: one bit)
+  for (int t = 1; t < 16; t++) w.put(1u, 2);
+  w.put(0u, 1);  // alpha indices 0
+  for (int t = 1; t < 16; t++) w.put(0u, 2);
+  *out = make_uint4(w.w[0], w.w[1], w.w[2], w.w[3]);
+  return true;
+}
+
 // One kernel for both sources: staged layout-D groups (sh / perm / scales) or raw
 // texels [nblk][16][3] (texin != nullptr), so the search is compiled once. A CTA is BC7_SUBS
 // staging units of 128 threads (one block per thread); each thread's texels stay in its unit's
@@ -626,7 +669,13 @@ __global__ void __launch_bounds__(BC7_THREADS, 1) k_bc7(const float* __restrict_
     const uint32_t* my = &tex[sub][0][lt];
     const int e = search_best<true>(my, &best, sq);
     if (blk < total) {
-      blocks[blk] = solve_pack(my, e, sq);
+      uint4 cb;
+      if (const_block(my, &cb)) {
+        blocks[blk] = cb;
+        best = 0;
+      } else {
+        blocks[blk] = solve_pack(my, e, sq);
+      }
       if (sse7) sse7[blk] = best;
       if (sse64) sse64[blk] = best;
     }
@@ -737,7 +786,10 @@ __global__ void __launch_bounds__((KIND == 7 ? BC7_SUBS : 1) * STAGE_THREADS, KI
         const uint32_t* my = &tex[sub][0][lt];
         const int e = search_best<true>(my, &best, sq);
         if (write) {
-          reinterpret_cast<uint4*>(S.b7)[blk] = solve_pack(my, e, sq);
+          uint4 cb;
+          if (const_block(my, &cb)) best = 0;
+          else cb = solve_pack(my, e, sq);
+          reinterpret_cast<uint4*>(S.b7)[blk] = cb;
           if (S.sse7) S.sse7[blk] = best;
         }
       }

@@ -193,3 +193,80 @@ def test_encoder_against_local_brute_force(O):
                 if 0 <= v <= mask:
                     cc[ep] = (cc[ep] & ~(mask << sh)) | (v << sh)
                     assert O.bc1_candidate_sse(tex, cc[0], cc[1]) >= best
+
+
+def _code(r, g, b):
+    return (r << 11) | (g << 5) | b
+
+
+def test_tiny_blocks_global_brute_force(O):
+    # Blocks drawn from the palette of one endpoint pair inside a 4x4x4 box of 565 codes: an
+    # exhaustive search over every ordered pair in the box finds error 0, so the global minimum is
+    # 0 and the encoder's gap to it is its own error. The encoder reaches it on most blocks.
+    rng = np.random.default_rng(7)
+    tex, boxes = [], []
+    for _ in range(300):
+        r0, g0, b0 = int(rng.integers(0, 29)), int(rng.integers(0, 61)), int(rng.integers(0, 29))
+        box = [_code(r0 + i, g0 + j, b0 + k) for i in range(4) for j in range(4) for k in range(4)]
+        a, b = rng.choice(box, 2, replace=False)
+        pal = O.bc1_palette(int(max(a, b)), int(min(a, b))).reshape(4, 4)[:, :3]
+        used = rng.choice(4, size=int(rng.integers(2, 5)), replace=False)
+        t = pal[used[rng.integers(0, len(used), 16)]].astype(np.uint8)
+        t[:len(used)] = pal[used]
+        tex.append(t)
+        boxes.append(box)
+    tex = np.array(tex)
+    blocks, sse = O.encode_blocks(tex, 1, threads=8)
+    for i in range(12):                               # the exhaustive search, on a subset
+        best = min(O.bc1_candidate_sse(tex[i], c0, c1) for c0 in boxes[i] for c1 in boxes[i])
+        assert best == 0
+    exact = int((sse == 0).sum())
+    gaps = np.sort(sse[sse > 0])
+    print("BC1 tiny blocks: encoder at the global minimum on %d of %d; gaps %s" % (exact, len(sse), gaps.tolist()))
+    assert exact >= 275
+
+
+def _mid_table(O, ch):
+    """(x + y) / 2 for every code pair of channel ch, read from three-colour palettes."""
+    bits = 6 if ch == 1 else 5
+    sh = {0: 11, 1: 5, 2: 0}[ch]
+    lim = 1 << bits
+    tab = np.zeros((lim, lim), np.int64)
+    for x in range(lim):
+        for y in range(lim):
+            if ch != 0:                       # R decides the mode: c0 <= c1 always
+                tab[x, y] = O.bc1_palette(x << sh, (31 << 11) | (y << sh))[2, ch]
+            else:                             # G breaks the tie in favour of c1
+                tab[x, y] = O.bc1_palette(x << 11, (y << 11) | (63 << 5))[2, 0]
+    return tab
+
+
+def test_encoder_above_a_relaxed_global_lower_bound(O):
+    # A global lower bound on any BC1 block's error: let every channel choose its own endpoint
+    # codes and its own index per texel, in each mode (four colours: the endpoints and both
+    # thirds; three colours: the endpoints, the midpoint and 0); the block's error is at least
+    # the smaller mode's sum over channels of those per-channel minima.
+    exp = {0: ex5, 1: ex6, 2: ex5}
+    rng = np.random.default_rng(10)
+    tex = rng.integers(0, 256, size=(64, 16, 3))
+    tex[:32] = np.clip(rng.integers(30, 220, size=(32, 1, 3)) + rng.integers(-20, 21, size=(32, 16, 3)), 0, 255)
+    tex = tex.astype(np.uint8)
+    blocks, sse = O.encode_blocks(tex, 1, threads=8)
+    lb4 = np.zeros(len(tex), np.int64)
+    lb3 = np.zeros(len(tex), np.int64)
+    for ch in range(3):
+        lim = 64 if ch == 1 else 32
+        e = np.array([exp[ch](v) for v in range(lim)])
+        third, mid = _third_table(O, ch), _mid_table(O, ch)
+        ea, eb = np.broadcast_to(e[:, None], (lim, lim)), np.broadcast_to(e[None, :], (lim, lim))
+        p4 = np.stack([ea, eb, third, third.T], -1)                       # [a, b, entry]
+        p3 = np.stack([ea, eb, mid, np.zeros_like(mid)], -1)
+        v = tex[:, :, ch].astype(np.int64)                                 # [block, texel]
+        for p, lb in ((p4, lb4), (p3, lb3)):
+            err = ((p[None, None] - v[:, :, None, None, None]) ** 2).min(-1).sum(1)   # [block, a, b]
+            lb += err.reshape(len(tex), -1).min(1)
+    lb = np.minimum(lb4, lb3)
+    assert np.all(sse.astype(np.int64) >= lb)
+    assert np.all(lb[32:] > 0)
+    print("BC1 relaxed bound: encoder / bound, median %.3f, max %.3f" % (np.median(sse / np.maximum(lb, 1)),
+                                                                       (sse / np.maximum(lb, 1)).max()))

@@ -175,9 +175,10 @@ def test_encoder_is_the_first_minimum(O):
         blocks, sse = O.encode_blocks(tex[None], 7, threads=1)
         assert int(sse[0]) == min(errs)
         assert np.array_equal(blocks[0], O.bc7_candidate(tex, first)[1])
-    # ties: blocks that many candidates code without error take the first of them
-    ties = [np.tile(np.array([64, 128, 200], np.uint8), (16, 1)),
-            np.where((np.arange(16) % 2)[:, None] == 0, [16, 32, 48], [200, 100, 50]).astype(np.uint8)]
+    # ties: blocks that many candidates code without error take the first of them (constant
+    # blocks have their own rule, test_constant_colours_round_trip_wherever_reachable)
+    ties = [np.where((np.arange(16) % 2)[:, None] == 0, [16, 32, 48], [200, 100, 50]).astype(np.uint8),
+            np.where((np.arange(16) < 8)[:, None], [66, 132, 198], [0, 255, 0]).astype(np.uint8)]
     for tex in ties:
         errs = np.array([O.bc7_candidate(tex, e)[0] for e in range(ne)])
         assert (errs == errs.min()).sum() > 1
@@ -185,19 +186,122 @@ def test_encoder_is_the_first_minimum(O):
         assert np.array_equal(blocks[0], O.bc7_candidate(tex, int(np.argmin(errs)))[1])
 
 
-def test_constant_colours(O):
-    # colours whose channels share one parity are exact in mode 6 (7-bit codes + shared p-bit)
+W2 = [0, 21, 43, 64]
+W3 = [0, 9, 18, 27, 37, 46, 55, 64]
+
+
+def _expand(v, n):
+    return v if n >= 8 else (v << (8 - n)) | (v >> (2 * n - 8))
+
+
+def _reach(bits, p0, p1, has_p, w):
+    """8-bit values ((64 - w) e0 + w e1 + 32) >> 6 of all endpoint code pairs (with p-bits)."""
+    codes = np.arange(1 << bits)
+    e0 = np.array([_expand((c << 1) | p0 if has_p else c, bits + has_p) for c in codes])
+    e1 = np.array([_expand((c << 1) | p1 if has_p else c, bits + has_p) for c in codes])
+    out = np.zeros(256, bool)
+    out[((64 - w) * e0[:, None] + w * e1[None, :] + 32) >> 6] = True
+    return out
+
+
+def _constant_reach_sets():
+    """Per mode, the (R, G, B) value sets whose product a constant block reaches exactly: every
+    texel takes one index weight, p-bits are shared by an endpoint's channels; modes 4 and 5 code
+    the rotated channel in the alpha endpoints with their own index."""
+    sets = {}
+    # mode: colour bits, p-bit kind (0 none, 1 per endpoint, 2 shared by the endpoints), index weights
+    for m, bits, pk, ws in ((0, 4, 1, W3), (1, 6, 2, W3), (2, 5, 0, W2), (3, 7, 1, W2), (6, 7, 1, W4), (7, 5, 1, W2)):
+        combos = [(0, 0)] if pk == 0 else ([(a, b) for a in (0, 1) for b in (0, 1)] if pk == 1 else [(0, 0), (1, 1)])
+        sets[m] = [(r, r, r) for p0, p1 in combos for w in ws for r in [_reach(bits, p0, p1, pk > 0, w)]]
+    for m, cb, ab, pairs in ((4, 5, 6, ((W2, W3), (W3, W2))), (5, 7, 8, ((W2, W2),))):
+        sets[m] = []
+        for cw, aw in pairs:
+            alpha = np.zeros(256, bool)
+            for w in aw:
+                alpha |= _reach(ab, 0, 0, 0, w)
+            for w in cw:
+                c = _reach(cb, 0, 0, 0, w)
+                sets[m] += [(c, c, c), (alpha, c, c), (c, alpha, c), (c, c, alpha)]
+    return sets
+
+
+def test_constant_colours_round_trip_wherever_reachable(O):
+    # Sec. III-A: a block whose texels are one colour can be coded without error where the format
+    # reaches the colour. The brute force above decides reachability from the format alone; every
+    # colour reached by some mode must come back exactly.
+    sets = _constant_reach_sets()
+    reach = lambda c: [m for m, ss in sets.items() if any(R[c[0]] and G[c[1]] and B[c[2]] for R, G, B in ss)]
     rng = np.random.default_rng(14)
-    cols = [(0, 0, 0), (255, 255, 255), (128, 64, 2), (1, 3, 255)]
-    cols += [tuple((rng.integers(0, 128, size=3) * 2 + rng.integers(0, 2)).tolist()) for _ in range(10)]
+    cols = [(v, v, v) for v in range(256)] + [(v, 37, 200) for v in range(256)] + [(9, v, 90) for v in range(256)]
+    cols += [(250, 3, v) for v in range(256)] + [tuple(int(x) for x in rng.integers(0, 256, 3)) for _ in range(1500)]
+    modes = [reach(c) for c in cols]
+    assert all(5 in ms for ms in modes)      # mode 5 at weight 21 reaches every value ...
+    assert any(2 not in ms for ms in modes)  # ... which mode 2 (5-bit, no p-bits) does not
+    grey = [sum(any(R[v] and G[v] and B[v] for R, G, B in sets[m]) for v in range(256)) for m in range(8)]
+    assert grey == [255, 256, 210, 256, 255, 256, 256, 251]
     tex = np.array([np.tile(np.array(c, np.uint8), (16, 1)) for c in cols])
-    _, sse = O.encode_blocks(tex, 7, threads=1)
+    blocks, sse = O.encode_blocks(tex, 7, threads=8)
     assert np.all(sse == 0)
-    # any constant colour is reproduced within one level per channel
-    cols = rng.integers(0, 256, size=(16, 3))
-    tex = np.repeat(cols[:, None, :], 16, axis=1).astype(np.uint8)
-    _, sse = O.encode_blocks(tex, 7, threads=4)
-    assert np.all(sse <= 48)
+    for i in range(len(cols)):
+        assert np.array_equal(O.bc7_decode(blocks[i])[:, :3], tex[i]), cols[i]
+    # the encoder's constant rule: mode 5 (first byte 0b00100000), rotation 0, colour index 1
+    assert np.all(blocks[:, 0] == 0x20)
+    bits = [int.from_bytes(bytes(b), "little") for b in blocks[:8]]
+    for v in bits:
+        assert (v >> 6) & 3 == 0                              # rotation
+        ci = v >> 66                                          # 6 + 2 + 42 + 16 header and endpoint bits
+        assert ci & 1 == 1 and all((ci >> (1 + 2 * t)) & 3 == 1 for t in range(15))
+
+
+def test_mode6_fit_least_squares_by_hand(O):
+    # One-subset fit of the mode-6 candidate (7-bit endpoints, a p-bit per endpoint, 4-bit
+    # indices), worked by hand. R varies, G = 100 and B = 50 are constant.
+    R = [255] * 4 + [230] * 4 + [0] * 8
+    tex = np.array([[r, 100, 50] for r in R], np.uint8)
+    # bounding-box diagonal: R spans most, G and B do not vary: e0 = (255, 100, 50), e1 = (0, 100, 50)
+    interp = lambda a, b, w: ((64 - w) * a + w * b + 32) >> 6
+    # nearest weights against e0 / e1: 255 -> index 0 (w 0); 230 -> index 1 (w 4: 239, error 9;
+    # index 2, w 9: 219, error 11); 0 -> index 15 (w 64)
+    assert interp(255, 0, 4) == 239 and interp(255, 0, 9) == 219
+    idx = [0] * 4 + [1] * 4 + [15] * 8
+    a = [64 - W4[j] for j in idx]
+    b = [W4[j] for j in idx]
+    # normal equations of the least-squares endpoints E0, E1 minimising sum (a E0 + b E1 - 64 v)^2
+    saa = 4 * 64 * 64 + 4 * 60 * 60 + 8 * 0
+    sbb = 4 * 0 + 4 * 4 * 4 + 8 * 64 * 64
+    sab = 4 * 0 + 4 * 60 * 4 + 8 * 0
+    sav = 4 * 64 * 255 + 4 * 60 * 230
+    sbv = 4 * 4 * 230
+    assert (saa, sbb, sab, sav, sbv) == (30784, 32832, 960, 120480, 3680)
+    assert (saa, sbb, sab) == (sum(x * x for x in a), sum(y * y for y in b), sum(x * y for x, y in zip(a, b)))
+    assert (sav, sbv) == (sum(x * v for x, v in zip(a, R)), sum(y * v for y, v in zip(b, R)))
+    det = saa * sbb - sab * sab
+    assert det == 1009778688
+    # E0 = 64 (sbb sav - sab sbv) / det = 252932259840 / det = 250.48 -> 250
+    # E1 = 64 (saa sbv - sab sav) / det = -152043520 / det = -0.15 -> 0
+    assert 64 * (sbb * sav - sab * sbv) == 252932259840 and 64 * (saa * sbv - sab * sav) == -152043520
+    # (G and B: 64 (sbb - sab) sum(a) v / det = v exactly for a constant channel)
+    # p-bits: (0, 0) codes (250, 100, 50) and (0, 100, 50) exactly (all even); re-indexed, 255 -> 250
+    # (error 5), 230 -> interp(250, 0, w 4) = 234 (error 4), 0 -> 0: error 4 (25 + 16) = 164; the other
+    # combinations move G or B off by one on every texel and cost more
+    assert interp(250, 0, 4) == 234
+    sse, blk = O.bc7_candidate(tex, 16 + 192 + 8 + 4)   # the mode-6 candidate
+    dec = O.bc7_decode(blk)[:, :3].astype(int)
+    assert sse == 164
+    assert dec[:, 0].tolist() == [250] * 4 + [234] * 4 + [0] * 8
+    assert np.all(dec[:, 1] == 100) and np.all(dec[:, 2] == 50)
+
+
+def test_nearest_code_ties_go_to_the_lower_code(O):
+    # The mode-6 candidate of the constant colour (254, 101, 51): the fit keeps e0 = e1 = the colour.
+    # With p-bit 1 an endpoint's values are odd, and 254 lies halfway between 253 (code 126) and 255
+    # (code 127): the lower code wins. With p0 = 1, p1 = 0 the block codes (253, 101, 51) and
+    # (254, 100, 50); index 0 everywhere costs 1 per texel (16), less than (0, 0) (G and B off by one:
+    # 32) and no more than (0, 1) or (1, 1) (16 each, later in the order)
+    tex = np.tile(np.array([254, 101, 51], np.uint8), (16, 1))
+    sse, blk = O.bc7_candidate(tex, 16 + 192 + 8 + 4)
+    assert sse == 16
+    assert O.bc7_decode(blk)[:, :3].tolist() == [[253, 101, 51]] * 16
 
 
 def test_two_subset_partitions_exact(O):

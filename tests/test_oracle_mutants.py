@@ -55,7 +55,7 @@ MUTANTS = {
     "BC7 endpoint expansion without bit replication": (
         [("static int expand_bits(int v, int n) { return n >= 8 ? v : ((v << (8 - n)) | (v >> (2 * n - 8))); }",
           "static int expand_bits(int v, int n) { return n >= 8 ? v : (v << (8 - n)); }")],
-        [T_BC7.test_hand_built_mode1_membership, T_BC7.test_hand_built_mode4_rotation, T_BC7.test_constant_colours]),
+        [T_BC7.test_hand_built_mode1_membership, T_BC7.test_hand_built_mode4_rotation, T_BC7.test_constant_colours_round_trip_wherever_reachable]),
     "SH without the Condon-Shortley phase": (
         [("for (int i = 1; i <= m; i++) pmm *= -(2.0 * i - 1.0) * s;",
           "for (int i = 1; i <= m; i++) pmm *= (2.0 * i - 1.0) * s;")],
@@ -192,7 +192,7 @@ MUTANTS = {
         [T_BC7.test_two_subset_partitions_exact, T_BC7.test_three_subset_partitions_exact]),
     "BC7 fit tries only the first p-bit combination": (
         [("int ncombo = ptype == 0 ? 1 : (ptype == 1 ? 4 : 2);", "int ncombo = 1;")],
-        [T_BC7.test_constant_colours, T_BC7.test_two_subset_partitions_exact,
+        [T_BC7.test_constant_colours_round_trip_wherever_reachable, T_BC7.test_two_subset_partitions_exact,
          T_BC7.test_three_subset_partitions_exact]),
     "decode places a texel with its neighbour slot's Gaussian": (
         [("          int32_t o = perm[16 * g + u];\n          if (o < 0) continue;",
@@ -235,6 +235,20 @@ MUTANTS = {
         [("    if (!(u < -64.0f)) left = 0;\n    if (!(u > W + 64.0f)) right = 0;",
           "    if (!(u < 0.0f)) left = 0;\n    if (!(u > W + 0.0f)) right = 0;")],
         [T_GEO.test_culling_keeps_adversarial_chunks]),
+    "BC7 nearest endpoint code keeps the last of equal distances": (
+        [("    if (be < 0 || d < be) { be = d; best = code; }\n  }\n  return best;",
+          "    if (be < 0 || d <= be) { be = d; best = code; }\n  }\n  return best;")],
+        [T_BC7.test_nearest_code_ties_go_to_the_lower_code]),
+    "BC7 fit without its least-squares step": (
+        [("  if (det != 0)\n    for (int i = 0; i < nch; i++) {\n      e0[i] = clampi(",
+          "  if (0)\n    for (int i = 0; i < nch; i++) {\n      e0[i] = clampi(")],
+        [T_BC7.test_mode6_fit_least_squares_by_hand]),
+    "BC1 encoder without its least-squares refinements": (
+        [("  for (int it = 0; it < 2; it++) {\n    static const int A3[4]", "  for (int it = 0; it < 0; it++) {\n    static const int A3[4]")],
+        [T_BC1.test_tiny_blocks_global_brute_force]),
+    "BC1 encoder without its neighbourhood search": (
+        [("  for (int round = 0; round < 4; round++) {\n    bc1_sol nb;", "  for (int round = 0; round < 0; round++) {\n    bc1_sol nb;")],
+        [T_BC1.test_tiny_blocks_global_brute_force, T_BC1.test_encoder_against_local_brute_force]),
     "SH tolerance sum of the coefficients without the basis": (
         [("aa += fabs(x * Y[k]);", "aa += fabs(x);")],
         [T_SH.test_tolerance_sum_is_the_sum_of_absolute_terms]),
@@ -242,24 +256,6 @@ MUTANTS = {
         [("ab[ch] += fabs(term);", "ab[ch] += fabs(gv * colour[3 * i + ch]);")],
         [T_REN.test_two_splats_blend_front_to_back]),
 }
-
-# Steps of the encoder's own search heuristic (the encoder specification, not the paper or the BC7
-# format): a change here gives another valid encoder with every format property the pins check
-# (lossless where representable, the first least-error candidate), so no external fact catches it.
-# The GPU encoder, written from the same specification, is compared with the oracle bit for bit,
-# which is what holds these steps. Strict: a pin that starts catching one of them fails this list.
-HEURISTIC_MUTANTS = {
-    "BC7 nearest endpoint code keeps the last of equal distances": (
-        [("    if (be < 0 || d < be) { be = d; best = code; }\n  }\n  return best;",
-          "    if (be < 0 || d <= be) { be = d; best = code; }\n  }\n  return best;")],
-        [T_BC7.test_constant_colours, T_BC7.test_encoder_is_the_first_minimum]),
-    "BC7 fit without its least-squares step": (
-        [("  if (det != 0)\n    for (int i = 0; i < nch; i++) {\n      e0[i] = clampi(",
-          "  if (0)\n    for (int i = 0; i < nch; i++) {\n      e0[i] = clampi(")],
-        [T_BC7.test_constant_colours, T_BC7.test_two_subset_partitions_exact,
-         T_BC7.test_three_subset_partitions_exact, T_BC7.test_encoder_is_the_first_minimum]),
-}
-
 
 def _build(path, patches):
     src = open(os.path.join(ORACLE, "gsc_oracle.c")).read()
@@ -278,7 +274,7 @@ def _build(path, patches):
 def mutant_libs(tmp_path_factory):
     """Every planted copy, compiled in parallel once for the module."""
     from concurrent.futures import ThreadPoolExecutor
-    jobs = {name: patches for name, (patches, _) in list(MUTANTS.items()) + list(HEURISTIC_MUTANTS.items())}
+    jobs = {name: patches for name, (patches, _) in MUTANTS.items()}
     dirs = {name: tmp_path_factory.mktemp("mutant") for name in jobs}
     with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
         futs = {name: ex.submit(_build, dirs[name], jobs[name]) for name in jobs}
@@ -297,20 +293,6 @@ def _mutant_oracle(so):
 @pytest.mark.parametrize("name", list(MUTANTS))
 def test_a_planted_mistake_fails_a_pin(mutant_libs, name):
     _, pins = MUTANTS[name]
-    M = _mutant_oracle(mutant_libs[name])
-    failed = []
-    for pin in pins:
-        try:
-            pin(M)
-        except AssertionError:
-            failed.append(getattr(pin, "__name__", "pin"))
-    assert failed, "no pin caught: " + name
-
-
-@pytest.mark.parametrize("name", list(HEURISTIC_MUTANTS))
-@pytest.mark.xfail(strict=True, reason="a step of the encoder's own heuristic: no pin outside the specification")
-def test_a_heuristic_change_is_not_caught_by_format_pins(mutant_libs, name):
-    _, pins = HEURISTIC_MUTANTS[name]
     M = _mutant_oracle(mutant_libs[name])
     failed = []
     for pin in pins:
