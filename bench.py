@@ -11,6 +11,10 @@ and BC7 codings, compared bit for bit on the device.
 
 `value` is whole-job throughput in millions of Gaussians per second through that step
 (inputs resident in HBM). Multi-GPU runs are weak scaling: every rank codes its own scene.
+The same line carries the batched form (64 scenes in one persistent encode launch and one
+captured evaluation graph, against per-scene calls on the same data: `batched`) and the served
+form (a Poisson request trace of `--serve-seconds` against the request loop with continuous
+batching and against a one-slot queue: `served`); `--scene-only` leaves both out.
 `--impl reference` times the plain CPU oracle on this host's cores on a bounded sample of
 the same workload.
 """
@@ -44,10 +48,16 @@ N_CAMS = 8
 BC7_EVALS_PER_BLOCK = (16 * (16 * 8 + 4 * 16 * 8) + 64 * (16 * 8 + 2 * 16 * 8) + 64 * (16 * 4 + 16 * 4)
                        + 64 * (16 * 4 + 4 * 16 * 4) + (128 + 256 + 3 * 768) + (128 + 3 * 256)
                        + (16 * 16 + 4 * 16 * 16) + 64 * (16 * 4 + 4 * 16 * 4))
-OPS_PER_EVAL = 8
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) measured with ncu on the
-# 3M-Gaussian workload for the kernels as they stand; to be reset to None when a kernel changes.
-MEASURED_TRAFFIC = {"scene3m": {"k_bc7": 886601472, "k_eval2_bc7": 442593536, "k_eval_tex_bc7": 388227328}}
+# integer operations of one palette evaluation as the search kernel computes it (best_key in
+# csrc/bc7.cu): the byte dot product of texel and entry, the entry's key minus 32 x that product,
+# and the running minimum; gsc_probe_op_rate kind 5 runs exactly this mix
+OPS_PER_EVAL = 3
+# per launch, measured with ncu for the kernels as they stand (to be reset to None when a kernel
+# changes): DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) on the 3M-Gaussian workload,
+# and the BC7 search's thread instructions per block (smsp__thread_inst_executed.sum / blocks)
+MEASURED_TRAFFIC = {"scene3m": {"k_bc7": None, "k_eval2_bc7_slots": None, "k_eval_tex_bc7": 388227328}}
+MEASURED_BC7_THREAD_INSTR_PER_BLOCK = 913370   # 262,144-Gaussian scene (the search is exhaustive: size-independent)
+ISSUE_LANES_PER_CLK_SM = 128   # 4 schedulers x 32 lanes, one warp instruction each per clock
 
 
 def workload_cfg(name):
@@ -163,9 +173,6 @@ def run_gsc(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
     cfg = dict(workload_cfg(args.workload))
     cfg["seed"] = cfg["seed"] + 1000 * rank
     n = cfg["n"]
@@ -184,6 +191,8 @@ def run_gsc(args, world, rank, local):
     rate_buf = torch.empty(ng * 256, dtype=torch.uint8, device=dev)
     rate_perm = torch.empty(ns, dtype=torch.int32, device=dev)
     rgb = torch.empty((3, n, N_CAMS, 3), dtype=torch.float32, device=dev)
+    pos_slot = torch.empty((ns, 3), dtype=torch.float32, device=dev)
+    pos_slot_r = torch.empty((ns, 3), dtype=torch.float32, device=dev)
     ok = torch.ones((), dtype=torch.bool, device=dev)
 
     last_perm = [None]
@@ -191,12 +200,15 @@ def run_gsc(args, world, rank, local):
     def step(pos_d, sh_d):
         perm, scales = gsc.gsc_plan_reorder(ctx, pos_d, sh_d, ws=ws, stream=stream)
         last_perm[0] = perm
+        gsc.gsc_positions_to_slots(ctx, pos_d, perm, out=pos_slot, stream=stream)
         rblk, rperm, rtab = gsc.gsc_encode(ctx, sh_d, perm, scales, gsc.FMT_RATE, RATE_TARGET_X4, ws=ws,
                                            out=rate_buf, perm_out=rate_perm, stream=stream, bc1_all=bc1, bc7_all=bc7)
+        gsc.gsc_positions_to_slots(ctx, pos_d, rperm, out=pos_slot_r, stream=stream)
         t1, t7 = gsc.forced_table(rtab, gsc.FMT_BC1), gsc.forced_table(rtab, gsc.FMT_BC7)
-        for i, (tab, blk, p) in enumerate([(t7, bc7, perm), (t1, bc1, perm), (rtab, rblk, rperm)]):
-            gsc.gsc_decode_eval_sh(ctx, tab, blk, p, pos=pos_d, cams=cams, out_order=gsc.OUT_GAUSS_MAJOR,
-                                   out=rgb[i], stream=stream)
+        for i, (tab, blk, p, ps) in enumerate([(t7, bc7, perm, pos_slot), (t1, bc1, perm, pos_slot),
+                                               (rtab, rblk, rperm, pos_slot_r)]):
+            gsc.gsc_decode_eval_sh_slots(ctx, tab, blk, p, pos_slot=ps, cams=cams, out_order=gsc.OUT_GAUSS_MAJOR,
+                                         out=rgb[i], stream=stream)
         with torch.cuda.stream(stream):
             for tab, blk in [(t7, bc7), (t1, bc1)]:
                 sw = gsc.gsc_decode(ctx, tab, blk, perm, stream=stream)
@@ -238,45 +250,58 @@ def run_gsc(args, world, rank, local):
 
     # dominant kernel: the BC7 search (integer ALU bound)
     bc7_ms = kt["bc7_encode"][0] / max(1, kt["bc7_encode"][1])
-    int_peak = gsc.int_peak(ctx, stream=stream)
-    bc7_ops = BC7_EVALS_PER_BLOCK * OPS_PER_EVAL * ns
-    bc7_achieved = bc7_ops / (bc7_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": round(bc7_achieved, 3), "peak": round(int_peak / 1e12, 3),
-                "unit": "Tops/s", "frac": round(bc7_achieved / (int_peak / 1e12), 4),
-                "traffic": MEASURED_TRAFFIC.get(args.workload, {}).get("k_bc7"),
-                "kernel": "k_bc7 (BC7 candidate search)",
-                "peak_source": "measured on this GPU by gsc_probe_int_peak (IADD3/LOP3/IMAD chains)",
-                "algorithmic": "%d palette evaluations x %d int ops per block, %d blocks" % (
-                    BC7_EVALS_PER_BLOCK, OPS_PER_EVAL, ns)}
-    # the fused decode + SH evaluation (HBM bound), all-BC7 coding, timed alone after the step:
-    # algorithmic bytes per launch = 16 B block + 4 B slot entry + 12 B position + 8 x 12 B output
+    roofline = bc7_roofline(ctx, gsc, stream, dev, clk, BC7_EVALS_PER_BLOCK * ns, bc7_ms,
+                            "k_bc7 (BC7 candidate search, thread per block)", ns,
+                            MEASURED_TRAFFIC.get(args.workload, {}).get("k_bc7"))
+    # the fused decode + SH evaluation (HBM bound) of each coding, timed alone after the step, with
+    # the centres resident in slot order (the step's own gsc_positions_to_slots output): algorithmic
+    # bytes per launch = the coded blocks + 4 B slot entry + 12 B centre + 8 x 12 B output per Gaussian
     hbm, hbm_src = peaks()
-    t7 = gsc.forced_table(rtab, gsc.FMT_BC7)
+    t1, t7 = gsc.forced_table(rtab, gsc.FMT_BC1), gsc.forced_table(rtab, gsc.FMT_BC7)
+    codings = {"bc7": (t7, bc7, last_perm[0], pos_slot), "bc1": (t1, bc1, last_perm[0], pos_slot),
+               "rate": (rtab, rblk, rperm, pos_slot_r)}
 
-    def time_eval7(order, out):
+    def time_eval(name, order, out, slots=True):
+        tab, blk, p, ps = codings[name]
+
+        def call():
+            if slots:
+                gsc.gsc_decode_eval_sh_slots(ctx, tab, blk, p, pos_slot=ps, cams=cams, out_order=order, out=out,
+                                             stream=stream)
+            else:
+                gsc.gsc_decode_eval_sh(ctx, tab, blk, p, pos=pos, cams=cams, out_order=order, out=out, stream=stream)
         for _ in range(3):
-            gsc.gsc_decode_eval_sh(ctx, t7, bc7, last_perm[0], pos=pos, cams=cams, out_order=order, out=out,
-                                   stream=stream)
+            call()
         stream.synchronize()
         gsc.set_timing(ctx, True)
-        for _ in range(max(5, args.steps)):
-            gsc.gsc_decode_eval_sh(ctx, t7, bc7, last_perm[0], pos=pos, cams=cams, out_order=order, out=out,
-                                   stream=stream)
+        for _ in range(max(10, args.steps)):
+            call()
         ms_, cnt_ = gsc.kernel_time(ctx, "decode_eval")
         gsc.set_timing(ctx, False)
         return ms_ / max(1, cnt_)
 
+    def eval_bytes(name):
+        return codings[name][0].total_bytes + (4 + 12 + N_CAMS * 12) * n
+
     ev_ms3 = kt["decode_eval"][0] / max(1, kt["decode_eval"][1])
-    ev_ms = time_eval7(gsc.OUT_GAUSS_MAJOR, rgb[0])
-    ev_bytes = (16 + 4 + 12 + N_CAMS * 12) * n
+    per_coding = {}
+    for name in ("bc7", "bc1", "rate"):
+        ms_c = time_eval(name, gsc.OUT_GAUSS_MAJOR, rgb[0])
+        gbs_c = eval_bytes(name) / (ms_c * 1e-3) / 1e9
+        per_coding[name] = {"ms": round(ms_c, 4), "GB_s": round(gbs_c, 1), "frac": round(gbs_c / hbm, 4),
+                            "bytes_per_gaussian": round(eval_bytes(name) / n, 2)}
+    ev_ms = per_coding["bc7"]["ms"]
+    ev_bytes = eval_bytes("bc7")
     ev_gbs = ev_bytes / (ev_ms * 1e-3) / 1e9
     roofline_eval = {"bound": "hbm", "achieved": round(ev_gbs, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(ev_gbs / hbm, 4), "peak_source": hbm_src,
                      "frac_of_nominal": round(ev_gbs / HBM_NOMINAL_GBS, 4),
-                     "traffic": MEASURED_TRAFFIC.get(args.workload, {}).get("k_eval2_bc7"),
-                     "kernel": "k_eval2 (software BC7 decode + SH eval, all-BC7 coding, %d cameras, "
-                               "Gaussian-major output)" % N_CAMS,
-                     "algorithmic": "16 B block + 4 B perm + 12 B position + %d x 12 B output per Gaussian" % N_CAMS}
+                     "traffic": MEASURED_TRAFFIC.get(args.workload, {}).get("k_eval2_bc7_slots"),
+                     "kernel": "k_eval2 (software BC7 decode + SH eval, all-BC7 coding, %d cameras, centres in "
+                               "slot order, Gaussian-major output)" % N_CAMS,
+                     "algorithmic": "16 B block + 4 B slot entry + 12 B centre + %d x 12 B output per Gaussian"
+                                    % N_CAMS,
+                     "codings": per_coding}
     stages = {}
     for k, (ms, cnt) in kt.items():
         stages[k + "_ms"] = round(ms / max(1, cnt), 4)
@@ -286,6 +311,10 @@ def run_gsc(args, world, rank, local):
     stages["decode_eval_bc7_MGauss_s"] = round(n / (ev_ms * 1e-3) / 1e6, 1)
     stages["decode_eval_bc7_GB_s"] = round(ev_gbs, 1)
     stages["decode_eval_3codings_mean_ms"] = round(ev_ms3, 4)
+    # the same call with the centres gathered through the slot order (gsc_decode_eval_sh)
+    ms_g = time_eval("bc7", gsc.OUT_GAUSS_MAJOR, rgb[0], slots=False)
+    stages["decode_eval_bc7_gather_ms"] = round(ms_g, 4)
+    stages["decode_eval_bc7_gather_GB_s"] = round(ev_bytes / (ms_g * 1e-3) / 1e9, 1)
     stages["rate_bits_per_texel"] = round(rtab.used_bits / (16.0 * n), 4)
 
     # the same evaluation on resident texture scenes (blocks decoded by the texture unit)
@@ -293,13 +322,13 @@ def run_gsc(args, world, rank, local):
     stages.update(tex_stats["stages"])
     # coalesced comparison: the all-BC7 coding evaluated into slot order (no scattered stores)
     rgb_slot = torch.empty((N_CAMS, ns, 3), dtype=torch.float32, device=dev)
-    ms_slot = time_eval7(gsc.OUT_SLOT_ORDER, rgb_slot)
+    ms_slot = time_eval("bc7", gsc.OUT_SLOT_ORDER, rgb_slot)
     stages["decode_eval_bc7_slot_order_ms"] = round(ms_slot, 4)
-    stages["decode_eval_bc7_slot_order_GB_s"] = round((16 + 4 + 12 + N_CAMS * 12) * n / (ms_slot * 1e-3) / 1e9, 1)
+    stages["decode_eval_bc7_slot_order_GB_s"] = round(ev_bytes / (ms_slot * 1e-3) / 1e9, 1)
     del rgb_slot
 
     # end to end through the public API with host buffers
-    e2e = run_e2e(args, ctx, gsc, stream, dev, sc, step, world)
+    e2e = run_e2e(args, ctx, gsc, stream, dev, sc, step, world, rgb)
 
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
@@ -311,12 +340,38 @@ def run_gsc(args, world, rank, local):
            "clocks": clk, "e2e": e2e, "gpu_launches": int(launches)}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
-    if rank == 0:
-        print(json.dumps(out), flush=True)
     ctx.close()
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    return out
+
+
+def bc7_roofline(ctx, gsc, stream, dev, clk, evals, ms, kernel, blocks, traffic):
+    """The BC7 search against the measured rate of its own evaluation mix (gsc_probe_op_rate kind 5),
+    and against the SM's issue ceiling (128 lanes per clock per SM at the sampled SM clock), with the
+    per-instruction probe rates beside them."""
+    import torch
+    probes = {gsc.PROBE_KINDS[k]: gsc.op_rate(ctx, k, stream=stream) for k in sorted(gsc.PROBE_KINDS)}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_mhz") or 2070.0
+    per_clk = {k: round(v / (sms * mhz * 1e6), 2) for k, v in probes.items()}
+    issue = sms * ISSUE_LANES_PER_CLK_SM * mhz * 1e6
+    peak = probes["bc7_palette_eval"]
+    ops = evals * OPS_PER_EVAL
+    ach = ops / (ms * 1e-3)
+    out = {"bound": "alu", "achieved": round(ach / 1e12, 3), "peak": round(peak / 1e12, 3), "unit": "Tops/s",
+           "frac": round(ach / peak, 4), "traffic": traffic, "kernel": kernel,
+           "peak_source": "measured on this GPU: gsc_probe_op_rate kind 5, the evaluation's own mix (dp4a, "
+                          "scaled key, minimum) in independent chains at full occupancy",
+           "algorithmic": "%d palette evaluations x %d int ops (dot, key, minimum), %d blocks"
+                          % (evals // max(1, blocks), OPS_PER_EVAL, blocks),
+           "issue_ceiling_Tops_s": round(issue / 1e12, 3), "frac_of_issue_ceiling": round(ach / issue, 4),
+           "probes_Tops_s": {k: round(v / 1e12, 3) for k, v in probes.items()},
+           "probes_ops_per_clk_per_sm": per_clk}
+    if MEASURED_BC7_THREAD_INSTR_PER_BLOCK:
+        ti = MEASURED_BC7_THREAD_INSTR_PER_BLOCK * blocks / (ms * 1e-3)
+        out["instructions"] = {"thread_instr_per_block": MEASURED_BC7_THREAD_INSTR_PER_BLOCK,
+                               "thread_instr_per_eval": round(MEASURED_BC7_THREAD_INSTR_PER_BLOCK * blocks / evals, 2),
+                               "Tinstr_s": round(ti / 1e12, 3), "frac_of_issue_ceiling": round(ti / issue, 4)}
+    return out
 
 
 def time_tex_eval(args, ctx, gsc, stream, dev, rtab, bc1, bc7, perm, pos, cams, n, ns):
@@ -357,7 +412,7 @@ def time_tex_eval(args, ctx, gsc, stream, dev, rtab, bc1, bc7, perm, pos, cams, 
     return res
 
 
-def run_e2e(args, ctx, gsc, stream, dev, sc, step, world):
+def run_e2e(args, ctx, gsc, stream, dev, sc, step, world, rgb):
     import torch
     pos_h = torch.from_numpy(sc.pos).pin_memory()
     sh_h = torch.from_numpy(sc.sh).pin_memory()
@@ -367,6 +422,7 @@ def run_e2e(args, ctx, gsc, stream, dev, sc, step, world):
     ns = (n + 15) // 16 * 16
     out_blocks = torch.empty(ns * 16, dtype=torch.uint8).pin_memory()
     out_perm = torch.empty(ns, dtype=torch.int32).pin_memory()
+    out_rgb = torch.empty(rgb.shape, dtype=rgb.dtype).pin_memory()
     bo = 0
 
     def one():
@@ -378,7 +434,8 @@ def run_e2e(args, ctx, gsc, stream, dev, sc, step, world):
         with torch.cuda.stream(stream):
             out_blocks[:rtab.total_bytes].copy_(rblk, non_blocking=True)
             out_perm.copy_(rperm, non_blocking=True)
-        bo = rtab.total_bytes + 4 * ns
+            out_rgb.copy_(rgb, non_blocking=True)
+        bo = rtab.total_bytes + 4 * ns + rgb.numel() * rgb.element_size()
         return rtab
 
     for _ in range(max(1, args.warmup // 2)):
@@ -393,7 +450,8 @@ def run_e2e(args, ctx, gsc, stream, dev, sc, step, world):
     t = max_over_ranks(t, world, dev)
     return {"value": round(world * n / t / 1e6, 3), "unit": UNIT, "h2d_bytes_per_step": int(n * (12 + 192)),
             "d2h_bytes_per_step": int(bo), "ms_per_step": round(t * 1e3, 3),
-            "path": "pinned host pos+SH -> plan/encode/decode/eval/texture compare -> rate streams + perm to host"}
+            "path": "pinned host pos+SH -> plan/encode/decode/eval/texture compare -> rate streams, perm and the "
+                    "three codings' evaluated colours to pinned host memory"}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -405,9 +463,6 @@ def run_layouts(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
     cfg = dict(S.SCENE)
     cfg["seed"] = cfg["seed"] + 1000 * rank
     n = cfg["n"]
@@ -484,14 +539,8 @@ def run_layouts(args, world, rank, local):
     hbm, hbm_src = peaks()
     bc7_blocks_step = sum(ng * j for _, _, _, j, _ in LAYOUT_CODINGS)
     bc7_ms = kt["bc7_encode"][0] / max(1, args.steps)
-    int_peak = gsc.int_peak(ctx, stream=stream)
-    bc7_achieved = BC7_EVALS_PER_BLOCK * OPS_PER_EVAL * bc7_blocks_step / (bc7_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": round(bc7_achieved, 3), "peak": round(int_peak / 1e12, 3),
-                "unit": "Tops/s", "frac": round(bc7_achieved / (int_peak / 1e12), 4), "traffic": None,
-                "kernel": "k_bc7 on staged texels (every BC7 block of the step's codings)",
-                "peak_source": "measured on this GPU by gsc_probe_int_peak (IADD3/LOP3/IMAD chains)",
-                "algorithmic": "%d palette evaluations x %d int ops per block, %d BC7 blocks per step" % (
-                    BC7_EVALS_PER_BLOCK, OPS_PER_EVAL, bc7_blocks_step)}
+    roofline = bc7_roofline(ctx, gsc, stream, dev, clk, BC7_EVALS_PER_BLOCK * bc7_blocks_step, bc7_ms,
+                            "k_bc7 on staged texels (every BC7 block of the step's codings)", bc7_blocks_step, None)
     stages, rooflines = {}, {}
     for name, lay, fmt, j, bpg in LAYOUT_CODINGS:
         enc_ms, ev_ms = acc[name][0] / args.steps, acc[name][1] / args.steps
@@ -555,12 +604,8 @@ def run_layouts(args, world, rank, local):
            "gpu_launches": int(launches)}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline("layouts3m", budget_s=args.cpu_seconds)
-    if rank == 0:
-        print(json.dumps(out), flush=True)
     ctx.close()
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    return out
 
 
 def run_render(args, world, rank, local):
@@ -571,9 +616,6 @@ def run_render(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
     cfg = dict(S.RENDER)
     n, W, H, V = cfg["n"], cfg["width"], cfg["height"], cfg["views"]
     sc = S.make_scene(n=n, seed=cfg["seed"] + 1000 * rank, clusters=cfg["clusters"], heavy_frac=cfg["heavy_frac"])
@@ -723,12 +765,8 @@ def run_render(args, world, rank, local):
            "roofline": roofline, "stages": stages, "clocks": clk, "e2e": e2e, "gpu_launches": int(launches)}
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_render(budget_s=args.cpu_seconds)
-    if rank == 0:
-        print(json.dumps(out), flush=True)
     ctx.close()
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    return out
 
 
 def cpu_baseline_render(budget_s=20.0):
@@ -759,7 +797,7 @@ def C_ref(x):
 
 
 # ------------------------------------------------------------------------------------------------
-def run_batch(args, world, rank, local):
+def run_batch(args, world, rank, local, cpu=True):
     """64 scenes of uneven sizes: one persistent encode launch + one captured evaluation graph,
     against per-scene plain calls (plan, encode, decode + SH eval per scene) on the same data."""
     import torch
@@ -767,9 +805,6 @@ def run_batch(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
     mix = S.batch_mix(**dict(S.BATCH, seed=S.BATCH["seed"] + 1000 * rank))
     fmt_of = {"bc1": gsc.FMT_BC1, "bc7": gsc.FMT_BC7, "rate": gsc.FMT_RATE}
     ctx = gsc.Context(local)
@@ -851,18 +886,13 @@ def run_batch(args, world, rank, local):
 
     ms_eval_plain = timed(eval_per_scene, max(5, args.steps))
 
-    # the persistent encode launch: BC7 candidate search of every BC7-searched block
+    # the persistent encode launch: BC7 candidate search of every BC7-searched block (BC1 work not counted)
     nb7 = sum(((m[0] + 15) // 16) * 16 for m in mix if m[2] != "bc1")
     kb_ms /= max(1, kb_cnt)
-    int_peak = gsc.int_peak(ctx, stream=stream)
-    ach = BC7_EVALS_PER_BLOCK * OPS_PER_EVAL * nb7 / (kb_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": round(ach, 3), "peak": round(int_peak / 1e12, 3), "unit": "Tops/s",
-                "frac": round(ach / (int_peak / 1e12), 4), "traffic": None,
-                "kernel": "k_batch (persistent BC1/BC7 search over all scenes, schedule %d, %d CTAs/SM, "
-                          "BC1 tiles of %d groups)" % (tuning.schedule, tuning.ctas_per_sm, tuning.bc1_tile_groups),
-                "peak_source": "measured on this GPU by gsc_probe_int_peak",
-                "algorithmic": "%d palette evaluations x %d int ops per BC7-searched block, %d blocks (BC1 work "
-                               "not counted)" % (BC7_EVALS_PER_BLOCK, OPS_PER_EVAL, nb7)}
+    roofline = bc7_roofline(ctx, gsc, stream, dev, clk, BC7_EVALS_PER_BLOCK * nb7, kb_ms,
+                            "k_batch (persistent BC1/BC7 search over all scenes, schedule %d, %d CTAs/SM, BC1 "
+                            "tiles of %d groups)" % (tuning.schedule, tuning.ctas_per_sm, tuning.bc1_tile_groups),
+                            nb7, None)
     hbm, hbm_src = peaks()
     ev_bytes = 0
     for i, (n, _, f, _) in enumerate(mix):
@@ -912,6 +942,7 @@ def run_batch(args, world, rank, local):
                       "l2": "inputs larger than L2", "bit_exact_vs_per_scene": same},
            "batched_vs_per_scene": {"batched_ms": round(ms_step, 3), "per_scene_ms": round(ms_plain, 3),
                                     "speedup": round(ms_plain / ms_step, 3),
+                                    "per_scene_value": round(world * total_n / (ms_plain * 1e-3) / 1e6, 3),
                                     "tuning": {"schedule": tuning.schedule, "ctas_per_sm": tuning.ctas_per_sm,
                                                "bc1_tile_groups": tuning.bc1_tile_groups,
                                                "proxy_ms": round(proxy_ms, 3)}},
@@ -923,15 +954,11 @@ def run_batch(args, world, rank, local):
                    "h2d_bytes_per_step": int(total_n * (12 + 192)), "d2h_bytes_per_step": int(bo),
                    "ms_per_step": round(t_e2e * 1e3, 3)},
            "gpu_launches": int(launches)}
-    if world == 1 and not args.no_cpu_baseline:
+    if cpu and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_mix(mix, budget_s=args.cpu_seconds)
-    if rank == 0:
-        print(json.dumps(out), flush=True)
     graph.close()
     ctx.close()
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    return out
 
 
 def run_serve(args, world, rank, local):
@@ -944,9 +971,6 @@ def run_serve(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
     cfg = dict(S.SERVE, seed=S.SERVE["seed"] + 1000 * rank)
     pool, reqs = S.serve_trace(**cfg, seconds=args.serve_seconds)
     fmt_of = {"bc1": gsc.FMT_BC1, "bc7": gsc.FMT_BC7}
@@ -1047,12 +1071,8 @@ def run_serve(args, world, rank, local):
            "clocks": clk, "gpu_launches": int(launches),
            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": 0,
                    "note": "requests carry pinned host scenes (encode) and device outputs (eval)"}}
-    if rank == 0:
-        print(json.dumps(out), flush=True)
     ctx.close()
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    return out
 
 
 def cpu_baseline_mix(mix, budget_s=20.0):
@@ -1184,7 +1204,8 @@ def main():
     ap.add_argument("--impl", default="gsc", choices=["gsc", "reference"])
     ap.add_argument("--workload", default="scene3m",
                     choices=["scene3m", "medium262k", "tiny4k", "layouts3m", "render3m", "batch64", "serve"])
-    ap.add_argument("--serve-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--scene-only", action="store_true", help="scene3m without the batched and served forms")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -1192,19 +1213,40 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
-    if args.workload == "batch64":
-        run_batch(args, world, rank, local)
-        return
-    if args.workload == "serve":
-        run_serve(args, world, rank, local)
-        return
-    if args.workload == "layouts3m":
-        run_layouts(args, world, rank, local)
-        return
-    if args.workload == "render3m":
-        run_render(args, world, rank, local)
-        return
-    run_gsc(args, world, rank, local)
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    run = {"batch64": run_batch, "serve": run_serve, "layouts3m": run_layouts, "render3m": run_render}
+    out = run.get(args.workload, run_gsc)(args, world, rank, local)
+    if args.workload == "scene3m" and not args.scene_only:
+        # the batched and served forms, beside the scene step on the same GPU(s)
+        torch.cuda.empty_cache()
+        b = run_batch(args, world, rank, local, cpu=False)
+        out["batched"] = {"value": b["value"], "unit": UNIT, "per_scene_value": b["batched_vs_per_scene"]["per_scene_value"],
+                          "ratio": b["batched_vs_per_scene"]["speedup"],
+                          "bit_identical": b["config"]["bit_exact_vs_per_scene"],
+                          "batched_ms": b["batched_vs_per_scene"]["batched_ms"],
+                          "per_scene_ms": b["batched_vs_per_scene"]["per_scene_ms"],
+                          "workload": b["config"]["workload"], "clocks": b["clocks"],
+                          "gpu_launches": b["gpu_launches"], "e2e": b["e2e"]}
+        torch.cuda.empty_cache()
+        v = run_serve(args, world, rank, local)
+        srv = v["serving"]
+        out["served"] = {kind: {"p50_ms": srv[kind]["latency"]["all"]["p50_ms"],
+                                "p99_ms": srv[kind]["latency"]["all"]["p99_ms"],
+                                "req_s": srv[kind]["served_req_s"], "MGauss_s": srv[kind]["MGauss_s"],
+                                "span_s": srv[kind]["span_s"], "failed": srv[kind]["failed"],
+                                "latency": srv[kind]["latency"]}
+                         for kind in ("continuous_batching", "plain_queue")}
+        out["served"]["trace"] = v["config"]["workload"]
+        out["served"]["clocks"] = v["clocks"]
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

@@ -545,6 +545,12 @@ gsc_status gsc_decode_blocks_tex(gsc_ctx* ctx, const uint8_t* d_blocks, int64_t 
  * and stores the achieved 32-bit integer operations per second; synchronises `stream`. */
 uint64_t gsc_launch_count(void);
 gsc_status gsc_probe_int_peak(gsc_ctx* ctx, double* ops_per_s, void* stream);
+/* gsc_probe_op_rate: throughput of one 32-bit integer instruction kind, independent chains at
+ * full occupancy: kind 1 three-input add, 2 three-input logic op (lop3), 3 multiply-add,
+ * 4 four-way byte dot product (dp4a), 5 the BC7 search's palette evaluation (dp4a of a texel
+ * with a palette entry, key - 32 * dot, running minimum: 3 operations per evaluation). Stores
+ * operations per second; GSC_ERR_INVALID_ARG for another kind; synchronises `stream`. */
+gsc_status gsc_probe_op_rate(gsc_ctx* ctx, int32_t kind, double* ops_per_s, void* stream);
 /* Kernel timing: when enabled, each call records CUDA events on its own stream around its
  * main kernels. gsc_kernel_time waits for the recorded events and returns the summed
  * milliseconds and launch count of one kernel ("plan", "bc1_encode", "bc7_encode",

@@ -122,6 +122,82 @@ extern "C" gsc_status gsc_probe_int_peak(gsc_ctx* c, double* ops_per_s, void* st
   return GSC_OK;
 }
 
+// Per-instruction throughput probes: 8 independent pairs of chains per thread; each step of a
+// pair is two instructions of one kind whose operands change every iteration, so no two of them
+// fold into one. Kind 5 is the BC7 search's palette evaluation: a dot product of a texel with a
+// palette entry, the scaled key (key - 32 * dot) and a running minimum, over 8 entries per texel.
+template <int KIND>
+__global__ void k_op_probe(uint32_t* out, int iters, uint32_t seed) {
+  uint32_t x[8], y[8];
+#pragma unroll
+  for (int j = 0; j < 8; j++) { x[j] = seed * (threadIdx.x + 1) + 97u * j; y[j] = (seed ^ (blockIdx.x * 77u)) + 31u * j; }
+  for (int i = 0; i < iters; i++) {
+    const uint32_t k = (uint32_t)i * 0x01030507u + seed;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      if (KIND == 1) {
+        x[j] = x[j] + y[j] + k;
+        y[j] = y[j] + x[j] + k;
+      } else if (KIND == 2) {
+        asm("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(x[j]) : "r"(y[j]), "r"(k));
+        asm("lop3.b32 %0, %0, %1, %2, 0xE8;" : "+r"(y[j]) : "r"(x[j]), "r"(k));
+      } else if (KIND == 3) {
+        x[j] = x[j] * y[j] + k;
+        y[j] = y[j] * x[j] + k;
+      } else if (KIND == 4) {
+        x[j] = (uint32_t)__dp4a(x[j], y[j], k);
+        y[j] = (uint32_t)__dp4a(y[j], x[j], k);
+      } else {
+        // x[j]: palette entry (fixed), y[j]: running minimum; 8 entries share one texel value k
+        const int key = (int)(x[j] & 0xFFFFu) - 32 * (int)__dp4a(k, x[j], 0u);
+        y[j] = (uint32_t)min((int)y[j], key);
+      }
+    }
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; j++) s ^= x[j] + y[j];
+  if (s == 0x12345678u) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+extern "C" gsc_status gsc_probe_op_rate(gsc_ctx* c, int32_t kind, double* ops_per_s, void* stream) {
+  if (!c || !ops_per_s || kind < 1 || kind > 5) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int threads = 256, blocks = c->sm_count * 8, iters = 4096;
+  uint32_t* d = nullptr;
+  GSC_CUDA(cudaMalloc(&d, sizeof(uint32_t) * threads * blocks));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; rep++) {
+    const uint32_t seed = 0x1234567u + rep;
+    cudaEventRecord(e0, st);
+    gsc_count_launch();
+    switch (kind) {
+      case 1: k_op_probe<1><<<blocks, threads, 0, st>>>(d, iters, seed); break;
+      case 2: k_op_probe<2><<<blocks, threads, 0, st>>>(d, iters, seed); break;
+      case 3: k_op_probe<3><<<blocks, threads, 0, st>>>(d, iters, seed); break;
+      case 4: k_op_probe<4><<<blocks, threads, 0, st>>>(d, iters, seed); break;
+      default: k_op_probe<5><<<blocks, threads, 0, st>>>(d, iters, seed); break;
+    }
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  cudaError_t e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d);
+  if (e != cudaSuccess) return GSC_ERR_CUDA;
+  // kinds 1-4: two instructions per chain pair and step; kind 5: three (dot, scaled key, minimum)
+  *ops_per_s = (double)threads * blocks * iters * 8.0 * (kind == 5 ? 3.0 : 2.0) / (best * 1e-3);
+  return GSC_OK;
+}
+
 int gsc_sm_count() {
   static std::atomic<int> cache[64];
   int dev = 0;

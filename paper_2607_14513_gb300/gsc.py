@@ -181,6 +181,7 @@ _SIGS = {
     "gsc_build_checked": [],
     "gsc_launch_count": [],
     "gsc_probe_int_peak": [_P, C.POINTER(C.c_double), _P],
+    "gsc_probe_op_rate": [_P, C.c_int32, C.POINTER(C.c_double), _P],
     "gsc_ctx_set_timing": [_P, C.c_int],
     "gsc_kernel_time": [_P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)],
 }
@@ -323,6 +324,16 @@ def forced_table(table, fmt):
 def int_peak(ctx, stream=None):
     v = C.c_double(0.0)
     _check(ctx.lib.gsc_probe_int_peak(ctx.h, C.byref(v), _stream(stream)), "gsc_probe_int_peak")
+    return v.value
+
+
+PROBE_KINDS = {1: "iadd3", 2: "lop3", 3: "imad", 4: "dp4a", 5: "bc7_palette_eval"}
+
+
+def op_rate(ctx, kind, stream=None):
+    """Operations per second of one instruction kind (gsc_probe_op_rate; kinds in PROBE_KINDS)."""
+    v = C.c_double(0.0)
+    _check(ctx.lib.gsc_probe_op_rate(ctx.h, kind, C.byref(v), _stream(stream)), "gsc_probe_op_rate")
     return v.value
 
 
