@@ -538,6 +538,100 @@ gsc_status gsc_decode_blocks(gsc_ctx* ctx, const uint8_t* d_blocks, int64_t nblk
 gsc_status gsc_decode_blocks_tex(gsc_ctx* ctx, const uint8_t* d_blocks, int64_t nblk, int32_t format,
                                  uint8_t* d_rgba, void* stream);
 
+/* ---- One scene split over shards (ranks or streams) ------------------------------------
+ * Sec. V-A fixes the 16 scales as order statistics of the whole scene, Sec. III-C reorders
+ * chunk by chunk within the spatial order, and Sec. IV-B spends one rate budget on the whole
+ * scene. These calls split that work: every shard computes an integer partial, the caller
+ * combines the partials of all shards (elementwise minimum / maximum / sum, or a gather) by any
+ * means (torch.distributed, NCCL, or in one process), and passes the combined values to the next
+ * call. With them every shard takes the decisions of the whole-scene calls, so the scales, the
+ * slot order, lambda, the streams and the permutation equal those of gsc_plan_reorder (sort = 1,
+ * group_size > 0) followed by gsc_encode (GSC_FMT_RATE), byte for byte. All partials are int64
+ * in device memory (`d_part` arguments: written; `d_total`/`d_in`/`d_hist`/`d_bb` as inputs: the
+ * combined values). Every call is queued on `stream` and does not synchronise it, except
+ * gsc_shard_rate_assemble. Errors: GSC_ERR_INVALID_ARG for a null or misaligned pointer, a size
+ * out of range or a pass out of range; GSC_ERR_OOM for a short workspace; GSC_ERR_BUDGET from
+ * the assembly when the budget cannot be met.
+ *
+ * Order of calls (S shards; "combine" is over all S; shard s holds inputs [in_s, in_s + m_s),
+ * contiguous and in shard order):
+ *  1. gsc_shard_bbox -> combine: min of [0,3), max of [3,6)            (6 values)
+ *  2. gsc_shard_morton with the combined box -> gather all keys in input order
+ *  3. gsc_shard_order on all keys: the spatial order of the scene (input indices); with
+ *     gsc_shard_bounds, shard s owns order[b_s, b_s+1), chunk-aligned; the caller moves those
+ *     Gaussians (centres, SH) to shard s, in that order.
+ *  4. gsc_shard_select_begin (the whole scene's n); for pass 0..3: gsc_shard_select_hist ->
+ *     combine: sum (16 x 256) -> gsc_shard_select_pick; then gsc_shard_select_scales.
+ *  5. gsc_shard_plan on the shard's owned Gaussians -> the shard's slot order (local indices).
+ *  6. gsc_shard_rate_begin -> combine: sum (1) -> gsc_shard_rate_search_begin; for pass 0..12:
+ *     gsc_shard_rate_count -> combine: sum (64) -> gsc_shard_rate_narrow.
+ *  7. gsc_shard_rate_fill -> d_part = {sum at lambda*, sum of this shard's fill deltas}; pass to
+ *     gsc_shard_rate_apply d_in = {sum over all shards of the first, sum of the second over the
+ *     shards before this one} -> d_part (15: groups per mode, bits used) -> gather all shards'.
+ *  8. gsc_shard_rate_assemble with the gathered parts [S][15]: writes this shard's groups into
+ *     the scene's stream buffer and slot order at the places the whole-scene call writes them
+ *     (d_index_map maps the shard's local indices to the scene's input indices), and fills the
+ *     whole scene's stream table. */
+#define GSC_SHARD_SELECT_PASSES 4
+#define GSC_SHARD_RATE_PASSES 13
+#define GSC_SHARD_RATE_PART 15
+/* Shard s of S gets chunks [floor(C s / S), floor(C (s + 1) / S)) of the C = ceil(n_total /
+ * group_size) chunks: bounds[s] = min(n_total, that chunk index x group_size), s = 0..S (host). */
+gsc_status gsc_shard_bounds(int64_t n_total, int32_t n_shards, int64_t group_size, int64_t* bounds);
+/* d_bb [6] out: order-preserving 32-bit codes of the per-axis minimum (3) and maximum (3) centre
+ * coordinate of the shard's n centres d_pos [n][3] (empty shard: 0xFFFFFFFF and 0). */
+gsc_status gsc_shard_bbox(gsc_ctx* ctx, const float* d_pos, int64_t n, int64_t* d_bb, void* stream);
+/* d_keys [n] out: the 30-bit Morton code of each centre on the 1024^3 grid of the combined box. */
+gsc_status gsc_shard_morton(gsc_ctx* ctx, const float* d_pos, int64_t n, const int64_t* d_bb, uint64_t* d_keys,
+                            void* stream);
+/* d_keys [n_total] (all shards' keys in input order; overwritten) -> d_order [n_total]: input
+ * indices stably sorted by key (the whole-scene spatial rank). Workspace: gsc_shard_order_ws_bytes,
+ * 256-byte aligned. */
+size_t gsc_shard_order_ws_bytes(int64_t n_total);
+gsc_status gsc_shard_order(gsc_ctx* ctx, uint64_t* d_keys, int64_t n_total, int32_t* d_order, void* d_ws,
+                           size_t ws_bytes, void* stream);
+/* Selection state (device, gsc_shard_select_state_bytes, 256-byte aligned, owned by the caller):
+ * begin sets the target rank ceil(permille x 3 n_total / 1000) - 1 per scale; pass p examines bits
+ * [24 - 8p, 32 - 8p) of |x|: hist writes the shard's d_hist [16][256], pick takes the combined
+ * one; scales writes d_scales [16] (s_k = 2 a_k, 1 where a_k = 0). */
+size_t gsc_shard_select_state_bytes(void);
+gsc_status gsc_shard_select_begin(gsc_ctx* ctx, int64_t n_total, uint32_t permille, void* d_state, void* stream);
+gsc_status gsc_shard_select_hist(gsc_ctx* ctx, const float* d_sh, int64_t n, int32_t pass, void* d_state,
+                                 int64_t* d_hist, void* stream);
+gsc_status gsc_shard_select_pick(gsc_ctx* ctx, void* d_state, const int64_t* d_hist, int32_t pass, void* stream);
+gsc_status gsc_shard_select_scales(gsc_ctx* ctx, const void* d_state, float* d_scales, void* stream);
+/* The slot order of a shard: d_sh [n][48] holds the shard's Gaussians in spatial-rank order, the
+ * first one starting a chunk of group_size (> 0, multiple of 16); d_perm [ceil(n/16)*16] out,
+ * local indices, -1 padding. Workspace gsc_shard_plan_ws_bytes(n), 256-byte aligned. */
+size_t gsc_shard_plan_ws_bytes(int64_t n);
+gsc_status gsc_shard_plan(gsc_ctx* ctx, const float* d_sh, int64_t n, const float* d_scales, int64_t group_size,
+                          int32_t* d_perm, void* d_ws, size_t ws_bytes, void* stream);
+/* Rate control of a shard of n Gaussians (its own workspace, gsc_shard_rate_ws_bytes(n), kept
+ * across the calls 6-8). begin codes the shard's groups (d_perm: its slot order) in BC1 into
+ * d_bc1 [ceil(n/16)][16][8] and in BC7 into d_bc7 [ceil(n/16)][16][16] (16-byte aligned; kept by
+ * the caller until assemble) and writes d_part [1]: the rate at lambda = 2^62. search_begin takes
+ * the combined value, the scene's n_total and target (1..64, in quarter bits per texel). */
+size_t gsc_shard_rate_ws_bytes(int64_t n);
+gsc_status gsc_shard_rate_begin(gsc_ctx* ctx, const float* d_sh, int64_t n, const int32_t* d_perm,
+                                const float* d_scales, uint8_t* d_bc1, uint8_t* d_bc7, void* d_ws, size_t ws_bytes,
+                                int64_t* d_part, void* stream);
+gsc_status gsc_shard_rate_search_begin(gsc_ctx* ctx, int64_t n, void* d_ws, int64_t n_total, uint32_t target_x4,
+                                       const int64_t* d_min_total, void* stream);
+gsc_status gsc_shard_rate_count(gsc_ctx* ctx, int64_t n, void* d_ws, int32_t pass, int64_t* d_part, void* stream);
+gsc_status gsc_shard_rate_narrow(gsc_ctx* ctx, int64_t n, void* d_ws, int32_t pass, const int64_t* d_total,
+                                 void* stream);
+gsc_status gsc_shard_rate_fill(gsc_ctx* ctx, int64_t n, void* d_ws, int64_t* d_part, void* stream);
+gsc_status gsc_shard_rate_apply(gsc_ctx* ctx, int64_t n, void* d_ws, const int64_t* d_in, int64_t* d_part,
+                                void* stream);
+/* d_blocks: the scene's stream buffer (16-byte aligned, at least the table's total_bytes);
+ * d_perm_out: the scene's slot order [ceil(n_total/16)*16]; d_index_map [n] (optional): the
+ * scene's input index of each of the shard's Gaussians; h_table: the whole scene's table, the
+ * same on every shard. Synchronises `stream`. */
+gsc_status gsc_shard_rate_assemble(gsc_ctx* ctx, int64_t n, void* d_ws, const uint8_t* d_bc1, const uint8_t* d_bc7,
+                                   const int32_t* d_perm, const int32_t* d_index_map, const float* d_scales,
+                                   const int64_t* d_parts_all, int32_t n_shards, int32_t shard, int64_t n_total,
+                                   uint8_t* d_blocks, int32_t* d_perm_out, gsc_stream_table* h_table, void* stream);
+
 /* Measurement helpers (not part of the codec).
  * gsc_launch_count: kernels this library has launched in this process so far.
  * gsc_probe_int_peak: runs an integer microbenchmark (independent IADD3 / LOP3 / IMAD

@@ -14,7 +14,7 @@ LIB = os.path.join(PKG, "lib", "libgsc.so")
 BUILD_CHECKED = os.path.join(PKG, "_build_checked")
 LIB_CHECKED = os.path.join(PKG, "lib", "libgsc_checked.so")
 SOURCES = ["api.cu", "plan.cu", "bc1.cu", "bc7.cu", "rate.cu", "decode.cu", "layout.cu", "render.cu",
-           "geometry.cu", "batch.cu", "serve.cu", "scene_file.cu"]
+           "geometry.cu", "batch.cu", "serve.cu", "scene_file.cu", "shard.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code: no contraction of multiply-adds, so host float/double results are the same on x86 and Arm

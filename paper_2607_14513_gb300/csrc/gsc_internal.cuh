@@ -195,3 +195,31 @@ gsc_status decode_tex_run(gsc_ctx* ctx, const DevTable& t, const uint8_t* blocks
 void tex_cache_free(gsc_ctx* ctx);
 gsc_status decode_blocks_tex_run(gsc_ctx* ctx, const uint8_t* blocks, int64_t nblk, int format, uint8_t* rgba,
                                  cudaStream_t st);
+
+// Sharded single-scene encode (plan.cu, rate.cu)
+cudaError_t shard_bbox(const float* pos, int64_t n, int64_t* bb, int sm_count, cudaStream_t st);
+cudaError_t shard_morton(const float* pos, int64_t n, const int64_t* bb, uint64_t* keys, int sm_count, cudaStream_t st);
+size_t shard_order_ws_bytes(int64_t n);
+cudaError_t shard_order(uint64_t* keys, int64_t n, int32_t* order, void* ws, int sm_count, cudaStream_t st);
+size_t shard_select_state_bytes();
+cudaError_t shard_select_begin(int64_t n_total, int permille, void* state, cudaStream_t st);
+cudaError_t shard_select_hist(const float* sh, int64_t n, int shift, void* state, int64_t* hist, int sm_count,
+                              cudaStream_t st);
+cudaError_t shard_select_pick(void* state, const int64_t* hist_total, int shift, cudaStream_t st);
+cudaError_t shard_select_scales(const void* state, float* scales, cudaStream_t st);
+size_t shard_plan_ws_bytes(int64_t n);
+gsc_status shard_plan(const float* sh, int64_t n, const float* scales, int64_t group_size, int32_t* perm, void* ws,
+                      size_t ws_bytes, int sm_count, cudaStream_t st);
+size_t shard_rate_ws_bytes(int64_t ng);
+gsc_status shard_rate_begin(gsc_ctx* ctx, const float* sh, int64_t n, const int32_t* perm, const float* scales,
+                            uint8_t* b1, uint8_t* b7, void* ws, size_t ws_bytes, int64_t* part, cudaStream_t st);
+gsc_status shard_rate_search_begin(int64_t ng, void* ws, int64_t n_total, uint32_t target_x4, const int64_t* min_total,
+                                   cudaStream_t st);
+gsc_status shard_rate_count(gsc_ctx* ctx, int64_t ng, void* ws, int pass, int64_t* part, cudaStream_t st);
+gsc_status shard_rate_narrow(int64_t ng, void* ws, int pass, const int64_t* total, cudaStream_t st);
+gsc_status shard_rate_fill(gsc_ctx* ctx, int64_t ng, void* ws, int64_t* part, cudaStream_t st);
+gsc_status shard_rate_apply(gsc_ctx* ctx, int64_t ng, void* ws, const int64_t* in, int64_t* part, cudaStream_t st);
+gsc_status shard_rate_assemble(gsc_ctx* ctx, int64_t ng, void* ws, const uint8_t* b1, const uint8_t* b7,
+                               const int32_t* perm, const int32_t* index_map, const int64_t* counts_all, int n_shards,
+                               int shard, int64_t n_total, uint8_t* blocks, int32_t* perm_out, gsc_stream_table* table,
+                               cudaStream_t st);

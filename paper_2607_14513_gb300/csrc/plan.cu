@@ -203,11 +203,11 @@ __global__ void k_sel_init(SelState* s, uint64_t r) {
 }
 
 __global__ void __launch_bounds__(256) k_sel_hist(const float4* __restrict__ sh4, int64_t n4, int shift,
-                                                  const SelState* __restrict__ st, uint32_t* __restrict__ hist) {
+                                                  const uint32_t* __restrict__ prefix, uint32_t* __restrict__ hist) {
   __shared__ uint32_t h[GSC_SH * 256];
   __shared__ uint32_t pre[GSC_SH];
   for (int i = threadIdx.x; i < GSC_SH * 256; i += blockDim.x) h[i] = 0;
-  if (threadIdx.x < GSC_SH) pre[threadIdx.x] = st->prefix[threadIdx.x];
+  if (threadIdx.x < GSC_SH) pre[threadIdx.x] = prefix[threadIdx.x];
   __syncthreads();
   const int hs = shift + 8;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
@@ -226,20 +226,24 @@ __global__ void __launch_bounds__(256) k_sel_hist(const float4* __restrict__ sh4
     if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
-__global__ void k_sel_pick(SelState* st, uint32_t* hist, int shift) {
+// The digit of this pass: the first whose cumulative count passes the remaining rank. ZERO clears
+// the histogram for the next pass (the whole-scene plan reuses one buffer).
+template <class T, bool ZERO>
+__global__ void k_sel_pick(SelState* st, T* hist, int shift) {
   const int k = threadIdx.x;
   if (k >= GSC_SH) return;
   uint64_t r = st->rank[k], cum = 0;
   int d = 0;
   for (d = 0; d < 256; d++) {
-    uint64_t c = hist[k * 256 + d];
+    uint64_t c = (uint64_t)hist[k * 256 + d];
     if (r < cum + c) break;
     cum += c;
   }
   if (d > 255) d = 255;
   st->prefix[k] |= (uint32_t)d << shift;
   st->rank[k] = r - cum;
-  for (int i = 0; i < 256; i++) hist[k * 256 + i] = 0;
+  if constexpr (ZERO)
+    for (int i = 0; i < 256; i++) hist[k * 256 + i] = 0;
 }
 
 __global__ void k_sel_finish(const SelState* st, float* scales) {
@@ -411,8 +415,8 @@ gsc_status plan_run(gsc_ctx* ctx, const float* pos, const float* sh, const gsc_p
     const int64_t n4 = n * 12;
     const int g = grid_stride(n4, 256, ctx->sm_count * 4);
     for (int shift = 24; shift >= 0; shift -= 8) {
-      gsc_count_launch(); k_sel_hist<<<g, 256, 0, st>>>(reinterpret_cast<const float4*>(sh), n4, shift, sel, hist);
-      gsc_count_launch(); k_sel_pick<<<1, 32, 0, st>>>(sel, hist, shift);
+      gsc_count_launch(); k_sel_hist<<<g, 256, 0, st>>>(reinterpret_cast<const float4*>(sh), n4, shift, sel->prefix, hist);
+      gsc_count_launch(); k_sel_pick<uint32_t, true><<<1, 32, 0, st>>>(sel, hist, shift);
     }
     gsc_count_launch(); k_sel_finish<<<1, 32, 0, st>>>(sel, scales);
   }
@@ -476,4 +480,133 @@ extern "C" gsc_status gsc_plan_reorder_static(gsc_ctx* c, const float* d_pos, co
   }
   GscTimed tm(c, T_PLAN, (cudaStream_t)stream);
   return plan_run(c, d_pos, d_sh, pp, d_perm, d_scales, ws, GSC_PLAN_STATIC_BYTES, (cudaStream_t)stream);
+}
+
+// ---- one scene split over shards (Sec. V-A: the scales are order statistics of the whole
+// scene; Sec. III-C: the reorder works chunk by chunk once the spatial order is known) --------
+// Shards hold contiguous ranges of the input. The exchanges are integer: the bounding box
+// (elementwise minimum / maximum of order-preserving float codes), the Morton codes of every
+// Gaussian (to fix the spatial ranks), and the selection histograms of each pass (sums). Every
+// partial and every merged value is int64, so any reduction library can combine them.
+
+__global__ void k_bbox_widen(int64_t* bb) {  // u32 codes [6] at the front of bb -> int64 [6]
+  if (threadIdx.x != 0) return;
+  const uint32_t* u = reinterpret_cast<const uint32_t*>(bb);
+  uint32_t v[6];
+  for (int a = 0; a < 6; a++) v[a] = u[a];
+  for (int a = 0; a < 6; a++) bb[a] = (int64_t)v[a];
+}
+
+__global__ void k_morton_shard(const float* __restrict__ pos, int64_t n, const int64_t* __restrict__ bb,
+                               uint64_t* __restrict__ keys) {
+  float lo[3], ext[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    lo[a] = ord2f((uint32_t)bb[a]);
+    ext[a] = __fsub_rn(ord2f((uint32_t)bb[3 + a]), lo[a]);
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t x = grid10(__ldg(pos + 3 * i + 0), lo[0], ext[0]);
+    uint32_t y = grid10(__ldg(pos + 3 * i + 1), lo[1], ext[1]);
+    uint32_t z = grid10(__ldg(pos + 3 * i + 2), lo[2], ext[2]);
+    keys[i] = (spread3(x) << 2) | (spread3(y) << 1) | spread3(z);
+  }
+}
+
+__global__ void k_iota(uint32_t* __restrict__ v, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = (uint32_t)i;
+}
+
+__global__ void k_widen_u32(const uint32_t* __restrict__ in, int64_t* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int64_t)in[i];
+}
+
+cudaError_t shard_bbox(const float* pos, int64_t n, int64_t* bb, int sm_count, cudaStream_t st) {
+  uint32_t* u = reinterpret_cast<uint32_t*>(bb);
+  gsc_count_launch(); k_bbox_init<<<1, 32, 0, st>>>(u);
+  if (n > 0) { gsc_count_launch(); k_bbox<<<grid_stride(n, 256, sm_count * 2), 256, 0, st>>>(pos, n, u); }
+  gsc_count_launch(); k_bbox_widen<<<1, 32, 0, st>>>(bb);
+  return cudaGetLastError();
+}
+
+cudaError_t shard_morton(const float* pos, int64_t n, const int64_t* bb, uint64_t* keys, int sm_count, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  gsc_count_launch(); k_morton_shard<<<grid_stride(n, 256, sm_count * 8), 256, 0, st>>>(pos, n, bb, keys);
+  return cudaGetLastError();
+}
+
+size_t shard_order_ws_bytes(int64_t n) { return radix_ws_bytes(n) + 256; }
+
+cudaError_t shard_order(uint64_t* keys, int64_t n, int32_t* order, void* ws, int sm_count, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  uint32_t* vals = reinterpret_cast<uint32_t*>(order);
+  gsc_count_launch(); k_iota<<<grid_stride(n, 256, sm_count * 8), 256, 0, st>>>(vals, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return radix_sort_pairs(keys, vals, n, 30, ws, st);  // stable: equal codes keep the input order
+}
+
+size_t shard_select_state_bytes() { return align_up(sizeof(SelState), 256) + sizeof(uint32_t) * GSC_SH * 256; }
+
+cudaError_t shard_select_begin(int64_t n_total, int permille, void* state, cudaStream_t st) {
+  SelState* sel = reinterpret_cast<SelState*>(state);
+  const uint64_t m = 3ull * (uint64_t)n_total;
+  const uint64_t r = n_total > 0 ? ((uint64_t)permille * m + 999) / 1000 - 1 : 0;
+  gsc_count_launch(); k_sel_init<<<1, 32, 0, st>>>(sel, r);
+  return cudaGetLastError();
+}
+
+cudaError_t shard_select_hist(const float* sh, int64_t n, int shift, void* state, int64_t* hist, int sm_count,
+                              cudaStream_t st) {
+  SelState* sel = reinterpret_cast<SelState*>(state);
+  uint32_t* h32 = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(state) + align_up(sizeof(SelState), 256));
+  cudaError_t e = cudaMemsetAsync(h32, 0, sizeof(uint32_t) * GSC_SH * 256, st);
+  if (e != cudaSuccess) return e;
+  if (n > 0) {
+    const int64_t n4 = n * 12;
+    gsc_count_launch();
+    k_sel_hist<<<grid_stride(n4, 256, sm_count * 4), 256, 0, st>>>(reinterpret_cast<const float4*>(sh), n4, shift,
+                                                                    sel->prefix, h32);
+  }
+  gsc_count_launch(); k_widen_u32<<<16, 256, 0, st>>>(h32, hist, GSC_SH * 256);
+  return cudaGetLastError();
+}
+
+cudaError_t shard_select_pick(void* state, const int64_t* hist_total, int shift, cudaStream_t st) {
+  gsc_count_launch();
+  k_sel_pick<const int64_t, false><<<1, 32, 0, st>>>(reinterpret_cast<SelState*>(state), hist_total, shift);
+  return cudaGetLastError();
+}
+
+cudaError_t shard_select_scales(const void* state, float* scales, cudaStream_t st) {
+  gsc_count_launch(); k_sel_finish<<<1, 32, 0, st>>>(reinterpret_cast<const SelState*>(state), scales);
+  return cudaGetLastError();
+}
+
+size_t shard_plan_ws_bytes(int64_t n) {
+  return align_up(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1), 256) +
+         align_up(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1), 256) + radix_ws_bytes(n) + 1024;
+}
+
+// Slot order of a shard whose Gaussians are given in spatial-rank order and whose first one
+// starts a chunk: the stable (chunk, colour key) sort of the whole-scene plan, on this range.
+gsc_status shard_plan(const float* sh, int64_t n, const float* scales, int64_t group_size, int32_t* perm, void* ws,
+                      size_t ws_bytes, int sm_count, cudaStream_t st) {
+  const int64_t ns = ceil_div64(n, 16) * 16;
+  if (ws_bytes < shard_plan_ws_bytes(n)) return GSC_ERR_OOM;
+  if (ns == 0) return GSC_OK;
+  Carve c{reinterpret_cast<uint8_t*>(ws), 0, ws_bytes};
+  uint64_t* keys = c.take<uint64_t>(n);
+  uint32_t* vals = c.take<uint32_t>(n);
+  void* rws = c.take<uint8_t>((int64_t)radix_ws_bytes(n));
+  gsc_count_launch(); k_iota<<<grid_stride(n, 256, sm_count * 8), 256, 0, st>>>(vals, n);
+  gsc_count_launch(); k_colour_keys<<<grid_stride(n, 256, sm_count * 8), 256, 0, st>>>(sh, scales, n, group_size, keys, vals);
+  GSC_CUDA(cudaGetLastError());
+  const uint64_t max_chunk = (uint64_t)((n - 1) / group_size);
+  GSC_CUDA(radix_sort_pairs(keys, vals, n, 24 + bits_for(max_chunk), rws, st));
+  gsc_count_launch(); k_finish_perm<<<grid_stride(ns, 256, sm_count * 8), 256, 0, st>>>(vals, n, ns, 0, perm);
+  GSC_CUDA(cudaGetLastError());
+  return GSC_OK;
 }

@@ -399,3 +399,268 @@ size_t rate_ws_bytes(int64_t ng) {
   return align_up(8 * (size_t)nb, 256) + align_up(16 * (size_t)nb, 256) + 3 * align_up(4 * (size_t)nb, 256) + 1024 +
          rate_select_ws_bytes(ng);
 }
+
+// ---- one scene split over shards (Sec. IV-B: one rate budget for the whole scene) -----------
+// A shard holds whole groups of the scene's slot order (the whole-scene plan split at chunk
+// boundaries). Each phase leaves an integer partial that the caller sums (or gathers) over the
+// shards and hands to the next phase; with those sums every shard takes the decisions the
+// whole-scene search takes, and writes its groups where the whole-scene call writes them.
+#define SHARD_PART 15  // per shard after the fill: groups per mode [14] and bits used
+
+struct ShardInfo {
+  int64_t first[GSC_MODES], ngroups[GSC_MODES], offset[GSC_MODES], before[GSC_MODES], local_first[GSC_MODES];
+  int64_t total_bytes, ng_total;
+  uint64_t lambda, used, budget;
+  int infeasible;
+  uint32_t weights[GSC_SH];
+};
+
+struct ShardRate {
+  uint32_t *sse1, *sse7, *sse0;
+  uint64_t *dtab, *step_l;
+  uint8_t *step_m, *n_steps, *mode, *alt;
+  uint64_t *delta, *prefix, *keys, *total;
+  uint32_t *vals, *w;
+  RateState* S;
+  ShardInfo* info;
+  void *rws, *sws;
+  size_t end;
+};
+
+static ShardRate shard_carve(void* ws, int64_t ng) {
+  Carve c{reinterpret_cast<uint8_t*>(ws), 0, 0};
+  ShardRate r;
+  r.sse1 = c.take<uint32_t>(ng * 16);
+  r.sse7 = c.take<uint32_t>(ng * 16);
+  r.sse0 = c.take<uint32_t>(ng * 16);
+  r.dtab = c.take<uint64_t>(ng * GSC_MODES);
+  r.step_l = c.take<uint64_t>(ng * GSC_MODES);
+  r.step_m = c.take<uint8_t>(ng * GSC_MODES);
+  r.n_steps = c.take<uint8_t>(ng);
+  r.mode = c.take<uint8_t>(ng);
+  r.alt = c.take<uint8_t>(ng);
+  r.delta = c.take<uint64_t>(ng);
+  r.prefix = c.take<uint64_t>(ng);
+  r.keys = c.take<uint64_t>(ng);
+  r.total = c.take<uint64_t>(1);
+  r.vals = c.take<uint32_t>(ng);
+  r.w = c.take<uint32_t>(GSC_SH);
+  r.S = c.take<RateState>(1);
+  r.info = c.take<ShardInfo>(1);
+  r.rws = c.take<uint8_t>((int64_t)radix_ws_bytes(ng));
+  r.sws = c.take<uint8_t>((int64_t)scan_ws_bytes(ng));
+  r.end = c.off;
+  return r;
+}
+
+size_t shard_rate_ws_bytes(int64_t ng) { return shard_carve(nullptr, ng).end + 256; }
+
+__global__ void k_shard_put(const RateState* __restrict__ S, int what, int pass, int64_t* __restrict__ part) {
+  const int i = threadIdx.x;
+  if (what == 0 && i == 0) part[0] = (int64_t)S->min_total;
+  if (what == 1 && i < 64) part[i] = (int64_t)S->cnt[pass][i];
+  if (what == 2 && i < GSC_MODES) part[i] = (int64_t)S->counts[i];
+  if (what == 2 && i == GSC_MODES) part[i] = (int64_t)S->used;
+}
+
+__global__ void k_shard_search_init(RateState* S, const int64_t* __restrict__ min_total, uint64_t budget) {
+  if (threadIdx.x != 0) return;
+  S->min_total = (uint64_t)min_total[0];
+  S->budget = budget;
+  S->infeasible = S->min_total > budget;
+  S->lo = 0;
+  S->hi = 1ull << 62;
+  S->done = S->infeasible;
+}
+
+__global__ void k_shard_set_cnt(RateState* S, int pass, const int64_t* __restrict__ tot) {
+  if (threadIdx.x < 64) S->cnt[pass][threadIdx.x] = (uint64_t)tot[threadIdx.x];
+}
+
+__global__ void k_shard_fill_part(const RateState* __restrict__ S, const uint64_t* __restrict__ total,
+                                  int64_t* __restrict__ part) {
+  if (threadIdx.x == 0) { part[0] = (int64_t)S->sum_star; part[1] = (int64_t)total[0]; }
+}
+
+__global__ void k_shard_offsets(RateState* S, const int64_t* __restrict__ in, uint64_t* __restrict__ prefix, int64_t ng) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) S->sum_star = (uint64_t)in[0];
+  const uint64_t before = (uint64_t)in[1];
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x)
+    prefix[g] += before;
+}
+
+__global__ void k_shard_info(const RateState* __restrict__ S, const uint32_t* __restrict__ w,
+                             const int64_t* __restrict__ counts_all, int n_shards, int shard, ShardInfo* __restrict__ info) {
+  if (threadIdx.x != 0) return;
+  int64_t g = 0, off = 0, lf = 0, ngt = 0;
+  uint64_t used = 0;
+  for (int s = 0; s < n_shards; s++) used += (uint64_t)counts_all[s * SHARD_PART + GSC_MODES];
+  for (int m = 0; m < GSC_MODES; m++) {
+    int64_t tot = 0, before = 0;
+    for (int s = 0; s < n_shards; s++) {
+      const int64_t c = counts_all[s * SHARD_PART + m];
+      tot += c;
+      if (s < shard) before += c;
+    }
+    info->first[m] = g;
+    info->ngroups[m] = tot;
+    info->offset[m] = off;
+    info->before[m] = before;
+    info->local_first[m] = lf;
+    lf += counts_all[shard * SHARD_PART + m];
+    g += tot;
+    off += tot * (16 * c_modeJ[m] + 8 * (c_modeB[m] - c_modeJ[m]));
+    ngt += tot;
+  }
+  info->total_bytes = off;
+  info->ng_total = ngt;
+  info->lambda = S->lo;
+  info->used = used;
+  info->budget = S->budget;
+  info->infeasible = S->infeasible;
+  for (int k = 0; k < GSC_SH; k++) info->weights[k] = w[k];
+}
+
+__global__ void k_shard_assemble(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ order, int64_t ng,
+                                 const ShardInfo* __restrict__ info, const uint2* __restrict__ b1,
+                                 const uint2* __restrict__ b7, const int32_t* __restrict__ perm,
+                                 const int32_t* __restrict__ index_map, uint8_t* __restrict__ out,
+                                 int32_t* __restrict__ perm_out) {
+  for (int64_t G = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; G < ng; G += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = order[G];
+    const int m = (int)keys[G];
+    const int J = c_modeJ[m], B = c_modeB[m];
+    const int64_t gbytes = 16 * J + 8 * (B - J);
+    const int64_t in_stream = info->before[m] + (G - info->local_first[m]);
+    uint2* dst = reinterpret_cast<uint2*>(out + info->offset[m] + in_stream * gbytes);
+    for (int k = 0; k < J; k++) { dst[2 * k] = b7[(g * 16 + k) * 2]; dst[2 * k + 1] = b7[(g * 16 + k) * 2 + 1]; }
+    for (int k = J; k < B; k++) dst[2 * J + (k - J)] = b1[g * 16 + k];
+    const int64_t gs = info->first[m] + in_stream;
+#pragma unroll
+    for (int t = 0; t < 16; t++) {
+      const int32_t p = perm[g * 16 + t];
+      perm_out[gs * 16 + t] = (p >= 0 && index_map) ? index_map[p] : p;
+    }
+  }
+}
+
+gsc_status shard_rate_begin(gsc_ctx* ctx, const float* sh, int64_t n, const int32_t* perm, const float* scales,
+                            uint8_t* b1, uint8_t* b7, void* ws, size_t ws_bytes, int64_t* part, cudaStream_t st) {
+  const int64_t ng = ceil_div64(n, 16);
+  if (ws_bytes < shard_rate_ws_bytes(ng)) return GSC_ERR_OOM;
+  ShardRate r = shard_carve(ws, ng);
+  const int cap = ctx->sm_count * 8;
+  GSC_CUDA(cudaMemsetAsync(r.S, 0, sizeof(RateState), st));
+  if (ng > 0) {
+    {
+      GscTimed tm(ctx, T_BC1, st);
+      GSC_CUDA(launch_bc1_groups(sh, perm, scales, ng, b1, r.sse1, r.sse0, st));
+    }
+    {
+      GscTimed tm(ctx, T_BC7, st);
+      GSC_CUDA(launch_bc7_groups(sh, perm, scales, ng, b7, r.sse7, st));
+    }
+  }
+  gsc_count_launch(); k_weights<<<1, 32, 0, st>>>(scales, r.w);
+  if (ng > 0) {
+    gsc_count_launch();
+    k_dtable<<<gsz(ng, 128, cap), 128, 0, st>>>(r.sse1, r.sse7, r.sse0, r.w, ng, r.dtab, r.step_l, r.step_m, r.n_steps, r.S);
+  }
+  gsc_count_launch(); k_shard_put<<<1, 64, 0, st>>>(r.S, 0, 0, part);
+  GSC_CUDA(cudaGetLastError());
+  return GSC_OK;
+}
+
+gsc_status shard_rate_search_begin(int64_t ng, void* ws, int64_t n_total, uint32_t target_x4, const int64_t* min_total,
+                                   cudaStream_t st) {
+  ShardRate r = shard_carve(ws, ng);
+  const uint64_t budget = (uint64_t)target_x4 * 4ull * (uint64_t)n_total;
+  gsc_count_launch(); k_shard_search_init<<<1, 32, 0, st>>>(r.S, min_total, budget);
+  GSC_CUDA(cudaGetLastError());
+  return GSC_OK;
+}
+
+gsc_status shard_rate_count(gsc_ctx* ctx, int64_t ng, void* ws, int pass, int64_t* part, cudaStream_t st) {
+  ShardRate r = shard_carve(ws, ng);
+  if (ng > 0) {
+    gsc_count_launch();
+    k_search_count<<<gsz(ng, 256, ctx->sm_count * 8), 256, 0, st>>>(r.step_l, r.step_m, r.n_steps, ng, r.S, pass);
+  }
+  gsc_count_launch(); k_shard_put<<<1, 64, 0, st>>>(r.S, 1, pass, part);
+  GSC_CUDA(cudaGetLastError());
+  return GSC_OK;
+}
+
+gsc_status shard_rate_narrow(int64_t ng, void* ws, int pass, const int64_t* total, cudaStream_t st) {
+  ShardRate r = shard_carve(ws, ng);
+  gsc_count_launch(); k_shard_set_cnt<<<1, 64, 0, st>>>(r.S, pass, total);
+  gsc_count_launch(); k_search_narrow<<<1, 32, 0, st>>>(r.S, pass);
+  GSC_CUDA(cudaGetLastError());
+  return GSC_OK;
+}
+
+gsc_status shard_rate_fill(gsc_ctx* ctx, int64_t ng, void* ws, int64_t* part, cudaStream_t st) {
+  ShardRate r = shard_carve(ws, ng);
+  GSC_CUDA(cudaMemsetAsync(r.total, 0, sizeof(uint64_t), st));
+  if (ng > 0) {
+    gsc_count_launch();
+    k_fill_prep<<<gsz(ng, 256, ctx->sm_count * 8), 256, 0, st>>>(r.step_l, r.step_m, r.n_steps, ng, r.S, r.mode, r.alt,
+                                                                 r.delta);
+    GSC_CUDA(cudaGetLastError());
+    GSC_CUDA(scan_exclusive<uint64_t>(r.delta, r.prefix, ng, r.total, r.sws, st));
+  }
+  gsc_count_launch(); k_shard_fill_part<<<1, 32, 0, st>>>(r.S, r.total, part);
+  GSC_CUDA(cudaGetLastError());
+  return GSC_OK;
+}
+
+gsc_status shard_rate_apply(gsc_ctx* ctx, int64_t ng, void* ws, const int64_t* in, int64_t* part, cudaStream_t st) {
+  ShardRate r = shard_carve(ws, ng);
+  const int cap = ctx->sm_count * 8;
+  gsc_count_launch(); k_shard_offsets<<<gsz(ng, 256, cap), 256, 0, st>>>(r.S, in, r.prefix, ng);
+  if (ng > 0) {
+    gsc_count_launch();
+    k_fill_apply<<<gsz(ng, 256, cap), 256, 0, st>>>(ng, r.S, r.mode, r.alt, r.delta, r.prefix, r.keys, r.vals);
+  }
+  gsc_count_launch(); k_shard_put<<<1, 64, 0, st>>>(r.S, 2, 0, part);
+  GSC_CUDA(cudaGetLastError());
+  return GSC_OK;
+}
+
+gsc_status shard_rate_assemble(gsc_ctx* ctx, int64_t ng, void* ws, const uint8_t* b1, const uint8_t* b7,
+                               const int32_t* perm, const int32_t* index_map, const int64_t* counts_all, int n_shards,
+                               int shard, int64_t n_total, uint8_t* blocks, int32_t* perm_out, gsc_stream_table* table,
+                               cudaStream_t st) {
+  ShardRate r = shard_carve(ws, ng);
+  gsc_count_launch(); k_shard_info<<<1, 32, 0, st>>>(r.S, r.w, counts_all, n_shards, shard, r.info);
+  GSC_CUDA(cudaGetLastError());
+  if (ng > 0) {
+    GSC_CUDA(radix_sort_pairs(r.keys, r.vals, ng, 4, r.rws, st));
+    gsc_count_launch();
+    k_shard_assemble<<<gsz(ng, 128, ctx->sm_count * 8), 128, 0, st>>>(
+        r.keys, r.vals, ng, r.info, reinterpret_cast<const uint2*>(b1), reinterpret_cast<const uint2*>(b7), perm,
+        index_map, blocks, perm_out);
+    GSC_CUDA(cudaGetLastError());
+  }
+  ShardInfo* h = reinterpret_cast<ShardInfo*>(ctx->h_pinned);
+  GSC_CUDA(cudaMemcpyAsync(h, r.info, sizeof(ShardInfo), cudaMemcpyDeviceToHost, st));
+  GSC_CUDA(cudaStreamSynchronize(st));
+  if (h->infeasible) return GSC_ERR_BUDGET;
+  table->n_streams = GSC_MODES;
+  table->format = GSC_FMT_RATE;
+  table->n = n_total;
+  table->n_groups = h->ng_total;
+  table->total_bytes = h->total_bytes;
+  table->budget_bits = h->budget;
+  table->used_bits = h->used;
+  table->lambda = h->lambda;
+  for (int k = 0; k < GSC_SH; k++) table->weights[k] = h->weights[k];
+  for (int m = 0; m < GSC_MODES; m++) {
+    table->s[m].bands = h_modeB[m];
+    table->s[m].bc7_blocks = h_modeJ[m];
+    table->s[m].first_group = h->first[m];
+    table->s[m].n_groups = h->ngroups[m];
+    table->s[m].byte_offset = h->offset[m];
+  }
+  return GSC_OK;
+}

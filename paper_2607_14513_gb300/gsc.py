@@ -178,6 +178,27 @@ _SIGS = {
     "gsc_server_destroy": [_P],
     "gsc_server_simulate": [C.POINTER(ServerParams), C.POINTER(SimRequest), C.c_int32, C.POINTER(SimResult),
                             C.POINTER(C.c_uint64)],
+    "gsc_shard_bounds": [C.c_int64, C.c_int32, C.c_int64, C.POINTER(C.c_int64)],
+    "gsc_shard_bbox": [_P, _P, C.c_int64, _P, _P],
+    "gsc_shard_morton": [_P, _P, C.c_int64, _P, _P, _P],
+    "gsc_shard_order_ws_bytes": [C.c_int64],
+    "gsc_shard_order": [_P, _P, C.c_int64, _P, _P, C.c_size_t, _P],
+    "gsc_shard_select_state_bytes": [],
+    "gsc_shard_select_begin": [_P, C.c_int64, C.c_uint32, _P, _P],
+    "gsc_shard_select_hist": [_P, _P, C.c_int64, C.c_int32, _P, _P, _P],
+    "gsc_shard_select_pick": [_P, _P, _P, C.c_int32, _P],
+    "gsc_shard_select_scales": [_P, _P, _P, _P],
+    "gsc_shard_plan_ws_bytes": [C.c_int64],
+    "gsc_shard_plan": [_P, _P, C.c_int64, _P, C.c_int64, _P, _P, C.c_size_t, _P],
+    "gsc_shard_rate_ws_bytes": [C.c_int64],
+    "gsc_shard_rate_begin": [_P, _P, C.c_int64, _P, _P, _P, _P, _P, C.c_size_t, _P, _P],
+    "gsc_shard_rate_search_begin": [_P, C.c_int64, _P, C.c_int64, C.c_uint32, _P, _P],
+    "gsc_shard_rate_count": [_P, C.c_int64, _P, C.c_int32, _P, _P],
+    "gsc_shard_rate_narrow": [_P, C.c_int64, _P, C.c_int32, _P, _P],
+    "gsc_shard_rate_fill": [_P, C.c_int64, _P, _P, _P],
+    "gsc_shard_rate_apply": [_P, C.c_int64, _P, _P, _P, _P],
+    "gsc_shard_rate_assemble": [_P, C.c_int64, _P, _P, _P, _P, _P, _P, _P, C.c_int32, C.c_int32, C.c_int64, _P, _P,
+                                C.POINTER(StreamTable), _P],
     "gsc_build_checked": [],
     "gsc_launch_count": [],
     "gsc_probe_int_peak": [_P, C.POINTER(C.c_double), _P],
@@ -214,6 +235,9 @@ def load(path: str | None = None):
             lib.gsc_render_workspace_bytes.restype = C.c_size_t
             lib.gsc_geometry_bytes.restype = C.c_size_t
             lib.gsc_geometry_layout.restype = C.c_size_t
+            for name in ("gsc_shard_order_ws_bytes", "gsc_shard_select_state_bytes", "gsc_shard_plan_ws_bytes",
+                         "gsc_shard_rate_ws_bytes"):
+                getattr(lib, name).restype = C.c_size_t
             _lib = lib
     return _lib
 
@@ -735,3 +759,141 @@ def scene_read(path, device=None):
     _check(lib.gsc_scene_read(os.fsencode(path), C.byref(t), _ptr(blocks), blocks.numel(), _ptr(perm),
                               4 * perm.numel(), _ptr(pos), 0 if pos is None else 4 * pos.numel()), "gsc_scene_read")
     return t, blocks[:t.total_bytes], perm[:t.n_groups * 16], (pos[:t.n] if pos is not None else None)
+
+
+# ---- one scene split over shards (argument marshalling only; the driver is shard.py) ---------
+SHARD_SELECT_PASSES = 4
+SHARD_RATE_PASSES = 13
+SHARD_RATE_PART = 15
+
+
+def shard_bounds(n_total, n_shards, group_size):
+    b = (C.c_int64 * (n_shards + 1))()
+    _check(load().gsc_shard_bounds(n_total, n_shards, group_size, b), "gsc_shard_bounds")
+    return [int(x) for x in b]
+
+
+def _i64(n, device):
+    import torch
+    return torch.zeros(n, dtype=torch.int64, device=device)
+
+
+def gsc_shard_bbox(ctx, pos, stream=None):
+    bb = _i64(6, pos.device)
+    _check(ctx.lib.gsc_shard_bbox(ctx.h, _ptr(pos), pos.shape[0], _ptr(bb), _stream(stream)), "gsc_shard_bbox")
+    return bb
+
+
+def gsc_shard_morton(ctx, pos, bb, stream=None):
+    import torch
+    keys = torch.empty(pos.shape[0], dtype=torch.int64, device=pos.device)
+    _check(ctx.lib.gsc_shard_morton(ctx.h, _ptr(pos), pos.shape[0], _ptr(bb), _ptr(keys), _stream(stream)),
+           "gsc_shard_morton")
+    return keys
+
+
+def gsc_shard_order(ctx, keys, stream=None):
+    """Input indices in spatial order; `keys` (all shards' Morton codes in input order) is clobbered."""
+    import torch
+    n = keys.shape[0]
+    order = torch.empty(n, dtype=torch.int32, device=keys.device)
+    wsb = ctx.lib.gsc_shard_order_ws_bytes(n)
+    ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=keys.device)
+    _check(ctx.lib.gsc_shard_order(ctx.h, _ptr(keys), n, _ptr(order), _ptr(ws), wsb, _stream(stream)),
+           "gsc_shard_order")
+    return order
+
+
+def shard_select_state(ctx, device):
+    import torch
+    return torch.zeros(ctx.lib.gsc_shard_select_state_bytes(), dtype=torch.uint8, device=device)
+
+
+def gsc_shard_select_begin(ctx, n_total, permille, state, stream=None):
+    _check(ctx.lib.gsc_shard_select_begin(ctx.h, n_total, permille, _ptr(state), _stream(stream)),
+           "gsc_shard_select_begin")
+
+
+def gsc_shard_select_hist(ctx, sh, p, state, stream=None):
+    hist = _i64(16 * 256, state.device)
+    _check(ctx.lib.gsc_shard_select_hist(ctx.h, _ptr(sh), sh.shape[0], p, _ptr(state), _ptr(hist), _stream(stream)),
+           "gsc_shard_select_hist")
+    return hist
+
+
+def gsc_shard_select_pick(ctx, state, hist, p, stream=None):
+    _check(ctx.lib.gsc_shard_select_pick(ctx.h, _ptr(state), _ptr(hist), p, _stream(stream)), "gsc_shard_select_pick")
+
+
+def gsc_shard_select_scales(ctx, state, stream=None):
+    import torch
+    scales = torch.empty(16, dtype=torch.float32, device=state.device)
+    _check(ctx.lib.gsc_shard_select_scales(ctx.h, _ptr(state), _ptr(scales), _stream(stream)),
+           "gsc_shard_select_scales")
+    return scales
+
+
+def gsc_shard_plan(ctx, sh, scales, group_size, stream=None):
+    import torch
+    n = sh.shape[0]
+    perm = torch.empty((n + 15) // 16 * 16, dtype=torch.int32, device=sh.device)
+    wsb = ctx.lib.gsc_shard_plan_ws_bytes(n)
+    ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=sh.device)
+    _check(ctx.lib.gsc_shard_plan(ctx.h, _ptr(sh), n, _ptr(scales), group_size, _ptr(perm), _ptr(ws), wsb,
+                                  _stream(stream)), "gsc_shard_plan")
+    return perm
+
+
+class ShardRate:
+    """One shard's rate-control state (workspace and its BC1 / BC7 codings) across the phases."""
+
+    def __init__(self, ctx, n, device):
+        import torch
+        self.ctx, self.n = ctx, n
+        ng = (n + 15) // 16
+        self.wsb = ctx.lib.gsc_shard_rate_ws_bytes(n)
+        self.ws = torch.empty(self.wsb, dtype=torch.uint8, device=device)
+        self.bc1 = torch.empty(max(ng * 128, 16), dtype=torch.uint8, device=device)
+        self.bc7 = torch.empty(max(ng * 256, 16), dtype=torch.uint8, device=device)
+        self.device = device
+
+    def begin(self, sh, perm, scales, stream=None):
+        part = _i64(1, self.device)
+        _check(self.ctx.lib.gsc_shard_rate_begin(self.ctx.h, _ptr(sh), self.n, _ptr(perm), _ptr(scales),
+                                                 _ptr(self.bc1), _ptr(self.bc7), _ptr(self.ws), self.wsb, _ptr(part),
+                                                 _stream(stream)), "gsc_shard_rate_begin")
+        return part
+
+    def search_begin(self, n_total, target_x4, min_total, stream=None):
+        _check(self.ctx.lib.gsc_shard_rate_search_begin(self.ctx.h, self.n, _ptr(self.ws), n_total, target_x4,
+                                                        _ptr(min_total), _stream(stream)), "gsc_shard_rate_search_begin")
+
+    def count(self, p, stream=None):
+        part = _i64(64, self.device)
+        _check(self.ctx.lib.gsc_shard_rate_count(self.ctx.h, self.n, _ptr(self.ws), p, _ptr(part), _stream(stream)),
+               "gsc_shard_rate_count")
+        return part
+
+    def narrow(self, p, total, stream=None):
+        _check(self.ctx.lib.gsc_shard_rate_narrow(self.ctx.h, self.n, _ptr(self.ws), p, _ptr(total), _stream(stream)),
+               "gsc_shard_rate_narrow")
+
+    def fill(self, stream=None):
+        part = _i64(2, self.device)
+        _check(self.ctx.lib.gsc_shard_rate_fill(self.ctx.h, self.n, _ptr(self.ws), _ptr(part), _stream(stream)),
+               "gsc_shard_rate_fill")
+        return part
+
+    def apply(self, inp, stream=None):
+        part = _i64(SHARD_RATE_PART, self.device)
+        _check(self.ctx.lib.gsc_shard_rate_apply(self.ctx.h, self.n, _ptr(self.ws), _ptr(inp), _ptr(part),
+                                                 _stream(stream)), "gsc_shard_rate_apply")
+        return part
+
+    def assemble(self, perm, index_map, scales, parts_all, shard, n_total, blocks, perm_out, stream=None):
+        t = StreamTable()
+        _check(self.ctx.lib.gsc_shard_rate_assemble(self.ctx.h, self.n, _ptr(self.ws), _ptr(self.bc1), _ptr(self.bc7),
+                                                    _ptr(perm), _ptr(index_map), _ptr(scales), _ptr(parts_all),
+                                                    parts_all.shape[0], shard, n_total, _ptr(blocks), _ptr(perm_out),
+                                                    C.byref(t), _stream(stream)), "gsc_shard_rate_assemble")
+        return t
