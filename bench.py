@@ -195,11 +195,11 @@ def run_gsc(args, world, rank, local):
     pos_slot_r = torch.empty((ns, 3), dtype=torch.float32, device=dev)
     ok = torch.ones((), dtype=torch.bool, device=dev)
 
-    last_perm = [None]
+    last_perm = [None, None]
 
     def step(pos_d, sh_d):
         perm, scales = gsc.gsc_plan_reorder(ctx, pos_d, sh_d, ws=ws, stream=stream)
-        last_perm[0] = perm
+        last_perm[0], last_perm[1] = perm, scales
         gsc.gsc_positions_to_slots(ctx, pos_d, perm, out=pos_slot, stream=stream)
         rblk, rperm, rtab = gsc.gsc_encode(ctx, sh_d, perm, scales, gsc.FMT_RATE, RATE_TARGET_X4, ws=ws,
                                            out=rate_buf, perm_out=rate_perm, stream=stream, bc1_all=bc1, bc7_all=bc7)
@@ -327,6 +327,9 @@ def run_gsc(args, world, rank, local):
     stages["decode_eval_bc7_slot_order_GB_s"] = round(ev_bytes / (ms_slot * 1e-3) / 1e9, 1)
     del rgb_slot
 
+    # the BC7 search's thread mapping: mode 1 alone, thread per block against warp per block
+    stages.update(time_bc7_mappings(ctx, gsc, stream, sh, last_perm[0], last_perm[1], n))
+
     # end to end through the public API with host buffers
     e2e = run_e2e(args, ctx, gsc, stream, dev, sc, step, world, rgb)
 
@@ -372,6 +375,29 @@ def bc7_roofline(ctx, gsc, stream, dev, clk, evals, ms, kernel, blocks, traffic)
                                "thread_instr_per_eval": round(MEASURED_BC7_THREAD_INSTR_PER_BLOCK * blocks / evals, 2),
                                "Tinstr_s": round(ti / 1e12, 3), "frac_of_issue_ceiling": round(ti / issue, 4)}
     return out
+
+
+def time_bc7_mappings(ctx, gsc, stream, sh, perm, scales, n):
+    """The mode-1 search (64 partitions) over the scene's staged BC7 texels, thread per block and
+    warp per block (gsc_probe_bc7_mode1): launch times and whether the results agree."""
+    import torch
+    q = gsc.gsc_quantise(ctx, sh, scales, stream=stream)
+    with torch.cuda.stream(stream):
+        qp = torch.cat([q.reshape(n, 48), torch.full((1, 48), 128, dtype=torch.uint8, device=q.device)])
+        idx = torch.where(perm < 0, torch.full_like(perm, n), perm).long()
+        tex = qp[idx].view(-1, 16, 16, 3).permute(0, 2, 1, 3).reshape(-1, 16, 3).contiguous()
+    res, out = {}, {}
+    for name, warp in (("thread_per_block", False), ("warp_per_block", True)):
+        gsc.bc7_mode1(ctx, tex, warp, stream=stream)
+        times = []
+        for _ in range(3):
+            sse, part, ms = gsc.bc7_mode1(ctx, tex, warp, stream=stream)
+            times.append(ms)
+        out[name] = (sse, part)
+        res["bc7_mode1_%s_ms" % name] = round(min(times), 3)
+    a, b = out["thread_per_block"], out["warp_per_block"]
+    res["bc7_mode1_mappings_equal"] = bool(torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]))
+    return res
 
 
 def time_tex_eval(args, ctx, gsc, stream, dev, rtab, bc1, bc7, perm, pos, cams, n, ns):

@@ -645,6 +645,13 @@ gsc_status gsc_probe_int_peak(gsc_ctx* ctx, double* ops_per_s, void* stream);
  * with a palette entry, key - 32 * dot, running minimum: 3 operations per evaluation). Stores
  * operations per second; GSC_ERR_INVALID_ARG for another kind; synchronises `stream`. */
 gsc_status gsc_probe_op_rate(gsc_ctx* ctx, int32_t kind, double* ops_per_s, void* stream);
+/* gsc_probe_bc7_mode1: the BC7 search restricted to mode 1 (64 two-subset partitions) over d_tex
+ * [nblk][16][3] (u8 texels, the layout of gsc_encode_blocks), mapped thread per block
+ * (warp_per_block 0, as the encoder) or warp per block (1: two partitions per lane and a shuffle
+ * minimum). Writes each block's least error d_sse [nblk] and its partition d_part [nblk] (ties to
+ * the lowest), the same for both mappings, and the launch's duration in *ms; synchronises `stream`. */
+gsc_status gsc_probe_bc7_mode1(gsc_ctx* ctx, const uint8_t* d_tex, int64_t nblk, int32_t warp_per_block,
+                               uint32_t* d_sse, int32_t* d_part, double* ms, void* stream);
 /* Kernel timing: when enabled, each call records CUDA events on its own stream around its
  * main kernels. gsc_kernel_time waits for the recorded events and returns the summed
  * milliseconds and launch count of one kernel ("plan", "bc1_encode", "bc7_encode",

@@ -198,6 +198,29 @@ extern "C" gsc_status gsc_probe_op_rate(gsc_ctx* c, int32_t kind, double* ops_pe
   return GSC_OK;
 }
 
+extern "C" gsc_status gsc_probe_bc7_mode1(gsc_ctx* c, const uint8_t* d_tex, int64_t nblk, int32_t warp_per_block,
+                                          uint32_t* d_sse, int32_t* d_part, double* ms, void* stream) {
+  if (!c || !ms || nblk < 0 || nblk > ((int64_t)1 << 40) || (warp_per_block != 0 && warp_per_block != 1))
+    return GSC_ERR_INVALID_ARG;
+  if (nblk > 0 && (!d_tex || !d_sse || !d_part)) return GSC_ERR_INVALID_ARG;
+  GSC_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  GSC_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return GSC_ERR_CUDA; }
+  cudaEventRecord(e0, st);
+  cudaError_t e = launch_bc7_mode1(d_tex, nblk, warp_per_block, d_sse, d_part, c->sm_count, st);
+  cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return GSC_ERR_CUDA;
+  *ms = t;
+  return GSC_OK;
+}
+
 int gsc_sm_count() {
   static std::atomic<int> cache[64];
   int dev = 0;

@@ -817,3 +817,84 @@ cudaError_t launch_batch_encode(int kind, const BatchSceneDev* scenes, int n_sce
   else k_batch<1><<<(int)grid, STAGE_THREADS, 0, st>>>(scenes, n_scenes, n_tiles, schedule, counter);
   return cudaGetLastError();
 }
+
+// ---- one mode family searched two ways (a measurement of the search's thread mapping) --------
+// Mode 1 only (64 two-subset partitions, 6-bit endpoints with a shared p-bit, 3-bit indices):
+// the least-error partition of each block, ties to the lowest, with its error. Thread per block
+// (as k_bc7: every lane of a warp fits the same partition, so the member loops are uniform) or
+// warp per block (lane l fits partitions l and l + 32 of the warp's block, then a shuffle
+// minimum over (error, partition)); the results are the same.
+template <bool WARP>
+__global__ void __launch_bounds__(STAGE_THREADS) k_bc7_mode1(const uint8_t* __restrict__ texin, int64_t nblk,
+                                                             uint32_t* __restrict__ sse_out,
+                                                             int32_t* __restrict__ part_out) {
+  __shared__ uint32_t tex[16][STAGE_STRIDE];
+  __shared__ uint16_t sq[12 * 256];
+  for (int i = threadIdx.x; i < 12 * 256; i += blockDim.x) sq[i] = (&g_qtab[0][0])[i];
+  const int lt = threadIdx.x;
+  for (int64_t b0 = (int64_t)blockIdx.x * STAGE_THREADS; b0 < nblk; b0 += (int64_t)gridDim.x * STAGE_THREADS) {
+    __syncthreads();
+    if (WARP) {
+      // 128 blocks per step: texel t of block b0 + j at tex[t][j]; warp w then takes blocks
+      // b0 + 32 w + i for i < 32 in turn
+      for (int i = lt; i < STAGE_THREADS * 16; i += STAGE_THREADS) {
+        const int j = i / 16, t = i % 16;
+        const int64_t blk = b0 + j;
+        const uint8_t* p = texin + blk * 48 + 3 * t;
+        tex[t][j] = blk < nblk ? ((uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16)) : 0x808080u;
+      }
+    } else {
+      const int64_t blk = b0 + lt;
+      const uint8_t* p = texin + blk * 48;
+#pragma unroll
+      for (int t = 0; t < 16; t++)
+        tex[t][lt] = blk < nblk ? ((uint32_t)p[3 * t] | ((uint32_t)p[3 * t + 1] << 8) | ((uint32_t)p[3 * t + 2] << 16))
+                                : 0x808080u;
+    }
+    __syncthreads();
+    if (WARP) {
+      const int w = lt >> 5, lane = lt & 31;
+#pragma unroll 1
+      for (int i = 0; i < 32; i++) {
+        const int j = 32 * w + i;
+        const uint32_t* my = &tex[0][j];
+        const uint32_t sa = score_part<2, 3, PT_SHARED, 6>(my, c_part2[lane], sq);
+        const uint32_t sb = score_part<2, 3, PT_SHARED, 6>(my, c_part2[lane + 32], sq);
+        uint32_t best = sa;
+        int bp = lane;
+        if (sb < best) { best = sb; bp = lane + 32; }
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) {
+          const uint32_t ob = __shfl_xor_sync(0xFFFFFFFFu, best, d);
+          const int op = __shfl_xor_sync(0xFFFFFFFFu, bp, d);
+          if (ob < best || (ob == best && op < bp)) { best = ob; bp = op; }
+        }
+        const int64_t blk = b0 + j;
+        if (lane == 0 && blk < nblk) { sse_out[blk] = best; part_out[blk] = bp; }
+      }
+    } else {
+      const uint32_t* my = &tex[0][lt];
+      uint32_t best = 0xFFFFFFFFu;
+      int bp = 0;
+#pragma unroll 1
+      for (int p = 0; p < 64; p++) {
+        const uint32_t s = score_part<2, 3, PT_SHARED, 6>(my, c_part2[p], sq);
+        if (s < best) { best = s; bp = p; }
+      }
+      const int64_t blk = b0 + lt;
+      if (blk < nblk) { sse_out[blk] = best; part_out[blk] = bp; }
+    }
+  }
+}
+
+cudaError_t launch_bc7_mode1(const uint8_t* tex, int64_t nblk, int warp, uint32_t* sse, int32_t* part, int sm_count,
+                             cudaStream_t st) {
+  if (nblk <= 0) return cudaSuccess;
+  int64_t g = ceil_div64(nblk, STAGE_THREADS);
+  const int64_t cap = (int64_t)sm_count * 8;
+  if (g > cap) g = cap;
+  gsc_count_launch();
+  if (warp) k_bc7_mode1<true><<<(int)g, STAGE_THREADS, 0, st>>>(tex, nblk, sse, part);
+  else k_bc7_mode1<false><<<(int)g, STAGE_THREADS, 0, st>>>(tex, nblk, sse, part);
+  return cudaGetLastError();
+}

@@ -223,3 +223,6 @@ gsc_status shard_rate_assemble(gsc_ctx* ctx, int64_t ng, void* ws, const uint8_t
                                const int32_t* perm, const int32_t* index_map, const int64_t* counts_all, int n_shards,
                                int shard, int64_t n_total, uint8_t* blocks, int32_t* perm_out, gsc_stream_table* table,
                                cudaStream_t st);
+// bc7.cu: the mode-1 search alone, thread per block (warp = 0) or warp per block (1)
+cudaError_t launch_bc7_mode1(const uint8_t* tex, int64_t nblk, int warp, uint32_t* sse, int32_t* part, int sm_count,
+                             cudaStream_t st);

@@ -203,6 +203,7 @@ _SIGS = {
     "gsc_launch_count": [],
     "gsc_probe_int_peak": [_P, C.POINTER(C.c_double), _P],
     "gsc_probe_op_rate": [_P, C.c_int32, C.POINTER(C.c_double), _P],
+    "gsc_probe_bc7_mode1": [_P, _P, C.c_int64, C.c_int32, _P, _P, C.POINTER(C.c_double), _P],
     "gsc_ctx_set_timing": [_P, C.c_int],
     "gsc_kernel_time": [_P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)],
 }
@@ -359,6 +360,18 @@ def op_rate(ctx, kind, stream=None):
     v = C.c_double(0.0)
     _check(ctx.lib.gsc_probe_op_rate(ctx.h, kind, C.byref(v), _stream(stream)), "gsc_probe_op_rate")
     return v.value
+
+
+def bc7_mode1(ctx, tex, warp_per_block, stream=None):
+    """The mode-1 search alone (gsc_probe_bc7_mode1): -> (sse uint32 [n], partition int32 [n], ms)."""
+    import torch
+    n = tex.shape[0]
+    sse = torch.empty(n, dtype=torch.int32, device=tex.device)
+    part = torch.empty(n, dtype=torch.int32, device=tex.device)
+    ms = C.c_double(0.0)
+    _check(ctx.lib.gsc_probe_bc7_mode1(ctx.h, _ptr(tex), n, 1 if warp_per_block else 0, _ptr(sse), _ptr(part),
+                                       C.byref(ms), _stream(stream)), "gsc_probe_bc7_mode1")
+    return sse, part, ms.value
 
 
 def set_timing(ctx, enable=True):

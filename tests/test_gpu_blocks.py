@@ -110,3 +110,20 @@ def test_texture_unit_bc7_every_candidate(ctx, O):
     assert bad.size == 0, "first mismatch block %d mode byte %d" % (bad[0], blks[bad[0], 0])
     sw = gsc.gsc_decode_blocks(ctx, torch.from_numpy(blks).cuda(), 7).cpu().numpy()
     assert np.array_equal(sw, ref)
+
+
+def test_bc7_mode1_thread_and_warp_mappings(ctx, O):
+    # the mode-1 search mapped thread per block and warp per block: the same least error and
+    # partition for every block, and both equal to the oracle's mode-1 candidates (Sec. III-B)
+    from paper_2607_14513_gb300 import gsc
+    rng = np.random.default_rng(107)
+    tex = _texels(rng, 777)
+    td = torch.from_numpy(tex).cuda()
+    s0, p0, _ = gsc.bc7_mode1(ctx, td, False)
+    s1, p1, _ = gsc.bc7_mode1(ctx, td, True)
+    torch.cuda.synchronize()
+    assert torch.equal(s0, s1) and torch.equal(p0, p1)
+    s0, p0 = s0.cpu().numpy(), p0.cpu().numpy()
+    for b in range(0, tex.shape[0], 7):
+        errs = [O.bc7_candidate(tex[b], 16 + p)[0] for p in range(64)]
+        assert int(s0[b]) == min(errs) and int(p0[b]) == int(np.argmin(errs)), b
