@@ -73,7 +73,11 @@ typedef enum { GSC_LAYOUT_D = 0, GSC_LAYOUT_A = 1, GSC_LAYOUT_B = 2 } gsc_layout
 typedef enum {
   GSC_OUT_VIEW_MAJOR = 0,  /* rgb [V][n][3], original Gaussian order (through the inverse permutation) */
   GSC_OUT_SLOT_ORDER = 1,  /* rgb [V][n_groups*16][3], slot order, padding slots written as 0 */
-  GSC_OUT_GAUSS_MAJOR = 2  /* rgb [n][V][3], original Gaussian order */
+  GSC_OUT_GAUSS_MAJOR = 2, /* rgb [n][V][3], original Gaussian order */
+  GSC_OUT_SLOT_ROWS = 3    /* rgb [n_groups*16][V][3], slot order (the order the coded scene keeps its
+                              Gaussians in: Sec. III-C reorders them with their coefficients), one
+                              row per Gaussian, padding rows written as 0; direct calls and the
+                              batched graph only (the request loop takes orders 0-2) */
 } gsc_out_order;
 
 typedef struct gsc_ctx gsc_ctx;

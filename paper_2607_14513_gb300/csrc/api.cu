@@ -545,7 +545,7 @@ extern "C" gsc_status gsc_decode_eval_sh(gsc_ctx* c, const gsc_stream_table* tab
   DevTable T;
   gsc_status s = make_dev_table(table, &T);
   if (s != GSC_OK) return s;
-  if (V < 1 || V > 64 || out_order < 0 || out_order > 2) return GSC_ERR_INVALID_ARG;
+  if (V < 1 || V > 64 || out_order < 0 || out_order > 3) return GSC_ERR_INVALID_ARG;
   if ((d_dirs == nullptr) == (d_cams == nullptr)) return GSC_ERR_INVALID_ARG;
   if (d_cams && !d_pos && T.n > 0) return GSC_ERR_INVALID_ARG;
   if (T.n_groups > 0 && (!d_blocks || !d_perm || !d_rgb)) return GSC_ERR_INVALID_ARG;
@@ -566,7 +566,7 @@ extern "C" gsc_status gsc_decode_eval_sh_slots(gsc_ctx* c, const gsc_stream_tabl
   DevTable T;
   gsc_status s = make_dev_table(table, &T);
   if (s != GSC_OK) return s;
-  if (V < 1 || V > 64 || out_order < 0 || out_order > 2) return GSC_ERR_INVALID_ARG;
+  if (V < 1 || V > 64 || out_order < 0 || out_order > 3) return GSC_ERR_INVALID_ARG;
   if ((d_dirs == nullptr) == (d_cams == nullptr)) return GSC_ERR_INVALID_ARG;
   if (d_cams && !d_pos_slot && T.n > 0) return GSC_ERR_INVALID_ARG;
   if (T.n_groups > 0 && (!d_blocks || !d_perm || !d_rgb)) return GSC_ERR_INVALID_ARG;

@@ -333,7 +333,7 @@ extern "C" gsc_status gsc_batch_eval_graph(gsc_ctx* c, const gsc_batch_scene* sc
                                            int32_t V, int32_t out_order, float* const* d_rgb, gsc_graph** out,
                                            void* stream) {
   GscRange gsc_range_("gsc_batch_eval_graph");
-  if (!c || !sc || n <= 0 || !out || !d_rgb || !d_cams || V < 1 || V > 64 || out_order < 0 || out_order > 2)
+  if (!c || !sc || n <= 0 || !out || !d_rgb || !d_cams || V < 1 || V > 64 || out_order < 0 || out_order > 3)
     return GSC_ERR_INVALID_ARG;
   *out = nullptr;
   std::vector<DevTable> T(n);

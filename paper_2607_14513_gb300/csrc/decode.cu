@@ -287,7 +287,9 @@ __global__ void __launch_bounds__(256) k_decode2(DevTable T, const uint8_t* __re
 // two-lane multiply-adds (one coefficient against the basis of two views), four views at a
 // time (three 16-byte stores of a Gaussian-major row when V is a multiple of 4).
 // VF > 0: a launch of exactly VF views into Gaussian-major rows, known at compile time.
-template <bool CAMS, int VF>
+// ORD: the output order known at compile time (GSC_OUT_SLOT_ROWS), or read at run time among
+// orders 0-2 (-1) or 0-3 (-3).
+template <bool CAMS, int VF, int ORD = -1>
 __device__ __forceinline__ void eval_store(const float (&xr)[16], const float (&xg)[16], const float (&xb)[16],
                                            int64_t o, int64_t s, float3 p, const float (*s_view)[64], int V_,
                                            int out_order_, int64_t n, int64_t ns, float* __restrict__ rgb) {
@@ -326,13 +328,30 @@ __device__ __forceinline__ void eval_store(const float (&xr)[16], const float (&
       res[6 * pr + 3] = ar.y; res[6 * pr + 4] = ag.y; res[6 * pr + 5] = ab.y;
     }
     const int nv = V - v0 < 4 ? V - v0 : 4;
-    if (out_order == GSC_OUT_GAUSS_MAJOR && (V & 3) == 0) {
+    if (ORD == GSC_OUT_SLOT_ROWS) {
+      if ((V & 3) == 0) {
+        float4* d = reinterpret_cast<float4*>(rgb + (s * V + v0) * 3);
+        d[0] = make_float4(res[0], res[1], res[2], res[3]);
+        d[1] = make_float4(res[4], res[5], res[6], res[7]);
+        d[2] = make_float4(res[8], res[9], res[10], res[11]);
+      } else {
+        float* d = rgb + (s * V + v0) * 3;
+#pragma unroll
+        for (int q = 0; q < 12; q++)
+          if (q < 3 * nv) d[q] = res[q];
+      }
+    } else if (out_order == GSC_OUT_GAUSS_MAJOR && (V & 3) == 0) {
       float4* d = reinterpret_cast<float4*>(rgb + (o * V + v0) * 3);
       d[0] = make_float4(res[0], res[1], res[2], res[3]);
       d[1] = make_float4(res[4], res[5], res[6], res[7]);
       d[2] = make_float4(res[8], res[9], res[10], res[11]);
     } else if (out_order == GSC_OUT_GAUSS_MAJOR) {
       float* d = rgb + (o * V + v0) * 3;
+#pragma unroll
+      for (int q = 0; q < 12; q++)
+        if (q < 3 * nv) d[q] = res[q];
+    } else if (ORD == -3 && out_order == GSC_OUT_SLOT_ROWS) {
+      float* d = rgb + (s * V + v0) * 3;
 #pragma unroll
       for (int q = 0; q < 12; q++)
         if (q < 3 * nv) d[q] = res[q];
@@ -368,7 +387,7 @@ __device__ __forceinline__ void load_views(float (*s_view)[64], float* s_deq, co
 #endif
 // LIST: only the groups listed in glist[0, n_list) (-1 entries skipped), e.g. those of the chunks a
 // view keeps.
-template <int KIND, bool CAMS, int VF, int LAYOUT, bool LIST>
+template <int KIND, bool CAMS, int VF, int LAYOUT, bool LIST, int ORD>
 __global__ void __launch_bounds__(EVAL_THREADS, EVAL_MIN_BLOCKS) k_eval2(DevTable T, const uint8_t* __restrict__ blocks,
                                                const int32_t* __restrict__ perm, const float* __restrict__ dirs,
                                                const float* __restrict__ pos, const float* __restrict__ cams, int V,
@@ -448,9 +467,11 @@ __global__ void __launch_bounds__(EVAL_THREADS, EVAL_MIN_BLOCKS) k_eval2(DevTabl
         const float2 b = __fmul2_rn(__fadd2_rn(make_float2(u23(p0, 2), u23(p1, 2)), m), f);
         xr[2 * j] = r.x; xr[2 * j + 1] = r.y; xg[2 * j] = gg.x; xg[2 * j + 1] = gg.y; xb[2 * j] = b.x; xb[2 * j + 1] = b.y;
       }
-      eval_store<CAMS, VF>(xr, xg, xb, o, s, p, s_view, V, out_order, n, ns, rgb);
+      eval_store<CAMS, VF, ORD>(xr, xg, xb, o, s, p, s_view, V, out_order, n, ns, rgb);
     } else if (live && out_order == GSC_OUT_SLOT_ORDER) {
       for (int v = 0; v < V; v++) { float* d = rgb + ((int64_t)v * ns + s) * 3; d[0] = d[1] = d[2] = 0.f; }
+    } else if (ORD == GSC_OUT_SLOT_ROWS && live) {
+      for (int q = 0; q < 3 * V; q++) rgb[s * V * 3 + q] = 0.f;
     }
     __syncwarp();
     raw = rawn;
@@ -503,6 +524,7 @@ cudaError_t launch_decode_eval(const DevTable& T, const uint8_t* blocks, const i
                                const float* pos, const float* cams, int V, int out_order, float* rgb, int sm_count,
                                cudaStream_t st, const int32_t* glist, int64_t n_list, const float* pos_slot) {
   if (T.n_groups == 0 || (glist && n_list == 0)) return cudaSuccess;
+  if (glist && out_order == GSC_OUT_SLOT_ROWS) return cudaErrorInvalidValue;  // group lists: orders 0-2
   const int grid = eval_grid(glist ? n_list : T.n_groups, sm_count, EVAL_THREADS / 32);
   const int kind = kind_of(T, blocks);
   // runtime view count only: a compile-time 8-view form raised this kernel to 140 registers (one
@@ -511,11 +533,14 @@ cudaError_t launch_decode_eval(const DevTable& T, const uint8_t* blocks, const i
   do {                                                                                                           \
     gsc_count_launch();                                                                                          \
     if (glist)                                                                                                   \
-      k_eval2<K, C, 0, L, true><<<grid, EVAL_THREADS, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order,   \
-                                                               rgb, glist, n_list, pos_slot);                    \
+      k_eval2<K, C, 0, L, true, -1><<<grid, EVAL_THREADS, 0, st>>>(T, blocks, perm, dirs, pos, cams, V,          \
+                                                                   out_order, rgb, glist, n_list, pos_slot);     \
+    else if (out_order == GSC_OUT_SLOT_ROWS)                                                                     \
+      k_eval2<K, C, 0, L, false, GSC_OUT_SLOT_ROWS><<<grid, EVAL_THREADS, 0, st>>>(                            \
+          T, blocks, perm, dirs, pos, cams, V, out_order, rgb, nullptr, 0, pos_slot);                            \
     else                                                                                                         \
-      k_eval2<K, C, 0, L, false><<<grid, EVAL_THREADS, 0, st>>>(T, blocks, perm, dirs, pos, cams, V, out_order,  \
-                                                                rgb, nullptr, 0, pos_slot);                      \
+      k_eval2<K, C, 0, L, false, -1><<<grid, EVAL_THREADS, 0, st>>>(T, blocks, perm, dirs, pos, cams, V,         \
+                                                                    out_order, rgb, nullptr, 0, pos_slot);       \
   } while (0)
 #define EVAL_KINDS(C, L)                                                                                         \
   do {                                                                                                           \
@@ -867,6 +892,8 @@ __global__ void __launch_bounds__(256) k_eval_tex(DevTable T, TexBases B, cudaTe
     if (o < 0) {
       if (out_order == GSC_OUT_SLOT_ORDER)
         for (int v = 0; v < V; v++) { float* d = rgb + ((int64_t)v * ns + s) * 3; d[0] = d[1] = d[2] = 0.f; }
+      else if (out_order == GSC_OUT_SLOT_ROWS)
+        for (int q = 0; q < 3 * V; q++) rgb[s * V * 3 + q] = 0.f;
       continue;
     }
     const int64_t g = s >> 4;
@@ -897,7 +924,7 @@ __global__ void __launch_bounds__(256) k_eval_tex(DevTable T, TexBases B, cudaTe
       const float q = s_deq[k];
       xr[k] = __fmul_rn(unorm_m128(f.x), q); xg[k] = __fmul_rn(unorm_m128(f.y), q); xb[k] = __fmul_rn(unorm_m128(f.z), q);
     }
-    eval_store<CAMS, VF>(xr, xg, xb, o, s, p, s_view, V, out_order, n, ns, rgb);
+    eval_store<CAMS, VF, -3>(xr, xg, xb, o, s, p, s_view, V, out_order, n, ns, rgb);
   }
 }
 
@@ -976,7 +1003,7 @@ extern "C" gsc_status gsc_decode_eval_sh_tex(gsc_ctx* c, const gsc_tex_scene* sc
   GscRange gsc_range_("gsc_decode_eval_sh_tex");
   if (!c || !sc || sc->device != c->device) return GSC_ERR_INVALID_ARG;
   const DevTable& T = sc->T;
-  if (V < 1 || V > 64 || out_order < 0 || out_order > 2) return GSC_ERR_INVALID_ARG;
+  if (V < 1 || V > 64 || out_order < 0 || out_order > 3) return GSC_ERR_INVALID_ARG;
   if ((d_dirs == nullptr) == (d_cams == nullptr)) return GSC_ERR_INVALID_ARG;
   if (d_cams && !d_pos && !sc->pos_slot && T.n > 0) return GSC_ERR_INVALID_ARG;
   if (T.n_groups > 0 && (!d_perm || !d_rgb)) return GSC_ERR_INVALID_ARG;

@@ -21,7 +21,7 @@ STATUS = {0: "GSC_OK", 1: "GSC_ERR_INVALID_ARG", 2: "GSC_ERR_CUDA", 3: "GSC_ERR_
           5: "GSC_ERR_TIMEOUT", 6: "GSC_ERR_UNSUPPORTED", 7: "GSC_ERR_DEVICE", 8: "GSC_ERR_CANCELLED"}
 FMT_RATE, FMT_BC1, FMT_MIXED, FMT_BC7 = 0, 1, 2, 7
 LAYOUT_D, LAYOUT_A, LAYOUT_B = 0, 1, 2
-OUT_VIEW_MAJOR, OUT_SLOT_ORDER, OUT_GAUSS_MAJOR = 0, 1, 2
+OUT_VIEW_MAJOR, OUT_SLOT_ORDER, OUT_GAUSS_MAJOR, OUT_SLOT_ROWS = 0, 1, 2, 3
 
 
 class GscError(RuntimeError):
@@ -403,7 +403,8 @@ def gsc_decode_eval_sh(ctx, table, blocks, perm, dirs=None, pos=None, cams=None,
     src = dirs if dirs is not None else cams
     V = src.shape[0]
     n, ns = table.n, table.n_groups * 16
-    shape = {OUT_VIEW_MAJOR: (V, n, 3), OUT_SLOT_ORDER: (V, ns, 3), OUT_GAUSS_MAJOR: (n, V, 3)}[out_order]
+    shape = {OUT_VIEW_MAJOR: (V, n, 3), OUT_SLOT_ORDER: (V, ns, 3), OUT_GAUSS_MAJOR: (n, V, 3),
+             OUT_SLOT_ROWS: (ns, V, 3)}[out_order]
     rgb = out if out is not None else torch.empty(shape, dtype=torch.float32, device=blocks.device)
     _check(ctx.lib.gsc_decode_eval_sh(ctx.h, C.byref(table), _ptr(blocks), _ptr(perm), _ptr(dirs), _ptr(pos),
                                       _ptr(cams), V, out_order, _ptr(rgb), _stream(stream)), "gsc_decode_eval_sh")
@@ -417,7 +418,8 @@ def gsc_decode_eval_sh_slots(ctx, table, blocks, perm, dirs=None, pos_slot=None,
     src = dirs if dirs is not None else cams
     V = src.shape[0]
     n, ns = table.n, table.n_groups * 16
-    shape = {OUT_VIEW_MAJOR: (V, n, 3), OUT_SLOT_ORDER: (V, ns, 3), OUT_GAUSS_MAJOR: (n, V, 3)}[out_order]
+    shape = {OUT_VIEW_MAJOR: (V, n, 3), OUT_SLOT_ORDER: (V, ns, 3), OUT_GAUSS_MAJOR: (n, V, 3),
+             OUT_SLOT_ROWS: (ns, V, 3)}[out_order]
     rgb = out if out is not None else torch.empty(shape, dtype=torch.float32, device=blocks.device)
     _check(ctx.lib.gsc_decode_eval_sh_slots(ctx.h, C.byref(table), _ptr(blocks), _ptr(perm), _ptr(dirs),
                                             _ptr(pos_slot), _ptr(cams), V, out_order, _ptr(rgb), _stream(stream)),
@@ -473,7 +475,8 @@ def gsc_decode_eval_sh_tex(ctx, scene, perm, dirs=None, pos=None, cams=None, out
     V = src.shape[0]
     table = scene.table
     n, ns = table.n, table.n_groups * 16
-    shape = {OUT_VIEW_MAJOR: (V, n, 3), OUT_SLOT_ORDER: (V, ns, 3), OUT_GAUSS_MAJOR: (n, V, 3)}[out_order]
+    shape = {OUT_VIEW_MAJOR: (V, n, 3), OUT_SLOT_ORDER: (V, ns, 3), OUT_GAUSS_MAJOR: (n, V, 3),
+             OUT_SLOT_ROWS: (ns, V, 3)}[out_order]
     rgb = out if out is not None else torch.empty(shape, dtype=torch.float32, device=perm.device)
     _check(ctx.lib.gsc_decode_eval_sh_tex(ctx.h, scene.h, _ptr(perm), _ptr(dirs), _ptr(pos), _ptr(cams), V,
                                           out_order, _ptr(rgb), _stream(stream)), "gsc_decode_eval_sh_tex")

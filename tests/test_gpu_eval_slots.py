@@ -46,7 +46,9 @@ def _view_major(got, order, perm, n):
     g = got.cpu().numpy().astype(np.float64)
     if order == 2:
         return g.transpose(1, 0, 2)
-    if order == 1:
+    if order == 3:                     # slot-order rows [ns][V][3] -> view-major slot order
+        g = g.transpose(1, 0, 2)
+    if order in (1, 3):
         pp = perm.cpu().numpy()
         valid = pp >= 0
         assert np.all(g[:, ~valid] == 0.0)
@@ -83,7 +85,7 @@ def test_eval_matches_oracle_and_texture_unit(ctx, O, n):
         pslot = gsc.gsc_positions_to_slots(ctx, dpos, po)
         scene = gsc.TexScene(ctx, tab, blk, perm=po, pos=dpos)
         try:
-            for order in (gsc.OUT_VIEW_MAJOR, gsc.OUT_GAUSS_MAJOR, gsc.OUT_SLOT_ORDER):
+            for order in (gsc.OUT_VIEW_MAJOR, gsc.OUT_GAUSS_MAJOR, gsc.OUT_SLOT_ORDER, gsc.OUT_SLOT_ROWS):
                 a = gsc.gsc_decode_eval_sh(ctx, tab, blk, po, pos=dpos, cams=dc, out_order=order)
                 b = gsc.gsc_decode_eval_sh_slots(ctx, tab, blk, po, pos_slot=pslot, cams=dc, out_order=order)
                 c = gsc.gsc_decode_eval_sh_tex(ctx, scene, po, cams=dc, out_order=order)
@@ -160,7 +162,7 @@ def test_shared_directions_and_view_counts(ctx, O, V):
             kw = dict(dirs=dd) if kind == "dirs" else dict(cams=dc, pos=dpos)
             okw = dict(dirs=dirs) if kind == "dirs" else dict(cams=cams, pos=pos)
             want, ab = O.eval_sh(tex, osc, want_abs=True, **okw)
-            for order in (gsc.OUT_GAUSS_MAJOR, gsc.OUT_SLOT_ORDER):
+            for order in (gsc.OUT_GAUSS_MAJOR, gsc.OUT_SLOT_ORDER, gsc.OUT_SLOT_ROWS):
                 a = gsc.gsc_decode_eval_sh(ctx, tab, blk, po, out_order=order, **kw)
                 ctx.sync()
                 got = _view_major(a, order, po, n)
