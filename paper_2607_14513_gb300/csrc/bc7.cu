@@ -171,12 +171,14 @@ __device__ __forceinline__ uint32_t member_mask(uint32_t part, int s) {
 }
 
 // Stage 1 of a subset fit: bounding-box diagonal oriented by covariance signs, indices
-// against the unquantised palette, one least-squares refinement. Returns the member count.
+// against the unquantised palette, one least-squares refinement. Returns the member count;
+// sumsq gets the members' summed squared norms over the coded channels (the part of every
+// palette error that does not depend on the palette).
 // `sel` permutes each texel's bytes on load (identity by default); the rotation search uses it
 // to move the rotated channel to byte 2, keeping the other two in their order.
 template <int IB, int CHMASK>
 __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t part, int s, int (&e0)[3], int (&e1)[3],
-                                      uint32_t sel = 0x3210u) {
+                                      int& sumsq, uint32_t sel = 0x3210u) {
   constexpr int F = 1 << IB;
   constexpr int NCH = ((CHMASK >> 0) & 1) + ((CHMASK >> 1) & 1) + ((CHMASK >> 2) & 1);
   constexpr uint32_t CM = ((CHMASK & 1) ? 0xFFu : 0u) | ((CHMASK & 2) ? 0xFF00u : 0u) | ((CHMASK & 4) ? 0xFF0000u : 0u);
@@ -186,7 +188,7 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
 #pragma unroll
     for (int c = 0; c < 3; c++) if ((CHMASK >> c) & 1) ch[k++] = c;
   }
-  int n = 0, lo[NCH], hi[NCH], s1[NCH], s2[3];
+  int n = 0, sq2 = 0, lo[NCH], hi[NCH], s1[NCH], s2[3];
 #pragma unroll
   for (int i = 0; i < NCH; i++) { lo[i] = 255; hi[i] = 0; s1[i] = 0; }
   s2[0] = s2[1] = s2[2] = 0;  // channel pairs (0,1), (0,2), (1,2) of the coded channels
@@ -195,6 +197,7 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
   const uint32_t mm = member_mask(part, s);
   auto box = [&](uint32_t v) {
     n++;
+    sq2 += (int)__dp4a(v & CM, v & CM, 0u);
     int c[NCH];
 #pragma unroll
     for (int i = 0; i < NCH; i++) {
@@ -218,6 +221,7 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
       box(va);
     }
   }
+  sumsq = sq2;
   if (n == 0) return 0;
   // reference channel = widest range (first on ties); selects, not indexing, keep the
   // per-channel sums in registers
@@ -287,7 +291,7 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
 // combination (first on ties) scores the subset.
 template <int IB, int CHMASK, int PT, int BITS, bool OUT>
 __device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex, uint32_t part, int s,
-                                               const int (&e0)[3], const int (&e1)[3], FitOut* out,
+                                               const int (&e0)[3], const int (&e1)[3], int sumsq, FitOut* out,
                                                const uint16_t* __restrict__ sq, uint32_t sel = 0x3210u) {
   constexpr int F = 1 << IB;
   constexpr int NCH = ((CHMASK >> 0) & 1) + ((CHMASK >> 1) & 1) + ((CHMASK >> 2) & 1);
@@ -317,14 +321,14 @@ __device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex,
     uint32_t pal[F];
     int pk[F];
     build_pal<IB>(v0, v1, pal, pk);  // uncoded channels have zero endpoints, so their bytes are 0
-    int sse = 0;
+    int sse = sumsq;
     uint32_t il = 0, ih = 0;
     if (OUT) {
       for (uint32_t m = member_mask(part, s); m; m &= m - 1) {
         const int t = (__ffs(m) - 1) >> 1;
         const uint32_t v = __byte_perm(tex[t * STAGE_STRIDE], 0u, sel) & CM;
         const int key = best_key<F>(v, pal, pk);
-        sse += (int)__dp4a(v, v, 0u) + (key >> 4);
+        sse += key >> 4;
         if (t < 8) il |= (uint32_t)(key & 15) << (4 * t); else ih |= (uint32_t)(key & 15) << (4 * (t - 8));
       }
     } else {
@@ -340,10 +344,10 @@ __device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex,
           m &= m - 1;
           const uint32_t vb = __byte_perm(tex[tb * STAGE_STRIDE], 0u, sel) & CM;
           const int ka = best_key<F>(va, pal, pk), kb = best_key<F>(vb, pal, pk);
-          sse += ((int)__dp4a(va, va, 0u) + (ka >> 4)) + ((int)__dp4a(vb, vb, 0u) + (kb >> 4));
+          sse += (ka >> 4) + (kb >> 4);
         } else {
           const int ka = best_key<F>(va, pal, pk);
-          sse += (int)__dp4a(va, va, 0u) + (ka >> 4);
+          sse += ka >> 4;
         }
       }
     }
@@ -367,8 +371,9 @@ __device__ __forceinline__ uint32_t fit_subset(const uint32_t* __restrict__ tex,
 #pragma unroll
     for (int i = 0; i < 3; i++) out->code[0][i] = out->code[1][i] = 0; }
   int e0[3] = {0, 0, 0}, e1[3] = {0, 0, 0};
-  if (prefit<IB, CHMASK>(tex, part, s, e0, e1, sel) == 0) return 0;
-  return quant_eval<IB, CHMASK, PT, BITS, OUT>(tex, part, s, e0, e1, out, sq, sel);
+  int sumsq = 0;
+  if (prefit<IB, CHMASK>(tex, part, s, e0, e1, sumsq, sel) == 0) return 0;
+  return quant_eval<IB, CHMASK, PT, BITS, OUT>(tex, part, s, e0, e1, sumsq, out, sq, sel);
 }
 
 // ---- candidate scoring (search phase) ----------------------------------------------
@@ -467,9 +472,10 @@ __device__ __noinline__ int search_best(const uint32_t* tex, uint32_t* best_sse,
 #pragma unroll 1
     for (int sub = 0; sub < 2; sub++) {
       int e0[3] = {0, 0, 0}, e1[3] = {0, 0, 0};
-      if (prefit<2, 7>(tex, part, sub, e0, e1) == 0) continue;
-      s3 += quant_eval<2, 7, PT_UNIQUE, 7, false>(tex, part, sub, e0, e1, nullptr, sq);
-      s7 += quant_eval<2, 7, PT_UNIQUE, 5, false>(tex, part, sub, e0, e1, nullptr, sq);
+      int sumsq = 0;
+      if (prefit<2, 7>(tex, part, sub, e0, e1, sumsq) == 0) continue;
+      s3 += quant_eval<2, 7, PT_UNIQUE, 7, false>(tex, part, sub, e0, e1, sumsq, nullptr, sq);
+      s7 += quant_eval<2, 7, PT_UNIQUE, 5, false>(tex, part, sub, e0, e1, sumsq, nullptr, sq);
     }
     CAND(s3, 144 + p);
     CAND(s7, 221 + p);
