@@ -31,6 +31,10 @@ __constant__ uint16_t c_const7[256];
 // sets in enumeration order, | 0x100 where that set occurs first (its fit is computed there)
 #define BC7_SUB3_SETS 140
 __constant__ uint16_t c_sub3[64 * 3];
+// member texels of each subset of the two- and three-subset partitions: texel indices in
+// increasing order, four bits each from bit 0, and the member count in bits 60-63
+__constant__ uint64_t c_mem2[64][2];
+__constant__ uint64_t c_mem3[64][3];
 cudaError_t bc7_kernel_attributes();
 
 static int h_expand(int v, int n) { return n >= 8 ? v : ((v << (8 - n)) | (v >> (2 * n - 8))); }
@@ -91,7 +95,22 @@ cudaError_t bc7_init_tables() {
         sub3[3 * pp + sb] = (uint16_t)id;
       }
     }
+  uint64_t mem2[64][2], mem3[64][3];
+  for (int pp = 0; pp < 64; pp++)
+    for (int ns = 2; ns <= 3; ns++)
+      for (int sb = 0; sb < ns; sb++) {
+        const uint32_t part = ns == 2 ? p2[pp] : p3[pp];
+        uint64_t list = 0;
+        int cnt = 0;
+        for (int t = 0; t < 16; t++)
+          if (((part >> (2 * t)) & 3u) == (uint32_t)sb) list |= (uint64_t)t << (4 * cnt++);
+        if (cnt > 15) return cudaErrorInvalidValue;
+        list |= (uint64_t)cnt << 60;
+        if (ns == 2) mem2[pp][sb] = list; else mem3[pp][sb] = list;
+      }
   cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(c_mem2, mem2, sizeof(mem2))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_mem3, mem3, sizeof(mem3))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_sub3, sub3, sizeof(sub3))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_const7, c7, sizeof(c7))) != cudaSuccess) return e;
   uint16_t t5[256], t6[256];
@@ -164,10 +183,17 @@ __device__ __forceinline__ int best_key(uint32_t v, const uint32_t (&pal)[F], co
   return k[0];
 }
 
-// Bit 2t set for every texel t of subset s of a partition (2 bits per texel).
-__device__ __forceinline__ uint32_t member_mask(uint32_t part, int s) {
-  const uint32_t x = part ^ ((uint32_t)s * 0x55555555u);
-  return ~(x | (x >> 1)) & 0x55555555u;
+// The member texels of one subset: indices four bits each from bit 0, increasing, and their
+// count (the same for every lane of a warp).
+struct Mem {
+  uint64_t list;
+  int n;
+};
+__device__ __forceinline__ Mem mem_all() { return {0xFEDCBA9876543210ull, 16}; }
+__device__ __forceinline__ Mem mem_of(int ns, int p, int s) {
+  if (ns == 1) return mem_all();
+  const uint64_t v = ns == 2 ? c_mem2[p][s] : c_mem3[p][s];
+  return {v, (int)(v >> 60)};
 }
 
 // Stage 1 of a subset fit: bounding-box diagonal oriented by covariance signs, indices
@@ -177,7 +203,7 @@ __device__ __forceinline__ uint32_t member_mask(uint32_t part, int s) {
 // `sel` permutes each texel's bytes on load (identity by default); the rotation search uses it
 // to move the rotated channel to byte 2, keeping the other two in their order.
 template <int IB, int CHMASK>
-__device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t part, int s, int (&e0)[3], int (&e1)[3],
+__device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, Mem M, int (&e0)[3], int (&e1)[3],
                                       int& sumsq, uint32_t sel = 0x3210u) {
   constexpr int F = 1 << IB;
   constexpr int NCH = ((CHMASK >> 0) & 1) + ((CHMASK >> 1) & 1) + ((CHMASK >> 2) & 1);
@@ -192,9 +218,8 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
 #pragma unroll
   for (int i = 0; i < NCH; i++) { lo[i] = 255; hi[i] = 0; s1[i] = 0; }
   s2[0] = s2[1] = s2[2] = 0;  // channel pairs (0,1), (0,2), (1,2) of the coded channels
-  // member texels only (the mask is the same for every lane); box and sums are order-free, so
+  // member texels only (the list is the same for every lane); box and sums are order-free, so
   // two texels per step: both shared-memory reads are in flight together
-  const uint32_t mm = member_mask(part, s);
   auto box = [&](uint32_t v) {
     n++;
     sq2 += (int)__dp4a(v & CM, v & CM, 0u);
@@ -207,19 +232,17 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
     if (NCH >= 2) s2[0] += c[0] * c[NCH >= 2 ? 1 : 0];
     if (NCH >= 3) { s2[1] += c[0] * c[NCH >= 3 ? 2 : 0]; s2[2] += c[NCH >= 2 ? 1 : 0] * c[NCH >= 3 ? 2 : 0]; }
   };
-  for (uint32_t m = mm; m;) {
-    const int ta = (__ffs(m) - 1) >> 1;
-    m &= m - 1;
-    const uint32_t va = __byte_perm(tex[ta * STAGE_STRIDE], 0u, sel);
-    if (m) {
-      const int tb = (__ffs(m) - 1) >> 1;
-      m &= m - 1;
+  {
+    uint64_t L = M.list;
+    for (int i = 1; i < M.n; i += 2) {
+      const int ta = (int)(L & 15), tb = (int)((L >> 4) & 15);
+      L >>= 8;
+      const uint32_t va = __byte_perm(tex[ta * STAGE_STRIDE], 0u, sel);
       const uint32_t vb = __byte_perm(tex[tb * STAGE_STRIDE], 0u, sel);
       box(va);
       box(vb);
-    } else {
-      box(va);
     }
+    if (M.n & 1) box(__byte_perm(tex[(int)(L & 15) * STAGE_STRIDE], 0u, sel));
   }
   sumsq = sq2;
   if (n == 0) return 0;
@@ -259,21 +282,19 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
       for (int i = 0; i < NCH; i++) { const int c = (v >> (8 * ch[i])) & 255; sav[i] += a * c; sbv[i] += w * c; }
     };
     // two member texels per step (independent palette searches; integer sums, order-free)
-    uint32_t m = mm;
-    while (m) {
-      const int ta = (__ffs(m) - 1) >> 1;
-      m &= m - 1;
+    uint64_t L = M.list;
+    for (int i = 1; i < M.n; i += 2) {
+      const int ta = (int)(L & 15), tb = (int)((L >> 4) & 15);
+      L >>= 8;
       const uint32_t va = __byte_perm(tex[ta * STAGE_STRIDE], 0u, sel) & CM;
-      if (m) {
-        const int tb = (__ffs(m) - 1) >> 1;
-        m &= m - 1;
-        const uint32_t vb = __byte_perm(tex[tb * STAGE_STRIDE], 0u, sel) & CM;
-        const int ka = best_key<F>(va, pal, pk), kb = best_key<F>(vb, pal, pk);
-        accumulate(va, ka);
-        accumulate(vb, kb);
-      } else {
-        accumulate(va, best_key<F>(va, pal, pk));
-      }
+      const uint32_t vb = __byte_perm(tex[tb * STAGE_STRIDE], 0u, sel) & CM;
+      const int ka = best_key<F>(va, pal, pk), kb = best_key<F>(vb, pal, pk);
+      accumulate(va, ka);
+      accumulate(vb, kb);
+    }
+    if (M.n & 1) {
+      const uint32_t va = __byte_perm(tex[(int)(L & 15) * STAGE_STRIDE], 0u, sel) & CM;
+      accumulate(va, best_key<F>(va, pal, pk));
     }
   }
   const long long det = (long long)saa * sbb - (long long)sab * sab;
@@ -290,7 +311,7 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, uint32_t
 // Stage 2: every p-bit combination quantised to the nearest codes and re-indexed; the best
 // combination (first on ties) scores the subset.
 template <int IB, int CHMASK, int PT, int BITS, bool OUT>
-__device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex, uint32_t part, int s,
+__device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex, Mem M,
                                                const int (&e0)[3], const int (&e1)[3], int sumsq, FitOut* out,
                                                const uint16_t* __restrict__ sq, uint32_t sel = 0x3210u) {
   constexpr int F = 1 << IB;
@@ -324,8 +345,9 @@ __device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex,
     int sse = sumsq;
     uint32_t il = 0, ih = 0;
     if (OUT) {
-      for (uint32_t m = member_mask(part, s); m; m &= m - 1) {
-        const int t = (__ffs(m) - 1) >> 1;
+      uint64_t L = M.list;
+      for (int i = 0; i < M.n; i++, L >>= 4) {
+        const int t = (int)(L & 15);
         const uint32_t v = __byte_perm(tex[t * STAGE_STRIDE], 0u, sel) & CM;
         const int key = best_key<F>(v, pal, pk);
         sse += key >> 4;
@@ -334,21 +356,18 @@ __device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex,
     } else {
       // two member texels per step: their palette searches are independent chains (the error is
       // an integer sum, so the order of the additions does not matter)
-      uint32_t m = member_mask(part, s);
-      while (m) {
-        const int ta = (__ffs(m) - 1) >> 1;
-        m &= m - 1;
+      uint64_t L = M.list;
+      for (int i = 1; i < M.n; i += 2) {
+        const int ta = (int)(L & 15), tb = (int)((L >> 4) & 15);
+        L >>= 8;
         const uint32_t va = __byte_perm(tex[ta * STAGE_STRIDE], 0u, sel) & CM;
-        if (m) {
-          const int tb = (__ffs(m) - 1) >> 1;
-          m &= m - 1;
-          const uint32_t vb = __byte_perm(tex[tb * STAGE_STRIDE], 0u, sel) & CM;
-          const int ka = best_key<F>(va, pal, pk), kb = best_key<F>(vb, pal, pk);
-          sse += (ka >> 4) + (kb >> 4);
-        } else {
-          const int ka = best_key<F>(va, pal, pk);
-          sse += ka >> 4;
-        }
+        const uint32_t vb = __byte_perm(tex[tb * STAGE_STRIDE], 0u, sel) & CM;
+        const int ka = best_key<F>(va, pal, pk), kb = best_key<F>(vb, pal, pk);
+        sse += (ka >> 4) + (kb >> 4);
+      }
+      if (M.n & 1) {
+        const uint32_t va = __byte_perm(tex[(int)(L & 15) * STAGE_STRIDE], 0u, sel) & CM;
+        sse += best_key<F>(va, pal, pk) >> 4;
       }
     }
     if ((uint32_t)sse < best_sse) {
@@ -365,25 +384,25 @@ __device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex,
 
 // Full subset fit = prefit + quant_eval.
 template <int IB, int CHMASK, int PT, int BITS, bool OUT>
-__device__ __forceinline__ uint32_t fit_subset(const uint32_t* __restrict__ tex, uint32_t part, int s, FitOut* out,
+__device__ __forceinline__ uint32_t fit_subset(const uint32_t* __restrict__ tex, Mem M, FitOut* out,
                                                const uint16_t* __restrict__ sq, uint32_t sel = 0x3210u) {
   if (OUT) { out->idx_lo = 0; out->idx_hi = 0; out->p[0] = out->p[1] = 0;
 #pragma unroll
     for (int i = 0; i < 3; i++) out->code[0][i] = out->code[1][i] = 0; }
   int e0[3] = {0, 0, 0}, e1[3] = {0, 0, 0};
   int sumsq = 0;
-  if (prefit<IB, CHMASK>(tex, part, s, e0, e1, sumsq, sel) == 0) return 0;
-  return quant_eval<IB, CHMASK, PT, BITS, OUT>(tex, part, s, e0, e1, sumsq, out, sq, sel);
+  if (prefit<IB, CHMASK>(tex, M, e0, e1, sumsq, sel) == 0) return 0;
+  return quant_eval<IB, CHMASK, PT, BITS, OUT>(tex, M, e0, e1, sumsq, out, sq, sel);
 }
 
 // ---- candidate scoring (search phase) ----------------------------------------------
 // Subsets in a rolled loop: one copy of the fit code per mode keeps the search's instruction
 // footprint small (warps at different candidates share the instruction cache).
 template <int NS, int IB, int PT, int BITS>
-__device__ __forceinline__ uint32_t score_part(const uint32_t* tex, uint32_t part, const uint16_t* sq) {
+__device__ __forceinline__ uint32_t score_part(const uint32_t* tex, int p, const uint16_t* sq) {
   uint32_t s = 0;
 #pragma unroll 1
-  for (int sub = 0; sub < NS; sub++) s += fit_subset<IB, 7, PT, BITS, false>(tex, part, sub, nullptr, sq);
+  for (int sub = 0; sub < NS; sub++) s += fit_subset<IB, 7, PT, BITS, false>(tex, mem_of(NS, p, sub), nullptr, sq);
   return s;
 }
 
@@ -392,14 +411,13 @@ __device__ __forceinline__ uint32_t score_part(const uint32_t* tex, uint32_t par
 // every lane). Mode 0 meets 36 distinct sets in its 48 subsets, mode 2 140 in 192.
 template <int IB, int PT, int BITS>
 __device__ __forceinline__ uint32_t score_part3(const uint32_t* tex, int p, const uint16_t* sq, uint32_t* cache) {
-  const uint32_t part = c_part3[p];
   uint32_t s = 0;
 #pragma unroll 1
   for (int sub = 0; sub < 3; sub++) {
     const uint32_t e = c_sub3[3 * p + sub];
     uint32_t r;
     if (e & 0x100u) {
-      r = fit_subset<IB, 7, PT, BITS, false>(tex, part, sub, nullptr, sq);
+      r = fit_subset<IB, 7, PT, BITS, false>(tex, mem_of(3, p, sub), nullptr, sq);
       cache[e & 0xFFu] = r;
     } else {
       r = cache[e & 0xFFu];
@@ -417,12 +435,12 @@ __device__ __forceinline__ uint32_t score_rot(const uint32_t* tex, FitOut* oc, F
   constexpr int CM = ROT == 0 ? 7 : (7 & ~(1 << (ROT - 1)));
   const bool out = oc != nullptr;
   uint32_t s;
-  if (out) s = fit_subset<CIB, CM, PT_NONE, CB, true>(tex, 0u, 0, oc, sq);
-  else s = fit_subset<CIB, CM, PT_NONE, CB, false>(tex, 0u, 0, nullptr, sq);
+  if (out) s = fit_subset<CIB, CM, PT_NONE, CB, true>(tex, mem_all(), oc, sq);
+  else s = fit_subset<CIB, CM, PT_NONE, CB, false>(tex, mem_all(), nullptr, sq);
   if constexpr (ROT != 0) {
     constexpr int AM = 1 << (ROT > 0 ? ROT - 1 : 0);
-    if (out) s += fit_subset<AIB, AM, PT_NONE, AB, true>(tex, 0u, 0, oa, sq);
-    else s += fit_subset<AIB, AM, PT_NONE, AB, false>(tex, 0u, 0, nullptr, sq);
+    if (out) s += fit_subset<AIB, AM, PT_NONE, AB, true>(tex, mem_all(), oa, sq);
+    else s += fit_subset<AIB, AM, PT_NONE, AB, false>(tex, mem_all(), nullptr, sq);
   }
   return s;
 }
@@ -435,8 +453,8 @@ template <int MODE, int ISB>
 __device__ __forceinline__ uint32_t score_rot_n(const uint32_t* tex, uint32_t sel, const uint16_t* sq) {
   constexpr int CB = MODE == 4 ? 5 : 7, AB = MODE == 4 ? 6 : 8;
   constexpr int CIB = MODE == 4 ? (ISB ? 3 : 2) : 2, AIB = MODE == 4 ? (ISB ? 2 : 3) : 2;
-  return fit_subset<CIB, 3, PT_NONE, CB, false>(tex, 0u, 0, nullptr, sq, sel) +
-         fit_subset<AIB, 4, PT_NONE, AB, false>(tex, 0u, 0, nullptr, sq, sel);
+  return fit_subset<CIB, 3, PT_NONE, CB, false>(tex, mem_all(), nullptr, sq, sel) +
+         fit_subset<AIB, 4, PT_NONE, AB, false>(tex, mem_all(), nullptr, sq, sel);
 }
 
 __device__ __forceinline__ uint32_t rot_sel(int rot) {
@@ -461,21 +479,21 @@ __device__ __noinline__ int search_best(const uint32_t* tex, uint32_t* best_sse,
   uint32_t cache[BC7_SUB3_SETS];
   for (int p = 0; p < 16; p++) CAND((score_part3<3, PT_UNIQUE, 4>(tex, p, sq, cache)), p);
   if (SYNC) __syncthreads();
-  for (int p = 0; p < 64; p++) CAND((score_part<2, 3, PT_SHARED, 6>(tex, c_part2[p], sq)), 16 + p);
+  for (int p = 0; p < 64; p++) CAND((score_part<2, 3, PT_SHARED, 6>(tex, p, sq)), 16 + p);
   if (SYNC) __syncthreads();
   for (int p = 0; p < 64; p++) CAND((score_part3<2, PT_NONE, 5>(tex, p, sq, cache)), 80 + p);
   if (SYNC) __syncthreads();
   // modes 3 and 7: same partitions and 2-bit weights, so one prefit per subset serves both
   for (int p = 0; p < 64; p++) {
-    const uint32_t part = c_part2[p];
     uint32_t s3 = 0, s7 = 0;
 #pragma unroll 1
     for (int sub = 0; sub < 2; sub++) {
       int e0[3] = {0, 0, 0}, e1[3] = {0, 0, 0};
       int sumsq = 0;
-      if (prefit<2, 7>(tex, part, sub, e0, e1, sumsq) == 0) continue;
-      s3 += quant_eval<2, 7, PT_UNIQUE, 7, false>(tex, part, sub, e0, e1, sumsq, nullptr, sq);
-      s7 += quant_eval<2, 7, PT_UNIQUE, 5, false>(tex, part, sub, e0, e1, sumsq, nullptr, sq);
+      const Mem M = mem_of(2, p, sub);
+      if (prefit<2, 7>(tex, M, e0, e1, sumsq) == 0) continue;
+      s3 += quant_eval<2, 7, PT_UNIQUE, 7, false>(tex, M, e0, e1, sumsq, nullptr, sq);
+      s7 += quant_eval<2, 7, PT_UNIQUE, 5, false>(tex, M, e0, e1, sumsq, nullptr, sq);
     }
     CAND(s3, 144 + p);
     CAND(s7, 221 + p);
@@ -491,7 +509,7 @@ __device__ __noinline__ int search_best(const uint32_t* tex, uint32_t* best_sse,
     CAND((score_rot_n<4, 1>(tex, sel, sq)), 209 + 2 * rot);
     CAND((score_rot_n<5, 0>(tex, sel, sq)), 216 + rot);
   }
-  CAND((score_part<1, 4, PT_UNIQUE, 7>(tex, 0u, sq)), 220);
+  CAND((score_part<1, 4, PT_UNIQUE, 7>(tex, 0, sq)), 220);
 #undef CAND
   *best_sse = best;
   return be;
@@ -549,12 +567,12 @@ __device__ __noinline__ uint4 solve_pack(const uint32_t* tx, int e, const uint16
   int acode[3][2];
   for (int s = 0; s < 3; s++) acode[s][0] = acode[s][1] = (1 << M.ab) - 1;
   switch (mode) {
-    case 0: for (int s = 0; s < 3; s++) fit_subset<3, 7, PT_UNIQUE, 4, true>(tx, pm, s, &f[s], sq); break;
-    case 1: for (int s = 0; s < 2; s++) fit_subset<3, 7, PT_SHARED, 6, true>(tx, pm, s, &f[s], sq); break;
-    case 2: for (int s = 0; s < 3; s++) fit_subset<2, 7, PT_NONE, 5, true>(tx, pm, s, &f[s], sq); break;
-    case 3: for (int s = 0; s < 2; s++) fit_subset<2, 7, PT_UNIQUE, 7, true>(tx, pm, s, &f[s], sq); break;
-    case 6: fit_subset<4, 7, PT_UNIQUE, 7, true>(tx, 0u, 0, &f[0], sq); break;
-    case 7: for (int s = 0; s < 2; s++) fit_subset<2, 7, PT_UNIQUE, 5, true>(tx, pm, s, &f[s], sq); break;
+    case 0: for (int s = 0; s < 3; s++) fit_subset<3, 7, PT_UNIQUE, 4, true>(tx, mem_of(3, part, s), &f[s], sq); break;
+    case 1: for (int s = 0; s < 2; s++) fit_subset<3, 7, PT_SHARED, 6, true>(tx, mem_of(2, part, s), &f[s], sq); break;
+    case 2: for (int s = 0; s < 3; s++) fit_subset<2, 7, PT_NONE, 5, true>(tx, mem_of(3, part, s), &f[s], sq); break;
+    case 3: for (int s = 0; s < 2; s++) fit_subset<2, 7, PT_UNIQUE, 7, true>(tx, mem_of(2, part, s), &f[s], sq); break;
+    case 6: fit_subset<4, 7, PT_UNIQUE, 7, true>(tx, mem_all(), &f[0], sq); break;
+    case 7: for (int s = 0; s < 2; s++) fit_subset<2, 7, PT_UNIQUE, 5, true>(tx, mem_of(2, part, s), &f[s], sq); break;
     case 4:
       switch (rot * 2 + isb) {
         case 0: score_rot<4, 0, 0>(tx, &f[0], &fa, sq); break;
@@ -913,8 +931,8 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_bc7_mode1(const uint8_t* __re
       for (int i = 0; i < 32; i++) {
         const int j = 32 * w + i;
         const uint32_t* my = &tex[0][j];
-        const uint32_t sa = score_part<2, 3, PT_SHARED, 6>(my, c_part2[lane], sq);
-        const uint32_t sb = score_part<2, 3, PT_SHARED, 6>(my, c_part2[lane + 32], sq);
+        const uint32_t sa = score_part<2, 3, PT_SHARED, 6>(my, lane, sq);
+        const uint32_t sb = score_part<2, 3, PT_SHARED, 6>(my, lane + 32, sq);
         uint32_t best = sa;
         int bp = lane;
         if (sb < best) { best = sb; bp = lane + 32; }
@@ -933,7 +951,7 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_bc7_mode1(const uint8_t* __re
       int bp = 0;
 #pragma unroll 1
       for (int p = 0; p < 64; p++) {
-        const uint32_t s = score_part<2, 3, PT_SHARED, 6>(my, c_part2[p], sq);
+        const uint32_t s = score_part<2, 3, PT_SHARED, 6>(my, p, sq);
         if (s < best) { best = s; bp = p; }
       }
       const int64_t blk = b0 + lt;
