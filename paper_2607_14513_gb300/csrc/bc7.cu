@@ -157,7 +157,9 @@ __device__ __forceinline__ uint32_t pack_rgb(int r, int g, int b) { return (uint
 // Palette of F entries between endpoints a and b (R, G, B; uncoded channels 0) with BC7 weights,
 // and its keys. Two channels share one multiply-add in 16-bit lanes scaled by 4, so byte 1 of
 // each lane is ((64 - w) a + w b + 32) >> 6 exactly.
-template <int IB>
+// IDX: keys 16 |entry|^2 + j (the index j in the low bits picks the first of equal errors);
+// otherwise |entry|^2 alone (when only the least error matters).
+template <int IB, bool IDX = true>
 __device__ __forceinline__ void build_pal(const int (&a)[3], const int (&b)[3], uint32_t (&pal)[1 << IB],
                                           int (&pk)[1 << IB]) {
   const uint32_t A = ((uint32_t)a[0] | ((uint32_t)a[1] << 16)) << 2, B = ((uint32_t)b[0] | ((uint32_t)b[1] << 16)) << 2;
@@ -167,15 +169,15 @@ __device__ __forceinline__ void build_pal(const int (&a)[3], const int (&b)[3], 
     const uint32_t w = (uint32_t)wgt<IB>(j);
     const uint32_t rg = (64u - w) * A + w * B + 0x00800080u, bb = (64u - w) * Ab + w * Bb + 0x80u;
     pal[j] = __byte_perm(rg, bb, 0x7531u);
-    pk[j] = 16 * (int)__dp4a(pal[j], pal[j], 0u) + j;
+    pk[j] = IDX ? 16 * (int)__dp4a(pal[j], pal[j], 0u) + j : (int)__dp4a(pal[j], pal[j], 0u);
   }
 }
 
-template <int F>
+template <int F, int SCALE = 32>
 __device__ __forceinline__ int best_key(uint32_t v, const uint32_t (&pal)[F], const int (&pk)[F]) {
   int k[F];
 #pragma unroll
-  for (int j = 0; j < F; j++) k[j] = pk[j] - 32 * (int)__dp4a(v, pal[j], 0u);
+  for (int j = 0; j < F; j++) k[j] = pk[j] - SCALE * (int)__dp4a(v, pal[j], 0u);
 #pragma unroll
   for (int w = F / 2; w >= 1; w /= 2)
 #pragma unroll
@@ -286,14 +288,15 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, Mem M, i
     for (int i = 1; i < M.n; i += 2) {
       const int ta = (int)(L & 15), tb = (int)((L >> 4) & 15);
       L >>= 8;
-      const uint32_t va = __byte_perm(tex[ta * STAGE_STRIDE], 0u, sel) & CM;
-      const uint32_t vb = __byte_perm(tex[tb * STAGE_STRIDE], 0u, sel) & CM;
+      // uncoded channels: their palette bytes are 0, so the products ignore those texel bytes
+      const uint32_t va = __byte_perm(tex[ta * STAGE_STRIDE], 0u, sel);
+      const uint32_t vb = __byte_perm(tex[tb * STAGE_STRIDE], 0u, sel);
       const int ka = best_key<F>(va, pal, pk), kb = best_key<F>(vb, pal, pk);
       accumulate(va, ka);
       accumulate(vb, kb);
     }
     if (M.n & 1) {
-      const uint32_t va = __byte_perm(tex[(int)(L & 15) * STAGE_STRIDE], 0u, sel) & CM;
+      const uint32_t va = __byte_perm(tex[(int)(L & 15) * STAGE_STRIDE], 0u, sel);
       accumulate(va, best_key<F>(va, pal, pk));
     }
   }
@@ -316,7 +319,6 @@ __device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex,
                                                const uint16_t* __restrict__ sq, uint32_t sel = 0x3210u) {
   constexpr int F = 1 << IB;
   constexpr int NCH = ((CHMASK >> 0) & 1) + ((CHMASK >> 1) & 1) + ((CHMASK >> 2) & 1);
-  constexpr uint32_t CM = ((CHMASK & 1) ? 0xFFu : 0u) | ((CHMASK & 2) ? 0xFF00u : 0u) | ((CHMASK & 4) ? 0xFF0000u : 0u);
   int ch[3] = {0, 0, 0};
   {
     int k = 0;
@@ -341,14 +343,14 @@ __device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex,
     }
     uint32_t pal[F];
     int pk[F];
-    build_pal<IB>(v0, v1, pal, pk);  // uncoded channels have zero endpoints, so their bytes are 0
+    build_pal<IB, OUT>(v0, v1, pal, pk);  // uncoded channels have zero endpoints, so their bytes are 0
     int sse = sumsq;
     uint32_t il = 0, ih = 0;
     if (OUT) {
       uint64_t L = M.list;
       for (int i = 0; i < M.n; i++, L >>= 4) {
         const int t = (int)(L & 15);
-        const uint32_t v = __byte_perm(tex[t * STAGE_STRIDE], 0u, sel) & CM;
+        const uint32_t v = __byte_perm(tex[t * STAGE_STRIDE], 0u, sel);
         const int key = best_key<F>(v, pal, pk);
         sse += key >> 4;
         if (t < 8) il |= (uint32_t)(key & 15) << (4 * t); else ih |= (uint32_t)(key & 15) << (4 * (t - 8));
@@ -360,14 +362,13 @@ __device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex,
       for (int i = 1; i < M.n; i += 2) {
         const int ta = (int)(L & 15), tb = (int)((L >> 4) & 15);
         L >>= 8;
-        const uint32_t va = __byte_perm(tex[ta * STAGE_STRIDE], 0u, sel) & CM;
-        const uint32_t vb = __byte_perm(tex[tb * STAGE_STRIDE], 0u, sel) & CM;
-        const int ka = best_key<F>(va, pal, pk), kb = best_key<F>(vb, pal, pk);
-        sse += (ka >> 4) + (kb >> 4);
+        const uint32_t va = __byte_perm(tex[ta * STAGE_STRIDE], 0u, sel);
+        const uint32_t vb = __byte_perm(tex[tb * STAGE_STRIDE], 0u, sel);
+        sse += best_key<F, 2>(va, pal, pk) + best_key<F, 2>(vb, pal, pk);  // |entry|^2 - 2 dot
       }
       if (M.n & 1) {
-        const uint32_t va = __byte_perm(tex[(int)(L & 15) * STAGE_STRIDE], 0u, sel) & CM;
-        sse += best_key<F>(va, pal, pk) >> 4;
+        const uint32_t va = __byte_perm(tex[(int)(L & 15) * STAGE_STRIDE], 0u, sel);
+        sse += best_key<F, 2>(va, pal, pk);
       }
     }
     if ((uint32_t)sse < best_sse) {
