@@ -327,41 +327,47 @@ __device__ __forceinline__ uint32_t quant_eval(const uint32_t* __restrict__ tex,
   }
   constexpr int NCOMBO = PT == PT_NONE ? 1 : (PT == PT_UNIQUE ? 4 : 2);
   constexpr int HP = PT == PT_NONE ? 0 : 1;
-  if constexpr (!OUT && NCOMBO > 1 && NCOMBO * F <= 16) {
-    // search form with small palettes: every combination's palette first, then one pass over
-    // the member texels evaluating all of them (each texel is loaded once)
-    uint32_t pal[NCOMBO][F];
-    int pk[NCOMBO][F], sse[NCOMBO];
+  // search form: the combinations' palettes built in chunks of at most 16 entries in all, and one
+  // pass over the member texels per chunk evaluating every palette of it (each texel is loaded
+  // once per chunk)
+  constexpr int CH = (NCOMBO * F <= 16) ? NCOMBO : (2 * F <= 16 ? 2 : 1);
+  if constexpr (!OUT && CH > 1) {
+    uint32_t b = 0xFFFFFFFFu;
 #pragma unroll
-    for (int cmb = 0; cmb < NCOMBO; cmb++) {
-      const int p0 = PT == PT_UNIQUE ? (cmb & 1) : cmb;
-      const int p1 = PT == PT_UNIQUE ? (cmb >> 1) : cmb;
-      const uint16_t* q0 = sq + 256 * qid(BITS, HP, p0);
-      const uint16_t* q1 = sq + 256 * qid(BITS, HP, p1);
-      int v0[3] = {0, 0, 0}, v1[3] = {0, 0, 0};
+    for (int c0 = 0; c0 < NCOMBO; c0 += CH) {
+      uint32_t pal[CH][F];
+      int pk[CH][F], sse[CH];
 #pragma unroll
-      for (int i = 0; i < NCH; i++) { v0[ch[i]] = q0[e0[i]] >> 8; v1[ch[i]] = q1[e1[i]] >> 8; }
-      build_pal<IB, false>(v0, v1, pal[cmb], pk[cmb]);
-      sse[cmb] = sumsq;
+      for (int u = 0; u < CH; u++) {
+        const int cmb = c0 + u;
+        const int p0 = PT == PT_UNIQUE ? (cmb & 1) : cmb;
+        const int p1 = PT == PT_UNIQUE ? (cmb >> 1) : cmb;
+        const uint16_t* q0 = sq + 256 * qid(BITS, HP, p0);
+        const uint16_t* q1 = sq + 256 * qid(BITS, HP, p1);
+        int v0[3] = {0, 0, 0}, v1[3] = {0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < NCH; i++) { v0[ch[i]] = q0[e0[i]] >> 8; v1[ch[i]] = q1[e1[i]] >> 8; }
+        build_pal<IB, false>(v0, v1, pal[u], pk[u]);
+        sse[u] = sumsq;
+      }
+      uint64_t L = M.list;
+      for (int i = 1; i < M.n; i += 2) {
+        const int ta = (int)(L & 15), tb = (int)((L >> 4) & 15);
+        L >>= 8;
+        const uint32_t va = __byte_perm(tex[ta * STAGE_STRIDE], 0u, sel);
+        const uint32_t vb = __byte_perm(tex[tb * STAGE_STRIDE], 0u, sel);
+#pragma unroll
+        for (int u = 0; u < CH; u++)
+          sse[u] += best_key<F, 2>(va, pal[u], pk[u]) + best_key<F, 2>(vb, pal[u], pk[u]);
+      }
+      if (M.n & 1) {
+        const uint32_t va = __byte_perm(tex[(int)(L & 15) * STAGE_STRIDE], 0u, sel);
+#pragma unroll
+        for (int u = 0; u < CH; u++) sse[u] += best_key<F, 2>(va, pal[u], pk[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < CH; u++) b = min(b, (uint32_t)sse[u]);
     }
-    uint64_t L = M.list;
-    for (int i = 1; i < M.n; i += 2) {
-      const int ta = (int)(L & 15), tb = (int)((L >> 4) & 15);
-      L >>= 8;
-      const uint32_t va = __byte_perm(tex[ta * STAGE_STRIDE], 0u, sel);
-      const uint32_t vb = __byte_perm(tex[tb * STAGE_STRIDE], 0u, sel);
-#pragma unroll
-      for (int cmb = 0; cmb < NCOMBO; cmb++)
-        sse[cmb] += best_key<F, 2>(va, pal[cmb], pk[cmb]) + best_key<F, 2>(vb, pal[cmb], pk[cmb]);
-    }
-    if (M.n & 1) {
-      const uint32_t va = __byte_perm(tex[(int)(L & 15) * STAGE_STRIDE], 0u, sel);
-#pragma unroll
-      for (int cmb = 0; cmb < NCOMBO; cmb++) sse[cmb] += best_key<F, 2>(va, pal[cmb], pk[cmb]);
-    }
-    uint32_t b = (uint32_t)sse[0];
-#pragma unroll
-    for (int cmb = 1; cmb < NCOMBO; cmb++) b = min(b, (uint32_t)sse[cmb]);
     return b;
   }
   uint32_t best_sse = 0xFFFFFFFFu;
