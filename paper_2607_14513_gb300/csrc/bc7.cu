@@ -547,12 +547,13 @@ __device__ __noinline__ int search_best(const uint32_t* tex, uint32_t* best_sse,
   CAND((score_rot<4, 0, 1>(tex, nullptr, nullptr, sq)), 209);
   CAND((score_rot<5, 0, 0>(tex, nullptr, nullptr, sq)), 216);
 #pragma unroll 1
-  for (int rot = 1; rot <= 3; rot++) {
-    const uint32_t sel = rot_sel(rot);
-    CAND((score_rot_n<4, 0>(tex, sel, sq)), 208 + 2 * rot);
-    CAND((score_rot_n<4, 1>(tex, sel, sq)), 209 + 2 * rot);
-    CAND((score_rot_n<5, 0>(tex, sel, sq)), 216 + rot);
-  }
+  for (int rot = 1; rot <= 3; rot++) CAND((score_rot_n<4, 0>(tex, rot_sel(rot), sq)), 208 + 2 * rot);
+  if (SYNC) __syncthreads();
+#pragma unroll 1
+  for (int rot = 1; rot <= 3; rot++) CAND((score_rot_n<4, 1>(tex, rot_sel(rot), sq)), 209 + 2 * rot);
+  if (SYNC) __syncthreads();
+#pragma unroll 1
+  for (int rot = 1; rot <= 3; rot++) CAND((score_rot_n<5, 0>(tex, rot_sel(rot), sq)), 216 + rot);
   CAND((score_part<1, 4, PT_UNIQUE, 7>(tex, 0, sq)), 220);
 #undef CAND
   *best_sse = best;
