@@ -122,10 +122,11 @@ __device__ __forceinline__ Bc1Res bc1_encode(const uint32_t (&tx)[16]) {
     }
     int det = saa * sbb - sab * sab;
     if (det == 0) break;
+    const RoundDiv255 rd = round_div255_of(det);
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-      e0[c] = round_div_clamp255(3LL * (sbb * sav[c] - sab * sbv[c]), det);
-      e1[c] = round_div_clamp255(3LL * (saa * sbv[c] - sab * sav[c]), det);
+      e0[c] = round_div255(rd, 3LL * (sbb * sav[c] - sab * sbv[c]));
+      e1[c] = round_div255(rd, 3LL * (saa * sbv[c] - sab * sav[c]));
     }
     Bc1Res r = bc1_eval(tx, pack565(e0[0], e0[1], e0[2]), pack565(e1[0], e1[1], e1[2]));
     if (r.sse < best.sse) best = r; else break;

@@ -164,10 +164,13 @@ __device__ __forceinline__ void build_pal(const int (&a)[3], const int (&b)[3], 
                                           int (&pk)[1 << IB]) {
   const uint32_t A = ((uint32_t)a[0] | ((uint32_t)a[1] << 16)) << 2, B = ((uint32_t)b[0] | ((uint32_t)b[1] << 16)) << 2;
   const uint32_t Ab = (uint32_t)a[2] << 2, Bb = (uint32_t)b[2] << 2;
+  // (64 - w) A + w B = 64 A + w (B - A): with B - A formed in 32-bit arithmetic a lane may be
+  // negative, but each lane's result lies in [0, 2^16), so the packed sum is exact
+  const uint32_t rg0 = 64u * A + 0x00800080u, drg = B - A, bb0 = 64u * Ab + 0x80u, dbb = Bb - Ab;
 #pragma unroll
   for (int j = 0; j < (1 << IB); j++) {
     const uint32_t w = (uint32_t)wgt<IB>(j);
-    const uint32_t rg = (64u - w) * A + w * B + 0x00800080u, bb = (64u - w) * Ab + w * Bb + 0x80u;
+    const uint32_t rg = rg0 + w * drg, bb = bb0 + w * dbb;
     pal[j] = __byte_perm(rg, bb, 0x7531u);
     pk[j] = IDX ? 16 * (int)__dp4a(pal[j], pal[j], 0u) + j : (int)__dp4a(pal[j], pal[j], 0u);
   }
@@ -302,10 +305,11 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, Mem M, i
   }
   const long long det = (long long)saa * sbb - (long long)sab * sab;
   if (det != 0) {
+    const RoundDiv255 rd = round_div255_of(det);
 #pragma unroll
     for (int i = 0; i < NCH; i++) {
-      e0[i] = round_div_clamp255(64LL * ((long long)sbb * sav[i] - (long long)sab * sbv[i]), det);
-      e1[i] = round_div_clamp255(64LL * ((long long)saa * sbv[i] - (long long)sab * sav[i]), det);
+      e0[i] = round_div255(rd, 64LL * ((long long)sbb * sav[i] - (long long)sab * sbv[i]));
+      e1[i] = round_div255(rd, 64LL * ((long long)saa * sbv[i] - (long long)sab * sav[i]));
     }
   }
   return n;

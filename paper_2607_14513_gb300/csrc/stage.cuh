@@ -54,19 +54,30 @@ __device__ __forceinline__ int tex_r(uint32_t v) { return v & 255; }
 __device__ __forceinline__ int tex_g(uint32_t v) { return (v >> 8) & 255; }
 __device__ __forceinline__ int tex_b(uint32_t v) { return (v >> 16) & 255; }
 
-// Exact clamp(round_div(num, den), 0, 255) for den > 0 with round_div rounding half away
-// from zero: a negative numerator always clamps to 0; otherwise floor((2num + den) / (2den))
-// is estimated in float and corrected exactly in 64-bit integers.
-__device__ __forceinline__ int round_div_clamp255(long long num, long long den) {
+// Exact clamp(round_div(num, den), 0, 255) for den > 0, round_div rounding half away from zero,
+// for several numerators over one denominator: a negative numerator clamps to 0; otherwise
+// floor((2num + den) / (2den)) is estimated in float with one reciprocal of 2den per
+// denominator and corrected exactly in 64-bit integers. The quotient is below 256 and the
+// conversions, the reciprocal and the product carry a relative error of a few 2^-24, so the
+// estimate's floor is off by at most one and one exact step each way lands on it.
+struct RoundDiv255 {
+  long long D;  // 2 den
+  float rcp;    // 1 / D, rounded
+};
+__device__ __forceinline__ RoundDiv255 round_div255_of(long long den) {
+  RoundDiv255 r;
+  r.D = 2 * den;
+  r.rcp = __frcp_rn((float)r.D);
+  return r;
+}
+__device__ __forceinline__ int round_div255(const RoundDiv255& r, long long num) {
   if (num < 0) return 0;
-  long long N = 2 * num + den, D = 2 * den;
-  if (N >= 256 * D) return 255;
-  // N / D < 256 and both conversions and the approximate quotient carry a relative error of a few
-  // 2^-24, so the estimate is within 1e-3 of the true quotient: its floor is off by at most one,
-  // and one exact step each way lands on floor(N / D)
-  int q = (int)__fdividef((float)N, (float)D);
+  const long long N = 2 * num + r.D / 2;
+  if (N >= 256 * r.D) return 255;
+  int q = (int)((float)N * r.rcp);
   q = min(max(q, 0), 255);
-  if (q > 0 && (long long)q * D > N) q--;
-  if (q < 255 && (long long)(q + 1) * D <= N) q++;
+  if (q > 0 && (long long)q * r.D > N) q--;
+  if (q < 255 && (long long)(q + 1) * r.D <= N) q++;
   return q;
 }
+
