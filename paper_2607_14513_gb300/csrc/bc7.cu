@@ -268,7 +268,10 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, Mem M, i
     e0[i] = flip ? lo[i] : hi[i];
     e1[i] = flip ? hi[i] : lo[i];
   }
-  int saa = 0, sbb = 0, sab = 0, sav[NCH], sbv[NCH];
+  // least-squares sums over the member texels with weights a = 64 - w and w: only sums of w,
+  // w^2 and w c are accumulated per texel; with n and the channel sums s1 of the box pass,
+  // sum a^2 = 4096 n - 128 sum w + sum w^2, sum a w = 64 sum w - sum w^2, sum a c = 64 s1 - sum w c
+  int sw = 0, sbb = 0, sbv[NCH];
   {
     uint32_t pal[F];
     int pk[F];
@@ -279,12 +282,12 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, Mem M, i
       build_pal<IB>(a, b, pal, pk);
     }
 #pragma unroll
-    for (int i = 0; i < NCH; i++) { sav[i] = 0; sbv[i] = 0; }
+    for (int i = 0; i < NCH; i++) sbv[i] = 0;
     auto accumulate = [&](uint32_t v, int key) {
-      const int w = wgt<IB>(key & 15), a = 64 - w;
-      saa += a * a; sbb += w * w; sab += a * w;
+      const int w = wgt<IB>(key & 15);
+      sw += w; sbb += w * w;
 #pragma unroll
-      for (int i = 0; i < NCH; i++) { const int c = (v >> (8 * ch[i])) & 255; sav[i] += a * c; sbv[i] += w * c; }
+      for (int i = 0; i < NCH; i++) sbv[i] += w * (int)((v >> (8 * ch[i])) & 255);
     };
     // two member texels per step (independent palette searches; integer sums, order-free)
     uint64_t L = M.list;
@@ -303,6 +306,10 @@ __device__ __forceinline__ int prefit(const uint32_t* __restrict__ tex, Mem M, i
       accumulate(va, best_key<F>(va, pal, pk));
     }
   }
+  const int saa = 4096 * n - 128 * sw + sbb, sab = 64 * sw - sbb;
+  int sav[NCH];
+#pragma unroll
+  for (int i = 0; i < NCH; i++) sav[i] = 64 * s1[i] - sbv[i];
   const long long det = (long long)saa * sbb - (long long)sab * sab;
   if (det != 0) {
     const RoundDiv255 rd = round_div255_of(det);
