@@ -754,8 +754,8 @@ __device__ __forceinline__ bool const_block(const uint32_t* tx, uint4* out) {
 // shared tile (column threadIdx.x % 128) for the whole search. Every thread searches (threads
 // past the last block on texels of 128) so that the barriers between the search's modes are
 // reached by the whole CTA.
-// 5 units (20 warps, at most 102 registers) per CTA and SM measured fastest: 100.9 ms for 3M
-// blocks against 107.7 ms with 4 units (128 registers) and 101.4 ms with 6 (80 registers).
+// 5 units (20 warps, at most 102 registers) per CTA and SM: 70.7 ms for 3M blocks against
+// 70.8-71.1 ms with 6 units (80 registers); 4 units (128 registers) were 6% slower.
 #ifndef BC7_SUBS
 #define BC7_SUBS 5
 #endif
