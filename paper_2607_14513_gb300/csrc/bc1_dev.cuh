@@ -64,6 +64,35 @@ __device__ __forceinline__ Bc1Res bc1_eval(const uint32_t (&tx)[16], uint32_t a,
   return r;
 }
 
+// The error of a candidate pair alone (no indices): sumsq is the block's summed squared texel
+// norms, and each texel adds min_j (|p_j|^2 - 2 v.p_j) over the palette (one entry when the two
+// endpoints are equal), the same integer as bc1_eval's error.
+__device__ __forceinline__ uint32_t bc1_sse(const uint32_t (&tx)[16], int sumsq, uint32_t a, uint32_t b) {
+  const uint32_t c0 = max(a, b), c1 = min(a, b);
+  const int ra = c0 >> 11, ga = (c0 >> 5) & 63, ba = c0 & 31;
+  const int rb = c1 >> 11, gb = (c1 >> 5) & 63, bb = c1 & 31;
+  const uint32_t P0 = (uint32_t)ex5(ra) | ((uint32_t)ex6(ga) << 8) | ((uint32_t)ex5(ba) << 16);
+  const int k0 = (int)__dp4a(P0, P0, 0u);
+  int s = 0;
+  if (c0 == c1) {
+#pragma unroll
+    for (int t = 0; t < 16; t++) s += k0 - 2 * (int)__dp4a(tx[t], P0, 0u);
+    return (uint32_t)(sumsq + s);
+  }
+  const uint32_t P1 = (uint32_t)ex5(rb) | ((uint32_t)ex6(gb) << 8) | ((uint32_t)ex5(bb) << 16);
+  const uint32_t P2 = (uint32_t)third5(ra, rb) | ((uint32_t)third6(ga, gb) << 8) | ((uint32_t)third5(ba, bb) << 16);
+  const uint32_t P3 = (uint32_t)third5(rb, ra) | ((uint32_t)third6(gb, ga) << 8) | ((uint32_t)third5(bb, ba) << 16);
+  const int k1 = (int)__dp4a(P1, P1, 0u), k2 = (int)__dp4a(P2, P2, 0u), k3 = (int)__dp4a(P3, P3, 0u);
+#pragma unroll
+  for (int t = 0; t < 16; t++) {
+    const uint32_t v = tx[t];
+    const int e0 = k0 - 2 * (int)__dp4a(v, P0, 0u), e1 = k1 - 2 * (int)__dp4a(v, P1, 0u);
+    const int e2 = k2 - 2 * (int)__dp4a(v, P2, 0u), e3 = k3 - 2 * (int)__dp4a(v, P3, 0u);
+    s += min(min(e0, e1), min(e2, e3));
+  }
+  return (uint32_t)(sumsq + s);
+}
+
 __device__ __forceinline__ int q5(int v) { return (v * 31 + 127) / 255; }
 __device__ __forceinline__ int q6(int v) { return (v * 63 + 127) / 255; }
 __device__ __forceinline__ uint32_t pack565(int r, int g, int b) { return (q5(r) << 11) | (q6(g) << 5) | q5(b); }
@@ -132,27 +161,32 @@ __device__ __forceinline__ Bc1Res bc1_encode(const uint32_t (&tx)[16]) {
     if (r.sse < best.sse) best = r; else break;
   }
   // +-1 neighbourhood, order: endpoint (c0, c1) x channel (R, G, B) x step (+1, -1); one copy of
-  // the candidate evaluation in a rolled loop keeps the code small enough for the instruction cache
+  // the candidate evaluation in a rolled loop keeps the code small enough for the instruction cache.
+  // Candidates are compared by error alone; the chosen pair's indices are computed at the end.
+  int sumsq = 0;
+#pragma unroll
+  for (int t = 0; t < 16; t++) sumsq += (int)__dp4a(tx[t] & 0xFFFFFFu, tx[t] & 0xFFFFFFu, 0u);
+  uint32_t bc0 = best.c0, bc1 = best.c1, bsse = best.sse;
+  bool moved = false;
   for (int round = 0; round < 4; round++) {
-    Bc1Res nb;
-    nb.sse = 0xFFFFFFFFu;
+    uint32_t nsse = 0xFFFFFFFFu, n0 = 0, n1 = 0;
     bool found = false;
 #pragma unroll 1
     for (int q = 0; q < 12; q++) {
       const int ep = q / 6, c = (q / 2) % 3, sgn = q & 1;
       const int shift = c == 0 ? 11 : (c == 1 ? 5 : 0), mask = c == 1 ? 63 : 31;
-      uint32_t cc0 = best.c0, cc1 = best.c1;
+      uint32_t cc0 = bc0, cc1 = bc1;
       uint32_t cur = ep ? cc1 : cc0;
       int v = (int)((cur >> shift) & mask) + (sgn ? -1 : 1);
       if (v < 0 || v > mask) continue;
       cur = (cur & ~((uint32_t)mask << shift)) | ((uint32_t)v << shift);
       if (ep) cc1 = cur; else cc0 = cur;
-      Bc1Res r = bc1_eval(tx, cc0, cc1);
-      if (!found || r.sse < nb.sse) { nb = r; found = true; }
+      const uint32_t e = bc1_sse(tx, sumsq, cc0, cc1);
+      if (!found || e < nsse) { nsse = e; n0 = max(cc0, cc1); n1 = min(cc0, cc1); found = true; }
     }
-    if (found && nb.sse < best.sse) best = nb; else break;
+    if (found && nsse < bsse) { bsse = nsse; bc0 = n0; bc1 = n1; moved = true; } else break;
   }
-  return best;
+  return moved ? bc1_eval(tx, bc0, bc1) : best;
 }
 
 __device__ __forceinline__ uint2 bc1_bits(const Bc1Res& r) {
