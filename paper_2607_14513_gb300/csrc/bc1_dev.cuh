@@ -93,6 +93,42 @@ __device__ __forceinline__ uint32_t bc1_sse(const uint32_t (&tx)[16], int sumsq,
   return (uint32_t)(sumsq + s);
 }
 
+// bc1_eval from byte dot products: key 4 (|p_j|^2 - 2 v.p_j) + j, whose minimum gives the first
+// entry of least error (j = key & 3) and the error above the texel's squared norm (key >> 2).
+__device__ __forceinline__ Bc1Res bc1_eval_k(const uint32_t (&tx)[16], int sumsq, uint32_t a, uint32_t b) {
+  Bc1Res r;
+  r.c0 = (uint16_t)max(a, b);
+  r.c1 = (uint16_t)min(a, b);
+  r.idx = 0;
+  const int ra = r.c0 >> 11, ga = (r.c0 >> 5) & 63, ba = r.c0 & 31;
+  const int rb = r.c1 >> 11, gb = (r.c1 >> 5) & 63, bb = r.c1 & 31;
+  const uint32_t P0 = (uint32_t)ex5(ra) | ((uint32_t)ex6(ga) << 8) | ((uint32_t)ex5(ba) << 16);
+  const int k0 = (int)__dp4a(P0, P0, 0u);
+  int s = 0;
+  if (r.c0 == r.c1) {
+#pragma unroll
+    for (int t = 0; t < 16; t++) s += k0 - 2 * (int)__dp4a(tx[t], P0, 0u);
+    r.sse = (uint32_t)(sumsq + s);
+    return r;
+  }
+  const uint32_t P1 = (uint32_t)ex5(rb) | ((uint32_t)ex6(gb) << 8) | ((uint32_t)ex5(bb) << 16);
+  const uint32_t P2 = (uint32_t)third5(ra, rb) | ((uint32_t)third6(ga, gb) << 8) | ((uint32_t)third5(ba, bb) << 16);
+  const uint32_t P3 = (uint32_t)third5(rb, ra) | ((uint32_t)third6(gb, ga) << 8) | ((uint32_t)third5(bb, ba) << 16);
+  const int q0 = 4 * k0, q1 = 4 * (int)__dp4a(P1, P1, 0u) + 1;
+  const int q2 = 4 * (int)__dp4a(P2, P2, 0u) + 2, q3 = 4 * (int)__dp4a(P3, P3, 0u) + 3;
+#pragma unroll
+  for (int t = 0; t < 16; t++) {
+    const uint32_t v = tx[t];
+    const int e0 = q0 - 8 * (int)__dp4a(v, P0, 0u), e1 = q1 - 8 * (int)__dp4a(v, P1, 0u);
+    const int e2 = q2 - 8 * (int)__dp4a(v, P2, 0u), e3 = q3 - 8 * (int)__dp4a(v, P3, 0u);
+    const int key = min(min(e0, e1), min(e2, e3));
+    s += key >> 2;
+    r.idx |= (uint32_t)(key & 3) << (2 * t);
+  }
+  r.sse = (uint32_t)(sumsq + s);
+  return r;
+}
+
 __device__ __forceinline__ int q5(int v) { return (v * 31 + 127) / 255; }
 __device__ __forceinline__ int q6(int v) { return (v * 63 + 127) / 255; }
 __device__ __forceinline__ uint32_t pack565(int r, int g, int b) { return (q5(r) << 11) | (q6(g) << 5) | q5(b); }
@@ -134,7 +170,10 @@ __device__ __forceinline__ Bc1Res bc1_encode(const uint32_t (&tx)[16]) {
     int d = (hi[c] - lo[c]) >> 4;
     if (e0[c] >= e1[c]) { e0[c] -= d; e1[c] += d; } else { e0[c] += d; e1[c] -= d; }
   }
-  Bc1Res best = bc1_eval(tx, pack565(e0[0], e0[1], e0[2]), pack565(e1[0], e1[1], e1[2]));
+  int sumsq = 0;
+#pragma unroll
+  for (int t = 0; t < 16; t++) sumsq += (int)__dp4a(tx[t] & 0xFFFFFFu, tx[t] & 0xFFFFFFu, 0u);
+  Bc1Res best = bc1_eval_k(tx, sumsq, pack565(e0[0], e0[1], e0[2]), pack565(e1[0], e1[1], e1[2]));
   // two least-squares refinements: weights (3,0,2,1)/3 on c0 for indices 0..3
   for (int it = 0; it < 2; it++) {
     if (best.c0 == best.c1) break;
@@ -157,15 +196,12 @@ __device__ __forceinline__ Bc1Res bc1_encode(const uint32_t (&tx)[16]) {
       e0[c] = round_div255(rd, 3LL * (sbb * sav[c] - sab * sbv[c]));
       e1[c] = round_div255(rd, 3LL * (saa * sbv[c] - sab * sav[c]));
     }
-    Bc1Res r = bc1_eval(tx, pack565(e0[0], e0[1], e0[2]), pack565(e1[0], e1[1], e1[2]));
+    Bc1Res r = bc1_eval_k(tx, sumsq, pack565(e0[0], e0[1], e0[2]), pack565(e1[0], e1[1], e1[2]));
     if (r.sse < best.sse) best = r; else break;
   }
   // +-1 neighbourhood, order: endpoint (c0, c1) x channel (R, G, B) x step (+1, -1); one copy of
   // the candidate evaluation in a rolled loop keeps the code small enough for the instruction cache.
   // Candidates are compared by error alone; the chosen pair's indices are computed at the end.
-  int sumsq = 0;
-#pragma unroll
-  for (int t = 0; t < 16; t++) sumsq += (int)__dp4a(tx[t] & 0xFFFFFFu, tx[t] & 0xFFFFFFu, 0u);
   uint32_t bc0 = best.c0, bc1 = best.c1, bsse = best.sse;
   bool moved = false;
   for (int round = 0; round < 4; round++) {
@@ -186,7 +222,7 @@ __device__ __forceinline__ Bc1Res bc1_encode(const uint32_t (&tx)[16]) {
     }
     if (found && nsse < bsse) { bsse = nsse; bc0 = n0; bc1 = n1; moved = true; } else break;
   }
-  return moved ? bc1_eval(tx, bc0, bc1) : best;
+  return moved ? bc1_eval_k(tx, sumsq, bc0, bc1) : best;
 }
 
 __device__ __forceinline__ uint2 bc1_bits(const Bc1Res& r) {
