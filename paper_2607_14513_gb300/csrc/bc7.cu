@@ -35,6 +35,17 @@ __constant__ uint16_t c_sub3[64 * 3];
 // increasing order, four bits each from bit 0, and the member count in bits 60-63
 __constant__ uint64_t c_mem2[64][2];
 __constant__ uint64_t c_mem3[64][3];
+// prefits shared across modes: a member set of the first 16 three-subset partitions that is also
+// a two-subset member set has the same 3-bit prefit in modes 0 and 1, and one of the 64
+// three-subset partitions the same 2-bit prefit in modes 2 and 3/7. Per three-subset subset the
+// slot its mode 0 (mode 2) fit stores its prefit in, per two-subset subset the slot its mode 1
+// (modes 3/7) fit reads it from; -1 where there is none.
+#define BC7_PF3_SLOTS 14
+#define BC7_PF_SLOTS 40
+__constant__ int8_t c_pf3b[64][3];  // 3-bit: mode 0 store slot
+__constant__ int8_t c_pf3a[64][3];  // 2-bit: mode 2 store slot
+__constant__ int8_t c_pf2b[64][2];  // 3-bit: mode 1 read slot
+__constant__ int8_t c_pf2a[64][2];  // 2-bit: modes 3/7 read slot
 cudaError_t bc7_kernel_attributes();
 
 static int h_expand(int v, int n) { return n >= 8 ? v : ((v << (8 - n)) | (v >> (2 * n - 8))); }
@@ -108,7 +119,48 @@ cudaError_t bc7_init_tables() {
         list |= (uint64_t)cnt << 60;
         if (ns == 2) mem2[pp][sb] = list; else mem3[pp][sb] = list;
       }
+  // shared prefit slots: 3-bit (mode 0 -> mode 1) first, then 2-bit (mode 2 -> modes 3/7), each
+  // set stored by its first subset in enumeration order
+  int8_t pf3b[64][3], pf3a[64][3], pf2b[64][2], pf2a[64][2];
+  memset(pf3b, -1, sizeof(pf3b)); memset(pf3a, -1, sizeof(pf3a));
+  memset(pf2b, -1, sizeof(pf2b)); memset(pf2a, -1, sizeof(pf2a));
+  {
+    auto set_of = [](uint32_t part, int sb) {
+      uint32_t m = 0;
+      for (int t = 0; t < 16; t++) if (((part >> (2 * t)) & 3u) == (uint32_t)sb) m |= 1u << t;
+      return m;
+    };
+    int slots = 0;
+    for (int kind = 0; kind < 2; kind++) {        // 0: 3-bit (modes 0 / 1), 1: 2-bit (modes 2 / 3, 7)
+      const int np3 = kind == 0 ? 16 : 64;
+      for (int pp = 0; pp < np3; pp++)
+        for (int sb = 0; sb < 3; sb++) {
+          const uint32_t m = set_of(p3[pp], sb);
+          bool first = true;
+          for (int q = 0; q < pp * 3 + sb && first; q++) first = set_of(p3[q / 3], q % 3) != m;
+          if (!first) continue;
+          int found = 0;
+          for (int p2i = 0; p2i < 64; p2i++)
+            for (int s2 = 0; s2 < 2; s2++)
+              if (set_of(p2[p2i], s2) == m) {
+                if (!found) {
+                  if (slots == BC7_PF_SLOTS) return cudaErrorInvalidValue;
+                  (kind == 0 ? pf3b : pf3a)[pp][sb] = (int8_t)slots;
+                  found = 1;
+                }
+                (kind == 0 ? pf2b : pf2a)[p2i][s2] = (int8_t)slots;
+              }
+          slots += found;
+        }
+      if (kind == 0 && slots != BC7_PF3_SLOTS) return cudaErrorInvalidValue;
+    }
+    if (slots != BC7_PF_SLOTS) return cudaErrorInvalidValue;
+  }
   cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(c_pf3b, pf3b, sizeof(pf3b))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_pf3a, pf3a, sizeof(pf3a))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_pf2b, pf2b, sizeof(pf2b))) != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_pf2a, pf2a, sizeof(pf2a))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_mem2, mem2, sizeof(mem2))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_mem3, mem3, sizeof(mem3))) != cudaSuccess) return e;
   if ((e = cudaMemcpyToSymbol(c_sub3, sub3, sizeof(sub3))) != cudaSuccess) return e;
@@ -464,15 +516,43 @@ __device__ __forceinline__ uint32_t score_part(const uint32_t* tex, int p, const
 // Three-subset partitions with the errors of repeated member sets reused (cache: the errors of
 // the distinct member sets met so far, indexed as c_sub3; the reuse pattern is the same for
 // every lane). Mode 0 meets 36 distinct sets in its 48 subsets, mode 2 140 in 192.
+// A prefit kept for a later mode: endpoints and the members' summed squared norms.
+struct Prefit {
+  int e0[3], e1[3], sumsq;
+};
+
+// The fit of a subset whose prefit may be shared: a slot >= 0 with STORE keeps the prefit there,
+// without STORE takes it from there.
+template <int IB, int PT, int BITS, bool STORE>
+__device__ __forceinline__ uint32_t fit_shared(const uint32_t* tex, Mem M, int slot, Prefit* pfc, const uint16_t* sq) {
+  if (slot < 0) return fit_subset<IB, 7, PT, BITS, false>(tex, M, nullptr, sq);
+  int e0[3] = {0, 0, 0}, e1[3] = {0, 0, 0}, sumsq = 0;
+  if (STORE) {
+    prefit<IB, 7>(tex, M, e0, e1, sumsq);
+    Prefit& f = pfc[slot];
+#pragma unroll
+    for (int i = 0; i < 3; i++) { f.e0[i] = e0[i]; f.e1[i] = e1[i]; }
+    f.sumsq = sumsq;
+  } else {
+    const Prefit& f = pfc[slot];
+#pragma unroll
+    for (int i = 0; i < 3; i++) { e0[i] = f.e0[i]; e1[i] = f.e1[i]; }
+    sumsq = f.sumsq;
+  }
+  return quant_eval<IB, 7, PT, BITS, false>(tex, M, e0, e1, sumsq, nullptr, sq);
+}
+
 template <int IB, int PT, int BITS>
-__device__ __forceinline__ uint32_t score_part3(const uint32_t* tex, int p, const uint16_t* sq, uint32_t* cache) {
+__device__ __forceinline__ uint32_t score_part3(const uint32_t* tex, int p, const uint16_t* sq, uint32_t* cache,
+                                                Prefit* pfc) {
   uint32_t s = 0;
 #pragma unroll 1
   for (int sub = 0; sub < 3; sub++) {
     const uint32_t e = c_sub3[3 * p + sub];
     uint32_t r;
     if (e & 0x100u) {
-      r = fit_subset<IB, 7, PT, BITS, false>(tex, mem_of(3, p, sub), nullptr, sq);
+      const int slot = IB == 3 ? c_pf3b[p][sub] : c_pf3a[p][sub];
+      r = fit_shared<IB, PT, BITS, true>(tex, mem_of(3, p, sub), slot, pfc, sq);
       cache[e & 0xFFu] = r;
     } else {
       r = cache[e & 0xFFu];
@@ -532,11 +612,18 @@ __device__ __noinline__ int search_best(const uint32_t* tex, uint32_t* best_sse,
     if (s_ < best || (s_ == best && e_ < be)) { best = s_; be = e_; } \
   } while (0)
   uint32_t cache[BC7_SUB3_SETS];
-  for (int p = 0; p < 16; p++) CAND((score_part3<3, PT_UNIQUE, 4>(tex, p, sq, cache)), p);
+  Prefit pfc[BC7_PF_SLOTS];
+  for (int p = 0; p < 16; p++) CAND((score_part3<3, PT_UNIQUE, 4>(tex, p, sq, cache, pfc)), p);
   if (SYNC) __syncthreads();
-  for (int p = 0; p < 64; p++) CAND((score_part<2, 3, PT_SHARED, 6>(tex, p, sq)), 16 + p);
+  for (int p = 0; p < 64; p++) {
+    uint32_t s1 = 0;
+#pragma unroll 1
+    for (int sub = 0; sub < 2; sub++)
+      s1 += fit_shared<3, PT_SHARED, 6, false>(tex, mem_of(2, p, sub), c_pf2b[p][sub], pfc, sq);
+    CAND(s1, 16 + p);
+  }
   if (SYNC) __syncthreads();
-  for (int p = 0; p < 64; p++) CAND((score_part3<2, PT_NONE, 5>(tex, p, sq, cache)), 80 + p);
+  for (int p = 0; p < 64; p++) CAND((score_part3<2, PT_NONE, 5>(tex, p, sq, cache, pfc)), 80 + p);
   if (SYNC) __syncthreads();
   // modes 3 and 7: same partitions and 2-bit weights, so one prefit per subset serves both
   for (int p = 0; p < 64; p++) {
@@ -546,7 +633,15 @@ __device__ __noinline__ int search_best(const uint32_t* tex, uint32_t* best_sse,
       int e0[3] = {0, 0, 0}, e1[3] = {0, 0, 0};
       int sumsq = 0;
       const Mem M = mem_of(2, p, sub);
-      if (prefit<2, 7>(tex, M, e0, e1, sumsq) == 0) continue;
+      const int slot = c_pf2a[p][sub];
+      if (slot >= 0) {
+        const Prefit& f = pfc[slot];
+#pragma unroll
+        for (int i = 0; i < 3; i++) { e0[i] = f.e0[i]; e1[i] = f.e1[i]; }
+        sumsq = f.sumsq;
+      } else if (prefit<2, 7>(tex, M, e0, e1, sumsq) == 0) {
+        continue;
+      }
       s3 += quant_eval<2, 7, PT_UNIQUE, 7, false>(tex, M, e0, e1, sumsq, nullptr, sq);
       s7 += quant_eval<2, 7, PT_UNIQUE, 5, false>(tex, M, e0, e1, sumsq, nullptr, sq);
     }
