@@ -580,18 +580,10 @@ __device__ __forceinline__ uint32_t score_rot(const uint32_t* tex, FitOut* oc, F
   return s;
 }
 
-// Search-only form of score_rot for rotations 1-3: the texels' bytes are permuted so that
-// the rotated channel sits in byte 2 and the colour channels keep their order in bytes 0-1;
-// the errors equal score_rot's (every step of the fit is symmetric in the channel positions,
-// and the order of the colour channels, which decides ties, is kept).
-template <int MODE, int ISB>
-__device__ __forceinline__ uint32_t score_rot_n(const uint32_t* tex, uint32_t sel, const uint16_t* sq) {
-  constexpr int CB = MODE == 4 ? 5 : 7, AB = MODE == 4 ? 6 : 8;
-  constexpr int CIB = MODE == 4 ? (ISB ? 3 : 2) : 2, AIB = MODE == 4 ? (ISB ? 2 : 3) : 2;
-  return fit_subset<CIB, 3, PT_NONE, CB, false>(tex, mem_all(), nullptr, sq, sel) +
-         fit_subset<AIB, 4, PT_NONE, AB, false>(tex, mem_all(), nullptr, sq, sel);
-}
-
+// Rotations 1-3 in the search: the texels' bytes are permuted so that the rotated channel sits in
+// byte 2 and the colour channels keep their order in bytes 0-1; the errors equal score_rot's
+// (every step of the fit is symmetric in the channel positions, and the order of the colour
+// channels, which decides ties, is kept).
 __device__ __forceinline__ uint32_t rot_sel(int rot) {
   // byte 2 <- rotated channel; bytes 0-1 <- the other two in order; byte 3 <- 0
   return rot == 1 ? 0x4021u : (rot == 2 ? 0x4120u : 0x4210u);
@@ -649,17 +641,44 @@ __device__ __noinline__ int search_best(const uint32_t* tex, uint32_t* best_sse,
     CAND(s7, 221 + p);
   }
   if (SYNC) __syncthreads();
-  CAND((score_rot<4, 0, 0>(tex, nullptr, nullptr, sq)), 208);
+  // Modes 4 and 5 over all 16 texels: mode 5's 2-bit colour prefit equals mode 4's (index
+  // selection 0) and its 2-bit alpha prefit equals mode 4's (index selection 1), rotation by
+  // rotation, so mode 5 takes them from there (the rotated forms permute the texels' bytes: the
+  // rotated channel to byte 2, the others in order).
+  Prefit pr[2][4];  // [colour, alpha][rotation]
+  {
+    int e0[3] = {0, 0, 0}, e1[3] = {0, 0, 0}, sumsq = 0;
+    prefit<2, 7>(tex, mem_all(), e0, e1, sumsq);
+    CAND((quant_eval<2, 7, PT_NONE, 5, false>(tex, mem_all(), e0, e1, sumsq, nullptr, sq)), 208);
+    CAND((quant_eval<2, 7, PT_NONE, 7, false>(tex, mem_all(), e0, e1, sumsq, nullptr, sq)), 216);
+  }
   CAND((score_rot<4, 0, 1>(tex, nullptr, nullptr, sq)), 209);
-  CAND((score_rot<5, 0, 0>(tex, nullptr, nullptr, sq)), 216);
 #pragma unroll 1
-  for (int rot = 1; rot <= 3; rot++) CAND((score_rot_n<4, 0>(tex, rot_sel(rot), sq)), 208 + 2 * rot);
+  for (int rot = 1; rot <= 3; rot++) {
+    const uint32_t sel = rot_sel(rot);
+    Prefit& f = pr[0][rot];
+    prefit<2, 3>(tex, mem_all(), f.e0, f.e1, f.sumsq, sel);
+    const uint32_t c = quant_eval<2, 3, PT_NONE, 5, false>(tex, mem_all(), f.e0, f.e1, f.sumsq, nullptr, sq, sel);
+    CAND((c + fit_subset<3, 4, PT_NONE, 6, false>(tex, mem_all(), nullptr, sq, sel)), 208 + 2 * rot);
+  }
   if (SYNC) __syncthreads();
 #pragma unroll 1
-  for (int rot = 1; rot <= 3; rot++) CAND((score_rot_n<4, 1>(tex, rot_sel(rot), sq)), 209 + 2 * rot);
+  for (int rot = 1; rot <= 3; rot++) {
+    const uint32_t sel = rot_sel(rot);
+    Prefit& f = pr[1][rot];
+    prefit<2, 4>(tex, mem_all(), f.e0, f.e1, f.sumsq, sel);
+    const uint32_t a = quant_eval<2, 4, PT_NONE, 6, false>(tex, mem_all(), f.e0, f.e1, f.sumsq, nullptr, sq, sel);
+    CAND((fit_subset<3, 3, PT_NONE, 5, false>(tex, mem_all(), nullptr, sq, sel) + a), 209 + 2 * rot);
+  }
   if (SYNC) __syncthreads();
 #pragma unroll 1
-  for (int rot = 1; rot <= 3; rot++) CAND((score_rot_n<5, 0>(tex, rot_sel(rot), sq)), 216 + rot);
+  for (int rot = 1; rot <= 3; rot++) {
+    const uint32_t sel = rot_sel(rot);
+    const Prefit &fc = pr[0][rot], &fa = pr[1][rot];
+    CAND((quant_eval<2, 3, PT_NONE, 7, false>(tex, mem_all(), fc.e0, fc.e1, fc.sumsq, nullptr, sq, sel) +
+          quant_eval<2, 4, PT_NONE, 8, false>(tex, mem_all(), fa.e0, fa.e1, fa.sumsq, nullptr, sq, sel)),
+         216 + rot);
+  }
   CAND((score_part<1, 4, PT_UNIQUE, 7>(tex, 0, sq)), 220);
 #undef CAND
   *best_sse = best;
